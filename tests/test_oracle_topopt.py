@@ -1,0 +1,105 @@
+"""Pins of the oracle's topology-optimisation step (Sec. 5).
+
+Independent checks: filter partition of unity, adjoint sensitivities against
+central finite differences of the compliance, exact volume after the OC
+bisection, bounds/move limits, compliance = energy, and the (empirical,
+reading Q22) monotone decrease of compliance over the first Picard steps.
+"""
+import numpy as np
+
+from oracle import direct, fem, topopt
+import workloads
+
+
+def test_filter_partition_of_unity():
+    H = topopt.filter_matrix((12, 7), 1.5)
+    assert np.allclose(H.sum(axis=1), 1.0)
+    x = np.random.default_rng(0).uniform(size=84)
+    assert np.allclose(H @ np.full(84, 0.37), 0.37)
+    # interior row: 3x3 stencil with weights 1.5 (centre), 0.5 (edge), 1.5-sqrt2
+    W = H.toarray()
+    e = 5 * 7 + 3
+    row = W[e]
+    assert np.count_nonzero(row) == 9
+    ref = np.array([1.5 - np.sqrt(2), 0.5, 1.5 - np.sqrt(2), 0.5, 1.5, 0.5,
+                    1.5 - np.sqrt(2), 0.5, 1.5 - np.sqrt(2)])
+    assert np.allclose(row[row > 0], ref / ref.sum())
+    assert 0 <= (H @ x).min() and (H @ x).max() <= 1
+
+
+def _mbb(nx, ny):
+    grid = fem.Grid(2, nx, ny)
+    fixed, f = fem.bc_from_spec(grid, workloads.mbb_half_2d(nx, ny))
+    Ke = fem.element_stiffness(2, 1.0, 0.3)
+    return grid, fixed, f, Ke
+
+
+def test_sensitivity_vs_finite_differences():
+    nx, ny = 8, 4
+    grid, fixed, f, Ke, = _mbb(nx, ny)
+    H = topopt.filter_matrix((nx, ny), 1.5)
+    rho = np.random.default_rng(1).uniform(0.3, 0.9, grid.n_elem)
+    p, E = 3.0, 1.0
+
+    def comp(r):
+        rf = H @ r
+        K = fem.assemble(grid, Ke, E * rf ** p)
+        u = direct.solve(K, f, fixed)
+        return f @ u, u, rf
+
+    c0, u, rf = comp(rho)
+    _, dcf = topopt.compliance_and_sensitivity(grid, Ke, E, p, rf, u, f)
+    dc = H.T @ dcf
+    h = 1e-6
+    for j in (0, 5, 13, 22, 31):
+        e = np.zeros_like(rho)
+        e[j] = h
+        fd = (comp(rho + e)[0] - comp(rho - e)[0]) / (2 * h)
+        assert np.isclose(dc[j], fd, rtol=1e-6, atol=1e-9 * abs(c0))
+
+
+def test_compliance_equals_energy_and_positive():
+    grid, fixed, f, Ke = _mbb(16, 8)
+    rho = np.full(grid.n_elem, 0.4)
+    K = fem.assemble(grid, Ke, rho ** 3)
+    u = direct.solve(K, f, fixed)
+    assert f @ u > 0
+    assert np.isclose(f @ u, u @ (K @ u), rtol=1e-12)
+
+
+def test_oc_volume_bounds_move():
+    rng = np.random.default_rng(2)
+    n = 200
+    rho = rng.uniform(0.05, 0.95, n)
+    dc = -rng.uniform(0.1, 10, n)
+    dv = rng.uniform(0.5, 1.5, n)
+    target = 0.4 * dv.sum()
+    new, lam = topopt.oc_update(rho, dc, dv, target, rho_min=1e-3, move=0.2)
+    assert abs(dv @ new - target) <= 1e-9 * target
+    assert np.all(new >= np.maximum(1e-3, rho - 0.2) - 1e-15)
+    assert np.all(new <= np.minimum(1.0, rho + 0.2) + 1e-15)
+    # stationarity form: free entries satisfy new = rho sqrt(-dc/(lam dv))
+    free = (new > np.maximum(1e-3, rho - 0.2) + 1e-12) & (new < np.minimum(1, rho + 0.2) - 1e-12)
+    assert free.any()
+    assert np.allclose(new[free], rho[free] * np.sqrt(-dc[free] / (lam * dv[free])), rtol=1e-12)
+
+
+def test_compliance_decreases_mbb():
+    # reading Q22: monotone decrease over the first steps of a small MBB run
+    nx, ny = 32, 16
+    grid, fixed, f, Ke = _mbb(nx, ny)
+    H = topopt.filter_matrix((nx, ny), 1.5)
+    rho = np.full(grid.n_elem, 0.4)
+
+    def solve(fac):
+        return direct.solve(fem.assemble(grid, Ke, fac), f, fixed)
+
+    cs = []
+    for _ in range(20):
+        rho, c, u, rf = topopt.topopt_step(grid, Ke, 1.0, 3.0, H, rho, f, solve, 0.4)
+        cs.append(c)
+        assert abs((H @ rho).sum() - 0.4 * grid.n_elem) <= 1e-9 * grid.n_elem
+        assert rho.min() >= 1e-3 - 1e-15 and rho.max() <= 1 + 1e-15
+    cs = np.array(cs)
+    assert np.all(cs[1:] <= cs[:-1] * (1 + 1e-6))
+    assert cs[-1] < 0.5 * cs[0]
