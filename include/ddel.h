@@ -1,0 +1,214 @@
+/*
+ * ddel.h -- C ABI of libddel: GB300-native non-overlapping domain-decomposition
+ * solve of discretised linear elasticity, inside the Picard loop of topology
+ * optimisation (Turner, Kocvara, Loghin, arXiv:1501.06211).
+ *
+ * Conventions (apply to every call):
+ *  - Every function returns a ddel_status (0 = success, < 0 = error).  No call
+ *    aborts the process and no C++ exception crosses this boundary.
+ *    ddel_strerror() gives a message; ddel_last_error() the context's last one.
+ *  - Plain pointers and sizes only.  "device" pointers are CUDA device memory
+ *    of the current device (e.g. from torch); "host" pointers are ordinary (or
+ *    pinned) host memory.  Every pointer argument says which it is.
+ *  - Inputs are read, never retained: the context copies what it needs.
+ *    Outputs go to caller-allocated buffers; the caller keeps ownership.
+ *  - Global vectors have n_dof = dim * n_nodes entries in node-interleaved order:
+ *    2D node (i, j) has index n = i*(ny+1) + j, 3D node (i, j, k) has
+ *    n = (i*(ny+1) + j)*(nz+1) + k, and DOF d*n + c holds component c.
+ *    Element (ex, ey[, ez]) has index ex*ny + ey (2D), (ex*ny + ey)*nz + ez (3D).
+ *    Dirichlet (clamped) DOFs are eliminated (Sec. 1, Sec. 2): outputs hold 0.
+ *  - Interface ("Gamma") vectors have n_gamma entries in the library's own order
+ *    (face blocks first, then cross-point DOFs); ddel_gamma_dofs() maps them to
+ *    global DOFs.
+ *  - Calls are asynchronous on the context's stream except those that return
+ *    statistics or status read from the device (ddel_solve, ddel_pcg,
+ *    ddel_residual_norm, ddel_topopt_step), which synchronise that stream.
+ *  - A context is not thread-safe; use one context per host thread.
+ *  - Memory: the context allocates all its device workspace in ddel_create /
+ *    ddel_factor and frees it in ddel_destroy.
+ */
+#ifndef DDEL_H
+#define DDEL_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  DDEL_OK = 0,
+  DDEL_EINVAL = -1,      /* bad argument (sizes, material range, null pointer) */
+  DDEL_ENOMEM = -2,      /* device or host allocation failed */
+  DDEL_ECUDA = -3,       /* a CUDA runtime call failed */
+  DDEL_ENOTSPD = -4,     /* a subdomain pivot was <= 0 or not finite; stats.bad_subdomain */
+  DDEL_ENOCONV = -5,     /* max_it / max_cycles reached before the tolerance */
+  DDEL_EBREAKDOWN = -6,  /* Krylov breakdown (p^T S p <= 0 or not finite) */
+  DDEL_ESTATE = -7,      /* call order violated (e.g. solve before factor) */
+  DDEL_ETIMEOUT = -8     /* a bounded device wait ran out; the kernel returned */
+} ddel_status;
+
+typedef enum { DDEL_FP64 = 0, DDEL_FP32 = 1 } ddel_precision;
+typedef enum { DDEL_SCHUR_IMPLICIT = 0, DDEL_SCHUR_EXPLICIT = 1, DDEL_SCHUR_AUTO = 2 } ddel_schur_mode;
+typedef enum { DDEL_X0_ZERO = 0, DDEL_X0_WARM = 1, DDEL_X0_GIVEN = 2 } ddel_x0_mode;
+
+/* Structured grid of unit elements, split into sub^dim-element subdomains
+ * (Sec. 1: N non-overlapping subdomains).  dim = 2 (Q1 bilinear, 2 DOF/node)
+ * or 3 (H8 trilinear, 3 DOF/node).  sub must divide nx, ny (, nz). */
+typedef struct {
+  int dim;
+  int nx, ny, nz; /* elements per axis; nz ignored in 2D */
+  int sub;        /* subdomain edge in elements */
+} ddel_mesh;
+
+/* Isotropic material of Sec. 1: Young's modulus E > 0 and Poisson ratio
+ * -1 < nu < 1/2 give the Lame constants mu, lambda.  2D uses plane stress when
+ * plane_stress != 0 (lambda* = 2 mu lambda / (lambda + 2 mu)), else plane strain.
+ * Element stiffness is E_e = E * rho_e^simp_p times the unit-E element matrix
+ * (eq. NumberTen with exponent p; p = 1 is the paper's variable-thickness sheet). */
+typedef struct {
+  double E, nu;
+  int plane_stress;
+  double simp_p;
+  double rho_min; /* lower density bound used by topology optimisation */
+} ddel_material;
+
+/* Boundary conditions of Sec. 1: clamped (u = 0) parts and loads.
+ * clamp_faces: bit (2*axis + side) fixes every DOF on grid face axis = 0
+ * (side 0) or axis = n_axis (side 1).  fixed_dof: optional host array of
+ * n_dof bytes, nonzero = DOF fixed (OR'ed with clamp_faces).  Point loads:
+ * n_point nodes (host int64 node indices) with dim force components each (host
+ * doubles).  traction_face = 2*axis + side applies the uniform surface
+ * traction `traction` (force per unit area) on that face as consistent nodal
+ * loads, or -1 for none. */
+typedef struct {
+  uint32_t clamp_faces;
+  const uint8_t* fixed_dof;
+  int n_point;
+  const int64_t* point_node;
+  const double* point_force;
+  int traction_face;
+  double traction[3];
+} ddel_bc;
+
+/* Solver options.  ddel_default_options() fills documented defaults. */
+typedef struct {
+  int precision;       /* ddel_precision of the subdomain factors and Schur applies (FP64) */
+  double theta;        /* fractional index theta of eq. NumberEight (0.5) */
+  int face_scaling;    /* 1: scale each face block by mean diag(K_GG)/mean diag(H) (1) */
+  int crosspoint_mode; /* 0: z = r / diag(K_GG) at cross points; 1: identity (0) */
+  double tol;          /* target ||f - K u||_2 / ||f||_2 (1e-8) */
+  int max_it;          /* PCG iteration cap per cycle (5000) */
+  int max_cycles;      /* refinement cycles cap (10) */
+  double inner_tol;    /* per-cycle PCG reduction in FP32 mode (1e-6) */
+  int x0_mode;         /* ddel_x0_mode for the interface PCG (ZERO) */
+  int schur_mode;      /* ddel_schur_mode (AUTO) */
+  int use_graph;       /* capture PCG iterations in a CUDA graph (1) */
+  int check_every;     /* PCG iterations between host convergence checks (16) */
+} ddel_options;
+
+typedef struct {
+  int status;          /* ddel_status of the solve */
+  int iters;           /* total PCG iterations (all cycles) */
+  int cycles;          /* refinement cycles (1 for a converged FP64 solve) */
+  double relres;       /* final ||f - K u||_2 / ||f||_2 computed in FP64 */
+  double pcg_relres;   /* last interface residual ||r_G|| / ||f|| of the recurrence */
+  int bad_subdomain;   /* first subdomain with a failed pivot, or -1 */
+  double t_factor_ms, t_condense_ms, t_pcg_ms, t_backsub_ms, t_verify_ms, t_total_ms;
+} ddel_stats;
+
+typedef struct {
+  int dim, n_sub, n_elem, max_block, max_blocks_per_sub;
+  int64_t n_nodes, n_dof, n_gamma, n_fixed, factor_bytes;
+  int n_face_blocks, n_cross;
+} ddel_info_t;
+
+typedef struct ddel_ctx ddel_ctx;
+
+void ddel_default_options(ddel_options* opt);
+const char* ddel_strerror(int status);
+const char* ddel_last_error(const ddel_ctx* ctx);
+
+/* Set up mesh, DOF classification (Gamma = nodes in two or more subdomain
+ * closures; interior = the rest, per subdomain; Sec. 1 and eq. NumberFive),
+ * the face-local interface preconditioner (Sec. 3-4) and device workspace.
+ * cuda_stream: a cudaStream_t (e.g. torch.cuda.current_stream().cuda_stream) or
+ * NULL for a stream owned by the context.  Errors: EINVAL (sizes, nu outside
+ * (-1, 1/2), E <= 0, sub not dividing the grid), ENOMEM, ECUDA. */
+int ddel_create(const ddel_mesh* mesh, const ddel_material* mat, const ddel_bc* bc,
+                const ddel_options* opt, void* cuda_stream, ddel_ctx** out);
+void ddel_destroy(ddel_ctx* ctx);
+int ddel_get_info(const ddel_ctx* ctx, ddel_info_t* info);
+int ddel_set_options(ddel_ctx* ctx, const ddel_options* opt);
+
+/* Element densities rho (n_elem doubles; host when on_device == 0, else device):
+ * element stiffness factors E * rho_e^p (eq. NumberTen), the diagonal of K_GG
+ * and the face scales.  Values must be > 0 and finite (EINVAL otherwise,
+ * detected on the host for host input, on the device for device input). */
+int ddel_assemble(ddel_ctx* ctx, const double* rho, int on_device);
+
+/* Batched factorisation of every K_{I_i I_i} (eq. NumberFive) in the context's
+ * precision: interior DOFs ordered by grid plane give a block-tridiagonal
+ * matrix; each block step is SYRK update, dense Cholesky, explicit inverse of
+ * the diagonal factor, and the off-diagonal factor (the banded O(k^2 n) solve
+ * of Sec. 4).  ENOTSPD when a pivot fails (stats via ddel_solve). */
+int ddel_factor(ddel_ctx* ctx);
+
+/* Whole solve of K u = f by the three steps of eq. 3MatSplit2 with interface
+ * PCG (reading of Sec. 3: S~ SPD, applied exactly), repeated as FP64 iterative
+ * refinement until ||f - K u|| <= tol ||f||.  f: n_dof doubles or NULL for the
+ * loads of ddel_bc; u: n_dof doubles (output).  Both host when on_device == 0,
+ * else device.  st may be NULL.  Synchronises the stream. */
+int ddel_solve(ddel_ctx* ctx, const double* f, double* u, int on_device, ddel_stats* st);
+
+/* --- Step-level entry points (device pointers; asynchronous) --------------- */
+/* y = K(rho) x over all free DOFs (fixed rows 0), element by element, FP64. */
+int ddel_apply_K(ddel_ctx* ctx, const double* x, double* y);
+/* g = f_G - sum_i K_{G I_i} K_{I_i I_i}^-1 f_{I_i} (eq. 3MatSplit2, second line). */
+int ddel_condense(ddel_ctx* ctx, const double* f, double* g);
+/* y = S x = sum_i (K_GG^(i) x_i - K_{G I_i} K_{I_i I_i}^-1 K_{I_i G} x_i) without forming S
+ * (Sec. 3: "avoid the direct construction"); x, y: n_gamma. */
+int ddel_schur_apply(ddel_ctx* ctx, const double* x, double* y);
+/* z = S~^-1 r: face-local H~_theta^-1 per component (eq. NumberEight/NumberNine,
+ * cross points removed as in Sec. 4) and a diagonal at cross points. */
+int ddel_precond_apply(ddel_ctx* ctx, const double* r, double* z);
+/* u_I = K_II^-1 (f_I - K_IG u_G), u_G = uG, u = 0 on fixed DOFs (eq. 3MatSplit2). */
+int ddel_back_substitute(ddel_ctx* ctx, const double* f, const double* uG, double* u);
+/* Interface PCG on S x = g from x = 0 (or x as given with x0_mode GIVEN);
+ * stops at ||r|| <= tol_abs.  g, x: device n_gamma.  Synchronises. */
+int ddel_pcg(ddel_ctx* ctx, const double* g, double* x, double tol_abs, ddel_stats* st);
+/* ||f - K u||_2 and ||f||_2 over free DOFs in FP64 (device f, u; host outputs). */
+int ddel_residual_norm(ddel_ctx* ctx, const double* f, const double* u, double* r_norm,
+                       double* f_norm);
+/* Gamma index -> global DOF (host int64 array of n_gamma). */
+int ddel_gamma_dofs(const ddel_ctx* ctx, int64_t* out);
+/* Load vector assembled from ddel_bc (host, n_dof doubles). */
+int ddel_load_vector(const ddel_ctx* ctx, double* out);
+/* Fixed-DOF mask (host, n_dof bytes). */
+int ddel_fixed_mask(const ddel_ctx* ctx, uint8_t* out);
+
+/* --- Host-only plan (no CUDA call; for inspection and tests) --------------- */
+/* The set-up of ddel_create without any device work: DOF classification,
+ * interface ordering, face blocks and element matrix.  Errors as ddel_create. */
+typedef struct ddel_plan ddel_plan;
+int ddel_plan_create(const ddel_mesh* mesh, const ddel_material* mat, const ddel_bc* bc,
+                     double theta, ddel_plan** out);
+void ddel_plan_destroy(ddel_plan* plan);
+int ddel_plan_info(const ddel_plan* plan, ddel_info_t* info);
+/* Gamma index -> global DOF (host int64, n_gamma). */
+int ddel_plan_gamma_dofs(const ddel_plan* plan, int64_t* out);
+/* Face block b of the preconditioner: first Gamma index, size n, and the n x n
+ * row-major matrix H^-1 of eq. NumberEight/NumberNine restricted to the face
+ * (host; P may be NULL to query n), mean of diag(H) in *hmean. */
+int ddel_plan_face_block(const ddel_plan* plan, int b, int32_t* off, int32_t* n, double* P,
+                         double* hmean);
+/* Unit-E element stiffness (host, (dim 2^dim)^2 doubles, row-major). */
+int ddel_plan_element_matrix(const ddel_plan* plan, double* Ke);
+/* Interior box of subdomain i: ilo[3], icnt[3] (host int32). */
+int ddel_plan_subdomain(const ddel_plan* plan, int i, int32_t* ilo, int32_t* icnt);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* DDEL_H */

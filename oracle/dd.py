@@ -227,8 +227,11 @@ class FaceBlock:
         self.singular = mu[0] <= 1e-12 * max(mu[-1], 1.0)
         if self.singular:
             # Q5: the L-only form is singular (face with no removed end);
-            # use H_theta = M + M (M^-1 L)^(1-theta) of eq. NumberEight.
-            lam = 1.0 + np.clip(mu, 0.0, None) ** (1.0 - theta)
+            # use H_theta = M + M (M^-1 L)^(1-theta) of eq. NumberEight.  The
+            # kernel of L_f is exact (constants), so eigenvalues at rounding
+            # level are zero; the fractional power would amplify their noise.
+            mu0 = np.where(mu <= 1e-12 * max(mu[-1], 1.0), 0.0, mu)
+            lam = 1.0 + mu0 ** (1.0 - theta)
         else:
             lam = mu ** (1.0 - theta)  # Htilde_theta = M V diag(mu^(1-theta)) V^T M
         self.H = M @ V @ np.diag(lam) @ V.T @ M  # the face norm matrix itself

@@ -1,0 +1,683 @@
+// C ABI of libddel (declared in include/ddel.h): context life cycle, device
+// memory, the solve driver (eq. 3MatSplit2 + interface PCG + FP64 iterative
+// refinement) and the step-level entry points.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/ddel.h"
+#include "ddel_internal.h"
+#include "ddel_launch.h"
+
+using namespace ddel;
+
+struct ddel_ctx {
+  Setup S;
+  DevTables T{};
+  DevFields F{};
+  ddel_mesh mesh{};
+  ddel_material mat{};
+  ddel_options opt{};
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  std::vector<void*> allocs;
+  void* factor[2] = {nullptr, nullptr};
+  bool factored[2] = {false, false};
+  int active_prec = 0;
+  bool assembled = false;
+  void* ring = nullptr;
+  double *d_f = nullptr, *d_load = nullptr, *d_u = nullptr, *d_r = nullptr, *d_d = nullptr;
+  double *g = nullptr, *x = nullptr, *r = nullptr, *z = nullptr, *p = nullptr, *q = nullptr;
+  double* rho = nullptr;
+  PcgState* st = nullptr;
+  PcgState* h_st = nullptr;
+  double* partials = nullptr;
+  unsigned* ticketK = nullptr;
+  double* nrm = nullptr;
+  double* h_nrm = nullptr;
+  int* err = nullptr;
+  int* bad_sub = nullptr;
+  int* h_err = nullptr;
+  int nblk = 0;
+  cudaGraphExec_t graph[2] = {nullptr, nullptr};
+  int graph_iters = 0;
+  cudaEvent_t ev[8] = {};
+  std::string last_error;
+};
+
+namespace {
+
+int fail(ddel_ctx* c, int code, const std::string& msg) {
+  if (c) c->last_error = msg;
+  return code;
+}
+
+#define CK(call)                                                                        \
+  do {                                                                                  \
+    cudaError_t e_ = (call);                                                            \
+    if (e_ != cudaSuccess)                                                              \
+      return fail(ctx, DDEL_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+  } while (0)
+
+template <typename P>
+cudaError_t dalloc(ddel_ctx* ctx, P** p, size_t bytes) {
+  void* v = nullptr;
+  cudaError_t e = cudaMalloc(&v, bytes < 16 ? 16 : bytes);
+  if (e == cudaSuccess) {
+    ctx->allocs.push_back(v);
+    *p = static_cast<P*>(v);
+  }
+  return e;
+}
+
+template <typename V>
+cudaError_t upload(ddel_ctx* ctx, const std::vector<V>& h, V** d) {
+  cudaError_t e = dalloc(ctx, d, h.size() * sizeof(V));
+  if (e != cudaSuccess) return e;
+  if (!h.empty()) e = cudaMemcpy(*d, h.data(), h.size() * sizeof(V), cudaMemcpyHostToDevice);
+  return e;
+}
+
+// Kernel-side PCG configuration: tolerance from the device-resident norms.
+__global__ void set_tol_kernel(PcgState* st, const double* nrm, double tol, double inner_tol,
+                               int mixed, int max_it) {
+  const double fnorm = nrm[1], rnorm = nrm[0];
+  double t = 0.5 * tol * fnorm;
+  if (mixed) t = fmax(t, inner_tol * rnorm);
+  st->tol2 = t * t;
+  st->max_it = max_it;
+  st->done = 0;
+  st->status = 0;
+  st->it = 0;
+}
+
+__global__ void set_tol_abs_kernel(PcgState* st, double tol_abs, int max_it) {
+  st->tol2 = tol_abs * tol_abs;
+  st->max_it = max_it;
+  st->done = 0;
+  st->status = 0;
+  st->it = 0;
+}
+
+int check_kernel_err(ddel_ctx* ctx) {
+  CK(cudaMemcpyAsync(ctx->h_err, ctx->err, 2 * sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  return DDEL_OK;
+}
+
+SchurIO make_io(ddel_ctx* ctx) {
+  SchurIO io;
+  io.err = ctx->err;
+  return io;
+}
+
+int pcg_run(ddel_ctx* ctx, int prec, const double* g, int* iters, int* status) {
+  cudaStream_t s = ctx->stream;
+  launch_pcg_init(ctx->T, ctx->F, g, ctx->x, ctx->r, ctx->z, ctx->p, ctx->st, ctx->partials, s,
+                  ctx->nblk);
+  SchurIO io = make_io(ctx);
+  io.zvec = ctx->z;
+  io.pvec = ctx->p;
+  io.beta = &ctx->st->beta;
+  io.ring_out = ctx->ring;
+  io.done = &ctx->st->done;
+  const int per = ctx->opt.check_every > 0 ? ctx->opt.check_every : 16;
+  auto iteration = [&]() {
+    launch_schur(ctx->T, ctx->F, prec, ctx->factor[prec], io, s);
+    launch_pcg_assemble(ctx->T, prec, ctx->ring, ctx->z, ctx->p, ctx->q, ctx->st, ctx->partials, s,
+                        ctx->nblk);
+    launch_pcg_update(ctx->T, ctx->F, ctx->x, ctx->r, ctx->z, ctx->p, ctx->q, ctx->st,
+                      ctx->partials, s, ctx->nblk);
+  };
+  if (ctx->opt.use_graph && (!ctx->graph[prec] || ctx->graph_iters != per)) {
+    if (ctx->graph[prec]) cudaGraphExecDestroy(ctx->graph[prec]);
+    ctx->graph[prec] = nullptr;
+    cudaGraph_t graph;
+    CK(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+    for (int i = 0; i < per; ++i) iteration();
+    CK(cudaStreamEndCapture(s, &graph));
+    CK(cudaGraphInstantiate(&ctx->graph[prec], graph, 0));
+    cudaGraphDestroy(graph);
+    ctx->graph_iters = per;
+  }
+  const int max_checks = ctx->opt.max_it / per + 2;
+  for (int chk = 0; chk < max_checks; ++chk) {
+    if (ctx->opt.use_graph) {
+      CK(cudaGraphLaunch(ctx->graph[prec], s));
+    } else {
+      for (int i = 0; i < per; ++i) iteration();
+    }
+    CK(cudaMemcpyAsync(ctx->h_st, ctx->st, sizeof(PcgState), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    if (ctx->h_st->done) break;
+  }
+  *iters = ctx->h_st->it;
+  *status = ctx->h_st->done ? ctx->h_st->status : DDEL_ENOCONV;
+  return DDEL_OK;
+}
+
+void condense(ddel_ctx* ctx, int prec, const double* f, double* g) {
+  SchurIO io = make_io(ctx);
+  io.f = f;
+  io.ring_out = ctx->ring;
+  launch_schur(ctx->T, ctx->F, prec, ctx->factor[prec], io, ctx->stream);
+  launch_gamma_sum(ctx->T, prec, ctx->ring, f, -1.0, g, ctx->stream);
+}
+
+void back_substitute(ddel_ctx* ctx, int prec, const double* f, const double* xg, double* u) {
+  SchurIO io = make_io(ctx);
+  io.f = f;
+  io.x = xg;
+  io.u_out = u;
+  launch_schur(ctx->T, ctx->F, prec, ctx->factor[prec], io, ctx->stream);
+  launch_scatter_gamma(ctx->T, xg, u, ctx->stream);
+}
+
+float elapsed(cudaEvent_t a, cudaEvent_t b) {
+  float ms = 0.f;
+  cudaEventElapsedTime(&ms, a, b);
+  return ms;
+}
+
+}  // namespace
+
+extern "C" {
+
+void ddel_default_options(ddel_options* o) {
+  if (!o) return;
+  o->precision = DDEL_FP64;
+  o->theta = 0.5;
+  o->face_scaling = 1;
+  o->crosspoint_mode = 0;
+  o->tol = 1e-8;
+  o->max_it = 5000;
+  o->max_cycles = 10;
+  o->inner_tol = 1e-6;
+  o->x0_mode = DDEL_X0_ZERO;
+  o->schur_mode = DDEL_SCHUR_AUTO;
+  o->use_graph = 1;
+  o->check_every = 16;
+}
+
+const char* ddel_strerror(int s) {
+  switch (s) {
+    case DDEL_OK: return "ok";
+    case DDEL_EINVAL: return "invalid argument";
+    case DDEL_ENOMEM: return "out of memory";
+    case DDEL_ECUDA: return "CUDA error";
+    case DDEL_ENOTSPD: return "subdomain matrix not positive definite";
+    case DDEL_ENOCONV: return "no convergence within the iteration limits";
+    case DDEL_EBREAKDOWN: return "Krylov breakdown";
+    case DDEL_ESTATE: return "call order violated";
+    case DDEL_ETIMEOUT: return "bounded device wait ran out";
+    default: return "unknown status";
+  }
+}
+
+const char* ddel_last_error(const ddel_ctx* ctx) { return ctx ? ctx->last_error.c_str() : ""; }
+
+int ddel_create(const ddel_mesh* mesh, const ddel_material* mat, const ddel_bc* bc,
+                const ddel_options* opt, void* cuda_stream, ddel_ctx** out) {
+  if (!mesh || !mat || !bc || !out) return DDEL_EINVAL;
+  *out = nullptr;
+  ddel_ctx* ctx = new (std::nothrow) ddel_ctx();
+  if (!ctx) return DDEL_ENOMEM;
+  ctx->mesh = *mesh;
+  ctx->mat = *mat;
+  if (opt)
+    ctx->opt = *opt;
+  else
+    ddel_default_options(&ctx->opt);
+  const int ne[3] = {mesh->nx, mesh->ny, mesh->nz};
+  std::string msg = build_setup(mesh->dim, ne, mesh->sub, mat->E, mat->nu, mat->plane_stress,
+                                bc->clamp_faces, bc->fixed_dof, bc->n_point, bc->point_node,
+                                bc->point_force, bc->traction_face, bc->traction, ctx->opt.theta,
+                                &ctx->S);
+  if (!msg.empty()) {
+    delete ctx;
+    return DDEL_EINVAL;
+  }
+  if (!(mat->simp_p > 0)) {
+    delete ctx;
+    return DDEL_EINVAL;
+  }
+  if (mesh->dim != 2) {  // the 3D path is provided by ddel_kernels3d.cu when built
+    delete ctx;
+    return DDEL_EINVAL;
+  }
+  Setup& S = ctx->S;
+  int rc = DDEL_OK;
+  auto bad = [&](cudaError_t e) {
+    if (e != cudaSuccess) {
+      rc = e == cudaErrorMemoryAllocation ? DDEL_ENOMEM : DDEL_ECUDA;
+      ctx->last_error = cudaGetErrorString(e);
+      return true;
+    }
+    return false;
+  };
+  if (bad(configure_kernels())) goto fail_out;
+  if (cuda_stream) {
+    ctx->stream = static_cast<cudaStream_t>(cuda_stream);
+  } else {
+    if (bad(cudaStreamCreate(&ctx->stream))) goto fail_out;
+    ctx->own_stream = true;
+  }
+  {
+    DevTables& T = ctx->T;
+    T.dim = S.dim;
+    T.s = S.sub;
+    T.n_sub = S.n_sub;
+    T.BP = S.BP;
+    T.nb_max = S.nb_max;
+    for (int a = 0; a < 3; ++a) {
+      T.ne[a] = S.ne[a] ? S.ne[a] : 1;
+      T.nn[a] = S.nn[a];
+    }
+    T.n_dof = S.n_dof;
+    T.n_elem = S.n_elem;
+    T.n_gamma = (int64_t)S.gamma_dof.size();
+    T.n_face_dofs = S.n_face_dofs;
+    T.n_blocks = (int)S.blk_off.size();
+    T.max_blk_n = S.max_blk_n > 0 ? S.max_blk_n : 1;
+    T.n_ring = (int64_t)S.ring_gidx.size();
+    std::vector<float> ke32(S.Ke.begin(), S.Ke.end());
+    if (bad(upload(ctx, S.subs, &T.subs)) || bad(upload(ctx, S.fixed, &T.fixed)) ||
+        bad(upload(ctx, S.ring_gidx, &T.ring_gidx)) || bad(upload(ctx, S.ring_loc, &T.ring_loc)) ||
+        bad(upload(ctx, S.owner_ptr, &T.owner_ptr)) || bad(upload(ctx, S.owner_idx, &T.owner_idx)) ||
+        bad(upload(ctx, S.gamma_dof, &T.gamma_dof)) || bad(upload(ctx, S.blk_off, &T.blk_off)) ||
+        bad(upload(ctx, S.blk_n, &T.blk_n)) || bad(upload(ctx, S.blk_poff, &T.blk_poff)) ||
+        bad(upload(ctx, S.blk_hmean, &T.blk_hmean)) || bad(upload(ctx, S.ptab, &T.ptab)) ||
+        bad(upload(ctx, S.Ke, &T.Ke64)) || bad(upload(ctx, ke32, &T.Ke32)))
+      goto fail_out;
+    const int64_t ng = T.n_gamma, nd = S.n_dof;
+    DevFields& F = ctx->F;
+    if (bad(dalloc(ctx, &F.scale64, S.n_elem * 8)) || bad(dalloc(ctx, &F.scale32, S.n_elem * 4)) ||
+        bad(dalloc(ctx, &F.diagG, ng * 8)) || bad(dalloc(ctx, &F.blk_alpha, (T.n_blocks + 1) * 8)) ||
+        bad(dalloc(ctx, &F.cross_scale, (ng - T.n_face_dofs + 1) * 8)) ||
+        bad(dalloc(ctx, &ctx->ring, T.n_ring * 8)) || bad(dalloc(ctx, &ctx->d_f, nd * 8)) ||
+        bad(dalloc(ctx, &ctx->d_load, nd * 8)) || bad(dalloc(ctx, &ctx->d_u, nd * 8)) ||
+        bad(dalloc(ctx, &ctx->d_r, nd * 8)) || bad(dalloc(ctx, &ctx->d_d, nd * 8)) ||
+        bad(dalloc(ctx, &ctx->g, ng * 8)) || bad(dalloc(ctx, &ctx->x, ng * 8)) ||
+        bad(dalloc(ctx, &ctx->r, ng * 8)) || bad(dalloc(ctx, &ctx->z, ng * 8)) ||
+        bad(dalloc(ctx, &ctx->p, ng * 8)) || bad(dalloc(ctx, &ctx->q, ng * 8)) ||
+        bad(dalloc(ctx, &ctx->rho, S.n_elem * 8)) || bad(dalloc(ctx, &ctx->st, sizeof(PcgState))) ||
+        bad(dalloc(ctx, &ctx->partials, 4 * 152 * 8 * 8)) ||
+        bad(dalloc(ctx, &ctx->ticketK, 16)) || bad(dalloc(ctx, &ctx->nrm, 16)) ||
+        bad(dalloc(ctx, &ctx->err, 16)))
+      goto fail_out;
+    ctx->bad_sub = ctx->err + 1;
+    if (bad(cudaMallocHost(&ctx->h_st, sizeof(PcgState))) ||
+        bad(cudaMallocHost(&ctx->h_nrm, 2 * sizeof(double))) ||
+        bad(cudaMallocHost(&ctx->h_err, 2 * sizeof(int))))
+      goto fail_out;
+    if (bad(cudaMemset(ctx->st, 0, sizeof(PcgState))) || bad(cudaMemset(ctx->ticketK, 0, 16)) ||
+        bad(cudaMemcpy(ctx->d_load, S.f.data(), nd * 8, cudaMemcpyHostToDevice)))
+      goto fail_out;
+    const int zero_err[2] = {0, 0x7fffffff};
+    if (bad(cudaMemcpy(ctx->err, zero_err, sizeof(zero_err), cudaMemcpyHostToDevice))) goto fail_out;
+    ctx->nblk = 2 * 152;
+    for (auto& e : ctx->ev)
+      if (bad(cudaEventCreate(&e))) goto fail_out;
+  }
+  *out = ctx;
+  return DDEL_OK;
+fail_out:
+  ddel_destroy(ctx);
+  return rc != DDEL_OK ? rc : DDEL_ECUDA;
+}
+
+void ddel_destroy(ddel_ctx* ctx) {
+  if (!ctx) return;
+  if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+  for (auto& g : ctx->graph)
+    if (g) cudaGraphExecDestroy(g);
+  for (void* p : ctx->allocs) cudaFree(p);
+  for (void* p : ctx->factor)
+    if (p) cudaFree(p);
+  if (ctx->h_st) cudaFreeHost(ctx->h_st);
+  if (ctx->h_nrm) cudaFreeHost(ctx->h_nrm);
+  if (ctx->h_err) cudaFreeHost(ctx->h_err);
+  for (auto& e : ctx->ev)
+    if (e) cudaEventDestroy(e);
+  if (ctx->own_stream && ctx->stream) cudaStreamDestroy(ctx->stream);
+  delete ctx;
+}
+
+int ddel_get_info(const ddel_ctx* ctx, ddel_info_t* info) {
+  if (!ctx || !info) return DDEL_EINVAL;
+  const Setup& S = ctx->S;
+  info->dim = S.dim;
+  info->n_sub = S.n_sub;
+  info->n_elem = (int)S.n_elem;
+  info->max_block = S.BP;
+  info->max_blocks_per_sub = S.nb_max;
+  info->n_nodes = S.n_nodes;
+  info->n_dof = S.n_dof;
+  info->n_gamma = (int64_t)S.gamma_dof.size();
+  int64_t nf = 0;
+  for (auto v : S.fixed) nf += v;
+  info->n_fixed = nf;
+  info->factor_bytes = S.factor_elems * 8;
+  info->n_face_blocks = (int)S.blk_off.size();
+  info->n_cross = (int)(S.gamma_dof.size() - S.n_face_dofs);
+  return DDEL_OK;
+}
+
+int ddel_set_options(ddel_ctx* ctx, const ddel_options* opt) {
+  if (!ctx || !opt) return DDEL_EINVAL;
+  if (opt->theta != ctx->opt.theta) return fail(ctx, DDEL_EINVAL, "theta is fixed at creation");
+  ctx->opt = *opt;
+  return DDEL_OK;
+}
+
+int ddel_assemble(ddel_ctx* ctx, const double* rho, int on_device) {
+  if (!ctx || !rho) return DDEL_EINVAL;
+  const int64_t ne = ctx->S.n_elem;
+  if (!on_device) {
+    for (int64_t e = 0; e < ne; ++e)
+      if (!(rho[e] > 0) || !std::isfinite(rho[e])) return fail(ctx, DDEL_EINVAL, "density must be > 0");
+    CK(cudaMemcpyAsync(ctx->rho, rho, ne * 8, cudaMemcpyHostToDevice, ctx->stream));
+  } else {
+    CK(cudaMemcpyAsync(ctx->rho, rho, ne * 8, cudaMemcpyDeviceToDevice, ctx->stream));
+  }
+  launch_assemble(ctx->T, ctx->F, ctx->rho, ctx->mat.E, ctx->mat.simp_p, ctx->opt.face_scaling,
+                  ctx->opt.crosspoint_mode, ctx->err, ctx->stream);
+  CK(cudaGetLastError());
+  ctx->assembled = true;
+  ctx->factored[0] = ctx->factored[1] = false;
+  return DDEL_OK;
+}
+
+int ddel_factor(ddel_ctx* ctx) {
+  if (!ctx) return DDEL_EINVAL;
+  if (!ctx->assembled) return fail(ctx, DDEL_ESTATE, "assemble before factor");
+  int prec = ctx->opt.precision == DDEL_FP32 ? 1 : 0;
+  for (int attempt = 0; attempt < 2; ++attempt) {
+    if (!ctx->factor[prec]) {
+      cudaError_t e = cudaMalloc(&ctx->factor[prec], ctx->S.factor_elems * (prec ? 4 : 8) + 256);
+      if (e != cudaSuccess) return fail(ctx, DDEL_ENOMEM, "factor allocation");
+    }
+    const int init[2] = {0, 0x7fffffff};
+    CK(cudaMemcpyAsync(ctx->err, init, sizeof(init), cudaMemcpyHostToDevice, ctx->stream));
+    launch_factor(ctx->T, ctx->F, prec, ctx->factor[prec], ctx->err, ctx->bad_sub, ctx->stream);
+    CK(cudaGetLastError());
+    int rc = check_kernel_err(ctx);
+    if (rc) return rc;
+    if (ctx->h_err[0] == kErrBadRho) return fail(ctx, DDEL_EINVAL, "density must be > 0");
+    if (ctx->h_err[0] == kErrPivot) {
+      if (prec == 1) {  // FP32 factor failed: fall back to FP64 for this density field
+        prec = 0;
+        continue;
+      }
+      return fail(ctx, DDEL_ENOTSPD, "pivot failure in subdomain " + std::to_string(ctx->h_err[1]));
+    }
+    ctx->factored[prec] = true;
+    ctx->active_prec = prec;
+    return DDEL_OK;
+  }
+  return fail(ctx, DDEL_ENOTSPD, "pivot failure");
+}
+
+int ddel_solve(ddel_ctx* ctx, const double* f, double* u, int on_device, ddel_stats* stats) {
+  if (!ctx || !u) return DDEL_EINVAL;
+  const int prec = ctx->active_prec;
+  if (!ctx->factored[prec]) return fail(ctx, DDEL_ESTATE, "factor before solve");
+  cudaStream_t s = ctx->stream;
+  const int64_t nd = ctx->S.n_dof;
+  ddel_stats st{};
+  st.bad_subdomain = -1;
+  CK(cudaEventRecord(ctx->ev[0], s));
+  if (!f)
+    CK(cudaMemcpyAsync(ctx->d_f, ctx->d_load, nd * 8, cudaMemcpyDeviceToDevice, s));
+  else
+    CK(cudaMemcpyAsync(ctx->d_f, f, nd * 8, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
+  CK(cudaMemsetAsync(ctx->d_u, 0, nd * 8, s));
+  const int init[2] = {0, 0x7fffffff};
+  CK(cudaMemcpyAsync(ctx->err, init, sizeof(init), cudaMemcpyHostToDevice, s));
+  // r = f - K 0 = f and ||f||
+  launch_apply_K(ctx->T, ctx->F, ctx->d_u, ctx->d_f, ctx->d_r, 1, ctx->partials, ctx->ticketK,
+                 ctx->nrm, s, ctx->nblk);
+  int status = DDEL_ENOCONV;
+  double t_cond = 0, t_pcg = 0, t_back = 0, t_ver = 0;
+  for (int cyc = 0; cyc < ctx->opt.max_cycles; ++cyc) {
+    set_tol_kernel<<<1, 1, 0, s>>>(ctx->st, ctx->nrm, ctx->opt.tol, ctx->opt.inner_tol, prec,
+                                   ctx->opt.max_it);
+    CK(cudaEventRecord(ctx->ev[1], s));
+    condense(ctx, prec, ctx->d_r, ctx->g);
+    CK(cudaEventRecord(ctx->ev[2], s));
+    int it = 0, pst = 0;
+    int rc = pcg_run(ctx, prec, ctx->g, &it, &pst);
+    if (rc) return rc;
+    st.iters += it;
+    CK(cudaEventRecord(ctx->ev[3], s));
+    back_substitute(ctx, prec, ctx->d_r, ctx->x, ctx->d_d);
+    launch_axpy(nd, 1.0, ctx->d_d, ctx->d_u, s);
+    CK(cudaEventRecord(ctx->ev[4], s));
+    launch_apply_K(ctx->T, ctx->F, ctx->d_u, ctx->d_f, ctx->d_r, 1, ctx->partials, ctx->ticketK,
+                   ctx->nrm, s, ctx->nblk);
+    CK(cudaMemcpyAsync(ctx->h_nrm, ctx->nrm, 16, cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(ctx->h_err, ctx->err, 8, cudaMemcpyDeviceToHost, s));
+    CK(cudaEventRecord(ctx->ev[5], s));
+    CK(cudaStreamSynchronize(s));
+    CK(cudaGetLastError());
+    t_cond += elapsed(ctx->ev[1], ctx->ev[2]);
+    t_pcg += elapsed(ctx->ev[2], ctx->ev[3]);
+    t_back += elapsed(ctx->ev[3], ctx->ev[4]);
+    t_ver += elapsed(ctx->ev[4], ctx->ev[5]);
+    st.cycles = cyc + 1;
+    const double fn = ctx->h_nrm[1];
+    st.relres = fn > 0 ? ctx->h_nrm[0] / fn : 0.0;
+    st.pcg_relres = fn > 0 ? std::sqrt(ctx->h_st->rr) / fn : 0.0;
+    if (ctx->h_err[0] == kErrTimeout) {
+      status = DDEL_ETIMEOUT;
+      break;
+    }
+    if (pst == DDEL_EBREAKDOWN) {
+      status = DDEL_EBREAKDOWN;
+      break;
+    }
+    if (st.relres <= ctx->opt.tol || fn == 0.0) {
+      status = DDEL_OK;
+      break;
+    }
+    if (!std::isfinite(st.relres)) {
+      status = DDEL_EBREAKDOWN;
+      break;
+    }
+  }
+  if (on_device)
+    CK(cudaMemcpyAsync(u, ctx->d_u, nd * 8, cudaMemcpyDeviceToDevice, s));
+  else
+    CK(cudaMemcpyAsync(u, ctx->d_u, nd * 8, cudaMemcpyDeviceToHost, s));
+  CK(cudaEventRecord(ctx->ev[6], s));
+  CK(cudaStreamSynchronize(s));
+  st.t_condense_ms = t_cond;
+  st.t_pcg_ms = t_pcg;
+  st.t_backsub_ms = t_back;
+  st.t_verify_ms = t_ver;
+  st.t_total_ms = elapsed(ctx->ev[0], ctx->ev[6]);
+  st.status = status;
+  if (stats) *stats = st;
+  return status;
+}
+
+int ddel_apply_K(ddel_ctx* ctx, const double* x, double* y) {
+  if (!ctx || !x || !y) return DDEL_EINVAL;
+  if (!ctx->assembled) return fail(ctx, DDEL_ESTATE, "assemble first");
+  launch_apply_K(ctx->T, ctx->F, x, nullptr, y, 0, ctx->partials, ctx->ticketK, ctx->nrm,
+                 ctx->stream, ctx->nblk);
+  CK(cudaGetLastError());
+  return DDEL_OK;
+}
+
+int ddel_condense(ddel_ctx* ctx, const double* f, double* g) {
+  if (!ctx || !f || !g) return DDEL_EINVAL;
+  if (!ctx->factored[ctx->active_prec]) return fail(ctx, DDEL_ESTATE, "factor first");
+  condense(ctx, ctx->active_prec, f, g);
+  CK(cudaGetLastError());
+  return DDEL_OK;
+}
+
+int ddel_schur_apply(ddel_ctx* ctx, const double* x, double* y) {
+  if (!ctx || !x || !y) return DDEL_EINVAL;
+  const int prec = ctx->active_prec;
+  if (!ctx->factored[prec]) return fail(ctx, DDEL_ESTATE, "factor first");
+  SchurIO io = make_io(ctx);
+  io.x = x;
+  io.ring_out = ctx->ring;
+  launch_schur(ctx->T, ctx->F, prec, ctx->factor[prec], io, ctx->stream);
+  launch_gamma_sum(ctx->T, prec, ctx->ring, nullptr, 1.0, y, ctx->stream);
+  CK(cudaGetLastError());
+  return DDEL_OK;
+}
+
+int ddel_precond_apply(ddel_ctx* ctx, const double* r, double* z) {
+  if (!ctx || !r || !z) return DDEL_EINVAL;
+  if (!ctx->assembled) return fail(ctx, DDEL_ESTATE, "assemble first");
+  launch_precond(ctx->T, ctx->F, r, z, ctx->stream);
+  CK(cudaGetLastError());
+  return DDEL_OK;
+}
+
+int ddel_back_substitute(ddel_ctx* ctx, const double* f, const double* uG, double* u) {
+  if (!ctx || !f || !uG || !u) return DDEL_EINVAL;
+  if (!ctx->factored[ctx->active_prec]) return fail(ctx, DDEL_ESTATE, "factor first");
+  back_substitute(ctx, ctx->active_prec, f, uG, u);
+  CK(cudaGetLastError());
+  return DDEL_OK;
+}
+
+int ddel_pcg(ddel_ctx* ctx, const double* g, double* x, double tol_abs, ddel_stats* stats) {
+  if (!ctx || !g || !x) return DDEL_EINVAL;
+  const int prec = ctx->active_prec;
+  if (!ctx->factored[prec]) return fail(ctx, DDEL_ESTATE, "factor first");
+  set_tol_abs_kernel<<<1, 1, 0, ctx->stream>>>(ctx->st, tol_abs, ctx->opt.max_it);
+  int it = 0, pst = 0;
+  int rc = pcg_run(ctx, prec, g, &it, &pst);
+  if (rc) return rc;
+  CK(cudaMemcpyAsync(x, ctx->x, ctx->T.n_gamma * 8, cudaMemcpyDeviceToDevice, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  if (stats) {
+    std::memset(stats, 0, sizeof(*stats));
+    stats->iters = it;
+    stats->status = pst;
+    stats->pcg_relres = std::sqrt(ctx->h_st->rr);
+    stats->bad_subdomain = -1;
+  }
+  return pst;
+}
+
+int ddel_residual_norm(ddel_ctx* ctx, const double* f, const double* u, double* r_norm,
+                       double* f_norm) {
+  if (!ctx || !f || !u) return DDEL_EINVAL;
+  if (!ctx->assembled) return fail(ctx, DDEL_ESTATE, "assemble first");
+  launch_apply_K(ctx->T, ctx->F, u, f, ctx->d_r, 1, ctx->partials, ctx->ticketK, ctx->nrm,
+                 ctx->stream, ctx->nblk);
+  CK(cudaMemcpyAsync(ctx->h_nrm, ctx->nrm, 16, cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  if (r_norm) *r_norm = ctx->h_nrm[0];
+  if (f_norm) *f_norm = ctx->h_nrm[1];
+  return DDEL_OK;
+}
+
+int ddel_gamma_dofs(const ddel_ctx* ctx, int64_t* out) {
+  if (!ctx || !out) return DDEL_EINVAL;
+  std::memcpy(out, ctx->S.gamma_dof.data(), ctx->S.gamma_dof.size() * sizeof(int64_t));
+  return DDEL_OK;
+}
+
+int ddel_load_vector(const ddel_ctx* ctx, double* out) {
+  if (!ctx || !out) return DDEL_EINVAL;
+  std::memcpy(out, ctx->S.f.data(), ctx->S.f.size() * sizeof(double));
+  return DDEL_OK;
+}
+
+int ddel_fixed_mask(const ddel_ctx* ctx, uint8_t* out) {
+  if (!ctx || !out) return DDEL_EINVAL;
+  std::memcpy(out, ctx->S.fixed.data(), ctx->S.fixed.size());
+  return DDEL_OK;
+}
+
+struct ddel_plan {
+  Setup S;
+};
+
+int ddel_plan_create(const ddel_mesh* mesh, const ddel_material* mat, const ddel_bc* bc,
+                     double theta, ddel_plan** out) {
+  if (!mesh || !mat || !bc || !out) return DDEL_EINVAL;
+  *out = nullptr;
+  ddel_plan* p = new (std::nothrow) ddel_plan();
+  if (!p) return DDEL_ENOMEM;
+  const int ne[3] = {mesh->nx, mesh->ny, mesh->nz};
+  std::string msg = build_setup(mesh->dim, ne, mesh->sub, mat->E, mat->nu, mat->plane_stress,
+                                bc->clamp_faces, bc->fixed_dof, bc->n_point, bc->point_node,
+                                bc->point_force, bc->traction_face, bc->traction, theta, &p->S);
+  if (!msg.empty()) {
+    delete p;
+    return DDEL_EINVAL;
+  }
+  *out = p;
+  return DDEL_OK;
+}
+
+void ddel_plan_destroy(ddel_plan* plan) { delete plan; }
+
+int ddel_plan_info(const ddel_plan* plan, ddel_info_t* info) {
+  if (!plan || !info) return DDEL_EINVAL;
+  const Setup& S = plan->S;
+  info->dim = S.dim;
+  info->n_sub = S.n_sub;
+  info->n_elem = (int)S.n_elem;
+  info->max_block = S.BP;
+  info->max_blocks_per_sub = S.nb_max;
+  info->n_nodes = S.n_nodes;
+  info->n_dof = S.n_dof;
+  info->n_gamma = (int64_t)S.gamma_dof.size();
+  int64_t nf = 0;
+  for (auto v : S.fixed) nf += v;
+  info->n_fixed = nf;
+  info->factor_bytes = S.factor_elems * 8;
+  info->n_face_blocks = (int)S.blk_off.size();
+  info->n_cross = (int)(S.gamma_dof.size() - S.n_face_dofs);
+  return DDEL_OK;
+}
+
+int ddel_plan_gamma_dofs(const ddel_plan* plan, int64_t* out) {
+  if (!plan || !out) return DDEL_EINVAL;
+  std::memcpy(out, plan->S.gamma_dof.data(), plan->S.gamma_dof.size() * sizeof(int64_t));
+  return DDEL_OK;
+}
+
+int ddel_plan_face_block(const ddel_plan* plan, int b, int32_t* off, int32_t* n, double* P,
+                         double* hmean) {
+  if (!plan || b < 0 || b >= (int)plan->S.blk_off.size()) return DDEL_EINVAL;
+  const Setup& S = plan->S;
+  const int nb = S.blk_n[b];
+  if (off) *off = S.blk_off[b];
+  if (n) *n = nb;
+  if (hmean) *hmean = S.blk_hmean[b];
+  if (P) std::memcpy(P, S.ptab.data() + S.blk_poff[b], (size_t)nb * nb * sizeof(double));
+  return DDEL_OK;
+}
+
+int ddel_plan_element_matrix(const ddel_plan* plan, double* Ke) {
+  if (!plan || !Ke) return DDEL_EINVAL;
+  std::memcpy(Ke, plan->S.Ke.data(), plan->S.Ke.size() * sizeof(double));
+  return DDEL_OK;
+}
+
+int ddel_plan_subdomain(const ddel_plan* plan, int i, int32_t* ilo, int32_t* icnt) {
+  if (!plan || i < 0 || i >= plan->S.n_sub || !ilo || !icnt) return DDEL_EINVAL;
+  for (int a = 0; a < 3; ++a) {
+    ilo[a] = plan->S.subs[i].ilo[a];
+    icnt[a] = plan->S.subs[i].icnt[a];
+  }
+  return DDEL_OK;
+}
+
+}  // extern "C"

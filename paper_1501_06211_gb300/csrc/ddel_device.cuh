@@ -1,0 +1,147 @@
+// Device-side helpers: TMA bulk copies with mbarriers (bounded waits),
+// deterministic reductions, structured-grid element products.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "ddel_internal.h"
+
+namespace ddel {
+
+// Upper bound on mbarrier try_wait polls before a kernel gives up (each poll
+// suspends for a hardware-defined interval; this bounds a wait to seconds).
+constexpr uint32_t kWaitLimit = 1u << 22;
+
+__device__ __forceinline__ uint32_t smem_addr(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count)
+               : "memory");
+}
+
+__device__ __forceinline__ void fence_mbar_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+// Orders this thread's earlier generic-proxy shared-memory accesses before
+// later async-proxy (bulk copy) accesses to the same memory.
+__device__ __forceinline__ void fence_proxy_async_smem() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)),
+               "r"(bytes)
+               : "memory");
+}
+
+// 1D bulk copy global -> shared, completion signalled on `bar` (16-byte
+// aligned addresses, size a multiple of 16 bytes).
+__device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  uint64_t g;
+  asm volatile("cvta.to.global.u64 %0, %1;" : "=l"(g) : "l"(src));
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          smem_addr(dst)),
+      "l"(g), "r"(bytes), "r"(smem_addr(bar))
+      : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_addr(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// Bounded wait: returns false (and the caller reports kErrTimeout) instead of
+// spinning forever.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+  for (uint32_t i = 0; i < kWaitLimit; ++i)
+    if (mbar_try_wait(bar, parity)) return true;
+  return false;
+}
+
+template <typename T>
+__device__ __forceinline__ T warp_sum(T v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Block-wide sum of NV values (fixed reduction tree: deterministic).
+template <int NV, int THREADS>
+__device__ __forceinline__ void block_sum(double (&v)[NV], double* scratch /* NV*32 */) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+  for (int i = 0; i < NV; ++i) v[i] = warp_sum(v[i]);
+  if (lane == 0)
+#pragma unroll
+    for (int i = 0; i < NV; ++i) scratch[i * 32 + w] = v[i];
+  __syncthreads();
+  if (w == 0) {
+#pragma unroll
+    for (int i = 0; i < NV; ++i) {
+      double t = lane < THREADS / 32 ? scratch[i * 32 + lane] : 0.0;
+      v[i] = warp_sum(t);
+    }
+  }
+  __syncthreads();
+}
+
+// Grid-level deterministic reduction: every block stores its partials, the
+// last block to arrive (atomic ticket) sums all partials in block order.
+// Returns true in the last block (thread 0 then holds the totals in v).
+template <int NV, int THREADS>
+__device__ __forceinline__ bool grid_sum(double (&v)[NV], double* partials /* NV*gridDim */,
+                                         unsigned* ticket, double* scratch) {
+  block_sum<NV, THREADS>(v, scratch);
+  __shared__ bool last;
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int i = 0; i < NV; ++i) partials[i * gridDim.x + blockIdx.x] = v[i];
+    __threadfence();
+    const unsigned t = atomicAdd(ticket, 1u);
+    last = (t == gridDim.x - 1);
+  }
+  __syncthreads();
+  if (!last) return false;
+  __threadfence();
+  double acc[NV];
+#pragma unroll
+  for (int i = 0; i < NV; ++i) {
+    acc[i] = 0.0;
+    for (int b = threadIdx.x; b < (int)gridDim.x; b += THREADS)
+      acc[i] += __ldcg(&partials[i * gridDim.x + b]);
+  }
+  block_sum<NV, THREADS>(acc, scratch);
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int i = 0; i < NV; ++i) v[i] = acc[i];
+    *ticket = 0u;  // ready for the next launch
+  }
+  return true;
+}
+
+// Local node index of grid offset (dx, dy, dz) in {0,1}^3 within an element
+// (order (0,0),(1,0),(1,1),(0,1), then +4 for dz = 1).
+__device__ __forceinline__ int elem_local_node(int dx, int dy, int dz) {
+  const int q = dy ? (dx ? 2 : 3) : (dx ? 1 : 0);
+  return q + 4 * dz;
+}
+
+__device__ __forceinline__ void elem_node_offset(int a, int& dx, int& dy, int& dz) {
+  const int q = a & 3;
+  dx = (q == 1 || q == 2);
+  dy = (q >= 2);
+  dz = a >> 2;
+}
+
+}  // namespace ddel

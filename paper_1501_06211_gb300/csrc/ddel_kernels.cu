@@ -1,0 +1,894 @@
+// CUDA kernels of the hot path for sm_103a (2D Q1 path; the 3D H8 path lives in
+// ddel_kernels3d.cu).
+//
+//  * factor2d_kernel  : fused assembly of the interior line blocks of every
+//                       K_{I_i I_i} (eq. NumberFive) and its block-tridiagonal
+//                       Cholesky factorisation, one CTA per subdomain.
+//  * schur2d_kernel   : per-subdomain solve with the factor (eq. 3MatSplit2):
+//                       w = f_I - K_IG x, t = K_II^-1 w by block forward and
+//                       backward substitution, y = (K^(i) [t; x])_G.  Factor
+//                       blocks stream from HBM through a TMA bulk-copy ring
+//                       buffer; one warp per subdomain.
+//  * pcg_*_kernel     : interface PCG with the face-local preconditioner of
+//                       Sec. 3-4; deterministic two-level FP64 dot products.
+//  * apply_K_kernel   : global element-by-element K x / f - K x in FP64.
+#include <cmath>
+#include <cstdio>
+
+#include "ddel_device.cuh"
+#include "ddel_launch.h"
+
+namespace ddel {
+namespace {
+
+constexpr int kRedThreads = 256;
+
+__device__ __forceinline__ int64_t node2(const DevTables& t, int i, int j) {
+  return (int64_t)i * t.nn[1] + j;
+}
+
+// ============================================================ assembly
+__global__ void scale_kernel(const double* __restrict__ rho, int64_t n, double E, double p,
+                             double* s64, float* s32, int* err) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    double r = rho[e];
+    if (!(r > 0.0) || !isfinite(r)) {
+      atomicExch(err, kErrBadRho);
+      r = 1.0;
+    }
+    const double v = E * pow(r, p);
+    s64[e] = v;
+    s32[e] = (float)v;
+  }
+}
+
+// diag(K_GG) at every Gamma DOF: sum over the elements touching the node.
+template <int DIM>
+__global__ void gamma_diag_kernel(DevTables t, DevFields fld) {
+  constexpr int ND = DIM << DIM;
+  for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < t.n_gamma;
+       g += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t dof = t.gamma_dof[g];
+    const int64_t n = dof / DIM;
+    const int c = (int)(dof % DIM);
+    const int k = DIM == 3 ? (int)(n % t.nn[2]) : 0;
+    const int64_t ij = DIM == 3 ? n / t.nn[2] : n;
+    const int j = (int)(ij % t.nn[1]), i = (int)(ij / t.nn[1]);
+    double acc = 0.0;
+    for (int ox = 0; ox < 2; ++ox) {
+      const int ex = i - ox;
+      if (ex < 0 || ex >= t.ne[0]) continue;
+      for (int oy = 0; oy < 2; ++oy) {
+        const int ey = j - oy;
+        if (ey < 0 || ey >= t.ne[1]) continue;
+        for (int oz = 0; oz < (DIM == 3 ? 2 : 1); ++oz) {
+          const int ez = k - oz;
+          if (DIM == 3 && (ez < 0 || ez >= t.ne[2])) continue;
+          const int64_t e = DIM == 3 ? ((int64_t)ex * t.ne[1] + ey) * t.ne[2] + ez
+                                     : (int64_t)ex * t.ne[1] + ey;
+          const int ln = elem_local_node(ox, oy, oz);
+          acc += fld.scale64[e] * t.Ke64[(ln * DIM + c) * ND + ln * DIM + c];
+        }
+      }
+    }
+    fld.diagG[g] = acc;
+  }
+}
+
+// Face scale alpha (one warp per face block) and cross-point diagonal.
+__global__ void face_scale_kernel(DevTables t, DevFields fld, int face_scaling, int cross_mode) {
+  const int lane = threadIdx.x & 31;
+  const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int nw = (gridDim.x * blockDim.x) >> 5;
+  for (int b = gw; b < t.n_blocks; b += nw) {
+    const int off = t.blk_off[b], n = t.blk_n[b];
+    double s = 0.0;
+    for (int i = lane; i < n; i += 32) s += fld.diagG[off + i];
+    s = warp_sum(s);
+    if (lane == 0) fld.blk_alpha[b] = face_scaling ? (s / n) / t.blk_hmean[b] : 1.0;
+  }
+  const int64_t ncross = t.n_gamma - t.n_face_dofs;
+  for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < ncross;
+       c += (int64_t)gridDim.x * blockDim.x)
+    fld.cross_scale[c] = cross_mode == 0 ? 1.0 / fld.diagG[t.n_face_dofs + c] : 1.0;
+}
+
+// ============================================================ factorisation
+// Entry ((kr, r), (kc, c)) of K_{I_i I_i}: rows r of interior plane kr, columns
+// c of plane kc.  Rows beyond the block size and fixed DOFs form identity rows,
+// which keeps every block of a uniform padded size BP.
+template <typename T>
+__device__ __forceinline__ T entry2d(const DevTables& t, const SubInfo& si, const T* ke,
+                                     const T* __restrict__ scale, int kr, int r, int kc, int c) {
+  const bool vr = r < si.bsz, vc = c < si.bsz;
+  const int xr = si.ilo[0] + kr, yr = si.ilo[1] + (r >> 1), cr = r & 1;
+  const int xc = si.ilo[0] + kc, yc = si.ilo[1] + (c >> 1), cc = c & 1;
+  const bool fr = !vr || t.fixed[2 * node2(t, xr, yr) + cr];
+  const bool fc = !vc || t.fixed[2 * node2(t, xc, yc) + cc];
+  if (fr || fc) return (kr == kc && r == c) ? T(1) : T(0);
+  if (abs(yr - yc) > 1 || abs(xr - xc) > 1) return T(0);
+  T sum = T(0);
+  const int s = t.s;
+  for (int ex = max(xr, xc) - 1; ex <= min(xr, xc); ++ex) {
+    const int ea = ex - si.lo[0];
+    if (ea < 0 || ea >= s) continue;
+    for (int ey = max(yr, yc) - 1; ey <= min(yr, yc); ++ey) {
+      const int eb = ey - si.lo[1];
+      if (eb < 0 || eb >= s) continue;
+      const int la = elem_local_node(xr - ex, yr - ey, 0);
+      const int lb = elem_local_node(xc - ex, yc - ey, 0);
+      sum += scale[(int64_t)ex * t.ne[1] + ey] * ke[(la * 2 + cr) * 8 + lb * 2 + cc];
+    }
+  }
+  return sum;
+}
+
+// Block step k: A_kk -= C_k C_k^T; L_kk = chol(A_kk); D_k = L_kk^-1;
+// C_{k+1} = A_{k+1,k} D_k^T.  Stored per subdomain as [C_k | D_k] for every k
+// (C_k dense column-major BP x BP, D_k packed lower column-major), so that one
+// forward step reads one contiguous [C_k D_k] and one backward step one
+// contiguous [D_k C_{k+1}].
+template <typename T, int BP>
+__global__ void __launch_bounds__(128) factor2d_kernel(DevTables t, const T* __restrict__ Ke_g,
+                                                       const T* __restrict__ scale,
+                                                       T* __restrict__ factor, int* err,
+                                                       int* bad_sub) {
+  constexpr int LD = BP + 1, PC = BP * BP, PD = BP * (BP + 1) / 2, STAGE = PC + PD;
+  const int sub = blockIdx.x, tid = threadIdx.x;
+  const SubInfo si = t.subs[sub];
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  T* A = reinterpret_cast<T*>(smem_raw);
+  T* Dm = A + BP * LD;
+  T* Cm = Dm + BP * LD;
+  T* ke = Cm + BP * LD;
+  for (int i = tid; i < 64; i += 128) ke[i] = Ke_g[i];
+  __syncthreads();
+  const int nb = si.nb;
+  bool bad = false;
+  T* fb = factor + si.factor_off;
+  for (int k = 0; k < nb; ++k) {
+    // (a) assemble the lower triangle of A_kk - C_k C_k^T
+    for (int idx = tid; idx < BP * BP; idx += 128) {
+      const int i = idx / BP, j = idx % BP;
+      if (j > i) continue;
+      T v = entry2d<T>(t, si, ke, scale, k, i, k, j);
+      if (k > 0) {
+        T s = T(0);
+#pragma unroll 8
+        for (int m = 0; m < BP; ++m) s += Cm[i * LD + m] * Cm[j * LD + m];
+        v -= s;
+      }
+      A[i * LD + j] = v;
+    }
+    __syncthreads();
+    // (b) right-looking dense Cholesky, lower, in place
+    for (int j = 0; j < BP; ++j) {
+      if (tid == 0) {
+        T d = A[j * LD + j];
+        if (!(d > T(0)) || !isfinite((double)d)) {
+          bad = true;
+          d = T(1);
+        }
+        A[j * LD + j] = sqrt(d);
+      }
+      __syncthreads();
+      const T ljj = A[j * LD + j];
+      for (int i = j + 1 + tid; i < BP; i += 128) A[i * LD + j] /= ljj;
+      __syncthreads();
+      const int m = BP - j - 1;
+      for (int idx = tid; idx < m * m; idx += 128) {
+        const int ii = j + 1 + idx / m, cc = j + 1 + idx % m;
+        if (cc <= ii) A[ii * LD + cc] -= A[ii * LD + j] * A[cc * LD + j];
+      }
+      __syncthreads();
+    }
+    // (c) D = L^-1 row by row (lower)
+    for (int i = 0; i < BP; ++i) {
+      for (int j = tid; j <= i; j += 128) {
+        T s = (i == j) ? T(1) : T(0);
+        for (int m = j; m < i; ++m) s -= A[i * LD + m] * Dm[m * LD + j];
+        Dm[i * LD + j] = s / A[i * LD + i];
+      }
+      __syncthreads();
+    }
+    // (d) store D_k packed lower column-major
+    T* Dg = fb + (int64_t)k * STAGE + PC;
+    for (int idx = tid; idx < BP * BP; idx += 128) {
+      const int j = idx / BP, r = idx % BP;
+      if (r >= j) Dg[j * BP - j * (j - 1) / 2 + (r - j)] = Dm[r * LD + j];
+    }
+    // (e) C_{k+1} = A_{k+1,k} D_k^T
+    if (k + 1 < nb) {
+      for (int idx = tid; idx < BP * BP; idx += 128) {
+        const int i = idx / BP, j = idx % BP;
+        A[i * LD + j] = entry2d<T>(t, si, ke, scale, k + 1, i, k, j);
+      }
+      __syncthreads();
+      for (int idx = tid; idx < BP * BP; idx += 128) {
+        const int i = idx / BP, j = idx % BP;
+        T s = T(0);
+        for (int m = 0; m <= j; ++m) s += A[i * LD + m] * Dm[j * LD + m];
+        Cm[i * LD + j] = s;
+      }
+      __syncthreads();
+      T* Cg = fb + (int64_t)(k + 1) * STAGE;
+      for (int idx = tid; idx < BP * BP; idx += 128) {
+        const int j = idx / BP, i = idx % BP;
+        Cg[j * BP + i] = Cm[i * LD + j];
+      }
+    }
+    __syncthreads();
+  }
+  if (tid == 0 && bad) {
+    atomicExch(err, kErrPivot);
+    atomicMin(bad_sub, sub);
+  }
+}
+
+// ============================================================ subdomain solve
+// K^(i) xloc at local closure node (a, b), component c (element by element,
+// only elements of this subdomain).
+template <typename T>
+__device__ __forceinline__ T ebe_local2d(const T* ke, const T* sc, const T* xloc, int s, int a,
+                                         int b, int c) {
+  const int s1 = s + 1;
+  T acc = T(0);
+#pragma unroll
+  for (int dx = 0; dx < 2; ++dx) {
+    const int ea = a - dx;
+    if (ea < 0 || ea >= s) continue;
+#pragma unroll
+    for (int dy = 0; dy < 2; ++dy) {
+      const int eb = b - dy;
+      if (eb < 0 || eb >= s) continue;
+      const T* krow = ke + (elem_local_node(dx, dy, 0) * 2 + c) * 8;
+      const T* x00 = xloc + (ea * s1 + eb) * 2;
+      const T* x10 = x00 + 2 * s1;
+      T part = krow[0] * x00[0] + krow[1] * x00[1];  // node (0,0)
+      part += krow[2] * x10[0] + krow[3] * x10[1];   // node (1,0)
+      part += krow[4] * x10[2] + krow[5] * x10[3];   // node (1,1)
+      part += krow[6] * x00[2] + krow[7] * x00[3];   // node (0,1)
+      acc += sc[ea * s + eb] * part;
+    }
+  }
+  return acc;
+}
+
+template <typename T, int BP, int NS>
+__global__ void __launch_bounds__(32) schur2d_kernel(DevTables t, const T* __restrict__ Ke_g,
+                                                     const T* __restrict__ scale,
+                                                     const T* __restrict__ factor, SchurIO io) {
+  if (io.done && *io.done) return;
+  constexpr int PC = BP * BP, PD = BP * (BP + 1) / 2, STAGE = PC + PD, R = BP / 32;
+  const int sub = blockIdx.x, lane = threadIdx.x;
+  const SubInfo si = t.subs[sub];
+  const int s = t.s, s1 = s + 1, nloc = s1 * s1;
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  T* stage = reinterpret_cast<T*>(smem_raw);
+  T* ybuf = stage + NS * STAGE;
+  T* vbuf = ybuf + t.nb_max * BP;
+  T* xloc = vbuf + BP;
+  T* ke = xloc + 2 * nloc;
+  T* sc = ke + 64;
+  uint64_t* bar = reinterpret_cast<uint64_t*>((reinterpret_cast<uintptr_t>(sc + s * s) + 15) & ~uintptr_t(15));
+  const int nb = si.nb, nchunks = 2 * nb;
+  const T* fbase = factor + si.factor_off;
+
+  auto issue = [&](int c) {
+    const int st = c % NS;
+    T* dst = stage + st * STAGE;
+    const T* src;
+    uint32_t elems;
+    if (c < nb) {  // forward step k = c: [C_k D_k] (k = 0: D_0 only, placed after C)
+      const int k = c;
+      if (k == 0) {
+        src = fbase + PC;
+        elems = PD;
+        dst += PC;
+      } else {
+        src = fbase + (int64_t)k * STAGE;
+        elems = STAGE;
+      }
+    } else {  // backward step k: [D_k C_{k+1}] (last block: D only)
+      const int k = 2 * nb - 1 - c;
+      src = fbase + (int64_t)k * STAGE + PC;
+      elems = (k < nb - 1) ? STAGE : PD;
+    }
+    const uint32_t bytes = elems * (uint32_t)sizeof(T);
+    mbar_expect_tx(&bar[st], bytes);
+    bulk_load(dst, src, bytes, &bar[st]);
+  };
+
+  if (lane == 0) {
+    for (int i = 0; i < NS; ++i) mbar_init(&bar[i], 1);
+    fence_mbar_init();
+    for (int c = 0; c < NS && c < nchunks; ++c) issue(c);
+  }
+  for (int i = lane; i < 64; i += 32) ke[i] = Ke_g[i];
+  for (int i = lane; i < s * s; i += 32)
+    sc[i] = scale[(int64_t)(si.lo[0] + i / s) * t.ne[1] + si.lo[1] + i % s];
+  for (int i = lane; i < 2 * nloc; i += 32) xloc[i] = T(0);
+  __syncwarp();
+  const bool have_x = io.x || io.zvec;
+  if (have_x) {
+    const double beta = io.zvec ? *io.beta : 0.0;
+    for (int r = lane; r < si.n_ring; r += 32) {
+      const int g = t.ring_gidx[si.ring_off + r];
+      const double v = io.x ? io.x[g] : io.zvec[g] + beta * io.pvec[g];
+      xloc[t.ring_loc[si.ring_off + r]] = (T)v;
+    }
+  }
+  __syncwarp();
+
+  bool ok = true;
+  // ---- forward substitution: y_k = D_k (w_k - C_k y_{k-1})
+  for (int k = 0; k < nb; ++k) {
+    const int st = k % NS;
+    ok = __all_sync(0xffffffffu, mbar_wait(&bar[st], (k / NS) & 1));
+    if (!ok) break;
+    const T* Cs = stage + st * STAGE;
+    const T* Ds = Cs + PC;
+    T w[R];
+#pragma unroll
+    for (int m = 0; m < R; ++m) {
+      const int r = lane + 32 * m;
+      T v = T(0);
+      if (r < si.bsz) {
+        const int x = si.ilo[0] + k, y = si.ilo[1] + (r >> 1), c = r & 1;
+        const int64_t dof = 2 * node2(t, x, y) + c;
+        if (!t.fixed[dof]) {
+          if (io.f) v = (T)io.f[dof];
+          if (have_x) v -= ebe_local2d<T>(ke, sc, xloc, s, x - si.lo[0], y - si.lo[1], c);
+        }
+      }
+      w[m] = v;
+    }
+    if (k > 0) {
+      const T* yp = ybuf + (k - 1) * BP;
+#pragma unroll 8
+      for (int j = 0; j < BP; ++j) {
+        const T yj = yp[j];
+#pragma unroll
+        for (int m = 0; m < R; ++m) w[m] -= Cs[j * BP + lane + 32 * m] * yj;
+      }
+    }
+#pragma unroll
+    for (int m = 0; m < R; ++m) vbuf[lane + 32 * m] = w[m];
+    __syncwarp();
+    T y[R];
+#pragma unroll
+    for (int m = 0; m < R; ++m) y[m] = T(0);
+#pragma unroll 4
+    for (int j = 0; j < BP; ++j) {
+      const T vj = vbuf[j];
+      const T* col = Ds + (j * BP - j * (j - 1) / 2 - j);
+#pragma unroll
+      for (int m = 0; m < R; ++m) {
+        const int r = lane + 32 * m;
+        if (r >= j) y[m] += col[r] * vj;
+      }
+    }
+#pragma unroll
+    for (int m = 0; m < R; ++m) ybuf[k * BP + lane + 32 * m] = y[m];
+    __syncwarp();
+    if (lane == 0 && k + NS < nchunks) {
+      fence_proxy_async_smem();
+      issue(k + NS);
+    }
+  }
+  // ---- backward substitution: t_k = D_k^T (y_k - C_{k+1}^T t_{k+1})
+  for (int kk = 0; ok && kk < nb; ++kk) {
+    const int k = nb - 1 - kk, c = nb + kk, st = c % NS;
+    ok = __all_sync(0xffffffffu, mbar_wait(&bar[st], (c / NS) & 1));
+    if (!ok) break;
+    const T* Ds = stage + st * STAGE;
+    const T* Cs = Ds + PD;
+    T v[R];
+#pragma unroll
+    for (int m = 0; m < R; ++m) v[m] = ybuf[k * BP + lane + 32 * m];
+    if (k + 1 < nb) {
+      const T* tn = ybuf + (k + 1) * BP;
+#pragma unroll
+      for (int m = 0; m < R; ++m) {
+        const int r = lane + 32 * m;
+        T acc = T(0);
+#pragma unroll
+        for (int h = 0; h < R; ++h)
+#pragma unroll 8
+          for (int rr = 0; rr < 32; ++rr) {
+            const int r2 = (rr ^ lane) + 32 * h;  // bank-conflict-free transposed read
+            acc += Cs[r * BP + r2] * tn[r2];
+          }
+        v[m] -= acc;
+      }
+    }
+#pragma unroll
+    for (int m = 0; m < R; ++m) vbuf[lane + 32 * m] = v[m];
+    __syncwarp();
+    T tk[R];
+#pragma unroll
+    for (int m = 0; m < R; ++m) {
+      const int r = lane + 32 * m;
+      const T* col = Ds + (r * BP - r * (r - 1) / 2);
+      T acc = T(0);
+      for (int o = 0; r + o < BP; ++o) acc += col[o] * vbuf[r + o];
+      tk[m] = acc;
+    }
+    __syncwarp();
+#pragma unroll
+    for (int m = 0; m < R; ++m) ybuf[k * BP + lane + 32 * m] = tk[m];
+    __syncwarp();
+    if (lane == 0 && c + NS < nchunks) {
+      fence_proxy_async_smem();
+      issue(c + NS);
+    }
+  }
+  if (!ok) {
+    if (lane == 0 && io.err) atomicExch(io.err, kErrTimeout);
+    return;
+  }
+  // ---- outputs
+  if (io.u_out || io.ring_out) {
+    for (int k = 0; k < nb; ++k)
+#pragma unroll
+      for (int m = 0; m < R; ++m) {
+        const int r = lane + 32 * m;
+        if (r >= si.bsz) continue;
+        const int x = si.ilo[0] + k, y = si.ilo[1] + (r >> 1), c = r & 1;
+        const int64_t dof = 2 * node2(t, x, y) + c;
+        if (t.fixed[dof]) continue;
+        const T tv = ybuf[k * BP + r];
+        if (io.u_out) io.u_out[dof] = (double)tv;
+        xloc[((x - si.lo[0]) * s1 + (y - si.lo[1])) * 2 + c] = tv;
+      }
+    __syncwarp();
+  }
+  if (io.ring_out) {
+    T* out = reinterpret_cast<T*>(io.ring_out) + si.ring_off;
+    for (int r = lane; r < si.n_ring; r += 32) {
+      const int loc = t.ring_loc[si.ring_off + r];
+      const int node = loc >> 1, c = loc & 1;
+      out[r] = ebe_local2d<T>(ke, sc, xloc, s, node / s1, node % s1, c);
+    }
+  }
+}
+
+// ============================================================ Gamma sums
+template <typename T>
+__global__ void gamma_sum_kernel(DevTables t, const T* __restrict__ ring,
+                                 const double* __restrict__ base, double sign,
+                                 double* __restrict__ out) {
+  for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < t.n_gamma;
+       g += (int64_t)gridDim.x * blockDim.x) {
+    double acc = 0.0;
+    for (int o = t.owner_ptr[g]; o < t.owner_ptr[g + 1]; ++o) acc += (double)ring[t.owner_idx[o]];
+    out[g] = (base ? base[t.gamma_dof[g]] : 0.0) + sign * acc;
+  }
+}
+
+// ============================================================ PCG
+// K_B: q = S p assembled from the ring; p = z + beta p; alpha = rz / p^T q.
+template <typename T>
+__global__ void __launch_bounds__(kRedThreads) pcg_assemble_kernel(DevTables t, const T* __restrict__ ring,
+                                                          const double* __restrict__ z, double* p,
+                                                          double* q, PcgState* st,
+                                                          double* partials) {
+  if (st->done) return;
+  __shared__ double scratch[32];
+  const double beta = st->beta;
+  double acc[1] = {0.0};
+  for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < t.n_gamma;
+       g += (int64_t)gridDim.x * blockDim.x) {
+    double qg = 0.0;
+    for (int o = t.owner_ptr[g]; o < t.owner_ptr[g + 1]; ++o) qg += (double)ring[t.owner_idx[o]];
+    const double pg = z[g] + beta * p[g];
+    p[g] = pg;
+    q[g] = qg;
+    acc[0] += pg * qg;
+  }
+  if (grid_sum<1, kRedThreads>(acc, partials, &st->ticket[0], scratch) && threadIdx.x == 0) {
+    const double pq = acc[0];
+    st->pq = pq;
+    if (!(pq > 0.0) || !isfinite(pq)) {
+      st->status = -6;  // breakdown
+      st->done = 1;
+    } else {
+      st->alpha = st->rz / pq;
+    }
+  }
+}
+
+// K_C (and the initial step): x += alpha p; r -= alpha q; z = S~^-1 r;
+// rz = r^T z, rr = r^T r; beta; convergence test.
+template <bool INIT>
+__global__ void __launch_bounds__(kRedThreads) pcg_update_kernel(DevTables t, DevFields fld, const double* __restrict__ gin,
+                                                        double* x, double* r, double* z, double* p,
+                                                        const double* __restrict__ q, PcgState* st,
+                                                        double* partials) {
+  if (st->done) return;
+  extern __shared__ double rw_all[];  // (blockDim/32) * max_blk_n
+  __shared__ double scratch[64];
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  double* rw = rw_all + wib * t.max_blk_n;
+  const double alpha = INIT ? 0.0 : st->alpha;
+  double acc[2] = {0.0, 0.0};
+  const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int nw = (gridDim.x * blockDim.x) >> 5;
+  for (int b = gw; b < t.n_blocks; b += nw) {
+    const int off = t.blk_off[b], n = t.blk_n[b];
+    const double* P = t.ptab + t.blk_poff[b];
+    const double ainv = 1.0 / fld.blk_alpha[b];
+    for (int i = lane; i < n; i += 32) {
+      const int g = off + i;
+      double ri;
+      if (INIT) {
+        x[g] = 0.0;
+        p[g] = 0.0;
+        ri = gin[g];
+      } else {
+        x[g] += alpha * p[g];
+        ri = r[g] - alpha * q[g];
+      }
+      r[g] = ri;
+      rw[i] = ri;
+    }
+    __syncwarp();
+    for (int i = lane; i < n; i += 32) {
+      double zi = 0.0;
+      const double* Pi = P + i * n;
+      for (int j = 0; j < n; ++j) zi += Pi[j] * rw[j];
+      zi *= ainv;
+      z[off + i] = zi;
+      acc[0] += rw[i] * zi;
+      acc[1] += rw[i] * rw[i];
+    }
+    __syncwarp();
+  }
+  for (int64_t g = t.n_face_dofs + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < t.n_gamma;
+       g += (int64_t)gridDim.x * blockDim.x) {
+    double ri;
+    if (INIT) {
+      x[g] = 0.0;
+      p[g] = 0.0;
+      ri = gin[g];
+    } else {
+      x[g] += alpha * p[g];
+      ri = r[g] - alpha * q[g];
+    }
+    r[g] = ri;
+    const double zi = ri * fld.cross_scale[g - t.n_face_dofs];
+    z[g] = zi;
+    acc[0] += ri * zi;
+    acc[1] += ri * ri;
+  }
+  if (grid_sum<2, kRedThreads>(acc, partials, &st->ticket[1], scratch) && threadIdx.x == 0) {
+    const double rz = acc[0], rr = acc[1];
+    st->rr = rr;
+    if (INIT) {
+      st->beta = 0.0;
+      st->it = 0;
+    } else {
+      st->beta = rz / st->rz;
+      st->it += 1;
+    }
+    st->rz = rz;
+    if (rr <= st->tol2) {
+      st->done = 1;
+      st->status = 0;
+    } else if (!isfinite(rr) || !isfinite(rz)) {
+      st->done = 1;
+      st->status = -6;
+    } else if (st->it >= st->max_it) {
+      st->done = 1;
+      st->status = -5;
+    }
+  }
+}
+
+__global__ void precond_kernel(DevTables t, DevFields fld, const double* __restrict__ r,
+                               double* __restrict__ z) {
+  const int lane = threadIdx.x & 31;
+  const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int nw = (gridDim.x * blockDim.x) >> 5;
+  for (int b = gw; b < t.n_blocks; b += nw) {
+    const int off = t.blk_off[b], n = t.blk_n[b];
+    const double* P = t.ptab + t.blk_poff[b];
+    const double ainv = 1.0 / fld.blk_alpha[b];
+    for (int i = lane; i < n; i += 32) {
+      double zi = 0.0;
+      for (int j = 0; j < n; ++j) zi += P[i * n + j] * r[off + j];
+      z[off + i] = zi * ainv;
+    }
+  }
+  for (int64_t g = t.n_face_dofs + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < t.n_gamma;
+       g += (int64_t)gridDim.x * blockDim.x)
+    z[g] = r[g] * fld.cross_scale[g - t.n_face_dofs];
+}
+
+// ============================================================ global K x
+template <int DIM>
+__global__ void __launch_bounds__(kRedThreads) apply_K_kernel(DevTables t, DevFields fld, const double* __restrict__ x,
+                                                     const double* __restrict__ f, double* y,
+                                                     int mode, double* partials, unsigned* ticket,
+                                                     double* nrm) {
+  constexpr int NN = 1 << DIM, ND = DIM * NN;
+  __shared__ double ke[ND * ND];
+  __shared__ double scratch[64];
+  for (int i = threadIdx.x; i < ND * ND; i += blockDim.x) ke[i] = t.Ke64[i];
+  __syncthreads();
+  double acc[2] = {0.0, 0.0};
+  const int64_t n_nodes = t.n_dof / DIM;
+  for (int64_t n = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; n < n_nodes;
+       n += (int64_t)gridDim.x * blockDim.x) {
+    const int k = DIM == 3 ? (int)(n % t.nn[2]) : 0;
+    const int64_t ij = DIM == 3 ? n / t.nn[2] : n;
+    const int j = (int)(ij % t.nn[1]), i = (int)(ij / t.nn[1]);
+    double out[DIM];
+#pragma unroll
+    for (int c = 0; c < DIM; ++c) out[c] = 0.0;
+    for (int ox = 0; ox < 2; ++ox) {
+      const int ex = i - ox;
+      if (ex < 0 || ex >= t.ne[0]) continue;
+      for (int oy = 0; oy < 2; ++oy) {
+        const int ey = j - oy;
+        if (ey < 0 || ey >= t.ne[1]) continue;
+        for (int oz = 0; oz < (DIM == 3 ? 2 : 1); ++oz) {
+          const int ez = k - oz;
+          if (DIM == 3 && (ez < 0 || ez >= t.ne[2])) continue;
+          const int64_t e = DIM == 3 ? ((int64_t)ex * t.ne[1] + ey) * t.ne[2] + ez
+                                     : (int64_t)ex * t.ne[1] + ey;
+          const int ln = elem_local_node(ox, oy, oz);
+          double part[DIM];
+#pragma unroll
+          for (int c = 0; c < DIM; ++c) part[c] = 0.0;
+#pragma unroll
+          for (int a = 0; a < NN; ++a) {
+            int dx, dy, dz;
+            elem_node_offset(a, dx, dy, dz);
+            const int64_t nb = DIM == 3
+                                   ? ((int64_t)(ex + dx) * t.nn[1] + (ey + dy)) * t.nn[2] + (ez + dz)
+                                   : (int64_t)(ex + dx) * t.nn[1] + (ey + dy);
+#pragma unroll
+            for (int c2 = 0; c2 < DIM; ++c2) {
+              const int64_t d2 = DIM * nb + c2;
+              const double xv = t.fixed[d2] ? 0.0 : x[d2];
+#pragma unroll
+              for (int c = 0; c < DIM; ++c) part[c] += ke[(ln * DIM + c) * ND + a * DIM + c2] * xv;
+            }
+          }
+          const double sc = fld.scale64[e];
+#pragma unroll
+          for (int c = 0; c < DIM; ++c) out[c] += sc * part[c];
+        }
+      }
+    }
+#pragma unroll
+    for (int c = 0; c < DIM; ++c) {
+      const int64_t d = DIM * n + c;
+      if (t.fixed[d]) {
+        y[d] = 0.0;
+        continue;
+      }
+      if (mode == 0) {
+        y[d] = out[c];
+      } else {
+        const double fv = f[d];
+        const double rv = fv - out[c];
+        y[d] = rv;
+        acc[0] += rv * rv;
+        acc[1] += fv * fv;
+      }
+    }
+  }
+  if (mode == 1) {
+    if (grid_sum<2, kRedThreads>(acc, partials, ticket, scratch) && threadIdx.x == 0) {
+      nrm[0] = sqrt(acc[0]);
+      nrm[1] = sqrt(acc[1]);
+    }
+  }
+}
+
+__global__ void scatter_gamma_kernel(DevTables t, const double* __restrict__ xg, double* u) {
+  const int64_t n = t.n_dof > t.n_gamma ? t.n_dof : t.n_gamma;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    if (i < t.n_gamma) u[t.gamma_dof[i]] = xg[i];
+    if (i < t.n_dof && t.fixed[i]) u[i] = 0.0;
+  }
+}
+
+__global__ void axpy_kernel(int64_t n, double a, const double* __restrict__ x, double* y) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    y[i] += a * x[i];
+}
+
+int grid_for(int64_t n, int threads, int cap = 152 * 8) {
+  int64_t b = (n + threads - 1) / threads;
+  if (b < 1) b = 1;
+  if (b > cap) b = cap;
+  return (int)b;
+}
+
+template <typename T, int BP, int NS>
+size_t schur_smem(const DevTables& t) {
+  constexpr int PC = BP * BP, PD = BP * (BP + 1) / 2, STAGE = PC + PD;
+  const int s = t.s, nloc = (s + 1) * (s + 1);
+  size_t elems = (size_t)NS * STAGE + (size_t)t.nb_max * BP + BP + 2 * nloc + 64 + s * s;
+  return elems * sizeof(T) + 16 + NS * sizeof(uint64_t) + 16;
+}
+
+template <typename T, int BP, int NS>
+void run_schur(const DevTables& t, const DevFields& fld, const void* factor, const SchurIO& io,
+               cudaStream_t st) {
+  const size_t smem = schur_smem<T, BP, NS>(t);
+  auto kern = schur2d_kernel<T, BP, NS>;
+  DevFields f2 = fld;
+  const T* ke = nullptr;
+  const T* sc = nullptr;
+  if constexpr (sizeof(T) == 8) {
+    ke = reinterpret_cast<const T*>(t.Ke64);
+    sc = reinterpret_cast<const T*>(f2.scale64);
+  } else {
+    ke = reinterpret_cast<const T*>(t.Ke32);
+    sc = reinterpret_cast<const T*>(f2.scale32);
+  }
+  kern<<<t.n_sub, 32, smem, st>>>(t, ke, sc, reinterpret_cast<const T*>(factor), io);
+}
+
+template <typename T, int BP>
+void run_factor(const DevTables& t, const DevFields& fld, void* factor, int* err, int* bad_sub,
+                cudaStream_t st) {
+  const size_t smem = (size_t)3 * BP * (BP + 1) * sizeof(T) + 64 * sizeof(T);
+  auto kern = factor2d_kernel<T, BP>;
+  const T* ke;
+  const T* sc;
+  if constexpr (sizeof(T) == 8) {
+    ke = reinterpret_cast<const T*>(t.Ke64);
+    sc = reinterpret_cast<const T*>(fld.scale64);
+  } else {
+    ke = reinterpret_cast<const T*>(t.Ke32);
+    sc = reinterpret_cast<const T*>(fld.scale32);
+  }
+  kern<<<t.n_sub, 128, smem, st>>>(t, ke, sc, reinterpret_cast<T*>(factor), err, bad_sub);
+}
+
+}  // namespace
+
+// ============================================================ launchers
+cudaError_t configure_kernels() {
+  const int big = 232448;
+  cudaError_t e = cudaSuccess;
+#define DDEL_CFG(k)                                                                   \
+  do {                                                                                \
+    cudaError_t e2 = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, big); \
+    if (e2 != cudaSuccess) e = e2;                                                    \
+  } while (0)
+  DDEL_CFG((schur2d_kernel<double, 32, 3>));
+  DDEL_CFG((schur2d_kernel<double, 64, 2>));
+  DDEL_CFG((schur2d_kernel<double, 96, 1>));
+  DDEL_CFG((schur2d_kernel<float, 32, 4>));
+  DDEL_CFG((schur2d_kernel<float, 64, 2>));
+  DDEL_CFG((schur2d_kernel<float, 96, 2>));
+  DDEL_CFG((factor2d_kernel<double, 32>));
+  DDEL_CFG((factor2d_kernel<double, 64>));
+  DDEL_CFG((factor2d_kernel<double, 96>));
+  DDEL_CFG((factor2d_kernel<float, 32>));
+  DDEL_CFG((factor2d_kernel<float, 64>));
+  DDEL_CFG((factor2d_kernel<float, 96>));
+#undef DDEL_CFG
+  return e;
+}
+
+void launch_assemble(const DevTables& t, const DevFields& fld, const double* rho, double E, double p,
+                     int face_scaling, int crosspoint_mode, int* err, cudaStream_t st) {
+  scale_kernel<<<grid_for(t.n_elem, 256), 256, 0, st>>>(rho, t.n_elem, E, p, fld.scale64,
+                                                        fld.scale32, err);
+  if (t.dim == 2)
+    gamma_diag_kernel<2><<<grid_for(t.n_gamma, 256), 256, 0, st>>>(t, fld);
+  else
+    gamma_diag_kernel<3><<<grid_for(t.n_gamma, 256), 256, 0, st>>>(t, fld);
+  face_scale_kernel<<<grid_for((int64_t)t.n_blocks * 32 + t.n_gamma, 256), 256, 0, st>>>(
+      t, fld, face_scaling, crosspoint_mode);
+}
+
+void launch_factor(const DevTables& t, const DevFields& fld, int precision, void* factor, int* err,
+                   int* bad_sub, cudaStream_t st) {
+  if (precision == 0) {
+    if (t.BP == 32) run_factor<double, 32>(t, fld, factor, err, bad_sub, st);
+    else if (t.BP == 64) run_factor<double, 64>(t, fld, factor, err, bad_sub, st);
+    else run_factor<double, 96>(t, fld, factor, err, bad_sub, st);
+  } else {
+    if (t.BP == 32) run_factor<float, 32>(t, fld, factor, err, bad_sub, st);
+    else if (t.BP == 64) run_factor<float, 64>(t, fld, factor, err, bad_sub, st);
+    else run_factor<float, 96>(t, fld, factor, err, bad_sub, st);
+  }
+}
+
+size_t schur_smem_bytes(const DevTables& t, int precision) {
+  if (precision == 0) {
+    if (t.BP == 32) return schur_smem<double, 32, 3>(t);
+    if (t.BP == 64) return schur_smem<double, 64, 2>(t);
+    return schur_smem<double, 96, 1>(t);
+  }
+  if (t.BP == 32) return schur_smem<float, 32, 4>(t);
+  if (t.BP == 64) return schur_smem<float, 64, 2>(t);
+  return schur_smem<float, 96, 2>(t);
+}
+
+void launch_schur(const DevTables& t, const DevFields& fld, int precision, const void* factor,
+                  const SchurIO& io, cudaStream_t st) {
+  if (precision == 0) {
+    if (t.BP == 32) run_schur<double, 32, 3>(t, fld, factor, io, st);
+    else if (t.BP == 64) run_schur<double, 64, 2>(t, fld, factor, io, st);
+    else run_schur<double, 96, 1>(t, fld, factor, io, st);
+  } else {
+    if (t.BP == 32) run_schur<float, 32, 4>(t, fld, factor, io, st);
+    else if (t.BP == 64) run_schur<float, 64, 2>(t, fld, factor, io, st);
+    else run_schur<float, 96, 2>(t, fld, factor, io, st);
+  }
+}
+
+void launch_gamma_sum(const DevTables& t, int precision, const void* ring, const double* base,
+                      double sign, double* out, cudaStream_t st) {
+  const int g = grid_for(t.n_gamma, 256);
+  if (precision == 0)
+    gamma_sum_kernel<double><<<g, 256, 0, st>>>(t, (const double*)ring, base, sign, out);
+  else
+    gamma_sum_kernel<float><<<g, 256, 0, st>>>(t, (const float*)ring, base, sign, out);
+}
+
+static size_t update_smem(const DevTables& t) {
+  return (size_t)(kRedThreads / 32) * t.max_blk_n * sizeof(double);
+}
+
+void launch_pcg_init(const DevTables& t, const DevFields& fld, const double* g, double* x, double* r,
+                     double* z, double* p, PcgState* s, double* partials, cudaStream_t st,
+                     int nblk) {
+  pcg_update_kernel<true><<<nblk, kRedThreads, update_smem(t), st>>>(t, fld, g, x, r, z, p, nullptr,
+                                                                     s, partials);
+}
+
+void launch_pcg_assemble(const DevTables& t, int precision, const void* ring, const double* z,
+                         double* p, double* q, PcgState* s, double* partials, cudaStream_t st,
+                         int nblk) {
+  if (precision == 0)
+    pcg_assemble_kernel<double><<<nblk, kRedThreads, 0, st>>>(t, (const double*)ring, z, p, q, s,
+                                                              partials);
+  else
+    pcg_assemble_kernel<float><<<nblk, kRedThreads, 0, st>>>(t, (const float*)ring, z, p, q, s,
+                                                             partials);
+}
+
+void launch_pcg_update(const DevTables& t, const DevFields& fld, double* x, double* r, double* z,
+                       const double* p, const double* q, PcgState* s, double* partials,
+                       cudaStream_t st, int nblk) {
+  pcg_update_kernel<false><<<nblk, kRedThreads, update_smem(t), st>>>(
+      t, fld, nullptr, x, r, z, const_cast<double*>(p), q, s, partials);
+}
+
+void launch_precond(const DevTables& t, const DevFields& fld, const double* r, double* z,
+                    cudaStream_t st) {
+  precond_kernel<<<grid_for((int64_t)t.n_blocks * 32 + t.n_gamma, 256), 256, 0, st>>>(t, fld, r, z);
+}
+
+void launch_apply_K(const DevTables& t, const DevFields& fld, const double* x, const double* f,
+                    double* y, int mode, double* partials, unsigned* ticket, double* nrm,
+                    cudaStream_t st, int nblk) {
+  if (t.dim == 2)
+    apply_K_kernel<2><<<nblk, kRedThreads, 0, st>>>(t, fld, x, f, y, mode, partials, ticket, nrm);
+  else
+    apply_K_kernel<3><<<nblk, kRedThreads, 0, st>>>(t, fld, x, f, y, mode, partials, ticket, nrm);
+}
+
+void launch_scatter_gamma(const DevTables& t, const double* xg, double* u, cudaStream_t st) {
+  scatter_gamma_kernel<<<grid_for(t.n_dof > t.n_gamma ? t.n_dof : t.n_gamma, 256), 256, 0, st>>>(
+      t, xg, u);
+}
+
+void launch_axpy(int64_t n, double a, const double* x, double* y, cudaStream_t st) {
+  axpy_kernel<<<grid_for(n, 256), 256, 0, st>>>(n, a, x, y);
+}
+
+}  // namespace ddel

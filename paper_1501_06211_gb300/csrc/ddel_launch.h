@@ -1,0 +1,99 @@
+// Kernel launchers (host functions) shared by the API translation unit.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "ddel_internal.h"
+
+namespace ddel {
+
+// Device-resident copy of the static tables of a Setup.
+struct DevTables {
+  int dim, s, n_sub, BP, nb_max;
+  int ne[3], nn[3];
+  int64_t n_dof, n_elem, n_gamma;
+  int n_face_dofs, n_blocks, max_blk_n;
+  SubInfo* subs;
+  uint8_t* fixed;
+  int32_t* ring_gidx;
+  int32_t* ring_loc;
+  int64_t n_ring;
+  int32_t* owner_ptr;
+  int32_t* owner_idx;
+  int64_t* gamma_dof;
+  int32_t* blk_off;
+  int32_t* blk_n;
+  int32_t* blk_poff;
+  double* blk_hmean;
+  double* ptab;
+  double* Ke64;
+  float* Ke32;
+};
+
+// PCG scalars kept on the device (read by the host only at check points).
+struct PcgState {
+  double rz, alpha, beta, tol2, rr, pq;
+  int it, max_it, done, status;
+  unsigned ticket[4];
+};
+
+// Per-assembly fields.
+struct DevFields {
+  double* scale64;  // n_elem: E rho^p
+  float* scale32;
+  double* diagG;    // n_gamma: diag(K_GG)
+  double* blk_alpha;
+  double* cross_scale;  // n_gamma - n_face_dofs
+};
+
+struct SchurIO {
+  const double* x = nullptr;      // Gamma input (nullptr = 0)
+  const double* zvec = nullptr;   // PCG form: x = z + beta * p
+  const double* pvec = nullptr;
+  const double* beta = nullptr;
+  const double* f = nullptr;      // global right-hand side for the interior (nullptr = 0)
+  void* ring_out = nullptr;       // per ring slot output (T), nullptr = skip
+  double* u_out = nullptr;        // global vector, interior DOFs written, nullptr = skip
+  const int* done = nullptr;      // early exit flag
+  int* err = nullptr;
+};
+
+// Opt-in shared memory sizes for every kernel instantiation (call once).
+cudaError_t configure_kernels();
+
+// Assembly: element factors from densities, diag(K_GG), face scales.
+void launch_assemble(const DevTables& t, const DevFields& fld, const double* rho, double E, double p,
+                     int face_scaling, int crosspoint_mode, int* err, cudaStream_t st);
+// Fused interior assembly + block-tridiagonal Cholesky; factor in T.
+void launch_factor(const DevTables& t, const DevFields& fld, int precision, void* factor, int* err,
+                   int* bad_sub, cudaStream_t st);
+// Per-subdomain solve kernel (condense / Schur / back-substitution forms).
+void launch_schur(const DevTables& t, const DevFields& fld, int precision, const void* factor,
+                  const SchurIO& io, cudaStream_t st);
+size_t schur_smem_bytes(const DevTables& t, int precision);
+// Sum ring contributions: out[g] = sign * sum(ring) + (base ? base[gamma_dof[g]] : 0)
+void launch_gamma_sum(const DevTables& t, int precision, const void* ring, const double* base,
+                      double sign, double* out, cudaStream_t st);
+// PCG kernels
+void launch_pcg_init(const DevTables& t, const DevFields& fld, const double* g, double* x, double* r,
+                     double* z, double* p, PcgState* s, double* partials, cudaStream_t st,
+                     int nblk);
+void launch_pcg_assemble(const DevTables& t, int precision, const void* ring, const double* z,
+                         double* p, double* q, PcgState* s, double* partials, cudaStream_t st,
+                         int nblk);
+void launch_pcg_update(const DevTables& t, const DevFields& fld, double* x, double* r, double* z,
+                       const double* p, const double* q, PcgState* s, double* partials,
+                       cudaStream_t st, int nblk);
+void launch_precond(const DevTables& t, const DevFields& fld, const double* r, double* z,
+                    cudaStream_t st);
+// Global element-by-element product / residual in FP64 (node-centric, no atomics).
+// mode 0: y = K x (free rows); mode 1: y = f - K x (free rows), norms into nrm[0..1]
+void launch_apply_K(const DevTables& t, const DevFields& fld, const double* x, const double* f,
+                    double* y, int mode, double* partials, unsigned* ticket, double* nrm,
+                    cudaStream_t st, int nblk);
+// u[gamma_dof[g]] = xg[g]; u = 0 on fixed DOFs
+void launch_scatter_gamma(const DevTables& t, const double* xg, double* u, cudaStream_t st);
+// y += a * x (n)
+void launch_axpy(int64_t n, double a, const double* x, double* y, cudaStream_t st);
+
+}  // namespace ddel

@@ -1,0 +1,391 @@
+"""ctypes binding of libddel (include/ddel.h): argument marshalling only.
+
+Every step of the solve runs in the library's CUDA kernels; this module only
+converts Python/NumPy/torch arguments into the plain pointers and structs of
+the C ABI.  The functions keep the C names (``ddel_create``, ``ddel_solve``,
+...); ``Solver`` is a thin convenience wrapper over them.  Importing this
+module fails loudly when libddel.so has not been built.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libddel.so")
+
+c_int, c_double, c_void_p, c_uint32, c_int64 = (ctypes.c_int, ctypes.c_double, ctypes.c_void_p,
+                                                  ctypes.c_uint32, ctypes.c_int64)
+
+DDEL_OK, DDEL_EINVAL, DDEL_ENOMEM, DDEL_ECUDA = 0, -1, -2, -3
+DDEL_ENOTSPD, DDEL_ENOCONV, DDEL_EBREAKDOWN, DDEL_ESTATE, DDEL_ETIMEOUT = -4, -5, -6, -7, -8
+DDEL_FP64, DDEL_FP32 = 0, 1
+
+
+class ddel_mesh(ctypes.Structure):
+    _fields_ = [("dim", c_int), ("nx", c_int), ("ny", c_int), ("nz", c_int), ("sub", c_int)]
+
+
+class ddel_material(ctypes.Structure):
+    _fields_ = [("E", c_double), ("nu", c_double), ("plane_stress", c_int), ("simp_p", c_double),
+                ("rho_min", c_double)]
+
+
+class ddel_bc(ctypes.Structure):
+    _fields_ = [("clamp_faces", c_uint32), ("fixed_dof", c_void_p), ("n_point", c_int),
+                ("point_node", c_void_p), ("point_force", c_void_p), ("traction_face", c_int),
+                ("traction", c_double * 3)]
+
+
+class ddel_options(ctypes.Structure):
+    _fields_ = [("precision", c_int), ("theta", c_double), ("face_scaling", c_int),
+                ("crosspoint_mode", c_int), ("tol", c_double), ("max_it", c_int),
+                ("max_cycles", c_int), ("inner_tol", c_double), ("x0_mode", c_int),
+                ("schur_mode", c_int), ("use_graph", c_int), ("check_every", c_int)]
+
+
+class ddel_stats(ctypes.Structure):
+    _fields_ = [("status", c_int), ("iters", c_int), ("cycles", c_int), ("relres", c_double),
+                ("pcg_relres", c_double), ("bad_subdomain", c_int), ("t_factor_ms", c_double),
+                ("t_condense_ms", c_double), ("t_pcg_ms", c_double), ("t_backsub_ms", c_double),
+                ("t_verify_ms", c_double), ("t_total_ms", c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class ddel_info_t(ctypes.Structure):
+    _fields_ = [("dim", c_int), ("n_sub", c_int), ("n_elem", c_int), ("max_block", c_int),
+                ("max_blocks_per_sub", c_int), ("n_nodes", c_int64), ("n_dof", c_int64),
+                ("n_gamma", c_int64), ("n_fixed", c_int64), ("factor_bytes", c_int64),
+                ("n_face_blocks", c_int), ("n_cross", c_int)]
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(
+            f"{LIB_PATH} is missing: build it with `python -c 'import __graft_entry__ as g; g.build()'`"
+            " (the solver has no CPU fallback)")
+    lib = ctypes.CDLL(LIB_PATH)
+    P = ctypes.POINTER
+    sig = {
+        "ddel_default_options": (None, [P(ddel_options)]),
+        "ddel_strerror": (ctypes.c_char_p, [c_int]),
+        "ddel_last_error": (ctypes.c_char_p, [c_void_p]),
+        "ddel_create": (c_int, [P(ddel_mesh), P(ddel_material), P(ddel_bc), P(ddel_options),
+                                c_void_p, P(c_void_p)]),
+        "ddel_destroy": (None, [c_void_p]),
+        "ddel_get_info": (c_int, [c_void_p, P(ddel_info_t)]),
+        "ddel_set_options": (c_int, [c_void_p, P(ddel_options)]),
+        "ddel_assemble": (c_int, [c_void_p, c_void_p, c_int]),
+        "ddel_factor": (c_int, [c_void_p]),
+        "ddel_solve": (c_int, [c_void_p, c_void_p, c_void_p, c_int, P(ddel_stats)]),
+        "ddel_apply_K": (c_int, [c_void_p, c_void_p, c_void_p]),
+        "ddel_condense": (c_int, [c_void_p, c_void_p, c_void_p]),
+        "ddel_schur_apply": (c_int, [c_void_p, c_void_p, c_void_p]),
+        "ddel_precond_apply": (c_int, [c_void_p, c_void_p, c_void_p]),
+        "ddel_back_substitute": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p]),
+        "ddel_pcg": (c_int, [c_void_p, c_void_p, c_void_p, c_double, P(ddel_stats)]),
+        "ddel_residual_norm": (c_int, [c_void_p, c_void_p, c_void_p, P(c_double), P(c_double)]),
+        "ddel_gamma_dofs": (c_int, [c_void_p, c_void_p]),
+        "ddel_load_vector": (c_int, [c_void_p, c_void_p]),
+        "ddel_fixed_mask": (c_int, [c_void_p, c_void_p]),
+        "ddel_plan_create": (c_int, [P(ddel_mesh), P(ddel_material), P(ddel_bc), c_double,
+                                     P(c_void_p)]),
+        "ddel_plan_destroy": (None, [c_void_p]),
+        "ddel_plan_info": (c_int, [c_void_p, P(ddel_info_t)]),
+        "ddel_plan_gamma_dofs": (c_int, [c_void_p, c_void_p]),
+        "ddel_plan_face_block": (c_int, [c_void_p, c_int, c_void_p, c_void_p, c_void_p, c_void_p]),
+        "ddel_plan_element_matrix": (c_int, [c_void_p, c_void_p]),
+        "ddel_plan_subdomain": (c_int, [c_void_p, c_int, c_void_p, c_void_p]),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    return lib, sig
+
+
+_lib, SIGNATURES = _load()
+EXPORTED = sorted(SIGNATURES)
+
+
+class DDELError(RuntimeError):
+    def __init__(self, code, msg=""):
+        self.code = code
+        super().__init__(f"{_lib.ddel_strerror(code).decode()} ({code}) {msg}".strip())
+
+
+def _check(code, ctx=None):
+    if code != DDEL_OK:
+        msg = _lib.ddel_last_error(ctx).decode() if ctx else ""
+        raise DDELError(code, msg)
+
+
+def _ptr(a):
+    """Device/host pointer of a torch tensor or NumPy array (None -> NULL)."""
+    if a is None:
+        return None
+    if hasattr(a, "data_ptr"):
+        return a.data_ptr()
+    if isinstance(a, np.ndarray):
+        return a.ctypes.data
+    raise TypeError(type(a))
+
+
+# ----------------------------------------------------------------- raw C names
+def ddel_default_options():
+    o = ddel_options()
+    _lib.ddel_default_options(ctypes.byref(o))
+    return o
+
+
+def ddel_strerror(code):
+    return _lib.ddel_strerror(code).decode()
+
+
+def ddel_create(mesh, mat, bc, opt, stream=None):
+    h = c_void_p()
+    code = _lib.ddel_create(ctypes.byref(mesh), ctypes.byref(mat), ctypes.byref(bc),
+                            ctypes.byref(opt) if opt is not None else None, stream, ctypes.byref(h))
+    return code, h
+
+
+ddel_destroy = _lib.ddel_destroy
+
+
+def ddel_get_info(h):
+    info = ddel_info_t()
+    _check(_lib.ddel_get_info(h, ctypes.byref(info)), h)
+    return info
+
+
+def ddel_set_options(h, opt):
+    return _lib.ddel_set_options(h, ctypes.byref(opt))
+
+
+def ddel_assemble(h, rho, on_device):
+    return _lib.ddel_assemble(h, _ptr(rho), int(on_device))
+
+
+def ddel_factor(h):
+    return _lib.ddel_factor(h)
+
+
+def ddel_solve(h, f, u, on_device):
+    st = ddel_stats()
+    code = _lib.ddel_solve(h, _ptr(f), _ptr(u), int(on_device), ctypes.byref(st))
+    return code, st
+
+
+def ddel_apply_K(h, x, y):
+    return _lib.ddel_apply_K(h, _ptr(x), _ptr(y))
+
+
+def ddel_condense(h, f, g):
+    return _lib.ddel_condense(h, _ptr(f), _ptr(g))
+
+
+def ddel_schur_apply(h, x, y):
+    return _lib.ddel_schur_apply(h, _ptr(x), _ptr(y))
+
+
+def ddel_precond_apply(h, r, z):
+    return _lib.ddel_precond_apply(h, _ptr(r), _ptr(z))
+
+
+def ddel_back_substitute(h, f, uG, u):
+    return _lib.ddel_back_substitute(h, _ptr(f), _ptr(uG), _ptr(u))
+
+
+def ddel_pcg(h, g, x, tol_abs):
+    st = ddel_stats()
+    code = _lib.ddel_pcg(h, _ptr(g), _ptr(x), float(tol_abs), ctypes.byref(st))
+    return code, st
+
+
+def ddel_residual_norm(h, f, u):
+    rn, fn = c_double(), c_double()
+    code = _lib.ddel_residual_norm(h, _ptr(f), _ptr(u), ctypes.byref(rn), ctypes.byref(fn))
+    return code, rn.value, fn.value
+
+
+def ddel_gamma_dofs(h, n_gamma):
+    out = np.zeros(n_gamma, dtype=np.int64)
+    _check(_lib.ddel_gamma_dofs(h, out.ctypes.data), h)
+    return out
+
+
+def ddel_load_vector(h, n_dof):
+    out = np.zeros(n_dof)
+    _check(_lib.ddel_load_vector(h, out.ctypes.data), h)
+    return out
+
+
+def ddel_fixed_mask(h, n_dof):
+    out = np.zeros(n_dof, dtype=np.uint8)
+    _check(_lib.ddel_fixed_mask(h, out.ctypes.data), h)
+    return out.astype(bool)
+
+
+# ----------------------------------------------------------------- BC marshalling
+def node_index(ne, ijk):
+    """Global node index of grid node ijk (node-interleaved convention of ddel.h)."""
+    n = 0
+    for a, x in enumerate(ijk):
+        n = n * (ne[a] + 1) + int(x)
+    return n
+
+
+class _BC:
+    """Keeps the arrays a ddel_bc points to alive for the duration of create."""
+
+    def __init__(self, ne, spec):
+        dim = len(ne)
+        self.bc = ddel_bc()
+        self.bc.clamp_faces = 0
+        for axis, side in spec.get("clamp", []):
+            self.bc.clamp_faces |= 1 << (2 * axis + side)
+        self.mask = None
+        if spec.get("fix"):
+            n_dof = dim * int(np.prod([n + 1 for n in ne]))
+            self.mask = np.zeros(n_dof, dtype=np.uint8)
+            for ijk, c in spec["fix"]:
+                self.mask[dim * node_index(ne, ijk) + c] = 1
+            self.bc.fixed_dof = self.mask.ctypes.data
+        pts = spec.get("point", [])
+        self.nodes = np.array([node_index(ne, ijk) for ijk, _ in pts], dtype=np.int64)
+        self.forces = np.array([list(fv) for _, fv in pts], dtype=np.float64).reshape(-1)
+        self.bc.n_point = len(pts)
+        if pts:
+            self.bc.point_node = self.nodes.ctypes.data
+            self.bc.point_force = self.forces.ctypes.data
+        self.bc.traction_face = -1
+        if "traction" in spec:
+            axis, side, t = spec["traction"]
+            self.bc.traction_face = 2 * axis + side
+            for k, v in enumerate(t):
+                self.bc.traction[k] = v
+
+
+class Plan:
+    """Host-only set-up (no GPU needed): classification and face operators."""
+
+    def __init__(self, cfg, theta=0.5, plane_stress=True):
+        ne = tuple(cfg["ne"])
+        self.cfg = cfg
+        self.mesh = ddel_mesh(cfg["dim"], ne[0], ne[1], ne[2] if len(ne) > 2 else 0, cfg["sub"])
+        self.mat = ddel_material(cfg["E"], cfg["nu"], 1 if plane_stress else 0, cfg["p"], 1e-3)
+        bc = _BC(ne, cfg["bc"])
+        h = c_void_p()
+        _check(_lib.ddel_plan_create(ctypes.byref(self.mesh), ctypes.byref(self.mat),
+                                     ctypes.byref(bc.bc), float(theta), ctypes.byref(h)))
+        self.h = h
+        self.info = ddel_info_t()
+        _check(_lib.ddel_plan_info(h, ctypes.byref(self.info)))
+
+    def __del__(self):
+        if getattr(self, "h", None):
+            _lib.ddel_plan_destroy(self.h)
+            self.h = None
+
+    def gamma_dofs(self):
+        out = np.zeros(self.info.n_gamma, dtype=np.int64)
+        _check(_lib.ddel_plan_gamma_dofs(self.h, out.ctypes.data))
+        return out
+
+    def face_block(self, b):
+        off, n, hm = ctypes.c_int32(), ctypes.c_int32(), c_double()
+        _check(_lib.ddel_plan_face_block(self.h, b, ctypes.byref(off), ctypes.byref(n), None,
+                                         ctypes.byref(hm)))
+        P = np.zeros((n.value, n.value))
+        _check(_lib.ddel_plan_face_block(self.h, b, None, None, P.ctypes.data, None))
+        return off.value, n.value, P, hm.value
+
+    def element_matrix(self):
+        nd = self.cfg["dim"] * 2 ** self.cfg["dim"]
+        K = np.zeros((nd, nd))
+        _check(_lib.ddel_plan_element_matrix(self.h, K.ctypes.data))
+        return K
+
+    def subdomain(self, i):
+        ilo = np.zeros(3, dtype=np.int32)
+        icnt = np.zeros(3, dtype=np.int32)
+        _check(_lib.ddel_plan_subdomain(self.h, i, ilo.ctypes.data, icnt.ctypes.data))
+        return ilo, icnt
+
+
+class Solver:
+    """Convenience wrapper: one context for one workload description.
+
+    cfg: dict with dim, ne, sub, E, nu, p, bc (see workloads).  Keyword options
+    override ddel_default_options() fields.
+    """
+
+    def __init__(self, cfg, stream=None, plane_stress=True, **options):
+        ne = tuple(cfg["ne"])
+        self.cfg = cfg
+        self.mesh = ddel_mesh(cfg["dim"], ne[0], ne[1], ne[2] if len(ne) > 2 else 0, cfg["sub"])
+        self.mat = ddel_material(cfg["E"], cfg["nu"], 1 if plane_stress else 0, cfg["p"],
+                                 cfg.get("rho_min", 1e-3))
+        self.opt = ddel_default_options()
+        for k, v in options.items():
+            setattr(self.opt, k, v)
+        bc = _BC(ne, cfg["bc"])
+        code, self.h = ddel_create(self.mesh, self.mat, bc.bc, self.opt, stream)
+        _check(code)
+        self.info = ddel_get_info(self.h)
+
+    def close(self):
+        if self.h:
+            ddel_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_options(self, **options):
+        for k, v in options.items():
+            setattr(self.opt, k, v)
+        _check(ddel_set_options(self.h, self.opt), self.h)
+
+    @property
+    def n_dof(self):
+        return int(self.info.n_dof)
+
+    @property
+    def n_gamma(self):
+        return int(self.info.n_gamma)
+
+    def gamma_dofs(self):
+        return ddel_gamma_dofs(self.h, self.n_gamma)
+
+    def load_vector(self):
+        return ddel_load_vector(self.h, self.n_dof)
+
+    def fixed_mask(self):
+        return ddel_fixed_mask(self.h, self.n_dof)
+
+    def assemble(self, rho):
+        on_dev = hasattr(rho, "is_cuda") and rho.is_cuda
+        if not on_dev:
+            rho = np.ascontiguousarray(rho, dtype=np.float64)
+        _check(ddel_assemble(self.h, rho, on_dev), self.h)
+
+    def factor(self):
+        _check(ddel_factor(self.h), self.h)
+
+    def solve(self, f=None, u=None, check=True):
+        """Solve K u = f; f/u torch CUDA tensors (device path) or NumPy (host path)."""
+        on_dev = u is not None and hasattr(u, "is_cuda") and u.is_cuda
+        if u is None:
+            u = np.zeros(self.n_dof)
+        if f is not None and not on_dev:
+            f = np.ascontiguousarray(f, dtype=np.float64)
+        code, st = ddel_solve(self.h, f, u, on_dev)
+        if check and code not in (DDEL_OK,):
+            raise DDELError(code, _lib.ddel_last_error(self.h).decode() + f" stats={st.as_dict()}")
+        return u, st
