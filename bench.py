@@ -1,0 +1,321 @@
+#!/usr/bin/env python3
+"""Benchmark: time to 1e-8 relative residual per elasticity solve.
+
+Workload (one step = one pass of the whole hot path): 2D Q1 plane-stress
+cantilever on a 512x256 element grid, 32x16 = 512 subdomains of 16x16
+elements, Gaussian-random-field densities in [1e-3, 1] (seed = rank), SIMP
+p = 3, E = 1, nu = 0.3.  A step assembles the densities, factorises every
+subdomain, condenses, runs interface PCG, back-substitutes and verifies
+||f - K u|| / ||f|| <= 1e-8 in FP64.
+
+`value` is the mixed-precision form (FP32 subdomain factors and Schur
+applies, FP64 Krylov vectors, dot products and refinement residual); the
+plain FP64 form is timed beside it.  Inputs are resident in HBM when the
+timed region starts; L2 is flushed between steps.  `e2e` repeats the step
+through the C ABI with host buffers (host->device copies of densities and
+loads, device->host copy of the displacement inside the timed region).
+
+Multi-GPU (torchrun): every rank solves its own independent instance (weak
+scaling, no collective on the data path); the step time is the max over ranks
+and value = that time / n_gpus (job-level time per solve).
+
+--impl reference times the CPU oracle (SciPy SuperLU direct solve of the same
+workload) on the host cores.
+"""
+import argparse
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "time to 1e-8 rel. residual per elasticity solve; mixed/learned vs FP64 plain"
+WORKLOAD = ("2D Q1 plane-stress cantilever 512x256 elements, 512 subdomains of 16x16, "
+            "GRF densities in [1e-3,1], SIMP p=3, E=1, nu=0.3, tol 1e-8")
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+# --------------------------------------------------------------- clocks
+class Clocks:
+    """Samples nvidia-smi during the timed region."""
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={q}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        os.unlink(self.path)
+        if not sm:
+            return None
+        sm.sort()
+        return {"sm_mhz": sm[len(sm) // 2], "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# --------------------------------------------------------------- reference (CPU oracle)
+def oracle_solve_ms(cfg, rho):
+    from oracle import direct, fem
+    t0 = time.perf_counter()
+    grid = fem.Grid(cfg["dim"], *cfg["ne"])
+    fixed, f = fem.bc_from_spec(grid, cfg["bc"])
+    K = fem.assemble(grid, fem.element_stiffness(cfg["dim"], cfg["E"] / cfg["E"], cfg["nu"]),
+                     fem.element_factors(rho, cfg["E"], cfg["p"]))
+    u = direct.solve(K, f, fixed)
+    rr = direct.rel_residual(K, f, u, fixed)
+    return 1e3 * (time.perf_counter() - t0), rr
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    import workloads
+    cfg = workloads.config("c1")
+    rho = workloads.density(cfg)
+    for _ in range(args.warmup):
+        oracle_solve_ms(cfg, rho)
+    times = []
+    rr = None
+    for _ in range(args.steps):
+        ms, rr = oracle_solve_ms(cfg, rho)
+        times.append(ms)
+    ms = sum(times) / len(times)
+    sample = "one full solve per step: assembly + SuperLU direct solve + 2 FP64 refinement steps"
+    out = {"impl": "reference", "metric": METRIC, "value": ms, "unit": "ms", "n_gpus": args.gpus,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": False,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": WORKLOAD, "solver": "CPU oracle (SciPy SuperLU, serial)"},
+           "relres": rr,
+           "cpu_baseline": {"value": ms, "unit": "ms", "cores": 1, "kind": "oracle", "sample": sample},
+           "e2e": {"value": ms, "unit": "ms", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out))
+
+
+# --------------------------------------------------------------- ours
+def main():
+    args = parse()
+    rank, world, local = dist_env()
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+    import numpy as np
+    import torch
+    import workloads
+    from paper_1501_06211_gb300.build import build
+    if rank == 0 or not os.path.exists(os.path.join(ROOT, "paper_1501_06211_gb300", "libddel.so")):
+        build()
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+        dist.barrier()
+    from paper_1501_06211_gb300 import ddel
+
+    cfg = workloads.config("c1")
+    cfg["density"] = ("grf", rank)
+    rho_h = workloads.density(cfg)
+    stream = torch.cuda.Stream()
+    rho_d = torch.as_tensor(rho_h, device="cuda")
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")  # > L2
+
+    def make(prec):
+        s = ddel.Solver(cfg, stream=stream.cuda_stream, precision=prec, tol=1e-8, max_it=20000)
+        f_d = torch.as_tensor(s.load_vector(), device="cuda")
+        u_d = torch.zeros_like(f_d)
+        return s, f_d, u_d
+
+    def barrier():
+        torch.cuda.synchronize()
+        if dist is not None:
+            dist.barrier()
+
+    def time_mode(prec, steps, warmup):
+        s, f_d, u_d = make(prec)
+        stats = []
+        for _ in range(warmup):
+            s.assemble(rho_d)
+            s.factor()
+            s.solve(f_d, u_d)
+        barrier()
+        total = 0.0
+        launches0 = None
+        for _ in range(steps):
+            with torch.cuda.stream(stream):
+                flush.zero_()
+            stream.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            s.assemble(rho_d)
+            s.factor()
+            _, st = s.solve(f_d, u_d)
+            e1.record(stream)
+            e1.synchronize()
+            total += e0.elapsed_time(e1)
+            stats.append(st)
+        barrier()
+        return s, f_d, u_d, total / steps, stats
+
+    clocks = Clocks(local)
+    clocks.start()
+    s32, f32_d, u32_d, ms32, st32 = time_mode(ddel.DDEL_FP32, args.steps, args.warmup)
+    gpu_launches = launches_per_step(s32, st32[-1]) * args.steps
+    s64, f64_d, u64_d, ms64, st64 = time_mode(ddel.DDEL_FP64, max(2, args.steps // 2),
+                                              max(1, args.warmup // 2))
+    clk = clocks.stop()
+    times = torch.tensor([ms32, ms64], device="cuda")
+    if dist is not None:
+        dist.all_reduce(times, op=dist.ReduceOp.MAX)
+    ms32, ms64 = times.tolist()
+
+    # end to end through the C ABI with host buffers (copies inside the timed region)
+    f_h = s32.load_vector()
+    u_h = np.zeros_like(f_h)
+    e2e_steps = max(2, args.steps // 2)
+    s32.assemble(rho_h)
+    s32.factor()
+    s32.solve(f_h, u_h)
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        s32.assemble(rho_h)
+        s32.factor()
+        s32.solve(f_h, u_h)
+    torch.cuda.synchronize()
+    e2e_ms = 1e3 * (time.perf_counter() - t0) / e2e_steps
+    h2d = rho_h.nbytes + f_h.nbytes
+    d2h = u_h.nbytes
+
+    # dominant kernel: the batched local Schur apply of the mixed-precision
+    # form (one launch per PCG iteration), timed alone with CUDA events
+    roof = kernel_roofline(ddel, s32, stream, torch)
+
+    it32 = [st.iters for st in st32]
+    out = {
+        "metric": METRIC, "value": ms32 / world, "unit": "ms", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms32,
+        "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32+f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "global_batch": world, "parallelism": f"replicas x{world}",
+                   "l2": "flushed between steps (512 MB write)", "step": "assemble+factor+solve"},
+        "modes": {"fp32_refined_ms": ms32, "fp64_plain_ms": ms64, "speedup_mixed_vs_fp64": ms64 / ms32},
+        "iters": {"fp32": it32[-1], "fp64": st64[-1].iters, "cycles_fp32": st32[-1].cycles,
+                  "fallback_fp32": st32[-1].fallback},
+        "relres": {"fp32": st32[-1].relres, "fp64": st64[-1].relres},
+        "e2e": {"value": e2e_ms / world, "unit": "ms", "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h},
+        "roofline": roof,
+        "gpu_launches": gpu_launches,
+    }
+    if clk is not None:
+        out["clocks"] = clk
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline()
+    if rank == 0:
+        print(json.dumps(out))
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def launches_per_step(s, st):
+    from paper_1501_06211_gb300 import ddel
+    return ddel.ddel_kernel_info(s.h)["launches_since_assemble"]
+
+
+def kernel_roofline(ddel, s, stream, torch):
+    import numpy as np
+    peaks = {}
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        peaks = json.load(open(path))
+    hbm = peaks.get("hbm_gbs", 6800.0)
+    src = "measured" if "hbm_gbs" in peaks else "fallback"
+    ng = s.n_gamma
+    x = torch.randn(ng, dtype=torch.float64, device="cuda")
+    y = torch.zeros_like(x)
+    reps = 200
+    for _ in range(5):
+        ddel.ddel_schur_apply(s.h, x, y)
+    stream.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(reps):
+        ddel.ddel_schur_apply(s.h, x, y)
+    e1.record(stream)
+    e1.synchronize()
+    avg_ms = e0.elapsed_time(e1) / reps
+    info = ddel.ddel_kernel_info(s.h)
+    bytes_ = info["schur_apply_bytes"]
+    gbs = bytes_ / (avg_ms * 1e-3) / 1e9
+    return {"bound": "hbm", "kernel": info["schur_apply_kernel"], "achieved": gbs, "peak": hbm,
+            "unit": "GB/s", "frac": gbs / hbm, "traffic": None, "peak_source": src,
+            "launch_ms": avg_ms, "algorithmic_bytes": bytes_}
+
+
+def cpu_baseline():
+    import workloads
+    cfg = workloads.config("c1")
+    rho = workloads.density(cfg)
+    ms, rr = oracle_solve_ms(cfg, rho)
+    return {"value": ms, "unit": "ms", "cores": 1, "kind": "oracle",
+            "sample": "one full 512x256 solve: assembly + SciPy SuperLU (serial) + 2 refinement steps"}
+
+
+if __name__ == "__main__":
+    main()

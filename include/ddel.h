@@ -96,14 +96,19 @@ typedef struct {
 typedef struct {
   int precision;       /* ddel_precision of the subdomain factors and Schur applies (FP64) */
   double theta;        /* fractional index theta of eq. NumberEight (0.5) */
-  int face_scaling;    /* 1: scale each face block by mean diag(K_GG)/mean diag(H) (1) */
+  int face_scaling;    /* face block S~_f = W H_f W (reading of Sec. 3 for heterogeneous
+                          material): 0 W = I; 1 W = sqrt(mean diag K_GG / mean diag H_f) I;
+                          2 W_ii = sqrt(diag(K_GG)_ii / diag(H_f)_ii)  (2) */
   int crosspoint_mode; /* 0: z = r / diag(K_GG) at cross points; 1: identity (0) */
   double tol;          /* target ||f - K u||_2 / ||f||_2 (1e-8) */
   int max_it;          /* PCG iteration cap per cycle (5000) */
   int max_cycles;      /* refinement cycles cap (10) */
   double inner_tol;    /* per-cycle PCG reduction in FP32 mode (1e-6) */
   int x0_mode;         /* ddel_x0_mode for the interface PCG (ZERO) */
-  int schur_mode;      /* ddel_schur_mode (AUTO) */
+  int schur_mode;      /* ddel_schur_mode (AUTO): EXPLICIT/AUTO form each local Schur
+                          complement S_i after the factorisation where the ring fits
+                          (2D, sub <= 16) and apply it as one dense product per PCG
+                          iteration; IMPLICIT applies it by block substitution */
   int use_graph;       /* capture PCG iterations in a CUDA graph (1) */
   int check_every;     /* PCG iterations between host convergence checks (16) */
 } ddel_options;
@@ -115,6 +120,7 @@ typedef struct {
   double relres;       /* final ||f - K u||_2 / ||f||_2 computed in FP64 */
   double pcg_relres;   /* last interface residual ||r_G|| / ||f|| of the recurrence */
   int bad_subdomain;   /* first subdomain with a failed pivot, or -1 */
+  int fallback;        /* 1 if an FP32 solve switched to the FP64 factors */
   double t_factor_ms, t_condense_ms, t_pcg_ms, t_backsub_ms, t_verify_ms, t_total_ms;
 } ddel_stats;
 
@@ -140,6 +146,8 @@ int ddel_create(const ddel_mesh* mesh, const ddel_material* mat, const ddel_bc* 
                 const ddel_options* opt, void* cuda_stream, ddel_ctx** out);
 void ddel_destroy(ddel_ctx* ctx);
 int ddel_get_info(const ddel_ctx* ctx, ddel_info_t* info);
+/* Changing precision or schur_mode requires a new ddel_factor (ESTATE until then);
+ * theta is fixed at creation (EINVAL). */
 int ddel_set_options(ddel_ctx* ctx, const ddel_options* opt);
 
 /* Element densities rho (n_elem doubles; host when on_device == 0, else device):
@@ -187,6 +195,20 @@ int ddel_gamma_dofs(const ddel_ctx* ctx, int64_t* out);
 int ddel_load_vector(const ddel_ctx* ctx, double* out);
 /* Fixed-DOF mask (host, n_dof bytes). */
 int ddel_fixed_mask(const ddel_ctx* ctx, uint8_t* out);
+
+/* Counters and work estimates for profiling (host output).  schur_apply_bytes:
+ * algorithmic bytes of one Schur application in the active form and precision
+ * (explicit: sum of n_ring_i^2 matrix entries; implicit: the nonzero entries of
+ * the block factors read twice, forward and backward) plus the ring vectors. */
+typedef struct {
+  int64_t launches_total;          /* kernel launches issued by the context */
+  int64_t launches_since_assemble; /* launches since the last ddel_assemble */
+  int64_t schur_apply_bytes;
+  int64_t schur_apply_flops;
+  int schur_form;                  /* 0 implicit (block substitution), 1 explicit */
+  int precision;                   /* active ddel_precision */
+} ddel_kernel_info_t;
+int ddel_kernel_info(const ddel_ctx* ctx, ddel_kernel_info_t* out);
 
 /* --- Host-only plan (no CUDA call; for inspection and tests) --------------- */
 /* The set-up of ddel_create without any device work: DOF classification,

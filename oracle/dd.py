@@ -244,13 +244,20 @@ class FacePreconditioner:
 
     S~ is block diagonal over (face, component) blocks (eq. NumberNine applied
     on each face Gamma_i with the cross points removed, Sec. 4) plus the
-    diagonal of K_GG at cross-point / wirebasket DOFs (reading Q7).  With
-    face_scaling, each block is multiplied by alpha = mean(diag K_GG over the
-    block) / mean(diag H over the block) (reading Q8); otherwise alpha = 1.
+    diagonal of K_GG at cross-point / wirebasket DOFs (reading Q7).  Scaling
+    of each face block against the material (reading Q8; the paper's tests are
+    homogeneous and it gives none):
+      face_scaling="dof" (default): S~_f = W H_f W with the diagonal
+        W = diag(sqrt(diag(K_GG)_i / diag(H_f)_i)), so diag(S~_f) = diag(K_GG)
+        on the face (close to the scalar scaling below on a homogeneous
+        face, where only diag(H_f) varies, near the face ends);
+      face_scaling="face" (or True): S~_f = alpha H_f with alpha =
+        mean(diag K_GG over the block) / mean(diag H_f);
+      face_scaling=False: S~_f = H_f (paper-literal).
     crosspoint="identity" is the paper-literal alternative of Q7.
     """
 
-    def __init__(self, dec, K, theta=0.5, face_scaling=True, crosspoint="diag"):
+    def __init__(self, dec, K, theta=0.5, face_scaling="dof", crosspoint="diag"):
         self.dec = dec
         grid = dec.grid
         d = grid.dim
@@ -273,8 +280,11 @@ class FacePreconditioner:
             Mf = M[nodes][:, nodes].toarray()
             Lf = L[nodes][:, nodes].toarray()
             fb = FaceBlock(np.array([pos[d * n + c] for n in nodes]), Mf, Lf, theta)
-            if face_scaling:
-                kd = Kdiag[G[fb.dofs]]
+            kd = Kdiag[G[fb.dofs]]
+            fb.w = np.ones(len(fb.dofs))  # S~_f^-1 = W^-1 H_f^-1 W^-1 / alpha
+            if face_scaling == "dof":
+                fb.w = np.sqrt(kd / np.diag(fb.H))
+            elif face_scaling:
                 fb.alpha = kd.mean() / np.diag(fb.H).mean()
             self.blocks.append(fb)
         self.cross_pos = np.array(self.cross_pos, dtype=np.int64)
@@ -286,7 +296,7 @@ class FacePreconditioner:
     def apply(self, r):
         z = np.zeros_like(r)
         for fb in self.blocks:
-            z[fb.dofs] = (fb.Hinv @ r[fb.dofs]) / fb.alpha
+            z[fb.dofs] = (fb.Hinv @ (r[fb.dofs] / fb.w)) / (fb.w * fb.alpha)
         z[self.cross_pos] = r[self.cross_pos] * self.cross_scale
         return z
 
@@ -295,7 +305,8 @@ class FacePreconditioner:
         n = len(self.dec.gamma_dofs)
         P = np.zeros((n, n))
         for fb in self.blocks:
-            P[np.ix_(fb.dofs, fb.dofs)] = fb.Hinv / fb.alpha
+            Wi = np.diag(1.0 / fb.w)
+            P[np.ix_(fb.dofs, fb.dofs)] = Wi @ fb.Hinv @ Wi / fb.alpha
         P[self.cross_pos, self.cross_pos] = self.cross_scale
         return P
 

@@ -27,6 +27,8 @@ struct ddel_ctx {
   bool own_stream = false;
   std::vector<void*> allocs;
   void* factor[2] = {nullptr, nullptr};
+  void* sexp[2] = {nullptr, nullptr};  // explicit local Schur complements (2D)
+  bool explicit_ok[2] = {false, false};
   bool factored[2] = {false, false};
   int active_prec = 0;
   bool assembled = false;
@@ -45,7 +47,10 @@ struct ddel_ctx {
   int* h_err = nullptr;
   int nblk = 0;
   cudaGraphExec_t graph[2] = {nullptr, nullptr};
+  bool graph_explicit[2] = {false, false};
   int graph_iters = 0;
+  int64_t launches = 0;           // kernel launches issued (graph-contained ones included)
+  int64_t launches_at_assemble = 0;
   cudaEvent_t ev[8] = {};
   std::string last_error;
 };
@@ -105,7 +110,7 @@ __global__ void set_tol_abs_kernel(PcgState* st, double tol_abs, int max_it) {
 }
 
 int check_kernel_err(ddel_ctx* ctx) {
-  CK(cudaMemcpyAsync(ctx->h_err, ctx->err, 2 * sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaMemcpyAsync(ctx->h_err, ctx->err, 4 * sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
   CK(cudaStreamSynchronize(ctx->stream));
   return DDEL_OK;
 }
@@ -120,6 +125,7 @@ int pcg_run(ddel_ctx* ctx, int prec, const double* g, int* iters, int* status) {
   cudaStream_t s = ctx->stream;
   launch_pcg_init(ctx->T, ctx->F, g, ctx->x, ctx->r, ctx->z, ctx->p, ctx->st, ctx->partials, s,
                   ctx->nblk);
+  ctx->launches += 1;
   SchurIO io = make_io(ctx);
   io.zvec = ctx->z;
   io.pvec = ctx->p;
@@ -127,8 +133,16 @@ int pcg_run(ddel_ctx* ctx, int prec, const double* g, int* iters, int* status) {
   io.ring_out = ctx->ring;
   io.done = &ctx->st->done;
   const int per = ctx->opt.check_every > 0 ? ctx->opt.check_every : 16;
+  const bool expl = ctx->explicit_ok[prec];
+  if (ctx->graph[prec] && ctx->graph_explicit[prec] != expl) {
+    cudaGraphExecDestroy(ctx->graph[prec]);
+    ctx->graph[prec] = nullptr;
+  }
   auto iteration = [&]() {
-    launch_schur(ctx->T, ctx->F, prec, ctx->factor[prec], io, s);
+    if (expl)
+      launch_schur_explicit(ctx->T, prec, ctx->sexp[prec], io, s);
+    else
+      launch_schur(ctx->T, ctx->F, prec, ctx->factor[prec], io, s);
     launch_pcg_assemble(ctx->T, prec, ctx->ring, ctx->z, ctx->p, ctx->q, ctx->st, ctx->partials, s,
                         ctx->nblk);
     launch_pcg_update(ctx->T, ctx->F, ctx->x, ctx->r, ctx->z, ctx->p, ctx->q, ctx->st,
@@ -144,6 +158,7 @@ int pcg_run(ddel_ctx* ctx, int prec, const double* g, int* iters, int* status) {
     CK(cudaGraphInstantiate(&ctx->graph[prec], graph, 0));
     cudaGraphDestroy(graph);
     ctx->graph_iters = per;
+    ctx->graph_explicit[prec] = expl;
   }
   const int max_checks = ctx->opt.max_it / per + 2;
   for (int chk = 0; chk < max_checks; ++chk) {
@@ -152,6 +167,7 @@ int pcg_run(ddel_ctx* ctx, int prec, const double* g, int* iters, int* status) {
     } else {
       for (int i = 0; i < per; ++i) iteration();
     }
+    ctx->launches += 3 * per;
     CK(cudaMemcpyAsync(ctx->h_st, ctx->st, sizeof(PcgState), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
     if (ctx->h_st->done) break;
@@ -167,6 +183,7 @@ void condense(ddel_ctx* ctx, int prec, const double* f, double* g) {
   io.ring_out = ctx->ring;
   launch_schur(ctx->T, ctx->F, prec, ctx->factor[prec], io, ctx->stream);
   launch_gamma_sum(ctx->T, prec, ctx->ring, f, -1.0, g, ctx->stream);
+  ctx->launches += 2;
 }
 
 void back_substitute(ddel_ctx* ctx, int prec, const double* f, const double* xg, double* u) {
@@ -176,6 +193,43 @@ void back_substitute(ddel_ctx* ctx, int prec, const double* f, const double* xg,
   io.u_out = u;
   launch_schur(ctx->T, ctx->F, prec, ctx->factor[prec], io, ctx->stream);
   launch_scatter_gamma(ctx->T, xg, u, ctx->stream);
+  ctx->launches += 2;
+}
+
+
+// Factor (and, where available, form the explicit local Schur complements) in
+// one precision.  ENOTSPD on a failed pivot, EINVAL on a bad density.
+int factor_prec(ddel_ctx* ctx, int prec) {
+  if (!ctx->factor[prec]) {
+    cudaError_t e = cudaMalloc(&ctx->factor[prec], ctx->S.factor_elems * (prec ? 4 : 8) + 256);
+    if (e != cudaSuccess) return fail(ctx, DDEL_ENOMEM, "factor allocation");
+  }
+  const int init[2] = {0, 0x7fffffff};
+  CK(cudaMemcpyAsync(ctx->err, init, sizeof(init), cudaMemcpyHostToDevice, ctx->stream));
+  launch_factor(ctx->T, ctx->F, prec, ctx->factor[prec], ctx->err, ctx->bad_sub, ctx->stream);
+  ctx->launches += 1;
+  CK(cudaGetLastError());
+  ctx->factored[prec] = false;
+  ctx->explicit_ok[prec] = false;
+  const int NR = explicit_ring_size(ctx->T);
+  const bool want_explicit = NR > 0 && ctx->opt.schur_mode != DDEL_SCHUR_IMPLICIT;
+  if (want_explicit) {
+    if (!ctx->sexp[prec]) {
+      cudaError_t e = cudaMalloc(&ctx->sexp[prec], (size_t)ctx->T.n_sub * NR * NR * (prec ? 4 : 8));
+      if (e != cudaSuccess) return fail(ctx, DDEL_ENOMEM, "explicit Schur allocation");
+    }
+    launch_schur_form(ctx->T, ctx->F, prec, ctx->factor[prec], ctx->sexp[prec], ctx->stream);
+    ctx->launches += 1;
+    CK(cudaGetLastError());
+  }
+  int rc = check_kernel_err(ctx);
+  if (rc) return rc;
+  if (ctx->h_err[2] == kErrBadRho) return fail(ctx, DDEL_EINVAL, "density must be > 0");
+  if (ctx->h_err[0] == kErrPivot)
+    return fail(ctx, DDEL_ENOTSPD, "pivot failure in subdomain " + std::to_string(ctx->h_err[1]));
+  ctx->factored[prec] = true;
+  ctx->explicit_ok[prec] = want_explicit;
+  return DDEL_OK;
 }
 
 float elapsed(cudaEvent_t a, cudaEvent_t b) {
@@ -192,7 +246,7 @@ void ddel_default_options(ddel_options* o) {
   if (!o) return;
   o->precision = DDEL_FP64;
   o->theta = 0.5;
-  o->face_scaling = 1;
+  o->face_scaling = 2;
   o->crosspoint_mode = 0;
   o->tol = 1e-8;
   o->max_it = 5000;
@@ -292,12 +346,14 @@ int ddel_create(const ddel_mesh* mesh, const ddel_material* mat, const ddel_bc* 
         bad(upload(ctx, S.gamma_dof, &T.gamma_dof)) || bad(upload(ctx, S.blk_off, &T.blk_off)) ||
         bad(upload(ctx, S.blk_n, &T.blk_n)) || bad(upload(ctx, S.blk_poff, &T.blk_poff)) ||
         bad(upload(ctx, S.blk_hmean, &T.blk_hmean)) || bad(upload(ctx, S.ptab, &T.ptab)) ||
+        bad(upload(ctx, S.hdiag, &T.hdiag)) ||
         bad(upload(ctx, S.Ke, &T.Ke64)) || bad(upload(ctx, ke32, &T.Ke32)))
       goto fail_out;
     const int64_t ng = T.n_gamma, nd = S.n_dof;
     DevFields& F = ctx->F;
     if (bad(dalloc(ctx, &F.scale64, S.n_elem * 8)) || bad(dalloc(ctx, &F.scale32, S.n_elem * 4)) ||
         bad(dalloc(ctx, &F.diagG, ng * 8)) || bad(dalloc(ctx, &F.blk_alpha, (T.n_blocks + 1) * 8)) ||
+        bad(dalloc(ctx, &F.face_w, (T.n_face_dofs + 1) * 8)) ||
         bad(dalloc(ctx, &F.cross_scale, (ng - T.n_face_dofs + 1) * 8)) ||
         bad(dalloc(ctx, &ctx->ring, T.n_ring * 8)) || bad(dalloc(ctx, &ctx->d_f, nd * 8)) ||
         bad(dalloc(ctx, &ctx->d_load, nd * 8)) || bad(dalloc(ctx, &ctx->d_u, nd * 8)) ||
@@ -308,17 +364,17 @@ int ddel_create(const ddel_mesh* mesh, const ddel_material* mat, const ddel_bc* 
         bad(dalloc(ctx, &ctx->rho, S.n_elem * 8)) || bad(dalloc(ctx, &ctx->st, sizeof(PcgState))) ||
         bad(dalloc(ctx, &ctx->partials, 4 * 152 * 8 * 8)) ||
         bad(dalloc(ctx, &ctx->ticketK, 16)) || bad(dalloc(ctx, &ctx->nrm, 16)) ||
-        bad(dalloc(ctx, &ctx->err, 16)))
+        bad(dalloc(ctx, &ctx->err, 4 * sizeof(int))))
       goto fail_out;
     ctx->bad_sub = ctx->err + 1;
     if (bad(cudaMallocHost(&ctx->h_st, sizeof(PcgState))) ||
         bad(cudaMallocHost(&ctx->h_nrm, 2 * sizeof(double))) ||
-        bad(cudaMallocHost(&ctx->h_err, 2 * sizeof(int))))
+        bad(cudaMallocHost(&ctx->h_err, 4 * sizeof(int))))
       goto fail_out;
     if (bad(cudaMemset(ctx->st, 0, sizeof(PcgState))) || bad(cudaMemset(ctx->ticketK, 0, 16)) ||
         bad(cudaMemcpy(ctx->d_load, S.f.data(), nd * 8, cudaMemcpyHostToDevice)))
       goto fail_out;
-    const int zero_err[2] = {0, 0x7fffffff};
+    const int zero_err[4] = {0, 0x7fffffff, 0, 0};
     if (bad(cudaMemcpy(ctx->err, zero_err, sizeof(zero_err), cudaMemcpyHostToDevice))) goto fail_out;
     ctx->nblk = 2 * 152;
     for (auto& e : ctx->ev)
@@ -338,6 +394,8 @@ void ddel_destroy(ddel_ctx* ctx) {
     if (g) cudaGraphExecDestroy(g);
   for (void* p : ctx->allocs) cudaFree(p);
   for (void* p : ctx->factor)
+    if (p) cudaFree(p);
+  for (void* p : ctx->sexp)
     if (p) cudaFree(p);
   if (ctx->h_st) cudaFreeHost(ctx->h_st);
   if (ctx->h_nrm) cudaFreeHost(ctx->h_nrm);
@@ -371,6 +429,8 @@ int ddel_get_info(const ddel_ctx* ctx, ddel_info_t* info) {
 int ddel_set_options(ddel_ctx* ctx, const ddel_options* opt) {
   if (!ctx || !opt) return DDEL_EINVAL;
   if (opt->theta != ctx->opt.theta) return fail(ctx, DDEL_EINVAL, "theta is fixed at creation");
+  if (opt->schur_mode != ctx->opt.schur_mode || opt->precision != ctx->opt.precision)
+    ctx->factored[0] = ctx->factored[1] = false;  // refactor to switch forms
   ctx->opt = *opt;
   return DDEL_OK;
 }
@@ -385,8 +445,11 @@ int ddel_assemble(ddel_ctx* ctx, const double* rho, int on_device) {
   } else {
     CK(cudaMemcpyAsync(ctx->rho, rho, ne * 8, cudaMemcpyDeviceToDevice, ctx->stream));
   }
+  CK(cudaMemsetAsync(ctx->err + 2, 0, sizeof(int), ctx->stream));
+  ctx->launches_at_assemble = ctx->launches;
+  ctx->launches += 3;
   launch_assemble(ctx->T, ctx->F, ctx->rho, ctx->mat.E, ctx->mat.simp_p, ctx->opt.face_scaling,
-                  ctx->opt.crosspoint_mode, ctx->err, ctx->stream);
+                  ctx->opt.crosspoint_mode, ctx->err + 2, ctx->stream);
   CK(cudaGetLastError());
   ctx->assembled = true;
   ctx->factored[0] = ctx->factored[1] = false;
@@ -396,37 +459,16 @@ int ddel_assemble(ddel_ctx* ctx, const double* rho, int on_device) {
 int ddel_factor(ddel_ctx* ctx) {
   if (!ctx) return DDEL_EINVAL;
   if (!ctx->assembled) return fail(ctx, DDEL_ESTATE, "assemble before factor");
-  int prec = ctx->opt.precision == DDEL_FP32 ? 1 : 0;
-  for (int attempt = 0; attempt < 2; ++attempt) {
-    if (!ctx->factor[prec]) {
-      cudaError_t e = cudaMalloc(&ctx->factor[prec], ctx->S.factor_elems * (prec ? 4 : 8) + 256);
-      if (e != cudaSuccess) return fail(ctx, DDEL_ENOMEM, "factor allocation");
-    }
-    const int init[2] = {0, 0x7fffffff};
-    CK(cudaMemcpyAsync(ctx->err, init, sizeof(init), cudaMemcpyHostToDevice, ctx->stream));
-    launch_factor(ctx->T, ctx->F, prec, ctx->factor[prec], ctx->err, ctx->bad_sub, ctx->stream);
-    CK(cudaGetLastError());
-    int rc = check_kernel_err(ctx);
-    if (rc) return rc;
-    if (ctx->h_err[0] == kErrBadRho) return fail(ctx, DDEL_EINVAL, "density must be > 0");
-    if (ctx->h_err[0] == kErrPivot) {
-      if (prec == 1) {  // FP32 factor failed: fall back to FP64 for this density field
-        prec = 0;
-        continue;
-      }
-      return fail(ctx, DDEL_ENOTSPD, "pivot failure in subdomain " + std::to_string(ctx->h_err[1]));
-    }
-    ctx->factored[prec] = true;
-    ctx->active_prec = prec;
-    return DDEL_OK;
-  }
-  return fail(ctx, DDEL_ENOTSPD, "pivot failure");
+  const int want = ctx->opt.precision == DDEL_FP32 ? 1 : 0;
+  int rc = factor_prec(ctx, want);
+  if (rc == DDEL_ENOTSPD && want == 1) rc = factor_prec(ctx, 0);  // FP32 pivot failed: FP64
+  if (rc == DDEL_OK) ctx->active_prec = ctx->factored[want] ? want : 0;
+  return rc;
 }
 
 int ddel_solve(ddel_ctx* ctx, const double* f, double* u, int on_device, ddel_stats* stats) {
   if (!ctx || !u) return DDEL_EINVAL;
-  const int prec = ctx->active_prec;
-  if (!ctx->factored[prec]) return fail(ctx, DDEL_ESTATE, "factor before solve");
+  if (!ctx->factored[ctx->active_prec]) return fail(ctx, DDEL_ESTATE, "factor before solve");
   cudaStream_t s = ctx->stream;
   const int64_t nd = ctx->S.n_dof;
   ddel_stats st{};
@@ -442,11 +484,15 @@ int ddel_solve(ddel_ctx* ctx, const double* f, double* u, int on_device, ddel_st
   // r = f - K 0 = f and ||f||
   launch_apply_K(ctx->T, ctx->F, ctx->d_u, ctx->d_f, ctx->d_r, 1, ctx->partials, ctx->ticketK,
                  ctx->nrm, s, ctx->nblk);
+  ctx->launches += 1;
   int status = DDEL_ENOCONV;
   double t_cond = 0, t_pcg = 0, t_back = 0, t_ver = 0;
+  double prev_relres = INFINITY;
+  int prec = ctx->active_prec;
   for (int cyc = 0; cyc < ctx->opt.max_cycles; ++cyc) {
     set_tol_kernel<<<1, 1, 0, s>>>(ctx->st, ctx->nrm, ctx->opt.tol, ctx->opt.inner_tol, prec,
                                    ctx->opt.max_it);
+    ctx->launches += 1;
     CK(cudaEventRecord(ctx->ev[1], s));
     condense(ctx, prec, ctx->d_r, ctx->g);
     CK(cudaEventRecord(ctx->ev[2], s));
@@ -457,9 +503,11 @@ int ddel_solve(ddel_ctx* ctx, const double* f, double* u, int on_device, ddel_st
     CK(cudaEventRecord(ctx->ev[3], s));
     back_substitute(ctx, prec, ctx->d_r, ctx->x, ctx->d_d);
     launch_axpy(nd, 1.0, ctx->d_d, ctx->d_u, s);
+    ctx->launches += 1;
     CK(cudaEventRecord(ctx->ev[4], s));
     launch_apply_K(ctx->T, ctx->F, ctx->d_u, ctx->d_f, ctx->d_r, 1, ctx->partials, ctx->ticketK,
                    ctx->nrm, s, ctx->nblk);
+    ctx->launches += 1;
     CK(cudaMemcpyAsync(ctx->h_nrm, ctx->nrm, 16, cudaMemcpyDeviceToHost, s));
     CK(cudaMemcpyAsync(ctx->h_err, ctx->err, 8, cudaMemcpyDeviceToHost, s));
     CK(cudaEventRecord(ctx->ev[5], s));
@@ -477,7 +525,26 @@ int ddel_solve(ddel_ctx* ctx, const double* f, double* u, int on_device, ddel_st
       status = DDEL_ETIMEOUT;
       break;
     }
-    if (pst == DDEL_EBREAKDOWN) {
+    const bool diverged = pst == DDEL_EBREAKDOWN || !std::isfinite(st.relres) ||
+                          st.relres > (cyc == 0 ? 1.0 : prev_relres);
+    if (diverged && prec == 1) {
+      // The FP32 operator lost definiteness or the correction diverged
+      // (possible at high stiffness contrast): discard this correction and
+      // continue the refinement with the FP64 factorisation.
+      launch_axpy(nd, -1.0, ctx->d_d, ctx->d_u, s);
+      launch_apply_K(ctx->T, ctx->F, ctx->d_u, ctx->d_f, ctx->d_r, 1, ctx->partials, ctx->ticketK,
+                     ctx->nrm, s, ctx->nblk);
+      ctx->launches += 2;
+      if (!ctx->factored[0]) {
+        int rc2 = factor_prec(ctx, 0);
+        if (rc2) return rc2;
+      }
+      prec = 0;
+      st.fallback = 1;
+      prev_relres = INFINITY;
+      continue;
+    }
+    if (pst == DDEL_EBREAKDOWN || !std::isfinite(st.relres)) {
       status = DDEL_EBREAKDOWN;
       break;
     }
@@ -485,10 +552,20 @@ int ddel_solve(ddel_ctx* ctx, const double* f, double* u, int on_device, ddel_st
       status = DDEL_OK;
       break;
     }
-    if (!std::isfinite(st.relres)) {
-      status = DDEL_EBREAKDOWN;
-      break;
+    if (cyc > 0 && st.relres > 0.5 * prev_relres) {
+      if (prec == 1) {  // FP32 refinement stalls above the target: finish in FP64
+        if (!ctx->factored[0]) {
+          int rc2 = factor_prec(ctx, 0);
+          if (rc2) return rc2;
+        }
+        prec = 0;
+        st.fallback = 1;
+        prev_relres = st.relres;
+        continue;
+      }
+      break;  // FP64 refinement at its rounding floor: the tolerance is unattainable
     }
+    prev_relres = st.relres;
   }
   if (on_device)
     CK(cudaMemcpyAsync(u, ctx->d_u, nd * 8, cudaMemcpyDeviceToDevice, s));
@@ -511,6 +588,7 @@ int ddel_apply_K(ddel_ctx* ctx, const double* x, double* y) {
   if (!ctx->assembled) return fail(ctx, DDEL_ESTATE, "assemble first");
   launch_apply_K(ctx->T, ctx->F, x, nullptr, y, 0, ctx->partials, ctx->ticketK, ctx->nrm,
                  ctx->stream, ctx->nblk);
+  ctx->launches += 1;
   CK(cudaGetLastError());
   return DDEL_OK;
 }
@@ -530,8 +608,12 @@ int ddel_schur_apply(ddel_ctx* ctx, const double* x, double* y) {
   SchurIO io = make_io(ctx);
   io.x = x;
   io.ring_out = ctx->ring;
-  launch_schur(ctx->T, ctx->F, prec, ctx->factor[prec], io, ctx->stream);
+  if (ctx->explicit_ok[prec])
+    launch_schur_explicit(ctx->T, prec, ctx->sexp[prec], io, ctx->stream);
+  else
+    launch_schur(ctx->T, ctx->F, prec, ctx->factor[prec], io, ctx->stream);
   launch_gamma_sum(ctx->T, prec, ctx->ring, nullptr, 1.0, y, ctx->stream);
+  ctx->launches += 2;
   CK(cudaGetLastError());
   return DDEL_OK;
 }
@@ -540,6 +622,7 @@ int ddel_precond_apply(ddel_ctx* ctx, const double* r, double* z) {
   if (!ctx || !r || !z) return DDEL_EINVAL;
   if (!ctx->assembled) return fail(ctx, DDEL_ESTATE, "assemble first");
   launch_precond(ctx->T, ctx->F, r, z, ctx->stream);
+  ctx->launches += 1;
   CK(cudaGetLastError());
   return DDEL_OK;
 }
@@ -557,6 +640,7 @@ int ddel_pcg(ddel_ctx* ctx, const double* g, double* x, double tol_abs, ddel_sta
   const int prec = ctx->active_prec;
   if (!ctx->factored[prec]) return fail(ctx, DDEL_ESTATE, "factor first");
   set_tol_abs_kernel<<<1, 1, 0, ctx->stream>>>(ctx->st, tol_abs, ctx->opt.max_it);
+  ctx->launches += 1;
   int it = 0, pst = 0;
   int rc = pcg_run(ctx, prec, g, &it, &pst);
   if (rc) return rc;
@@ -578,6 +662,7 @@ int ddel_residual_norm(ddel_ctx* ctx, const double* f, const double* u, double* 
   if (!ctx->assembled) return fail(ctx, DDEL_ESTATE, "assemble first");
   launch_apply_K(ctx->T, ctx->F, u, f, ctx->d_r, 1, ctx->partials, ctx->ticketK, ctx->nrm,
                  ctx->stream, ctx->nblk);
+  ctx->launches += 1;
   CK(cudaMemcpyAsync(ctx->h_nrm, ctx->nrm, 16, cudaMemcpyDeviceToHost, ctx->stream));
   CK(cudaStreamSynchronize(ctx->stream));
   if (r_norm) *r_norm = ctx->h_nrm[0];
@@ -600,6 +685,31 @@ int ddel_load_vector(const ddel_ctx* ctx, double* out) {
 int ddel_fixed_mask(const ddel_ctx* ctx, uint8_t* out) {
   if (!ctx || !out) return DDEL_EINVAL;
   std::memcpy(out, ctx->S.fixed.data(), ctx->S.fixed.size());
+  return DDEL_OK;
+}
+
+int ddel_kernel_info(const ddel_ctx* ctx, ddel_kernel_info_t* out) {
+  if (!ctx || !out) return DDEL_EINVAL;
+  std::memset(out, 0, sizeof(*out));
+  out->launches_total = ctx->launches;
+  out->launches_since_assemble = ctx->launches - ctx->launches_at_assemble;
+  const int prec = ctx->active_prec;
+  const int64_t tb = prec ? 4 : 8;
+  out->precision = prec;
+  out->schur_form = ctx->explicit_ok[prec] ? 1 : 0;
+  int64_t mat = 0, ring = 0;
+  for (const SubInfo& si : ctx->S.subs) {
+    ring += si.n_ring;
+    if (ctx->explicit_ok[prec]) {
+      mat += (int64_t)si.n_ring * si.n_ring;
+    } else {
+      const int64_t b = si.bsz;
+      mat += 2 * (si.nb * b * (b + 1) / 2 + (si.nb > 0 ? si.nb - 1 : 0) * b * b);
+    }
+  }
+  // matrix entries read once, plus the ring gather (z and p, FP64) and the ring output
+  out->schur_apply_bytes = mat * tb + ring * (16 + tb);
+  out->schur_apply_flops = 2 * mat;
   return DDEL_OK;
 }
 

@@ -58,6 +58,7 @@ struct Setup {
   int n_face_dofs = 0;
   std::vector<int32_t> blk_off, blk_n, blk_poff;  // per (face, component) block
   std::vector<double> blk_hmean;                  // mean of diag(H) per block
+  std::vector<double> hdiag;                      // diag(H_f) per face DOF
   std::vector<double> ptab;                       // concatenated dense H^-1 (row-major)
   int max_blk_n = 0;
   int n_singular_faces = 0;

@@ -76,7 +76,11 @@ __global__ void gamma_diag_kernel(DevTables t, DevFields fld) {
   }
 }
 
-// Face scale alpha (one warp per face block) and cross-point diagonal.
+// Face scaling (one warp per face block) and cross-point diagonal.  Each face
+// block is applied as S~_f^-1 r = W^-1 H_f^-1 W^-1 r with a diagonal W:
+//   mode 0: W = I (paper-literal);
+//   mode 1: W = sqrt(alpha) I, alpha = mean diag(K_GG) / mean diag(H_f);
+//   mode 2: W_ii = sqrt(diag(K_GG)_i / diag(H_f)_i), so diag(S~_f) = diag(K_GG).
 __global__ void face_scale_kernel(DevTables t, DevFields fld, int face_scaling, int cross_mode) {
   const int lane = threadIdx.x & 31;
   const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -86,7 +90,14 @@ __global__ void face_scale_kernel(DevTables t, DevFields fld, int face_scaling, 
     double s = 0.0;
     for (int i = lane; i < n; i += 32) s += fld.diagG[off + i];
     s = warp_sum(s);
-    if (lane == 0) fld.blk_alpha[b] = face_scaling ? (s / n) / t.blk_hmean[b] : 1.0;
+    const double alpha = (s / n) / t.blk_hmean[b];
+    if (lane == 0) fld.blk_alpha[b] = face_scaling == 1 ? alpha : 1.0;
+    for (int i = lane; i < n; i += 32) {
+      double w = 1.0;
+      if (face_scaling == 1) w = sqrt(alpha);
+      if (face_scaling == 2) w = sqrt(fld.diagG[off + i] / t.hdiag[off + i]);
+      fld.face_w[off + i] = w;
+    }
   }
   const int64_t ncross = t.n_gamma - t.n_face_dofs;
   for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < ncross;
@@ -454,6 +465,178 @@ __global__ void __launch_bounds__(32) schur2d_kernel(DevTables t, const T* __res
   }
 }
 
+// ============================================================ explicit local Schur
+// S_i = K_GG^(i) - K_GI^(i) K_II^-1 K_IG^(i) = K_GG^(i) - W^T W with W = L^-1 K_IG^(i)
+// (block forward substitution with the n_ring right-hand sides of the ring).
+// One CTA of 256 threads per subdomain; the NR x NR result is accumulated in
+// registers as 16 x 16 thread tiles across all block steps and stored dense
+// (symmetric, so row- and column-major coincide).
+template <typename T>
+__device__ __forceinline__ T kig_entry2d(const DevTables& t, const SubInfo& si, const T* ke,
+                                         const T* sc, int k, int r, int loc) {
+  // K^(i)[interior (block k, row r)][ring DOF with local closure index loc]
+  if (r >= si.bsz || loc < 0) return T(0);
+  const int s = t.s, s1 = s + 1;
+  const int x = si.ilo[0] + k, y = si.ilo[1] + (r >> 1), c = r & 1;
+  if (t.fixed[2 * node2(t, x, y) + c]) return T(0);
+  const int a = x - si.lo[0], b = y - si.lo[1];
+  const int nj = loc >> 1, cj = loc & 1, aj = nj / s1, bj = nj % s1;
+  if (abs(a - aj) > 1 || abs(b - bj) > 1) return T(0);
+  T sum = T(0);
+  for (int ea = max(a, aj) - 1; ea <= min(a, aj); ++ea) {
+    if (ea < 0 || ea >= s) continue;
+    for (int eb = max(b, bj) - 1; eb <= min(b, bj); ++eb) {
+      if (eb < 0 || eb >= s) continue;
+      const int la = elem_local_node(a - ea, b - eb, 0), lb = elem_local_node(aj - ea, bj - eb, 0);
+      sum += sc[ea * s + eb] * ke[(la * 2 + c) * 8 + lb * 2 + cj];
+    }
+  }
+  return sum;
+}
+
+template <typename T>
+__device__ __forceinline__ T kgg_entry2d(int s, const T* ke, const T* sc, int li, int lj) {
+  // K^(i)[ring li][ring lj], both local closure DOF indices
+  if (li < 0 || lj < 0) return T(0);
+  const int s1 = s + 1;
+  const int ni = li >> 1, ci = li & 1, ai = ni / s1, bi = ni % s1;
+  const int nj = lj >> 1, cj = lj & 1, aj = nj / s1, bj = nj % s1;
+  if (abs(ai - aj) > 1 || abs(bi - bj) > 1) return T(0);
+  T sum = T(0);
+  for (int ea = max(ai, aj) - 1; ea <= min(ai, aj); ++ea) {
+    if (ea < 0 || ea >= s) continue;
+    for (int eb = max(bi, bj) - 1; eb <= min(bi, bj); ++eb) {
+      if (eb < 0 || eb >= s) continue;
+      const int la = elem_local_node(ai - ea, bi - eb, 0), lb = elem_local_node(aj - ea, bj - eb, 0);
+      sum += sc[ea * s + eb] * ke[(la * 2 + ci) * 8 + lb * 2 + cj];
+    }
+  }
+  return sum;
+}
+
+template <typename T, int BP, int NR>
+__global__ void __launch_bounds__(256) schur_form2d_kernel(DevTables t, const T* __restrict__ Ke_g,
+                                                           const T* __restrict__ scale,
+                                                           const T* __restrict__ factor,
+                                                           T* __restrict__ Sexp) {
+  constexpr int PC = BP * BP, PD = BP * (BP + 1) / 2, STAGE = PC + PD, TL = NR / 16;
+  const int sub = blockIdx.x, tid = threadIdx.x;
+  const SubInfo si = t.subs[sub];
+  const int s = t.s;
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  T* Wb = reinterpret_cast<T*>(smem_raw);  // BP x NR
+  T* Tb = Wb + BP * NR;                     // BP x NR
+  T* Cs = Tb + BP * NR;                     // PC
+  T* Ds = Cs + PC;                          // PD
+  T* ke = Ds + PD;                          // 64
+  T* sc = ke + 64;                          // s*s
+  int* rloc = reinterpret_cast<int*>(sc + s * s);  // NR
+  for (int i = tid; i < 64; i += 256) ke[i] = Ke_g[i];
+  for (int i = tid; i < s * s; i += 256)
+    sc[i] = scale[(int64_t)(si.lo[0] + i / s) * t.ne[1] + si.lo[1] + i % s];
+  for (int j = tid; j < NR; j += 256) rloc[j] = j < si.n_ring ? t.ring_loc[si.ring_off + j] : -1;
+  for (int i = tid; i < BP * NR; i += 256) Wb[i] = T(0);
+  __syncthreads();
+  const int ty = tid >> 4, tx = tid & 15;
+  T acc[TL][TL];
+#pragma unroll
+  for (int a = 0; a < TL; ++a)
+#pragma unroll
+    for (int b = 0; b < TL; ++b)
+      acc[a][b] = kgg_entry2d<T>(s, ke, sc, rloc[ty * TL + a], rloc[tx * TL + b]);
+  const T* fb = factor + si.factor_off;
+  for (int k = 0; k < si.nb; ++k) {
+    const T* src = fb + (int64_t)k * STAGE;
+    for (int i = tid; i < STAGE; i += 256) {
+      if (i < PC) {
+        if (k > 0) Cs[i] = src[i];
+      } else {
+        Ds[i - PC] = src[i];
+      }
+    }
+    for (int i = tid; i < BP * NR; i += 256) {
+      const int r = i / NR, j = i % NR;
+      Tb[i] = kig_entry2d<T>(t, si, ke, sc, k, r, rloc[j]);
+    }
+    __syncthreads();
+    if (k > 0) {  // T = B_k - C_k W_{k-1}
+      for (int i = tid; i < BP * NR; i += 256) {
+        const int r = i / NR, j = i % NR;
+        T v = Tb[i];
+#pragma unroll 8
+        for (int m = 0; m < BP; ++m) v -= Cs[m * BP + r] * Wb[m * NR + j];
+        Tb[i] = v;
+      }
+      __syncthreads();
+    }
+    for (int i = tid; i < BP * NR; i += 256) {  // W_k = D_k T
+      const int r = i / NR, j = i % NR;
+      T v = T(0);
+      for (int m = 0; m <= r; ++m) v += Ds[m * BP - m * (m - 1) / 2 + (r - m)] * Tb[m * NR + j];
+      Wb[i] = v;
+    }
+    __syncthreads();
+#pragma unroll 2
+    for (int m = 0; m < BP; ++m) {  // S -= W_k^T W_k
+      T wi[TL], wj[TL];
+#pragma unroll
+      for (int a = 0; a < TL; ++a) {
+        wi[a] = Wb[m * NR + ty * TL + a];
+        wj[a] = Wb[m * NR + tx * TL + a];
+      }
+#pragma unroll
+      for (int a = 0; a < TL; ++a)
+#pragma unroll
+        for (int b = 0; b < TL; ++b) acc[a][b] -= wi[a] * wj[b];
+    }
+    __syncthreads();
+  }
+  T* out = Sexp + (int64_t)sub * NR * NR;
+#pragma unroll
+  for (int a = 0; a < TL; ++a)
+#pragma unroll
+    for (int b = 0; b < TL; ++b) out[(ty * TL + a) * NR + tx * TL + b] = acc[a][b];
+}
+
+// y_ring = S_i x_ring for every subdomain (PCG form x = z + beta p when zvec).
+template <typename T, int NR>
+__global__ void __launch_bounds__(256) schur_explicit_kernel(DevTables t, const T* __restrict__ Sexp,
+                                                             SchurIO io) {
+  if (io.done && *io.done) return;
+  constexpr int H = 256 / NR;  // column groups
+  const int sub = blockIdx.x, tid = threadIdx.x;
+  const SubInfo si = t.subs[sub];
+  __shared__ T xr[NR];
+  __shared__ T part[256];
+  const double beta = io.zvec ? *io.beta : 0.0;
+  for (int j = tid; j < NR; j += 256) {
+    T v = T(0);
+    if (j < si.n_ring) {
+      const int g = t.ring_gidx[si.ring_off + j];
+      v = (T)(io.x ? io.x[g] : io.zvec[g] + beta * io.pvec[g]);
+    }
+    xr[j] = v;
+  }
+  __syncthreads();
+  const int r = tid % NR, h = tid / NR;
+  const T* Sc = Sexp + (int64_t)sub * NR * NR;
+  T acc0 = T(0), acc1 = T(0);
+  const int j0 = h * (NR / H), j1 = j0 + NR / H;
+#pragma unroll 4
+  for (int j = j0; j < j1; j += 2) {
+    acc0 += Sc[j * NR + r] * xr[j];
+    acc1 += Sc[(j + 1) * NR + r] * xr[j + 1];
+  }
+  part[tid] = acc0 + acc1;
+  __syncthreads();
+  if (tid < NR && tid < si.n_ring) {
+    T y = T(0);
+#pragma unroll
+    for (int q = 0; q < H; ++q) y += part[q * NR + tid];
+    reinterpret_cast<T*>(io.ring_out)[si.ring_off + tid] = y;
+  }
+}
+
 // ============================================================ Gamma sums
 template <typename T>
 __global__ void gamma_sum_kernel(DevTables t, const T* __restrict__ ring,
@@ -518,7 +701,6 @@ __global__ void __launch_bounds__(kRedThreads) pcg_update_kernel(DevTables t, De
   for (int b = gw; b < t.n_blocks; b += nw) {
     const int off = t.blk_off[b], n = t.blk_n[b];
     const double* P = t.ptab + t.blk_poff[b];
-    const double ainv = 1.0 / fld.blk_alpha[b];
     for (int i = lane; i < n; i += 32) {
       const int g = off + i;
       double ri;
@@ -531,17 +713,17 @@ __global__ void __launch_bounds__(kRedThreads) pcg_update_kernel(DevTables t, De
         ri = r[g] - alpha * q[g];
       }
       r[g] = ri;
-      rw[i] = ri;
+      acc[1] += ri * ri;
+      rw[i] = ri / fld.face_w[g];
     }
     __syncwarp();
     for (int i = lane; i < n; i += 32) {
       double zi = 0.0;
       const double* Pi = P + i * n;
       for (int j = 0; j < n; ++j) zi += Pi[j] * rw[j];
-      zi *= ainv;
-      z[off + i] = zi;
+      // r_i z_i = (w_i rw_i) (zi / w_i) = rw_i zi
       acc[0] += rw[i] * zi;
-      acc[1] += rw[i] * rw[i];
+      z[off + i] = zi / fld.face_w[off + i];
     }
     __syncwarp();
   }
@@ -594,11 +776,10 @@ __global__ void precond_kernel(DevTables t, DevFields fld, const double* __restr
   for (int b = gw; b < t.n_blocks; b += nw) {
     const int off = t.blk_off[b], n = t.blk_n[b];
     const double* P = t.ptab + t.blk_poff[b];
-    const double ainv = 1.0 / fld.blk_alpha[b];
     for (int i = lane; i < n; i += 32) {
       double zi = 0.0;
-      for (int j = 0; j < n; ++j) zi += P[i * n + j] * r[off + j];
-      z[off + i] = zi * ainv;
+      for (int j = 0; j < n; ++j) zi += P[i * n + j] * (r[off + j] / fld.face_w[off + j]);
+      z[off + i] = zi / fld.face_w[off + i];
     }
   }
   for (int64_t g = t.n_face_dofs + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < t.n_gamma;
@@ -754,7 +935,59 @@ void run_factor(const DevTables& t, const DevFields& fld, void* factor, int* err
   kern<<<t.n_sub, 128, smem, st>>>(t, ke, sc, reinterpret_cast<T*>(factor), err, bad_sub);
 }
 
+template <typename T, int BP, int NR>
+size_t form_smem(const DevTables& t) {
+  constexpr int PC = BP * BP, PD = BP * (BP + 1) / 2;
+  return (size_t)(2 * BP * NR + PC + PD + 64 + t.s * t.s) * sizeof(T) + NR * sizeof(int) + 16;
+}
+
+template <typename T, int BP, int NR>
+void run_form(const DevTables& t, const DevFields& fld, const void* factor, void* Sexp,
+              cudaStream_t st) {
+  const T* ke;
+  const T* sc;
+  if constexpr (sizeof(T) == 8) {
+    ke = reinterpret_cast<const T*>(t.Ke64);
+    sc = reinterpret_cast<const T*>(fld.scale64);
+  } else {
+    ke = reinterpret_cast<const T*>(t.Ke32);
+    sc = reinterpret_cast<const T*>(fld.scale32);
+  }
+  schur_form2d_kernel<T, BP, NR><<<t.n_sub, 256, form_smem<T, BP, NR>(t), st>>>(
+      t, ke, sc, reinterpret_cast<const T*>(factor), reinterpret_cast<T*>(Sexp));
+}
+
 }  // namespace
+
+int explicit_ring_size(const DevTables& t) {
+  // NR: padded ring size of the explicit form (0 = explicit form unavailable)
+  if (t.dim != 2 || t.BP != 32) return 0;
+  return t.s <= 8 ? 64 : (t.s <= 16 ? 128 : 0);
+}
+
+void launch_schur_form(const DevTables& t, const DevFields& fld, int precision, const void* factor,
+                       void* Sexp, cudaStream_t st) {
+  const int NR = explicit_ring_size(t);
+  if (precision == 0) {
+    if (NR == 64) run_form<double, 32, 64>(t, fld, factor, Sexp, st);
+    else run_form<double, 32, 128>(t, fld, factor, Sexp, st);
+  } else {
+    if (NR == 64) run_form<float, 32, 64>(t, fld, factor, Sexp, st);
+    else run_form<float, 32, 128>(t, fld, factor, Sexp, st);
+  }
+}
+
+void launch_schur_explicit(const DevTables& t, int precision, const void* Sexp, const SchurIO& io,
+                           cudaStream_t st) {
+  const int NR = explicit_ring_size(t);
+  if (precision == 0) {
+    if (NR == 64) schur_explicit_kernel<double, 64><<<t.n_sub, 256, 0, st>>>(t, (const double*)Sexp, io);
+    else schur_explicit_kernel<double, 128><<<t.n_sub, 256, 0, st>>>(t, (const double*)Sexp, io);
+  } else {
+    if (NR == 64) schur_explicit_kernel<float, 64><<<t.n_sub, 256, 0, st>>>(t, (const float*)Sexp, io);
+    else schur_explicit_kernel<float, 128><<<t.n_sub, 256, 0, st>>>(t, (const float*)Sexp, io);
+  }
+}
 
 // ============================================================ launchers
 cudaError_t configure_kernels() {
@@ -777,6 +1010,10 @@ cudaError_t configure_kernels() {
   DDEL_CFG((factor2d_kernel<float, 32>));
   DDEL_CFG((factor2d_kernel<float, 64>));
   DDEL_CFG((factor2d_kernel<float, 96>));
+  DDEL_CFG((schur_form2d_kernel<double, 32, 64>));
+  DDEL_CFG((schur_form2d_kernel<double, 32, 128>));
+  DDEL_CFG((schur_form2d_kernel<float, 32, 64>));
+  DDEL_CFG((schur_form2d_kernel<float, 32, 128>));
 #undef DDEL_CFG
   return e;
 }

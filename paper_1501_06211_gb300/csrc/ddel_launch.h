@@ -25,6 +25,7 @@ struct DevTables {
   int32_t* blk_n;
   int32_t* blk_poff;
   double* blk_hmean;
+  double* hdiag;  // n_face_dofs: diag(H_f)
   double* ptab;
   double* Ke64;
   float* Ke32;
@@ -43,6 +44,7 @@ struct DevFields {
   float* scale32;
   double* diagG;    // n_gamma: diag(K_GG)
   double* blk_alpha;
+  double* face_w;       // n_face_dofs: S~_f^-1 = W^-1 H_f^-1 W^-1
   double* cross_scale;  // n_gamma - n_face_dofs
 };
 
@@ -71,6 +73,13 @@ void launch_factor(const DevTables& t, const DevFields& fld, int precision, void
 void launch_schur(const DevTables& t, const DevFields& fld, int precision, const void* factor,
                   const SchurIO& io, cudaStream_t st);
 size_t schur_smem_bytes(const DevTables& t, int precision);
+// Explicit local Schur complements (2D, ring size NR <= 128): formation after the
+// factorisation, and the batched dense apply used inside PCG.
+int explicit_ring_size(const DevTables& t);
+void launch_schur_form(const DevTables& t, const DevFields& fld, int precision, const void* factor,
+                       void* Sexp, cudaStream_t st);
+void launch_schur_explicit(const DevTables& t, int precision, const void* Sexp, const SchurIO& io,
+                           cudaStream_t st);
 // Sum ring contributions: out[g] = sign * sum(ring) + (base ? base[gamma_dof[g]] : 0)
 void launch_gamma_sum(const DevTables& t, int precision, const void* ring, const double* base,
                       double sign, double* out, cudaStream_t st);

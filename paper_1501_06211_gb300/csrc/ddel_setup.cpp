@@ -307,6 +307,8 @@ std::string build_setup(int dim, const int ne_in[3], int sub, double E, double n
   S->blk_hmean.clear();
   S->ptab.clear();
   std::map<std::vector<double>, std::pair<int, double>> pcache;  // key -> (poff, hmean)
+  std::map<std::vector<double>, std::vector<double>> hcache;     // key -> diag(H)
+  S->hdiag.clear();
   const int pn = s + 1;                                          // patch nodes per axis
   const int np = dim == 2 ? pn : pn * pn;
   std::vector<double> Mp(np * np, 0.0), Lp(np * np, 0.0);
@@ -393,10 +395,16 @@ std::string build_setup(int dim, const int ne_in[3], int sub, double E, double n
             MV[a * nb + m] = v;
           }
         double hsum = 0.0;
-        for (int a = 0; a < nb; ++a)
-          for (int m = 0; m < nb; ++m) hsum += MV[a * nb + m] * MV[a * nb + m] * lam[m];
+        std::vector<double> hd(nb, 0.0);
+        for (int a = 0; a < nb; ++a) {
+          for (int m = 0; m < nb; ++m) hd[a] += MV[a * nb + m] * MV[a * nb + m] * lam[m];
+          hsum += hd[a];
+        }
+        hcache.emplace(key, hd);
         it = pcache.emplace(key, std::make_pair(poff, hsum / nb)).first;
       }
+      const std::vector<double>& hd = hcache[key];
+      S->hdiag.insert(S->hdiag.end(), hd.begin(), hd.end());
       S->blk_off.push_back((int)S->gamma_dof.size());
       S->blk_n.push_back(nb);
       S->blk_poff.push_back(it->second.first);

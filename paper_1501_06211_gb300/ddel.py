@@ -46,7 +46,8 @@ class ddel_options(ctypes.Structure):
 
 class ddel_stats(ctypes.Structure):
     _fields_ = [("status", c_int), ("iters", c_int), ("cycles", c_int), ("relres", c_double),
-                ("pcg_relres", c_double), ("bad_subdomain", c_int), ("t_factor_ms", c_double),
+                ("pcg_relres", c_double), ("bad_subdomain", c_int), ("fallback", c_int),
+                ("t_factor_ms", c_double),
                 ("t_condense_ms", c_double), ("t_pcg_ms", c_double), ("t_backsub_ms", c_double),
                 ("t_verify_ms", c_double), ("t_total_ms", c_double)]
 
@@ -59,6 +60,12 @@ class ddel_info_t(ctypes.Structure):
                 ("max_blocks_per_sub", c_int), ("n_nodes", c_int64), ("n_dof", c_int64),
                 ("n_gamma", c_int64), ("n_fixed", c_int64), ("factor_bytes", c_int64),
                 ("n_face_blocks", c_int), ("n_cross", c_int)]
+
+
+class ddel_kernel_info_t(ctypes.Structure):
+    _fields_ = [("launches_total", c_int64), ("launches_since_assemble", c_int64),
+                ("schur_apply_bytes", c_int64), ("schur_apply_flops", c_int64),
+                ("schur_form", c_int), ("precision", c_int)]
 
 
 def _load():
@@ -90,6 +97,7 @@ def _load():
         "ddel_gamma_dofs": (c_int, [c_void_p, c_void_p]),
         "ddel_load_vector": (c_int, [c_void_p, c_void_p]),
         "ddel_fixed_mask": (c_int, [c_void_p, c_void_p]),
+        "ddel_kernel_info": (c_int, [c_void_p, P(ddel_kernel_info_t)]),
         "ddel_plan_create": (c_int, [P(ddel_mesh), P(ddel_material), P(ddel_bc), c_double,
                                      P(c_void_p)]),
         "ddel_plan_destroy": (None, [c_void_p]),
@@ -208,6 +216,15 @@ def ddel_residual_norm(h, f, u):
     rn, fn = c_double(), c_double()
     code = _lib.ddel_residual_norm(h, _ptr(f), _ptr(u), ctypes.byref(rn), ctypes.byref(fn))
     return code, rn.value, fn.value
+
+
+def ddel_kernel_info(h):
+    k = ddel_kernel_info_t()
+    _check(_lib.ddel_kernel_info(h, ctypes.byref(k)), h)
+    d = {n: getattr(k, n) for n, _ in k._fields_}
+    d["schur_apply_kernel"] = ("schur_explicit_kernel" if k.schur_form else "schur2d_kernel") + \
+        ("<float>" if k.precision else "<double>")
+    return d
 
 
 def ddel_gamma_dofs(h, n_gamma):

@@ -230,3 +230,19 @@ def test_table1_trend_matches_paper_identity_growth():
         its.append(dd.pcg(dds.schur_apply, lambda r: r, g, 1e-6, 500)[1])
     growth = np.array(its[1:], float) / np.array(its[:-1], float)
     assert np.all(np.abs(growth - paper_growth.mean()) < 0.2)
+
+
+def test_dof_scaled_face_blocks_match_stiffness_diagonal():
+    # reading Q8 (default): S~_f = W H_f W with diag(S~_f) = diag(K_GG) on every
+    # face; S~ stays SPD, and the other two scalings are SPD as well
+    grid, fixed, f, Ke, fac, dec, K, dds = _system(64, 32, 8, seed=9)
+    Kd = K.diagonal()[dec.gamma_dofs]
+    for mode in ("dof", "face", False):
+        pre = dd.FacePreconditioner(dec, K, face_scaling=mode)
+        P = pre.dense()
+        assert np.allclose(P, P.T, atol=1e-13 * np.abs(P).max())
+        assert np.linalg.eigvalsh(P).min() > 0
+        if mode == "dof":
+            for fb in pre.blocks:
+                Sf = np.linalg.inv(P[np.ix_(fb.dofs, fb.dofs)])
+                assert np.allclose(np.diag(Sf), Kd[fb.dofs], rtol=1e-10)
