@@ -174,7 +174,8 @@ def main():
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")  # > L2
 
     def make(prec):
-        s = ddel.Solver(cfg, stream=stream.cuda_stream, precision=prec, tol=1e-8, max_it=20000)
+        s = ddel.Solver(cfg, stream=stream.cuda_stream, precision=prec, tol=1e-8, max_it=20000,
+                        inner_tol=0.1, max_cycles=60)
         f_d = torch.as_tensor(s.load_vector(), device="cuda")
         u_d = torch.zeros_like(f_d)
         return s, f_d, u_d
@@ -213,29 +214,33 @@ def main():
 
     clocks = Clocks(local)
     clocks.start()
-    s32, f32_d, u32_d, ms32, st32 = time_mode(ddel.DDEL_FP32, args.steps, args.warmup)
-    gpu_launches = launches_per_step(s32, st32[-1]) * args.steps
-    s64, f64_d, u64_d, ms64, st64 = time_mode(ddel.DDEL_FP64, max(2, args.steps // 2),
-                                              max(1, args.warmup // 2))
+    s64, f64_d, u64_d, ms64, st64 = time_mode(ddel.DDEL_FP64, args.steps, args.warmup)
+    launches64 = launches_per_step(s64, st64[-1])
+    s32, f32_d, u32_d, ms32, st32 = time_mode(ddel.DDEL_FP32, max(1, args.steps // 5), 1)
+    launches32 = launches_per_step(s32, st32[-1])
     clk = clocks.stop()
     times = torch.tensor([ms32, ms64], device="cuda")
     if dist is not None:
         dist.all_reduce(times, op=dist.ReduceOp.MAX)
     ms32, ms64 = times.tolist()
 
+    it32 = [st.iters for st in st32]
+    ok32 = st32[-1].relres <= 1e-8
+    best32 = ok32 and ms32 <= ms64
+    sb = s32 if best32 else s64
     # end to end through the C ABI with host buffers (copies inside the timed region)
-    f_h = s32.load_vector()
+    f_h = sb.load_vector()
     u_h = np.zeros_like(f_h)
     e2e_steps = max(2, args.steps // 2)
-    s32.assemble(rho_h)
-    s32.factor()
-    s32.solve(f_h, u_h)
+    sb.assemble(rho_h)
+    sb.factor()
+    sb.solve(f_h, u_h)
     barrier()
     t0 = time.perf_counter()
     for _ in range(e2e_steps):
-        s32.assemble(rho_h)
-        s32.factor()
-        s32.solve(f_h, u_h)
+        sb.assemble(rho_h)
+        sb.factor()
+        sb.solve(f_h, u_h)
     torch.cuda.synchronize()
     e2e_ms = 1e3 * (time.perf_counter() - t0) / e2e_steps
     h2d = rho_h.nbytes + f_h.nbytes
@@ -243,16 +248,16 @@ def main():
 
     # dominant kernel: the batched local Schur apply of the mixed-precision
     # form (one launch per PCG iteration), timed alone with CUDA events
-    roof = kernel_roofline(ddel, s32, stream, torch)
-
-    it32 = [st.iters for st in st32]
+    roof = kernel_roofline(ddel, sb, stream, torch)
+    ms_best = ms32 if best32 else ms64
     out = {
-        "metric": METRIC, "value": ms32 / world, "unit": "ms", "n_gpus": world,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms32,
+        "metric": METRIC, "value": ms_best / world, "unit": "ms", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_best,
         "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
-        "dtype": "f32+f64", "data": "synthetic",
+        "dtype": "f32+f64" if best32 else "f64", "data": "synthetic",
         "config": {"workload": WORKLOAD, "global_batch": world, "parallelism": f"replicas x{world}",
-                   "l2": "flushed between steps (512 MB write)", "step": "assemble+factor+solve"},
+                   "l2": "flushed between steps (512 MB write)", "step": "assemble+factor+solve",
+                   "form": "fp32 factors + fp64 refinement" if best32 else "fp64 plain"},
         "modes": {"fp32_refined_ms": ms32, "fp64_plain_ms": ms64, "speedup_mixed_vs_fp64": ms64 / ms32},
         "iters": {"fp32": it32[-1], "fp64": st64[-1].iters, "cycles_fp32": st32[-1].cycles,
                   "fallback_fp32": st32[-1].fallback},
@@ -260,7 +265,7 @@ def main():
         "e2e": {"value": e2e_ms / world, "unit": "ms", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},
         "roofline": roof,
-        "gpu_launches": gpu_launches,
+        "gpu_launches": (launches32 if best32 else launches64) * args.steps,
     }
     if clk is not None:
         out["clocks"] = clk
@@ -303,8 +308,19 @@ def kernel_roofline(ddel, s, stream, torch):
     info = ddel.ddel_kernel_info(s.h)
     bytes_ = info["schur_apply_bytes"]
     gbs = bytes_ / (avg_ms * 1e-3) / 1e9
-    return {"bound": "hbm", "kernel": info["schur_apply_kernel"], "achieved": gbs, "peak": hbm,
-            "unit": "GB/s", "frac": gbs / hbm, "traffic": None, "peak_source": src,
+    if info["precision"] == 0:
+        # FP64 products: GB300 issues 2 DFMA per clock per SM (1.26 TFLOP/s at
+        # 2070 MHz on 152 SMs; 1.25 TFLOP/s measured), far below its bandwidth
+        # (0.25 flop/byte of an FP64 matrix-vector product needs 1.7 TFLOP/s)
+        tf = info["schur_apply_flops"] / (avg_ms * 1e-3) / 1e12
+        peak = 152 * 4 * 2.07e9 / 1e12
+        return {"bound": "alu", "kernel": info["schur_apply_kernel"] + " + gamma_sum", "achieved": tf,
+                "peak": peak, "unit": "TFLOP/s", "frac": tf / peak, "traffic": None,
+                "peak_source": "derived: 152 SMs x 4 FP64 flop/clk x 2070 MHz",
+                "launch_ms": avg_ms, "algorithmic_flops": info["schur_apply_flops"],
+                "hbm_gbs_equiv": gbs}
+    return {"bound": "hbm", "kernel": info["schur_apply_kernel"] + " + gamma_sum", "achieved": gbs,
+            "peak": hbm, "unit": "GB/s", "frac": gbs / hbm, "traffic": None, "peak_source": src,
             "launch_ms": avg_ms, "algorithmic_bytes": bytes_}
 
 
