@@ -35,6 +35,7 @@ struct ddel_ctx {
   void* ring = nullptr;
   double *d_f = nullptr, *d_load = nullptr, *d_u = nullptr, *d_r = nullptr, *d_d = nullptr;
   double *g = nullptr, *x = nullptr, *r = nullptr, *z = nullptr, *p = nullptr, *q = nullptr;
+  double* sv = nullptr;  // s = S p of the Chronopoulos-Gear recurrence
   double* rho = nullptr;
   PcgState* st = nullptr;
   PcgState* h_st = nullptr;
@@ -123,15 +124,15 @@ SchurIO make_io(ddel_ctx* ctx) {
 
 int pcg_run(ddel_ctx* ctx, int prec, const double* g, int* iters, int* status) {
   cudaStream_t s = ctx->stream;
-  launch_pcg_init(ctx->T, ctx->F, g, ctx->x, ctx->r, ctx->z, ctx->p, ctx->st, ctx->partials, s,
-                  ctx->nblk);
+  launch_pcg_init(ctx->T, ctx->F, g, ctx->x, ctx->r, ctx->z, ctx->p, ctx->sv, ctx->st, s, ctx->nblk);
   ctx->launches += 1;
+  // one iteration: w = S u (ring) with delta = (S u, u) -> alpha, beta; then the
+  // vector updates and u = S~^-1 r with gamma = (r, u)
   SchurIO io = make_io(ctx);
-  io.zvec = ctx->z;
-  io.pvec = ctx->p;
-  io.beta = &ctx->st->beta;
+  io.x = ctx->z;
   io.ring_out = ctx->ring;
   io.done = &ctx->st->done;
+  io.pcg = ctx->st;
   const int per = ctx->opt.check_every > 0 ? ctx->opt.check_every : 16;
   const bool expl = ctx->explicit_ok[prec];
   if (ctx->graph[prec] && ctx->graph_explicit[prec] != expl) {
@@ -143,10 +144,8 @@ int pcg_run(ddel_ctx* ctx, int prec, const double* g, int* iters, int* status) {
       launch_schur_explicit(ctx->T, prec, ctx->sexp[prec], io, s);
     else
       launch_schur(ctx->T, ctx->F, prec, ctx->factor[prec], io, s);
-    launch_pcg_assemble(ctx->T, prec, ctx->ring, ctx->z, ctx->p, ctx->q, ctx->st, ctx->partials, s,
-                        ctx->nblk);
-    launch_pcg_update(ctx->T, ctx->F, ctx->x, ctx->r, ctx->z, ctx->p, ctx->q, ctx->st,
-                      ctx->partials, s, ctx->nblk);
+    launch_pcg_update(ctx->T, ctx->F, prec, ctx->ring, ctx->x, ctx->r, ctx->z, ctx->p, ctx->sv,
+                      ctx->st, s, ctx->nblk);
   };
   if (ctx->opt.use_graph && (!ctx->graph[prec] || ctx->graph_iters != per)) {
     if (ctx->graph[prec]) cudaGraphExecDestroy(ctx->graph[prec]);
@@ -167,7 +166,7 @@ int pcg_run(ddel_ctx* ctx, int prec, const double* g, int* iters, int* status) {
     } else {
       for (int i = 0; i < per; ++i) iteration();
     }
-    ctx->launches += 3 * per;
+    ctx->launches += 2 * per;
     CK(cudaMemcpyAsync(ctx->h_st, ctx->st, sizeof(PcgState), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
     if (ctx->h_st->done) break;
@@ -361,8 +360,9 @@ int ddel_create(const ddel_mesh* mesh, const ddel_material* mat, const ddel_bc* 
         bad(dalloc(ctx, &ctx->g, ng * 8)) || bad(dalloc(ctx, &ctx->x, ng * 8)) ||
         bad(dalloc(ctx, &ctx->r, ng * 8)) || bad(dalloc(ctx, &ctx->z, ng * 8)) ||
         bad(dalloc(ctx, &ctx->p, ng * 8)) || bad(dalloc(ctx, &ctx->q, ng * 8)) ||
+        bad(dalloc(ctx, &ctx->sv, ng * 8)) ||
         bad(dalloc(ctx, &ctx->rho, S.n_elem * 8)) || bad(dalloc(ctx, &ctx->st, sizeof(PcgState))) ||
-        bad(dalloc(ctx, &ctx->partials, 4 * 152 * 8 * 8)) ||
+        bad(dalloc(ctx, &ctx->partials, (size_t)(4 * 152 * 8 + 2 * T.n_sub + 64) * 8)) ||
         bad(dalloc(ctx, &ctx->ticketK, 16)) || bad(dalloc(ctx, &ctx->nrm, 16)) ||
         bad(dalloc(ctx, &ctx->err, 4 * sizeof(int))))
       goto fail_out;
@@ -371,7 +371,10 @@ int ddel_create(const ddel_mesh* mesh, const ddel_material* mat, const ddel_bc* 
         bad(cudaMallocHost(&ctx->h_nrm, 2 * sizeof(double))) ||
         bad(cudaMallocHost(&ctx->h_err, 4 * sizeof(int))))
       goto fail_out;
-    if (bad(cudaMemset(ctx->st, 0, sizeof(PcgState))) || bad(cudaMemset(ctx->ticketK, 0, 16)) ||
+    PcgState st0{};
+    st0.partials = ctx->partials;
+    if (bad(cudaMemcpy(ctx->st, &st0, sizeof(PcgState), cudaMemcpyHostToDevice)) ||
+        bad(cudaMemset(ctx->ticketK, 0, 16)) ||
         bad(cudaMemcpy(ctx->d_load, S.f.data(), nd * 8, cudaMemcpyHostToDevice)))
       goto fail_out;
     const int zero_err[4] = {0, 0x7fffffff, 0, 0};
@@ -651,6 +654,7 @@ int ddel_pcg(ddel_ctx* ctx, const double* g, double* x, double tol_abs, ddel_sta
     stats->iters = it;
     stats->status = pst;
     stats->pcg_relres = std::sqrt(ctx->h_st->rr);
+    stats->cycles = 1;
     stats->bad_subdomain = -1;
   }
   return pst;

@@ -237,6 +237,25 @@ __global__ void __launch_bounds__(128) factor2d_kernel(DevTables t, const T* __r
   }
 }
 
+// Alpha and beta of the Chronopoulos-Gear recurrence, from gamma = (r, u) of
+// the last update and delta = (S u, u) of the Schur apply just finished.
+__device__ __forceinline__ void cg_coefficients(PcgState* st, double delta) {
+  st->delta = delta;
+  const double gamma = st->gamma;
+  double beta = 0.0, den = delta;
+  if (st->it > 0) {
+    beta = gamma / st->gamma_prev;
+    den = delta - beta * gamma / st->alpha_prev;
+  }
+  if (!(den > 0.0) || !isfinite(den)) {
+    st->status = -6;  // breakdown
+    st->done = 1;
+    return;
+  }
+  st->beta = beta;
+  st->alpha = gamma / den;
+}
+
 // ============================================================ subdomain solve
 // K^(i) xloc at local closure node (a, b), component c (element by element,
 // only elements of this subdomain).
@@ -455,13 +474,21 @@ __global__ void __launch_bounds__(32) schur2d_kernel(DevTables t, const T* __res
       }
     __syncwarp();
   }
+  double d[1] = {0.0};
   if (io.ring_out) {
     T* out = reinterpret_cast<T*>(io.ring_out) + si.ring_off;
     for (int r = lane; r < si.n_ring; r += 32) {
       const int loc = t.ring_loc[si.ring_off + r];
       const int node = loc >> 1, c = loc & 1;
-      out[r] = ebe_local2d<T>(ke, sc, xloc, s, node / s1, node % s1, c);
+      const T y = ebe_local2d<T>(ke, sc, xloc, s, node / s1, node % s1, c);
+      out[r] = y;
+      d[0] += (double)xloc[loc] * (double)y;
     }
+  }
+  if (io.pcg) {  // delta = (S u, u) = sum over subdomains of u_i^T S_i u_i
+    __shared__ double red[32];
+    if (grid_sum<1, 32>(d, io.pcg->partials, &io.pcg->ticket[0], red) && lane == 0)
+      cg_coefficients(io.pcg, d[0]);
   }
 }
 
@@ -629,11 +656,18 @@ __global__ void __launch_bounds__(256) schur_explicit_kernel(DevTables t, const 
   }
   part[tid] = acc0 + acc1;
   __syncthreads();
+  double d[1] = {0.0};
   if (tid < NR && tid < si.n_ring) {
     T y = T(0);
 #pragma unroll
     for (int q = 0; q < H; ++q) y += part[q * NR + tid];
     reinterpret_cast<T*>(io.ring_out)[si.ring_off + tid] = y;
+    d[0] = (double)xr[tid] * (double)y;
+  }
+  if (io.pcg) {  // delta = (S u, u) = sum over subdomains of u_i^T S_i u_i
+    __shared__ double red[32];
+    if (grid_sum<1, 256>(d, io.pcg->partials, &io.pcg->ticket[0], red) && tid == 0)
+      cg_coefficients(io.pcg, d[0]);
   }
 }
 
@@ -651,114 +685,90 @@ __global__ void gamma_sum_kernel(DevTables t, const T* __restrict__ ring,
 }
 
 // ============================================================ PCG
-// K_B: q = S p assembled from the ring; p = z + beta p; alpha = rz / p^T q.
-template <typename T>
-__global__ void __launch_bounds__(kRedThreads) pcg_assemble_kernel(DevTables t, const T* __restrict__ ring,
-                                                          const double* __restrict__ z, double* p,
-                                                          double* q, PcgState* st,
-                                                          double* partials) {
-  if (st->done) return;
-  __shared__ double scratch[32];
-  const double beta = st->beta;
-  double acc[1] = {0.0};
-  for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < t.n_gamma;
-       g += (int64_t)gridDim.x * blockDim.x) {
-    double qg = 0.0;
-    for (int o = t.owner_ptr[g]; o < t.owner_ptr[g + 1]; ++o) qg += (double)ring[t.owner_idx[o]];
-    const double pg = z[g] + beta * p[g];
-    p[g] = pg;
-    q[g] = qg;
-    acc[0] += pg * qg;
-  }
-  if (grid_sum<1, kRedThreads>(acc, partials, &st->ticket[0], scratch) && threadIdx.x == 0) {
-    const double pq = acc[0];
-    st->pq = pq;
-    if (!(pq > 0.0) || !isfinite(pq)) {
-      st->status = -6;  // breakdown
-      st->done = 1;
-    } else {
-      st->alpha = st->rz / pq;
-    }
-  }
-}
-
-// K_C (and the initial step): x += alpha p; r -= alpha q; z = S~^-1 r;
-// rz = r^T z, rr = r^T r; beta; convergence test.
-template <bool INIT>
-__global__ void __launch_bounds__(kRedThreads) pcg_update_kernel(DevTables t, DevFields fld, const double* __restrict__ gin,
-                                                        double* x, double* r, double* z, double* p,
-                                                        const double* __restrict__ q, PcgState* st,
-                                                        double* partials) {
+// Face blocks: one warp per (face, component) block, z = W^-1 P W^-1 r with P
+// symmetric, read by columns (coalesced); cross points: one thread per DOF.
+// INIT: x = 0, r = g, p = s = 0.  Otherwise w_g = sum of the ring entries of
+// the owning subdomains, p = u + beta p, s = w + beta s, x += alpha p,
+// r -= alpha s.  Both: u = S~^-1 r, gamma = (r, u), rr = (r, r).
+template <typename T, bool INIT>
+__global__ void __launch_bounds__(kRedThreads) pcg_cg_kernel(DevTables t, DevFields fld,
+                                                             const double* __restrict__ gin,
+                                                             const T* __restrict__ ring, double* x,
+                                                             double* r, double* u, double* p,
+                                                             double* sv, PcgState* st) {
   if (st->done) return;
   extern __shared__ double rw_all[];  // (blockDim/32) * max_blk_n
   __shared__ double scratch[64];
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   double* rw = rw_all + wib * t.max_blk_n;
-  const double alpha = INIT ? 0.0 : st->alpha;
+  double alpha = 0.0, beta = 0.0;
+  if (!INIT) {
+    alpha = st->alpha;
+    beta = st->beta;
+  }
   double acc[2] = {0.0, 0.0};
+  auto step = [&](int64_t g) -> double {
+    if (INIT) {
+      x[g] = 0.0;
+      p[g] = 0.0;
+      sv[g] = 0.0;
+      r[g] = gin[g];
+      return gin[g];
+    }
+    double w = 0.0;
+    for (int o = t.owner_ptr[g]; o < t.owner_ptr[g + 1]; ++o) w += (double)ring[t.owner_idx[o]];
+    const double pg = u[g] + beta * p[g];
+    const double sg = w + beta * sv[g];
+    p[g] = pg;
+    sv[g] = sg;
+    x[g] += alpha * pg;
+    const double rg = r[g] - alpha * sg;
+    r[g] = rg;
+    return rg;
+  };
   const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int nw = (gridDim.x * blockDim.x) >> 5;
   for (int b = gw; b < t.n_blocks; b += nw) {
     const int off = t.blk_off[b], n = t.blk_n[b];
     const double* P = t.ptab + t.blk_poff[b];
     for (int i = lane; i < n; i += 32) {
-      const int g = off + i;
-      double ri;
-      if (INIT) {
-        x[g] = 0.0;
-        p[g] = 0.0;
-        ri = gin[g];
-      } else {
-        x[g] += alpha * p[g];
-        ri = r[g] - alpha * q[g];
-      }
-      r[g] = ri;
+      const double ri = step(off + i);
       acc[1] += ri * ri;
-      rw[i] = ri / fld.face_w[g];
+      rw[i] = ri / fld.face_w[off + i];
     }
     __syncwarp();
     for (int i = lane; i < n; i += 32) {
       double zi = 0.0;
-      const double* Pi = P + i * n;
-      for (int j = 0; j < n; ++j) zi += Pi[j] * rw[j];
-      // r_i z_i = (w_i rw_i) (zi / w_i) = rw_i zi
-      acc[0] += rw[i] * zi;
-      z[off + i] = zi / fld.face_w[off + i];
+      for (int j = 0; j < n; ++j) zi += P[j * n + i] * rw[j];
+      acc[0] += rw[i] * zi;  // r_i u_i = (w_i rw_i)(zi / w_i)
+      u[off + i] = zi / fld.face_w[off + i];
     }
     __syncwarp();
   }
   for (int64_t g = t.n_face_dofs + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < t.n_gamma;
        g += (int64_t)gridDim.x * blockDim.x) {
-    double ri;
-    if (INIT) {
-      x[g] = 0.0;
-      p[g] = 0.0;
-      ri = gin[g];
-    } else {
-      x[g] += alpha * p[g];
-      ri = r[g] - alpha * q[g];
-    }
-    r[g] = ri;
+    const double ri = step(g);
     const double zi = ri * fld.cross_scale[g - t.n_face_dofs];
-    z[g] = zi;
+    u[g] = zi;
     acc[0] += ri * zi;
     acc[1] += ri * ri;
   }
-  if (grid_sum<2, kRedThreads>(acc, partials, &st->ticket[1], scratch) && threadIdx.x == 0) {
-    const double rz = acc[0], rr = acc[1];
+  if (grid_sum<2, kRedThreads>(acc, st->partials, &st->ticket[1], scratch) && threadIdx.x == 0) {
+    const double gamma = acc[0], rr = acc[1];
     st->rr = rr;
     if (INIT) {
-      st->beta = 0.0;
       st->it = 0;
+      st->beta = 0.0;
     } else {
-      st->beta = rz / st->rz;
+      st->gamma_prev = st->gamma;
+      st->alpha_prev = st->alpha;
       st->it += 1;
     }
-    st->rz = rz;
+    st->gamma = gamma;
     if (rr <= st->tol2) {
       st->done = 1;
       st->status = 0;
-    } else if (!isfinite(rr) || !isfinite(rz)) {
+    } else if (!isfinite(rr) || !isfinite(gamma)) {
       st->done = 1;
       st->status = -6;
     } else if (st->it >= st->max_it) {
@@ -778,7 +788,7 @@ __global__ void precond_kernel(DevTables t, DevFields fld, const double* __restr
     const double* P = t.ptab + t.blk_poff[b];
     for (int i = lane; i < n; i += 32) {
       double zi = 0.0;
-      for (int j = 0; j < n; ++j) zi += P[i * n + j] * (r[off + j] / fld.face_w[off + j]);
+      for (int j = 0; j < n; ++j) zi += P[j * n + i] * (r[off + j] / fld.face_w[off + j]);
       z[off + i] = zi / fld.face_w[off + i];
     }
   }
@@ -1081,28 +1091,20 @@ static size_t update_smem(const DevTables& t) {
 }
 
 void launch_pcg_init(const DevTables& t, const DevFields& fld, const double* g, double* x, double* r,
-                     double* z, double* p, PcgState* s, double* partials, cudaStream_t st,
-                     int nblk) {
-  pcg_update_kernel<true><<<nblk, kRedThreads, update_smem(t), st>>>(t, fld, g, x, r, z, p, nullptr,
-                                                                     s, partials);
+                     double* u, double* p, double* sv, PcgState* s, cudaStream_t st, int nblk) {
+  pcg_cg_kernel<double, true><<<nblk, kRedThreads, update_smem(t), st>>>(t, fld, g, nullptr, x, r, u,
+                                                                          p, sv, s);
 }
 
-void launch_pcg_assemble(const DevTables& t, int precision, const void* ring, const double* z,
-                         double* p, double* q, PcgState* s, double* partials, cudaStream_t st,
-                         int nblk) {
-  if (precision == 0)
-    pcg_assemble_kernel<double><<<nblk, kRedThreads, 0, st>>>(t, (const double*)ring, z, p, q, s,
-                                                              partials);
-  else
-    pcg_assemble_kernel<float><<<nblk, kRedThreads, 0, st>>>(t, (const float*)ring, z, p, q, s,
-                                                             partials);
-}
-
-void launch_pcg_update(const DevTables& t, const DevFields& fld, double* x, double* r, double* z,
-                       const double* p, const double* q, PcgState* s, double* partials,
+void launch_pcg_update(const DevTables& t, const DevFields& fld, int precision, const void* ring,
+                       double* x, double* r, double* u, double* p, double* sv, PcgState* s,
                        cudaStream_t st, int nblk) {
-  pcg_update_kernel<false><<<nblk, kRedThreads, update_smem(t), st>>>(
-      t, fld, nullptr, x, r, z, const_cast<double*>(p), q, s, partials);
+  if (precision == 0)
+    pcg_cg_kernel<double, false><<<nblk, kRedThreads, update_smem(t), st>>>(
+        t, fld, nullptr, (const double*)ring, x, r, u, p, sv, s);
+  else
+    pcg_cg_kernel<float, false><<<nblk, kRedThreads, update_smem(t), st>>>(
+        t, fld, nullptr, (const float*)ring, x, r, u, p, sv, s);
 }
 
 void launch_precond(const DevTables& t, const DevFields& fld, const double* r, double* z,

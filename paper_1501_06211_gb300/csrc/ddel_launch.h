@@ -32,10 +32,13 @@ struct DevTables {
 };
 
 // PCG scalars kept on the device (read by the host only at check points).
+// Chronopoulos-Gear form of PCG: gamma = (r, u), delta = (S u, u) with
+// u = S~^-1 r; one Schur apply and one preconditioner apply per iteration.
 struct PcgState {
-  double rz, alpha, beta, tol2, rr, pq;
+  double gamma, gamma_prev, delta, alpha, alpha_prev, beta, tol2, rr;
   int it, max_it, done, status;
   unsigned ticket[4];
+  double* partials;  // per-block partial sums (reduction scratch)
 };
 
 // Per-assembly fields.
@@ -57,6 +60,7 @@ struct SchurIO {
   void* ring_out = nullptr;       // per ring slot output (T), nullptr = skip
   double* u_out = nullptr;        // global vector, interior DOFs written, nullptr = skip
   const int* done = nullptr;      // early exit flag
+  PcgState* pcg = nullptr;        // PCG form: also reduce delta = (S u, u) -> alpha, beta
   int* err = nullptr;
 };
 
@@ -83,15 +87,13 @@ void launch_schur_explicit(const DevTables& t, int precision, const void* Sexp, 
 // Sum ring contributions: out[g] = sign * sum(ring) + (base ? base[gamma_dof[g]] : 0)
 void launch_gamma_sum(const DevTables& t, int precision, const void* ring, const double* base,
                       double sign, double* out, cudaStream_t st);
-// PCG kernels
+// PCG kernels (Chronopoulos-Gear form).  init: x = 0, r = g, p = s = 0,
+// u = S~^-1 r, gamma.  update: w = sum(ring), p = u + beta p, s = w + beta s,
+// x += alpha p, r -= alpha s, u = S~^-1 r, gamma; convergence test.
 void launch_pcg_init(const DevTables& t, const DevFields& fld, const double* g, double* x, double* r,
-                     double* z, double* p, PcgState* s, double* partials, cudaStream_t st,
-                     int nblk);
-void launch_pcg_assemble(const DevTables& t, int precision, const void* ring, const double* z,
-                         double* p, double* q, PcgState* s, double* partials, cudaStream_t st,
-                         int nblk);
-void launch_pcg_update(const DevTables& t, const DevFields& fld, double* x, double* r, double* z,
-                       const double* p, const double* q, PcgState* s, double* partials,
+                     double* u, double* p, double* sv, PcgState* s, cudaStream_t st, int nblk);
+void launch_pcg_update(const DevTables& t, const DevFields& fld, int precision, const void* ring,
+                       double* x, double* r, double* u, double* p, double* sv, PcgState* s,
                        cudaStream_t st, int nblk);
 void launch_precond(const DevTables& t, const DevFields& fld, const double* r, double* z,
                     cudaStream_t st);
