@@ -134,6 +134,7 @@ typedef struct ddel_ctx ddel_ctx;
 
 void ddel_default_options(ddel_options* opt);
 const char* ddel_strerror(int status);
+/* Message of the context's last error; with ctx == NULL, of the last failed ddel_create. */
 const char* ddel_last_error(const ddel_ctx* ctx);
 
 /* Set up mesh, DOF classification (Gamma = nodes in two or more subdomain

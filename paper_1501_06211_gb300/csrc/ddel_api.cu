@@ -58,6 +58,8 @@ struct ddel_ctx {
 
 namespace {
 
+std::string g_create_error;  // message of the last failed ddel_create (ddel_last_error(NULL))
+
 int fail(ddel_ctx* c, int code, const std::string& msg) {
   if (c) c->last_error = msg;
   return code;
@@ -272,7 +274,9 @@ const char* ddel_strerror(int s) {
   }
 }
 
-const char* ddel_last_error(const ddel_ctx* ctx) { return ctx ? ctx->last_error.c_str() : ""; }
+const char* ddel_last_error(const ddel_ctx* ctx) {
+  return ctx ? ctx->last_error.c_str() : g_create_error.c_str();
+}
 
 int ddel_create(const ddel_mesh* mesh, const ddel_material* mat, const ddel_bc* bc,
                 const ddel_options* opt, void* cuda_stream, ddel_ctx** out) {
@@ -292,6 +296,7 @@ int ddel_create(const ddel_mesh* mesh, const ddel_material* mat, const ddel_bc* 
                                 bc->point_force, bc->traction_face, bc->traction, ctx->opt.theta,
                                 &ctx->S);
   if (!msg.empty()) {
+    g_create_error = msg;
     delete ctx;
     return DDEL_EINVAL;
   }
@@ -313,7 +318,10 @@ int ddel_create(const ddel_mesh* mesh, const ddel_material* mat, const ddel_bc* 
     }
     return false;
   };
-  if (bad(configure_kernels())) goto fail_out;
+  if (bad(configure_kernels())) {
+    ctx->last_error = "kernel configuration: " + ctx->last_error;
+    goto fail_out;
+  }
   if (cuda_stream) {
     ctx->stream = static_cast<cudaStream_t>(cuda_stream);
   } else {
@@ -386,6 +394,7 @@ int ddel_create(const ddel_mesh* mesh, const ddel_material* mat, const ddel_bc* 
   *out = ctx;
   return DDEL_OK;
 fail_out:
+  g_create_error = ctx->last_error;
   ddel_destroy(ctx);
   return rc != DDEL_OK ? rc : DDEL_ECUDA;
 }
@@ -585,6 +594,7 @@ int ddel_solve(ddel_ctx* ctx, const double* f, double* u, int on_device, ddel_st
   if (stats) *stats = st;
   return status;
 }
+
 
 int ddel_apply_K(ddel_ctx* ctx, const double* x, double* y) {
   if (!ctx || !x || !y) return DDEL_EINVAL;

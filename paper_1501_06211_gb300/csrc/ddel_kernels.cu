@@ -564,13 +564,24 @@ __global__ void __launch_bounds__(256) schur_form2d_kernel(DevTables t, const T*
   for (int j = tid; j < NR; j += 256) rloc[j] = j < si.n_ring ? t.ring_loc[si.ring_off + j] : -1;
   for (int i = tid; i < BP * NR; i += 256) Wb[i] = T(0);
   __syncthreads();
-  const int ty = tid >> 4, tx = tid & 15;
+  // S is symmetric: threads 0..135 own the 136 upper tiles (ty <= tx) of the
+  // 16 x 16 grid of TL x TL tiles; the other warps sit out the SYRK.
+  int ty = 0, tx = 0;
+  const bool owner = tid < 136;
+  if (owner) {
+    int q = tid;
+    while (q >= 16 - ty) {
+      q -= 16 - ty;
+      ++ty;
+    }
+    tx = ty + q;
+  }
   T acc[TL][TL];
 #pragma unroll
   for (int a = 0; a < TL; ++a)
 #pragma unroll
     for (int b = 0; b < TL; ++b)
-      acc[a][b] = kgg_entry2d<T>(s, ke, sc, rloc[ty * TL + a], rloc[tx * TL + b]);
+      acc[a][b] = owner ? kgg_entry2d<T>(s, ke, sc, rloc[ty * TL + a], rloc[tx * TL + b]) : T(0);
   const T* fb = factor + si.factor_off;
   for (int k = 0; k < si.nb; ++k) {
     const T* src = fb + (int64_t)k * STAGE;
@@ -604,7 +615,8 @@ __global__ void __launch_bounds__(256) schur_form2d_kernel(DevTables t, const T*
     }
     __syncthreads();
 #pragma unroll 2
-    for (int m = 0; m < BP; ++m) {  // S -= W_k^T W_k
+    if (owner)
+    for (int m = 0; m < BP; ++m) {  // S -= W_k^T W_k (upper tiles)
       T wi[TL], wj[TL];
 #pragma unroll
       for (int a = 0; a < TL; ++a) {
@@ -619,10 +631,15 @@ __global__ void __launch_bounds__(256) schur_form2d_kernel(DevTables t, const T*
     __syncthreads();
   }
   T* out = Sexp + (int64_t)sub * NR * NR;
+  if (owner) {
 #pragma unroll
-  for (int a = 0; a < TL; ++a)
+    for (int a = 0; a < TL; ++a)
 #pragma unroll
-    for (int b = 0; b < TL; ++b) out[(ty * TL + a) * NR + tx * TL + b] = acc[a][b];
+      for (int b = 0; b < TL; ++b) {
+        out[(ty * TL + a) * NR + tx * TL + b] = acc[a][b];
+        out[(tx * TL + b) * NR + ty * TL + a] = acc[a][b];  // mirror
+      }
+  }
 }
 
 // y_ring = S_i x_ring for every subdomain (PCG form x = z + beta p when zvec).
@@ -1001,11 +1018,18 @@ void launch_schur_explicit(const DevTables& t, int precision, const void* Sexp, 
 
 // ============================================================ launchers
 cudaError_t configure_kernels() {
-  const int big = 232448;
+  int dev = 0, big = 232448;
+  if (cudaGetDevice(&dev) == cudaSuccess)
+    cudaDeviceGetAttribute(&big, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
   cudaError_t e = cudaSuccess;
+  // dynamic opt-in = device maximum minus the kernel's static shared memory
 #define DDEL_CFG(k)                                                                   \
   do {                                                                                \
-    cudaError_t e2 = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, big); \
+    cudaFuncAttributes fa;                                                            \
+    cudaError_t e2 = cudaFuncGetAttributes(&fa, k);                                   \
+    if (e2 == cudaSuccess)                                                            \
+      e2 = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,        \
+                                big - (int)fa.sharedSizeBytes);                       \
     if (e2 != cudaSuccess) e = e2;                                                    \
   } while (0)
   DDEL_CFG((schur2d_kernel<double, 32, 3>));

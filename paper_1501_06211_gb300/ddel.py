@@ -126,8 +126,7 @@ class DDELError(RuntimeError):
 
 def _check(code, ctx=None):
     if code != DDEL_OK:
-        msg = _lib.ddel_last_error(ctx).decode() if ctx else ""
-        raise DDELError(code, msg)
+        raise DDELError(code, _lib.ddel_last_error(ctx).decode())
 
 
 def _ptr(a):
