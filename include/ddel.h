@@ -211,6 +211,42 @@ typedef struct {
 } ddel_kernel_info_t;
 int ddel_kernel_info(const ddel_ctx* ctx, ddel_kernel_info_t* out);
 
+/* --- Residual check without allocation ----------------------------------------
+ * The paper has no counterpart: this entry point exists for callers that cannot
+ * allocate device memory themselves -- code running under an allocator or
+ * runtime that forbids cudaMalloc, or a component that is handed device
+ * buffers by someone else and must not own any.  It computes the same FP64
+ * quantities as ddel_residual_norm without a context and without allocating:
+ * r = f - K(rho) u on the free DOFs (0 on fixed ones) and
+ * norms[0] = ||r||_2, norms[1] = ||f||_2 over the free DOFs.
+ *
+ * Arguments (all device pointers except the sizes and the stream):
+ *   dim, nx, ny, nz  grid of unit elements (nz ignored in 2D), node-interleaved
+ *                    DOFs as everywhere in this header;
+ *   Ke               unit-E element stiffness, (dim 2^dim)^2 doubles, row-major,
+ *                    local node order (0,0),(1,0),(1,1),(0,1) [then z = 1];
+ *   factors          n_elem doubles: the element stiffness factors E rho_e^p;
+ *   fixed            n_dof bytes, nonzero = fixed DOF, or NULL for none;
+ *   f, u             n_dof doubles; r: n_dof doubles output or NULL;
+ *   norms            2 doubles, written on the device;
+ *   cuda_stream      the stream to run on (NULL = legacy default stream).
+ * The call is asynchronous on the stream; read norms after synchronising it.
+ *
+ * Scratch: a fixed 64 KB device array inside the library (one pair of partial
+ * sums per thread block plus an arrival counter), present on every GPU that
+ * loads the library until the process exits.  It caps the grid at 1,048,576
+ * nodes; larger grids return DDEL_EINVAL without launching.  The first call on
+ * each device looks up the array's device address (with that device current);
+ * make that first call before any stream capture.  Every call on a device
+ * shares the one array: calls whose kernels overlap on the GPU (different
+ * streams, no ordering between them) race and may return wrong norms;
+ * serialise them.  The call clears the counter itself; no other state carries
+ * over between calls.  Errors: EINVAL (sizes, null inputs, grid too large),
+ * ECUDA (device address lookup or launch failed). */
+int ddel_residual_norm_noalloc(int dim, int nx, int ny, int nz, const double* Ke,
+                               const double* factors, const uint8_t* fixed, const double* f,
+                               const double* u, double* r, double* norms, void* cuda_stream);
+
 /* --- Host-only plan (no CUDA call; for inspection and tests) --------------- */
 /* The set-up of ddel_create without any device work: DOF classification,
  * interface ordering, face blocks and element matrix.  Errors as ddel_create. */

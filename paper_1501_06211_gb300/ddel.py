@@ -98,6 +98,9 @@ def _load():
         "ddel_load_vector": (c_int, [c_void_p, c_void_p]),
         "ddel_fixed_mask": (c_int, [c_void_p, c_void_p]),
         "ddel_kernel_info": (c_int, [c_void_p, P(ddel_kernel_info_t)]),
+        "ddel_residual_norm_noalloc": (c_int, [c_int, c_int, c_int, c_int, c_void_p, c_void_p,
+                                               c_void_p, c_void_p, c_void_p, c_void_p, c_void_p,
+                                               c_void_p]),
         "ddel_plan_create": (c_int, [P(ddel_mesh), P(ddel_material), P(ddel_bc), c_double,
                                      P(c_void_p)]),
         "ddel_plan_destroy": (None, [c_void_p]),
@@ -224,6 +227,12 @@ def ddel_kernel_info(h):
     d["schur_apply_kernel"] = ("schur_explicit_kernel" if k.schur_form else "schur2d_kernel") + \
         ("<float>" if k.precision else "<double>")
     return d
+
+
+def ddel_residual_norm_noalloc(dim, nx, ny, nz, Ke, factors, fixed, f, u, r, norms, stream=None):
+    """Residual check that allocates nothing (device tensors in, device norms out)."""
+    return _lib.ddel_residual_norm_noalloc(dim, nx, ny, nz, _ptr(Ke), _ptr(factors), _ptr(fixed),
+                                           _ptr(f), _ptr(u), _ptr(r), _ptr(norms), stream)
 
 
 def ddel_gamma_dofs(h, n_gamma):
