@@ -171,6 +171,34 @@ int ddel_factor(ddel_ctx* ctx);
  * else device.  st may be NULL.  Synchronises the stream. */
 int ddel_solve(ddel_ctx* ctx, const double* f, double* u, int on_device, ddel_stats* st);
 
+/* --- Topology optimisation (Sec. 5) ------------------------------------------
+ * One Picard step of the variable-thickness-sheet / SIMP problem of
+ * eq. NumberTen: density filter rho~ = Hbar rho (hat weights
+ * max(0, r_min - distance), rows normalised), finite-element analysis with
+ * element factors E rho~^p (assemble + factor + solve of this library),
+ * compliance c = f^T u, adjoint sensitivities dc/drho~_e = -p E rho~_e^(p-1)
+ * u_e^T K_e u_e, filter chain rule, and the optimality-criteria update
+ * rho_new = clamp(rho (-dc / (lambda dV))^(1/2), max(rho_min, rho - move),
+ * min(1, rho + move)) with lambda found by 64 bisection steps on [0, 1e9] so
+ * that sum(rho~_new) = volfrac * n_elem.  The paper names OC without formulas
+ * (Sec. 5); these are the standard optimality conditions of the Lagrangian. */
+typedef struct {
+  double* rho;        /* device, n_elem: design densities, updated in place */
+  double volfrac;     /* target volume fraction of the filtered densities */
+  double r_min;       /* filter radius in elements (e.g. 1.5) */
+  double move;        /* OC move limit (e.g. 0.2) */
+  int iteration;      /* incremented by every step */
+  double compliance;  /* out: f^T u of this step's analysis */
+  double volume;      /* out: sum of the filtered new densities / n_elem */
+  double change;      /* out: max |rho_new - rho| */
+  double lambda;      /* out: OC volume multiplier */
+  double* u;          /* device, n_dof, or NULL: displacement of this step */
+  double* rho_phys;   /* device, n_elem, or NULL: filtered densities of this step */
+} ddel_topopt_state;
+/* Densities must lie in [rho_min, 1]; the loads are those of ddel_bc.
+ * Synchronises the stream.  st (may be NULL) receives the solve statistics. */
+int ddel_topopt_step(ddel_ctx* ctx, ddel_topopt_state* state, ddel_stats* st);
+
 /* --- Step-level entry points (device pointers; asynchronous) --------------- */
 /* y = K(rho) x over all free DOFs (fixed rows 0), element by element, FP64. */
 int ddel_apply_K(ddel_ctx* ctx, const double* x, double* y);

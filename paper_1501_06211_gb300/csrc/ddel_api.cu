@@ -13,6 +13,7 @@
 #include "../../include/ddel.h"
 #include "ddel_internal.h"
 #include "ddel_launch.h"
+#include "ddel_topopt.h"
 
 using namespace ddel;
 
@@ -53,6 +54,11 @@ struct ddel_ctx {
   int64_t launches = 0;           // kernel launches issued (graph-contained ones included)
   int64_t launches_at_assemble = 0;
   cudaEvent_t ev[8] = {};
+  // topology optimisation buffers (allocated on first use)
+  double *rho_f = nullptr, *dcf = nullptr, *dc = nullptr, *dv = nullptr, *topo_u = nullptr;
+  double* topo_out = nullptr;    // device: lambda, volume, change, compliance
+  double* h_topo = nullptr;      // pinned copy
+  double dv_rmin = -1.0;         // filter radius dv was computed for
   std::string last_error;
 };
 
@@ -412,6 +418,7 @@ void ddel_destroy(ddel_ctx* ctx) {
   if (ctx->h_st) cudaFreeHost(ctx->h_st);
   if (ctx->h_nrm) cudaFreeHost(ctx->h_nrm);
   if (ctx->h_err) cudaFreeHost(ctx->h_err);
+  if (ctx->h_topo) cudaFreeHost(ctx->h_topo);
   for (auto& e : ctx->ev)
     if (e) cudaEventDestroy(e);
   if (ctx->own_stream && ctx->stream) cudaStreamDestroy(ctx->stream);
@@ -595,6 +602,53 @@ int ddel_solve(ddel_ctx* ctx, const double* f, double* u, int on_device, ddel_st
   return status;
 }
 
+
+int ddel_topopt_step(ddel_ctx* ctx, ddel_topopt_state* ts, ddel_stats* stats) {
+  if (!ctx || !ts || !ts->rho) return DDEL_EINVAL;
+  if (!(ts->volfrac > 0.0 && ts->volfrac <= 1.0) || !(ts->r_min > 0.0) || !(ts->move > 0.0))
+    return fail(ctx, DDEL_EINVAL, "topopt: need 0 < volfrac <= 1, r_min > 0, move > 0");
+  if (ts->r_min > 8.0) return fail(ctx, DDEL_EINVAL, "topopt: r_min above 8 elements");
+  cudaStream_t s = ctx->stream;
+  const int64_t ne = ctx->S.n_elem, nd = ctx->S.n_dof;
+  if (!ctx->rho_f) {
+    if (dalloc(ctx, &ctx->rho_f, ne * 8) || dalloc(ctx, &ctx->dcf, ne * 8) ||
+        dalloc(ctx, &ctx->dc, ne * 8) || dalloc(ctx, &ctx->dv, ne * 8) ||
+        dalloc(ctx, &ctx->topo_u, nd * 8) || dalloc(ctx, &ctx->topo_out, 8 * 8))
+      return fail(ctx, DDEL_ENOMEM, "topopt buffers");
+    CK(cudaMallocHost(&ctx->h_topo, 8 * 8));
+  }
+  if (ctx->dv_rmin != ts->r_min) {  // dV/drho = Hbar^T 1
+    launch_fill(ctx->dcf, ne, 1.0, s);
+    launch_filter(ctx->T, ts->r_min, ctx->dcf, ctx->dv, 1, s);
+    ctx->launches += 2;
+    ctx->dv_rmin = ts->r_min;
+  }
+  launch_filter(ctx->T, ts->r_min, ts->rho, ctx->rho_f, 0, s);
+  ctx->launches += 1;
+  int rc = ddel_assemble(ctx, ctx->rho_f, 1);
+  if (rc) return rc;
+  rc = ddel_factor(ctx);
+  if (rc) return rc;
+  double* u = ts->u ? ts->u : ctx->topo_u;
+  rc = ddel_solve(ctx, nullptr, u, 1, stats);
+  if (rc) return rc;
+  launch_dot(ctx->d_load, u, nd, ctx->partials, ctx->ticketK, ctx->topo_out + 3, s);
+  launch_sensitivity(ctx->T, ctx->mat.E, ctx->mat.simp_p, ctx->rho_f, u, ctx->dcf, s);
+  launch_filter(ctx->T, ts->r_min, ctx->dcf, ctx->dc, 1, s);
+  if (ts->rho_phys)
+    CK(cudaMemcpyAsync(ts->rho_phys, ctx->rho_f, ne * 8, cudaMemcpyDeviceToDevice, s));
+  CK(launch_oc(ts->rho, ctx->dc, ctx->dv, ne, ts->volfrac * (double)ne, ctx->mat.rho_min, ts->move,
+               ctx->partials, ctx->topo_out, s));
+  ctx->launches += 4;
+  CK(cudaMemcpyAsync(ctx->h_topo, ctx->topo_out, 4 * 8, cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  ts->lambda = ctx->h_topo[0];
+  ts->volume = ctx->h_topo[1] / (double)ne;
+  ts->change = ctx->h_topo[2];
+  ts->compliance = ctx->h_topo[3];
+  ts->iteration += 1;
+  return DDEL_OK;
+}
 
 int ddel_apply_K(ddel_ctx* ctx, const double* x, double* y) {
   if (!ctx || !x || !y) return DDEL_EINVAL;

@@ -68,6 +68,12 @@ class ddel_kernel_info_t(ctypes.Structure):
                 ("schur_form", c_int), ("precision", c_int)]
 
 
+class ddel_topopt_state(ctypes.Structure):
+    _fields_ = [("rho", c_void_p), ("volfrac", c_double), ("r_min", c_double), ("move", c_double),
+                ("iteration", c_int), ("compliance", c_double), ("volume", c_double),
+                ("change", c_double), ("lambda_", c_double), ("u", c_void_p), ("rho_phys", c_void_p)]
+
+
 def _load():
     if not os.path.exists(LIB_PATH):
         raise ImportError(
@@ -98,6 +104,7 @@ def _load():
         "ddel_load_vector": (c_int, [c_void_p, c_void_p]),
         "ddel_fixed_mask": (c_int, [c_void_p, c_void_p]),
         "ddel_kernel_info": (c_int, [c_void_p, P(ddel_kernel_info_t)]),
+        "ddel_topopt_step": (c_int, [c_void_p, P(ddel_topopt_state), P(ddel_stats)]),
         "ddel_residual_norm_noalloc": (c_int, [c_int, c_int, c_int, c_int, c_void_p, c_void_p,
                                                c_void_p, c_void_p, c_void_p, c_void_p, c_void_p,
                                                c_void_p]),
@@ -218,6 +225,12 @@ def ddel_residual_norm(h, f, u):
     rn, fn = c_double(), c_double()
     code = _lib.ddel_residual_norm(h, _ptr(f), _ptr(u), ctypes.byref(rn), ctypes.byref(fn))
     return code, rn.value, fn.value
+
+
+def ddel_topopt_step(h, state):
+    st = ddel_stats()
+    code = _lib.ddel_topopt_step(h, ctypes.byref(state), ctypes.byref(st))
+    return code, st
 
 
 def ddel_kernel_info(h):
@@ -402,6 +415,21 @@ class Solver:
 
     def factor(self):
         _check(ddel_factor(self.h), self.h)
+
+    def topopt_state(self, rho, volfrac, r_min=1.5, move=0.2, u=None, rho_phys=None):
+        """State for ddel_topopt_step; rho is a CUDA tensor updated in place."""
+        ts = ddel_topopt_state()
+        ts.rho = _ptr(rho)
+        ts.volfrac, ts.r_min, ts.move = volfrac, r_min, move
+        ts.u = _ptr(u)
+        ts.rho_phys = _ptr(rho_phys)
+        self._topo_refs = (rho, u, rho_phys)
+        return ts
+
+    def topopt_step(self, ts):
+        code, st = ddel_topopt_step(self.h, ts)
+        _check(code, self.h)
+        return st
 
     def solve(self, f=None, u=None, check=True):
         """Solve K u = f; f/u torch CUDA tensors (device path) or NumPy (host path)."""
