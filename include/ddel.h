@@ -49,7 +49,14 @@ typedef enum {
   DDEL_ETIMEOUT = -8     /* a bounded device wait ran out; the kernel returned */
 } ddel_status;
 
-typedef enum { DDEL_FP64 = 0, DDEL_FP32 = 1 } ddel_precision;
+/* FP64: factors, local Schur complements and their applications in FP64.
+ * FP32: factors and applications in FP32 (FP64 Krylov vectors and dot
+ *       products, FP64 residual and refinement).
+ * MIXED: FP64 factors and local Schur complements, which are stored and
+ *       applied in FP32 inside PCG (FP64 vectors and dot products); condensation,
+ *       back-substitution and the refinement residual stay FP64.  Where the
+ *       explicit form is unavailable it behaves as FP64. */
+typedef enum { DDEL_FP64 = 0, DDEL_FP32 = 1, DDEL_MIXED = 2 } ddel_precision;
 typedef enum { DDEL_SCHUR_IMPLICIT = 0, DDEL_SCHUR_EXPLICIT = 1, DDEL_SCHUR_AUTO = 2 } ddel_schur_mode;
 typedef enum { DDEL_X0_ZERO = 0, DDEL_X0_WARM = 1, DDEL_X0_GIVEN = 2 } ddel_x0_mode;
 

@@ -28,7 +28,10 @@ struct ddel_ctx {
   bool own_stream = false;
   std::vector<void*> allocs;
   void* factor[2] = {nullptr, nullptr};
+  void* work3d[2] = {nullptr, nullptr};  // 3D factorisation scratch
   void* sexp[2] = {nullptr, nullptr};  // explicit local Schur complements (2D)
+  float* sexp32 = nullptr;             // MIXED: FP64-formed S_i rounded to FP32
+  bool mixed_ready = false;
   bool explicit_ok[2] = {false, false};
   bool factored[2] = {false, false};
   int active_prec = 0;
@@ -50,6 +53,7 @@ struct ddel_ctx {
   int nblk = 0;
   cudaGraphExec_t graph[2] = {nullptr, nullptr};
   bool graph_explicit[2] = {false, false};
+  bool graph_apply32[2] = {false, false};
   int graph_iters = 0;
   int64_t launches = 0;           // kernel launches issued (graph-contained ones included)
   int64_t launches_at_assemble = 0;
@@ -130,53 +134,79 @@ SchurIO make_io(ddel_ctx* ctx) {
   return io;
 }
 
-int pcg_run(ddel_ctx* ctx, int prec, const double* g, int* iters, int* status) {
+// One PCG iteration: w = S u (ring) with delta = (S u, u) -> alpha, beta; then
+// the vector updates and u = S~^-1 r with gamma = (r, u).
+void pcg_iteration(ddel_ctx* ctx, int prec, bool apply32) {
   cudaStream_t s = ctx->stream;
-  launch_pcg_init(ctx->T, ctx->F, g, ctx->x, ctx->r, ctx->z, ctx->p, ctx->sv, ctx->st, s, ctx->nblk);
-  ctx->launches += 1;
-  // one iteration: w = S u (ring) with delta = (S u, u) -> alpha, beta; then the
-  // vector updates and u = S~^-1 r with gamma = (r, u)
   SchurIO io = make_io(ctx);
   io.x = ctx->z;
   io.ring_out = ctx->ring;
   io.done = &ctx->st->done;
   io.pcg = ctx->st;
+  const bool expl = ctx->explicit_ok[prec];
+  const int aprec = apply32 ? 1 : prec;  // precision of the Schur apply and ring
+  const void* smat = apply32 ? (const void*)ctx->sexp32 : ctx->sexp[prec];
+  if (expl)
+    launch_schur_explicit(ctx->T, aprec, smat, io, s);
+  else
+    launch_schur(ctx->T, ctx->F, prec, ctx->factor[prec], io, s);
+  launch_pcg_update(ctx->T, ctx->F, expl ? aprec : prec, ctx->ring, ctx->x, ctx->r, ctx->z, ctx->p,
+                    ctx->sv, ctx->st, s, ctx->nblk);
+}
+
+// PCG initialisation (asynchronous) and, with use_graph, the CUDA graph of
+// check_every iterations for this precision and form.
+int pcg_start(ddel_ctx* ctx, int prec, const double* g, bool apply32) {
+  cudaStream_t s = ctx->stream;
+  launch_pcg_init(ctx->T, ctx->F, g, ctx->x, ctx->r, ctx->z, ctx->p, ctx->sv, ctx->st, s, ctx->nblk);
+  ctx->launches += 1;
   const int per = ctx->opt.check_every > 0 ? ctx->opt.check_every : 16;
   const bool expl = ctx->explicit_ok[prec];
-  if (ctx->graph[prec] && ctx->graph_explicit[prec] != expl) {
+  if (ctx->graph[prec] && (ctx->graph_explicit[prec] != expl || ctx->graph_apply32[prec] != apply32 ||
+                           ctx->graph_iters != per)) {
     cudaGraphExecDestroy(ctx->graph[prec]);
     ctx->graph[prec] = nullptr;
   }
-  auto iteration = [&]() {
-    if (expl)
-      launch_schur_explicit(ctx->T, prec, ctx->sexp[prec], io, s);
-    else
-      launch_schur(ctx->T, ctx->F, prec, ctx->factor[prec], io, s);
-    launch_pcg_update(ctx->T, ctx->F, prec, ctx->ring, ctx->x, ctx->r, ctx->z, ctx->p, ctx->sv,
-                      ctx->st, s, ctx->nblk);
-  };
-  if (ctx->opt.use_graph && (!ctx->graph[prec] || ctx->graph_iters != per)) {
-    if (ctx->graph[prec]) cudaGraphExecDestroy(ctx->graph[prec]);
-    ctx->graph[prec] = nullptr;
+  if (ctx->opt.use_graph && !ctx->graph[prec]) {
     cudaGraph_t graph;
     CK(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
-    for (int i = 0; i < per; ++i) iteration();
+    for (int i = 0; i < per; ++i) pcg_iteration(ctx, prec, apply32);
     CK(cudaStreamEndCapture(s, &graph));
     CK(cudaGraphInstantiate(&ctx->graph[prec], graph, 0));
     cudaGraphDestroy(graph);
     ctx->graph_iters = per;
     ctx->graph_explicit[prec] = expl;
+    ctx->graph_apply32[prec] = apply32;
   }
+  return DDEL_OK;
+}
+
+// Issues check_every iterations and the copy of the PCG state to the host
+// (asynchronous; ctx->ev[7] is recorded after the copy).
+int pcg_issue(ddel_ctx* ctx, int prec, bool apply32) {
+  cudaStream_t s = ctx->stream;
+  const int per = ctx->opt.check_every > 0 ? ctx->opt.check_every : 16;
+  if (ctx->opt.use_graph) {
+    CK(cudaGraphLaunch(ctx->graph[prec], s));
+  } else {
+    for (int i = 0; i < per; ++i) pcg_iteration(ctx, prec, apply32);
+  }
+  ctx->launches += 2 * per;
+  CK(cudaMemcpyAsync(ctx->h_st, ctx->st, sizeof(PcgState), cudaMemcpyDeviceToHost, s));
+  CK(cudaEventRecord(ctx->ev[7], s));
+  return DDEL_OK;
+}
+
+int pcg_run(ddel_ctx* ctx, int prec, const double* g, int* iters, int* status,
+            bool apply32 = false) {
+  int rc = pcg_start(ctx, prec, g, apply32);
+  if (rc) return rc;
+  const int per = ctx->opt.check_every > 0 ? ctx->opt.check_every : 16;
   const int max_checks = ctx->opt.max_it / per + 2;
   for (int chk = 0; chk < max_checks; ++chk) {
-    if (ctx->opt.use_graph) {
-      CK(cudaGraphLaunch(ctx->graph[prec], s));
-    } else {
-      for (int i = 0; i < per; ++i) iteration();
-    }
-    ctx->launches += 2 * per;
-    CK(cudaMemcpyAsync(ctx->h_st, ctx->st, sizeof(PcgState), cudaMemcpyDeviceToHost, s));
-    CK(cudaStreamSynchronize(s));
+    rc = pcg_issue(ctx, prec, apply32);
+    if (rc) return rc;
+    CK(cudaEventSynchronize(ctx->ev[7]));
     if (ctx->h_st->done) break;
   }
   *iters = ctx->h_st->it;
@@ -213,7 +243,12 @@ int factor_prec(ddel_ctx* ctx, int prec) {
   }
   const int init[2] = {0, 0x7fffffff};
   CK(cudaMemcpyAsync(ctx->err, init, sizeof(init), cudaMemcpyHostToDevice, ctx->stream));
-  launch_factor(ctx->T, ctx->F, prec, ctx->factor[prec], ctx->err, ctx->bad_sub, ctx->stream);
+  if (ctx->T.dim == 3 && !ctx->work3d[prec]) {
+    cudaError_t e = cudaMalloc(&ctx->work3d[prec], factor3d_work_elems(ctx->T) * (prec ? 4 : 8));
+    if (e != cudaSuccess) return fail(ctx, DDEL_ENOMEM, "3D factor scratch");
+  }
+  launch_factor(ctx->T, ctx->F, prec, ctx->factor[prec], ctx->work3d[prec], ctx->err, ctx->bad_sub,
+                ctx->stream);
   ctx->launches += 1;
   CK(cudaGetLastError());
   ctx->factored[prec] = false;
@@ -307,10 +342,6 @@ int ddel_create(const ddel_mesh* mesh, const ddel_material* mat, const ddel_bc* 
     return DDEL_EINVAL;
   }
   if (!(mat->simp_p > 0)) {
-    delete ctx;
-    return DDEL_EINVAL;
-  }
-  if (mesh->dim != 2) {  // the 3D path is provided by ddel_kernels3d.cu when built
     delete ctx;
     return DDEL_EINVAL;
   }
@@ -415,6 +446,9 @@ void ddel_destroy(ddel_ctx* ctx) {
     if (p) cudaFree(p);
   for (void* p : ctx->sexp)
     if (p) cudaFree(p);
+  for (void* p : ctx->work3d)
+    if (p) cudaFree(p);
+  if (ctx->sexp32) cudaFree(ctx->sexp32);
   if (ctx->h_st) cudaFreeHost(ctx->h_st);
   if (ctx->h_nrm) cudaFreeHost(ctx->h_nrm);
   if (ctx->h_err) cudaFreeHost(ctx->h_err);
@@ -482,6 +516,18 @@ int ddel_factor(ddel_ctx* ctx) {
   int rc = factor_prec(ctx, want);
   if (rc == DDEL_ENOTSPD && want == 1) rc = factor_prec(ctx, 0);  // FP32 pivot failed: FP64
   if (rc == DDEL_OK) ctx->active_prec = ctx->factored[want] ? want : 0;
+  ctx->mixed_ready = false;
+  if (rc == DDEL_OK && ctx->opt.precision == DDEL_MIXED && ctx->explicit_ok[0]) {
+    // FP64-formed local Schur complements, stored (and applied) in FP32
+    const int NR = explicit_ring_size(ctx->T);
+    const int64_t n = (int64_t)ctx->T.n_sub * NR * NR;
+    if (!ctx->sexp32 && cudaMalloc(&ctx->sexp32, n * 4) != cudaSuccess)
+      return fail(ctx, DDEL_ENOMEM, "mixed Schur allocation");
+    launch_round_f32((const double*)ctx->sexp[0], ctx->sexp32, n, ctx->stream);
+    ctx->launches += 1;
+    CK(cudaGetLastError());
+    ctx->mixed_ready = true;
+  }
   return rc;
 }
 
@@ -508,15 +554,16 @@ int ddel_solve(ddel_ctx* ctx, const double* f, double* u, int on_device, ddel_st
   double t_cond = 0, t_pcg = 0, t_back = 0, t_ver = 0;
   double prev_relres = INFINITY;
   int prec = ctx->active_prec;
+  bool apply32 = ctx->mixed_ready && prec == 0;
   for (int cyc = 0; cyc < ctx->opt.max_cycles; ++cyc) {
-    set_tol_kernel<<<1, 1, 0, s>>>(ctx->st, ctx->nrm, ctx->opt.tol, ctx->opt.inner_tol, prec,
-                                   ctx->opt.max_it);
+    set_tol_kernel<<<1, 1, 0, s>>>(ctx->st, ctx->nrm, ctx->opt.tol, ctx->opt.inner_tol,
+                                   (prec == 1 || apply32) ? 1 : 0, ctx->opt.max_it);
     ctx->launches += 1;
     CK(cudaEventRecord(ctx->ev[1], s));
     condense(ctx, prec, ctx->d_r, ctx->g);
     CK(cudaEventRecord(ctx->ev[2], s));
     int it = 0, pst = 0;
-    int rc = pcg_run(ctx, prec, ctx->g, &it, &pst);
+    int rc = pcg_run(ctx, prec, ctx->g, &it, &pst, apply32);
     if (rc) return rc;
     st.iters += it;
     CK(cudaEventRecord(ctx->ev[3], s));
@@ -546,6 +593,16 @@ int ddel_solve(ddel_ctx* ctx, const double* f, double* u, int on_device, ddel_st
     }
     const bool diverged = pst == DDEL_EBREAKDOWN || !std::isfinite(st.relres) ||
                           st.relres > (cyc == 0 ? 1.0 : prev_relres);
+    if (diverged && apply32) {  // FP32-stored Schur complements: continue with FP64 ones
+      launch_axpy(nd, -1.0, ctx->d_d, ctx->d_u, s);
+      launch_apply_K(ctx->T, ctx->F, ctx->d_u, ctx->d_f, ctx->d_r, 1, ctx->partials, ctx->ticketK,
+                     ctx->nrm, s, ctx->nblk);
+      ctx->launches += 2;
+      apply32 = false;
+      st.fallback = 1;
+      prev_relres = INFINITY;
+      continue;
+    }
     if (diverged && prec == 1) {
       // The FP32 operator lost definiteness or the correction diverged
       // (possible at high stiffness contrast): discard this correction and
@@ -572,6 +629,12 @@ int ddel_solve(ddel_ctx* ctx, const double* f, double* u, int on_device, ddel_st
       break;
     }
     if (cyc > 0 && st.relres > 0.5 * prev_relres) {
+      if (apply32) {  // stalled above the target: finish with the FP64 Schur complements
+        apply32 = false;
+        st.fallback = 1;
+        prev_relres = st.relres;
+        continue;
+      }
       if (prec == 1) {  // FP32 refinement stalls above the target: finish in FP64
         if (!ctx->factored[0]) {
           int rc2 = factor_prec(ctx, 0);

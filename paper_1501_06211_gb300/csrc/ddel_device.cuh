@@ -5,6 +5,7 @@
 #include <stdint.h>
 
 #include "ddel_internal.h"
+#include "ddel_launch.h"
 
 namespace ddel {
 
@@ -142,6 +143,25 @@ __device__ __forceinline__ void elem_node_offset(int a, int& dx, int& dy, int& d
   dx = (q == 1 || q == 2);
   dy = (q >= 2);
   dz = a >> 2;
+}
+
+// Alpha and beta of the Chronopoulos-Gear recurrence, from gamma = (r, u) of
+// the last update and delta = (S u, u) of the Schur apply just finished.
+__device__ __forceinline__ void cg_coefficients(PcgState* st, double delta) {
+  st->delta = delta;
+  const double gamma = st->gamma;
+  double beta = 0.0, den = delta;
+  if (st->it > 0) {
+    beta = gamma / st->gamma_prev;
+    den = delta - beta * gamma / st->alpha_prev;
+  }
+  if (!(den > 0.0) || !isfinite(den)) {
+    st->status = -6;  // breakdown
+    st->done = 1;
+    return;
+  }
+  st->beta = beta;
+  st->alpha = gamma / den;
 }
 
 }  // namespace ddel

@@ -237,25 +237,6 @@ __global__ void __launch_bounds__(128) factor2d_kernel(DevTables t, const T* __r
   }
 }
 
-// Alpha and beta of the Chronopoulos-Gear recurrence, from gamma = (r, u) of
-// the last update and delta = (S u, u) of the Schur apply just finished.
-__device__ __forceinline__ void cg_coefficients(PcgState* st, double delta) {
-  st->delta = delta;
-  const double gamma = st->gamma;
-  double beta = 0.0, den = delta;
-  if (st->it > 0) {
-    beta = gamma / st->gamma_prev;
-    den = delta - beta * gamma / st->alpha_prev;
-  }
-  if (!(den > 0.0) || !isfinite(den)) {
-    st->status = -6;  // breakdown
-    st->done = 1;
-    return;
-  }
-  st->beta = beta;
-  st->alpha = gamma / den;
-}
-
 // ============================================================ subdomain solve
 // K^(i) xloc at local closure node (a, b), component c (element by element,
 // only elements of this subdomain).
@@ -1049,7 +1030,8 @@ cudaError_t configure_kernels() {
   DDEL_CFG((schur_form2d_kernel<float, 32, 64>));
   DDEL_CFG((schur_form2d_kernel<float, 32, 128>));
 #undef DDEL_CFG
-  return e;
+  cudaError_t e3 = configure_kernels3d();
+  return e != cudaSuccess ? e : e3;
 }
 
 void launch_assemble(const DevTables& t, const DevFields& fld, const double* rho, double E, double p,
@@ -1064,8 +1046,12 @@ void launch_assemble(const DevTables& t, const DevFields& fld, const double* rho
       t, fld, face_scaling, crosspoint_mode);
 }
 
-void launch_factor(const DevTables& t, const DevFields& fld, int precision, void* factor, int* err,
-                   int* bad_sub, cudaStream_t st) {
+void launch_factor(const DevTables& t, const DevFields& fld, int precision, void* factor, void* work,
+                   int* err, int* bad_sub, cudaStream_t st) {
+  if (t.dim == 3) {
+    launch_factor3d(t, fld, precision, factor, work, err, bad_sub, st);
+    return;
+  }
   if (precision == 0) {
     if (t.BP == 32) run_factor<double, 32>(t, fld, factor, err, bad_sub, st);
     else if (t.BP == 64) run_factor<double, 64>(t, fld, factor, err, bad_sub, st);
@@ -1090,6 +1076,10 @@ size_t schur_smem_bytes(const DevTables& t, int precision) {
 
 void launch_schur(const DevTables& t, const DevFields& fld, int precision, const void* factor,
                   const SchurIO& io, cudaStream_t st) {
+  if (t.dim == 3) {
+    launch_schur3d(t, fld, precision, factor, io, st);
+    return;
+  }
   if (precision == 0) {
     if (t.BP == 32) run_schur<double, 32, 3>(t, fld, factor, io, st);
     else if (t.BP == 64) run_schur<double, 64, 2>(t, fld, factor, io, st);
@@ -1148,6 +1138,16 @@ void launch_apply_K(const DevTables& t, const DevFields& fld, const double* x, c
 void launch_scatter_gamma(const DevTables& t, const double* xg, double* u, cudaStream_t st) {
   scatter_gamma_kernel<<<grid_for(t.n_dof > t.n_gamma ? t.n_dof : t.n_gamma, 256), 256, 0, st>>>(
       t, xg, u);
+}
+
+__global__ void round_f32_kernel(const double* __restrict__ in, float* __restrict__ out, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    out[i] = (float)in[i];
+}
+
+void launch_round_f32(const double* in, float* out, int64_t n, cudaStream_t st) {
+  round_f32_kernel<<<grid_for(n, 256), 256, 0, st>>>(in, out, n);
 }
 
 void launch_axpy(int64_t n, double a, const double* x, double* y, cudaStream_t st) {

@@ -1,0 +1,452 @@
+// 3D H8 path: factorisation and per-subdomain solve for blocks too large for
+// shared memory (interior planes of up to 8 x 8 nodes x 3 components).
+//
+//  * factor3d_kernel: one CTA per subdomain; per interior plane k the block
+//    A_kk - C_k C_k^T is assembled in a global scratch matrix, factorised by a
+//    blocked right-looking Cholesky (32-wide panels through shared memory),
+//    inverted by blocked forward substitution (D_k = L_kk^-1), and
+//    C_{k+1} = A_{k+1,k} D_k^T is formed by a tiled product.  The factor layout
+//    is the one of the 2D path: [C_k (column-major) | D_k (packed lower,
+//    column-major)] per plane.
+//  * schur3d_kernel: one CTA per subdomain: w = f_I - K_IG x element by element,
+//    block forward/backward substitution with coalesced column reads of the
+//    factor, t into the local closure, y = (K^(i) [t; x])_G on the ring.
+#include <cmath>
+
+#include "ddel_device.cuh"
+#include "ddel_launch.h"
+
+namespace ddel {
+namespace {
+
+constexpr int kT3 = 256;  // threads per CTA
+constexpr int TB = 32;    // tile edge
+
+__device__ __forceinline__ int64_t node3(const DevTables& t, int i, int j, int k) {
+  return ((int64_t)i * t.nn[1] + j) * t.nn[2] + k;
+}
+
+// Interior row r of plane k -> grid node and component (3D): rows enumerate
+// (y, z) of the plane with z fastest, then the 3 components.
+__device__ __forceinline__ void row_node3(const SubInfo& si, int k, int r, int& x, int& y, int& z,
+                                          int& c) {
+  c = r % 3;
+  const int q = r / 3;
+  x = si.ilo[0] + k;
+  y = si.ilo[1] + q / si.icnt[2];
+  z = si.ilo[2] + q % si.icnt[2];
+}
+
+template <typename T>
+__device__ T entry3d(const DevTables& t, const SubInfo& si, const T* ke, const T* __restrict__ scale,
+                     int kr, int r, int kc, int c) {
+  const bool vr = r < si.bsz, vc = c < si.bsz;
+  if (!vr || !vc) return (kr == kc && r == c) ? T(1) : T(0);
+  int xr, yr, zr, cr, xc, yc, zc, cc;
+  row_node3(si, kr, r, xr, yr, zr, cr);
+  row_node3(si, kc, c, xc, yc, zc, cc);
+  const bool fr = t.fixed[3 * node3(t, xr, yr, zr) + cr];
+  const bool fc = t.fixed[3 * node3(t, xc, yc, zc) + cc];
+  if (fr || fc) return (kr == kc && r == c) ? T(1) : T(0);
+  if (abs(xr - xc) > 1 || abs(yr - yc) > 1 || abs(zr - zc) > 1) return T(0);
+  T sum = T(0);
+  const int s = t.s;
+  for (int ex = max(xr, xc) - 1; ex <= min(xr, xc); ++ex) {
+    if (ex - si.lo[0] < 0 || ex - si.lo[0] >= s) continue;
+    for (int ey = max(yr, yc) - 1; ey <= min(yr, yc); ++ey) {
+      if (ey - si.lo[1] < 0 || ey - si.lo[1] >= s) continue;
+      for (int ez = max(zr, zc) - 1; ez <= min(zr, zc); ++ez) {
+        if (ez - si.lo[2] < 0 || ez - si.lo[2] >= s) continue;
+        const int la = elem_local_node(xr - ex, yr - ey, zr - ez);
+        const int lb = elem_local_node(xc - ex, yc - ey, zc - ez);
+        const int64_t e = ((int64_t)ex * t.ne[1] + ey) * t.ne[2] + ez;
+        sum += scale[e] * ke[(la * 3 + cr) * 24 + lb * 3 + cc];
+      }
+    }
+  }
+  return sum;
+}
+
+// C(i, j) += alpha * sum_m A(i, m) B(j, m) for i < M, j < N (j <= i when lower),
+// with general strides A(i, m) = A[i * ai + m * am], B(j, m) = B[j * bj + m * bm],
+// C(i, j) = C[i * ci + j * cj].  32 x 32 x 32 tiles through shared memory.
+template <typename T>
+__device__ void cta_gemm(int M, int N, int K, const T* A, int ai, int am, const T* B, int bj, int bm,
+                         T* C, int ci, int cj, T alpha, bool lower, T* sA, T* sB) {
+  const int tid = threadIdx.x;
+  const int ty = tid / 16, tx = tid % 16;  // each thread: rows ty, ty+16; cols tx, tx+16
+  for (int i0 = 0; i0 < M; i0 += TB)
+    for (int j0 = 0; j0 < N; j0 += TB) {
+      if (lower && j0 > i0 + TB - 1) continue;
+      T acc[2][2] = {{T(0), T(0)}, {T(0), T(0)}};
+      for (int m0 = 0; m0 < K; m0 += TB) {
+        for (int q = tid; q < TB * TB; q += kT3) {
+          const int a = q / TB, b = q % TB;  // a: row in tile, b: m in tile
+          const int i = i0 + a, j = j0 + a, m = m0 + b;
+          sA[a * (TB + 1) + b] = (i < M && m < K) ? A[(int64_t)i * ai + (int64_t)m * am] : T(0);
+          sB[a * (TB + 1) + b] = (j < N && m < K) ? B[(int64_t)j * bj + (int64_t)m * bm] : T(0);
+        }
+        __syncthreads();
+#pragma unroll 8
+        for (int b = 0; b < TB; ++b) {
+          const T a0 = sA[ty * (TB + 1) + b], a1 = sA[(ty + 16) * (TB + 1) + b];
+          const T b0 = sB[tx * (TB + 1) + b], b1 = sB[(tx + 16) * (TB + 1) + b];
+          acc[0][0] += a0 * b0;
+          acc[0][1] += a0 * b1;
+          acc[1][0] += a1 * b0;
+          acc[1][1] += a1 * b1;
+        }
+        __syncthreads();
+      }
+#pragma unroll
+      for (int u = 0; u < 2; ++u)
+#pragma unroll
+        for (int v = 0; v < 2; ++v) {
+          const int i = i0 + ty + 16 * u, j = j0 + tx + 16 * v;
+          if (i < M && j < N && (!lower || j <= i))
+            C[(int64_t)i * ci + (int64_t)j * cj] += alpha * acc[u][v];
+        }
+    }
+  __syncthreads();
+}
+
+// Blocked right-looking Cholesky of the row-major n x n matrix A (lower part);
+// pivots that are not positive set *bad and are replaced by 1.
+template <typename T>
+__device__ void cta_cholesky(T* A, int n, T* sA, T* sB, bool* bad) {
+  const int tid = threadIdx.x;
+  for (int jb = 0; jb < n; jb += TB) {
+    const int w = min(TB, n - jb);
+    // diagonal tile in shared memory
+    for (int q = tid; q < TB * TB; q += kT3) {
+      const int a = q / TB, b = q % TB;
+      sA[a * (TB + 1) + b] = (a < w && b < w) ? A[(int64_t)(jb + a) * n + jb + b] : T(0);
+    }
+    __syncthreads();
+    for (int j = 0; j < w; ++j) {
+      if (tid == 0) {
+        T d = sA[j * (TB + 1) + j];
+        if (!(d > T(0)) || !isfinite((double)d)) {
+          *bad = true;
+          d = T(1);
+        }
+        sA[j * (TB + 1) + j] = sqrt(d);
+      }
+      __syncthreads();
+      const T ljj = sA[j * (TB + 1) + j];
+      if (tid > j && tid < w) sA[tid * (TB + 1) + j] /= ljj;
+      __syncthreads();
+      for (int q = tid; q < TB * TB; q += kT3) {
+        const int a = q / TB, b = q % TB;
+        if (a > j && b > j && b <= a && a < w) sA[a * (TB + 1) + b] -= sA[a * (TB + 1) + j] * sA[b * (TB + 1) + j];
+      }
+      __syncthreads();
+    }
+    for (int q = tid; q < TB * TB; q += kT3) {
+      const int a = q / TB, b = q % TB;
+      if (a < w && b <= a) A[(int64_t)(jb + a) * n + jb + b] = sA[a * (TB + 1) + b];
+    }
+    __syncthreads();
+    // panel: rows below, X L11^T = A21 (forward substitution across the w columns)
+    for (int i = jb + w + tid; i < n; i += kT3) {
+      T* row = A + (int64_t)i * n + jb;
+      for (int c = 0; c < w; ++c) {
+        T v = row[c];
+        for (int m = 0; m < c; ++m) v -= row[m] * sA[c * (TB + 1) + m];
+        row[c] = v / sA[c * (TB + 1) + c];
+      }
+    }
+    __syncthreads();
+    // trailing update A22 -= L21 L21^T (lower)
+    const int r0 = jb + w;
+    if (r0 < n)
+      cta_gemm<T>(n - r0, n - r0, w, A + (int64_t)r0 * n + jb, n, 1, A + (int64_t)r0 * n + jb, n, 1,
+                  A + (int64_t)r0 * n + r0, n, 1, T(-1), true, sA, sB);
+  }
+}
+
+// D = L^-1 (both row-major n x n, lower) by block rows:
+// D_i,: = L_ii^-1 (E_i - L_i,<i D_<i,:).
+template <typename T>
+__device__ void cta_tri_inverse(const T* L, T* D, int n, T* sA, T* sB) {
+  const int tid = threadIdx.x;
+  for (int q = tid; q < n * n; q += kT3) D[q] = T(0);
+  __syncthreads();
+  for (int ib = 0; ib < n; ib += TB) {
+    const int w = min(TB, n - ib);
+    // R = E_i - L_i,<i D_<i,: for columns 0 .. ib+w-1 (stored into D's block row)
+    for (int q = tid; q < w * (ib + w); q += kT3) {
+      const int a = q / (ib + w), j = q % (ib + w);
+      D[(int64_t)(ib + a) * n + j] = (ib + a == j) ? T(1) : T(0);
+    }
+    __syncthreads();
+    if (ib > 0)
+      cta_gemm<T>(w, ib, ib, L + (int64_t)ib * n, n, 1, D, 1, n, D + (int64_t)ib * n, n, 1, T(-1),
+                  false, sA, sB);
+    // solve L_ii X = R in place (forward substitution down the w rows)
+    for (int q = tid; q < TB * TB; q += kT3) {
+      const int a = q / TB, b = q % TB;
+      sA[a * (TB + 1) + b] = (a < w && b < w) ? L[(int64_t)(ib + a) * n + ib + b] : T(0);
+    }
+    __syncthreads();
+    for (int a = 0; a < w; ++a) {
+      for (int j = tid; j < ib + w; j += kT3) {
+        T v = D[(int64_t)(ib + a) * n + j];
+        for (int m = 0; m < a; ++m) v -= sA[a * (TB + 1) + m] * D[(int64_t)(ib + m) * n + j];
+        D[(int64_t)(ib + a) * n + j] = v / sA[a * (TB + 1) + a];
+      }
+      __syncthreads();
+    }
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kT3) factor3d_kernel(DevTables t, const T* __restrict__ Ke_g,
+                                                       const T* __restrict__ scale,
+                                                       T* __restrict__ factor, T* __restrict__ work,
+                                                       int* err, int* bad_sub) {
+  const int BP = t.BP, PC = BP * BP, PD = BP * (BP + 1) / 2, STAGE = PC + PD;
+  const int sub = blockIdx.x, tid = threadIdx.x;
+  const SubInfo si = t.subs[sub];
+  __shared__ T ke[576];
+  __shared__ T sA[TB * (TB + 1)], sB[TB * (TB + 1)];
+  __shared__ bool bad;
+  for (int i = tid; i < 576; i += kT3) ke[i] = Ke_g[i];
+  if (tid == 0) bad = false;
+  __syncthreads();
+  T* A = work + (int64_t)sub * 2 * PC;  // A_kk, then L_kk, then A_{k+1,k}
+  T* D = A + PC;                         // dense D_k
+  T* fb = factor + si.factor_off;
+  for (int k = 0; k < si.nb; ++k) {
+    for (int q = tid; q < PC; q += kT3) {
+      const int i = q / BP, j = q % BP;
+      A[q] = j <= i ? entry3d<T>(t, si, ke, scale, k, i, k, j) : T(0);
+    }
+    __syncthreads();
+    if (k > 0) {  // A -= C_k C_k^T, C_k column-major in the factor
+      const T* Ck = fb + (int64_t)k * STAGE;
+      cta_gemm<T>(BP, BP, BP, Ck, 1, BP, Ck, 1, BP, A, BP, 1, T(-1), true, sA, sB);
+    }
+    cta_cholesky<T>(A, BP, sA, sB, &bad);
+    cta_tri_inverse<T>(A, D, BP, sA, sB);
+    __syncthreads();
+    T* Dg = fb + (int64_t)k * STAGE + PC;
+    for (int q = tid; q < PC; q += kT3) {
+      const int j = q / BP, r = q % BP;  // column-major walk
+      if (r >= j) Dg[j * BP - j * (j - 1) / 2 + (r - j)] = D[(int64_t)r * BP + j];
+    }
+    if (k + 1 < si.nb) {
+      for (int q = tid; q < PC; q += kT3) {
+        const int i = q / BP, j = q % BP;
+        A[q] = entry3d<T>(t, si, ke, scale, k + 1, i, k, j);
+      }
+      __syncthreads();
+      // C_{k+1}^T = D N^T, stored row-major = C_{k+1} column-major
+      T* Cg = fb + (int64_t)(k + 1) * STAGE;
+      for (int q = tid; q < PC; q += kT3) Cg[q] = T(0);
+      __syncthreads();
+      cta_gemm<T>(BP, BP, BP, D, BP, 1, A, BP, 1, Cg, BP, 1, T(1), false, sA, sB);
+    }
+    __syncthreads();
+  }
+  if (tid == 0 && bad) {
+    atomicExch(err, kErrPivot);
+    atomicMin(bad_sub, sub);
+  }
+}
+
+// K^(i) xloc at local closure node (a, b, c), component comp (3D).
+template <typename T>
+__device__ __forceinline__ T ebe_local3d(const T* ke, const T* sc, const T* xloc, int s, int a, int b,
+                                         int c, int comp) {
+  const int s1 = s + 1;
+  T acc = T(0);
+  for (int dx = 0; dx < 2; ++dx) {
+    const int ea = a - dx;
+    if (ea < 0 || ea >= s) continue;
+    for (int dy = 0; dy < 2; ++dy) {
+      const int eb = b - dy;
+      if (eb < 0 || eb >= s) continue;
+      for (int dz = 0; dz < 2; ++dz) {
+        const int ec = c - dz;
+        if (ec < 0 || ec >= s) continue;
+        const T* krow = ke + (elem_local_node(dx, dy, dz) * 3 + comp) * 24;
+        T part = T(0);
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+          int ox, oy, oz;
+          elem_node_offset(q, ox, oy, oz);
+          const T* xn = xloc + (((ea + ox) * s1 + (eb + oy)) * s1 + (ec + oz)) * 3;
+          part += krow[3 * q] * xn[0] + krow[3 * q + 1] * xn[1] + krow[3 * q + 2] * xn[2];
+        }
+        acc += sc[(ea * s + eb) * s + ec] * part;
+      }
+    }
+  }
+  return acc;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kT3) schur3d_kernel(DevTables t, const T* __restrict__ Ke_g,
+                                                      const T* __restrict__ scale,
+                                                      const T* __restrict__ factor, SchurIO io) {
+  if (io.done && *io.done) return;
+  const int BP = t.BP, PC = BP * BP, PD = BP * (BP + 1) / 2, STAGE = PC + PD;
+  const int sub = blockIdx.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const SubInfo si = t.subs[sub];
+  const int s = t.s, s1 = s + 1, nloc = s1 * s1 * s1;
+  extern __shared__ __align__(128) unsigned char smem_raw3[];
+  T* ybuf = reinterpret_cast<T*>(smem_raw3);  // nb_max * BP
+  T* vbuf = ybuf + t.nb_max * BP;             // BP
+  T* xloc = vbuf + BP;                        // 3 * nloc
+  T* ke = xloc + 3 * nloc;                    // 576
+  T* sc = ke + 576;                           // s^3
+  for (int i = tid; i < 576; i += kT3) ke[i] = Ke_g[i];
+  for (int i = tid; i < s * s * s; i += kT3) {
+    const int a = i / (s * s), b = (i / s) % s, c = i % s;
+    sc[i] = scale[((int64_t)(si.lo[0] + a) * t.ne[1] + si.lo[1] + b) * t.ne[2] + si.lo[2] + c];
+  }
+  for (int i = tid; i < 3 * nloc; i += kT3) xloc[i] = T(0);
+  __syncthreads();
+  const bool have_x = io.x != nullptr;
+  if (have_x)
+    for (int r = tid; r < si.n_ring; r += kT3)
+      xloc[t.ring_loc[si.ring_off + r]] = (T)io.x[t.ring_gidx[si.ring_off + r]];
+  __syncthreads();
+  const int nb = si.nb;
+  const T* fb = factor + si.factor_off;
+  // forward: y_k = D_k (w_k - C_k y_{k-1})
+  for (int k = 0; k < nb; ++k) {
+    const T* Ck = fb + (int64_t)k * STAGE;
+    const T* Dk = Ck + PC;
+    for (int r = tid; r < BP; r += kT3) {
+      T v = T(0);
+      if (r < si.bsz) {
+        int x, y, z, c;
+        row_node3(si, k, r, x, y, z, c);
+        const int64_t dof = 3 * node3(t, x, y, z) + c;
+        if (!t.fixed[dof]) {
+          if (io.f) v = (T)io.f[dof];
+          if (have_x) v -= ebe_local3d<T>(ke, sc, xloc, s, x - si.lo[0], y - si.lo[1], z - si.lo[2], c);
+        }
+      }
+      if (k > 0) {
+        const T* yp = ybuf + (k - 1) * BP;
+        for (int j = 0; j < BP; ++j) v -= Ck[(int64_t)j * BP + r] * yp[j];
+      }
+      vbuf[r] = v;
+    }
+    __syncthreads();
+    for (int r = tid; r < BP; r += kT3) {
+      T acc = T(0);
+      for (int j = 0; j <= r; ++j) acc += Dk[j * BP - j * (j - 1) / 2 + (r - j)] * vbuf[j];
+      ybuf[k * BP + r] = acc;
+    }
+    __syncthreads();
+  }
+  // backward: t_k = D_k^T (y_k - C_{k+1}^T t_{k+1}); one warp per output entry
+  for (int k = nb - 1; k >= 0; --k) {
+    const T* Dk = fb + (int64_t)k * STAGE + PC;
+    const T* Cn = fb + (int64_t)(k + 1) * STAGE;
+    for (int j = warp; j < BP; j += kT3 / 32) {
+      T acc = T(0);
+      if (k + 1 < nb) {
+        const T* tn = ybuf + (k + 1) * BP;
+        for (int r = lane; r < BP; r += 32) acc += Cn[(int64_t)j * BP + r] * tn[r];
+      }
+      acc = warp_sum(acc);
+      if (lane == 0) vbuf[j] = ybuf[k * BP + j] - acc;
+    }
+    __syncthreads();
+    for (int j = warp; j < BP; j += kT3 / 32) {
+      const T* col = Dk + (j * BP - j * (j - 1) / 2);
+      T acc = T(0);
+      for (int i = j + lane; i < BP; i += 32) acc += col[i - j] * vbuf[i];
+      acc = warp_sum(acc);
+      if (lane == 0) ybuf[k * BP + j] = acc;
+    }
+    __syncthreads();
+  }
+  // outputs
+  if (io.u_out || io.ring_out) {
+    for (int k = 0; k < nb; ++k)
+      for (int r = tid; r < si.bsz; r += kT3) {
+        int x, y, z, c;
+        row_node3(si, k, r, x, y, z, c);
+        const int64_t dof = 3 * node3(t, x, y, z) + c;
+        if (t.fixed[dof]) continue;
+        const T tv = ybuf[k * BP + r];
+        if (io.u_out) io.u_out[dof] = (double)tv;
+        xloc[(((x - si.lo[0]) * s1 + (y - si.lo[1])) * s1 + (z - si.lo[2])) * 3 + c] = tv;
+      }
+    __syncthreads();
+  }
+  double d[1] = {0.0};
+  if (io.ring_out) {
+    T* out = reinterpret_cast<T*>(io.ring_out) + si.ring_off;
+    for (int r = tid; r < si.n_ring; r += kT3) {
+      const int loc = t.ring_loc[si.ring_off + r];
+      const int node = loc / 3, c = loc % 3;
+      const int a = node / (s1 * s1), b = (node / s1) % s1, cc = node % s1;
+      const T y = ebe_local3d<T>(ke, sc, xloc, s, a, b, cc, c);
+      out[r] = y;
+      d[0] += (double)xloc[loc] * (double)y;
+    }
+  }
+  if (io.pcg) {
+    __shared__ double red[32];
+    if (grid_sum<1, kT3>(d, io.pcg->partials, &io.pcg->ticket[0], red) && tid == 0)
+      cg_coefficients(io.pcg, d[0]);
+  }
+}
+
+}  // namespace
+
+size_t factor3d_work_elems(const DevTables& t) { return (size_t)t.n_sub * 2 * t.BP * t.BP; }
+
+void launch_factor3d(const DevTables& t, const DevFields& fld, int precision, void* factor,
+                     void* work, int* err, int* bad_sub, cudaStream_t st) {
+  if (precision == 0)
+    factor3d_kernel<double><<<t.n_sub, kT3, 0, st>>>(t, t.Ke64, fld.scale64, (double*)factor,
+                                                     (double*)work, err, bad_sub);
+  else
+    factor3d_kernel<float><<<t.n_sub, kT3, 0, st>>>(t, t.Ke32, fld.scale32, (float*)factor,
+                                                    (float*)work, err, bad_sub);
+}
+
+size_t schur3d_smem(const DevTables& t, int precision) {
+  const int s = t.s, nloc = (s + 1) * (s + 1) * (s + 1);
+  const size_t elems = (size_t)t.nb_max * t.BP + t.BP + 3 * nloc + 576 + s * s * s;
+  return elems * (precision ? 4 : 8) + 16;
+}
+
+void launch_schur3d(const DevTables& t, const DevFields& fld, int precision, const void* factor,
+                    const SchurIO& io, cudaStream_t st) {
+  const size_t smem = schur3d_smem(t, precision);
+  if (precision == 0)
+    schur3d_kernel<double><<<t.n_sub, kT3, smem, st>>>(t, t.Ke64, fld.scale64,
+                                                       (const double*)factor, io);
+  else
+    schur3d_kernel<float><<<t.n_sub, kT3, smem, st>>>(t, t.Ke32, fld.scale32, (const float*)factor,
+                                                      io);
+}
+
+cudaError_t configure_kernels3d() {
+  int dev = 0, big = 232448;
+  if (cudaGetDevice(&dev) == cudaSuccess)
+    cudaDeviceGetAttribute(&big, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  cudaError_t e = cudaSuccess;
+  cudaFuncAttributes fa;
+  if (cudaFuncGetAttributes(&fa, schur3d_kernel<double>) == cudaSuccess)
+    e = cudaFuncSetAttribute(schur3d_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             big - (int)fa.sharedSizeBytes);
+  if (cudaFuncGetAttributes(&fa, schur3d_kernel<float>) == cudaSuccess) {
+    cudaError_t e2 = cudaFuncSetAttribute(schur3d_kernel<float>,
+                                          cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          big - (int)fa.sharedSizeBytes);
+    if (e2 != cudaSuccess) e = e2;
+  }
+  return e;
+}
+
+}  // namespace ddel

@@ -70,9 +70,17 @@ cudaError_t configure_kernels();
 // Assembly: element factors from densities, diag(K_GG), face scales.
 void launch_assemble(const DevTables& t, const DevFields& fld, const double* rho, double E, double p,
                      int face_scaling, int crosspoint_mode, int* err, cudaStream_t st);
-// Fused interior assembly + block-tridiagonal Cholesky; factor in T.
-void launch_factor(const DevTables& t, const DevFields& fld, int precision, void* factor, int* err,
-                   int* bad_sub, cudaStream_t st);
+// Fused interior assembly + block-tridiagonal Cholesky; factor in T.  work:
+// 3D scratch of factor3d_work_elems() elements of the precision (unused in 2D).
+void launch_factor(const DevTables& t, const DevFields& fld, int precision, void* factor, void* work,
+                   int* err, int* bad_sub, cudaStream_t st);
+// 3D path (ddel_kernels3d.cu)
+size_t factor3d_work_elems(const DevTables& t);
+void launch_factor3d(const DevTables& t, const DevFields& fld, int precision, void* factor,
+                     void* work, int* err, int* bad_sub, cudaStream_t st);
+void launch_schur3d(const DevTables& t, const DevFields& fld, int precision, const void* factor,
+                    const SchurIO& io, cudaStream_t st);
+cudaError_t configure_kernels3d();
 // Per-subdomain solve kernel (condense / Schur / back-substitution forms).
 void launch_schur(const DevTables& t, const DevFields& fld, int precision, const void* factor,
                   const SchurIO& io, cudaStream_t st);
@@ -104,6 +112,8 @@ void launch_apply_K(const DevTables& t, const DevFields& fld, const double* x, c
                     cudaStream_t st, int nblk);
 // u[gamma_dof[g]] = xg[g]; u = 0 on fixed DOFs
 void launch_scatter_gamma(const DevTables& t, const double* xg, double* u, cudaStream_t st);
+// out = (float) in, n elements
+void launch_round_f32(const double* in, float* out, int64_t n, cudaStream_t st);
 // y += a * x (n)
 void launch_axpy(int64_t n, double a, const double* x, double* y, cudaStream_t st);
 

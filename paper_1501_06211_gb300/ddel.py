@@ -19,7 +19,7 @@ c_int, c_double, c_void_p, c_uint32, c_int64 = (ctypes.c_int, ctypes.c_double, c
 
 DDEL_OK, DDEL_EINVAL, DDEL_ENOMEM, DDEL_ECUDA = 0, -1, -2, -3
 DDEL_ENOTSPD, DDEL_ENOCONV, DDEL_EBREAKDOWN, DDEL_ESTATE, DDEL_ETIMEOUT = -4, -5, -6, -7, -8
-DDEL_FP64, DDEL_FP32 = 0, 1
+DDEL_FP64, DDEL_FP32, DDEL_MIXED = 0, 1, 2
 
 
 class ddel_mesh(ctypes.Structure):
