@@ -308,6 +308,13 @@ def kernel_roofline(ddel, s, stream, torch):
     info = ddel.ddel_kernel_info(s.h)
     bytes_ = info["schur_apply_bytes"]
     gbs = bytes_ / (avg_ms * 1e-3) / 1e9
+    if info["precision"] == 0 and info.get("double_float"):
+        # FP64 operator applied in FP32-pair arithmetic: the matrix streams once
+        # per apply (8 bytes per entry), so the bound is memory bandwidth
+        return {"bound": "hbm", "kernel": info["schur_apply_kernel"] + " + gamma_sum",
+                "achieved": gbs, "peak": hbm, "unit": "GB/s", "frac": gbs / hbm, "traffic": None,
+                "peak_source": src, "launch_ms": avg_ms, "algorithmic_bytes": bytes_,
+                "note": "S_i (67 MB) stays L2-resident between PCG iterations"}
     if info["precision"] == 0:
         # FP64 products: GB300 issues 2 DFMA per clock per SM (1.26 TFLOP/s at
         # 2070 MHz on 152 SMs; 1.25 TFLOP/s measured), far below its bandwidth

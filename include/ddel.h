@@ -206,6 +206,35 @@ typedef struct {
  * Synchronises the stream.  st (may be NULL) receives the solve statistics. */
 int ddel_topopt_step(ddel_ctx* ctx, ddel_topopt_state* state, ddel_stats* st);
 
+/* --- Batched independent problems ---------------------------------------------
+ * Solves n independent, assembled problems (each its own context: any grid,
+ * subdomain size, material) for their ddel_bc loads, concurrently: all
+ * factorisations are launched before any is checked, and the PCG iterations of
+ * every context are issued in batches of check_every as soon as that
+ * context's previous batch has reported, so kernels of different problems run
+ * side by side (contexts need distinct streams: create them with
+ * cuda_stream = NULL).  u: array of n device pointers (n_dof of each problem)
+ * or NULL entries; stats: n entries or NULL.  A problem that misses its
+ * tolerance after one cycle is finished by the refinement loop of
+ * ddel_solve.  The result of every problem is bitwise the one of ddel_solve
+ * in FP64 (same kernels, same order).  Synchronises all streams. */
+int ddel_batch_solve(ddel_ctx* const* ctxs, int n, double* const* u, ddel_stats* stats);
+
+/* --- Autotuner ------------------------------------------------------------------
+ * Chooses the Schur form (IMPLICIT block substitution, EXPLICIT FP64, or AUTO =
+ * explicit applied in double-float arithmetic) and the PCG graph batch size
+ * (check_every in {8, 16, 32}) for an assembled context by timing them on this
+ * GPU: one solve gives the iteration count N, then each candidate is
+ * factorised and runs 48 PCG iterations; the predicted solve time is
+ * factor (+ formation) time + N x time per iteration.  The winner is applied
+ * to the context (ddel_set_options semantics: refactor before solving) and,
+ * with cache_path != NULL, appended to that text file under the key
+ * "dim sub BP n_sub precision"; a later call with the same key reads the file
+ * and applies the cached choice without timing (*from_cache = 1).
+ * chosen_mode / chosen_check: outputs (may be NULL).  Synchronises. */
+int ddel_autotune(ddel_ctx* ctx, const char* cache_path, int* chosen_mode, int* chosen_check,
+                  int* from_cache);
+
 /* --- Step-level entry points (device pointers; asynchronous) --------------- */
 /* y = K(rho) x over all free DOFs (fixed rows 0), element by element, FP64. */
 int ddel_apply_K(ddel_ctx* ctx, const double* x, double* y);
@@ -243,6 +272,8 @@ typedef struct {
   int64_t schur_apply_flops;
   int schur_form;                  /* 0 implicit (block substitution), 1 explicit */
   int precision;                   /* active ddel_precision */
+  int double_float;                /* 1: explicit FP64 apply in FP32-pair (double-float)
+                                      arithmetic, the default with schur_mode AUTO */
 } ddel_kernel_info_t;
 int ddel_kernel_info(const ddel_ctx* ctx, ddel_kernel_info_t* out);
 

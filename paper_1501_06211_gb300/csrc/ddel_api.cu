@@ -8,6 +8,7 @@
 #include <cstring>
 #include <new>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "../../include/ddel.h"
@@ -32,11 +33,18 @@ struct ddel_ctx {
   void* sexp[2] = {nullptr, nullptr};  // explicit local Schur complements (2D)
   float* sexp32 = nullptr;             // MIXED: FP64-formed S_i rounded to FP32
   bool mixed_ready = false;
+  float2* sexp_df = nullptr;           // FP64 S_i as FP32 (hi, lo) pairs (double-float apply)
+  bool df_ok = false;
+  bool graph_df = false;
+  bool pending_explicit = false;
   bool explicit_ok[2] = {false, false};
   bool factored[2] = {false, false};
   int active_prec = 0;
   bool assembled = false;
-  void* ring = nullptr;
+  // owner-major ring buffers, one per precision: their zero padding must not see
+  // writes of the other element size
+  void* ring = nullptr;    // FP64
+  void* ring32 = nullptr;  // FP32
   double *d_f = nullptr, *d_load = nullptr, *d_u = nullptr, *d_r = nullptr, *d_d = nullptr;
   double *g = nullptr, *x = nullptr, *r = nullptr, *z = nullptr, *p = nullptr, *q = nullptr;
   double* sv = nullptr;  // s = S p of the Chronopoulos-Gear recurrence
@@ -128,6 +136,8 @@ int check_kernel_err(ddel_ctx* ctx) {
   return DDEL_OK;
 }
 
+void* ring_of(ddel_ctx* ctx, int prec) { return prec ? ctx->ring32 : ctx->ring; }
+
 SchurIO make_io(ddel_ctx* ctx) {
   SchurIO io;
   io.err = ctx->err;
@@ -138,19 +148,21 @@ SchurIO make_io(ddel_ctx* ctx) {
 // the vector updates and u = S~^-1 r with gamma = (r, u).
 void pcg_iteration(ddel_ctx* ctx, int prec, bool apply32) {
   cudaStream_t s = ctx->stream;
-  SchurIO io = make_io(ctx);
-  io.x = ctx->z;
-  io.ring_out = ctx->ring;
-  io.done = &ctx->st->done;
-  io.pcg = ctx->st;
   const bool expl = ctx->explicit_ok[prec];
   const int aprec = apply32 ? 1 : prec;  // precision of the Schur apply and ring
+  SchurIO io = make_io(ctx);
+  io.x = ctx->z;
+  io.ring_out = ring_of(ctx, expl ? aprec : prec);
+  io.done = &ctx->st->done;
+  io.pcg = ctx->st;
   const void* smat = apply32 ? (const void*)ctx->sexp32 : ctx->sexp[prec];
-  if (expl)
+  if (expl && prec == 0 && !apply32 && ctx->df_ok)
+    launch_schur_explicit_df(ctx->T, ctx->sexp_df, io, s);
+  else if (expl)
     launch_schur_explicit(ctx->T, aprec, smat, io, s);
   else
     launch_schur(ctx->T, ctx->F, prec, ctx->factor[prec], io, s);
-  launch_pcg_update(ctx->T, ctx->F, expl ? aprec : prec, ctx->ring, ctx->x, ctx->r, ctx->z, ctx->p,
+  launch_pcg_update(ctx->T, ctx->F, expl ? aprec : prec, io.ring_out, ctx->x, ctx->r, ctx->z, ctx->p,
                     ctx->sv, ctx->st, s, ctx->nblk);
 }
 
@@ -162,8 +174,9 @@ int pcg_start(ddel_ctx* ctx, int prec, const double* g, bool apply32) {
   ctx->launches += 1;
   const int per = ctx->opt.check_every > 0 ? ctx->opt.check_every : 16;
   const bool expl = ctx->explicit_ok[prec];
+  const bool df = prec == 0 && ctx->df_ok;
   if (ctx->graph[prec] && (ctx->graph_explicit[prec] != expl || ctx->graph_apply32[prec] != apply32 ||
-                           ctx->graph_iters != per)) {
+                           ctx->graph_iters != per || (prec == 0 && ctx->graph_df != df))) {
     cudaGraphExecDestroy(ctx->graph[prec]);
     ctx->graph[prec] = nullptr;
   }
@@ -177,6 +190,7 @@ int pcg_start(ddel_ctx* ctx, int prec, const double* g, bool apply32) {
     ctx->graph_iters = per;
     ctx->graph_explicit[prec] = expl;
     ctx->graph_apply32[prec] = apply32;
+    if (prec == 0) ctx->graph_df = df;
   }
   return DDEL_OK;
 }
@@ -217,9 +231,9 @@ int pcg_run(ddel_ctx* ctx, int prec, const double* g, int* iters, int* status,
 void condense(ddel_ctx* ctx, int prec, const double* f, double* g) {
   SchurIO io = make_io(ctx);
   io.f = f;
-  io.ring_out = ctx->ring;
+  io.ring_out = ring_of(ctx, prec);
   launch_schur(ctx->T, ctx->F, prec, ctx->factor[prec], io, ctx->stream);
-  launch_gamma_sum(ctx->T, prec, ctx->ring, f, -1.0, g, ctx->stream);
+  launch_gamma_sum(ctx->T, prec, io.ring_out, f, -1.0, g, ctx->stream);
   ctx->launches += 2;
 }
 
@@ -235,8 +249,9 @@ void back_substitute(ddel_ctx* ctx, int prec, const double* f, const double* xg,
 
 
 // Factor (and, where available, form the explicit local Schur complements) in
-// one precision.  ENOTSPD on a failed pivot, EINVAL on a bad density.
-int factor_prec(ddel_ctx* ctx, int prec) {
+// one precision: launch (asynchronous) and check (ENOTSPD on a failed pivot,
+// EINVAL on a bad density).
+int factor_launch(ddel_ctx* ctx, int prec) {
   if (!ctx->factor[prec]) {
     cudaError_t e = cudaMalloc(&ctx->factor[prec], ctx->S.factor_elems * (prec ? 4 : 8) + 256);
     if (e != cudaSuccess) return fail(ctx, DDEL_ENOMEM, "factor allocation");
@@ -264,14 +279,37 @@ int factor_prec(ddel_ctx* ctx, int prec) {
     ctx->launches += 1;
     CK(cudaGetLastError());
   }
+  ctx->pending_explicit = want_explicit;
+  return DDEL_OK;
+}
+
+// Reads the error words of a launched factorisation (synchronises the stream).
+int factor_check(ddel_ctx* ctx, int prec) {
   int rc = check_kernel_err(ctx);
   if (rc) return rc;
   if (ctx->h_err[2] == kErrBadRho) return fail(ctx, DDEL_EINVAL, "density must be > 0");
   if (ctx->h_err[0] == kErrPivot)
     return fail(ctx, DDEL_ENOTSPD, "pivot failure in subdomain " + std::to_string(ctx->h_err[1]));
   ctx->factored[prec] = true;
-  ctx->explicit_ok[prec] = want_explicit;
+  ctx->explicit_ok[prec] = ctx->pending_explicit;
+  if (prec == 0) ctx->df_ok = false;
+  if (prec == 0 && ctx->explicit_ok[0] && ctx->opt.schur_mode == DDEL_SCHUR_AUTO) {
+    // FP64 local Schur complements as FP32 (hi, lo) pairs for the double-float apply
+    const int NR = explicit_ring_size(ctx->T);
+    const int64_t n = (int64_t)ctx->T.n_sub * NR * NR;
+    if (!ctx->sexp_df && cudaMalloc(&ctx->sexp_df, n * sizeof(float2)) != cudaSuccess)
+      return fail(ctx, DDEL_ENOMEM, "double-float Schur allocation");
+    launch_split_df((const double*)ctx->sexp[0], ctx->sexp_df, n, ctx->stream);
+    ctx->launches += 1;
+    CK(cudaGetLastError());
+    ctx->df_ok = true;
+  }
   return DDEL_OK;
+}
+
+int factor_prec(ddel_ctx* ctx, int prec) {
+  int rc = factor_launch(ctx, prec);
+  return rc ? rc : factor_check(ctx, prec);
 }
 
 float elapsed(cudaEvent_t a, cudaEvent_t b) {
@@ -383,10 +421,12 @@ int ddel_create(const ddel_mesh* mesh, const ddel_material* mat, const ddel_bc* 
     T.n_blocks = (int)S.blk_off.size();
     T.max_blk_n = S.max_blk_n > 0 ? S.max_blk_n : 1;
     T.n_ring = (int64_t)S.ring_gidx.size();
+    T.max_owners = S.max_owners;
     std::vector<float> ke32(S.Ke.begin(), S.Ke.end());
     if (bad(upload(ctx, S.subs, &T.subs)) || bad(upload(ctx, S.fixed, &T.fixed)) ||
         bad(upload(ctx, S.ring_gidx, &T.ring_gidx)) || bad(upload(ctx, S.ring_loc, &T.ring_loc)) ||
         bad(upload(ctx, S.owner_ptr, &T.owner_ptr)) || bad(upload(ctx, S.owner_idx, &T.owner_idx)) ||
+        bad(upload(ctx, S.owner_pad, &T.owner_pad)) || bad(upload(ctx, S.ring_dst, &T.ring_dst)) ||
         bad(upload(ctx, S.gamma_dof, &T.gamma_dof)) || bad(upload(ctx, S.blk_off, &T.blk_off)) ||
         bad(upload(ctx, S.blk_n, &T.blk_n)) || bad(upload(ctx, S.blk_poff, &T.blk_poff)) ||
         bad(upload(ctx, S.blk_hmean, &T.blk_hmean)) || bad(upload(ctx, S.ptab, &T.ptab)) ||
@@ -394,12 +434,15 @@ int ddel_create(const ddel_mesh* mesh, const ddel_material* mat, const ddel_bc* 
         bad(upload(ctx, S.Ke, &T.Ke64)) || bad(upload(ctx, ke32, &T.Ke32)))
       goto fail_out;
     const int64_t ng = T.n_gamma, nd = S.n_dof;
+    // owner-major ring (ng x max_owners entries of up to 8 bytes), zero padded
+    const size_t ring_bytes = (size_t)(ng * S.max_owners + 4) * 8;
     DevFields& F = ctx->F;
     if (bad(dalloc(ctx, &F.scale64, S.n_elem * 8)) || bad(dalloc(ctx, &F.scale32, S.n_elem * 4)) ||
         bad(dalloc(ctx, &F.diagG, ng * 8)) || bad(dalloc(ctx, &F.blk_alpha, (T.n_blocks + 1) * 8)) ||
         bad(dalloc(ctx, &F.face_w, (T.n_face_dofs + 1) * 8)) ||
         bad(dalloc(ctx, &F.cross_scale, (ng - T.n_face_dofs + 1) * 8)) ||
-        bad(dalloc(ctx, &ctx->ring, T.n_ring * 8)) || bad(dalloc(ctx, &ctx->d_f, nd * 8)) ||
+        bad(dalloc(ctx, &ctx->ring, ring_bytes)) || bad(dalloc(ctx, &ctx->ring32, ring_bytes)) ||
+        bad(dalloc(ctx, &ctx->d_f, nd * 8)) ||
         bad(dalloc(ctx, &ctx->d_load, nd * 8)) || bad(dalloc(ctx, &ctx->d_u, nd * 8)) ||
         bad(dalloc(ctx, &ctx->d_r, nd * 8)) || bad(dalloc(ctx, &ctx->d_d, nd * 8)) ||
         bad(dalloc(ctx, &ctx->g, ng * 8)) || bad(dalloc(ctx, &ctx->x, ng * 8)) ||
@@ -419,7 +462,8 @@ int ddel_create(const ddel_mesh* mesh, const ddel_material* mat, const ddel_bc* 
     PcgState st0{};
     st0.partials = ctx->partials;
     if (bad(cudaMemcpy(ctx->st, &st0, sizeof(PcgState), cudaMemcpyHostToDevice)) ||
-        bad(cudaMemset(ctx->ticketK, 0, 16)) ||
+        bad(cudaMemset(ctx->ticketK, 0, 16)) || bad(cudaMemset(ctx->ring, 0, ring_bytes)) ||
+        bad(cudaMemset(ctx->ring32, 0, ring_bytes)) ||
         bad(cudaMemcpy(ctx->d_load, S.f.data(), nd * 8, cudaMemcpyHostToDevice)))
       goto fail_out;
     const int zero_err[4] = {0, 0x7fffffff, 0, 0};
@@ -449,6 +493,7 @@ void ddel_destroy(ddel_ctx* ctx) {
   for (void* p : ctx->work3d)
     if (p) cudaFree(p);
   if (ctx->sexp32) cudaFree(ctx->sexp32);
+  if (ctx->sexp_df) cudaFree(ctx->sexp_df);
   if (ctx->h_st) cudaFreeHost(ctx->h_st);
   if (ctx->h_nrm) cudaFreeHost(ctx->h_nrm);
   if (ctx->h_err) cudaFreeHost(ctx->h_err);
@@ -713,6 +758,219 @@ int ddel_topopt_step(ddel_ctx* ctx, ddel_topopt_state* ts, ddel_stats* stats) {
   return DDEL_OK;
 }
 
+
+int ddel_batch_solve(ddel_ctx* const* ctxs, int n, double* const* u, ddel_stats* stats) {
+  if (!ctxs || n <= 0) return DDEL_EINVAL;
+  for (int i = 0; i < n; ++i)
+    if (!ctxs[i] || !ctxs[i]->assembled) return ctxs[i] ? fail(ctxs[i], DDEL_ESTATE, "assemble first") : DDEL_EINVAL;
+  std::vector<int> prec(n), checks(n, 0), state(n, 0);  // state: 0 PCG running, 1 finished
+  std::vector<bool> a32(n, false);
+  // 1. all factorisations in flight at once (one stream per context)
+  for (int i = 0; i < n; ++i) {
+    ddel_ctx* c = ctxs[i];
+    prec[i] = c->opt.precision == DDEL_FP32 ? 1 : 0;
+    int rc = factor_launch(c, prec[i]);
+    if (rc) return rc;
+  }
+  for (int i = 0; i < n; ++i) {
+    ddel_ctx* c = ctxs[i];
+    int rc = factor_check(c, prec[i]);
+    if (rc == DDEL_ENOTSPD && prec[i] == 1) {
+      prec[i] = 0;
+      rc = factor_prec(c, 0);
+    }
+    if (rc) return rc;
+    c->active_prec = prec[i];
+    c->mixed_ready = false;
+  }
+  // 2. right-hand sides, condensation, PCG start
+  for (int i = 0; i < n; ++i) {
+    ddel_ctx* ctx = ctxs[i];
+    cudaStream_t s = ctx->stream;
+    const int64_t nd = ctx->S.n_dof;
+    CK(cudaEventRecord(ctx->ev[0], s));
+    CK(cudaMemcpyAsync(ctx->d_f, ctx->d_load, nd * 8, cudaMemcpyDeviceToDevice, s));
+    CK(cudaMemsetAsync(ctx->d_u, 0, nd * 8, s));
+    launch_apply_K(ctx->T, ctx->F, ctx->d_u, ctx->d_f, ctx->d_r, 1, ctx->partials, ctx->ticketK,
+                   ctx->nrm, s, ctx->nblk);
+    set_tol_kernel<<<1, 1, 0, s>>>(ctx->st, ctx->nrm, ctx->opt.tol, ctx->opt.inner_tol, prec[i],
+                                   ctx->opt.max_it);
+    ctx->launches += 2;
+    condense(ctx, prec[i], ctx->d_r, ctx->g);
+    int rc = pcg_start(ctx, prec[i], ctx->g, false);
+    if (rc) return rc;
+    rc = pcg_issue(ctx, prec[i], false);
+    if (rc) return rc;
+  }
+  // 3. round robin: relaunch each unfinished context as soon as its last
+  //    batch of iterations has reported, finish the others
+  int remaining = n;
+  while (remaining > 0) {
+    bool progressed = false;
+    for (int i = 0; i < n; ++i) {
+      if (state[i]) continue;
+      ddel_ctx* ctx = ctxs[i];
+      const cudaError_t q = cudaEventQuery(ctx->ev[7]);
+      if (q == cudaErrorNotReady) continue;
+      CK(q);
+      progressed = true;
+      const int per = ctx->opt.check_every > 0 ? ctx->opt.check_every : 16;
+      if (!ctx->h_st->done && ++checks[i] < ctx->opt.max_it / per + 2) {
+        int rc = pcg_issue(ctx, prec[i], false);
+        if (rc) return rc;
+        continue;
+      }
+      state[i] = 1;
+      --remaining;
+      cudaStream_t s = ctx->stream;
+      back_substitute(ctx, prec[i], ctx->d_r, ctx->x, ctx->d_d);
+      launch_axpy(ctx->S.n_dof, 1.0, ctx->d_d, ctx->d_u, s);
+      launch_apply_K(ctx->T, ctx->F, ctx->d_u, ctx->d_f, ctx->d_r, 1, ctx->partials, ctx->ticketK,
+                     ctx->nrm, s, ctx->nblk);
+      ctx->launches += 2;
+      CK(cudaMemcpyAsync(ctx->h_nrm, ctx->nrm, 16, cudaMemcpyDeviceToHost, s));
+      CK(cudaEventRecord(ctx->ev[6], s));
+    }
+    if (!progressed) std::this_thread::yield();
+  }
+  // 4. statistics; a context that missed the tolerance is finished by the
+  //    ordinary refinement loop
+  int status = DDEL_OK;
+  for (int i = 0; i < n; ++i) {
+    ddel_ctx* ctx = ctxs[i];
+    CK(cudaEventSynchronize(ctx->ev[6]));
+    ddel_stats st{};
+    st.bad_subdomain = -1;
+    st.iters = ctx->h_st->it;
+    st.cycles = 1;
+    const double fn = ctx->h_nrm[1];
+    st.relres = fn > 0 ? ctx->h_nrm[0] / fn : 0.0;
+    st.pcg_relres = fn > 0 ? std::sqrt(ctx->h_st->rr) / fn : 0.0;
+    st.t_total_ms = elapsed(ctx->ev[0], ctx->ev[6]);
+    st.status = DDEL_OK;
+    if (!(st.relres <= ctx->opt.tol) && fn > 0) {
+      const int rc = ddel_solve(ctx, nullptr, u && u[i] ? u[i] : ctx->d_d, 1, &st);
+      if (rc && status == DDEL_OK) status = rc;
+      if (u && u[i]) {
+        if (stats) stats[i] = st;
+        continue;
+      }
+      CK(cudaMemcpyAsync(ctx->d_u, ctx->d_d, ctx->S.n_dof * 8, cudaMemcpyDeviceToDevice, ctx->stream));
+    }
+    if (u && u[i])
+      CK(cudaMemcpyAsync(u[i], ctx->d_u, ctx->S.n_dof * 8, cudaMemcpyDeviceToDevice, ctx->stream));
+    if (stats) stats[i] = st;
+  }
+  for (int i = 0; i < n; ++i) {
+    ddel_ctx* ctx = ctxs[i];
+    CK(cudaStreamSynchronize(ctx->stream));
+  }
+  return status;
+}
+
+int ddel_autotune(ddel_ctx* ctx, const char* cache_path, int* chosen_mode, int* chosen_check,
+                  int* from_cache) {
+  if (!ctx) return DDEL_EINVAL;
+  if (!ctx->assembled) return fail(ctx, DDEL_ESTATE, "assemble before autotune");
+  const int prec = ctx->opt.precision == DDEL_FP32 ? 1 : 0;
+  char key[128];
+  std::snprintf(key, sizeof(key), "%d %d %d %d %d", ctx->S.dim, ctx->S.sub, ctx->S.BP, ctx->S.n_sub,
+                ctx->opt.precision);
+  if (from_cache) *from_cache = 0;
+  auto apply = [&](int mode, int check) {
+    ctx->opt.schur_mode = mode;
+    ctx->opt.check_every = check;
+    ctx->factored[0] = ctx->factored[1] = false;
+    if (chosen_mode) *chosen_mode = mode;
+    if (chosen_check) *chosen_check = check;
+  };
+  if (cache_path) {
+    if (FILE* fp = std::fopen(cache_path, "r")) {
+      char line[256];
+      int mode = -1, check = 0;
+      while (std::fgets(line, sizeof(line), fp)) {
+        int d, s, b, n, p, m, c;
+        if (std::sscanf(line, "%d %d %d %d %d %d %d", &d, &s, &b, &n, &p, &m, &c) == 7) {
+          char k2[128];
+          std::snprintf(k2, sizeof(k2), "%d %d %d %d %d", d, s, b, n, p);
+          if (std::strcmp(k2, key) == 0) {
+            mode = m;
+            check = c;
+          }
+        }
+      }
+      std::fclose(fp);
+      if (mode >= 0) {
+        apply(mode, check);
+        if (from_cache) *from_cache = 1;
+        return DDEL_OK;
+      }
+    }
+  }
+  // iteration count of the problem: one solve in the current configuration
+  ddel_options saved = ctx->opt;
+  int rc = ddel_factor(ctx);
+  if (rc) return rc;
+  ddel_stats st{};
+  rc = ddel_solve(ctx, nullptr, ctx->d_d, 1, &st);
+  if (rc != DDEL_OK && rc != DDEL_ENOCONV) return rc;
+  const double n_iter = st.iters > 0 ? st.iters : 1;
+  const bool has_explicit = explicit_ring_size(ctx->T) > 0;
+  std::vector<int> modes = {DDEL_SCHUR_IMPLICIT};
+  if (has_explicit && prec == 0) modes.push_back(DDEL_SCHUR_AUTO);
+  if (has_explicit) modes.push_back(DDEL_SCHUR_EXPLICIT);
+  const int checks[3] = {8, 16, 32};
+  double best = 1e300;
+  int best_mode = saved.schur_mode, best_check = saved.check_every;
+  cudaStream_t s = ctx->stream;
+  for (int mode : modes)
+    for (int check : checks) {
+      ctx->opt = saved;
+      ctx->opt.schur_mode = mode;
+      ctx->opt.check_every = check;
+      CK(cudaEventRecord(ctx->ev[0], s));
+      rc = ddel_factor(ctx);
+      if (rc) return rc;
+      CK(cudaEventRecord(ctx->ev[1], s));
+      // 48 iterations of this form (tolerance 0: nothing converges early)
+      set_tol_abs_kernel<<<1, 1, 0, s>>>(ctx->st, 0.0, 48);
+      const int p = ctx->active_prec;
+      launch_apply_K(ctx->T, ctx->F, ctx->d_u, ctx->d_load, ctx->d_r, 1, ctx->partials,
+                     ctx->ticketK, ctx->nrm, s, ctx->nblk);
+      condense(ctx, p, ctx->d_load, ctx->g);
+      rc = pcg_start(ctx, p, ctx->g, false);
+      if (rc) return rc;
+      CK(cudaEventRecord(ctx->ev[2], s));
+      int done_it = 0;
+      while (done_it < 48) {
+        rc = pcg_issue(ctx, p, false);
+        if (rc) return rc;
+        done_it += check;
+      }
+      CK(cudaEventRecord(ctx->ev[3], s));
+      CK(cudaEventSynchronize(ctx->ev[3]));
+      const double t_fact = elapsed(ctx->ev[0], ctx->ev[1]);
+      const double it_done = ctx->h_st->it > 0 ? ctx->h_st->it : 1;
+      const double t_it = elapsed(ctx->ev[2], ctx->ev[3]) / it_done;
+      // graph launches cover whole batches: add the expected idle tail
+      const double predicted = t_fact + (n_iter + 0.5 * check) * t_it;
+      if (predicted < best) {
+        best = predicted;
+        best_mode = mode;
+        best_check = check;
+      }
+    }
+  ctx->opt = saved;
+  apply(best_mode, best_check);
+  if (cache_path) {
+    if (FILE* fp = std::fopen(cache_path, "a")) {
+      std::fprintf(fp, "%s %d %d\n", key, best_mode, best_check);
+      std::fclose(fp);
+    }
+  }
+  return DDEL_OK;
+}
+
 int ddel_apply_K(ddel_ctx* ctx, const double* x, double* y) {
   if (!ctx || !x || !y) return DDEL_EINVAL;
   if (!ctx->assembled) return fail(ctx, DDEL_ESTATE, "assemble first");
@@ -737,12 +995,14 @@ int ddel_schur_apply(ddel_ctx* ctx, const double* x, double* y) {
   if (!ctx->factored[prec]) return fail(ctx, DDEL_ESTATE, "factor first");
   SchurIO io = make_io(ctx);
   io.x = x;
-  io.ring_out = ctx->ring;
-  if (ctx->explicit_ok[prec])
+  io.ring_out = ring_of(ctx, prec);
+  if (prec == 0 && ctx->df_ok)
+    launch_schur_explicit_df(ctx->T, ctx->sexp_df, io, ctx->stream);
+  else if (ctx->explicit_ok[prec])
     launch_schur_explicit(ctx->T, prec, ctx->sexp[prec], io, ctx->stream);
   else
     launch_schur(ctx->T, ctx->F, prec, ctx->factor[prec], io, ctx->stream);
-  launch_gamma_sum(ctx->T, prec, ctx->ring, nullptr, 1.0, y, ctx->stream);
+  launch_gamma_sum(ctx->T, prec, io.ring_out, nullptr, 1.0, y, ctx->stream);
   ctx->launches += 2;
   CK(cudaGetLastError());
   return DDEL_OK;
@@ -828,6 +1088,7 @@ int ddel_kernel_info(const ddel_ctx* ctx, ddel_kernel_info_t* out) {
   const int64_t tb = prec ? 4 : 8;
   out->precision = prec;
   out->schur_form = ctx->explicit_ok[prec] ? 1 : 0;
+  out->double_float = (prec == 0 && ctx->df_ok) ? 1 : 0;
   int64_t mat = 0, ring = 0;
   for (const SubInfo& si : ctx->S.subs) {
     ring += si.n_ring;

@@ -54,6 +54,9 @@ struct Setup {
   std::vector<int32_t> ring_loc;  // local closure DOF (node*dim + comp)
   std::vector<int32_t> owner_ptr; // n_gamma + 1
   std::vector<int32_t> owner_idx; // ring slots contributing to each gamma DOF
+  int max_owners = 4;             // 2^(dim-1) ... 2^dim: 4 in 2D, 8 in 3D
+  std::vector<int32_t> owner_pad; // n_gamma * max_owners ring slots, -1 padded
+  std::vector<int32_t> ring_dst;  // per ring slot: g * max_owners + (rank among g's owners)
   // preconditioner (face blocks first, then cross DOFs)
   int n_face_dofs = 0;
   std::vector<int32_t> blk_off, blk_n, blk_poff;  // per (face, component) block

@@ -96,7 +96,7 @@ __global__ void face_scale_kernel(DevTables t, DevFields fld, int face_scaling, 
       double w = 1.0;
       if (face_scaling == 1) w = sqrt(alpha);
       if (face_scaling == 2) w = sqrt(fld.diagG[off + i] / t.hdiag[off + i]);
-      fld.face_w[off + i] = w;
+      fld.face_w[off + i] = 1.0 / w;  // stored as the reciprocal: products, no divisions later
     }
   }
   const int64_t ncross = t.n_gamma - t.n_face_dofs;
@@ -457,12 +457,12 @@ __global__ void __launch_bounds__(32) schur2d_kernel(DevTables t, const T* __res
   }
   double d[1] = {0.0};
   if (io.ring_out) {
-    T* out = reinterpret_cast<T*>(io.ring_out) + si.ring_off;
+    T* out = reinterpret_cast<T*>(io.ring_out);
     for (int r = lane; r < si.n_ring; r += 32) {
       const int loc = t.ring_loc[si.ring_off + r];
       const int node = loc >> 1, c = loc & 1;
       const T y = ebe_local2d<T>(ke, sc, xloc, s, node / s1, node % s1, c);
-      out[r] = y;
+      out[t.ring_dst[si.ring_off + r]] = y;
       d[0] += (double)xloc[loc] * (double)y;
     }
   }
@@ -628,8 +628,10 @@ template <typename T, int NR>
 __global__ void __launch_bounds__(256) schur_explicit_kernel(DevTables t, const T* __restrict__ Sexp,
                                                              SchurIO io) {
   if (io.done && *io.done) return;
-  constexpr int H = 256 / NR;  // column groups
-  const int sub = blockIdx.x, tid = threadIdx.x;
+  // two CTAs per subdomain (rows [half * RH, half * RH + RH)), H column groups
+  // per row: 2 * n_sub CTAs balance the SMs better than one CTA per subdomain
+  constexpr int RH = NR / 2, H = 256 / RH;
+  const int sub = blockIdx.x >> 1, half = blockIdx.x & 1, tid = threadIdx.x;
   const SubInfo si = t.subs[sub];
   __shared__ T xr[NR];
   __shared__ T part[256];
@@ -643,7 +645,7 @@ __global__ void __launch_bounds__(256) schur_explicit_kernel(DevTables t, const 
     xr[j] = v;
   }
   __syncthreads();
-  const int r = tid % NR, h = tid / NR;
+  const int r = half * RH + tid % RH, h = tid / RH;
   const T* Sc = Sexp + (int64_t)sub * NR * NR;
   T acc0 = T(0), acc1 = T(0);
   const int j0 = h * (NR / H), j1 = j0 + NR / H;
@@ -655,12 +657,13 @@ __global__ void __launch_bounds__(256) schur_explicit_kernel(DevTables t, const 
   part[tid] = acc0 + acc1;
   __syncthreads();
   double d[1] = {0.0};
-  if (tid < NR && tid < si.n_ring) {
+  const int row = half * RH + tid;
+  if (tid < RH && row < si.n_ring) {
     T y = T(0);
 #pragma unroll
-    for (int q = 0; q < H; ++q) y += part[q * NR + tid];
-    reinterpret_cast<T*>(io.ring_out)[si.ring_off + tid] = y;
-    d[0] = (double)xr[tid] * (double)y;
+    for (int q = 0; q < H; ++q) y += part[q * RH + tid];
+    reinterpret_cast<T*>(io.ring_out)[t.ring_dst[si.ring_off + row]] = y;
+    d[0] = (double)xr[row] * (double)y;
   }
   if (io.pcg) {  // delta = (S u, u) = sum over subdomains of u_i^T S_i u_i
     __shared__ double red[32];
@@ -669,17 +672,109 @@ __global__ void __launch_bounds__(256) schur_explicit_kernel(DevTables t, const 
   }
 }
 
+// ---- double-float form of the explicit apply --------------------------------
+// S_i is stored as pairs (hi, lo) of FP32 with hi + lo = S to 2^-48 relative,
+// the ring vector likewise, and each row sum is accumulated as a pair with
+// error-free transformations: Dekker's product split via FMA
+// (p = a*b, e = fma(a, b, -p)) and Knuth's TwoSum, so the arithmetic runs on
+// the FP32 pipes (GB300: 128 lanes/clk/SM) instead of the FP64 pipe
+// (2 DFMA/clk/SM) while keeping about 48 significant bits.
+// (rounded intrinsics: the compiler may not contract them into FMAs, which
+// would break the error-free transformations)
+__device__ __forceinline__ void df_add(float& hi, float& lo, float p) {
+  const float s = __fadd_rn(hi, p);
+  const float bp = __fsub_rn(s, hi);
+  const float err = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bp)), __fsub_rn(p, bp));
+  hi = s;
+  lo = __fadd_rn(lo, err);
+}
+
+__global__ void split_df_kernel(const double* __restrict__ in, float2* __restrict__ out, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const double v = in[i];
+    const float hi = (float)v;
+    out[i] = make_float2(hi, (float)(v - (double)hi));
+  }
+}
+
+template <int NR>
+__global__ void __launch_bounds__(256) schur_explicit_df_kernel(DevTables t, const float2* __restrict__ Sexp,
+                                                                SchurIO io) {
+  if (io.done && *io.done) return;
+  constexpr int RH = NR / 2, H = 256 / RH;
+  const int sub = blockIdx.x >> 1, half = blockIdx.x & 1, tid = threadIdx.x;
+  const SubInfo si = t.subs[sub];
+  __shared__ float2 xr[NR];
+  __shared__ double xd[NR];
+  __shared__ double part[256];
+  for (int j = tid; j < NR; j += 256) {
+    double v = 0.0;
+    if (j < si.n_ring) v = io.x[t.ring_gidx[si.ring_off + j]];
+    const float hi = (float)v;
+    xr[j] = make_float2(hi, (float)(v - (double)hi));
+    xd[j] = v;
+  }
+  __syncthreads();
+  const int r = half * RH + tid % RH, h = tid / RH;
+  const float2* Sc = Sexp + (int64_t)sub * NR * NR;
+  constexpr int JN = NR / H;  // columns per thread
+  const int j0 = h * JN;
+  float hi = 0.f, lo = 0.f;
+#pragma unroll 8
+  for (int q = 0; q < JN; ++q) {
+    const float2 s = Sc[(j0 + q) * NR + r], x = xr[j0 + q];
+    const float p = __fmul_rn(s.x, x.x);
+    // low-order part: product error (exact via FMA) and the hi*lo cross terms
+    lo = __fadd_rn(lo, __fadd_rn(__fmaf_rn(s.x, x.x, -p), __fmaf_rn(s.x, x.y, __fmul_rn(s.y, x.x))));
+    df_add(hi, lo, p);
+  }
+  const double tot = (double)hi + (double)lo;
+  part[tid] = tot;
+  __syncthreads();
+  double d[1] = {0.0};
+  const int row = half * RH + tid;
+  if (tid < RH && row < si.n_ring) {
+    double y = 0.0;
+#pragma unroll
+    for (int q = 0; q < H; ++q) y += part[q * RH + tid];
+    reinterpret_cast<double*>(io.ring_out)[t.ring_dst[si.ring_off + row]] = y;
+    d[0] = xd[row] * y;
+  }
+  if (io.pcg) {
+    __shared__ double red[32];
+    if (grid_sum<1, 256>(d, io.pcg->partials, &io.pcg->ticket[0], red) && tid == 0)
+      cg_coefficients(io.pcg, d[0]);
+  }
+}
+
 // ============================================================ Gamma sums
+// Sum of the owners' contributions to Gamma DOF g, in owner (subdomain) order;
+// the owner-major layout makes them one contiguous, aligned vector load.
+template <typename T>
+__device__ __forceinline__ double ring_sum(const DevTables& t, const T* __restrict__ ring, int64_t g) {
+  if (t.max_owners == 4) {
+    if constexpr (sizeof(T) == 8) {
+      const double2 a = reinterpret_cast<const double2*>(ring)[2 * g];
+      const double2 b = reinterpret_cast<const double2*>(ring)[2 * g + 1];
+      return ((a.x + a.y) + b.x) + b.y;
+    } else {
+      const float4 v = reinterpret_cast<const float4*>(ring)[g];
+      return (((double)v.x + (double)v.y) + (double)v.z) + (double)v.w;
+    }
+  }
+  double acc = 0.0;
+  for (int k = 0; k < t.max_owners; ++k) acc += (double)ring[g * t.max_owners + k];
+  return acc;
+}
+
 template <typename T>
 __global__ void gamma_sum_kernel(DevTables t, const T* __restrict__ ring,
                                  const double* __restrict__ base, double sign,
                                  double* __restrict__ out) {
   for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < t.n_gamma;
-       g += (int64_t)gridDim.x * blockDim.x) {
-    double acc = 0.0;
-    for (int o = t.owner_ptr[g]; o < t.owner_ptr[g + 1]; ++o) acc += (double)ring[t.owner_idx[o]];
-    out[g] = (base ? base[t.gamma_dof[g]] : 0.0) + sign * acc;
-  }
+       g += (int64_t)gridDim.x * blockDim.x)
+    out[g] = (base ? base[t.gamma_dof[g]] : 0.0) + sign * ring_sum<T>(t, ring, g);
 }
 
 // ============================================================ PCG
@@ -713,8 +808,9 @@ __global__ void __launch_bounds__(kRedThreads) pcg_cg_kernel(DevTables t, DevFie
       r[g] = gin[g];
       return gin[g];
     }
-    double w = 0.0;
-    for (int o = t.owner_ptr[g]; o < t.owner_ptr[g + 1]; ++o) w += (double)ring[t.owner_idx[o]];
+    // S u at this DOF: the ring entries of its owners (fixed-width table,
+    // subdomain order, so the sum order is fixed)
+    const double w = ring_sum<T>(t, ring, g);
     const double pg = u[g] + beta * p[g];
     const double sg = w + beta * sv[g];
     p[g] = pg;
@@ -732,14 +828,23 @@ __global__ void __launch_bounds__(kRedThreads) pcg_cg_kernel(DevTables t, DevFie
     for (int i = lane; i < n; i += 32) {
       const double ri = step(off + i);
       acc[1] += ri * ri;
-      rw[i] = ri / fld.face_w[off + i];
+      rw[i] = ri * fld.face_w[off + i];  // W^-1 r (face_w holds 1 / W_ii)
     }
     __syncwarp();
     for (int i = lane; i < n; i += 32) {
-      double zi = 0.0;
-      for (int j = 0; j < n; ++j) zi += P[j * n + i] * rw[j];
-      acc[0] += rw[i] * zi;  // r_i u_i = (w_i rw_i)(zi / w_i)
-      u[off + i] = zi / fld.face_w[off + i];
+      // column i of the symmetric P, two independent accumulators
+      const double* Pc = P + i;
+      double z0 = 0.0, z1 = 0.0;
+      int j = 0;
+#pragma unroll 4
+      for (; j + 1 < n; j += 2) {
+        z0 += Pc[j * n] * rw[j];
+        z1 += Pc[(j + 1) * n] * rw[j + 1];
+      }
+      if (j < n) z0 += Pc[j * n] * rw[j];
+      const double zi = z0 + z1;
+      acc[0] += rw[i] * zi;  // r_i u_i = (W rw)_i (W^-1 zi)_i
+      u[off + i] = zi * fld.face_w[off + i];
     }
     __syncwarp();
   }
@@ -786,8 +891,8 @@ __global__ void precond_kernel(DevTables t, DevFields fld, const double* __restr
     const double* P = t.ptab + t.blk_poff[b];
     for (int i = lane; i < n; i += 32) {
       double zi = 0.0;
-      for (int j = 0; j < n; ++j) zi += P[j * n + i] * (r[off + j] / fld.face_w[off + j]);
-      z[off + i] = zi / fld.face_w[off + i];
+      for (int j = 0; j < n; ++j) zi += P[j * n + i] * (r[off + j] * fld.face_w[off + j]);
+      z[off + i] = zi * fld.face_w[off + i];
     }
   }
   for (int64_t g = t.n_face_dofs + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < t.n_gamma;
@@ -985,15 +1090,27 @@ void launch_schur_form(const DevTables& t, const DevFields& fld, int precision, 
   }
 }
 
+void launch_split_df(const double* in, float2* out, int64_t n, cudaStream_t st) {
+  split_df_kernel<<<grid_for(n, 256), 256, 0, st>>>(in, out, n);
+}
+
+void launch_schur_explicit_df(const DevTables& t, const float2* Sexp, const SchurIO& io,
+                              cudaStream_t st) {
+  if (explicit_ring_size(t) == 64)
+    schur_explicit_df_kernel<64><<<2 * t.n_sub, 256, 0, st>>>(t, Sexp, io);
+  else
+    schur_explicit_df_kernel<128><<<2 * t.n_sub, 256, 0, st>>>(t, Sexp, io);
+}
+
 void launch_schur_explicit(const DevTables& t, int precision, const void* Sexp, const SchurIO& io,
                            cudaStream_t st) {
   const int NR = explicit_ring_size(t);
   if (precision == 0) {
-    if (NR == 64) schur_explicit_kernel<double, 64><<<t.n_sub, 256, 0, st>>>(t, (const double*)Sexp, io);
-    else schur_explicit_kernel<double, 128><<<t.n_sub, 256, 0, st>>>(t, (const double*)Sexp, io);
+    if (NR == 64) schur_explicit_kernel<double, 64><<<2 * t.n_sub, 256, 0, st>>>(t, (const double*)Sexp, io);
+    else schur_explicit_kernel<double, 128><<<2 * t.n_sub, 256, 0, st>>>(t, (const double*)Sexp, io);
   } else {
-    if (NR == 64) schur_explicit_kernel<float, 64><<<t.n_sub, 256, 0, st>>>(t, (const float*)Sexp, io);
-    else schur_explicit_kernel<float, 128><<<t.n_sub, 256, 0, st>>>(t, (const float*)Sexp, io);
+    if (NR == 64) schur_explicit_kernel<float, 64><<<2 * t.n_sub, 256, 0, st>>>(t, (const float*)Sexp, io);
+    else schur_explicit_kernel<float, 128><<<2 * t.n_sub, 256, 0, st>>>(t, (const float*)Sexp, io);
   }
 }
 

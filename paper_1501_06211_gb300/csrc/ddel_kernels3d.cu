@@ -383,13 +383,13 @@ __global__ void __launch_bounds__(kT3) schur3d_kernel(DevTables t, const T* __re
   }
   double d[1] = {0.0};
   if (io.ring_out) {
-    T* out = reinterpret_cast<T*>(io.ring_out) + si.ring_off;
+    T* out = reinterpret_cast<T*>(io.ring_out);
     for (int r = tid; r < si.n_ring; r += kT3) {
       const int loc = t.ring_loc[si.ring_off + r];
       const int node = loc / 3, c = loc % 3;
       const int a = node / (s1 * s1), b = (node / s1) % s1, cc = node % s1;
       const T y = ebe_local3d<T>(ke, sc, xloc, s, a, b, cc, c);
-      out[r] = y;
+      out[t.ring_dst[si.ring_off + r]] = y;
       d[0] += (double)xloc[loc] * (double)y;
     }
   }

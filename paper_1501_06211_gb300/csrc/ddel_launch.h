@@ -20,6 +20,12 @@ struct DevTables {
   int64_t n_ring;
   int32_t* owner_ptr;
   int32_t* owner_idx;
+  int32_t* owner_pad;  // n_gamma x max_owners, -1 padded (16-byte aligned rows in 2D)
+  // Ring entries are stored owner-major: the contribution of ring slot q lives
+  // at ring[ring_dst[q]] = ring[g * max_owners + k]; a Gamma DOF reads its
+  // max_owners entries contiguously (unused entries hold 0).
+  int32_t* ring_dst;
+  int max_owners;
   int64_t* gamma_dof;
   int32_t* blk_off;
   int32_t* blk_n;
@@ -47,7 +53,7 @@ struct DevFields {
   float* scale32;
   double* diagG;    // n_gamma: diag(K_GG)
   double* blk_alpha;
-  double* face_w;       // n_face_dofs: S~_f^-1 = W^-1 H_f^-1 W^-1
+  double* face_w;       // n_face_dofs: S~_f^-1 = W^-1 H_f^-1 W^-1; stores 1 / W_ii
   double* cross_scale;  // n_gamma - n_face_dofs
 };
 
@@ -90,6 +96,11 @@ size_t schur_smem_bytes(const DevTables& t, int precision);
 int explicit_ring_size(const DevTables& t);
 void launch_schur_form(const DevTables& t, const DevFields& fld, int precision, const void* factor,
                        void* Sexp, cudaStream_t st);
+// Double-float form: S_i split into FP32 (hi, lo) pairs; the apply runs on the
+// FP32 pipes with about 48 significant bits (ring output FP64).
+void launch_split_df(const double* in, float2* out, int64_t n, cudaStream_t st);
+void launch_schur_explicit_df(const DevTables& t, const float2* Sexp, const SchurIO& io,
+                              cudaStream_t st);
 void launch_schur_explicit(const DevTables& t, int precision, const void* Sexp, const SchurIO& io,
                            cudaStream_t st);
 // Sum ring contributions: out[g] = sign * sum(ring) + (base ? base[gamma_dof[g]] : 0)

@@ -490,6 +490,22 @@ std::string build_setup(int dim, const int ne_in[3], int sub, double E, double n
   S->owner_idx.assign(S->ring_gidx.size(), 0);
   std::vector<int32_t> fill(S->owner_ptr.begin(), S->owner_ptr.end() - 1);
   for (size_t r = 0; r < S->ring_gidx.size(); ++r) S->owner_idx[fill[S->ring_gidx[r]]++] = (int32_t)r;
+  // the same owners as a fixed-width table (one vector load per Gamma DOF)
+  S->max_owners = dim == 2 ? 4 : 8;
+  S->owner_pad.assign((size_t)ng * S->max_owners, -1);
+  for (int64_t g = 0; g < ng; ++g) {
+    if (S->owner_ptr[g + 1] - S->owner_ptr[g] > S->max_owners) return "internal: too many owners";
+    for (int o = S->owner_ptr[g]; o < S->owner_ptr[g + 1]; ++o)
+      S->owner_pad[(size_t)g * S->max_owners + (o - S->owner_ptr[g])] = S->owner_idx[o];
+  }
+  // owner-major destination of every ring slot: subdomain contributions land
+  // in the max_owners consecutive entries of their Gamma DOF (unused ones stay 0)
+  S->ring_dst.assign(S->ring_gidx.size(), -1);
+  for (int64_t g = 0; g < ng; ++g)
+    for (int k = 0; k < S->max_owners; ++k) {
+      const int32_t slot = S->owner_pad[(size_t)g * S->max_owners + k];
+      if (slot >= 0) S->ring_dst[slot] = (int32_t)(g * S->max_owners + k);
+    }
   return "";
 }
 

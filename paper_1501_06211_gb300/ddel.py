@@ -65,7 +65,7 @@ class ddel_info_t(ctypes.Structure):
 class ddel_kernel_info_t(ctypes.Structure):
     _fields_ = [("launches_total", c_int64), ("launches_since_assemble", c_int64),
                 ("schur_apply_bytes", c_int64), ("schur_apply_flops", c_int64),
-                ("schur_form", c_int), ("precision", c_int)]
+                ("schur_form", c_int), ("precision", c_int), ("double_float", c_int)]
 
 
 class ddel_topopt_state(ctypes.Structure):
@@ -104,6 +104,8 @@ def _load():
         "ddel_load_vector": (c_int, [c_void_p, c_void_p]),
         "ddel_fixed_mask": (c_int, [c_void_p, c_void_p]),
         "ddel_kernel_info": (c_int, [c_void_p, P(ddel_kernel_info_t)]),
+        "ddel_batch_solve": (c_int, [c_void_p, c_int, c_void_p, c_void_p]),
+        "ddel_autotune": (c_int, [c_void_p, ctypes.c_char_p, c_void_p, c_void_p, c_void_p]),
         "ddel_topopt_step": (c_int, [c_void_p, P(ddel_topopt_state), P(ddel_stats)]),
         "ddel_residual_norm_noalloc": (c_int, [c_int, c_int, c_int, c_int, c_void_p, c_void_p,
                                                c_void_p, c_void_p, c_void_p, c_void_p, c_void_p,
@@ -233,12 +235,32 @@ def ddel_topopt_step(h, state):
     return code, st
 
 
+def ddel_batch_solve(handles, us=None):
+    """Concurrent solves of several assembled contexts; us: device tensors or None."""
+    n = len(handles)
+    harr = (c_void_p * n)(*[h.value if hasattr(h, "value") else h for h in handles])
+    uarr = (c_void_p * n)(*[(_ptr(u) if u is not None else None) for u in (us or [None] * n)])
+    sts = (ddel_stats * n)()
+    code = _lib.ddel_batch_solve(harr, n, uarr, sts)
+    return code, list(sts)
+
+
+def ddel_autotune(h, cache_path=None):
+    """Times the Schur forms and batch sizes on this GPU; returns (code, mode, check, cached)."""
+    m, c, fc = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    code = _lib.ddel_autotune(h, cache_path.encode() if cache_path else None, ctypes.byref(m),
+                              ctypes.byref(c), ctypes.byref(fc))
+    return code, m.value, c.value, bool(fc.value)
+
+
 def ddel_kernel_info(h):
     k = ddel_kernel_info_t()
     _check(_lib.ddel_kernel_info(h, ctypes.byref(k)), h)
     d = {n: getattr(k, n) for n, _ in k._fields_}
-    d["schur_apply_kernel"] = ("schur_explicit_kernel" if k.schur_form else "schur2d_kernel") + \
-        ("<float>" if k.precision else "<double>")
+    d["schur_apply_kernel"] = (
+        "schur_explicit_df_kernel (FP32-pair arithmetic)" if k.double_float else
+        ("schur_explicit_kernel" if k.schur_form else "schur2d_kernel") +
+        ("<float>" if k.precision else "<double>"))
     return d
 
 

@@ -77,7 +77,7 @@ def test_apply_K(name):
     assert rel(y.cpu().numpy(), ref) < 1e-13
 
 
-@pytest.mark.parametrize("mode", [0, 1], ids=["implicit", "explicit"])
+@pytest.mark.parametrize("mode", [0, 1, 2], ids=["implicit", "explicit", "auto_double_float"])
 @pytest.mark.parametrize("name", list(CASES))
 def test_condense_schur_precond_backsub(name, mode):
     from paper_1501_06211_gb300 import ddel
