@@ -58,7 +58,13 @@ typedef enum {
  *       explicit form is unavailable it behaves as FP64. */
 typedef enum { DDEL_FP64 = 0, DDEL_FP32 = 1, DDEL_MIXED = 2 } ddel_precision;
 typedef enum { DDEL_SCHUR_IMPLICIT = 0, DDEL_SCHUR_EXPLICIT = 1, DDEL_SCHUR_AUTO = 2 } ddel_schur_mode;
-typedef enum { DDEL_X0_ZERO = 0, DDEL_X0_WARM = 1, DDEL_X0_GIVEN = 2 } ddel_x0_mode;
+/* Initial iterate of ddel_solve: ZERO (u = 0), WARM (the previous converged
+ * solution of this context, e.g. of the last Picard step; 0 before the first). */
+typedef enum { DDEL_X0_ZERO = 0, DDEL_X0_WARM = 1 } ddel_x0_mode;
+/* Coarse-space use (ddel_set_coarse).  Not in the paper, whose preconditioner
+ * is face-local only. */
+typedef enum { DDEL_COARSE_X0 = 1, DDEL_COARSE_CORRECT = 2, DDEL_COARSE_DEFLATE = 4 } ddel_coarse_flags;
+#define DDEL_MAX_COARSE 8
 
 /* Structured grid of unit elements, split into sub^dim-element subdomains
  * (Sec. 1: N non-overlapping subdomains).  dim = 2 (Q1 bilinear, 2 DOF/node)
@@ -111,7 +117,7 @@ typedef struct {
   int max_it;          /* PCG iteration cap per cycle (5000) */
   int max_cycles;      /* refinement cycles cap (10) */
   double inner_tol;    /* per-cycle PCG reduction in FP32 mode (1e-6) */
-  int x0_mode;         /* ddel_x0_mode for the interface PCG (ZERO) */
+  int x0_mode;         /* ddel_x0_mode of ddel_solve (ZERO) */
   int schur_mode;      /* ddel_schur_mode (AUTO): EXPLICIT/AUTO form each local Schur
                           complement S_i after the factorisation where the ring fits
                           (2D, sub <= 16) and apply it as one dense product per PCG
@@ -127,8 +133,11 @@ typedef struct {
   double relres;       /* final ||f - K u||_2 / ||f||_2 computed in FP64 */
   double pcg_relres;   /* last interface residual ||r_G|| / ||f|| of the recurrence */
   int bad_subdomain;   /* first subdomain with a failed pivot, or -1 */
-  int fallback;        /* 1 if an FP32 solve switched to the FP64 factors */
+  int fallback;        /* bit 0: an FP32 solve switched to the FP64 factors; bit 1: the
+                          coarse space was dropped after a Krylov breakdown */
   double t_factor_ms, t_condense_ms, t_pcg_ms, t_backsub_ms, t_verify_ms, t_total_ms;
+  int coarse_k;        /* coarse dimension used by the interface PCG (0: none) */
+  int x0_used;         /* cycles whose PCG started from the Galerkin guess */
 } ddel_stats;
 
 typedef struct {
@@ -178,6 +187,24 @@ int ddel_factor(ddel_ctx* ctx);
  * else device.  st may be NULL.  Synchronises the stream. */
 int ddel_solve(ddel_ctx* ctx, const double* f, double* u, int on_device, ddel_stats* st);
 
+/* Coarse space for the interface PCG (an addition to the paper's face-local
+ * preconditioner of Sec. 3-4).  Z: k vectors over the Gamma DOFs (column-major,
+ * k x n_gamma doubles in ddel_gamma_dofs order; host when on_device == 0, else
+ * device), 0 <= k <= DDEL_MAX_COARSE; k == 0 removes the coarse space.  The
+ * library orthonormalises Z (Cholesky QR, twice; numerically dependent columns
+ * are dropped), forms E = Q^T S Q with the context's Schur apply after each
+ * factorisation (lazily, at the next solve) and, with flags:
+ *   DDEL_COARSE_X0:      each PCG starts from the Galerkin guess
+ *                        x0 = Q E^-1 Q^T g (kept only if ||g - S x0|| <= ||g||);
+ *   DDEL_COARSE_CORRECT: preconditioner S~^-1 r + Q E^-1 Q^T r (additive, SPD);
+ *   DDEL_COARSE_DEFLATE: instead, Q E^-1 Q^T r + (I - Q E^-1 Q^T S) S~^-1 r
+ *                        (deflation in the "A-DEF2" form of Tang, Nabben, Vuik
+ *                        and Erlangga 2009; eigenvalue 1 on span(Q)).
+ * If E is not SPD the solve runs plain PCG (stats.coarse_k = 0).  Z is copied;
+ * the caller keeps ownership.  Errors: EINVAL (k or flags out of range, or
+ * CORRECT together with DEFLATE). */
+int ddel_set_coarse(ddel_ctx* ctx, const double* Z, int k, int flags, int on_device);
+
 /* --- Topology optimisation (Sec. 5) ------------------------------------------
  * One Picard step of the variable-thickness-sheet / SIMP problem of
  * eq. NumberTen: density filter rho~ = Hbar rho (hat weights
@@ -201,6 +228,8 @@ typedef struct {
   double lambda;      /* out: OC volume multiplier */
   double* u;          /* device, n_dof, or NULL: displacement of this step */
   double* rho_phys;   /* device, n_elem, or NULL: filtered densities of this step */
+  void* learner;      /* a ddel_learner of this context (ddel_learn.h) or NULL: coarse
+                         space predicted before the solve, observation after it */
 } ddel_topopt_state;
 /* Densities must lie in [rho_min, 1]; the loads are those of ddel_bc.
  * Synchronises the stream.  st (may be NULL) receives the solve statistics. */
@@ -248,8 +277,9 @@ int ddel_schur_apply(ddel_ctx* ctx, const double* x, double* y);
 int ddel_precond_apply(ddel_ctx* ctx, const double* r, double* z);
 /* u_I = K_II^-1 (f_I - K_IG u_G), u_G = uG, u = 0 on fixed DOFs (eq. 3MatSplit2). */
 int ddel_back_substitute(ddel_ctx* ctx, const double* f, const double* uG, double* u);
-/* Interface PCG on S x = g from x = 0 (or x as given with x0_mode GIVEN);
- * stops at ||r|| <= tol_abs.  g, x: device n_gamma.  Synchronises. */
+/* Interface PCG on S x = g from x = 0 (from the Galerkin guess, and with the
+ * coarse correction, when ddel_set_coarse gave a coarse space); stops at
+ * ||r|| <= tol_abs.  g, x: device n_gamma.  Synchronises. */
 int ddel_pcg(ddel_ctx* ctx, const double* g, double* x, double tol_abs, ddel_stats* st);
 /* ||f - K u||_2 and ||f||_2 over free DOFs in FP64 (device f, u; host outputs). */
 int ddel_residual_norm(ddel_ctx* ctx, const double* f, const double* u, double* r_norm,

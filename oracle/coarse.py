@@ -9,7 +9,10 @@ correction and the Galerkin initial guess that the solver adds on top of it:
   E      = Q^T S Q   (k x k, must be SPD, else the coarse space is unusable),
   x0     = Q E^-1 Q^T g   (the S-orthogonal projection of S^-1 g onto span(Q);
          discarded when ||g - S x0|| > ||g||),
-  P_c r  = P r + Q E^-1 Q^T r   (additive, SPD when P and E are).
+  P_c r  = P r + Q E^-1 Q^T r   (additive, SPD when P and E are),
+  P_d r  = Q E^-1 Q^T r + (I - Q E^-1 Q^T S) P r   (deflation, the "A-DEF2"
+         form of Tang, Nabben, Vuik and Erlangga, J. Sci. Comput. 39 (2009):
+         eigenvalue 1 on span(Q) and the preconditioned spectrum elsewhere).
 """
 import numpy as np
 
@@ -70,13 +73,25 @@ class CoarseSpace:
             return apply_P
         return lambda r: apply_P(r) + self.Q @ self.solve_E(self.Q.T @ r)
 
+    def deflated_preconditioner(self, apply_P):
+        if not self.spd or self.k == 0:
+            return apply_P
 
-def coarse_pcg(apply_S, apply_P, g, Z, tol, max_it, ref_norm=None):
+        def apply(r):
+            z = apply_P(r)
+            # Q^T S z = (S Q)^T z, S symmetric
+            return z + self.Q @ self.solve_E(self.Q.T @ r - self.SQ.T @ z)
+        return apply
+
+
+def coarse_pcg(apply_S, apply_P, g, Z, tol, max_it, ref_norm=None, deflate=False):
     """Interface PCG with the coarse space of Z: Galerkin x0 and the additive
-    correction.  Returns (x, iterations, history, coarse_space)."""
+    (or, with deflate, the deflation) correction.  Returns (x, iterations,
+    history, coarse_space)."""
     from oracle.dd import pcg
     cs = CoarseSpace(apply_S, Z)
     x0 = cs.x0(g)
     ref = np.linalg.norm(g) if ref_norm is None else ref_norm
-    x, it, hist = pcg(apply_S, cs.preconditioner(apply_P), g, tol, max_it, x0=x0, ref_norm=ref)
+    P = cs.deflated_preconditioner(apply_P) if deflate else cs.preconditioner(apply_P)
+    x, it, hist = pcg(apply_S, P, g, tol, max_it, x0=x0, ref_norm=ref)
     return x, it, hist, cs

@@ -5,6 +5,7 @@
 
 #include <cmath>
 #include <cstdio>
+#include <algorithm>
 #include <cstring>
 #include <new>
 #include <string>
@@ -12,6 +13,7 @@
 #include <vector>
 
 #include "../../include/ddel.h"
+#include "../../include/ddel_learn.h"
 #include "ddel_internal.h"
 #include "ddel_launch.h"
 #include "ddel_topopt.h"
@@ -71,8 +73,32 @@ struct ddel_ctx {
   double* topo_out = nullptr;    // device: lambda, volume, change, compliance
   double* h_topo = nullptr;      // pinned copy
   double dv_rmin = -1.0;         // filter radius dv was computed for
+  // coarse space of the interface PCG (ddel_set_coarse; allocated on first use)
+  double *cZ = nullptr, *cQ1 = nullptr, *cQ = nullptr, *cSQ = nullptr;
+  double* csmall = nullptr;      // 6 k x k blocks: G1 T1 G2 T2 E Einv | Gsq
+  int* cflags = nullptr;         // k after pass 1, k after pass 2, E SPD
+  unsigned* cticket = nullptr;
+  int* h_cflags = nullptr;
+  int ck_in = 0;                 // columns given
+  int ck = 0;                    // usable coarse dimension (0: plain PCG)
+  int coarse_flags = 0;          // DDEL_COARSE_* bits
+  int coarse_prec = -1;          // precision whose S formed E (-1: stale)
+  int graph_ck[2] = {0, 0};      // coarse dimension captured in graph[prec]
+  bool u_valid = false;          // d_u holds a converged solution (x0_mode WARM)
+  std::vector<ddel_learner*> learners;  // attached learners (detached on destroy)
   std::string last_error;
 };
+
+namespace ddel {
+cudaStream_t ctx_stream(const ddel_ctx* ctx) { return ctx->stream; }
+ddel_mesh ctx_mesh(const ddel_ctx* ctx) { return ctx->mesh; }
+void ctx_attach_learner(ddel_ctx* ctx, ddel_learner* L) { ctx->learners.push_back(L); }
+void ctx_detach_learner(ddel_ctx* ctx, ddel_learner* L) {
+  auto& v = ctx->learners;
+  v.erase(std::remove(v.begin(), v.end(), L), v.end());
+}
+void learner_context_gone(ddel_learner* L);  // ddel_learner.cu
+}  // namespace ddel
 
 namespace {
 
@@ -144,39 +170,76 @@ SchurIO make_io(ddel_ctx* ctx) {
   return io;
 }
 
-// One PCG iteration: w = S u (ring) with delta = (S u, u) -> alpha, beta; then
-// the vector updates and u = S~^-1 r with gamma = (r, u).
-void pcg_iteration(ddel_ctx* ctx, int prec, bool apply32) {
-  cudaStream_t s = ctx->stream;
+// The Schur apply that the PCG of precision prec uses (double-float explicit,
+// explicit, or implicit block substitution), into the ring of that precision.
+int apply_prec(ddel_ctx* ctx, int prec, bool apply32) {
   const bool expl = ctx->explicit_ok[prec];
-  const int aprec = apply32 ? 1 : prec;  // precision of the Schur apply and ring
-  SchurIO io = make_io(ctx);
-  io.x = ctx->z;
-  io.ring_out = ring_of(ctx, expl ? aprec : prec);
-  io.done = &ctx->st->done;
-  io.pcg = ctx->st;
+  return expl ? (apply32 ? 1 : prec) : prec;
+}
+
+void schur_dispatch(ddel_ctx* ctx, int prec, bool apply32, SchurIO& io, cudaStream_t s) {
+  const bool expl = ctx->explicit_ok[prec];
+  io.ring_out = ring_of(ctx, apply_prec(ctx, prec, apply32));
   const void* smat = apply32 ? (const void*)ctx->sexp32 : ctx->sexp[prec];
   if (expl && prec == 0 && !apply32 && ctx->df_ok)
     launch_schur_explicit_df(ctx->T, ctx->sexp_df, io, s);
   else if (expl)
-    launch_schur_explicit(ctx->T, aprec, smat, io, s);
+    launch_schur_explicit(ctx->T, apply32 ? 1 : prec, smat, io, s);
   else
     launch_schur(ctx->T, ctx->F, prec, ctx->factor[prec], io, s);
-  launch_pcg_update(ctx->T, ctx->F, expl ? aprec : prec, io.ring_out, ctx->x, ctx->r, ctx->z, ctx->p,
-                    ctx->sv, ctx->st, s, ctx->nblk);
+}
+
+CoarseDev coarse_dev(ddel_ctx* ctx) {
+  CoarseDev cd;
+  if (ctx->ck <= 0) return cd;
+  const int KK = kMaxCoarse * kMaxCoarse;
+  cd.Q = ctx->cQ;
+  cd.SQ = ctx->cSQ;
+  cd.Einv = ctx->csmall + 5 * KK;
+  cd.G = ctx->csmall + 6 * KK;
+  cd.k = ctx->ck;
+  cd.correct = (ctx->coarse_flags & DDEL_COARSE_CORRECT) ? 1 : (ctx->coarse_flags & DDEL_COARSE_DEFLATE) ? 2 : 0;
+  cd.x0 = (ctx->coarse_flags & DDEL_COARSE_X0) ? 1 : 0;
+  return cd;
+}
+
+// One PCG iteration: w = S u (ring) with delta = (S u, u) -> alpha, beta; then
+// the vector updates and u = S~^-1 r (+ the coarse part) with gamma = (r, u).
+void pcg_iteration(ddel_ctx* ctx, int prec, bool apply32) {
+  cudaStream_t s = ctx->stream;
+  const CoarseDev cd = coarse_dev(ctx);
+  SchurIO io = make_io(ctx);
+  io.x = ctx->z;
+  io.done = &ctx->st->done;
+  io.pcg = ctx->st;
+  if (cd.k > 0 && cd.correct) {
+    io.cq = cd.Q;
+    io.ccoef = ctx->st->cc;
+    io.ck = cd.k;
+  }
+  schur_dispatch(ctx, prec, apply32, io, s);
+  launch_pcg_update(ctx->T, ctx->F, apply_prec(ctx, prec, apply32), io.ring_out, ctx->x, ctx->r,
+                    ctx->z, ctx->p, ctx->sv, ctx->st, s, ctx->nblk, cd);
 }
 
 // PCG initialisation (asynchronous) and, with use_graph, the CUDA graph of
 // check_every iterations for this precision and form.
 int pcg_start(ddel_ctx* ctx, int prec, const double* g, bool apply32) {
   cudaStream_t s = ctx->stream;
-  launch_pcg_init(ctx->T, ctx->F, g, ctx->x, ctx->r, ctx->z, ctx->p, ctx->sv, ctx->st, s, ctx->nblk);
+  const CoarseDev cd = coarse_dev(ctx);
+  if (cd.k > 0 && cd.x0) {
+    launch_coarse_x0(cd, g, ctx->T.n_gamma, ctx->st, s);
+    ctx->launches += 1;
+  }
+  launch_pcg_init(ctx->T, ctx->F, g, ctx->x, ctx->r, ctx->z, ctx->p, ctx->sv, ctx->st, s, ctx->nblk, cd);
   ctx->launches += 1;
   const int per = ctx->opt.check_every > 0 ? ctx->opt.check_every : 16;
   const bool expl = ctx->explicit_ok[prec];
   const bool df = prec == 0 && ctx->df_ok;
+  const int gck = cd.k > 0 && cd.correct ? cd.k : 0;
   if (ctx->graph[prec] && (ctx->graph_explicit[prec] != expl || ctx->graph_apply32[prec] != apply32 ||
-                           ctx->graph_iters != per || (prec == 0 && ctx->graph_df != df))) {
+                           ctx->graph_iters != per || (prec == 0 && ctx->graph_df != df) ||
+                           ctx->graph_ck[prec] != gck)) {
     cudaGraphExecDestroy(ctx->graph[prec]);
     ctx->graph[prec] = nullptr;
   }
@@ -190,6 +253,7 @@ int pcg_start(ddel_ctx* ctx, int prec, const double* g, bool apply32) {
     ctx->graph_iters = per;
     ctx->graph_explicit[prec] = expl;
     ctx->graph_apply32[prec] = apply32;
+    ctx->graph_ck[prec] = gck;
     if (prec == 0) ctx->graph_df = df;
   }
   return DDEL_OK;
@@ -292,6 +356,8 @@ int factor_check(ddel_ctx* ctx, int prec) {
     return fail(ctx, DDEL_ENOTSPD, "pivot failure in subdomain " + std::to_string(ctx->h_err[1]));
   ctx->factored[prec] = true;
   ctx->explicit_ok[prec] = ctx->pending_explicit;
+  ctx->coarse_prec = -1;  // E must be formed again with the new S (next ddel_solve)
+  ctx->ck = 0;
   if (prec == 0) ctx->df_ok = false;
   if (prec == 0 && ctx->explicit_ok[0] && ctx->opt.schur_mode == DDEL_SCHUR_AUTO) {
     // FP64 local Schur complements as FP32 (hi, lo) pairs for the double-float apply
@@ -310,6 +376,52 @@ int factor_check(ddel_ctx* ctx, int prec) {
 int factor_prec(ddel_ctx* ctx, int prec) {
   int rc = factor_launch(ctx, prec);
   return rc ? rc : factor_check(ctx, prec);
+}
+
+// Coarse space for the PCG of precision prec (and apply32): Cholesky QR of Z
+// twice, S Q with the same Schur apply as the PCG, E = Q^T S Q and its
+// inverse, G = (S Q)^T S Q.  Synchronises (three small read-backs).
+int coarse_build(ddel_ctx* ctx, int prec, bool apply32) {
+  cudaStream_t s = ctx->stream;
+  const int64_t n = ctx->T.n_gamma;
+  const int KK = kMaxCoarse * kMaxCoarse;
+  double* cs = ctx->csmall;
+  ctx->ck = 0;
+  launch_gram(ctx->cZ, ctx->cZ, ctx->ck_in, n, cs, ctx->partials, ctx->cticket, s);
+  launch_cholqr_factor(cs, ctx->ck_in, 1e-10, cs + KK, ctx->cflags, s);
+  launch_apply_T(ctx->cZ, cs + KK, ctx->ck_in, ctx->cflags, n, ctx->cQ1, s);
+  ctx->launches += 3;
+  int k1 = 0;
+  CK(cudaMemcpyAsync(ctx->h_cflags, ctx->cflags, sizeof(int), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  k1 = ctx->h_cflags[0];
+  ctx->coarse_prec = prec * 2 + (apply32 ? 1 : 0);
+  if (k1 <= 0) return DDEL_OK;
+  launch_gram(ctx->cQ1, ctx->cQ1, k1, n, cs + 2 * KK, ctx->partials, ctx->cticket, s);
+  launch_cholqr_factor(cs + 2 * KK, k1, 1e-10, cs + 3 * KK, ctx->cflags + 1, s);
+  launch_apply_T(ctx->cQ1, cs + 3 * KK, k1, ctx->cflags + 1, n, ctx->cQ, s);
+  ctx->launches += 3;
+  CK(cudaMemcpyAsync(ctx->h_cflags + 1, ctx->cflags + 1, sizeof(int), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  const int k2 = ctx->h_cflags[1];
+  if (k2 <= 0) return DDEL_OK;
+  const int ap = apply_prec(ctx, prec, apply32);
+  for (int i = 0; i < k2; ++i) {
+    SchurIO io = make_io(ctx);
+    io.x = ctx->cQ + i * n;
+    schur_dispatch(ctx, prec, apply32, io, s);
+    launch_gamma_sum(ctx->T, ap, io.ring_out, nullptr, 1.0, ctx->cSQ + i * n, s);
+    ctx->launches += 2;
+  }
+  launch_gram(ctx->cQ, ctx->cSQ, k2, n, cs + 4 * KK, ctx->partials, ctx->cticket, s);
+  launch_gram(ctx->cSQ, ctx->cSQ, k2, n, cs + 6 * KK, ctx->partials, ctx->cticket, s);
+  launch_coarse_invert(cs + 4 * KK, k2, cs + 5 * KK, ctx->cflags + 2, s);
+  ctx->launches += 3;
+  CK(cudaMemcpyAsync(ctx->h_cflags + 2, ctx->cflags + 2, sizeof(int), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  CK(cudaGetLastError());
+  ctx->ck = ctx->h_cflags[2] ? k2 : 0;
+  return DDEL_OK;
 }
 
 float elapsed(cudaEvent_t a, cudaEvent_t b) {
@@ -450,7 +562,7 @@ int ddel_create(const ddel_mesh* mesh, const ddel_material* mat, const ddel_bc* 
         bad(dalloc(ctx, &ctx->p, ng * 8)) || bad(dalloc(ctx, &ctx->q, ng * 8)) ||
         bad(dalloc(ctx, &ctx->sv, ng * 8)) ||
         bad(dalloc(ctx, &ctx->rho, S.n_elem * 8)) || bad(dalloc(ctx, &ctx->st, sizeof(PcgState))) ||
-        bad(dalloc(ctx, &ctx->partials, (size_t)(4 * 152 * 8 + 2 * T.n_sub + 64) * 8)) ||
+        bad(dalloc(ctx, &ctx->partials, (size_t)(4 * 152 * (2 + 2 * kMaxCoarse) + 2 * T.n_sub + 64) * 8)) ||
         bad(dalloc(ctx, &ctx->ticketK, 16)) || bad(dalloc(ctx, &ctx->nrm, 16)) ||
         bad(dalloc(ctx, &ctx->err, 4 * sizeof(int))))
       goto fail_out;
@@ -483,6 +595,8 @@ fail_out:
 void ddel_destroy(ddel_ctx* ctx) {
   if (!ctx) return;
   if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+  for (ddel_learner* L : ctx->learners) learner_context_gone(L);  // they must not touch ctx again
+  ctx->learners.clear();
   for (auto& g : ctx->graph)
     if (g) cudaGraphExecDestroy(g);
   for (void* p : ctx->allocs) cudaFree(p);
@@ -498,6 +612,7 @@ void ddel_destroy(ddel_ctx* ctx) {
   if (ctx->h_nrm) cudaFreeHost(ctx->h_nrm);
   if (ctx->h_err) cudaFreeHost(ctx->h_err);
   if (ctx->h_topo) cudaFreeHost(ctx->h_topo);
+  if (ctx->h_cflags) cudaFreeHost(ctx->h_cflags);
   for (auto& e : ctx->ev)
     if (e) cudaEventDestroy(e);
   if (ctx->own_stream && ctx->stream) cudaStreamDestroy(ctx->stream);
@@ -588,10 +703,11 @@ int ddel_solve(ddel_ctx* ctx, const double* f, double* u, int on_device, ddel_st
     CK(cudaMemcpyAsync(ctx->d_f, ctx->d_load, nd * 8, cudaMemcpyDeviceToDevice, s));
   else
     CK(cudaMemcpyAsync(ctx->d_f, f, nd * 8, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
-  CK(cudaMemsetAsync(ctx->d_u, 0, nd * 8, s));
+  // ZERO: u = 0; WARM: u = the previous solution (d_u keeps it between solves)
+  if (!(ctx->opt.x0_mode == DDEL_X0_WARM && ctx->u_valid)) CK(cudaMemsetAsync(ctx->d_u, 0, nd * 8, s));
   const int init[2] = {0, 0x7fffffff};
   CK(cudaMemcpyAsync(ctx->err, init, sizeof(init), cudaMemcpyHostToDevice, s));
-  // r = f - K 0 = f and ||f||
+  // r = f - K u and ||f||
   launch_apply_K(ctx->T, ctx->F, ctx->d_u, ctx->d_f, ctx->d_r, 1, ctx->partials, ctx->ticketK,
                  ctx->nrm, s, ctx->nblk);
   ctx->launches += 1;
@@ -605,12 +721,27 @@ int ddel_solve(ddel_ctx* ctx, const double* f, double* u, int on_device, ddel_st
                                    (prec == 1 || apply32) ? 1 : 0, ctx->opt.max_it);
     ctx->launches += 1;
     CK(cudaEventRecord(ctx->ev[1], s));
+    if (ctx->ck_in > 0 && ctx->coarse_prec != prec * 2 + (apply32 ? 1 : 0)) {
+      int rc = coarse_build(ctx, prec, apply32);
+      if (rc) return rc;
+    }
     condense(ctx, prec, ctx->d_r, ctx->g);
     CK(cudaEventRecord(ctx->ev[2], s));
     int it = 0, pst = 0;
     int rc = pcg_run(ctx, prec, ctx->g, &it, &pst, apply32);
     if (rc) return rc;
     st.iters += it;
+    st.coarse_k = ctx->ck;
+    if (ctx->ck > 0 && (ctx->coarse_flags & DDEL_COARSE_X0)) st.x0_used += ctx->h_st->x0_used;
+    if (pst == DDEL_EBREAKDOWN && ctx->ck > 0) {
+      // The coarse-corrected recurrence lost definiteness (rounding with an
+      // ill-conditioned or inaccurate coarse space): drop the coarse space for
+      // the rest of this solve and redo the cycle with plain PCG.
+      ctx->ck = 0;
+      st.coarse_k = 0;
+      st.fallback |= 2;
+      continue;
+    }
     CK(cudaEventRecord(ctx->ev[3], s));
     back_substitute(ctx, prec, ctx->d_r, ctx->x, ctx->d_d);
     launch_axpy(nd, 1.0, ctx->d_d, ctx->d_u, s);
@@ -706,6 +837,7 @@ int ddel_solve(ddel_ctx* ctx, const double* f, double* u, int on_device, ddel_st
   st.t_verify_ms = t_ver;
   st.t_total_ms = elapsed(ctx->ev[0], ctx->ev[6]);
   st.status = status;
+  ctx->u_valid = status == DDEL_OK;
   if (stats) *stats = st;
   return status;
 }
@@ -737,9 +869,12 @@ int ddel_topopt_step(ddel_ctx* ctx, ddel_topopt_state* ts, ddel_stats* stats) {
   if (rc) return rc;
   rc = ddel_factor(ctx);
   if (rc) return rc;
+  ddel_learner* learner = static_cast<ddel_learner*>(ts->learner);
+  if (learner && (rc = ddel_learner_predict(learner, ctx->rho_f))) return rc;
   double* u = ts->u ? ts->u : ctx->topo_u;
   rc = ddel_solve(ctx, nullptr, u, 1, stats);
   if (rc) return rc;
+  if (learner && (rc = ddel_learner_observe(learner, ctx->rho_f, u))) return rc;
   launch_dot(ctx->d_load, u, nd, ctx->partials, ctx->ticketK, ctx->topo_out + 3, s);
   launch_sensitivity(ctx->T, ctx->mat.E, ctx->mat.simp_p, ctx->rho_f, u, ctx->dcf, s);
   launch_filter(ctx->T, ts->r_min, ctx->dcf, ctx->dc, 1, s);
@@ -995,16 +1130,44 @@ int ddel_schur_apply(ddel_ctx* ctx, const double* x, double* y) {
   if (!ctx->factored[prec]) return fail(ctx, DDEL_ESTATE, "factor first");
   SchurIO io = make_io(ctx);
   io.x = x;
-  io.ring_out = ring_of(ctx, prec);
-  if (prec == 0 && ctx->df_ok)
-    launch_schur_explicit_df(ctx->T, ctx->sexp_df, io, ctx->stream);
-  else if (ctx->explicit_ok[prec])
-    launch_schur_explicit(ctx->T, prec, ctx->sexp[prec], io, ctx->stream);
-  else
-    launch_schur(ctx->T, ctx->F, prec, ctx->factor[prec], io, ctx->stream);
-  launch_gamma_sum(ctx->T, prec, io.ring_out, nullptr, 1.0, y, ctx->stream);
+  schur_dispatch(ctx, prec, false, io, ctx->stream);
+  launch_gamma_sum(ctx->T, apply_prec(ctx, prec, false), io.ring_out, nullptr, 1.0, y, ctx->stream);
   ctx->launches += 2;
   CK(cudaGetLastError());
+  return DDEL_OK;
+}
+
+int ddel_set_coarse(ddel_ctx* ctx, const double* Z, int k, int flags, int on_device) {
+  if (!ctx) return DDEL_EINVAL;
+  if (k < 0 || k > kMaxCoarse || (k > 0 && !Z))
+    return fail(ctx, DDEL_EINVAL, "coarse space: need 0 <= k <= DDEL_MAX_COARSE and Z");
+  if (k > 0 && (flags <= 0 || (flags & ~(DDEL_COARSE_X0 | DDEL_COARSE_CORRECT | DDEL_COARSE_DEFLATE)) ||
+                ((flags & DDEL_COARSE_CORRECT) && (flags & DDEL_COARSE_DEFLATE))))
+    return fail(ctx, DDEL_EINVAL,
+                "coarse space: flags = DDEL_COARSE_X0 and/or one of DDEL_COARSE_CORRECT, DDEL_COARSE_DEFLATE");
+  ctx->ck = 0;
+  ctx->coarse_prec = -1;
+  ctx->ck_in = k;
+  ctx->coarse_flags = k > 0 ? flags : 0;
+  if (k == 0) return DDEL_OK;
+  const int64_t n = ctx->T.n_gamma;
+  if (!ctx->cZ) {
+    const size_t vb = (size_t)kMaxCoarse * n * 8;
+    if (dalloc(ctx, &ctx->cZ, vb) || dalloc(ctx, &ctx->cQ1, vb) || dalloc(ctx, &ctx->cQ, vb) ||
+        dalloc(ctx, &ctx->cSQ, vb) || dalloc(ctx, &ctx->csmall, 7 * kMaxCoarse * kMaxCoarse * 8) ||
+        dalloc(ctx, &ctx->cflags, 4 * sizeof(int)) || dalloc(ctx, &ctx->cticket, 16)) {
+      ctx->ck_in = 0;
+      return fail(ctx, DDEL_ENOMEM, "coarse space allocation");
+    }
+    if (cudaMallocHost(&ctx->h_cflags, 4 * sizeof(int)) != cudaSuccess) {
+      ctx->ck_in = 0;
+      return fail(ctx, DDEL_ENOMEM, "coarse space allocation");
+    }
+    CK(cudaMemsetAsync(ctx->cticket, 0, 16, ctx->stream));
+  }
+  CK(cudaMemcpyAsync(ctx->cZ, Z, (size_t)k * n * 8,
+                     on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, ctx->stream));
+  if (!on_device) CK(cudaStreamSynchronize(ctx->stream));
   return DDEL_OK;
 }
 
@@ -1029,6 +1192,10 @@ int ddel_pcg(ddel_ctx* ctx, const double* g, double* x, double tol_abs, ddel_sta
   if (!ctx || !g || !x) return DDEL_EINVAL;
   const int prec = ctx->active_prec;
   if (!ctx->factored[prec]) return fail(ctx, DDEL_ESTATE, "factor first");
+  if (ctx->ck_in > 0 && ctx->coarse_prec != prec * 2) {
+    int rc = coarse_build(ctx, prec, false);
+    if (rc) return rc;
+  }
   set_tol_abs_kernel<<<1, 1, 0, ctx->stream>>>(ctx->st, tol_abs, ctx->opt.max_it);
   ctx->launches += 1;
   int it = 0, pst = 0;

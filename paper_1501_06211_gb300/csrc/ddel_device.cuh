@@ -145,6 +145,14 @@ __device__ __forceinline__ void elem_node_offset(int a, int& dx, int& dy, int& d
   dz = a >> 2;
 }
 
+// Interface input of a Schur apply at Gamma DOF g: x[g] plus, inside a PCG
+// with a coarse space, the coarse part Q cc of the preconditioned residual.
+__device__ __forceinline__ double gamma_input(const DevTables& t, const SchurIO& io, int64_t g) {
+  double v = io.x[g];
+  for (int i = 0; i < io.ck; ++i) v += io.cq[i * t.n_gamma + g] * io.ccoef[i];
+  return v;
+}
+
 // Alpha and beta of the Chronopoulos-Gear recurrence, from gamma = (r, u) of
 // the last update and delta = (S u, u) of the Schur apply just finished.
 __device__ __forceinline__ void cg_coefficients(PcgState* st, double delta) {

@@ -321,13 +321,11 @@ __global__ void __launch_bounds__(32) schur2d_kernel(DevTables t, const T* __res
     sc[i] = scale[(int64_t)(si.lo[0] + i / s) * t.ne[1] + si.lo[1] + i % s];
   for (int i = lane; i < 2 * nloc; i += 32) xloc[i] = T(0);
   __syncwarp();
-  const bool have_x = io.x || io.zvec;
+  const bool have_x = io.x != nullptr;
   if (have_x) {
-    const double beta = io.zvec ? *io.beta : 0.0;
     for (int r = lane; r < si.n_ring; r += 32) {
       const int g = t.ring_gidx[si.ring_off + r];
-      const double v = io.x ? io.x[g] : io.zvec[g] + beta * io.pvec[g];
-      xloc[t.ring_loc[si.ring_off + r]] = (T)v;
+      xloc[t.ring_loc[si.ring_off + r]] = (T)gamma_input(t, io, g);
     }
   }
   __syncwarp();
@@ -623,7 +621,7 @@ __global__ void __launch_bounds__(256) schur_form2d_kernel(DevTables t, const T*
   }
 }
 
-// y_ring = S_i x_ring for every subdomain (PCG form x = z + beta p when zvec).
+// y_ring = S_i x_ring for every subdomain.
 template <typename T, int NR>
 __global__ void __launch_bounds__(256) schur_explicit_kernel(DevTables t, const T* __restrict__ Sexp,
                                                              SchurIO io) {
@@ -635,13 +633,9 @@ __global__ void __launch_bounds__(256) schur_explicit_kernel(DevTables t, const 
   const SubInfo si = t.subs[sub];
   __shared__ T xr[NR];
   __shared__ T part[256];
-  const double beta = io.zvec ? *io.beta : 0.0;
   for (int j = tid; j < NR; j += 256) {
     T v = T(0);
-    if (j < si.n_ring) {
-      const int g = t.ring_gidx[si.ring_off + j];
-      v = (T)(io.x ? io.x[g] : io.zvec[g] + beta * io.pvec[g]);
-    }
+    if (j < si.n_ring) v = (T)gamma_input(t, io, t.ring_gidx[si.ring_off + j]);
     xr[j] = v;
   }
   __syncthreads();
@@ -710,7 +704,7 @@ __global__ void __launch_bounds__(256) schur_explicit_df_kernel(DevTables t, con
   __shared__ double part[256];
   for (int j = tid; j < NR; j += 256) {
     double v = 0.0;
-    if (j < si.n_ring) v = io.x[t.ring_gidx[si.ring_off + j]];
+    if (j < si.n_ring) v = gamma_input(t, io, t.ring_gidx[si.ring_off + j]);
     const float hi = (float)v;
     xr[j] = make_float2(hi, (float)(v - (double)hi));
     xd[j] = v;
@@ -780,18 +774,25 @@ __global__ void gamma_sum_kernel(DevTables t, const T* __restrict__ ring,
 // ============================================================ PCG
 // Face blocks: one warp per (face, component) block, z = W^-1 P W^-1 r with P
 // symmetric, read by columns (coalesced); cross points: one thread per DOF.
-// INIT: x = 0, r = g, p = s = 0.  Otherwise w_g = sum of the ring entries of
-// the owning subdomains, p = u + beta p, s = w + beta s, x += alpha p,
-// r -= alpha s.  Both: u = S~^-1 r, gamma = (r, u), rr = (r, r).
-template <typename T, bool INIT>
+// INIT: x = x0, r = g - S x0, p = s = 0 (x0 = 0 without a coarse space).
+// Otherwise w_g = sum of the ring entries of the owning subdomains,
+// p = u + beta p, s = w + beta s, x += alpha p, r -= alpha s.
+// Both: u = S~^-1 r, gamma = (r, u), rr = (r, r).
+// COARSE: u = S~^-1 r + Q cc with cc = E^-1 Q^T r (additive correction) or
+// cc = E^-1 (Q^T r - (S Q)^T S~^-1 r) (deflation, u = Q E^-1 Q^T r +
+// (I - Q E^-1 Q^T S) S~^-1 r).  The array u keeps the face-local part; cc
+// needs grid reductions, so it goes to PcgState and every reader of u adds
+// Q cc; gamma = (r, S~^-1 r) + (Q^T r)^T cc.
+template <typename T, bool INIT, bool COARSE>
 __global__ void __launch_bounds__(kRedThreads) pcg_cg_kernel(DevTables t, DevFields fld,
                                                              const double* __restrict__ gin,
                                                              const T* __restrict__ ring, double* x,
                                                              double* r, double* u, double* p,
-                                                             double* sv, PcgState* st) {
+                                                             double* sv, PcgState* st, CoarseDev cd) {
   if (st->done) return;
+  constexpr int KC = COARSE ? kMaxCoarse : 0, NV = 2 + 2 * KC;
   extern __shared__ double rw_all[];  // (blockDim/32) * max_blk_n
-  __shared__ double scratch[64];
+  __shared__ double scratch[NV * 32];
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   double* rw = rw_all + wib * t.max_blk_n;
   double alpha = 0.0, beta = 0.0;
@@ -799,25 +800,50 @@ __global__ void __launch_bounds__(kRedThreads) pcg_cg_kernel(DevTables t, DevFie
     alpha = st->alpha;
     beta = st->beta;
   }
-  double acc[2] = {0.0, 0.0};
+  const int kc = COARSE && cd.correct ? cd.k : 0;  // coarse correction dimension
+  const bool deflate = COARSE && cd.correct == 2;
+  const int kn = COARSE ? (INIT ? (cd.x0 ? cd.k : 0) : kc) : 0;  // columns in cc
+  double cc[KC > 0 ? KC : 1];  // INIT: x0 coefficients; else coarse part of the current u
+#pragma unroll
+  for (int i = 0; i < KC; ++i) cc[i] = i < kn ? (INIT ? st->c0[i] : st->cc[i]) : 0.0;
+  auto coarse = [&](const double* V, int64_t g) -> double {
+    double v = 0.0;
+#pragma unroll
+    for (int i = 0; i < KC; ++i)
+      if (i < kn) v += V[i * t.n_gamma + g] * cc[i];
+    return v;
+  };
+  double acc[NV];
+#pragma unroll
+  for (int i = 0; i < NV; ++i) acc[i] = 0.0;
   auto step = [&](int64_t g) -> double {
+    double rg;
     if (INIT) {
-      x[g] = 0.0;
       p[g] = 0.0;
       sv[g] = 0.0;
-      r[g] = gin[g];
-      return gin[g];
+      if (COARSE) {
+        x[g] = coarse(cd.Q, g);
+        rg = gin[g] - coarse(cd.SQ, g);
+      } else {
+        x[g] = 0.0;
+        rg = gin[g];
+      }
+    } else {
+      // S u at this DOF: the ring entries of its owners (fixed-width table,
+      // subdomain order, so the sum order is fixed)
+      const double w = ring_sum<T>(t, ring, g);
+      const double pg = u[g] + (COARSE ? coarse(cd.Q, g) : 0.0) + beta * p[g];
+      const double sg = w + beta * sv[g];
+      p[g] = pg;
+      sv[g] = sg;
+      x[g] += alpha * pg;
+      rg = r[g] - alpha * sg;
     }
-    // S u at this DOF: the ring entries of its owners (fixed-width table,
-    // subdomain order, so the sum order is fixed)
-    const double w = ring_sum<T>(t, ring, g);
-    const double pg = u[g] + beta * p[g];
-    const double sg = w + beta * sv[g];
-    p[g] = pg;
-    sv[g] = sg;
-    x[g] += alpha * pg;
-    const double rg = r[g] - alpha * sg;
     r[g] = rg;
+    acc[1] += rg * rg;
+#pragma unroll
+    for (int i = 0; i < KC; ++i)
+      if (i < kc) acc[2 + i] += cd.Q[i * t.n_gamma + g] * rg;
     return rg;
   };
   const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -827,7 +853,6 @@ __global__ void __launch_bounds__(kRedThreads) pcg_cg_kernel(DevTables t, DevFie
     const double* P = t.ptab + t.blk_poff[b];
     for (int i = lane; i < n; i += 32) {
       const double ri = step(off + i);
-      acc[1] += ri * ri;
       rw[i] = ri * fld.face_w[off + i];  // W^-1 r (face_w holds 1 / W_ii)
     }
     __syncwarp();
@@ -844,7 +869,12 @@ __global__ void __launch_bounds__(kRedThreads) pcg_cg_kernel(DevTables t, DevFie
       if (j < n) z0 += Pc[j * n] * rw[j];
       const double zi = z0 + z1;
       acc[0] += rw[i] * zi;  // r_i u_i = (W rw)_i (W^-1 zi)_i
-      u[off + i] = zi * fld.face_w[off + i];
+      const double ui = zi * fld.face_w[off + i];
+      u[off + i] = ui;
+      if (deflate)
+#pragma unroll
+        for (int q = 0; q < KC; ++q)
+          if (q < kc) acc[2 + KC + q] += cd.SQ[q * t.n_gamma + off + i] * ui;
     }
     __syncwarp();
   }
@@ -854,10 +884,27 @@ __global__ void __launch_bounds__(kRedThreads) pcg_cg_kernel(DevTables t, DevFie
     const double zi = ri * fld.cross_scale[g - t.n_face_dofs];
     u[g] = zi;
     acc[0] += ri * zi;
-    acc[1] += ri * ri;
+    if (deflate)
+#pragma unroll
+      for (int q = 0; q < KC; ++q)
+        if (q < kc) acc[2 + KC + q] += cd.SQ[q * t.n_gamma + g] * zi;
   }
-  if (grid_sum<2, kRedThreads>(acc, st->partials, &st->ticket[1], scratch) && threadIdx.x == 0) {
-    const double gamma = acc[0], rr = acc[1];
+  if (grid_sum<NV, kRedThreads>(acc, st->partials, &st->ticket[1], scratch) && threadIdx.x == 0) {
+    double gamma = acc[0];
+    const double rr = acc[1];
+    if (COARSE) {  // cc = E^-1 y, y = Q^T r (- (S Q)^T S~^-1 r); gamma += (Q^T r)^T cc
+      // (static indices only: a runtime index would move acc to local memory)
+#pragma unroll
+      for (int i = 0; i < KC; ++i) {
+        if (i >= kc) continue;
+        double c = 0.0;
+#pragma unroll
+        for (int j = 0; j < KC; ++j)
+          if (j < kc) c += cd.Einv[i * kMaxCoarse + j] * (acc[2 + j] - (deflate ? acc[2 + KC + j] : 0.0));
+        st->cc[i] = c;
+        gamma += acc[2 + i] * c;
+      }
+    }
     st->rr = rr;
     if (INIT) {
       st->it = 0;
@@ -1222,20 +1269,35 @@ static size_t update_smem(const DevTables& t) {
 }
 
 void launch_pcg_init(const DevTables& t, const DevFields& fld, const double* g, double* x, double* r,
-                     double* u, double* p, double* sv, PcgState* s, cudaStream_t st, int nblk) {
-  pcg_cg_kernel<double, true><<<nblk, kRedThreads, update_smem(t), st>>>(t, fld, g, nullptr, x, r, u,
-                                                                          p, sv, s);
+                     double* u, double* p, double* sv, PcgState* s, cudaStream_t st, int nblk,
+                     const CoarseDev& cd) {
+  if (cd.k > 0)  // initial guess x0 = Q c0 (and the coarse part of u0 when correcting)
+    pcg_cg_kernel<double, true, true><<<nblk, kRedThreads, update_smem(t), st>>>(
+        t, fld, g, nullptr, x, r, u, p, sv, s, cd);
+  else
+    pcg_cg_kernel<double, true, false><<<nblk, kRedThreads, update_smem(t), st>>>(
+        t, fld, g, nullptr, x, r, u, p, sv, s, cd);
 }
 
 void launch_pcg_update(const DevTables& t, const DevFields& fld, int precision, const void* ring,
                        double* x, double* r, double* u, double* p, double* sv, PcgState* s,
-                       cudaStream_t st, int nblk) {
-  if (precision == 0)
-    pcg_cg_kernel<double, false><<<nblk, kRedThreads, update_smem(t), st>>>(
-        t, fld, nullptr, (const double*)ring, x, r, u, p, sv, s);
-  else
-    pcg_cg_kernel<float, false><<<nblk, kRedThreads, update_smem(t), st>>>(
-        t, fld, nullptr, (const float*)ring, x, r, u, p, sv, s);
+                       cudaStream_t st, int nblk, const CoarseDev& cd) {
+  const bool c = cd.k > 0 && cd.correct;
+  if (precision == 0) {
+    if (c)
+      pcg_cg_kernel<double, false, true><<<nblk, kRedThreads, update_smem(t), st>>>(
+          t, fld, nullptr, (const double*)ring, x, r, u, p, sv, s, cd);
+    else
+      pcg_cg_kernel<double, false, false><<<nblk, kRedThreads, update_smem(t), st>>>(
+          t, fld, nullptr, (const double*)ring, x, r, u, p, sv, s, cd);
+  } else {
+    if (c)
+      pcg_cg_kernel<float, false, true><<<nblk, kRedThreads, update_smem(t), st>>>(
+          t, fld, nullptr, (const float*)ring, x, r, u, p, sv, s, cd);
+    else
+      pcg_cg_kernel<float, false, false><<<nblk, kRedThreads, update_smem(t), st>>>(
+          t, fld, nullptr, (const float*)ring, x, r, u, p, sv, s, cd);
+  }
 }
 
 void launch_precond(const DevTables& t, const DevFields& fld, const double* r, double* z,

@@ -311,7 +311,7 @@ __global__ void __launch_bounds__(kT3) schur3d_kernel(DevTables t, const T* __re
   const bool have_x = io.x != nullptr;
   if (have_x)
     for (int r = tid; r < si.n_ring; r += kT3)
-      xloc[t.ring_loc[si.ring_off + r]] = (T)io.x[t.ring_gidx[si.ring_off + r]];
+      xloc[t.ring_loc[si.ring_off + r]] = (T)gamma_input(t, io, t.ring_gidx[si.ring_off + r]);
   __syncthreads();
   const int nb = si.nb;
   const T* fb = factor + si.factor_off;

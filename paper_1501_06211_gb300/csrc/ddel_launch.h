@@ -40,11 +40,32 @@ struct DevTables {
 // PCG scalars kept on the device (read by the host only at check points).
 // Chronopoulos-Gear form of PCG: gamma = (r, u), delta = (S u, u) with
 // u = S~^-1 r; one Schur apply and one preconditioner apply per iteration.
+// Largest coarse space of the interface PCG.
+constexpr int kMaxCoarse = 8;
+
 struct PcgState {
   double gamma, gamma_prev, delta, alpha, alpha_prev, beta, tol2, rr;
   int it, max_it, done, status;
   unsigned ticket[4];
   double* partials;  // per-block partial sums (reduction scratch)
+  // Coarse space (when in use): u = S~^-1 r + Q cc with cc = E^-1 Q^T r of the
+  // current residual; c0 = coefficients of the initial guess x0 = Q c0.
+  double cc[kMaxCoarse];
+  double c0[kMaxCoarse];
+  int x0_used;
+};
+
+// Coarse space of the interface PCG: orthonormal Q (k columns of n_gamma,
+// column-major), S Q, E^-1 = (Q^T S Q)^-1 and G = (S Q)^T (S Q), k x k
+// row-major with leading dimension kMaxCoarse.
+struct CoarseDev {
+  const double* Q = nullptr;
+  const double* SQ = nullptr;
+  const double* Einv = nullptr;
+  const double* G = nullptr;
+  int k = 0;
+  int correct = 1;  // 0: initial guess only; 1: additive correction; 2: deflation
+  int x0 = 1;       // start from the Galerkin guess Q c0 (else from 0)
 };
 
 // Per-assembly fields.
@@ -59,15 +80,16 @@ struct DevFields {
 
 struct SchurIO {
   const double* x = nullptr;      // Gamma input (nullptr = 0)
-  const double* zvec = nullptr;   // PCG form: x = z + beta * p
-  const double* pvec = nullptr;
-  const double* beta = nullptr;
   const double* f = nullptr;      // global right-hand side for the interior (nullptr = 0)
   void* ring_out = nullptr;       // per ring slot output (T), nullptr = skip
   double* u_out = nullptr;        // global vector, interior DOFs written, nullptr = skip
   const int* done = nullptr;      // early exit flag
   PcgState* pcg = nullptr;        // PCG form: also reduce delta = (S u, u) -> alpha, beta
   int* err = nullptr;
+  // coarse part of the PCG input: x[g] + sum_i cq[i * n_gamma + g] * ccoef[i]
+  const double* cq = nullptr;
+  const double* ccoef = nullptr;
+  int ck = 0;
 };
 
 // Opt-in shared memory sizes for every kernel instantiation (call once).
@@ -109,11 +131,30 @@ void launch_gamma_sum(const DevTables& t, int precision, const void* ring, const
 // PCG kernels (Chronopoulos-Gear form).  init: x = 0, r = g, p = s = 0,
 // u = S~^-1 r, gamma.  update: w = sum(ring), p = u + beta p, s = w + beta s,
 // x += alpha p, r -= alpha s, u = S~^-1 r, gamma; convergence test.
+// With a coarse space (cd.k > 0) the preconditioner is S~^-1 r + Q E^-1 Q^T r
+// (u keeps the face-local part; the coarse part lives in PcgState::cc), and
+// init starts from x0 = Q c0 (PcgState::c0, set by launch_coarse_x0).
 void launch_pcg_init(const DevTables& t, const DevFields& fld, const double* g, double* x, double* r,
-                     double* u, double* p, double* sv, PcgState* s, cudaStream_t st, int nblk);
+                     double* u, double* p, double* sv, PcgState* s, cudaStream_t st, int nblk,
+                     const CoarseDev& cd = CoarseDev());
 void launch_pcg_update(const DevTables& t, const DevFields& fld, int precision, const void* ring,
                        double* x, double* r, double* u, double* p, double* sv, PcgState* s,
-                       cudaStream_t st, int nblk);
+                       cudaStream_t st, int nblk, const CoarseDev& cd = CoarseDev());
+// Coarse-space set-up (ddel_coarse.cu).  Gram matrix out = A^T B (k x k,
+// leading dimension kMaxCoarse) of k <= kMaxCoarse columns of length n.
+void launch_gram(const double* A, const double* B, int k, int64_t n, double* out, double* partials,
+                 unsigned* ticket, cudaStream_t st);
+// Cholesky QR step on the Gram matrix G of k columns: T (k x k) with Z T
+// orthonormal, columns whose pivot falls below drop * max pivot removed;
+// *k_out = number kept.
+void launch_cholqr_factor(const double* G, int k, double drop, double* T, int* k_out, cudaStream_t st);
+// out (k_out columns) = Z (k columns) T
+void launch_apply_T(const double* Z, const double* T, int k, const int* k_out, int64_t n, double* out,
+                    cudaStream_t st);
+// E = Q^T S Q (symmetrised) -> Einv, and flag = 1 when E is SPD (else 0).
+void launch_coarse_invert(const double* E, int k, double* Einv, int* flag, cudaStream_t st);
+// c0 = E^-1 Q^T g, or 0 when ||g - S Q c0|| > ||g|| (PcgState::x0_used).
+void launch_coarse_x0(const CoarseDev& cd, const double* g, int64_t n, PcgState* s, cudaStream_t st);
 void launch_precond(const DevTables& t, const DevFields& fld, const double* r, double* z,
                     cudaStream_t st);
 // Global element-by-element product / residual in FP64 (node-centric, no atomics).

@@ -20,6 +20,9 @@ c_int, c_double, c_void_p, c_uint32, c_int64 = (ctypes.c_int, ctypes.c_double, c
 DDEL_OK, DDEL_EINVAL, DDEL_ENOMEM, DDEL_ECUDA = 0, -1, -2, -3
 DDEL_ENOTSPD, DDEL_ENOCONV, DDEL_EBREAKDOWN, DDEL_ESTATE, DDEL_ETIMEOUT = -4, -5, -6, -7, -8
 DDEL_FP64, DDEL_FP32, DDEL_MIXED = 0, 1, 2
+DDEL_X0_ZERO, DDEL_X0_WARM = 0, 1
+DDEL_COARSE_X0, DDEL_COARSE_CORRECT, DDEL_COARSE_DEFLATE = 1, 2, 4
+DDEL_MAX_COARSE = 8
 
 
 class ddel_mesh(ctypes.Structure):
@@ -49,7 +52,8 @@ class ddel_stats(ctypes.Structure):
                 ("pcg_relres", c_double), ("bad_subdomain", c_int), ("fallback", c_int),
                 ("t_factor_ms", c_double),
                 ("t_condense_ms", c_double), ("t_pcg_ms", c_double), ("t_backsub_ms", c_double),
-                ("t_verify_ms", c_double), ("t_total_ms", c_double)]
+                ("t_verify_ms", c_double), ("t_total_ms", c_double), ("coarse_k", c_int),
+                ("x0_used", c_int)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -71,7 +75,22 @@ class ddel_kernel_info_t(ctypes.Structure):
 class ddel_topopt_state(ctypes.Structure):
     _fields_ = [("rho", c_void_p), ("volfrac", c_double), ("r_min", c_double), ("move", c_double),
                 ("iteration", c_int), ("compliance", c_double), ("volume", c_double),
-                ("change", c_double), ("lambda_", c_double), ("u", c_void_p), ("rho_phys", c_void_p)]
+                ("change", c_double), ("lambda_", c_double), ("u", c_void_p), ("rho_phys", c_void_p),
+                ("learner", c_void_p)]
+
+
+class ddel_learner_options(ctypes.Structure):
+    _fields_ = [("mode", c_int), ("coarse_flags", c_int), ("k_history", c_int), ("replay", c_int),
+                ("train_steps", c_int), ("min_samples", c_int), ("lr", c_double),
+                ("widths", c_int * 4), ("seed", ctypes.c_uint64)]
+
+
+class ddel_learner_info(ctypes.Structure):
+    _fields_ = [("samples", c_int), ("predictions", c_int), ("adam_steps", c_int64),
+                ("last_loss", c_double), ("t_train_ms", c_double), ("t_predict_ms", c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
 
 
 def _load():
@@ -107,9 +126,29 @@ def _load():
         "ddel_batch_solve": (c_int, [c_void_p, c_int, c_void_p, c_void_p]),
         "ddel_autotune": (c_int, [c_void_p, ctypes.c_char_p, c_void_p, c_void_p, c_void_p]),
         "ddel_topopt_step": (c_int, [c_void_p, P(ddel_topopt_state), P(ddel_stats)]),
+        "ddel_set_coarse": (c_int, [c_void_p, c_void_p, c_int, c_int, c_int]),
         "ddel_residual_norm_noalloc": (c_int, [c_int, c_int, c_int, c_int, c_void_p, c_void_p,
                                                c_void_p, c_void_p, c_void_p, c_void_p, c_void_p,
                                                c_void_p]),
+        "ddel_cnn_create": (c_int, [c_int, c_int, c_int, c_int, c_int, c_void_p, ctypes.c_uint64,
+                                    c_void_p, P(c_void_p)]),
+        "ddel_cnn_destroy": (None, [c_void_p]),
+        "ddel_cnn_last_error": (ctypes.c_char_p, [c_void_p]),
+        "ddel_cnn_num_params": (c_int64, [c_void_p]),
+        "ddel_cnn_get_params": (c_int, [c_void_p, c_void_p, c_int]),
+        "ddel_cnn_set_params": (c_int, [c_void_p, c_void_p, c_int]),
+        "ddel_cnn_forward": (c_int, [c_void_p, c_void_p, c_int, c_void_p]),
+        "ddel_cnn_loss_grad": (c_int, [c_void_p, c_void_p, c_void_p, c_int, P(c_double), c_void_p]),
+        "ddel_cnn_adam_step": (c_int, [c_void_p, c_double, c_double, c_double, c_double]),
+        "ddel_learner_default_options": (None, [P(ddel_learner_options)]),
+        "ddel_learner_create": (c_int, [c_void_p, P(ddel_learner_options), P(c_void_p)]),
+        "ddel_learner_destroy": (None, [c_void_p]),
+        "ddel_learner_predict": (c_int, [c_void_p, c_void_p]),
+        "ddel_learner_observe": (c_int, [c_void_p, c_void_p, c_void_p]),
+        "ddel_learner_get_info": (c_int, [c_void_p, P(ddel_learner_info)]),
+        "ddel_learner_features": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
+        "ddel_learner_grid": (c_int, [c_void_p, P(c_int), P(c_int)]),
+        "ddel_learner_network": (c_void_p, [c_void_p]),
         "ddel_plan_create": (c_int, [P(ddel_mesh), P(ddel_material), P(ddel_bc), c_double,
                                      P(c_void_p)]),
         "ddel_plan_destroy": (None, [c_void_p]),
@@ -229,6 +268,11 @@ def ddel_residual_norm(h, f, u):
     return code, rn.value, fn.value
 
 
+def ddel_set_coarse(h, Z, k, flags, on_device):
+    """Coarse space: Z holds k vectors over the Gamma DOFs (k x n_gamma, row-major)."""
+    return _lib.ddel_set_coarse(h, _ptr(Z), int(k), int(flags), int(on_device))
+
+
 def ddel_topopt_step(h, state):
     st = ddel_stats()
     code = _lib.ddel_topopt_step(h, ctypes.byref(state), ctypes.byref(st))
@@ -286,6 +330,124 @@ def ddel_fixed_mask(h, n_dof):
     out = np.zeros(n_dof, dtype=np.uint8)
     _check(_lib.ddel_fixed_mask(h, out.ctypes.data), h)
     return out.astype(bool)
+
+
+# ----------------------------------------------------------------- learned coarse space
+DDEL_LEARN_CNN, DDEL_LEARN_HISTORY, DDEL_LEARN_CNN_HISTORY = 0, 1, 2
+
+
+def ddel_cnn_create(in_ch, out_ch, H, W, max_batch, widths=None, seed=1, stream=None):
+    h = c_void_p()
+    w = (c_int * 4)(*widths) if widths is not None else None
+    code = _lib.ddel_cnn_create(in_ch, out_ch, H, W, max_batch, w, seed, stream, ctypes.byref(h))
+    return code, h
+
+
+ddel_cnn_destroy = _lib.ddel_cnn_destroy
+
+
+def ddel_cnn_num_params(net):
+    return int(_lib.ddel_cnn_num_params(net))
+
+
+def ddel_cnn_get_params(net, out, on_device):
+    return _lib.ddel_cnn_get_params(net, _ptr(out), int(on_device))
+
+
+def ddel_cnn_set_params(net, p, on_device):
+    return _lib.ddel_cnn_set_params(net, _ptr(p), int(on_device))
+
+
+def ddel_cnn_forward(net, x, n, y):
+    return _lib.ddel_cnn_forward(net, _ptr(x), int(n), _ptr(y))
+
+
+def ddel_cnn_loss_grad(net, x, target, n, grad=None):
+    loss = c_double()
+    code = _lib.ddel_cnn_loss_grad(net, _ptr(x), _ptr(target), int(n), ctypes.byref(loss), _ptr(grad))
+    return code, loss.value
+
+
+def ddel_cnn_adam_step(net, lr, beta1=0.9, beta2=0.999, eps=1e-8):
+    return _lib.ddel_cnn_adam_step(net, lr, beta1, beta2, eps)
+
+
+def ddel_learner_default_options():
+    o = ddel_learner_options()
+    _lib.ddel_learner_default_options(ctypes.byref(o))
+    return o
+
+
+def ddel_learner_create(ctx, opt=None):
+    h = c_void_p()
+    code = _lib.ddel_learner_create(ctx, ctypes.byref(opt) if opt is not None else None, ctypes.byref(h))
+    return code, h
+
+
+ddel_learner_destroy = _lib.ddel_learner_destroy
+
+
+def ddel_learner_predict(L, rho_f):
+    return _lib.ddel_learner_predict(L, _ptr(rho_f))
+
+
+def ddel_learner_observe(L, rho_f, u):
+    return _lib.ddel_learner_observe(L, _ptr(rho_f), _ptr(u))
+
+
+def ddel_learner_get_info(L):
+    info = ddel_learner_info()
+    code = _lib.ddel_learner_get_info(L, ctypes.byref(info))
+    return code, info
+
+
+def ddel_learner_features(L, rho_f, u, x, target):
+    return _lib.ddel_learner_features(L, _ptr(rho_f), _ptr(u), _ptr(x), _ptr(target))
+
+
+def ddel_learner_grid(L):
+    H, W = c_int(), c_int()
+    code = _lib.ddel_learner_grid(L, ctypes.byref(H), ctypes.byref(W))
+    return code, H.value, W.value
+
+
+def ddel_learner_network(L):
+    return _lib.ddel_learner_network(L)
+
+
+class Learner:
+    """Learned (or history) coarse space attached to a Solver; pass it to
+    Solver.topopt_state(..., learner=...)."""
+
+    def __init__(self, solver, **options):
+        self.opt = ddel_learner_default_options()
+        for k, v in options.items():
+            if k == "widths":
+                self.opt.widths = (c_int * 4)(*v)
+            else:
+                setattr(self.opt, k, v)
+        code, self.h = ddel_learner_create(solver.h, self.opt)
+        _check(code, solver.h)
+        self._solver = solver  # the context must outlive the learner
+
+    def info(self):
+        code, info = ddel_learner_get_info(self.h)
+        _check(code)
+        return info
+
+    def grid(self):
+        return ddel_learner_grid(self.h)[1:]
+
+    def close(self):
+        if self.h:
+            ddel_learner_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 # ----------------------------------------------------------------- BC marshalling
@@ -438,14 +600,26 @@ class Solver:
     def factor(self):
         _check(ddel_factor(self.h), self.h)
 
-    def topopt_state(self, rho, volfrac, r_min=1.5, move=0.2, u=None, rho_phys=None):
+    def set_coarse(self, Z, flags=DDEL_COARSE_X0 | DDEL_COARSE_CORRECT):
+        """Z: (k, n_gamma) torch CUDA tensor or NumPy array; None or k = 0 removes it."""
+        if Z is None:
+            _check(ddel_set_coarse(self.h, None, 0, 0, 0), self.h)
+            return
+        on_dev = hasattr(Z, "is_cuda") and Z.is_cuda
+        if not on_dev:
+            Z = np.ascontiguousarray(Z, dtype=np.float64)
+        self._coarse_ref = Z
+        _check(ddel_set_coarse(self.h, Z, Z.shape[0], flags, on_dev), self.h)
+
+    def topopt_state(self, rho, volfrac, r_min=1.5, move=0.2, u=None, rho_phys=None, learner=None):
         """State for ddel_topopt_step; rho is a CUDA tensor updated in place."""
         ts = ddel_topopt_state()
         ts.rho = _ptr(rho)
         ts.volfrac, ts.r_min, ts.move = volfrac, r_min, move
         ts.u = _ptr(u)
         ts.rho_phys = _ptr(rho_phys)
-        self._topo_refs = (rho, u, rho_phys)
+        ts.learner = learner.h.value if learner is not None else None
+        self._topo_refs = (rho, u, rho_phys, learner)
         return ts
 
     def topopt_step(self, ts):

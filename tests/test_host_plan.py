@@ -1,7 +1,7 @@
 """CPU tests of the C-ABI library: exports and the host set-up against the oracle.
 
 No compute call touches a GPU here: the library is loaded, every symbol that
-include/ddel.h declares is looked up, and the host-only plan (DOF
+include/*.h declares is looked up, and the host-only plan (DOF
 classification, interface ordering, face operators, element matrix, loads) is
 compared with the oracle's independent construction.
 """
@@ -24,7 +24,8 @@ def _lib():
 
 
 def _declared_functions():
-    text = open(os.path.join(ROOT, "include", "ddel.h")).read()
+    text = "".join(open(os.path.join(ROOT, "include", h)).read()
+                   for h in sorted(os.listdir(os.path.join(ROOT, "include"))) if h.endswith(".h"))
     text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
     return sorted(set(re.findall(r"\b(ddel_[a-z0-9_]+)\s*\(", text)))
 

@@ -62,6 +62,20 @@ def test_additive_correction_shifts_the_deflated_eigenvalues_by_one():
     assert np.allclose(ev, expect, rtol=1e-10)
 
 
+def test_deflation_moves_the_deflated_eigenvalues_to_one():
+    # P = I, Z = k eigenvectors of S: P_d S has eigenvalue 1 on span(Z) and
+    # keeps lambda on the S-invariant complement
+    n, k = 16, 3
+    S = spd(n, 6, cond=50)
+    lam, V = np.linalg.eigh(S)
+    cs = coarse.CoarseSpace(lambda v: S @ v, V[:, :k])
+    Pd = cs.deflated_preconditioner(lambda r: r)
+    M = np.stack([Pd(S[:, j]) for j in range(n)], axis=1)
+    ev = np.sort(np.linalg.eigvals(M).real)
+    expect = np.sort(np.concatenate([np.ones(k), lam[k:]]))
+    assert np.allclose(ev, expect, rtol=1e-10)
+
+
 def test_indefinite_coarse_matrix_falls_back_to_plain_pcg():
     A = np.diag([1.0, -1.0, 2.0])
     cs = coarse.CoarseSpace(lambda v: A @ v, np.eye(3)[:, :2])
@@ -110,7 +124,9 @@ def test_coarse_pcg_same_solution_and_fewer_iterations_with_history(small_dd):
         g_j = dds_j.condense(o["f"])
         x_j, _, _ = dd.pcg(dds_j.schur_apply, pre.apply, g_j, 1e-12, 5000)
         Zs.append(x_j)
-    x, it, hist, cs = coarse.coarse_pcg(dds.schur_apply, pre.apply, g, np.stack(Zs, axis=1), tol, 5000)
-    assert cs.spd and cs.k == 3
-    assert np.linalg.norm(x - x_ref) <= 1e-8 * np.linalg.norm(x_ref)
-    assert it < it_ref
+    for deflate in (False, True):
+        x, it, hist, cs = coarse.coarse_pcg(dds.schur_apply, pre.apply, g, np.stack(Zs, axis=1), tol,
+                                            5000, deflate=deflate)
+        assert cs.spd and cs.k == 3
+        assert np.linalg.norm(x - x_ref) <= 1e-8 * np.linalg.norm(x_ref)
+        assert it < it_ref
