@@ -54,6 +54,8 @@ struct ddel_ctx {
   PcgState* st = nullptr;
   PcgState* h_st = nullptr;
   double* partials = nullptr;
+  double* pcg_pd = nullptr;  // PCG partial sums: Schur kernel (delta), update kernel (2 parities)
+  double* pcg_pu = nullptr;
   unsigned* ticketK = nullptr;
   double* nrm = nullptr;
   double* h_nrm = nullptr;
@@ -177,16 +179,21 @@ int apply_prec(ddel_ctx* ctx, int prec, bool apply32) {
   return expl ? (apply32 ? 1 : prec) : prec;
 }
 
-void schur_dispatch(ddel_ctx* ctx, int prec, bool apply32, SchurIO& io, cudaStream_t s) {
+// Returns the number of blocks launched (one delta partial each in a PCG).
+int schur_dispatch(ddel_ctx* ctx, int prec, bool apply32, SchurIO& io, cudaStream_t s) {
   const bool expl = ctx->explicit_ok[prec];
   io.ring_out = ring_of(ctx, apply_prec(ctx, prec, apply32));
   const void* smat = apply32 ? (const void*)ctx->sexp32 : ctx->sexp[prec];
-  if (expl && prec == 0 && !apply32 && ctx->df_ok)
+  if (expl && prec == 0 && !apply32 && ctx->df_ok) {
     launch_schur_explicit_df(ctx->T, ctx->sexp_df, io, s);
-  else if (expl)
+    return 2 * ctx->T.n_sub;
+  }
+  if (expl) {
     launch_schur_explicit(ctx->T, apply32 ? 1 : prec, smat, io, s);
-  else
-    launch_schur(ctx->T, ctx->F, prec, ctx->factor[prec], io, s);
+    return 2 * ctx->T.n_sub;
+  }
+  launch_schur(ctx->T, ctx->F, prec, ctx->factor[prec], io, s);
+  return ctx->T.n_sub;
 }
 
 CoarseDev coarse_dev(ddel_ctx* ctx) {
@@ -214,12 +221,13 @@ void pcg_iteration(ddel_ctx* ctx, int prec, bool apply32) {
   io.pcg = ctx->st;
   if (cd.k > 0 && cd.correct) {
     io.cq = cd.Q;
-    io.ccoef = ctx->st->cc;
+    io.cEinv = cd.Einv;
     io.ck = cd.k;
+    io.cdeflate = cd.correct == 2;
   }
-  schur_dispatch(ctx, prec, apply32, io, s);
+  const int nd = schur_dispatch(ctx, prec, apply32, io, s);
   launch_pcg_update(ctx->T, ctx->F, apply_prec(ctx, prec, apply32), io.ring_out, ctx->x, ctx->r,
-                    ctx->z, ctx->p, ctx->sv, ctx->st, s, ctx->nblk, cd);
+                    ctx->z, ctx->p, ctx->sv, ctx->st, s, ctx->nblk, nd, cd);
 }
 
 // PCG initialisation (asynchronous) and, with use_graph, the CUDA graph of
@@ -563,6 +571,8 @@ int ddel_create(const ddel_mesh* mesh, const ddel_material* mat, const ddel_bc* 
         bad(dalloc(ctx, &ctx->sv, ng * 8)) ||
         bad(dalloc(ctx, &ctx->rho, S.n_elem * 8)) || bad(dalloc(ctx, &ctx->st, sizeof(PcgState))) ||
         bad(dalloc(ctx, &ctx->partials, (size_t)(4 * 152 * (2 + 2 * kMaxCoarse) + 2 * T.n_sub + 64) * 8)) ||
+        bad(dalloc(ctx, &ctx->pcg_pd, (size_t)(2 * T.n_sub + 64) * 8)) ||
+        bad(dalloc(ctx, &ctx->pcg_pu, (size_t)2 * kPcgRows * 2 * 152 * 8)) ||
         bad(dalloc(ctx, &ctx->ticketK, 16)) || bad(dalloc(ctx, &ctx->nrm, 16)) ||
         bad(dalloc(ctx, &ctx->err, 4 * sizeof(int))))
       goto fail_out;
@@ -571,8 +581,13 @@ int ddel_create(const ddel_mesh* mesh, const ddel_material* mat, const ddel_bc* 
         bad(cudaMallocHost(&ctx->h_nrm, 2 * sizeof(double))) ||
         bad(cudaMallocHost(&ctx->h_err, 4 * sizeof(int))))
       goto fail_out;
+    ctx->nblk = 2 * 152;
     PcgState st0{};
     st0.partials = ctx->partials;
+    st0.pd = ctx->pcg_pd;
+    st0.pu[0] = ctx->pcg_pu;
+    st0.pu[1] = ctx->pcg_pu + (size_t)kPcgRows * ctx->nblk;
+    st0.nu = ctx->nblk;
     if (bad(cudaMemcpy(ctx->st, &st0, sizeof(PcgState), cudaMemcpyHostToDevice)) ||
         bad(cudaMemset(ctx->ticketK, 0, 16)) || bad(cudaMemset(ctx->ring, 0, ring_bytes)) ||
         bad(cudaMemset(ctx->ring32, 0, ring_bytes)) ||

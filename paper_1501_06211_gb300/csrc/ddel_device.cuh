@@ -146,30 +146,75 @@ __device__ __forceinline__ void elem_node_offset(int a, int& dx, int& dy, int& d
 }
 
 // Interface input of a Schur apply at Gamma DOF g: x[g] plus, inside a PCG
-// with a coarse space, the coarse part Q cc of the preconditioned residual.
-__device__ __forceinline__ double gamma_input(const DevTables& t, const SchurIO& io, int64_t g) {
+// with a coarse space, the coarse part Q cc of the preconditioned residual
+// (cc in shared memory, from coarse_coefficients).
+__device__ __forceinline__ double gamma_input(const DevTables& t, const SchurIO& io, int64_t g,
+                                              const double* cc) {
   double v = io.x[g];
-  for (int i = 0; i < io.ck; ++i) v += io.cq[i * t.n_gamma + g] * io.ccoef[i];
+  for (int i = 0; i < io.ck; ++i) v += io.cq[i * t.n_gamma + g] * cc[i];
   return v;
 }
 
-// Alpha and beta of the Chronopoulos-Gear recurrence, from gamma = (r, u) of
-// the last update and delta = (S u, u) of the Schur apply just finished.
-__device__ __forceinline__ void cg_coefficients(PcgState* st, double delta) {
-  st->delta = delta;
-  const double gamma = st->gamma;
-  double beta = 0.0, den = delta;
-  if (st->it > 0) {
-    beta = gamma / st->gamma_prev;
-    den = delta - beta * gamma / st->alpha_prev;
+// Sum of src[0..n) by one warp in a fixed order (lane-strided, then the warp
+// tree); every lane returns the total, and every block that calls it on the
+// same data obtains the same bits.
+__device__ __forceinline__ double reduce_partials_warp(const double* __restrict__ src, int n) {
+  const int lane = threadIdx.x & 31;
+  double a = 0.0;
+  for (int b = lane; b < n; b += 32) a += __ldcg(src + b);
+  return warp_sum(a);
+}
+
+// Row index in the update partials of coarse sum v (v < k: Q^T r; else (S Q)^T u).
+__device__ __forceinline__ int coarse_row(int v, int k) { return v < k ? 2 + v : 2 + kMaxCoarse + (v - k); }
+
+// Coarse coefficients of the current preconditioned residual (Schur kernels of
+// a PCG with a coarse correction): cc = E^-1 (Q^T r_j - [deflate] (S Q)^T u_j)
+// from the partials of update iteration j.  All threads of the block call it.
+__device__ __forceinline__ void coarse_coefficients(const SchurIO& io, double* cc, double* tmp) {
+  const PcgState* st = io.pcg;
+  const int k = io.ck, nv = io.cdeflate ? 2 * k : k;
+  const double* P = st->pu[st->kS & 1];
+  const int nw = blockDim.x >> 5;
+  for (int v = threadIdx.x >> 5; v < nv; v += nw) {
+    const double s = reduce_partials_warp(P + (size_t)coarse_row(v, k) * st->nu, st->nu);
+    if ((threadIdx.x & 31) == 0) tmp[v] = s;
   }
-  if (!(den > 0.0) || !isfinite(den)) {
-    st->status = -6;  // breakdown
-    st->done = 1;
-    return;
+  __syncthreads();
+  if ((int)threadIdx.x < k) {
+    double c = 0.0;
+    for (int j = 0; j < k; ++j)
+      c += io.cEinv[threadIdx.x * kMaxCoarse + j] * (tmp[j] - (io.cdeflate ? tmp[k + j] : 0.0));
+    cc[threadIdx.x] = c;
   }
-  st->beta = beta;
-  st->alpha = gamma / den;
+  __syncthreads();
+}
+
+// Schur kernel of a PCG iteration: record the iteration index and, with a
+// coarse correction, the coarse coefficients.  All threads call it.
+__device__ __forceinline__ void schur_pcg_prologue(const SchurIO& io, double* cc, double* tmp) {
+  if (!io.pcg) return;
+  if (blockIdx.x == 0 && threadIdx.x == 0) io.pcg->kU = io.pcg->kS;
+  if (io.ck > 0) coarse_coefficients(io, cc, tmp);
+}
+
+// The block's share of delta = (S u, u): the values d of warps [0, NW) summed,
+// written by thread 0 to pd[blockIdx.x].  All threads call it.
+template <int NW>
+__device__ __forceinline__ void schur_pcg_epilogue(const SchurIO& io, double d, double* red) {
+  if (!io.pcg) return;
+  const int w = threadIdx.x >> 5;
+  if (w < NW) {
+    const double s = warp_sum(d);
+    if ((threadIdx.x & 31) == 0) red[w] = s;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double tot = 0.0;
+#pragma unroll
+    for (int i = 0; i < NW; ++i) tot += red[i];
+    io.pcg->pd[blockIdx.x] = tot;
+  }
 }
 
 }  // namespace ddel

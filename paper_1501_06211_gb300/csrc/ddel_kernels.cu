@@ -271,6 +271,8 @@ __global__ void __launch_bounds__(32) schur2d_kernel(DevTables t, const T* __res
                                                      const T* __restrict__ scale,
                                                      const T* __restrict__ factor, SchurIO io) {
   if (io.done && *io.done) return;
+  __shared__ double ccs[kMaxCoarse], ctmp[2 * kMaxCoarse];
+  schur_pcg_prologue(io, ccs, ctmp);
   constexpr int PC = BP * BP, PD = BP * (BP + 1) / 2, STAGE = PC + PD, R = BP / 32;
   const int sub = blockIdx.x, lane = threadIdx.x;
   const SubInfo si = t.subs[sub];
@@ -325,7 +327,7 @@ __global__ void __launch_bounds__(32) schur2d_kernel(DevTables t, const T* __res
   if (have_x) {
     for (int r = lane; r < si.n_ring; r += 32) {
       const int g = t.ring_gidx[si.ring_off + r];
-      xloc[t.ring_loc[si.ring_off + r]] = (T)gamma_input(t, io, g);
+      xloc[t.ring_loc[si.ring_off + r]] = (T)gamma_input(t, io, g, ccs);
     }
   }
   __syncwarp();
@@ -464,11 +466,8 @@ __global__ void __launch_bounds__(32) schur2d_kernel(DevTables t, const T* __res
       d[0] += (double)xloc[loc] * (double)y;
     }
   }
-  if (io.pcg) {  // delta = (S u, u) = sum over subdomains of u_i^T S_i u_i
-    __shared__ double red[32];
-    if (grid_sum<1, 32>(d, io.pcg->partials, &io.pcg->ticket[0], red) && lane == 0)
-      cg_coefficients(io.pcg, d[0]);
-  }
+  __shared__ double red[1];  // delta = (S u, u) = sum over subdomains of u_i^T S_i u_i
+  schur_pcg_epilogue<1>(io, d[0], red);
 }
 
 // ============================================================ explicit local Schur
@@ -633,9 +632,11 @@ __global__ void __launch_bounds__(256) schur_explicit_kernel(DevTables t, const 
   const SubInfo si = t.subs[sub];
   __shared__ T xr[NR];
   __shared__ T part[256];
+  __shared__ double ccs[kMaxCoarse], ctmp[2 * kMaxCoarse], red[RH / 32];
+  schur_pcg_prologue(io, ccs, ctmp);
   for (int j = tid; j < NR; j += 256) {
     T v = T(0);
-    if (j < si.n_ring) v = (T)gamma_input(t, io, t.ring_gidx[si.ring_off + j]);
+    if (j < si.n_ring) v = (T)gamma_input(t, io, t.ring_gidx[si.ring_off + j], ccs);
     xr[j] = v;
   }
   __syncthreads();
@@ -659,11 +660,7 @@ __global__ void __launch_bounds__(256) schur_explicit_kernel(DevTables t, const 
     reinterpret_cast<T*>(io.ring_out)[t.ring_dst[si.ring_off + row]] = y;
     d[0] = (double)xr[row] * (double)y;
   }
-  if (io.pcg) {  // delta = (S u, u) = sum over subdomains of u_i^T S_i u_i
-    __shared__ double red[32];
-    if (grid_sum<1, 256>(d, io.pcg->partials, &io.pcg->ticket[0], red) && tid == 0)
-      cg_coefficients(io.pcg, d[0]);
-  }
+  schur_pcg_epilogue<RH / 32>(io, d[0], red);  // delta: rows of this CTA
 }
 
 // ---- double-float form of the explicit apply --------------------------------
@@ -702,9 +699,11 @@ __global__ void __launch_bounds__(256) schur_explicit_df_kernel(DevTables t, con
   __shared__ float2 xr[NR];
   __shared__ double xd[NR];
   __shared__ double part[256];
+  __shared__ double ccs[kMaxCoarse], ctmp[2 * kMaxCoarse], red[RH / 32];
+  schur_pcg_prologue(io, ccs, ctmp);
   for (int j = tid; j < NR; j += 256) {
     double v = 0.0;
-    if (j < si.n_ring) v = gamma_input(t, io, t.ring_gidx[si.ring_off + j]);
+    if (j < si.n_ring) v = gamma_input(t, io, t.ring_gidx[si.ring_off + j], ccs);
     const float hi = (float)v;
     xr[j] = make_float2(hi, (float)(v - (double)hi));
     xd[j] = v;
@@ -735,11 +734,7 @@ __global__ void __launch_bounds__(256) schur_explicit_df_kernel(DevTables t, con
     reinterpret_cast<double*>(io.ring_out)[t.ring_dst[si.ring_off + row]] = y;
     d[0] = xd[row] * y;
   }
-  if (io.pcg) {
-    __shared__ double red[32];
-    if (grid_sum<1, 256>(d, io.pcg->partials, &io.pcg->ticket[0], red) && tid == 0)
-      cg_coefficients(io.pcg, d[0]);
-  }
+  schur_pcg_epilogue<RH / 32>(io, d[0], red);
 }
 
 // ============================================================ Gamma sums
@@ -775,37 +770,105 @@ __global__ void gamma_sum_kernel(DevTables t, const T* __restrict__ ring,
 // Face blocks: one warp per (face, component) block, z = W^-1 P W^-1 r with P
 // symmetric, read by columns (coalesced); cross points: one thread per DOF.
 // INIT: x = x0, r = g - S x0, p = s = 0 (x0 = 0 without a coarse space).
-// Otherwise w_g = sum of the ring entries of the owning subdomains,
+// Update j: every block first reduces the partials of the Schur apply
+// (delta_j) and of update j-1 (gamma_j, rr_j, coarse sums), tests
+// convergence, and forms alpha_j, beta_j itself (the same bits in every
+// block); then w_g = sum of the ring entries of the owning subdomains,
 // p = u + beta p, s = w + beta s, x += alpha p, r -= alpha s.
-// Both: u = S~^-1 r, gamma = (r, u), rr = (r, r).
+// Both: u = S~^-1 r and the block's partials of gamma = (r, u), rr = (r, r).
 // COARSE: u = S~^-1 r + Q cc with cc = E^-1 Q^T r (additive correction) or
 // cc = E^-1 (Q^T r - (S Q)^T S~^-1 r) (deflation, u = Q E^-1 Q^T r +
-// (I - Q E^-1 Q^T S) S~^-1 r).  The array u keeps the face-local part; cc
-// needs grid reductions, so it goes to PcgState and every reader of u adds
-// Q cc; gamma = (r, S~^-1 r) + (Q^T r)^T cc.
+// (I - Q E^-1 Q^T S) S~^-1 r).  The array u keeps the face-local part and every
+// reader of u adds Q cc; gamma = (r, S~^-1 r) + (Q^T r)^T cc.
 template <typename T, bool INIT, bool COARSE>
 __global__ void __launch_bounds__(kRedThreads) pcg_cg_kernel(DevTables t, DevFields fld,
                                                              const double* __restrict__ gin,
                                                              const T* __restrict__ ring, double* x,
                                                              double* r, double* u, double* p,
-                                                             double* sv, PcgState* st, CoarseDev cd) {
+                                                             double* sv, PcgState* st, CoarseDev cd, int nd) {
   if (st->done) return;
   constexpr int KC = COARSE ? kMaxCoarse : 0, NV = 2 + 2 * KC;
   extern __shared__ double rw_all[];  // (blockDim/32) * max_blk_n
   __shared__ double scratch[NV * 32];
+  __shared__ double sums[3 + 2 * kMaxCoarse];  // delta, gamma, rr, Q^T r, (S Q)^T u
+  __shared__ double sab[2 + kMaxCoarse];       // alpha, beta, cc
+  __shared__ int sflag;
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   double* rw = rw_all + wib * t.max_blk_n;
-  double alpha = 0.0, beta = 0.0;
-  if (!INIT) {
-    alpha = st->alpha;
-    beta = st->beta;
-  }
   const int kc = COARSE && cd.correct ? cd.k : 0;  // coarse correction dimension
   const bool deflate = COARSE && cd.correct == 2;
-  const int kn = COARSE ? (INIT ? (cd.x0 ? cd.k : 0) : kc) : 0;  // columns in cc
+  const int j = INIT ? -1 : st->kU;
+  double alpha = 0.0, beta = 0.0;
   double cc[KC > 0 ? KC : 1];  // INIT: x0 coefficients; else coarse part of the current u
+  int kn = 0;                  // columns in cc
+  if (!INIT) {
+    const double* U = st->pu[j & 1];
+    const int nu = st->nu, nvals = 3 + (deflate ? 2 * kc : kc);
+    for (int v = wib; v < nvals; v += blockDim.x >> 5) {
+      double sum;
+      if (v == 0) sum = reduce_partials_warp(st->pd, nd);
+      else if (v <= 2) sum = reduce_partials_warp(U + (size_t)(v - 1) * nu, nu);
+      else sum = reduce_partials_warp(U + (size_t)coarse_row(v - 3, kc) * nu, nu);
+      if (lane == 0) sums[v] = sum;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      // coarse coefficients of u_j first: gamma_j = (r, S~^-1 r) + (Q^T r)^T cc
+      double gamma = sums[1];
+      for (int i = 0; i < kc; ++i) {
+        double c = 0.0;
+        for (int q = 0; q < kc; ++q)
+          c += cd.Einv[i * kMaxCoarse + q] * (sums[3 + q] - (deflate ? sums[3 + kc + q] : 0.0));
+        sab[2 + i] = c;
+        gamma += sums[3 + i] * c;
+      }
+      const double delta = sums[0], rr = sums[2];
+      int status = 1;  // 1: iterate
+      double a = 0.0, b = 0.0;
+      if (rr <= st->tol2) {
+        status = 0;
+      } else if (!isfinite(rr) || !isfinite(gamma)) {
+        status = -6;
+      } else if (j >= st->max_it) {
+        status = -5;
+      } else {
+        double den = delta;  // p^T S p in the Chronopoulos-Gear recurrence
+        if (j > 0) {
+          b = gamma / st->gamma_s[(j - 1) & 1];
+          den = delta - b * gamma / st->alpha_s[(j - 1) & 1];
+        }
+        if (!(den > 0.0) || !isfinite(den)) status = -6;  // breakdown
+        else a = gamma / den;
+      }
+      sab[0] = a;
+      sab[1] = b;
+      sflag = status;
+      if (blockIdx.x == 0) {
+        st->rr = rr;
+        st->it = j;
+        if (status != 1) {
+          st->done = 1;
+          st->status = status;
+        } else {
+          st->alpha_s[j & 1] = a;
+          st->gamma_s[j & 1] = gamma;
+          st->kS = j + 1;
+        }
+      }
+    }
+    __syncthreads();
+    if (sflag != 1) return;
+    alpha = sab[0];
+    beta = sab[1];
+    kn = kc;
 #pragma unroll
-  for (int i = 0; i < KC; ++i) cc[i] = i < kn ? (INIT ? st->c0[i] : st->cc[i]) : 0.0;
+    for (int i = 0; i < KC; ++i) cc[i] = i < kc ? sab[2 + i] : 0.0;
+  } else {
+    kn = COARSE && cd.x0 ? cd.k : 0;
+#pragma unroll
+    for (int i = 0; i < KC; ++i) cc[i] = i < kn ? st->c0[i] : 0.0;
+    if (blockIdx.x == 0 && threadIdx.x == 0) st->kS = 0;
+  }
   auto coarse = [&](const double* V, int64_t g) -> double {
     double v = 0.0;
 #pragma unroll
@@ -860,21 +923,21 @@ __global__ void __launch_bounds__(kRedThreads) pcg_cg_kernel(DevTables t, DevFie
       // column i of the symmetric P, two independent accumulators
       const double* Pc = P + i;
       double z0 = 0.0, z1 = 0.0;
-      int j = 0;
+      int q = 0;
 #pragma unroll 4
-      for (; j + 1 < n; j += 2) {
-        z0 += Pc[j * n] * rw[j];
-        z1 += Pc[(j + 1) * n] * rw[j + 1];
+      for (; q + 1 < n; q += 2) {
+        z0 += Pc[q * n] * rw[q];
+        z1 += Pc[(q + 1) * n] * rw[q + 1];
       }
-      if (j < n) z0 += Pc[j * n] * rw[j];
+      if (q < n) z0 += Pc[q * n] * rw[q];
       const double zi = z0 + z1;
       acc[0] += rw[i] * zi;  // r_i u_i = (W rw)_i (W^-1 zi)_i
       const double ui = zi * fld.face_w[off + i];
       u[off + i] = ui;
       if (deflate)
 #pragma unroll
-        for (int q = 0; q < KC; ++q)
-          if (q < kc) acc[2 + KC + q] += cd.SQ[q * t.n_gamma + off + i] * ui;
+        for (int c = 0; c < KC; ++c)
+          if (c < kc) acc[2 + KC + c] += cd.SQ[c * t.n_gamma + off + i] * ui;
     }
     __syncwarp();
   }
@@ -886,45 +949,15 @@ __global__ void __launch_bounds__(kRedThreads) pcg_cg_kernel(DevTables t, DevFie
     acc[0] += ri * zi;
     if (deflate)
 #pragma unroll
-      for (int q = 0; q < KC; ++q)
-        if (q < kc) acc[2 + KC + q] += cd.SQ[q * t.n_gamma + g] * zi;
+      for (int c = 0; c < KC; ++c)
+        if (c < kc) acc[2 + KC + c] += cd.SQ[c * t.n_gamma + g] * zi;
   }
-  if (grid_sum<NV, kRedThreads>(acc, st->partials, &st->ticket[1], scratch) && threadIdx.x == 0) {
-    double gamma = acc[0];
-    const double rr = acc[1];
-    if (COARSE) {  // cc = E^-1 y, y = Q^T r (- (S Q)^T S~^-1 r); gamma += (Q^T r)^T cc
-      // (static indices only: a runtime index would move acc to local memory)
+  // this block's partials of iteration j + 1 (gamma, rr, coarse sums)
+  block_sum<NV, kRedThreads>(acc, scratch);
+  if (threadIdx.x == 0) {
+    double* Pn = st->pu[(j + 1) & 1];
 #pragma unroll
-      for (int i = 0; i < KC; ++i) {
-        if (i >= kc) continue;
-        double c = 0.0;
-#pragma unroll
-        for (int j = 0; j < KC; ++j)
-          if (j < kc) c += cd.Einv[i * kMaxCoarse + j] * (acc[2 + j] - (deflate ? acc[2 + KC + j] : 0.0));
-        st->cc[i] = c;
-        gamma += acc[2 + i] * c;
-      }
-    }
-    st->rr = rr;
-    if (INIT) {
-      st->it = 0;
-      st->beta = 0.0;
-    } else {
-      st->gamma_prev = st->gamma;
-      st->alpha_prev = st->alpha;
-      st->it += 1;
-    }
-    st->gamma = gamma;
-    if (rr <= st->tol2) {
-      st->done = 1;
-      st->status = 0;
-    } else if (!isfinite(rr) || !isfinite(gamma)) {
-      st->done = 1;
-      st->status = -6;
-    } else if (st->it >= st->max_it) {
-      st->done = 1;
-      st->status = -5;
-    }
+    for (int i = 0; i < NV; ++i) Pn[(size_t)i * st->nu + blockIdx.x] = acc[i];
   }
 }
 
@@ -1271,32 +1304,32 @@ static size_t update_smem(const DevTables& t) {
 void launch_pcg_init(const DevTables& t, const DevFields& fld, const double* g, double* x, double* r,
                      double* u, double* p, double* sv, PcgState* s, cudaStream_t st, int nblk,
                      const CoarseDev& cd) {
-  if (cd.k > 0)  // initial guess x0 = Q c0 (and the coarse part of u0 when correcting)
+  if (cd.k > 0)  // initial guess x0 = Q c0 (and the coarse sums of u0 when correcting)
     pcg_cg_kernel<double, true, true><<<nblk, kRedThreads, update_smem(t), st>>>(
-        t, fld, g, nullptr, x, r, u, p, sv, s, cd);
+        t, fld, g, nullptr, x, r, u, p, sv, s, cd, 0);
   else
     pcg_cg_kernel<double, true, false><<<nblk, kRedThreads, update_smem(t), st>>>(
-        t, fld, g, nullptr, x, r, u, p, sv, s, cd);
+        t, fld, g, nullptr, x, r, u, p, sv, s, cd, 0);
 }
 
 void launch_pcg_update(const DevTables& t, const DevFields& fld, int precision, const void* ring,
                        double* x, double* r, double* u, double* p, double* sv, PcgState* s,
-                       cudaStream_t st, int nblk, const CoarseDev& cd) {
+                       cudaStream_t st, int nblk, int nd, const CoarseDev& cd) {
   const bool c = cd.k > 0 && cd.correct;
   if (precision == 0) {
     if (c)
       pcg_cg_kernel<double, false, true><<<nblk, kRedThreads, update_smem(t), st>>>(
-          t, fld, nullptr, (const double*)ring, x, r, u, p, sv, s, cd);
+          t, fld, nullptr, (const double*)ring, x, r, u, p, sv, s, cd, nd);
     else
       pcg_cg_kernel<double, false, false><<<nblk, kRedThreads, update_smem(t), st>>>(
-          t, fld, nullptr, (const double*)ring, x, r, u, p, sv, s, cd);
+          t, fld, nullptr, (const double*)ring, x, r, u, p, sv, s, cd, nd);
   } else {
     if (c)
       pcg_cg_kernel<float, false, true><<<nblk, kRedThreads, update_smem(t), st>>>(
-          t, fld, nullptr, (const float*)ring, x, r, u, p, sv, s, cd);
+          t, fld, nullptr, (const float*)ring, x, r, u, p, sv, s, cd, nd);
     else
       pcg_cg_kernel<float, false, false><<<nblk, kRedThreads, update_smem(t), st>>>(
-          t, fld, nullptr, (const float*)ring, x, r, u, p, sv, s, cd);
+          t, fld, nullptr, (const float*)ring, x, r, u, p, sv, s, cd, nd);
   }
 }
 

@@ -37,21 +37,29 @@ struct DevTables {
   float* Ke32;
 };
 
-// PCG scalars kept on the device (read by the host only at check points).
+// PCG state kept on the device (read by the host only at check points).
 // Chronopoulos-Gear form of PCG: gamma = (r, u), delta = (S u, u) with
-// u = S~^-1 r; one Schur apply and one preconditioner apply per iteration.
-// Largest coarse space of the interface PCG.
+// u = S~^-1 r; one Schur apply and one update kernel per iteration.  Grid-wide
+// sums have no single-block tail: every block of a kernel writes its partial
+// sums, and every block of the next kernel reduces them itself in a fixed
+// order (all blocks obtain bitwise the same totals), so each kernel starts
+// with the scalars it needs.  Iteration j: the Schur kernel reads kS = j and
+// records kU = j; the update kernel reads kU, stores alpha_j, gamma_j in slot
+// j & 1 and sets kS = j + 1; update partials are double-buffered by parity.
 constexpr int kMaxCoarse = 8;
+constexpr int kPcgRows = 2 + 2 * kMaxCoarse;  // gamma, rr, Q^T r (k), (S Q)^T u (k)
 
 struct PcgState {
-  double gamma, gamma_prev, delta, alpha, alpha_prev, beta, tol2, rr;
+  double tol2, rr;
   int it, max_it, done, status;
+  int kS, kU;
+  double alpha_s[2], gamma_s[2];
+  double* pd;      // Schur kernel: one delta partial per block
+  double* pu[2];   // update kernel: kPcgRows x nu partials, by parity of j
+  int nu;          // update kernel blocks
   unsigned ticket[4];
-  double* partials;  // per-block partial sums (reduction scratch)
-  // Coarse space (when in use): u = S~^-1 r + Q cc with cc = E^-1 Q^T r of the
-  // current residual; c0 = coefficients of the initial guess x0 = Q c0.
-  double cc[kMaxCoarse];
-  double c0[kMaxCoarse];
+  double* partials;  // scratch of grid_sum-based one-off kernels
+  double c0[kMaxCoarse];  // coefficients of the initial guess x0 = Q c0
   int x0_used;
 };
 
@@ -86,10 +94,12 @@ struct SchurIO {
   const int* done = nullptr;      // early exit flag
   PcgState* pcg = nullptr;        // PCG form: also reduce delta = (S u, u) -> alpha, beta
   int* err = nullptr;
-  // coarse part of the PCG input: x[g] + sum_i cq[i * n_gamma + g] * ccoef[i]
+  // coarse part of the PCG input: x[g] + sum_i cq[i * n_gamma + g] * cc_i, with
+  // cc = cEinv (Q^T r - [cdeflate] (S Q)^T u) from the update partials
   const double* cq = nullptr;
-  const double* ccoef = nullptr;
+  const double* cEinv = nullptr;
   int ck = 0;
+  int cdeflate = 0;
 };
 
 // Opt-in shared memory sizes for every kernel instantiation (call once).
@@ -137,9 +147,10 @@ void launch_gamma_sum(const DevTables& t, int precision, const void* ring, const
 void launch_pcg_init(const DevTables& t, const DevFields& fld, const double* g, double* x, double* r,
                      double* u, double* p, double* sv, PcgState* s, cudaStream_t st, int nblk,
                      const CoarseDev& cd = CoarseDev());
+// nd: blocks of the Schur kernel that wrote the delta partials.
 void launch_pcg_update(const DevTables& t, const DevFields& fld, int precision, const void* ring,
                        double* x, double* r, double* u, double* p, double* sv, PcgState* s,
-                       cudaStream_t st, int nblk, const CoarseDev& cd = CoarseDev());
+                       cudaStream_t st, int nblk, int nd, const CoarseDev& cd = CoarseDev());
 // Coarse-space set-up (ddel_coarse.cu).  Gram matrix out = A^T B (k x k,
 // leading dimension kMaxCoarse) of k <= kMaxCoarse columns of length n.
 void launch_gram(const double* A, const double* B, int k, int64_t n, double* out, double* partials,
