@@ -235,6 +235,21 @@ typedef struct {
  * Synchronises the stream.  st (may be NULL) receives the solve statistics. */
 int ddel_topopt_step(ddel_ctx* ctx, ddel_topopt_state* state, ddel_stats* st);
 
+/* Checkpoint / resume of a topology-optimisation run (the paper has no
+ * counterpart).  save writes the design densities (state->rho, device), the
+ * state scalars (volfrac, r_min, move, iteration, compliance, volume, change,
+ * lambda) and the identity of the problem (mesh and material) to `path`,
+ * through a temporary file renamed into place, with a 64-bit FNV-1a checksum.
+ * load checks magic, version, problem identity and checksum, then copies the
+ * densities into state->rho (device, n_elem doubles, caller-owned) and sets the
+ * scalars; it leaves u, rho_phys and learner untouched.  A resumed run repeats
+ * the original bitwise (every reduction has a fixed order), except that a
+ * WARM or coarse-space initial guess restarts from nothing.
+ * Errors: EINVAL (bad arguments, unreadable or foreign file, checksum or
+ * identity mismatch), ECUDA.  Both synchronise the stream. */
+int ddel_checkpoint_save(const ddel_ctx* ctx, const ddel_topopt_state* state, const char* path);
+int ddel_checkpoint_load(ddel_ctx* ctx, ddel_topopt_state* state, const char* path);
+
 /* --- Batched independent problems ---------------------------------------------
  * Solves n independent, assembled problems (each its own context: any grid,
  * subdomain size, material) for their ddel_bc loads, concurrently: all

@@ -909,6 +909,112 @@ int ddel_topopt_step(ddel_ctx* ctx, ddel_topopt_state* ts, ddel_stats* stats) {
 }
 
 
+namespace {
+// Checkpoint file: header, densities, checksum (little-endian host layout).
+struct CkpHeader {
+  char magic[8];  // "DDELCKP1"
+  uint32_t version, dim;
+  int32_t nx, ny, nz, sub, plane_stress, pad;
+  double E, nu, simp_p, rho_min;
+  int64_t n_elem;
+  double volfrac, r_min, move, compliance, volume, change, lambda;
+  int64_t iteration;
+};
+constexpr char kCkpMagic[8] = {'D', 'D', 'E', 'L', 'C', 'K', 'P', '1'};
+
+uint64_t fnv1a(const unsigned char* p, size_t n, uint64_t h = 1469598103934665603ull) {
+  for (size_t i = 0; i < n; ++i) h = (h ^ p[i]) * 1099511628211ull;
+  return h;
+}
+
+CkpHeader ckp_identity(const ddel_ctx* ctx) {
+  CkpHeader h{};
+  std::memcpy(h.magic, kCkpMagic, 8);
+  h.version = 1;
+  h.dim = (uint32_t)ctx->mesh.dim;
+  h.nx = ctx->mesh.nx;
+  h.ny = ctx->mesh.ny;
+  h.nz = ctx->mesh.dim == 3 ? ctx->mesh.nz : 0;
+  h.sub = ctx->mesh.sub;
+  h.plane_stress = ctx->mat.plane_stress;
+  h.E = ctx->mat.E;
+  h.nu = ctx->mat.nu;
+  h.simp_p = ctx->mat.simp_p;
+  h.rho_min = ctx->mat.rho_min;
+  h.n_elem = ctx->S.n_elem;
+  return h;
+}
+}  // namespace
+
+int ddel_checkpoint_save(const ddel_ctx* cctx, const ddel_topopt_state* ts, const char* path) {
+  ddel_ctx* ctx = const_cast<ddel_ctx*>(cctx);
+  if (!ctx || !ts || !ts->rho || !path) return DDEL_EINVAL;
+  CkpHeader h = ckp_identity(ctx);
+  h.volfrac = ts->volfrac;
+  h.r_min = ts->r_min;
+  h.move = ts->move;
+  h.compliance = ts->compliance;
+  h.volume = ts->volume;
+  h.change = ts->change;
+  h.lambda = ts->lambda;
+  h.iteration = ts->iteration;
+  std::vector<double> rho(ctx->S.n_elem);
+  CK(cudaMemcpyAsync(rho.data(), ts->rho, rho.size() * 8, cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  uint64_t sum = fnv1a(reinterpret_cast<const unsigned char*>(&h), sizeof(h));
+  sum = fnv1a(reinterpret_cast<const unsigned char*>(rho.data()), rho.size() * 8, sum);
+  const std::string tmp = std::string(path) + ".tmp";
+  FILE* f = std::fopen(tmp.c_str(), "wb");
+  if (!f) return fail(ctx, DDEL_EINVAL, "checkpoint: cannot write " + tmp);
+  bool ok = std::fwrite(&h, sizeof(h), 1, f) == 1 && std::fwrite(rho.data(), 8, rho.size(), f) == rho.size() &&
+            std::fwrite(&sum, sizeof(sum), 1, f) == 1;
+  ok = (std::fclose(f) == 0) && ok;
+  if (!ok || std::rename(tmp.c_str(), path) != 0) {
+    std::remove(tmp.c_str());
+    return fail(ctx, DDEL_EINVAL, std::string("checkpoint: cannot write ") + path);
+  }
+  return DDEL_OK;
+}
+
+int ddel_checkpoint_load(ddel_ctx* ctx, ddel_topopt_state* ts, const char* path) {
+  if (!ctx || !ts || !ts->rho || !path) return DDEL_EINVAL;
+  FILE* f = std::fopen(path, "rb");
+  if (!f) return fail(ctx, DDEL_EINVAL, std::string("checkpoint: cannot read ") + path);
+  CkpHeader h{};
+  const CkpHeader want = ckp_identity(ctx);
+  std::vector<double> rho;
+  uint64_t sum = 0;
+  bool ok = std::fread(&h, sizeof(h), 1, f) == 1 && std::memcmp(h.magic, kCkpMagic, 8) == 0 && h.version == 1 &&
+            h.n_elem == want.n_elem;
+  if (ok) {
+    rho.resize(h.n_elem);
+    ok = std::fread(rho.data(), 8, rho.size(), f) == rho.size() && std::fread(&sum, sizeof(sum), 1, f) == 1;
+  }
+  ok = ok && std::fgetc(f) == EOF;
+  std::fclose(f);
+  if (!ok) return fail(ctx, DDEL_EINVAL, std::string("checkpoint: not a checkpoint of this size: ") + path);
+  uint64_t chk = fnv1a(reinterpret_cast<const unsigned char*>(&h), sizeof(h));
+  chk = fnv1a(reinterpret_cast<const unsigned char*>(rho.data()), rho.size() * 8, chk);
+  if (chk != sum) return fail(ctx, DDEL_EINVAL, "checkpoint: checksum mismatch");
+  if (h.dim != want.dim || h.nx != want.nx || h.ny != want.ny || h.nz != want.nz || h.sub != want.sub ||
+      h.plane_stress != want.plane_stress || h.E != want.E || h.nu != want.nu || h.simp_p != want.simp_p ||
+      h.rho_min != want.rho_min)
+    return fail(ctx, DDEL_EINVAL, "checkpoint: written for another mesh or material");
+  CK(cudaMemcpyAsync(ts->rho, rho.data(), rho.size() * 8, cudaMemcpyHostToDevice, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  ts->volfrac = h.volfrac;
+  ts->r_min = h.r_min;
+  ts->move = h.move;
+  ts->compliance = h.compliance;
+  ts->volume = h.volume;
+  ts->change = h.change;
+  ts->lambda = h.lambda;
+  ts->iteration = (int)h.iteration;
+  ctx->u_valid = false;  // a WARM start must not pick up an unrelated solution
+  return DDEL_OK;
+}
+
+
 int ddel_batch_solve(ddel_ctx* const* ctxs, int n, double* const* u, ddel_stats* stats) {
   if (!ctxs || n <= 0) return DDEL_EINVAL;
   for (int i = 0; i < n; ++i)

@@ -155,14 +155,42 @@ __device__ __forceinline__ double gamma_input(const DevTables& t, const SchurIO&
   return v;
 }
 
-// Sum of src[0..n) by one warp in a fixed order (lane-strided, then the warp
-// tree); every lane returns the total, and every block that calls it on the
-// same data obtains the same bits.
+// Sum of src[0..n) by one warp in a fixed order (lane-strided with four
+// independent accumulators, so that the loads overlap, then the warp tree);
+// every lane returns the total, and every block that calls it on the same
+// data obtains the same bits.
 __device__ __forceinline__ double reduce_partials_warp(const double* __restrict__ src, int n) {
   const int lane = threadIdx.x & 31;
-  double a = 0.0;
-  for (int b = lane; b < n; b += 32) a += __ldcg(src + b);
-  return warp_sum(a);
+  double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+  int b = lane;
+  for (; b + 96 < n; b += 128) {
+    a0 += __ldcg(src + b);
+    a1 += __ldcg(src + b + 32);
+    a2 += __ldcg(src + b + 64);
+    a3 += __ldcg(src + b + 96);
+  }
+  for (; b < n; b += 32) a0 += __ldcg(src + b);
+  return warp_sum((a0 + a1) + (a2 + a3));
+}
+
+// Fixed-order sum over the block of nv <= NV values per thread: a binary tree
+// in shared memory in which every addition is useful (FP64 is scarce on this
+// GPU: two DFMA per clock per SM).  red: NV * blockDim.x doubles, blockDim.x a
+// power of two.  On return (block synchronised) red[v * blockDim.x] holds sum v.
+template <int NV>
+__device__ __forceinline__ void block_tree_sum(const double (&a)[NV], int nv, double* red) {
+  const int tid = threadIdx.x, T = blockDim.x;
+#pragma unroll
+  for (int v = 0; v < NV; ++v)
+    if (v < nv) red[v * T + tid] = a[v];
+  __syncthreads();
+  for (int s = T / 2; s > 0; s >>= 1) {
+    if (tid < s)
+#pragma unroll
+      for (int v = 0; v < NV; ++v)
+        if (v < nv) red[v * T + tid] += red[v * T + tid + s];
+    __syncthreads();
+  }
 }
 
 // Row index in the update partials of coarse sum v (v < k: Q^T r; else (S Q)^T u).

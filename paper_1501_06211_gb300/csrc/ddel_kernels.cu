@@ -787,9 +787,9 @@ __global__ void __launch_bounds__(kRedThreads) pcg_cg_kernel(DevTables t, DevFie
                                                              double* r, double* u, double* p,
                                                              double* sv, PcgState* st, CoarseDev cd, int nd) {
   if (st->done) return;
-  constexpr int KC = COARSE ? kMaxCoarse : 0, NV = 2 + 2 * KC;
+  constexpr int KC = COARSE ? kMaxCoarse : 0, NV = 2 + 2 * KC, NP = 3 + 2 * KC;
   extern __shared__ double rw_all[];  // (blockDim/32) * max_blk_n
-  __shared__ double scratch[NV * 32];
+  __shared__ double red[NP * kRedThreads];     // tree sums (prologue NP values, epilogue NV)
   __shared__ double sums[3 + 2 * kMaxCoarse];  // delta, gamma, rr, Q^T r, (S Q)^T u
   __shared__ double sab[2 + kMaxCoarse];       // alpha, beta, cc
   __shared__ int sflag;
@@ -802,15 +802,32 @@ __global__ void __launch_bounds__(kRedThreads) pcg_cg_kernel(DevTables t, DevFie
   double cc[KC > 0 ? KC : 1];  // INIT: x0 coefficients; else coarse part of the current u
   int kn = 0;                  // columns in cc
   if (!INIT) {
+    // scalars of thread 0 loaded first, so that their latency overlaps the sums
+    double tol2 = 0.0, gprev = 1.0, aprev = 1.0;
+    int max_it = 0;
+    if (threadIdx.x == 0) {
+      tol2 = st->tol2;
+      max_it = st->max_it;
+      if (j > 0) {
+        gprev = st->gamma_s[(j - 1) & 1];
+        aprev = st->alpha_s[(j - 1) & 1];
+      }
+    }
+    // every thread loads its strided share of all partial vectors at once
+    // (independent loads in flight), then one tree sum per value
     const double* U = st->pu[j & 1];
     const int nu = st->nu, nvals = 3 + (deflate ? 2 * kc : kc);
-    for (int v = wib; v < nvals; v += blockDim.x >> 5) {
-      double sum;
-      if (v == 0) sum = reduce_partials_warp(st->pd, nd);
-      else if (v <= 2) sum = reduce_partials_warp(U + (size_t)(v - 1) * nu, nu);
-      else sum = reduce_partials_warp(U + (size_t)coarse_row(v - 3, kc) * nu, nu);
-      if (lane == 0) sums[v] = sum;
+    double a[NP];
+#pragma unroll
+    for (int v = 0; v < NP; ++v) {
+      a[v] = 0.0;
+      if (v >= nvals) continue;
+      const double* src = v == 0 ? st->pd : U + (size_t)(v <= 2 ? v - 1 : coarse_row(v - 3, kc)) * nu;
+      const int n = v == 0 ? nd : nu;
+      for (int b = threadIdx.x; b < n; b += kRedThreads) a[v] += __ldcg(src + b);
     }
+    block_tree_sum<NP>(a, nvals, red);
+    if (threadIdx.x < nvals) sums[threadIdx.x] = red[threadIdx.x * kRedThreads];
     __syncthreads();
     if (threadIdx.x == 0) {
       // coarse coefficients of u_j first: gamma_j = (r, S~^-1 r) + (Q^T r)^T cc
@@ -825,17 +842,17 @@ __global__ void __launch_bounds__(kRedThreads) pcg_cg_kernel(DevTables t, DevFie
       const double delta = sums[0], rr = sums[2];
       int status = 1;  // 1: iterate
       double a = 0.0, b = 0.0;
-      if (rr <= st->tol2) {
+      if (rr <= tol2) {
         status = 0;
       } else if (!isfinite(rr) || !isfinite(gamma)) {
         status = -6;
-      } else if (j >= st->max_it) {
+      } else if (j >= max_it) {
         status = -5;
       } else {
         double den = delta;  // p^T S p in the Chronopoulos-Gear recurrence
         if (j > 0) {
-          b = gamma / st->gamma_s[(j - 1) & 1];
-          den = delta - b * gamma / st->alpha_s[(j - 1) & 1];
+          b = gamma / gprev;
+          den = delta - b * gamma / aprev;
         }
         if (!(den > 0.0) || !isfinite(den)) status = -6;  // breakdown
         else a = gamma / den;
@@ -953,12 +970,8 @@ __global__ void __launch_bounds__(kRedThreads) pcg_cg_kernel(DevTables t, DevFie
         if (c < kc) acc[2 + KC + c] += cd.SQ[c * t.n_gamma + g] * zi;
   }
   // this block's partials of iteration j + 1 (gamma, rr, coarse sums)
-  block_sum<NV, kRedThreads>(acc, scratch);
-  if (threadIdx.x == 0) {
-    double* Pn = st->pu[(j + 1) & 1];
-#pragma unroll
-    for (int i = 0; i < NV; ++i) Pn[(size_t)i * st->nu + blockIdx.x] = acc[i];
-  }
+  block_tree_sum<NV>(acc, NV, red);
+  if (threadIdx.x < NV) st->pu[(j + 1) & 1][(size_t)threadIdx.x * st->nu + blockIdx.x] = red[threadIdx.x * kRedThreads];
 }
 
 __global__ void precond_kernel(DevTables t, DevFields fld, const double* __restrict__ r,

@@ -127,6 +127,8 @@ def _load():
         "ddel_autotune": (c_int, [c_void_p, ctypes.c_char_p, c_void_p, c_void_p, c_void_p]),
         "ddel_topopt_step": (c_int, [c_void_p, P(ddel_topopt_state), P(ddel_stats)]),
         "ddel_set_coarse": (c_int, [c_void_p, c_void_p, c_int, c_int, c_int]),
+        "ddel_checkpoint_save": (c_int, [c_void_p, P(ddel_topopt_state), ctypes.c_char_p]),
+        "ddel_checkpoint_load": (c_int, [c_void_p, P(ddel_topopt_state), ctypes.c_char_p]),
         "ddel_residual_norm_noalloc": (c_int, [c_int, c_int, c_int, c_int, c_void_p, c_void_p,
                                                c_void_p, c_void_p, c_void_p, c_void_p, c_void_p,
                                                c_void_p]),
@@ -271,6 +273,14 @@ def ddel_residual_norm(h, f, u):
 def ddel_set_coarse(h, Z, k, flags, on_device):
     """Coarse space: Z holds k vectors over the Gamma DOFs (k x n_gamma, row-major)."""
     return _lib.ddel_set_coarse(h, _ptr(Z), int(k), int(flags), int(on_device))
+
+
+def ddel_checkpoint_save(h, state, path):
+    return _lib.ddel_checkpoint_save(h, ctypes.byref(state), os.fsencode(path))
+
+
+def ddel_checkpoint_load(h, state, path):
+    return _lib.ddel_checkpoint_load(h, ctypes.byref(state), os.fsencode(path))
 
 
 def ddel_topopt_step(h, state):
@@ -621,6 +631,12 @@ class Solver:
         ts.learner = learner.h.value if learner is not None else None
         self._topo_refs = (rho, u, rho_phys, learner)
         return ts
+
+    def checkpoint_save(self, ts, path):
+        _check(ddel_checkpoint_save(self.h, ts, path), self.h)
+
+    def checkpoint_load(self, ts, path):
+        _check(ddel_checkpoint_load(self.h, ts, path), self.h)
 
     def topopt_step(self, ts):
         code, st = ddel_topopt_step(self.h, ts)
