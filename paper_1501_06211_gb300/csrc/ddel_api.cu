@@ -553,6 +553,10 @@ int ddel_create(const ddel_mesh* mesh, const ddel_material* mat, const ddel_bc* 
         bad(upload(ctx, S.hdiag, &T.hdiag)) ||
         bad(upload(ctx, S.Ke, &T.Ke64)) || bad(upload(ctx, ke32, &T.Ke32)))
       goto fail_out;
+    // face preconditioner blocks also as FP32 (hi, lo) pairs (see pcg_cg_kernel)
+    if (bad(dalloc(ctx, &T.ptab_df, S.ptab.size() * sizeof(float2)))) goto fail_out;
+    if (!S.ptab.empty()) launch_split_df(T.ptab, T.ptab_df, (int64_t)S.ptab.size(), nullptr);
+    if (bad(cudaDeviceSynchronize()) || bad(cudaGetLastError())) goto fail_out;
     const int64_t ng = T.n_gamma, nd = S.n_dof;
     // owner-major ring (ng x max_owners entries of up to 8 bytes), zero padded
     const size_t ring_bytes = (size_t)(ng * S.max_owners + 4) * 8;

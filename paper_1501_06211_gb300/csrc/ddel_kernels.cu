@@ -788,13 +788,14 @@ __global__ void __launch_bounds__(kRedThreads) pcg_cg_kernel(DevTables t, DevFie
                                                              double* sv, PcgState* st, CoarseDev cd, int nd) {
   if (st->done) return;
   constexpr int KC = COARSE ? kMaxCoarse : 0, NV = 2 + 2 * KC, NP = 3 + 2 * KC;
-  extern __shared__ double rw_all[];  // (blockDim/32) * max_blk_n
+  extern __shared__ double rw_all[];  // (blockDim/32) * max_blk_n doubles, then as many float2
   __shared__ double red[NP * kRedThreads];     // tree sums (prologue NP values, epilogue NV)
   __shared__ double sums[3 + 2 * kMaxCoarse];  // delta, gamma, rr, Q^T r, (S Q)^T u
   __shared__ double sab[2 + kMaxCoarse];       // alpha, beta, cc
   __shared__ int sflag;
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   double* rw = rw_all + wib * t.max_blk_n;
+  float2* rwf = reinterpret_cast<float2*>(rw_all + (blockDim.x >> 5) * t.max_blk_n) + wib * t.max_blk_n;
   const int kc = COARSE && cd.correct ? cd.k : 0;  // coarse correction dimension
   const bool deflate = COARSE && cd.correct == 2;
   const int j = INIT ? -1 : st->kU;
@@ -930,24 +931,28 @@ __global__ void __launch_bounds__(kRedThreads) pcg_cg_kernel(DevTables t, DevFie
   const int nw = (gridDim.x * blockDim.x) >> 5;
   for (int b = gw; b < t.n_blocks; b += nw) {
     const int off = t.blk_off[b], n = t.blk_n[b];
-    const double* P = t.ptab + t.blk_poff[b];
     for (int i = lane; i < n; i += 32) {
       const double ri = step(off + i);
-      rw[i] = ri * fld.face_w[off + i];  // W^-1 r (face_w holds 1 / W_ii)
+      const double v = ri * fld.face_w[off + i];  // W^-1 r (face_w holds 1 / W_ii)
+      rw[i] = v;
+      const float hi = (float)v;
+      rwf[i] = make_float2(hi, (float)(v - (double)hi));
     }
     __syncwarp();
     for (int i = lane; i < n; i += 32) {
-      // column i of the symmetric P, two independent accumulators
-      const double* Pc = P + i;
-      double z0 = 0.0, z1 = 0.0;
-      int q = 0;
+      // column i of the symmetric P in double-float arithmetic on the FP32
+      // pipes (about 48 significant bits; this GPU issues 2 DFMA per clock per
+      // SM), the same error-free transformations as the explicit Schur apply
+      const float2* Pc = t.ptab_df + t.blk_poff[b] + i;
+      float hi = 0.f, lo = 0.f;
 #pragma unroll 4
-      for (; q + 1 < n; q += 2) {
-        z0 += Pc[q * n] * rw[q];
-        z1 += Pc[(q + 1) * n] * rw[q + 1];
+      for (int q = 0; q < n; ++q) {
+        const float2 s = Pc[q * n], x = rwf[q];
+        const float p = __fmul_rn(s.x, x.x);
+        lo = __fadd_rn(lo, __fadd_rn(__fmaf_rn(s.x, x.x, -p), __fmaf_rn(s.x, x.y, __fmul_rn(s.y, x.x))));
+        df_add(hi, lo, p);
       }
-      if (q < n) z0 += Pc[q * n] * rw[q];
-      const double zi = z0 + z1;
+      const double zi = (double)hi + (double)lo;
       acc[0] += rw[i] * zi;  // r_i u_i = (W rw)_i (W^-1 zi)_i
       const double ui = zi * fld.face_w[off + i];
       u[off + i] = ui;
@@ -1311,7 +1316,7 @@ void launch_gamma_sum(const DevTables& t, int precision, const void* ring, const
 }
 
 static size_t update_smem(const DevTables& t) {
-  return (size_t)(kRedThreads / 32) * t.max_blk_n * sizeof(double);
+  return (size_t)(kRedThreads / 32) * t.max_blk_n * (sizeof(double) + sizeof(float2));
 }
 
 void launch_pcg_init(const DevTables& t, const DevFields& fld, const double* g, double* x, double* r,

@@ -33,6 +33,7 @@ struct DevTables {
   double* blk_hmean;
   double* hdiag;  // n_face_dofs: diag(H_f)
   double* ptab;
+  float2* ptab_df;  // ptab as FP32 (hi, lo) pairs for the double-float preconditioner product
   double* Ke64;
   float* Ke32;
 };
