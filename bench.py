@@ -8,12 +8,16 @@ p = 3, E = 1, nu = 0.3.  A step assembles the densities, factorises every
 subdomain, condenses, runs interface PCG, back-substitutes and verifies
 ||f - K u|| / ||f|| <= 1e-8 in FP64.
 
-`value` is the mixed-precision form (FP32 subdomain factors and Schur
-applies, FP64 Krylov vectors, dot products and refinement residual); the
-plain FP64 form is timed beside it.  Inputs are resident in HBM when the
-timed region starts; L2 is flushed between steps.  `e2e` repeats the step
-through the C ABI with host buffers (host->device copies of densities and
-loads, device->host copy of the displacement inside the timed region).
+`value` is the faster of the two forms that reach the tolerance: plain FP64
+(local Schur complements applied in double-float arithmetic, FP64 Krylov
+vectors) and mixed precision (FP32 subdomain factors and Schur applies, FP64
+refinement).  Inputs are resident in HBM when the timed region starts; L2 is
+flushed between steps.  `e2e` repeats the step through the C ABI with host
+buffers (host->device copies of densities and loads, device->host copy of the
+displacement inside the timed region).  `learned` compares, on the 256x128
+MBB topology-optimisation workload, the time per Picard solve of plain PCG
+with PCG whose coarse space comes from the last Picard solutions and the
+online-trained U-Net (training time included).
 
 Multi-GPU (torchrun): every rank solves its own independent instance (weak
 scaling, no collective on the data path); the step time is the max over ranks
@@ -246,9 +250,21 @@ def main():
     h2d = rho_h.nbytes + f_h.nbytes
     d2h = u_h.nbytes
 
-    # dominant kernel: the batched local Schur apply of the mixed-precision
-    # form (one launch per PCG iteration), timed alone with CUDA events
+    # dominant kernel: the batched local Schur apply (one launch per PCG
+    # iteration), timed alone with CUDA events; and the whole PCG iteration
+    # (Schur apply + update kernel) from the timed solves themselves
     roof = kernel_roofline(ddel, sb, stream, torch)
+    st_b = st32 if best32 else st64
+    it_us = [1e3 * st.t_pcg_ms / st.iters for st in st_b if st.iters > 0]
+    info_b = ddel.ddel_kernel_info(sb.h)
+    it_bytes = info_b["schur_apply_bytes"] + sb.n_gamma * 8 * 16  # + Krylov vectors, ring sums
+    if it_us:
+        us = sum(it_us) / len(it_us)
+        roof["pcg_iteration"] = {"us": us, "algorithmic_bytes": it_bytes,
+                                 "achieved_gbs": it_bytes / (us * 1e-6) / 1e9,
+                                 "frac": it_bytes / (us * 1e-6) / 1e9 / roof["peak"] if roof["unit"] == "GB/s" else None,
+                                 "source": "t_pcg_ms / iterations of the timed solves"}
+    learned = learned_vs_plain(ddel, torch, workloads, stream) if world == 1 else None
     ms_best = ms32 if best32 else ms64
     out = {
         "metric": METRIC, "value": ms_best / world, "unit": "ms", "n_gpus": world,
@@ -267,6 +283,8 @@ def main():
         "roofline": roof,
         "gpu_launches": (launches32 if best32 else launches64) * args.steps,
     }
+    if learned is not None:
+        out["learned"] = learned
     if clk is not None:
         out["clocks"] = clk
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -277,9 +295,56 @@ def main():
         dist.destroy_process_group()
 
 
+def learned_vs_plain(ddel, torch, workloads, stream, steps=16, skip=4):
+    """Per-solve time of topology steps on the 256x128 MBB beam (V = 0.4,
+    r_min = 1.5): plain PCG against coarse spaces from the last Picard
+    solutions (HISTORY, k = 8) and from those plus the online U-Net
+    (CNN_HISTORY, 4 + 4 vectors, 5 Adam steps per solve).  The first `skip`
+    steps warm up; time per step is the device time of the whole Picard step
+    (filter, assembly, factorisation, coarse set-up, solve, training, OC)."""
+    cfg = workloads.config("c4")
+    ne = int(cfg["ne"][0] * cfg["ne"][1])
+    res = {"workload": "MBB 256x128, 128 subdomains of 16x16, V=0.4, p=3, r_min=1.5, tol 1e-8",
+           "steps": steps - skip}
+    for name, lopt in (("plain", None),
+                       ("history8", dict(mode=ddel.DDEL_LEARN_HISTORY, k_history=8)),
+                       ("cnn+history4", dict(mode=ddel.DDEL_LEARN_CNN_HISTORY, k_history=4, train_steps=5))):
+        s = ddel.Solver(cfg, stream=stream.cuda_stream, tol=1e-8, max_it=20000)
+        L = ddel.Learner(s, **lopt) if lopt else None
+        rho = torch.full((ne,), cfg["v_frac"], dtype=torch.float64, device="cuda")
+        ts = s.topopt_state(rho, cfg["v_frac"], r_min=1.5, move=0.2, learner=L)
+        ms, its = [], []
+        for k in range(steps):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            st = s.topopt_step(ts)
+            e1.record(stream)
+            e1.synchronize()
+            if k >= skip:
+                ms.append(e0.elapsed_time(e1))
+                its.append(st.iters)
+        res[name] = {"ms_per_step": sum(ms) / len(ms), "iters_per_solve": sum(its) / len(its),
+                     "compliance": ts.compliance}
+        if L is not None:
+            res[name]["train_ms"] = L.info().t_train_ms
+            L.close()
+        s.close()
+    for name in ("history8", "cnn+history4"):
+        res[name]["speedup_vs_plain"] = res["plain"]["ms_per_step"] / res[name]["ms_per_step"]
+        res[name]["iteration_ratio"] = res[name]["iters_per_solve"] / res["plain"]["iters_per_solve"]
+    return res
+
+
 def launches_per_step(s, st):
     from paper_1501_06211_gb300 import ddel
     return ddel.ddel_kernel_info(s.h)["launches_since_assemble"]
+
+
+# DRAM bytes (read + write) of one launch of schur_explicit_df_kernel<128> on
+# this workload, from one `ncu --set full --clock-control none` capture of the
+# kernel (cold L2): 67.909888 MB read + 0.245504 MB written.
+DF_C1_TRAFFIC = 67909888 + 245504
 
 
 def kernel_roofline(ddel, s, stream, torch):
@@ -312,9 +377,12 @@ def kernel_roofline(ddel, s, stream, torch):
         # FP64 operator applied in FP32-pair arithmetic: the matrix streams once
         # per apply (8 bytes per entry), so the bound is memory bandwidth
         return {"bound": "hbm", "kernel": info["schur_apply_kernel"] + " + gamma_sum",
-                "achieved": gbs, "peak": hbm, "unit": "GB/s", "frac": gbs / hbm, "traffic": None,
-                "peak_source": src, "launch_ms": avg_ms, "algorithmic_bytes": bytes_,
-                "note": "S_i (67 MB) stays L2-resident between PCG iterations"}
+                "achieved": gbs, "peak": hbm, "unit": "GB/s", "frac": gbs / hbm,
+                "traffic": DF_C1_TRAFFIC, "peak_source": src, "launch_ms": avg_ms,
+                "algorithmic_bytes": bytes_,
+                "note": ("launch_ms: 200 applies (Schur kernel + gamma_sum) timed with CUDA events "
+                         "after the timed steps; traffic: one ncu capture, cold L2 "
+                         "(in the PCG loop S_i, 63 MB as FP32 pairs, stays L2-resident)")}
     if info["precision"] == 0:
         # FP64 products: GB300 issues 2 DFMA per clock per SM (1.26 TFLOP/s at
         # 2070 MHz on 152 SMs; 1.25 TFLOP/s measured), far below its bandwidth
