@@ -203,6 +203,7 @@ CoarseDev coarse_dev(ddel_ctx* ctx) {
   cd.Q = ctx->cQ;
   cd.SQ = ctx->cSQ;
   cd.Einv = ctx->csmall + 5 * KK;
+  cd.E = ctx->csmall + 4 * KK;
   cd.G = ctx->csmall + 6 * KK;
   cd.k = ctx->ck;
   cd.correct = (ctx->coarse_flags & DDEL_COARSE_CORRECT) ? 1 : (ctx->coarse_flags & DDEL_COARSE_DEFLATE) ? 2 : 0;
@@ -219,12 +220,6 @@ void pcg_iteration(ddel_ctx* ctx, int prec, bool apply32) {
   io.x = ctx->z;
   io.done = &ctx->st->done;
   io.pcg = ctx->st;
-  if (cd.k > 0 && cd.correct) {
-    io.cq = cd.Q;
-    io.cEinv = cd.Einv;
-    io.ck = cd.k;
-    io.cdeflate = cd.correct == 2;
-  }
   const int nd = schur_dispatch(ctx, prec, apply32, io, s);
   launch_pcg_update(ctx->T, ctx->F, apply_prec(ctx, prec, apply32), io.ring_out, ctx->x, ctx->r,
                     ctx->z, ctx->p, ctx->sv, ctx->st, s, ctx->nblk, nd, cd);

@@ -145,16 +145,6 @@ __device__ __forceinline__ void elem_node_offset(int a, int& dx, int& dy, int& d
   dz = a >> 2;
 }
 
-// Interface input of a Schur apply at Gamma DOF g: x[g] plus, inside a PCG
-// with a coarse space, the coarse part Q cc of the preconditioned residual
-// (cc in shared memory, from coarse_coefficients).
-__device__ __forceinline__ double gamma_input(const DevTables& t, const SchurIO& io, int64_t g,
-                                              const double* cc) {
-  double v = io.x[g];
-  for (int i = 0; i < io.ck; ++i) v += io.cq[i * t.n_gamma + g] * cc[i];
-  return v;
-}
-
 // Sum of src[0..n) by one warp in a fixed order (lane-strided with four
 // independent accumulators, so that the loads overlap, then the warp tree);
 // every lane returns the total, and every block that calls it on the same
@@ -184,46 +174,24 @@ __device__ __forceinline__ void block_tree_sum(const double (&a)[NV], int nv, do
   for (int v = 0; v < NV; ++v)
     if (v < nv) red[v * T + tid] = a[v];
   __syncthreads();
-  for (int s = T / 2; s > 0; s >>= 1) {
-    if (tid < s)
-#pragma unroll
-      for (int v = 0; v < NV; ++v)
-        if (v < nv) red[v * T + tid] += red[v * T + tid + s];
+  // each level's nv * s additions are spread over all threads (the same
+  // additions in the same order as one tree per value)
+  int ls = 0;
+  while ((1 << ls) < T) ++ls;
+  for (int s = T / 2, l = ls - 1; s > 0; s >>= 1, --l) {
+    for (int e = tid; e < nv * s; e += T) {
+      const int v = e >> l, i = e & (s - 1);
+      red[v * T + i] += red[v * T + i + s];
+    }
     __syncthreads();
   }
 }
 
-// Row index in the update partials of coarse sum v (v < k: Q^T r; else (S Q)^T u).
-__device__ __forceinline__ int coarse_row(int v, int k) { return v < k ? 2 + v : 2 + kMaxCoarse + (v - k); }
-
-// Coarse coefficients of the current preconditioned residual (Schur kernels of
-// a PCG with a coarse correction): cc = E^-1 (Q^T r_j - [deflate] (S Q)^T u_j)
-// from the partials of update iteration j.  All threads of the block call it.
-__device__ __forceinline__ void coarse_coefficients(const SchurIO& io, double* cc, double* tmp) {
-  const PcgState* st = io.pcg;
-  const int k = io.ck, nv = io.cdeflate ? 2 * k : k;
-  const double* P = st->pu[st->kS & 1];
-  const int nw = blockDim.x >> 5;
-  for (int v = threadIdx.x >> 5; v < nv; v += nw) {
-    const double s = reduce_partials_warp(P + (size_t)coarse_row(v, k) * st->nu, st->nu);
-    if ((threadIdx.x & 31) == 0) tmp[v] = s;
-  }
-  __syncthreads();
-  if ((int)threadIdx.x < k) {
-    double c = 0.0;
-    for (int j = 0; j < k; ++j)
-      c += io.cEinv[threadIdx.x * kMaxCoarse + j] * (tmp[j] - (io.cdeflate ? tmp[k + j] : 0.0));
-    cc[threadIdx.x] = c;
-  }
-  __syncthreads();
-}
-
-// Schur kernel of a PCG iteration: record the iteration index and, with a
-// coarse correction, the coarse coefficients.  All threads call it.
-__device__ __forceinline__ void schur_pcg_prologue(const SchurIO& io, double* cc, double* tmp) {
-  if (!io.pcg) return;
-  if (blockIdx.x == 0 && threadIdx.x == 0) io.pcg->kU = io.pcg->kS;
-  if (io.ck > 0) coarse_coefficients(io, cc, tmp);
+// Schur kernel of a PCG iteration: record the iteration index for the update
+// kernel.  (With a coarse space the Schur kernels apply S to the face-local
+// part of u only; the update kernel adds S Q cc from the stored S Q.)
+__device__ __forceinline__ void schur_pcg_prologue(const SchurIO& io) {
+  if (io.pcg && blockIdx.x == 0 && threadIdx.x == 0) io.pcg->kU = io.pcg->kS;
 }
 
 // The block's share of delta = (S u, u): the values d of warps [0, NW) summed,

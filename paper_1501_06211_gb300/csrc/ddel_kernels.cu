@@ -271,8 +271,7 @@ __global__ void __launch_bounds__(32) schur2d_kernel(DevTables t, const T* __res
                                                      const T* __restrict__ scale,
                                                      const T* __restrict__ factor, SchurIO io) {
   if (io.done && *io.done) return;
-  __shared__ double ccs[kMaxCoarse], ctmp[2 * kMaxCoarse];
-  schur_pcg_prologue(io, ccs, ctmp);
+  schur_pcg_prologue(io);
   constexpr int PC = BP * BP, PD = BP * (BP + 1) / 2, STAGE = PC + PD, R = BP / 32;
   const int sub = blockIdx.x, lane = threadIdx.x;
   const SubInfo si = t.subs[sub];
@@ -327,7 +326,7 @@ __global__ void __launch_bounds__(32) schur2d_kernel(DevTables t, const T* __res
   if (have_x) {
     for (int r = lane; r < si.n_ring; r += 32) {
       const int g = t.ring_gidx[si.ring_off + r];
-      xloc[t.ring_loc[si.ring_off + r]] = (T)gamma_input(t, io, g, ccs);
+      xloc[t.ring_loc[si.ring_off + r]] = (T)io.x[g];
     }
   }
   __syncwarp();
@@ -632,11 +631,11 @@ __global__ void __launch_bounds__(256) schur_explicit_kernel(DevTables t, const 
   const SubInfo si = t.subs[sub];
   __shared__ T xr[NR];
   __shared__ T part[256];
-  __shared__ double ccs[kMaxCoarse], ctmp[2 * kMaxCoarse], red[RH / 32];
-  schur_pcg_prologue(io, ccs, ctmp);
+  __shared__ double red[RH / 32];
+  schur_pcg_prologue(io);
   for (int j = tid; j < NR; j += 256) {
     T v = T(0);
-    if (j < si.n_ring) v = (T)gamma_input(t, io, t.ring_gidx[si.ring_off + j], ccs);
+    if (j < si.n_ring) v = (T)io.x[t.ring_gidx[si.ring_off + j]];
     xr[j] = v;
   }
   __syncthreads();
@@ -699,11 +698,11 @@ __global__ void __launch_bounds__(256) schur_explicit_df_kernel(DevTables t, con
   __shared__ float2 xr[NR];
   __shared__ double xd[NR];
   __shared__ double part[256];
-  __shared__ double ccs[kMaxCoarse], ctmp[2 * kMaxCoarse], red[RH / 32];
-  schur_pcg_prologue(io, ccs, ctmp);
+  __shared__ double red[RH / 32];
+  schur_pcg_prologue(io);
   for (int j = tid; j < NR; j += 256) {
     double v = 0.0;
-    if (j < si.n_ring) v = gamma_input(t, io, t.ring_gidx[si.ring_off + j], ccs);
+    if (j < si.n_ring) v = io.x[t.ring_gidx[si.ring_off + j]];
     const float hi = (float)v;
     xr[j] = make_float2(hi, (float)(v - (double)hi));
     xd[j] = v;
@@ -775,34 +774,45 @@ __global__ void gamma_sum_kernel(DevTables t, const T* __restrict__ ring,
 // convergence, and forms alpha_j, beta_j itself (the same bits in every
 // block); then w_g = sum of the ring entries of the owning subdomains,
 // p = u + beta p, s = w + beta s, x += alpha p, r -= alpha s.
-// Both: u = S~^-1 r and the block's partials of gamma = (r, u), rr = (r, r).
-// COARSE: u = S~^-1 r + Q cc with cc = E^-1 Q^T r (additive correction) or
-// cc = E^-1 (Q^T r - (S Q)^T S~^-1 r) (deflation, u = Q E^-1 Q^T r +
-// (I - Q E^-1 Q^T S) S~^-1 r).  The array u keeps the face-local part and every
-// reader of u adds Q cc; gamma = (r, S~^-1 r) + (Q^T r)^T cc.
-template <typename T, bool INIT, bool COARSE>
+// Both: u^ = S~^-1 r and the block's partials of gamma^ = (r, u^), rr = (r, r).
+// Coarse space (KC > 0, k <= KC columns): u = u^ + Q cc with cc = E^-1 Q^T r
+// (additive correction) or cc = E^-1 (Q^T r - (S Q)^T u^) (deflation,
+// u = Q E^-1 Q^T r + (I - Q E^-1 Q^T S) u^).  The array u and the Schur
+// kernels see only u^; the update adds Q cc to u and S Q cc to w = S u^, and
+// forms gamma = gamma^ + (Q^T r)^T cc and delta = (S u, u) = delta^ +
+// 2 cc^T (S Q)^T u^ + cc^T E cc from the partial sums of Q^T r and (S Q)^T u^.
+template <typename T, bool INIT, int KC>
 __global__ void __launch_bounds__(kRedThreads) pcg_cg_kernel(DevTables t, DevFields fld,
                                                              const double* __restrict__ gin,
                                                              const T* __restrict__ ring, double* x,
                                                              double* r, double* u, double* p,
                                                              double* sv, PcgState* st, CoarseDev cd, int nd) {
   if (st->done) return;
-  constexpr int KC = COARSE ? kMaxCoarse : 0, NV = 2 + 2 * KC, NP = 3 + 2 * KC;
+  constexpr int NV = 2 + 2 * KC, NP = 3 + 2 * KC;
   extern __shared__ double rw_all[];  // (blockDim/32) * max_blk_n doubles, then as many float2
-  __shared__ double red[NP * kRedThreads];     // tree sums (prologue NP values, epilogue NV)
-  __shared__ double sums[3 + 2 * kMaxCoarse];  // delta, gamma, rr, Q^T r, (S Q)^T u
-  __shared__ double sab[2 + kMaxCoarse];       // alpha, beta, cc
+  __shared__ double red[NP * kRedThreads];  // tree sums (prologue NP values, epilogue NV)
+  __shared__ double sums[NP];               // delta^, gamma^, rr, Q^T r, (S Q)^T u^
+  __shared__ double sab[2 + kMaxCoarse];    // alpha, beta, cc
   __shared__ int sflag;
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   double* rw = rw_all + wib * t.max_blk_n;
   float2* rwf = reinterpret_cast<float2*>(rw_all + (blockDim.x >> 5) * t.max_blk_n) + wib * t.max_blk_n;
-  const int kc = COARSE && cd.correct ? cd.k : 0;  // coarse correction dimension
-  const bool deflate = COARSE && cd.correct == 2;
+  const int k = KC > 0 ? cd.k : 0;  // coarse columns
+  const bool deflate = KC > 0 && cd.correct == 2;
   const int j = INIT ? -1 : st->kU;
   double alpha = 0.0, beta = 0.0;
-  double cc[KC > 0 ? KC : 1];  // INIT: x0 coefficients; else coarse part of the current u
-  int kn = 0;                  // columns in cc
+  double cc[KC > 0 ? KC : 1];  // INIT: x0 coefficients; else coarse coefficients of u_j
   if (!INIT) {
+    // E^-1 and E staged in shared memory by all threads at once (thread 0's
+    // scalar phase below would otherwise wait on a chain of global loads)
+    __shared__ double sEinv[KC > 0 ? KC * KC : 1], sE[KC > 0 ? KC * KC : 1];
+    for (int i = threadIdx.x; i < KC * KC; i += blockDim.x) {
+      const int a = i / KC, b = i % KC;
+      if (a < k && b < k) {
+        sEinv[i] = cd.Einv[a * kMaxCoarse + b];
+        sE[i] = 0.5 * (cd.E[a * kMaxCoarse + b] + cd.E[b * kMaxCoarse + a]);
+      }
+    }
     // scalars of thread 0 loaded first, so that their latency overlaps the sums
     double tol2 = 0.0, gprev = 1.0, aprev = 1.0;
     int max_it = 0;
@@ -817,32 +827,38 @@ __global__ void __launch_bounds__(kRedThreads) pcg_cg_kernel(DevTables t, DevFie
     // every thread loads its strided share of all partial vectors at once
     // (independent loads in flight), then one tree sum per value
     const double* U = st->pu[j & 1];
-    const int nu = st->nu, nvals = 3 + (deflate ? 2 * kc : kc);
+    const int nu = st->nu;
     double a[NP];
 #pragma unroll
     for (int v = 0; v < NP; ++v) {
       a[v] = 0.0;
-      if (v >= nvals) continue;
-      const double* src = v == 0 ? st->pd : U + (size_t)(v <= 2 ? v - 1 : coarse_row(v - 3, kc)) * nu;
+      if (v >= 3 && (v - 3) % KC >= k) continue;  // coarse rows beyond k
+      const double* src = v == 0 ? st->pd : U + (size_t)(v - 1) * nu;
       const int n = v == 0 ? nd : nu;
       for (int b = threadIdx.x; b < n; b += kRedThreads) a[v] += __ldcg(src + b);
     }
-    block_tree_sum<NP>(a, nvals, red);
-    if (threadIdx.x < nvals) sums[threadIdx.x] = red[threadIdx.x * kRedThreads];
+    block_tree_sum<NP>(a, NP, red);
+    if (threadIdx.x < NP) sums[threadIdx.x] = red[threadIdx.x * kRedThreads];
     __syncthreads();
     if (threadIdx.x == 0) {
-      // coarse coefficients of u_j first: gamma_j = (r, S~^-1 r) + (Q^T r)^T cc
-      double gamma = sums[1];
-      for (int i = 0; i < kc; ++i) {
+      double gamma = sums[1], delta = sums[0];
+      const double rr = sums[2];
+      const double* y = sums + 3;       // Q^T r_j
+      const double* vq = sums + 3 + KC;  // (S Q)^T u^_j
+      for (int i = 0; i < k; ++i) {
         double c = 0.0;
-        for (int q = 0; q < kc; ++q)
-          c += cd.Einv[i * kMaxCoarse + q] * (sums[3 + q] - (deflate ? sums[3 + kc + q] : 0.0));
+        for (int q = 0; q < k; ++q) c += sEinv[i * KC + q] * (y[q] - (deflate ? vq[q] : 0.0));
         sab[2 + i] = c;
-        gamma += sums[3 + i] * c;
       }
-      const double delta = sums[0], rr = sums[2];
+      for (int i = 0; i < k; ++i) {
+        const double ci = sab[2 + i];
+        gamma += y[i] * ci;
+        double ec = 0.0;
+        for (int q = 0; q < k; ++q) ec += sE[i * KC + q] * sab[2 + q];
+        delta += ci * (2.0 * vq[i] + ec);
+      }
       int status = 1;  // 1: iterate
-      double a = 0.0, b = 0.0;
+      double a_ = 0.0, b_ = 0.0;
       if (rr <= tol2) {
         status = 0;
       } else if (!isfinite(rr) || !isfinite(gamma)) {
@@ -852,14 +868,14 @@ __global__ void __launch_bounds__(kRedThreads) pcg_cg_kernel(DevTables t, DevFie
       } else {
         double den = delta;  // p^T S p in the Chronopoulos-Gear recurrence
         if (j > 0) {
-          b = gamma / gprev;
-          den = delta - b * gamma / aprev;
+          b_ = gamma / gprev;
+          den = delta - b_ * gamma / aprev;
         }
         if (!(den > 0.0) || !isfinite(den)) status = -6;  // breakdown
-        else a = gamma / den;
+        else a_ = gamma / den;
       }
-      sab[0] = a;
-      sab[1] = b;
+      sab[0] = a_;
+      sab[1] = b_;
       sflag = status;
       if (blockIdx.x == 0) {
         st->rr = rr;
@@ -868,7 +884,7 @@ __global__ void __launch_bounds__(kRedThreads) pcg_cg_kernel(DevTables t, DevFie
           st->done = 1;
           st->status = status;
         } else {
-          st->alpha_s[j & 1] = a;
+          st->alpha_s[j & 1] = a_;
           st->gamma_s[j & 1] = gamma;
           st->kS = j + 1;
         }
@@ -878,20 +894,18 @@ __global__ void __launch_bounds__(kRedThreads) pcg_cg_kernel(DevTables t, DevFie
     if (sflag != 1) return;
     alpha = sab[0];
     beta = sab[1];
-    kn = kc;
 #pragma unroll
-    for (int i = 0; i < KC; ++i) cc[i] = i < kc ? sab[2 + i] : 0.0;
+    for (int i = 0; i < KC; ++i) cc[i] = i < k ? sab[2 + i] : 0.0;
   } else {
-    kn = COARSE && cd.x0 ? cd.k : 0;
 #pragma unroll
-    for (int i = 0; i < KC; ++i) cc[i] = i < kn ? st->c0[i] : 0.0;
+    for (int i = 0; i < KC; ++i) cc[i] = (i < k && cd.x0) ? st->c0[i] : 0.0;
     if (blockIdx.x == 0 && threadIdx.x == 0) st->kS = 0;
   }
   auto coarse = [&](const double* V, int64_t g) -> double {
     double v = 0.0;
 #pragma unroll
     for (int i = 0; i < KC; ++i)
-      if (i < kn) v += V[i * t.n_gamma + g] * cc[i];
+      if (i < k) v += V[i * t.n_gamma + g] * cc[i];
     return v;
   };
   double acc[NV];
@@ -902,7 +916,7 @@ __global__ void __launch_bounds__(kRedThreads) pcg_cg_kernel(DevTables t, DevFie
     if (INIT) {
       p[g] = 0.0;
       sv[g] = 0.0;
-      if (COARSE) {
+      if (KC > 0) {
         x[g] = coarse(cd.Q, g);
         rg = gin[g] - coarse(cd.SQ, g);
       } else {
@@ -911,9 +925,9 @@ __global__ void __launch_bounds__(kRedThreads) pcg_cg_kernel(DevTables t, DevFie
       }
     } else {
       // S u at this DOF: the ring entries of its owners (fixed-width table,
-      // subdomain order, so the sum order is fixed)
-      const double w = ring_sum<T>(t, ring, g);
-      const double pg = u[g] + (COARSE ? coarse(cd.Q, g) : 0.0) + beta * p[g];
+      // subdomain order, so the sum order is fixed), plus S Q cc
+      const double w = ring_sum<T>(t, ring, g) + (KC > 0 ? coarse(cd.SQ, g) : 0.0);
+      const double pg = u[g] + (KC > 0 ? coarse(cd.Q, g) : 0.0) + beta * p[g];
       const double sg = w + beta * sv[g];
       p[g] = pg;
       sv[g] = sg;
@@ -924,8 +938,15 @@ __global__ void __launch_bounds__(kRedThreads) pcg_cg_kernel(DevTables t, DevFie
     acc[1] += rg * rg;
 #pragma unroll
     for (int i = 0; i < KC; ++i)
-      if (i < kc) acc[2 + i] += cd.Q[i * t.n_gamma + g] * rg;
+      if (i < k) acc[2 + i] += cd.Q[i * t.n_gamma + g] * rg;
     return rg;
+  };
+  auto local = [&](int64_t g, double ri, double ui) {  // u^ at g: store and sum
+    u[g] = ui;
+    acc[0] += ri * ui;
+#pragma unroll
+    for (int i = 0; i < KC; ++i)
+      if (i < k) acc[2 + KC + i] += cd.SQ[i * t.n_gamma + g] * ui;
   };
   const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int nw = (gridDim.x * blockDim.x) >> 5;
@@ -947,34 +968,23 @@ __global__ void __launch_bounds__(kRedThreads) pcg_cg_kernel(DevTables t, DevFie
       float hi = 0.f, lo = 0.f;
 #pragma unroll 4
       for (int q = 0; q < n; ++q) {
-        const float2 s = Pc[q * n], x = rwf[q];
-        const float p = __fmul_rn(s.x, x.x);
-        lo = __fadd_rn(lo, __fadd_rn(__fmaf_rn(s.x, x.x, -p), __fmaf_rn(s.x, x.y, __fmul_rn(s.y, x.x))));
-        df_add(hi, lo, p);
+        const float2 s = Pc[q * n], xq = rwf[q];
+        const float pr = __fmul_rn(s.x, xq.x);
+        lo = __fadd_rn(lo, __fadd_rn(__fmaf_rn(s.x, xq.x, -pr), __fmaf_rn(s.x, xq.y, __fmul_rn(s.y, xq.x))));
+        df_add(hi, lo, pr);
       }
       const double zi = (double)hi + (double)lo;
-      acc[0] += rw[i] * zi;  // r_i u_i = (W rw)_i (W^-1 zi)_i
-      const double ui = zi * fld.face_w[off + i];
-      u[off + i] = ui;
-      if (deflate)
-#pragma unroll
-        for (int c = 0; c < KC; ++c)
-          if (c < kc) acc[2 + KC + c] += cd.SQ[c * t.n_gamma + off + i] * ui;
+      // u^_i = W^-1 zi; r_i (this thread wrote it in the first loop)
+      local(off + i, r[off + i], zi * fld.face_w[off + i]);
     }
     __syncwarp();
   }
   for (int64_t g = t.n_face_dofs + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < t.n_gamma;
        g += (int64_t)gridDim.x * blockDim.x) {
     const double ri = step(g);
-    const double zi = ri * fld.cross_scale[g - t.n_face_dofs];
-    u[g] = zi;
-    acc[0] += ri * zi;
-    if (deflate)
-#pragma unroll
-      for (int c = 0; c < KC; ++c)
-        if (c < kc) acc[2 + KC + c] += cd.SQ[c * t.n_gamma + g] * zi;
+    local(g, ri, ri * fld.cross_scale[g - t.n_face_dofs]);
   }
-  // this block's partials of iteration j + 1 (gamma, rr, coarse sums)
+  // this block's partials of iteration j + 1 (gamma^, rr, Q^T r, (S Q)^T u^)
   block_tree_sum<NV>(acc, NV, red);
   if (threadIdx.x < NV) st->pu[(j + 1) & 1][(size_t)threadIdx.x * st->nu + blockIdx.x] = red[threadIdx.x * kRedThreads];
 }
@@ -1319,36 +1329,49 @@ static size_t update_smem(const DevTables& t) {
   return (size_t)(kRedThreads / 32) * t.max_blk_n * (sizeof(double) + sizeof(float2));
 }
 
+// Coarse columns padded to 4 or 8 (template width of the coarse sums).
+static int coarse_width(int k) { return k <= 0 ? 0 : k <= 4 ? 4 : 8; }
+
 void launch_pcg_init(const DevTables& t, const DevFields& fld, const double* g, double* x, double* r,
                      double* u, double* p, double* sv, PcgState* s, cudaStream_t st, int nblk,
                      const CoarseDev& cd) {
-  if (cd.k > 0)  // initial guess x0 = Q c0 (and the coarse sums of u0 when correcting)
-    pcg_cg_kernel<double, true, true><<<nblk, kRedThreads, update_smem(t), st>>>(
-        t, fld, g, nullptr, x, r, u, p, sv, s, cd, 0);
-  else
-    pcg_cg_kernel<double, true, false><<<nblk, kRedThreads, update_smem(t), st>>>(
-        t, fld, g, nullptr, x, r, u, p, sv, s, cd, 0);
+  const size_t sm = update_smem(t);
+  switch (coarse_width(cd.k)) {  // x0 = Q c0 and the coarse sums of iteration 0
+    case 4:
+      pcg_cg_kernel<double, true, 4><<<nblk, kRedThreads, sm, st>>>(t, fld, g, nullptr, x, r, u, p, sv, s, cd, 0);
+      break;
+    case 8:
+      pcg_cg_kernel<double, true, 8><<<nblk, kRedThreads, sm, st>>>(t, fld, g, nullptr, x, r, u, p, sv, s, cd, 0);
+      break;
+    default:
+      pcg_cg_kernel<double, true, 0><<<nblk, kRedThreads, sm, st>>>(t, fld, g, nullptr, x, r, u, p, sv, s, cd, 0);
+  }
+}
+
+template <typename T>
+static void launch_update_t(const DevTables& t, const DevFields& fld, const T* ring, double* x, double* r,
+                            double* u, double* p, double* sv, PcgState* s, cudaStream_t st, int nblk, int nd,
+                            const CoarseDev& cd) {
+  const size_t sm = update_smem(t);
+  switch (cd.correct ? coarse_width(cd.k) : 0) {
+    case 4:
+      pcg_cg_kernel<T, false, 4><<<nblk, kRedThreads, sm, st>>>(t, fld, nullptr, ring, x, r, u, p, sv, s, cd, nd);
+      break;
+    case 8:
+      pcg_cg_kernel<T, false, 8><<<nblk, kRedThreads, sm, st>>>(t, fld, nullptr, ring, x, r, u, p, sv, s, cd, nd);
+      break;
+    default:
+      pcg_cg_kernel<T, false, 0><<<nblk, kRedThreads, sm, st>>>(t, fld, nullptr, ring, x, r, u, p, sv, s, cd, nd);
+  }
 }
 
 void launch_pcg_update(const DevTables& t, const DevFields& fld, int precision, const void* ring,
                        double* x, double* r, double* u, double* p, double* sv, PcgState* s,
                        cudaStream_t st, int nblk, int nd, const CoarseDev& cd) {
-  const bool c = cd.k > 0 && cd.correct;
-  if (precision == 0) {
-    if (c)
-      pcg_cg_kernel<double, false, true><<<nblk, kRedThreads, update_smem(t), st>>>(
-          t, fld, nullptr, (const double*)ring, x, r, u, p, sv, s, cd, nd);
-    else
-      pcg_cg_kernel<double, false, false><<<nblk, kRedThreads, update_smem(t), st>>>(
-          t, fld, nullptr, (const double*)ring, x, r, u, p, sv, s, cd, nd);
-  } else {
-    if (c)
-      pcg_cg_kernel<float, false, true><<<nblk, kRedThreads, update_smem(t), st>>>(
-          t, fld, nullptr, (const float*)ring, x, r, u, p, sv, s, cd, nd);
-    else
-      pcg_cg_kernel<float, false, false><<<nblk, kRedThreads, update_smem(t), st>>>(
-          t, fld, nullptr, (const float*)ring, x, r, u, p, sv, s, cd, nd);
-  }
+  if (precision == 0)
+    launch_update_t(t, fld, (const double*)ring, x, r, u, p, sv, s, st, nblk, nd, cd);
+  else
+    launch_update_t(t, fld, (const float*)ring, x, r, u, p, sv, s, st, nblk, nd, cd);
 }
 
 void launch_precond(const DevTables& t, const DevFields& fld, const double* r, double* z,

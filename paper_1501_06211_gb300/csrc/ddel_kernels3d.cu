@@ -291,8 +291,7 @@ __global__ void __launch_bounds__(kT3) schur3d_kernel(DevTables t, const T* __re
                                                       const T* __restrict__ scale,
                                                       const T* __restrict__ factor, SchurIO io) {
   if (io.done && *io.done) return;
-  __shared__ double ccs[kMaxCoarse], ctmp[2 * kMaxCoarse];
-  schur_pcg_prologue(io, ccs, ctmp);
+  schur_pcg_prologue(io);
   const int BP = t.BP, PC = BP * BP, PD = BP * (BP + 1) / 2, STAGE = PC + PD;
   const int sub = blockIdx.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const SubInfo si = t.subs[sub];
@@ -313,7 +312,7 @@ __global__ void __launch_bounds__(kT3) schur3d_kernel(DevTables t, const T* __re
   const bool have_x = io.x != nullptr;
   if (have_x)
     for (int r = tid; r < si.n_ring; r += kT3)
-      xloc[t.ring_loc[si.ring_off + r]] = (T)gamma_input(t, io, t.ring_gidx[si.ring_off + r], ccs);
+      xloc[t.ring_loc[si.ring_off + r]] = (T)io.x[t.ring_gidx[si.ring_off + r]];
   __syncthreads();
   const int nb = si.nb;
   const T* fb = factor + si.factor_off;

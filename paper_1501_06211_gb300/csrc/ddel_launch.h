@@ -48,7 +48,7 @@ struct DevTables {
 // records kU = j; the update kernel reads kU, stores alpha_j, gamma_j in slot
 // j & 1 and sets kS = j + 1; update partials are double-buffered by parity.
 constexpr int kMaxCoarse = 8;
-constexpr int kPcgRows = 2 + 2 * kMaxCoarse;  // gamma, rr, Q^T r (k), (S Q)^T u (k)
+constexpr int kPcgRows = 2 + 2 * kMaxCoarse;  // gamma, rr, Q^T r (k), (S Q)^T u^ (k)
 
 struct PcgState {
   double tol2, rr;
@@ -71,6 +71,7 @@ struct CoarseDev {
   const double* Q = nullptr;
   const double* SQ = nullptr;
   const double* Einv = nullptr;
+  const double* E = nullptr;  // Q^T S Q (as formed; symmetrised where used)
   const double* G = nullptr;
   int k = 0;
   int correct = 1;  // 0: initial guess only; 1: additive correction; 2: deflation
@@ -95,12 +96,6 @@ struct SchurIO {
   const int* done = nullptr;      // early exit flag
   PcgState* pcg = nullptr;        // PCG form: also reduce delta = (S u, u) -> alpha, beta
   int* err = nullptr;
-  // coarse part of the PCG input: x[g] + sum_i cq[i * n_gamma + g] * cc_i, with
-  // cc = cEinv (Q^T r - [cdeflate] (S Q)^T u) from the update partials
-  const double* cq = nullptr;
-  const double* cEinv = nullptr;
-  int ck = 0;
-  int cdeflate = 0;
 };
 
 // Opt-in shared memory sizes for every kernel instantiation (call once).
