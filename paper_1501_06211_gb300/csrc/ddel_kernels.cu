@@ -688,16 +688,32 @@ __global__ void split_df_kernel(const double* __restrict__ in, float2* __restric
   }
 }
 
+// (hi, lo) += (p_hi, p_lo): double-float addition (Knuth's TwoSum on the high
+// parts, low parts added, renormalised).
+__device__ __forceinline__ void df_add2(float& hi, float& lo, float phi, float plo) {
+  const float s = __fadd_rn(hi, phi);
+  const float bp = __fsub_rn(s, hi);
+  const float err = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bp)), __fsub_rn(phi, bp));
+  const float t = __fadd_rn(__fadd_rn(lo, plo), err);
+  hi = __fadd_rn(s, t);
+  lo = __fsub_rn(t, __fsub_rn(hi, s));
+}
+
+// One CTA per half of a subdomain's rows; each thread owns two adjacent rows
+// and JN columns, loading both rows' entries of a column as one 16-byte
+// float4 (S_i stored column-major as (hi, lo) pairs); the H column groups of a
+// row are combined in double-float as well, so FP64 work is left to the
+// final row values.
 template <int NR>
 __global__ void __launch_bounds__(256) schur_explicit_df_kernel(DevTables t, const float2* __restrict__ Sexp,
                                                                 SchurIO io) {
   if (io.done && *io.done) return;
-  constexpr int RH = NR / 2, H = 256 / RH;
+  constexpr int RH = NR / 2, RP = RH / 2, H = 256 / RP, JN = NR / H;
   const int sub = blockIdx.x >> 1, half = blockIdx.x & 1, tid = threadIdx.x;
   const SubInfo si = t.subs[sub];
   __shared__ float2 xr[NR];
   __shared__ double xd[NR];
-  __shared__ double part[256];
+  __shared__ float2 part[2 * 256];
   __shared__ double red[RH / 32];
   schur_pcg_prologue(io);
   for (int j = tid; j < NR; j += 256) {
@@ -708,28 +724,37 @@ __global__ void __launch_bounds__(256) schur_explicit_df_kernel(DevTables t, con
     xd[j] = v;
   }
   __syncthreads();
-  const int r = half * RH + tid % RH, h = tid / RH;
-  const float2* Sc = Sexp + (int64_t)sub * NR * NR;
-  constexpr int JN = NR / H;  // columns per thread
-  const int j0 = h * JN;
-  float hi = 0.f, lo = 0.f;
+  const int rp = tid % RP, h = tid / RP;
+  const int r0 = half * RH + 2 * rp;
+  const float4* Sc = reinterpret_cast<const float4*>(Sexp + (int64_t)sub * NR * NR);
+  float hi0 = 0.f, lo0 = 0.f, hi1 = 0.f, lo1 = 0.f;
+  auto term = [](float& hi, float& lo, float sx, float sy, float2 x) {
+    const float p = __fmul_rn(sx, x.x);
+    // low-order part: product error (exact via FMA) and the hi*lo cross terms
+    lo = __fadd_rn(lo, __fadd_rn(__fmaf_rn(sx, x.x, -p), __fmaf_rn(sx, x.y, __fmul_rn(sy, x.x))));
+    df_add(hi, lo, p);
+  };
 #pragma unroll 8
   for (int q = 0; q < JN; ++q) {
-    const float2 s = Sc[(j0 + q) * NR + r], x = xr[j0 + q];
-    const float p = __fmul_rn(s.x, x.x);
-    // low-order part: product error (exact via FMA) and the hi*lo cross terms
-    lo = __fadd_rn(lo, __fadd_rn(__fmaf_rn(s.x, x.x, -p), __fmaf_rn(s.x, x.y, __fmul_rn(s.y, x.x))));
-    df_add(hi, lo, p);
+    const int j = h * JN + q;
+    const float4 sv4 = Sc[(j * NR + r0) >> 1];
+    const float2 x = xr[j];
+    term(hi0, lo0, sv4.x, sv4.y, x);
+    term(hi1, lo1, sv4.z, sv4.w, x);
   }
-  const double tot = (double)hi + (double)lo;
-  part[tid] = tot;
+  part[2 * tid] = make_float2(hi0, lo0);
+  part[2 * tid + 1] = make_float2(hi1, lo1);
   __syncthreads();
   double d[1] = {0.0};
   const int row = half * RH + tid;
   if (tid < RH && row < si.n_ring) {
-    double y = 0.0;
+    float yh = 0.f, yl = 0.f;
 #pragma unroll
-    for (int q = 0; q < H; ++q) y += part[q * RH + tid];
+    for (int q = 0; q < H; ++q) {
+      const float2 pq = part[2 * (q * RP + (tid >> 1)) + (tid & 1)];
+      df_add2(yh, yl, pq.x, pq.y);
+    }
+    const double y = (double)yh + (double)yl;
     reinterpret_cast<double*>(io.ring_out)[t.ring_dst[si.ring_off + row]] = y;
     d[0] = xd[row] * y;
   }
