@@ -211,18 +211,30 @@ CoarseDev coarse_dev(ddel_ctx* ctx) {
   return cd;
 }
 
-// One PCG iteration: w = S u (ring) with delta = (S u, u) -> alpha, beta; then
-// the vector updates and u = S~^-1 r (+ the coarse part) with gamma = (r, u).
-void pcg_iteration(ddel_ctx* ctx, int prec, bool apply32) {
+// Iterations issued between host checks: even, so that the parity of the
+// double-buffered partial sums repeats across graph launches.
+int pcg_per(const ddel_ctx* ctx) {
+  const int per = ctx->opt.check_every > 0 ? ctx->opt.check_every : 16;
+  return per + (per & 1);
+}
+
+double* pcg_partials(ddel_ctx* ctx, int par) { return ctx->pcg_pu + (size_t)par * kPcgRows * ctx->nblk; }
+
+// One PCG iteration: w = S u (ring) with the partials of delta = (S u, u);
+// then alpha, beta, the vector updates and u = S~^-1 r (+ the coarse part)
+// with the partials of gamma = (r, u).  par = iteration parity.
+void pcg_iteration(ddel_ctx* ctx, int prec, bool apply32, int par) {
   cudaStream_t s = ctx->stream;
   const CoarseDev cd = coarse_dev(ctx);
   SchurIO io = make_io(ctx);
   io.x = ctx->z;
   io.done = &ctx->st->done;
   io.pcg = ctx->st;
+  io.pd = ctx->pcg_pd;
   const int nd = schur_dispatch(ctx, prec, apply32, io, s);
   launch_pcg_update(ctx->T, ctx->F, apply_prec(ctx, prec, apply32), io.ring_out, ctx->x, ctx->r,
-                    ctx->z, ctx->p, ctx->sv, ctx->st, s, ctx->nblk, nd, cd);
+                    ctx->z, ctx->p, ctx->sv, ctx->st, ctx->pcg_pd, nd, pcg_partials(ctx, par),
+                    pcg_partials(ctx, par ^ 1), par, s, ctx->nblk, cd);
 }
 
 // PCG initialisation (asynchronous) and, with use_graph, the CUDA graph of
@@ -234,9 +246,10 @@ int pcg_start(ddel_ctx* ctx, int prec, const double* g, bool apply32) {
     launch_coarse_x0(cd, g, ctx->T.n_gamma, ctx->st, s);
     ctx->launches += 1;
   }
-  launch_pcg_init(ctx->T, ctx->F, g, ctx->x, ctx->r, ctx->z, ctx->p, ctx->sv, ctx->st, s, ctx->nblk, cd);
+  launch_pcg_init(ctx->T, ctx->F, g, ctx->x, ctx->r, ctx->z, ctx->p, ctx->sv, ctx->st, pcg_partials(ctx, 0), s,
+                  ctx->nblk, cd);
   ctx->launches += 1;
-  const int per = ctx->opt.check_every > 0 ? ctx->opt.check_every : 16;
+  const int per = pcg_per(ctx);
   const bool expl = ctx->explicit_ok[prec];
   const bool df = prec == 0 && ctx->df_ok;
   const int gck = cd.k > 0 && cd.correct ? cd.k : 0;
@@ -249,7 +262,7 @@ int pcg_start(ddel_ctx* ctx, int prec, const double* g, bool apply32) {
   if (ctx->opt.use_graph && !ctx->graph[prec]) {
     cudaGraph_t graph;
     CK(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
-    for (int i = 0; i < per; ++i) pcg_iteration(ctx, prec, apply32);
+    for (int i = 0; i < per; ++i) pcg_iteration(ctx, prec, apply32, i & 1);
     CK(cudaStreamEndCapture(s, &graph));
     CK(cudaGraphInstantiate(&ctx->graph[prec], graph, 0));
     cudaGraphDestroy(graph);
@@ -266,11 +279,11 @@ int pcg_start(ddel_ctx* ctx, int prec, const double* g, bool apply32) {
 // (asynchronous; ctx->ev[7] is recorded after the copy).
 int pcg_issue(ddel_ctx* ctx, int prec, bool apply32) {
   cudaStream_t s = ctx->stream;
-  const int per = ctx->opt.check_every > 0 ? ctx->opt.check_every : 16;
+  const int per = pcg_per(ctx);
   if (ctx->opt.use_graph) {
     CK(cudaGraphLaunch(ctx->graph[prec], s));
   } else {
-    for (int i = 0; i < per; ++i) pcg_iteration(ctx, prec, apply32);
+    for (int i = 0; i < per; ++i) pcg_iteration(ctx, prec, apply32, i & 1);
   }
   ctx->launches += 2 * per;
   CK(cudaMemcpyAsync(ctx->h_st, ctx->st, sizeof(PcgState), cudaMemcpyDeviceToHost, s));
@@ -282,7 +295,7 @@ int pcg_run(ddel_ctx* ctx, int prec, const double* g, int* iters, int* status,
             bool apply32 = false) {
   int rc = pcg_start(ctx, prec, g, apply32);
   if (rc) return rc;
-  const int per = ctx->opt.check_every > 0 ? ctx->opt.check_every : 16;
+  const int per = pcg_per(ctx);
   const int max_checks = ctx->opt.max_it / per + 2;
   for (int chk = 0; chk < max_checks; ++chk) {
     rc = pcg_issue(ctx, prec, apply32);
@@ -583,10 +596,7 @@ int ddel_create(const ddel_mesh* mesh, const ddel_material* mat, const ddel_bc* 
     ctx->nblk = 2 * 152;
     PcgState st0{};
     st0.partials = ctx->partials;
-    st0.pd = ctx->pcg_pd;
-    st0.pu[0] = ctx->pcg_pu;
-    st0.pu[1] = ctx->pcg_pu + (size_t)kPcgRows * ctx->nblk;
-    st0.nu = ctx->nblk;
+
     if (bad(cudaMemcpy(ctx->st, &st0, sizeof(PcgState), cudaMemcpyHostToDevice)) ||
         bad(cudaMemset(ctx->ticketK, 0, 16)) || bad(cudaMemset(ctx->ring, 0, ring_bytes)) ||
         bad(cudaMemset(ctx->ring32, 0, ring_bytes)) ||
@@ -1069,7 +1079,7 @@ int ddel_batch_solve(ddel_ctx* const* ctxs, int n, double* const* u, ddel_stats*
       if (q == cudaErrorNotReady) continue;
       CK(q);
       progressed = true;
-      const int per = ctx->opt.check_every > 0 ? ctx->opt.check_every : 16;
+      const int per = pcg_per(ctx);
       if (!ctx->h_st->done && ++checks[i] < ctx->opt.max_it / per + 2) {
         int rc = pcg_issue(ctx, prec[i], false);
         if (rc) return rc;

@@ -209,7 +209,7 @@ __device__ __forceinline__ void schur_pcg_epilogue(const SchurIO& io, double d, 
     double tot = 0.0;
 #pragma unroll
     for (int i = 0; i < NW; ++i) tot += red[i];
-    io.pcg->pd[blockIdx.x] = tot;
+    io.pd[blockIdx.x] = tot;
   }
 }
 

@@ -811,7 +811,10 @@ __global__ void __launch_bounds__(kRedThreads) pcg_cg_kernel(DevTables t, DevFie
                                                              const double* __restrict__ gin,
                                                              const T* __restrict__ ring, double* x,
                                                              double* r, double* u, double* p,
-                                                             double* sv, PcgState* st, CoarseDev cd, int nd) {
+                                                             double* sv, PcgState* st, CoarseDev cd,
+                                                             const double* __restrict__ pd, int nd,
+                                                             const double* __restrict__ pu_in,
+                                                             double* __restrict__ pu_out, int par) {
   if (st->done) return;
   constexpr int NV = 2 + 2 * KC, NP = 3 + 2 * KC;
   extern __shared__ double rw_all[];  // (blockDim/32) * max_blk_n doubles, then as many float2
@@ -839,26 +842,24 @@ __global__ void __launch_bounds__(kRedThreads) pcg_cg_kernel(DevTables t, DevFie
       }
     }
     // scalars of thread 0 loaded first, so that their latency overlaps the sums
-    double tol2 = 0.0, gprev = 1.0, aprev = 1.0;
+    double tol2 = 0.0, ginv = 0.0, ainv = 0.0;
     int max_it = 0;
     if (threadIdx.x == 0) {
       tol2 = st->tol2;
       max_it = st->max_it;
-      if (j > 0) {
-        gprev = st->gamma_s[(j - 1) & 1];
-        aprev = st->alpha_s[(j - 1) & 1];
-      }
+      ginv = st->ginv_s[par ^ 1];
+      ainv = st->ainv_s[par ^ 1];
     }
     // every thread loads its strided share of all partial vectors at once
     // (independent loads in flight), then one tree sum per value
-    const double* U = st->pu[j & 1];
-    const int nu = st->nu;
+    const double* U = pu_in;
+    const int nu = gridDim.x;
     double a[NP];
 #pragma unroll
     for (int v = 0; v < NP; ++v) {
       a[v] = 0.0;
       if (v >= 3 && (v - 3) % KC >= k) continue;  // coarse rows beyond k
-      const double* src = v == 0 ? st->pd : U + (size_t)(v - 1) * nu;
+      const double* src = v == 0 ? pd : U + (size_t)(v - 1) * nu;
       const int n = v == 0 ? nd : nu;
       for (int b = threadIdx.x; b < n; b += kRedThreads) a[v] += __ldcg(src + b);
     }
@@ -883,7 +884,8 @@ __global__ void __launch_bounds__(kRedThreads) pcg_cg_kernel(DevTables t, DevFie
         delta += ci * (2.0 * vq[i] + ec);
       }
       int status = 1;  // 1: iterate
-      double a_ = 0.0, b_ = 0.0;
+      double a_ = 0.0, b_ = 0.0, den = delta;  // den = p^T S p (Chronopoulos-Gear)
+      const double gi = 1.0 / gamma;          // independent of the division below
       if (rr <= tol2) {
         status = 0;
       } else if (!isfinite(rr) || !isfinite(gamma)) {
@@ -891,10 +893,9 @@ __global__ void __launch_bounds__(kRedThreads) pcg_cg_kernel(DevTables t, DevFie
       } else if (j >= max_it) {
         status = -5;
       } else {
-        double den = delta;  // p^T S p in the Chronopoulos-Gear recurrence
         if (j > 0) {
-          b_ = gamma / gprev;
-          den = delta - b_ * gamma / aprev;
+          b_ = gamma * ginv;  // gamma_j / gamma_{j-1}
+          den = delta - b_ * gamma * ainv;
         }
         if (!(den > 0.0) || !isfinite(den)) status = -6;  // breakdown
         else a_ = gamma / den;
@@ -909,8 +910,8 @@ __global__ void __launch_bounds__(kRedThreads) pcg_cg_kernel(DevTables t, DevFie
           st->done = 1;
           st->status = status;
         } else {
-          st->alpha_s[j & 1] = a_;
-          st->gamma_s[j & 1] = gamma;
+          st->ainv_s[par] = den * gi;  // 1 / alpha_j = den / gamma_j
+          st->ginv_s[par] = gi;
           st->kS = j + 1;
         }
       }
@@ -1011,7 +1012,7 @@ __global__ void __launch_bounds__(kRedThreads) pcg_cg_kernel(DevTables t, DevFie
   }
   // this block's partials of iteration j + 1 (gamma^, rr, Q^T r, (S Q)^T u^)
   block_tree_sum<NV>(acc, NV, red);
-  if (threadIdx.x < NV) st->pu[(j + 1) & 1][(size_t)threadIdx.x * st->nu + blockIdx.x] = red[threadIdx.x * kRedThreads];
+  if (threadIdx.x < NV) pu_out[(size_t)threadIdx.x * gridDim.x + blockIdx.x] = red[threadIdx.x * kRedThreads];
 }
 
 __global__ void precond_kernel(DevTables t, DevFields fld, const double* __restrict__ r,
@@ -1358,45 +1359,53 @@ static size_t update_smem(const DevTables& t) {
 static int coarse_width(int k) { return k <= 0 ? 0 : k <= 4 ? 4 : 8; }
 
 void launch_pcg_init(const DevTables& t, const DevFields& fld, const double* g, double* x, double* r,
-                     double* u, double* p, double* sv, PcgState* s, cudaStream_t st, int nblk,
-                     const CoarseDev& cd) {
+                     double* u, double* p, double* sv, PcgState* s, double* pu_out, cudaStream_t st,
+                     int nblk, const CoarseDev& cd) {
   const size_t sm = update_smem(t);
   switch (coarse_width(cd.k)) {  // x0 = Q c0 and the coarse sums of iteration 0
     case 4:
-      pcg_cg_kernel<double, true, 4><<<nblk, kRedThreads, sm, st>>>(t, fld, g, nullptr, x, r, u, p, sv, s, cd, 0);
+      pcg_cg_kernel<double, true, 4><<<nblk, kRedThreads, sm, st>>>(t, fld, g, nullptr, x, r, u, p, sv, s, cd,
+                                                                     nullptr, 0, nullptr, pu_out, 1);
       break;
     case 8:
-      pcg_cg_kernel<double, true, 8><<<nblk, kRedThreads, sm, st>>>(t, fld, g, nullptr, x, r, u, p, sv, s, cd, 0);
+      pcg_cg_kernel<double, true, 8><<<nblk, kRedThreads, sm, st>>>(t, fld, g, nullptr, x, r, u, p, sv, s, cd,
+                                                                     nullptr, 0, nullptr, pu_out, 1);
       break;
     default:
-      pcg_cg_kernel<double, true, 0><<<nblk, kRedThreads, sm, st>>>(t, fld, g, nullptr, x, r, u, p, sv, s, cd, 0);
+      pcg_cg_kernel<double, true, 0><<<nblk, kRedThreads, sm, st>>>(t, fld, g, nullptr, x, r, u, p, sv, s, cd,
+                                                                     nullptr, 0, nullptr, pu_out, 1);
   }
 }
 
 template <typename T>
 static void launch_update_t(const DevTables& t, const DevFields& fld, const T* ring, double* x, double* r,
-                            double* u, double* p, double* sv, PcgState* s, cudaStream_t st, int nblk, int nd,
+                            double* u, double* p, double* sv, PcgState* s, const double* pd, int nd,
+                            const double* pu_in, double* pu_out, int par, cudaStream_t st, int nblk,
                             const CoarseDev& cd) {
   const size_t sm = update_smem(t);
   switch (cd.correct ? coarse_width(cd.k) : 0) {
     case 4:
-      pcg_cg_kernel<T, false, 4><<<nblk, kRedThreads, sm, st>>>(t, fld, nullptr, ring, x, r, u, p, sv, s, cd, nd);
+      pcg_cg_kernel<T, false, 4><<<nblk, kRedThreads, sm, st>>>(t, fld, nullptr, ring, x, r, u, p, sv, s, cd, pd,
+                                                                nd, pu_in, pu_out, par);
       break;
     case 8:
-      pcg_cg_kernel<T, false, 8><<<nblk, kRedThreads, sm, st>>>(t, fld, nullptr, ring, x, r, u, p, sv, s, cd, nd);
+      pcg_cg_kernel<T, false, 8><<<nblk, kRedThreads, sm, st>>>(t, fld, nullptr, ring, x, r, u, p, sv, s, cd, pd,
+                                                                nd, pu_in, pu_out, par);
       break;
     default:
-      pcg_cg_kernel<T, false, 0><<<nblk, kRedThreads, sm, st>>>(t, fld, nullptr, ring, x, r, u, p, sv, s, cd, nd);
+      pcg_cg_kernel<T, false, 0><<<nblk, kRedThreads, sm, st>>>(t, fld, nullptr, ring, x, r, u, p, sv, s, cd, pd,
+                                                                nd, pu_in, pu_out, par);
   }
 }
 
 void launch_pcg_update(const DevTables& t, const DevFields& fld, int precision, const void* ring,
                        double* x, double* r, double* u, double* p, double* sv, PcgState* s,
-                       cudaStream_t st, int nblk, int nd, const CoarseDev& cd) {
+                       const double* pd, int nd, const double* pu_in, double* pu_out, int par,
+                       cudaStream_t st, int nblk, const CoarseDev& cd) {
   if (precision == 0)
-    launch_update_t(t, fld, (const double*)ring, x, r, u, p, sv, s, st, nblk, nd, cd);
+    launch_update_t(t, fld, (const double*)ring, x, r, u, p, sv, s, pd, nd, pu_in, pu_out, par, st, nblk, cd);
   else
-    launch_update_t(t, fld, (const float*)ring, x, r, u, p, sv, s, st, nblk, nd, cd);
+    launch_update_t(t, fld, (const float*)ring, x, r, u, p, sv, s, pd, nd, pu_in, pu_out, par, st, nblk, cd);
 }
 
 void launch_precond(const DevTables& t, const DevFields& fld, const double* r, double* z,

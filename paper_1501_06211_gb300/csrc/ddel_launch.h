@@ -45,8 +45,9 @@ struct DevTables {
 // sums, and every block of the next kernel reduces them itself in a fixed
 // order (all blocks obtain bitwise the same totals), so each kernel starts
 // with the scalars it needs.  Iteration j: the Schur kernel reads kS = j and
-// records kU = j; the update kernel reads kU, stores alpha_j, gamma_j in slot
-// j & 1 and sets kS = j + 1; update partials are double-buffered by parity.
+// records kU = j; the update kernel reads kU, stores 1/alpha_j, 1/gamma_j in
+// slot j & 1 and sets kS = j + 1; the update partials are double-buffered by
+// parity (the buffers are kernel arguments).
 constexpr int kMaxCoarse = 8;
 constexpr int kPcgRows = 2 + 2 * kMaxCoarse;  // gamma, rr, Q^T r (k), (S Q)^T u^ (k)
 
@@ -54,10 +55,7 @@ struct PcgState {
   double tol2, rr;
   int it, max_it, done, status;
   int kS, kU;
-  double alpha_s[2], gamma_s[2];
-  double* pd;      // Schur kernel: one delta partial per block
-  double* pu[2];   // update kernel: kPcgRows x nu partials, by parity of j
-  int nu;          // update kernel blocks
+  double ainv_s[2], ginv_s[2];  // 1 / alpha_j and 1 / gamma_j in slot j & 1
   unsigned ticket[4];
   double* partials;  // scratch of grid_sum-based one-off kernels
   double c0[kMaxCoarse];  // coefficients of the initial guess x0 = Q c0
@@ -94,7 +92,8 @@ struct SchurIO {
   void* ring_out = nullptr;       // per ring slot output (T), nullptr = skip
   double* u_out = nullptr;        // global vector, interior DOFs written, nullptr = skip
   const int* done = nullptr;      // early exit flag
-  PcgState* pcg = nullptr;        // PCG form: also reduce delta = (S u, u) -> alpha, beta
+  PcgState* pcg = nullptr;        // PCG form: also write this block's share of delta = (S u, u)
+  double* pd = nullptr;           // PCG form: the delta partials (one per block)
   int* err = nullptr;
 };
 
@@ -140,13 +139,18 @@ void launch_gamma_sum(const DevTables& t, int precision, const void* ring, const
 // With a coarse space (cd.k > 0) the preconditioner is S~^-1 r + Q E^-1 Q^T r
 // (u keeps the face-local part; the coarse part lives in PcgState::cc), and
 // init starts from x0 = Q c0 (PcgState::c0, set by launch_coarse_x0).
+// pu_out: the update partials written (kPcgRows x nblk).
 void launch_pcg_init(const DevTables& t, const DevFields& fld, const double* g, double* x, double* r,
-                     double* u, double* p, double* sv, PcgState* s, cudaStream_t st, int nblk,
-                     const CoarseDev& cd = CoarseDev());
-// nd: blocks of the Schur kernel that wrote the delta partials.
+                     double* u, double* p, double* sv, PcgState* s, double* pu_out, cudaStream_t st,
+                     int nblk, const CoarseDev& cd = CoarseDev());
+// Update j: pd holds the nd delta partials of the Schur kernel, pu_in the
+// update partials of iteration j (written by update j-1 or init), pu_out
+// receives those of j + 1; par = j & 1 (recurrence scalar slots).  Passing
+// them as arguments keeps a dependent load off the start of the kernel.
 void launch_pcg_update(const DevTables& t, const DevFields& fld, int precision, const void* ring,
                        double* x, double* r, double* u, double* p, double* sv, PcgState* s,
-                       cudaStream_t st, int nblk, int nd, const CoarseDev& cd = CoarseDev());
+                       const double* pd, int nd, const double* pu_in, double* pu_out, int par,
+                       cudaStream_t st, int nblk, const CoarseDev& cd = CoarseDev());
 // Coarse-space set-up (ddel_coarse.cu).  Gram matrix out = A^T B (k x k,
 // leading dimension kMaxCoarse) of k <= kMaxCoarse columns of length n.
 void launch_gram(const double* A, const double* B, int k, int64_t n, double* out, double* partials,
