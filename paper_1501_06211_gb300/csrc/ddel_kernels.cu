@@ -707,7 +707,8 @@ __device__ __forceinline__ void df_add2(float& hi, float& lo, float phi, float p
 template <int NR>
 __global__ void __launch_bounds__(256) schur_explicit_df_kernel(DevTables t, const float2* __restrict__ Sexp,
                                                                 SchurIO io) {
-  if (io.done && *io.done) return;
+  // the flag's load overlaps the gather; nothing is written before the test
+  const int done = io.done ? *io.done : 0;
   constexpr int RH = NR / 2, RP = RH / 2, H = 256 / RP, JN = NR / H;
   const int sub = blockIdx.x >> 1, half = blockIdx.x & 1, tid = threadIdx.x;
   const SubInfo si = t.subs[sub];
@@ -715,7 +716,6 @@ __global__ void __launch_bounds__(256) schur_explicit_df_kernel(DevTables t, con
   __shared__ double xd[NR];
   __shared__ float2 part[2 * 256];
   __shared__ double red[RH / 32];
-  schur_pcg_prologue(io);
   for (int j = tid; j < NR; j += 256) {
     double v = 0.0;
     if (j < si.n_ring) v = io.x[t.ring_gidx[si.ring_off + j]];
@@ -723,6 +723,8 @@ __global__ void __launch_bounds__(256) schur_explicit_df_kernel(DevTables t, con
     xr[j] = make_float2(hi, (float)(v - (double)hi));
     xd[j] = v;
   }
+  if (done) return;  // uniform over the grid: converged in an earlier iteration
+  schur_pcg_prologue(io);
   __syncthreads();
   const int rp = tid % RP, h = tid / RP;
   const int r0 = half * RH + 2 * rp;
@@ -815,7 +817,7 @@ __global__ void __launch_bounds__(kRedThreads) pcg_cg_kernel(DevTables t, DevFie
                                                              const double* __restrict__ pd, int nd,
                                                              const double* __restrict__ pu_in,
                                                              double* __restrict__ pu_out, int par) {
-  if (st->done) return;
+  const int done = st->done;  // tested once the prologue's loads are in flight
   constexpr int NV = 2 + 2 * KC, NP = 3 + 2 * KC;
   extern __shared__ double rw_all[];  // (blockDim/32) * max_blk_n doubles, then as many float2
   __shared__ double red[NP * kRedThreads];  // tree sums (prologue NP values, epilogue NV)
@@ -863,6 +865,7 @@ __global__ void __launch_bounds__(kRedThreads) pcg_cg_kernel(DevTables t, DevFie
       const int n = v == 0 ? nd : nu;
       for (int b = threadIdx.x; b < n; b += kRedThreads) a[v] += __ldcg(src + b);
     }
+    if (done) return;  // uniform over the grid
     block_tree_sum<NP>(a, NP, red);
     if (threadIdx.x < NP) sums[threadIdx.x] = red[threadIdx.x * kRedThreads];
     __syncthreads();
@@ -923,6 +926,7 @@ __global__ void __launch_bounds__(kRedThreads) pcg_cg_kernel(DevTables t, DevFie
 #pragma unroll
     for (int i = 0; i < KC; ++i) cc[i] = i < k ? sab[2 + i] : 0.0;
   } else {
+    if (done) return;
 #pragma unroll
     for (int i = 0; i < KC; ++i) cc[i] = (i < k && cd.x0) ? st->c0[i] : 0.0;
     if (blockIdx.x == 0 && threadIdx.x == 0) st->kS = 0;
