@@ -299,7 +299,7 @@ def learned_vs_plain(ddel, torch, workloads, stream, steps=16, skip=4):
     """Per-solve time of topology steps on the 256x128 MBB beam (V = 0.4,
     r_min = 1.5): plain PCG against coarse spaces from the last Picard
     solutions (HISTORY, k = 8) and from those plus the online U-Net
-    (CNN_HISTORY, 4 + 4 vectors, 5 Adam steps per solve).  The first `skip`
+    (CNN_HISTORY, 4 + 4 vectors, 4 Adam steps on the 8 newest observations per solve).  The first `skip`
     steps warm up; time per step is the device time of the whole Picard step
     (filter, assembly, factorisation, coarse set-up, solve, training, OC)."""
     cfg = workloads.config("c4")
@@ -308,7 +308,7 @@ def learned_vs_plain(ddel, torch, workloads, stream, steps=16, skip=4):
            "steps": steps - skip}
     for name, lopt in (("plain", None),
                        ("history8", dict(mode=ddel.DDEL_LEARN_HISTORY, k_history=8)),
-                       ("cnn+history4", dict(mode=ddel.DDEL_LEARN_CNN_HISTORY, k_history=4, train_steps=5))):
+                       ("cnn+history4", dict(mode=ddel.DDEL_LEARN_CNN_HISTORY, k_history=4, train_steps=4, batch=8))):
         s = ddel.Solver(cfg, stream=stream.cuda_stream, tol=1e-8, max_it=20000)
         L = ddel.Learner(s, **lopt) if lopt else None
         rho = torch.full((ne,), cfg["v_frac"], dtype=torch.float64, device="cuda")

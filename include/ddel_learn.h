@@ -68,7 +68,8 @@ int ddel_cnn_adam_step(ddel_cnn* net, double lr, double beta1, double beta2, dou
  * from the best (energy-norm) combination of them.
  * mode CNN: before each solve, fields of the network (once min_samples
  * observations are stored); after it, the observation joins a replay buffer of
- * the last `replay` steps and train_steps Adam steps run on all of it.
+ * the last `replay` steps and train_steps Adam steps run on its `batch` newest
+ * observations.
  * mode HISTORY: the coarse space is the last k_history interface solutions.
  * mode CNN_HISTORY: both, the k_history solutions first (k_history <= 4). */
 typedef enum { DDEL_LEARN_CNN = 0, DDEL_LEARN_HISTORY = 1, DDEL_LEARN_CNN_HISTORY = 2 } ddel_learn_mode;
@@ -78,7 +79,8 @@ typedef struct {
   int k_history;      /* HISTORY, CNN_HISTORY: solutions kept (4; at most DDEL_MAX_COARSE,
                          or DDEL_MAX_COARSE - 4 with the network) */
   int replay;         /* CNN: observations kept (16) */
-  int train_steps;    /* CNN: Adam steps per observation (20) */
+  int train_steps;    /* CNN: Adam steps per observation (4) */
+  int batch;          /* CNN: minibatch, the newest observations of the replay buffer (8) */
   int min_samples;    /* CNN: observations before the first prediction (2) */
   double lr;          /* CNN: Adam learning rate (1e-3) */
   int widths[4];      /* CNN: level widths (16, 32, 48, 64) */

@@ -158,7 +158,8 @@ void ddel_learner_default_options(ddel_learner_options* o) {
   o->coarse_flags = DDEL_COARSE_X0 | DDEL_COARSE_CORRECT;
   o->k_history = 4;
   o->replay = 16;
-  o->train_steps = 20;
+  o->train_steps = 4;
+  o->batch = 8;
   o->min_samples = 2;
   o->lr = 1e-3;
   const int w[4] = {16, 32, 48, 64};
@@ -178,7 +179,8 @@ int ddel_learner_create(ddel_ctx* ctx, const ddel_learner_options* opt, ddel_lea
     return DDEL_EINVAL;
   const int kmax = o.mode == DDEL_LEARN_HISTORY ? DDEL_MAX_COARSE : DDEL_MAX_COARSE - 4;
   if (o.mode != DDEL_LEARN_CNN && (o.k_history < 1 || o.k_history > kmax)) return DDEL_EINVAL;
-  if (o.mode != DDEL_LEARN_HISTORY && (o.replay < 1 || o.train_steps < 0 || o.min_samples < 1 || !(o.lr > 0)))
+  if (o.mode != DDEL_LEARN_HISTORY &&
+      (o.replay < 1 || o.train_steps < 0 || o.min_samples < 1 || !(o.lr > 0) || o.batch < 1))
     return DDEL_EINVAL;
   ddel_info_t info;
   if (int rc = ddel_get_info(ctx, &info)) return rc;
@@ -318,9 +320,15 @@ int ddel_learner_observe(ddel_learner* L, const double* rho_f, const double* u) 
   L->count = std::min(L->count + 1, L->opt.replay);
   L->info.samples = L->count;
   cudaEventRecord(L->ev[0], L->s);
+  // minibatch: the `batch` newest observations as one contiguous run of slots
+  // (when the newest lie at the start of the ring, the first `batch` slots)
+  const int nb = std::min(L->count, L->opt.batch);
+  const int first = L->next >= nb ? L->next - nb : 0;
+  const float* bx = L->rx + (int64_t)first * 3 * plane;
+  const float* bt = L->rt + (int64_t)first * 4 * plane;
   for (int step = 0; step < L->opt.train_steps; ++step) {
     double loss = 0.0;
-    rc = ddel_cnn_loss_grad(L->net, L->rx, L->rt, L->count, &loss, nullptr);
+    rc = ddel_cnn_loss_grad(L->net, bx, bt, nb, &loss, nullptr);
     if (!rc) rc = ddel_cnn_adam_step(L->net, L->opt.lr, 0.9, 0.999, 1e-8);
     if (rc) return rc;
     if (step == 0) L->info.last_loss = loss;

@@ -81,7 +81,7 @@ class ddel_topopt_state(ctypes.Structure):
 
 class ddel_learner_options(ctypes.Structure):
     _fields_ = [("mode", c_int), ("coarse_flags", c_int), ("k_history", c_int), ("replay", c_int),
-                ("train_steps", c_int), ("min_samples", c_int), ("lr", c_double),
+                ("train_steps", c_int), ("batch", c_int), ("min_samples", c_int), ("lr", c_double),
                 ("widths", c_int * 4), ("seed", ctypes.c_uint64)]
 
 

@@ -212,5 +212,8 @@ def test_topopt_with_history_and_learned_coarse_space():
     assert all(r[1] >= 2 for r in lrn[2:]) and ih.samples == 4 and il.samples == 8
     assert all(r[1] >= 4 for r in both[2:]) and ib.samples == steps
     assert il.adam_steps == 10 * steps and il.last_loss >= 0 and ib.adam_steps == 5 * steps
-    # reusing previous solutions pays: fewer PCG iterations after the first steps
+    # what the coarse spaces gain over the plain method once they exist: fewer
+    # PCG iterations per Picard solve (previous solutions, and the trained
+    # network's fields on their own)
     assert sum(r[0] for r in hist[3:]) < sum(r[0] for r in plain[3:])
+    assert sum(r[0] for r in lrn[3:]) < sum(r[0] for r in plain[3:])
