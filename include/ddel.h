@@ -354,6 +354,14 @@ int ddel_kernel_info(const ddel_ctx* ctx, ddel_kernel_info_t* out);
  * serialise them.  The call clears the counter itself; no other state carries
  * over between calls.  Errors: EINVAL (sizes, null inputs, grid too large),
  * ECUDA (device address lookup or launch failed). */
+/* Self-test of failure detection without a fault: a kernel waits on a device
+ * barrier that nothing completes, through the same bounded wait (poll_limit
+ * polls, 1 <= poll_limit <= 2^22) and error word as the solver's bulk-copy
+ * waits, and gives up; *status = DDEL_ETIMEOUT when the timeout was detected
+ * and reported (DDEL_OK would mean the wait completed, which cannot happen).
+ * The paper has no counterpart.  Synchronises the device. */
+int ddel_selftest_wait_timeout(unsigned int poll_limit, int* status);
+
 int ddel_residual_norm_noalloc(int dim, int nx, int ny, int nz, const double* Ke,
                                const double* factors, const uint8_t* fixed, const double* f,
                                const double* u, double* r, double* norms, void* cuda_stream);

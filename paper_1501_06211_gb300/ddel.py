@@ -127,6 +127,7 @@ def _load():
         "ddel_autotune": (c_int, [c_void_p, ctypes.c_char_p, c_void_p, c_void_p, c_void_p]),
         "ddel_topopt_step": (c_int, [c_void_p, P(ddel_topopt_state), P(ddel_stats)]),
         "ddel_set_coarse": (c_int, [c_void_p, c_void_p, c_int, c_int, c_int]),
+        "ddel_selftest_wait_timeout": (c_int, [ctypes.c_uint, P(c_int)]),
         "ddel_checkpoint_save": (c_int, [c_void_p, P(ddel_topopt_state), ctypes.c_char_p]),
         "ddel_checkpoint_load": (c_int, [c_void_p, P(ddel_topopt_state), ctypes.c_char_p]),
         "ddel_residual_norm_noalloc": (c_int, [c_int, c_int, c_int, c_int, c_void_p, c_void_p,
@@ -281,6 +282,12 @@ def ddel_checkpoint_save(h, state, path):
 
 def ddel_checkpoint_load(h, state, path):
     return _lib.ddel_checkpoint_load(h, ctypes.byref(state), os.fsencode(path))
+
+
+def ddel_selftest_wait_timeout(poll_limit):
+    st = c_int(0)
+    code = _lib.ddel_selftest_wait_timeout(int(poll_limit), ctypes.byref(st))
+    return code, st.value
 
 
 def ddel_topopt_step(h, state):
