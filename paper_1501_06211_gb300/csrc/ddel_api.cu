@@ -37,6 +37,8 @@ struct ddel_ctx {
   bool mixed_ready = false;
   float2* sexp_df = nullptr;           // FP64 S_i as FP32 (hi, lo) pairs (double-float apply)
   bool df_ok = false;
+  float2* factor_df = nullptr;         // 3D: FP64 factor as FP32 pairs (double-float apply)
+  bool df3_ok = false;
   bool graph_df = false;
   bool pending_explicit = false;
   bool explicit_ok[2] = {false, false};
@@ -192,7 +194,10 @@ int schur_dispatch(ddel_ctx* ctx, int prec, bool apply32, SchurIO& io, cudaStrea
     launch_schur_explicit(ctx->T, apply32 ? 1 : prec, smat, io, s);
     return 2 * ctx->T.n_sub;
   }
-  launch_schur(ctx->T, ctx->F, prec, ctx->factor[prec], io, s);
+  if (ctx->T.dim == 3 && prec == 0 && !apply32 && ctx->df3_ok)
+    launch_schur3d_df(ctx->T, ctx->F, ctx->factor_df, io, s);
+  else
+    launch_schur(ctx->T, ctx->F, prec, ctx->factor[prec], io, s);
   return ctx->T.n_sub;
 }
 
@@ -374,7 +379,16 @@ int factor_check(ddel_ctx* ctx, int prec) {
   ctx->explicit_ok[prec] = ctx->pending_explicit;
   ctx->coarse_prec = -1;  // E must be formed again with the new S (next ddel_solve)
   ctx->ck = 0;
-  if (prec == 0) ctx->df_ok = false;
+  if (prec == 0) ctx->df_ok = ctx->df3_ok = false;
+  if (prec == 0 && ctx->T.dim == 3 && ctx->opt.schur_mode == DDEL_SCHUR_AUTO) {
+    // 3D: the FP64 factor as FP32 (hi, lo) pairs for the double-float PCG apply
+    if (!ctx->factor_df && cudaMalloc(&ctx->factor_df, ctx->S.factor_elems * sizeof(float2) + 256) != cudaSuccess)
+      return fail(ctx, DDEL_ENOMEM, "double-float factor allocation");
+    launch_split_df((const double*)ctx->factor[0], ctx->factor_df, ctx->S.factor_elems, ctx->stream);
+    ctx->launches += 1;
+    CK(cudaGetLastError());
+    ctx->df3_ok = true;
+  }
   if (prec == 0 && ctx->explicit_ok[0] && ctx->opt.schur_mode == DDEL_SCHUR_AUTO) {
     // FP64 local Schur complements as FP32 (hi, lo) pairs for the double-float apply
     const int NR = explicit_ring_size(ctx->T);
@@ -632,6 +646,7 @@ void ddel_destroy(ddel_ctx* ctx) {
     if (p) cudaFree(p);
   if (ctx->sexp32) cudaFree(ctx->sexp32);
   if (ctx->sexp_df) cudaFree(ctx->sexp_df);
+  if (ctx->factor_df) cudaFree(ctx->factor_df);
   if (ctx->h_st) cudaFreeHost(ctx->h_st);
   if (ctx->h_nrm) cudaFreeHost(ctx->h_nrm);
   if (ctx->h_err) cudaFreeHost(ctx->h_err);

@@ -145,6 +145,52 @@ __device__ __forceinline__ void elem_node_offset(int a, int& dx, int& dy, int& d
   dz = a >> 2;
 }
 
+// ---- double-float arithmetic (value = hi + lo, two FP32 numbers) ----------
+// Error-free transformations with explicitly rounded intrinsics (the compiler
+// may not contract them into FMAs, which would break them): Dekker's product
+// split via FMA and Knuth's TwoSum, about 48 significant bits on the FP32
+// pipes (this GPU issues 2 FP64 multiply-adds per clock per SM).
+__device__ __forceinline__ void df_add(float& hi, float& lo, float p) {
+  const float s = __fadd_rn(hi, p);
+  const float bp = __fsub_rn(s, hi);
+  const float err = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bp)), __fsub_rn(p, bp));
+  hi = s;
+  lo = __fadd_rn(lo, err);
+}
+
+// (hi, lo) += (p_hi, p_lo): double-float addition (Knuth's TwoSum on the high
+// parts, low parts added, renormalised).
+__device__ __forceinline__ void df_add2(float& hi, float& lo, float phi, float plo) {
+  const float s = __fadd_rn(hi, phi);
+  const float bp = __fsub_rn(s, hi);
+  const float err = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bp)), __fsub_rn(phi, bp));
+  const float t = __fadd_rn(__fadd_rn(lo, plo), err);
+  hi = __fadd_rn(s, t);
+  lo = __fsub_rn(t, __fsub_rn(hi, s));
+}
+
+// (hi, lo) += s * x for double-float s and x: the high product p = s.hi x.hi,
+// its exact rounding error by FMA and the hi*lo cross terms go to lo.
+__device__ __forceinline__ void df_mad(float& hi, float& lo, float2 s, float2 x) {
+  const float p = __fmul_rn(s.x, x.x);
+  lo = __fadd_rn(lo, __fadd_rn(__fmaf_rn(s.x, x.x, -p), __fmaf_rn(s.x, x.y, __fmul_rn(s.y, x.x))));
+  df_add(hi, lo, p);
+}
+
+__device__ __forceinline__ float2 df_from(double v) {
+  const float hi = (float)v;
+  return make_float2(hi, (float)(v - (double)hi));
+}
+
+// Warp-wide double-float sum (the same bits in every lane).
+__device__ __forceinline__ void df_warp_sum(float& hi, float& lo) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const float ph = __shfl_xor_sync(0xffffffffu, hi, o), pl = __shfl_xor_sync(0xffffffffu, lo, o);
+    df_add2(hi, lo, ph, pl);
+  }
+}
+
 // Sum of src[0..n) by one warp in a fixed order (lane-strided with four
 // independent accumulators, so that the loads overlap, then the warp tree);
 // every lane returns the total, and every block that calls it on the same

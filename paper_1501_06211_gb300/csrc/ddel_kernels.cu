@@ -664,20 +664,10 @@ __global__ void __launch_bounds__(256) schur_explicit_kernel(DevTables t, const 
 
 // ---- double-float form of the explicit apply --------------------------------
 // S_i is stored as pairs (hi, lo) of FP32 with hi + lo = S to 2^-48 relative,
-// the ring vector likewise, and each row sum is accumulated as a pair with
-// error-free transformations: Dekker's product split via FMA
-// (p = a*b, e = fma(a, b, -p)) and Knuth's TwoSum, so the arithmetic runs on
+// the ring vector likewise, and each row sum is accumulated as a pair with the
+// error-free transformations of df_mad / df_add2, so the arithmetic runs on
 // the FP32 pipes (GB300: 128 lanes/clk/SM) instead of the FP64 pipe
 // (2 DFMA/clk/SM) while keeping about 48 significant bits.
-// (rounded intrinsics: the compiler may not contract them into FMAs, which
-// would break the error-free transformations)
-__device__ __forceinline__ void df_add(float& hi, float& lo, float p) {
-  const float s = __fadd_rn(hi, p);
-  const float bp = __fsub_rn(s, hi);
-  const float err = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bp)), __fsub_rn(p, bp));
-  hi = s;
-  lo = __fadd_rn(lo, err);
-}
 
 __global__ void split_df_kernel(const double* __restrict__ in, float2* __restrict__ out, int64_t n) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
@@ -688,16 +678,6 @@ __global__ void split_df_kernel(const double* __restrict__ in, float2* __restric
   }
 }
 
-// (hi, lo) += (p_hi, p_lo): double-float addition (Knuth's TwoSum on the high
-// parts, low parts added, renormalised).
-__device__ __forceinline__ void df_add2(float& hi, float& lo, float phi, float plo) {
-  const float s = __fadd_rn(hi, phi);
-  const float bp = __fsub_rn(s, hi);
-  const float err = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bp)), __fsub_rn(phi, bp));
-  const float t = __fadd_rn(__fadd_rn(lo, plo), err);
-  hi = __fadd_rn(s, t);
-  lo = __fsub_rn(t, __fsub_rn(hi, s));
-}
 
 // One CTA per half of a subdomain's rows; each thread owns two adjacent rows
 // and JN columns, loading both rows' entries of a column as one 16-byte

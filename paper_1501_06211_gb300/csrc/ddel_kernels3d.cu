@@ -286,6 +286,37 @@ __device__ __forceinline__ T ebe_local3d(const T* ke, const T* sc, const T* xloc
   return acc;
 }
 
+// ebe_local3d in double-float arithmetic: (hi, lo) += (K^(i) xloc) at local
+// node (a, b, c), component comp (ke, sc, xloc as FP32 pairs).
+__device__ __forceinline__ void ebe_local3d_df(const float2* ke, const float2* sc, const float2* xloc, int s,
+                                               int a, int b, int c, int comp, float& hi, float& lo) {
+  const int s1 = s + 1;
+  for (int dx = 0; dx < 2; ++dx) {
+    const int ea = a - dx;
+    if (ea < 0 || ea >= s) continue;
+    for (int dy = 0; dy < 2; ++dy) {
+      const int eb = b - dy;
+      if (eb < 0 || eb >= s) continue;
+      for (int dz = 0; dz < 2; ++dz) {
+        const int ec = c - dz;
+        if (ec < 0 || ec >= s) continue;
+        const float2* krow = ke + (elem_local_node(dx, dy, dz) * 3 + comp) * 24;
+        float ph = 0.f, pl = 0.f;
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+          int ox, oy, oz;
+          elem_node_offset(q, ox, oy, oz);
+          const float2* xn = xloc + (((ea + ox) * s1 + (eb + oy)) * s1 + (ec + oz)) * 3;
+          df_mad(ph, pl, krow[3 * q], xn[0]);
+          df_mad(ph, pl, krow[3 * q + 1], xn[1]);
+          df_mad(ph, pl, krow[3 * q + 2], xn[2]);
+        }
+        df_mad(hi, lo, sc[(ea * s + eb) * s + ec], make_float2(ph, pl));
+      }
+    }
+  }
+}
+
 template <typename T>
 __global__ void __launch_bounds__(kT3) schur3d_kernel(DevTables t, const T* __restrict__ Ke_g,
                                                       const T* __restrict__ scale,
@@ -398,6 +429,137 @@ __global__ void __launch_bounds__(kT3) schur3d_kernel(DevTables t, const T* __re
   schur_pcg_epilogue<kT3 / 32>(io, d[0], red);
 }
 
+// Double-float form of schur3d_kernel<double> for the PCG apply: the factor
+// blocks, element matrix, element factors and local vectors as FP32 (hi, lo)
+// pairs, every product in double-float arithmetic on the FP32 pipes (the FP64
+// form keeps this GPU's FP64 pipe 84 % busy); interior rows with no
+// neighbour on the subdomain boundary skip K_IG x (it vanishes there).
+__global__ void __launch_bounds__(kT3) schur3d_df_kernel(DevTables t, const double* __restrict__ Ke_g,
+                                                         const double* __restrict__ scale,
+                                                         const float2* __restrict__ factor, SchurIO io) {
+  if (io.done && *io.done) return;
+  schur_pcg_prologue(io);
+  const int BP = t.BP, PC = BP * BP, PD = BP * (BP + 1) / 2, STAGE = PC + PD;
+  const int sub = blockIdx.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const SubInfo si = t.subs[sub];
+  const int s = t.s, s1 = s + 1, nloc = s1 * s1 * s1;
+  extern __shared__ __align__(128) unsigned char smem_df3[];
+  float2* ybuf = reinterpret_cast<float2*>(smem_df3);  // nb_max * BP
+  float2* vbuf = ybuf + t.nb_max * BP;                  // BP
+  float2* xloc = vbuf + BP;                             // 3 * nloc
+  float2* ke = xloc + 3 * nloc;                         // 576
+  float2* sc = ke + 576;                                // s^3
+  for (int i = tid; i < 576; i += kT3) ke[i] = df_from(Ke_g[i]);
+  for (int i = tid; i < s * s * s; i += kT3) {
+    const int a = i / (s * s), b = (i / s) % s, c = i % s;
+    sc[i] = df_from(scale[((int64_t)(si.lo[0] + a) * t.ne[1] + si.lo[1] + b) * t.ne[2] + si.lo[2] + c]);
+  }
+  for (int i = tid; i < 3 * nloc; i += kT3) xloc[i] = make_float2(0.f, 0.f);
+  __syncthreads();
+  const bool have_x = io.x != nullptr;
+  if (have_x)
+    for (int r = tid; r < si.n_ring; r += kT3)
+      xloc[t.ring_loc[si.ring_off + r]] = df_from(io.x[t.ring_gidx[si.ring_off + r]]);
+  __syncthreads();
+  const int nb = si.nb;
+  const float2* fb = factor + si.factor_off;
+  // forward: y_k = D_k (w_k - C_k y_{k-1})
+  for (int k = 0; k < nb; ++k) {
+    const float2* Ck = fb + (int64_t)k * STAGE;
+    const float2* Dk = Ck + PC;
+    for (int r = tid; r < BP; r += kT3) {
+      float2 v = make_float2(0.f, 0.f);
+      if (r < si.bsz) {
+        int x, y, z, c;
+        row_node3(si, k, r, x, y, z, c);
+        const int64_t dof = 3 * node3(t, x, y, z) + c;
+        if (!t.fixed[dof]) {
+          if (io.f) v = df_from(io.f[dof]);
+          const int a = x - si.lo[0], b = y - si.lo[1], cz = z - si.lo[2];
+          const bool near = a <= 1 || a >= s - 1 || b <= 1 || b >= s - 1 || cz <= 1 || cz >= s - 1;
+          if (have_x && near) {
+            float eh = 0.f, el = 0.f;
+            ebe_local3d_df(ke, sc, xloc, s, a, b, cz, c, eh, el);
+            df_add2(v.x, v.y, -eh, -el);
+          }
+        }
+      }
+      if (k > 0) {
+        const float2* yp = ybuf + (k - 1) * BP;
+        float ah = 0.f, al = 0.f;
+#pragma unroll 4
+        for (int j = 0; j < BP; ++j) df_mad(ah, al, Ck[(int64_t)j * BP + r], yp[j]);
+        df_add2(v.x, v.y, -ah, -al);
+      }
+      vbuf[r] = v;
+    }
+    __syncthreads();
+    for (int r = tid; r < BP; r += kT3) {
+      float ah = 0.f, al = 0.f;
+      for (int j = 0; j <= r; ++j) df_mad(ah, al, Dk[j * BP - j * (j - 1) / 2 + (r - j)], vbuf[j]);
+      ybuf[k * BP + r] = make_float2(ah, al);
+    }
+    __syncthreads();
+  }
+  // backward: t_k = D_k^T (y_k - C_{k+1}^T t_{k+1}); one warp per output entry
+  for (int k = nb - 1; k >= 0; --k) {
+    const float2* Dk = fb + (int64_t)k * STAGE + PC;
+    const float2* Cn = fb + (int64_t)(k + 1) * STAGE;
+    for (int j = warp; j < BP; j += kT3 / 32) {
+      float ah = 0.f, al = 0.f;
+      if (k + 1 < nb) {
+        const float2* tn = ybuf + (k + 1) * BP;
+        for (int r = lane; r < BP; r += 32) df_mad(ah, al, Cn[(int64_t)j * BP + r], tn[r]);
+      }
+      df_warp_sum(ah, al);
+      if (lane == 0) {
+        float2 v = ybuf[k * BP + j];
+        df_add2(v.x, v.y, -ah, -al);
+        vbuf[j] = v;
+      }
+    }
+    __syncthreads();
+    for (int j = warp; j < BP; j += kT3 / 32) {
+      const float2* col = Dk + (j * BP - j * (j - 1) / 2);
+      float ah = 0.f, al = 0.f;
+      for (int i = j + lane; i < BP; i += 32) df_mad(ah, al, col[i - j], vbuf[i]);
+      df_warp_sum(ah, al);
+      if (lane == 0) ybuf[k * BP + j] = make_float2(ah, al);
+    }
+    __syncthreads();
+  }
+  // outputs: t into the local closure, y = (K^(i) [t; x])_G on the ring
+  if (io.u_out || io.ring_out) {
+    for (int k = 0; k < nb; ++k)
+      for (int r = tid; r < si.bsz; r += kT3) {
+        int x, y, z, c;
+        row_node3(si, k, r, x, y, z, c);
+        const int64_t dof = 3 * node3(t, x, y, z) + c;
+        if (t.fixed[dof]) continue;
+        const float2 tv = ybuf[k * BP + r];
+        if (io.u_out) io.u_out[dof] = (double)tv.x + (double)tv.y;
+        xloc[(((x - si.lo[0]) * s1 + (y - si.lo[1])) * s1 + (z - si.lo[2])) * 3 + c] = tv;
+      }
+    __syncthreads();
+  }
+  double d[1] = {0.0};
+  if (io.ring_out) {
+    double* out = reinterpret_cast<double*>(io.ring_out);
+    for (int r = tid; r < si.n_ring; r += kT3) {
+      const int loc = t.ring_loc[si.ring_off + r];
+      const int node = loc / 3, c = loc % 3;
+      const int a = node / (s1 * s1), b = (node / s1) % s1, cc = node % s1;
+      float yh = 0.f, yl = 0.f;
+      ebe_local3d_df(ke, sc, xloc, s, a, b, cc, c, yh, yl);
+      const double y = (double)yh + (double)yl;
+      out[t.ring_dst[si.ring_off + r]] = y;
+      d[0] += ((double)xloc[loc].x + (double)xloc[loc].y) * y;
+    }
+  }
+  __shared__ double red[kT3 / 32];
+  schur_pcg_epilogue<kT3 / 32>(io, d[0], red);
+}
+
 }  // namespace
 
 size_t factor3d_work_elems(const DevTables& t) { return (size_t)t.n_sub * 2 * t.BP * t.BP; }
@@ -410,6 +572,13 @@ void launch_factor3d(const DevTables& t, const DevFields& fld, int precision, vo
   else
     factor3d_kernel<float><<<t.n_sub, kT3, 0, st>>>(t, t.Ke32, fld.scale32, (float*)factor,
                                                     (float*)work, err, bad_sub);
+}
+
+size_t schur3d_smem(const DevTables& t, int precision);
+
+void launch_schur3d_df(const DevTables& t, const DevFields& fld, const float2* factor, const SchurIO& io,
+                       cudaStream_t st) {
+  schur3d_df_kernel<<<t.n_sub, kT3, schur3d_smem(t, 0), st>>>(t, t.Ke64, fld.scale64, factor, io);
 }
 
 size_t schur3d_smem(const DevTables& t, int precision) {
@@ -435,6 +604,11 @@ cudaError_t configure_kernels3d() {
     cudaDeviceGetAttribute(&big, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
   cudaError_t e = cudaSuccess;
   cudaFuncAttributes fa;
+  if (cudaFuncGetAttributes(&fa, schur3d_df_kernel) == cudaSuccess) {
+    cudaError_t e2 = cudaFuncSetAttribute(schur3d_df_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          big - (int)fa.sharedSizeBytes);
+    if (e2 != cudaSuccess) e = e2;
+  }
   if (cudaFuncGetAttributes(&fa, schur3d_kernel<double>) == cudaSuccess)
     e = cudaFuncSetAttribute(schur3d_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              big - (int)fa.sharedSizeBytes);

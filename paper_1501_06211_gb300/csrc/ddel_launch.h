@@ -113,6 +113,9 @@ void launch_factor3d(const DevTables& t, const DevFields& fld, int precision, vo
                      void* work, int* err, int* bad_sub, cudaStream_t st);
 void launch_schur3d(const DevTables& t, const DevFields& fld, int precision, const void* factor,
                     const SchurIO& io, cudaStream_t st);
+// FP64 operator in double-float arithmetic: factor as FP32 (hi, lo) pairs.
+void launch_schur3d_df(const DevTables& t, const DevFields& fld, const float2* factor, const SchurIO& io,
+                       cudaStream_t st);
 cudaError_t configure_kernels3d();
 // Per-subdomain solve kernel (condense / Schur / back-substitution forms).
 void launch_schur(const DevTables& t, const DevFields& fld, int precision, const void* factor,
