@@ -38,6 +38,7 @@ struct ddel_ctx {
   float2* sexp_df = nullptr;           // FP64 S_i as FP32 (hi, lo) pairs (double-float apply)
   bool df_ok = false;
   float2* factor_df = nullptr;         // 3D: FP64 factor as FP32 pairs (double-float apply)
+  int64_t* df3_off = nullptr;          // 3D: per-subdomain offsets into factor_df
   bool df3_ok = false;
   bool graph_df = false;
   bool pending_explicit = false;
@@ -195,7 +196,7 @@ int schur_dispatch(ddel_ctx* ctx, int prec, bool apply32, SchurIO& io, cudaStrea
     return 2 * ctx->T.n_sub;
   }
   if (ctx->T.dim == 3 && prec == 0 && !apply32 && ctx->df3_ok)
-    launch_schur3d_df(ctx->T, ctx->F, ctx->factor_df, io, s);
+    launch_schur3d_df(ctx->T, ctx->F, ctx->factor_df, ctx->df3_off, io, s);
   else
     launch_schur(ctx->T, ctx->F, prec, ctx->factor[prec], io, s);
   return ctx->T.n_sub;
@@ -381,10 +382,22 @@ int factor_check(ddel_ctx* ctx, int prec) {
   ctx->ck = 0;
   if (prec == 0) ctx->df_ok = ctx->df3_ok = false;
   if (prec == 0 && ctx->T.dim == 3 && ctx->opt.schur_mode == DDEL_SCHUR_AUTO) {
-    // 3D: the FP64 factor as FP32 (hi, lo) pairs for the double-float PCG apply
-    if (!ctx->factor_df && cudaMalloc(&ctx->factor_df, ctx->S.factor_elems * sizeof(float2) + 256) != cudaSuccess)
-      return fail(ctx, DDEL_ENOMEM, "double-float factor allocation");
-    launch_split_df((const double*)ctx->factor[0], ctx->factor_df, ctx->S.factor_elems, ctx->stream);
+    // 3D: the FP64 factor as FP32 (hi, lo) pairs, in the order of the sweeps,
+    // for the double-float PCG apply
+    if (!ctx->factor_df) {
+      std::vector<int64_t> off(ctx->S.n_sub);
+      const int64_t tot = df3_layout(ctx->S.subs.data(), ctx->S.n_sub, off.data());
+      if (cudaMalloc(&ctx->factor_df, tot * sizeof(float2) + 256) != cudaSuccess ||
+          cudaMalloc(&ctx->df3_off, off.size() * sizeof(int64_t)) != cudaSuccess) {
+        if (ctx->factor_df) cudaFree(ctx->factor_df);
+        ctx->factor_df = nullptr;
+        ctx->df3_off = nullptr;
+        return fail(ctx, DDEL_ENOMEM, "double-float factor allocation");
+      }
+      CK(cudaMemcpy(ctx->df3_off, off.data(), off.size() * sizeof(int64_t), cudaMemcpyHostToDevice));
+      CK(cudaMemsetAsync(ctx->factor_df, 0, tot * sizeof(float2), ctx->stream));
+    }
+    launch_build_df3(ctx->T, (const double*)ctx->factor[0], ctx->df3_off, ctx->factor_df, ctx->stream);
     ctx->launches += 1;
     CK(cudaGetLastError());
     ctx->df3_ok = true;
@@ -647,6 +660,7 @@ void ddel_destroy(ddel_ctx* ctx) {
   if (ctx->sexp32) cudaFree(ctx->sexp32);
   if (ctx->sexp_df) cudaFree(ctx->sexp_df);
   if (ctx->factor_df) cudaFree(ctx->factor_df);
+  if (ctx->df3_off) cudaFree(ctx->df3_off);
   if (ctx->h_st) cudaFreeHost(ctx->h_st);
   if (ctx->h_nrm) cudaFreeHost(ctx->h_nrm);
   if (ctx->h_err) cudaFreeHost(ctx->h_err);

@@ -429,123 +429,196 @@ __global__ void __launch_bounds__(kT3) schur3d_kernel(DevTables t, const T* __re
   schur_pcg_epilogue<kT3 / 32>(io, d[0], red);
 }
 
-// Double-float form of schur3d_kernel<double> for the PCG apply: the factor
-// blocks, element matrix, element factors and local vectors as FP32 (hi, lo)
-// pairs, every product in double-float arithmetic on the FP32 pipes (the FP64
-// form keeps this GPU's FP64 pipe 84 % busy); interior rows with no
-// neighbour on the subdomain boundary skip K_IG x (it vanishes there).
-__global__ void __launch_bounds__(kT3) schur3d_df_kernel(DevTables t, const double* __restrict__ Ke_g,
-                                                         const double* __restrict__ scale,
-                                                         const float2* __restrict__ factor, SchurIO io) {
+// --- Double-float PCG apply --------------------------------------------------
+// The FP64 operator of schur3d_kernel<double> with every product in
+// double-float arithmetic on the FP32 pipes (the FP64 form keeps this GPU's
+// FP64 pipe 84 % busy).  The factor is the stream-ordered copy of
+// launch_build_df3 (no padding rows; a row-major copy for the backward sweep),
+// read once per apply in the order of use, each block step prefetched into L2
+// (bulk prefetch) one step ahead.  Each warp serves 16 rows: lanes l and l + 16
+// take the two halves of a row's dot product (coalesced over the rows) and add
+// them by one shuffle; 8 loads per thread are in flight.
+constexpr int kT3D = 384;  // 12 warps x 16 rows: blocks of up to 192 rows in one pass
+
+__host__ __device__ __forceinline__ int64_t pad16(int64_t v) { return (v + 15) & ~int64_t(15); }
+
+// L2 prefetch of [p, p + bytes) (16-byte aligned, multiple of 16 bytes), 16 KB
+// per thread.
+__device__ __forceinline__ void prefetch_l2(const float2* p, int64_t bytes) {
+  for (int64_t o = (int64_t)threadIdx.x << 14; o < bytes; o += (int64_t)blockDim.x << 14) {
+    const uint32_t b = (uint32_t)min(bytes - o, (int64_t)16384);
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"((const char*)p + o), "r"(b) : "memory");
+  }
+}
+
+// (hi, lo) += sum_{j = j0}^{j1 - 1} M[a_j] v[j] with a_{j0} = a, a_{j+1} = a_j + st_j,
+// st_{j+1} = st_j + dst (dst 0: a strided column; -1, +1: the packed triangles).
+__device__ __forceinline__ void df_dot(const float2* __restrict__ M, int a, int st, int dst,
+                                       const float2* v, int j0, int j1, float& hi, float& lo) {
+  int j = j0;
+  for (; j + 8 <= j1; j += 8) {
+    float2 e[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      e[u] = __ldcs(M + a);
+      a += st;
+      st += dst;
+    }
+#pragma unroll
+    for (int u = 0; u < 8; ++u) df_mad(hi, lo, e[u], v[j + u]);
+  }
+  for (; j < j1; ++j) {
+    df_mad(hi, lo, __ldcs(M + a), v[j]);
+    a += st;
+    st += dst;
+  }
+}
+
+// Sum of the partials of lanes l and l ^ 16 (lanes 0-15 hold the result used).
+__device__ __forceinline__ void df_half_sum(float& hi, float& lo) {
+  const float ph = __shfl_xor_sync(0xffffffffu, hi, 16), pl = __shfl_xor_sync(0xffffffffu, lo, 16);
+  df_add2(hi, lo, ph, pl);
+}
+
+__global__ void __launch_bounds__(kT3D, 3) schur3d_df_kernel(DevTables t, const double* __restrict__ Ke_g,
+                                                             const double* __restrict__ scale,
+                                                             const float2* __restrict__ factor,
+                                                             const int64_t* __restrict__ off, SchurIO io) {
   if (io.done && *io.done) return;
   schur_pcg_prologue(io);
-  const int BP = t.BP, PC = BP * BP, PD = BP * (BP + 1) / 2, STAGE = PC + PD;
   const int sub = blockIdx.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int hh = lane >> 4, hl = lane & 15;
   const SubInfo si = t.subs[sub];
-  const int s = t.s, s1 = s + 1, nloc = s1 * s1 * s1;
+  const int s = t.s, s1 = s + 1, nloc = s1 * s1 * s1, NM = t.BP;
+  const int n = si.bsz, nb = si.nb, nh = (n + 1) / 2;
+  const int szC = (int)pad16((int64_t)n * n), szD = (int)pad16((int64_t)n * (n + 1) / 2);
+  const float2* fw = factor + off[sub];
+  const float2* bw = fw + (int64_t)nb * szD + (int64_t)(nb - 1) * szC;
+  prefetch_l2(fw, (int64_t)szD * 8);  // D_0
   extern __shared__ __align__(128) unsigned char smem_df3[];
-  float2* ybuf = reinterpret_cast<float2*>(smem_df3);  // nb_max * BP
-  float2* vbuf = ybuf + t.nb_max * BP;                  // BP
-  float2* xloc = vbuf + BP;                             // 3 * nloc
+  float2* ybuf = reinterpret_cast<float2*>(smem_df3);  // nb_max * NM: w_k, then y_k, then t_k
+  float2* vbuf = ybuf + t.nb_max * NM;                  // NM
+  float2* xloc = vbuf + NM;                             // 3 * nloc
   float2* ke = xloc + 3 * nloc;                         // 576
   float2* sc = ke + 576;                                // s^3
-  for (int i = tid; i < 576; i += kT3) ke[i] = df_from(Ke_g[i]);
-  for (int i = tid; i < s * s * s; i += kT3) {
+  for (int i = tid; i < 576; i += kT3D) ke[i] = df_from(Ke_g[i]);
+  for (int i = tid; i < s * s * s; i += kT3D) {
     const int a = i / (s * s), b = (i / s) % s, c = i % s;
     sc[i] = df_from(scale[((int64_t)(si.lo[0] + a) * t.ne[1] + si.lo[1] + b) * t.ne[2] + si.lo[2] + c]);
   }
-  for (int i = tid; i < 3 * nloc; i += kT3) xloc[i] = make_float2(0.f, 0.f);
+  for (int i = tid; i < 3 * nloc; i += kT3D) xloc[i] = make_float2(0.f, 0.f);
   __syncthreads();
   const bool have_x = io.x != nullptr;
   if (have_x)
-    for (int r = tid; r < si.n_ring; r += kT3)
+    for (int r = tid; r < si.n_ring; r += kT3D)
       xloc[t.ring_loc[si.ring_off + r]] = df_from(io.x[t.ring_gidx[si.ring_off + r]]);
   __syncthreads();
-  const int nb = si.nb;
-  const float2* fb = factor + si.factor_off;
+  // w_k = f_I - K_IG x for every plane (K_IG x vanishes on rows with no
+  // neighbour on the subdomain boundary)
+  for (int q = tid; q < nb * n; q += kT3D) {
+    const int k = q / n, r = q % n;
+    int x, y, z, c;
+    row_node3(si, k, r, x, y, z, c);
+    const int64_t dof = 3 * node3(t, x, y, z) + c;
+    float2 v = make_float2(0.f, 0.f);
+    if (!t.fixed[dof]) {
+      if (io.f) v = df_from(io.f[dof]);
+      const int a = x - si.lo[0], b = y - si.lo[1], cz = z - si.lo[2];
+      const bool near = a <= 1 || a >= s - 1 || b <= 1 || b >= s - 1 || cz <= 1 || cz >= s - 1;
+      if (have_x && near) {
+        float eh = 0.f, el = 0.f;
+        ebe_local3d_df(ke, sc, xloc, s, a, b, cz, c, eh, el);
+        df_add2(v.x, v.y, -eh, -el);
+      }
+    }
+    ybuf[k * NM + r] = v;
+  }
+  __syncthreads();
   // forward: y_k = D_k (w_k - C_k y_{k-1})
   for (int k = 0; k < nb; ++k) {
-    const float2* Ck = fb + (int64_t)k * STAGE;
-    const float2* Dk = Ck + PC;
-    for (int r = tid; r < BP; r += kT3) {
-      float2 v = make_float2(0.f, 0.f);
-      if (r < si.bsz) {
-        int x, y, z, c;
-        row_node3(si, k, r, x, y, z, c);
-        const int64_t dof = 3 * node3(t, x, y, z) + c;
-        if (!t.fixed[dof]) {
-          if (io.f) v = df_from(io.f[dof]);
-          const int a = x - si.lo[0], b = y - si.lo[1], cz = z - si.lo[2];
-          const bool near = a <= 1 || a >= s - 1 || b <= 1 || b >= s - 1 || cz <= 1 || cz >= s - 1;
-          if (have_x && near) {
-            float eh = 0.f, el = 0.f;
-            ebe_local3d_df(ke, sc, xloc, s, a, b, cz, c, eh, el);
-            df_add2(v.x, v.y, -eh, -el);
-          }
-        }
+    const float2* D = fw + (int64_t)k * (szC + szD);
+    if (k > 0) prefetch_l2(D, (int64_t)szD * 8);
+    for (int r0 = 0; r0 < n; r0 += kT3D / 2) {
+      const int r = r0 + warp * 16 + hl;
+      float ah = 0.f, al = 0.f;
+      if (k > 0 && r < n) {
+        const int j0 = hh ? nh : 0, j1 = hh ? n : nh;
+        df_dot(D - szC, j0 * n + r, n, 0, ybuf + (k - 1) * NM, j0, j1, ah, al);
       }
-      if (k > 0) {
-        const float2* yp = ybuf + (k - 1) * BP;
-        float ah = 0.f, al = 0.f;
-#pragma unroll 4
-        for (int j = 0; j < BP; ++j) df_mad(ah, al, Ck[(int64_t)j * BP + r], yp[j]);
-        df_add2(v.x, v.y, -ah, -al);
+      df_half_sum(ah, al);
+      if (r < n && hh == 0) {
+        float2 w = ybuf[k * NM + r];
+        df_add2(w.x, w.y, -ah, -al);
+        vbuf[r] = w;
       }
-      vbuf[r] = v;
     }
     __syncthreads();
-    for (int r = tid; r < BP; r += kT3) {
+    if (k + 1 < nb)
+      prefetch_l2(D + szD, (int64_t)szC * 8);  // C_{k+1}
+    else
+      prefetch_l2(bw, (int64_t)szD * 8);  // the backward sweep's D_{nb-1}
+    for (int r0 = 0; r0 < n; r0 += kT3D / 2) {
+      const int r = r0 + warp * 16 + hl;
       float ah = 0.f, al = 0.f;
-      for (int j = 0; j <= r; ++j) df_mad(ah, al, Dk[j * BP - j * (j - 1) / 2 + (r - j)], vbuf[j]);
-      ybuf[k * BP + r] = make_float2(ah, al);
+      if (r < n) {
+        const int j0 = hh ? nh : 0, j1 = min(hh ? n : nh, r + 1);
+        if (j0 < j1) df_dot(D, j0 * n - j0 * (j0 - 1) / 2 + (r - j0), n - j0 - 1, -1, vbuf, j0, j1, ah, al);
+      }
+      df_half_sum(ah, al);
+      if (r < n && hh == 0) ybuf[k * NM + r] = make_float2(ah, al);
     }
     __syncthreads();
   }
-  // backward: t_k = D_k^T (y_k - C_{k+1}^T t_{k+1}); one warp per output entry
+  // backward: t_k = D_k^T (y_k - C_{k+1}^T t_{k+1}), one thread pair per output
   for (int k = nb - 1; k >= 0; --k) {
-    const float2* Dk = fb + (int64_t)k * STAGE + PC;
-    const float2* Cn = fb + (int64_t)(k + 1) * STAGE;
-    for (int j = warp; j < BP; j += kT3 / 32) {
+    const float2* Db = bw + (int64_t)(nb - 1 - k) * (szC + szD);
+    if (k + 1 < nb) prefetch_l2(Db, (int64_t)szD * 8);
+    for (int j0 = 0; j0 < n; j0 += kT3D / 2) {
+      const int j = j0 + warp * 16 + hl;
       float ah = 0.f, al = 0.f;
-      if (k + 1 < nb) {
-        const float2* tn = ybuf + (k + 1) * BP;
-        for (int r = lane; r < BP; r += 32) df_mad(ah, al, Cn[(int64_t)j * BP + r], tn[r]);
+      if (k + 1 < nb && j < n) {
+        const int i0 = hh ? nh : 0, i1 = hh ? n : nh;
+        df_dot(Db - szC, i0 * n + j, n, 0, ybuf + (k + 1) * NM, i0, i1, ah, al);
       }
-      df_warp_sum(ah, al);
-      if (lane == 0) {
-        float2 v = ybuf[k * BP + j];
-        df_add2(v.x, v.y, -ah, -al);
-        vbuf[j] = v;
+      df_half_sum(ah, al);
+      if (j < n && hh == 0) {
+        float2 w = ybuf[k * NM + j];
+        df_add2(w.x, w.y, -ah, -al);
+        vbuf[j] = w;
       }
     }
     __syncthreads();
-    for (int j = warp; j < BP; j += kT3 / 32) {
-      const float2* col = Dk + (j * BP - j * (j - 1) / 2);
+    if (k > 0) prefetch_l2(Db + szD, (int64_t)szC * 8);  // C_k, row-major
+    for (int j0 = 0; j0 < n; j0 += kT3D / 2) {
+      const int j = j0 + warp * 16 + hl;
       float ah = 0.f, al = 0.f;
-      for (int i = j + lane; i < BP; i += 32) df_mad(ah, al, col[i - j], vbuf[i]);
-      df_warp_sum(ah, al);
-      if (lane == 0) ybuf[k * BP + j] = make_float2(ah, al);
+      if (j < n) {
+        const int i0 = max(j, hh ? nh : 0), i1 = hh ? n : nh;
+        if (i0 < i1) df_dot(Db, i0 * (i0 + 1) / 2 + j, i0 + 1, 1, vbuf, i0, i1, ah, al);
+      }
+      df_half_sum(ah, al);
+      if (j < n && hh == 0) ybuf[k * NM + j] = make_float2(ah, al);
     }
     __syncthreads();
   }
   // outputs: t into the local closure, y = (K^(i) [t; x])_G on the ring
   if (io.u_out || io.ring_out) {
-    for (int k = 0; k < nb; ++k)
-      for (int r = tid; r < si.bsz; r += kT3) {
-        int x, y, z, c;
-        row_node3(si, k, r, x, y, z, c);
-        const int64_t dof = 3 * node3(t, x, y, z) + c;
-        if (t.fixed[dof]) continue;
-        const float2 tv = ybuf[k * BP + r];
-        if (io.u_out) io.u_out[dof] = (double)tv.x + (double)tv.y;
-        xloc[(((x - si.lo[0]) * s1 + (y - si.lo[1])) * s1 + (z - si.lo[2])) * 3 + c] = tv;
-      }
+    for (int q = tid; q < nb * n; q += kT3D) {
+      const int k = q / n, r = q % n;
+      int x, y, z, c;
+      row_node3(si, k, r, x, y, z, c);
+      const int64_t dof = 3 * node3(t, x, y, z) + c;
+      if (t.fixed[dof]) continue;
+      const float2 tv = ybuf[k * NM + r];
+      if (io.u_out) io.u_out[dof] = (double)tv.x + (double)tv.y;
+      xloc[(((x - si.lo[0]) * s1 + (y - si.lo[1])) * s1 + (z - si.lo[2])) * 3 + c] = tv;
+    }
     __syncthreads();
   }
   double d[1] = {0.0};
   if (io.ring_out) {
     double* out = reinterpret_cast<double*>(io.ring_out);
-    for (int r = tid; r < si.n_ring; r += kT3) {
+    for (int r = tid; r < si.n_ring; r += kT3D) {
       const int loc = t.ring_loc[si.ring_off + r];
       const int node = loc / 3, c = loc % 3;
       const int a = node / (s1 * s1), b = (node / s1) % s1, cc = node % s1;
@@ -556,8 +629,43 @@ __global__ void __launch_bounds__(kT3) schur3d_df_kernel(DevTables t, const doub
       d[0] += ((double)xloc[loc].x + (double)xloc[loc].y) * y;
     }
   }
-  __shared__ double red[kT3 / 32];
-  schur_pcg_epilogue<kT3 / 32>(io, d[0], red);
+  __shared__ double red[kT3D / 32];
+  schur_pcg_epilogue<kT3D / 32>(io, d[0], red);
+}
+
+// FP64 factor (padded planes of launch_factor3d) -> the stream-ordered
+// double-float copy; one CTA per subdomain.
+__global__ void __launch_bounds__(256) build_df3_kernel(DevTables t, const double* __restrict__ factor,
+                                                        const int64_t* __restrict__ off,
+                                                        float2* __restrict__ out) {
+  const SubInfo si = t.subs[blockIdx.x];
+  const int BP = t.BP, PC = BP * BP, STAGE = PC + BP * (BP + 1) / 2;
+  const int n = si.bsz, nb = si.nb;
+  const int64_t szC = pad16((int64_t)n * n), szD = pad16((int64_t)n * (n + 1) / 2);
+  float2* fw = out + off[blockIdx.x];
+  float2* bw = fw + nb * szD + (nb - 1) * szC;
+  const double* fb = factor + si.factor_off;
+  for (int k = 0; k < nb; ++k) {
+    const double* Ck = fb + (int64_t)k * STAGE;
+    const double* Dk = Ck + PC;
+    float2* Df = fw + k * (szC + szD);
+    float2* Cf = Df - szC;
+    float2* Db = bw + (nb - 1 - k) * (szC + szD);
+    float2* Cb = bw + (nb - k) * (szC + szD) - szC;  // used by the backward step k - 1
+    for (int q = threadIdx.x; q < n * n; q += blockDim.x) {
+      const int j = q / n, r = q % n;
+      if (k > 0) {
+        const float2 c = df_from(Ck[(int64_t)j * BP + r]);
+        Cf[(int64_t)j * n + r] = c;
+        Cb[(int64_t)r * n + j] = c;
+      }
+      if (r >= j) {
+        const float2 d = df_from(Dk[(int64_t)j * BP - j * (j - 1) / 2 + (r - j)]);
+        Df[(int64_t)j * n - j * (j - 1) / 2 + (r - j)] = d;
+        Db[(int64_t)r * (r + 1) / 2 + j] = d;
+      }
+    }
+  }
 }
 
 }  // namespace
@@ -576,9 +684,24 @@ void launch_factor3d(const DevTables& t, const DevFields& fld, int precision, vo
 
 size_t schur3d_smem(const DevTables& t, int precision);
 
-void launch_schur3d_df(const DevTables& t, const DevFields& fld, const float2* factor, const SchurIO& io,
-                       cudaStream_t st) {
-  schur3d_df_kernel<<<t.n_sub, kT3, schur3d_smem(t, 0), st>>>(t, t.Ke64, fld.scale64, factor, io);
+int64_t df3_layout(const SubInfo* subs, int n_sub, int64_t* off) {
+  int64_t tot = 0;
+  for (int i = 0; i < n_sub; ++i) {
+    const int64_t n = subs[i].bsz, nb = subs[i].nb;
+    off[i] = tot;
+    if (nb > 0) tot += 2 * (nb * pad16(n * (n + 1) / 2) + (nb - 1) * pad16(n * n));
+  }
+  return tot;
+}
+
+void launch_build_df3(const DevTables& t, const double* factor, const int64_t* off, float2* out,
+                      cudaStream_t st) {
+  build_df3_kernel<<<t.n_sub, 256, 0, st>>>(t, factor, off, out);
+}
+
+void launch_schur3d_df(const DevTables& t, const DevFields& fld, const float2* factor, const int64_t* off,
+                       const SchurIO& io, cudaStream_t st) {
+  schur3d_df_kernel<<<t.n_sub, kT3D, schur3d_smem(t, 0), st>>>(t, t.Ke64, fld.scale64, factor, off, io);
 }
 
 size_t schur3d_smem(const DevTables& t, int precision) {

@@ -113,9 +113,19 @@ void launch_factor3d(const DevTables& t, const DevFields& fld, int precision, vo
                      void* work, int* err, int* bad_sub, cudaStream_t st);
 void launch_schur3d(const DevTables& t, const DevFields& fld, int precision, const void* factor,
                     const SchurIO& io, cudaStream_t st);
-// FP64 operator in double-float arithmetic: factor as FP32 (hi, lo) pairs.
-void launch_schur3d_df(const DevTables& t, const DevFields& fld, const float2* factor, const SchurIO& io,
-                       cudaStream_t st);
+// FP64 operator in double-float arithmetic on a stream-ordered copy of the
+// FP64 factor as FP32 (hi, lo) pairs: per subdomain (n = bsz rows per plane, nb
+// planes, blocks padded to 16 pairs) the forward sweep's blocks D_0, C_1, D_1,
+// ..., C_{nb-1}, D_{nb-1} (C column-major n x n, D packed lower column-major),
+// then the backward sweep's D_{nb-1}, C_{nb-1}, D_{nb-2}, ..., C_1, D_0 (C
+// row-major, D packed lower row-major), so that both sweeps read it in order
+// with one thread per output row.  df3_layout fills the per-subdomain offsets
+// (n_sub entries) and returns the total number of pairs.
+int64_t df3_layout(const SubInfo* subs, int n_sub, int64_t* off);
+void launch_build_df3(const DevTables& t, const double* factor, const int64_t* off, float2* out,
+                      cudaStream_t st);
+void launch_schur3d_df(const DevTables& t, const DevFields& fld, const float2* factor, const int64_t* off,
+                       const SchurIO& io, cudaStream_t st);
 cudaError_t configure_kernels3d();
 // Per-subdomain solve kernel (condense / Schur / back-substitution forms).
 void launch_schur(const DevTables& t, const DevFields& fld, int precision, const void* factor,
