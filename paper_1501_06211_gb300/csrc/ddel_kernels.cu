@@ -332,10 +332,12 @@ __global__ void __launch_bounds__(32) schur2d_kernel(DevTables t, const T* __res
   __syncwarp();
 
   bool ok = true;
+  int cfail = 0;  // the chunk whose wait ran out
   // ---- forward substitution: y_k = D_k (w_k - C_k y_{k-1})
   for (int k = 0; k < nb; ++k) {
     const int st = k % NS;
     ok = __all_sync(0xffffffffu, mbar_wait(&bar[st], (k / NS) & 1));
+    cfail = k;
     if (!ok) break;
     const T* Cs = stage + st * STAGE;
     const T* Ds = Cs + PC;
@@ -391,6 +393,7 @@ __global__ void __launch_bounds__(32) schur2d_kernel(DevTables t, const T* __res
   for (int kk = 0; ok && kk < nb; ++kk) {
     const int k = nb - 1 - kk, c = nb + kk, st = c % NS;
     ok = __all_sync(0xffffffffu, mbar_wait(&bar[st], (c / NS) & 1));
+    cfail = c;
     if (!ok) break;
     const T* Ds = stage + st * STAGE;
     const T* Cs = Ds + PD;
@@ -435,7 +438,12 @@ __global__ void __launch_bounds__(32) schur2d_kernel(DevTables t, const T* __res
     }
   }
   if (!ok) {
-    if (lane == 0 && io.err) atomicExch(io.err, kErrTimeout);
+    // bounded wait for this CTA's copies still in flight (chunks cfail ..
+    // cfail + NS - 1 were issued), then report
+    if (lane == 0) {
+      for (int c = cfail; c < cfail + NS && c < nchunks; ++c) mbar_wait(&bar[c % NS], (c / NS) & 1);
+      if (io.err) atomicExch(io.err, kErrTimeout);
+    }
     return;
   }
   // ---- outputs

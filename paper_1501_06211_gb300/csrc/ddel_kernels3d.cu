@@ -434,38 +434,31 @@ __global__ void __launch_bounds__(kT3) schur3d_kernel(DevTables t, const T* __re
 // double-float arithmetic on the FP32 pipes (the FP64 form keeps this GPU's
 // FP64 pipe 84 % busy).  The factor is the stream-ordered copy of
 // launch_build_df3 (no padding rows; a row-major copy for the backward sweep),
-// read once per apply in the order of use, each block step prefetched into L2
-// (bulk prefetch) one step ahead.  Each warp serves 16 rows: lanes l and l + 16
-// take the two halves of a row's dot product (coalesced over the rows) and add
-// them by one shuffle; 8 loads per thread are in flight.
+// read once per apply in the order of use with streaming (evict-first) loads.
+// Each warp serves 16 rows: lanes l and l + 16 take the two halves of a row's
+// dot product (coalesced over the rows) and add them by one shuffle; 12 loads
+// per thread are in flight.  (An L2 bulk prefetch of the next block step,
+// 75 MB over all subdomains, evicted lines before their use: slower.)
 constexpr int kT3D = 384;  // 12 warps x 16 rows: blocks of up to 192 rows in one pass
 
 __host__ __device__ __forceinline__ int64_t pad16(int64_t v) { return (v + 15) & ~int64_t(15); }
 
-// L2 prefetch of [p, p + bytes) (16-byte aligned, multiple of 16 bytes), 16 KB
-// per thread.
-__device__ __forceinline__ void prefetch_l2(const float2* p, int64_t bytes) {
-  for (int64_t o = (int64_t)threadIdx.x << 14; o < bytes; o += (int64_t)blockDim.x << 14) {
-    const uint32_t b = (uint32_t)min(bytes - o, (int64_t)16384);
-    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"((const char*)p + o), "r"(b) : "memory");
-  }
-}
-
 // (hi, lo) += sum_{j = j0}^{j1 - 1} M[a_j] v[j] with a_{j0} = a, a_{j+1} = a_j + st_j,
-// st_{j+1} = st_j + dst (dst 0: a strided column; -1, +1: the packed triangles).
+// st_{j+1} = st_j + dst (dst 0: a strided column; -1, +1: the packed triangles);
+// twelve loads issued ahead of their products.
 __device__ __forceinline__ void df_dot(const float2* __restrict__ M, int a, int st, int dst,
                                        const float2* v, int j0, int j1, float& hi, float& lo) {
   int j = j0;
-  for (; j + 8 <= j1; j += 8) {
-    float2 e[8];
+  for (; j + 12 <= j1; j += 12) {
+    float2 e[12];
 #pragma unroll
-    for (int u = 0; u < 8; ++u) {
+    for (int u = 0; u < 12; ++u) {
       e[u] = __ldcs(M + a);
       a += st;
       st += dst;
     }
 #pragma unroll
-    for (int u = 0; u < 8; ++u) df_mad(hi, lo, e[u], v[j + u]);
+    for (int u = 0; u < 12; ++u) df_mad(hi, lo, e[u], v[j + u]);
   }
   for (; j < j1; ++j) {
     df_mad(hi, lo, __ldcs(M + a), v[j]);
@@ -494,7 +487,6 @@ __global__ void __launch_bounds__(kT3D, 3) schur3d_df_kernel(DevTables t, const 
   const int szC = (int)pad16((int64_t)n * n), szD = (int)pad16((int64_t)n * (n + 1) / 2);
   const float2* fw = factor + off[sub];
   const float2* bw = fw + (int64_t)nb * szD + (int64_t)(nb - 1) * szC;
-  prefetch_l2(fw, (int64_t)szD * 8);  // D_0
   extern __shared__ __align__(128) unsigned char smem_df3[];
   float2* ybuf = reinterpret_cast<float2*>(smem_df3);  // nb_max * NM: w_k, then y_k, then t_k
   float2* vbuf = ybuf + t.nb_max * NM;                  // NM
@@ -537,7 +529,6 @@ __global__ void __launch_bounds__(kT3D, 3) schur3d_df_kernel(DevTables t, const 
   // forward: y_k = D_k (w_k - C_k y_{k-1})
   for (int k = 0; k < nb; ++k) {
     const float2* D = fw + (int64_t)k * (szC + szD);
-    if (k > 0) prefetch_l2(D, (int64_t)szD * 8);
     for (int r0 = 0; r0 < n; r0 += kT3D / 2) {
       const int r = r0 + warp * 16 + hl;
       float ah = 0.f, al = 0.f;
@@ -553,10 +544,6 @@ __global__ void __launch_bounds__(kT3D, 3) schur3d_df_kernel(DevTables t, const 
       }
     }
     __syncthreads();
-    if (k + 1 < nb)
-      prefetch_l2(D + szD, (int64_t)szC * 8);  // C_{k+1}
-    else
-      prefetch_l2(bw, (int64_t)szD * 8);  // the backward sweep's D_{nb-1}
     for (int r0 = 0; r0 < n; r0 += kT3D / 2) {
       const int r = r0 + warp * 16 + hl;
       float ah = 0.f, al = 0.f;
@@ -572,7 +559,6 @@ __global__ void __launch_bounds__(kT3D, 3) schur3d_df_kernel(DevTables t, const 
   // backward: t_k = D_k^T (y_k - C_{k+1}^T t_{k+1}), one thread pair per output
   for (int k = nb - 1; k >= 0; --k) {
     const float2* Db = bw + (int64_t)(nb - 1 - k) * (szC + szD);
-    if (k + 1 < nb) prefetch_l2(Db, (int64_t)szD * 8);
     for (int j0 = 0; j0 < n; j0 += kT3D / 2) {
       const int j = j0 + warp * 16 + hl;
       float ah = 0.f, al = 0.f;
@@ -588,7 +574,6 @@ __global__ void __launch_bounds__(kT3D, 3) schur3d_df_kernel(DevTables t, const 
       }
     }
     __syncthreads();
-    if (k > 0) prefetch_l2(Db + szD, (int64_t)szC * 8);  // C_k, row-major
     for (int j0 = 0; j0 < n; j0 += kT3D / 2) {
       const int j = j0 + warp * 16 + hl;
       float ah = 0.f, al = 0.f;
