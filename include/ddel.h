@@ -120,7 +120,7 @@ typedef struct {
   int x0_mode;         /* ddel_x0_mode of ddel_solve (ZERO) */
   int schur_mode;      /* ddel_schur_mode (AUTO): EXPLICIT/AUTO form each local Schur
                           complement S_i after the factorisation where the ring fits
-                          (2D, sub <= 16) and apply it as one dense product per PCG
+                          (2D, sub <= 32) and apply it as one dense product per PCG
                           iteration; IMPLICIT applies it by block substitution */
   int use_graph;       /* capture PCG iterations in a CUDA graph (1) */
   int check_every;     /* PCG iterations between host convergence checks (16) */

@@ -33,6 +33,7 @@ struct ddel_ctx {
   void* factor[2] = {nullptr, nullptr};
   void* work3d[2] = {nullptr, nullptr};  // 3D factorisation scratch
   void* sexp[2] = {nullptr, nullptr};  // explicit local Schur complements (2D)
+  void* form_work[2] = {nullptr, nullptr};  // W = L^-1 K_IG scratch of the widest rings
   float* sexp32 = nullptr;             // MIXED: FP64-formed S_i rounded to FP32
   bool mixed_ready = false;
   float2* sexp_df = nullptr;           // FP64 S_i as FP32 (hi, lo) pairs (double-float apply)
@@ -361,7 +362,13 @@ int factor_launch(ddel_ctx* ctx, int prec) {
       cudaError_t e = cudaMalloc(&ctx->sexp[prec], (size_t)ctx->T.n_sub * NR * NR * (prec ? 4 : 8));
       if (e != cudaSuccess) return fail(ctx, DDEL_ENOMEM, "explicit Schur allocation");
     }
-    launch_schur_form(ctx->T, ctx->F, prec, ctx->factor[prec], ctx->sexp[prec], ctx->stream);
+    const size_t we = explicit_form_work_elems(ctx->T);
+    if (we && !ctx->form_work[prec]) {
+      cudaError_t e = cudaMalloc(&ctx->form_work[prec], we * (prec ? 4 : 8));
+      if (e != cudaSuccess) return fail(ctx, DDEL_ENOMEM, "explicit Schur scratch allocation");
+    }
+    launch_schur_form(ctx->T, ctx->F, prec, ctx->factor[prec], ctx->form_work[prec], ctx->sexp[prec],
+                      ctx->stream);
     ctx->launches += 1;
     CK(cudaGetLastError());
   }
@@ -654,6 +661,8 @@ void ddel_destroy(ddel_ctx* ctx) {
   for (void* p : ctx->factor)
     if (p) cudaFree(p);
   for (void* p : ctx->sexp)
+    if (p) cudaFree(p);
+  for (void* p : ctx->form_work)
     if (p) cudaFree(p);
   for (void* p : ctx->work3d)
     if (p) cudaFree(p);

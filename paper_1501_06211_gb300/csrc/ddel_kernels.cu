@@ -627,6 +627,144 @@ __global__ void __launch_bounds__(256) schur_form2d_kernel(DevTables t, const T*
   }
 }
 
+// Explicit S_i for rings too wide for one CTA's registers and shared memory
+// (NR = 256: up to 32 x 32-element subdomains, planes of BP = 64 or 96 rows), in two
+// passes through a global scratch W (per subdomain nb_max planes of BP x NR):
+//  1. form_w2d_kernel, one CTA per (subdomain, group of GC ring columns):
+//     W_k = D_k (B_k - C_k W_{k-1}) with B_k the K_IG rows of plane k, the block
+//     forward substitution of schur_form2d_kernel restricted to GC columns;
+//  2. form_syrk2d_kernel, one CTA per (subdomain, TQ x TQ tile (qa <= qb)):
+//     S tile = K_GG tile - sum_k W_k[:, qa]^T W_k[:, qb], mirrored below the
+//     diagonal.
+template <typename T, int BP, int NR, int GC>
+__global__ void __launch_bounds__(256) form_w2d_kernel(DevTables t, const T* __restrict__ Ke_g,
+                                                       const T* __restrict__ scale,
+                                                       const T* __restrict__ factor, T* __restrict__ W) {
+  constexpr int PC = BP * BP, PD = BP * (BP + 1) / 2, STAGE = PC + PD;
+  const int sub = blockIdx.x, g = blockIdx.y, tid = threadIdx.x;
+  const SubInfo si = t.subs[sub];
+  const int s = t.s;
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  T* Cs = reinterpret_cast<T*>(smem_raw);  // PC
+  T* Ds = Cs + PC;                          // PD
+  T* Wp = Ds + PD;                          // BP x GC: W_{k-1}, then W_k
+  T* Tb = Wp + BP * GC;                     // BP x GC
+  T* ke = Tb + BP * GC;                     // 64
+  T* sc = ke + 64;                          // s*s
+  int* rloc = reinterpret_cast<int*>(sc + s * s);  // GC
+  for (int i = tid; i < 64; i += 256) ke[i] = Ke_g[i];
+  for (int i = tid; i < s * s; i += 256)
+    sc[i] = scale[(int64_t)(si.lo[0] + i / s) * t.ne[1] + si.lo[1] + i % s];
+  for (int j = tid; j < GC; j += 256) {
+    const int jr = g * GC + j;
+    rloc[j] = jr < si.n_ring ? t.ring_loc[si.ring_off + jr] : -1;
+  }
+  for (int i = tid; i < BP * GC; i += 256) Wp[i] = T(0);
+  __syncthreads();
+  const T* fb = factor + si.factor_off;
+  T* Wout = W + (int64_t)sub * t.nb_max * BP * NR;
+  for (int k = 0; k < si.nb; ++k) {
+    const T* src = fb + (int64_t)k * STAGE;
+    for (int i = tid; i < STAGE; i += 256) {
+      if (i < PC) {
+        if (k > 0) Cs[i] = src[i];
+      } else {
+        Ds[i - PC] = src[i];
+      }
+    }
+    for (int i = tid; i < BP * GC; i += 256) Tb[i] = kig_entry2d<T>(t, si, ke, sc, k, i / GC, rloc[i % GC]);
+    __syncthreads();
+    if (k > 0) {  // T = B_k - C_k W_{k-1}
+      for (int i = tid; i < BP * GC; i += 256) {
+        const int r = i / GC, j = i % GC;
+        T v = Tb[i];
+#pragma unroll 8
+        for (int m = 0; m < BP; ++m) v -= Cs[m * BP + r] * Wp[m * GC + j];
+        Tb[i] = v;
+      }
+      __syncthreads();
+    }
+    for (int i = tid; i < BP * GC; i += 256) {  // W_k = D_k T
+      const int r = i / GC, j = i % GC;
+      T v = T(0);
+      for (int m = 0; m <= r; ++m) v += Ds[m * BP - m * (m - 1) / 2 + (r - m)] * Tb[m * GC + j];
+      Wp[i] = v;
+      Wout[((int64_t)k * BP + r) * NR + g * GC + j] = v;
+    }
+    __syncthreads();
+  }
+}
+
+template <typename T, int BP, int NR, int TQ>
+__global__ void __launch_bounds__(256) form_syrk2d_kernel(DevTables t, const T* __restrict__ Ke_g,
+                                                          const T* __restrict__ scale,
+                                                          const T* __restrict__ W, T* __restrict__ Sexp) {
+  constexpr int NQ = NR / TQ, TA = TQ / 16;
+  const int sub = blockIdx.x, tid = threadIdx.x;
+  int qa = 0, q = blockIdx.y;  // tile index -> (qa, qb), qa <= qb
+  while (q >= NQ - qa) {
+    q -= NQ - qa;
+    ++qa;
+  }
+  const int qb = qa + q;
+  const SubInfo si = t.subs[sub];
+  const int s = t.s;
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  T* Wa = reinterpret_cast<T*>(smem_raw);  // BP x TQ
+  T* Wb = Wa + BP * TQ;                     // BP x TQ
+  T* ke = Wb + BP * TQ;                     // 64
+  T* sc = ke + 64;                          // s*s
+  int* rl = reinterpret_cast<int*>(sc + s * s);  // 2 TQ: ring rows of qa, then of qb
+  for (int i = tid; i < 64; i += 256) ke[i] = Ke_g[i];
+  for (int i = tid; i < s * s; i += 256)
+    sc[i] = scale[(int64_t)(si.lo[0] + i / s) * t.ne[1] + si.lo[1] + i % s];
+  for (int j = tid; j < 2 * TQ; j += 256) {
+    const int jr = (j < TQ ? qa : qb) * TQ + j % TQ;
+    rl[j] = jr < si.n_ring ? t.ring_loc[si.ring_off + jr] : -1;
+  }
+  __syncthreads();
+  // thread (ty, tx) owns rows ty + 16 a of block qa and columns tx + 16 b of qb
+  const int ty = tid / 16, tx = tid % 16;
+  T acc[TA][TA];
+#pragma unroll
+  for (int a = 0; a < TA; ++a)
+#pragma unroll
+    for (int b = 0; b < TA; ++b) acc[a][b] = kgg_entry2d<T>(s, ke, sc, rl[ty + 16 * a], rl[TQ + tx + 16 * b]);
+  const T* Win = W + (int64_t)sub * t.nb_max * BP * NR;
+  for (int k = 0; k < si.nb; ++k) {
+    for (int i = tid; i < BP * TQ; i += 256) {
+      const int m = i / TQ, j = i % TQ;
+      const T* row = Win + ((int64_t)k * BP + m) * NR;
+      Wa[i] = row[qa * TQ + j];
+      Wb[i] = row[qb * TQ + j];
+    }
+    __syncthreads();
+#pragma unroll 4
+    for (int m = 0; m < BP; ++m) {
+      T wi[TA], wj[TA];
+#pragma unroll
+      for (int a = 0; a < TA; ++a) {
+        wi[a] = Wa[m * TQ + ty + 16 * a];
+        wj[a] = Wb[m * TQ + tx + 16 * a];
+      }
+#pragma unroll
+      for (int a = 0; a < TA; ++a)
+#pragma unroll
+        for (int b = 0; b < TA; ++b) acc[a][b] -= wi[a] * wj[b];
+    }
+    __syncthreads();
+  }
+  T* out = Sexp + (int64_t)sub * NR * NR;
+#pragma unroll
+  for (int a = 0; a < TA; ++a)
+#pragma unroll
+    for (int b = 0; b < TA; ++b) {
+      const int i = qa * TQ + ty + 16 * a, j = qb * TQ + tx + 16 * b;
+      out[(int64_t)i * NR + j] = acc[a][b];
+      if (qa != qb) out[(int64_t)j * NR + i] = acc[a][b];
+    }
+}
+
 // y_ring = S_i x_ring for every subdomain.
 template <typename T, int NR>
 __global__ void __launch_bounds__(256) schur_explicit_kernel(DevTables t, const T* __restrict__ Sexp,
@@ -1180,6 +1318,39 @@ size_t form_smem(const DevTables& t) {
   return (size_t)(2 * BP * NR + PC + PD + 64 + t.s * t.s) * sizeof(T) + NR * sizeof(int) + 16;
 }
 
+constexpr int kFormGC = 32, kFormTQ = 64;  // NR = 256 formation: W column group, S tile
+
+template <typename T, int BP, int NR>
+size_t form_w_smem(const DevTables& t) {
+  constexpr int PC = BP * BP, PD = BP * (BP + 1) / 2;
+  return (size_t)(PC + PD + 2 * BP * kFormGC + 64 + t.s * t.s) * sizeof(T) + kFormGC * sizeof(int) + 16;
+}
+
+template <typename T, int BP, int NR>
+size_t form_syrk_smem(const DevTables& t) {
+  return (size_t)(2 * BP * kFormTQ + 64 + t.s * t.s) * sizeof(T) + 2 * kFormTQ * sizeof(int) + 16;
+}
+
+template <typename T, int BP, int NR>
+void run_form_wide(const DevTables& t, const DevFields& fld, const void* factor, void* work, void* Sexp,
+                   cudaStream_t st) {
+  const T* ke;
+  const T* sc;
+  if constexpr (sizeof(T) == 8) {
+    ke = reinterpret_cast<const T*>(t.Ke64);
+    sc = reinterpret_cast<const T*>(fld.scale64);
+  } else {
+    ke = reinterpret_cast<const T*>(t.Ke32);
+    sc = reinterpret_cast<const T*>(fld.scale32);
+  }
+  constexpr int NQ = NR / kFormTQ;
+  form_w2d_kernel<T, BP, NR, kFormGC><<<dim3(t.n_sub, NR / kFormGC), 256, form_w_smem<T, BP, NR>(t), st>>>(
+      t, ke, sc, reinterpret_cast<const T*>(factor), reinterpret_cast<T*>(work));
+  form_syrk2d_kernel<T, BP, NR, kFormTQ><<<dim3(t.n_sub, NQ * (NQ + 1) / 2), 256, form_syrk_smem<T, BP, NR>(t),
+                                          st>>>(t, ke, sc, reinterpret_cast<const T*>(work),
+                                                reinterpret_cast<T*>(Sexp));
+}
+
 template <typename T, int BP, int NR>
 void run_form(const DevTables& t, const DevFields& fld, const void* factor, void* Sexp,
               cudaStream_t st) {
@@ -1200,19 +1371,29 @@ void run_form(const DevTables& t, const DevFields& fld, const void* factor, void
 
 int explicit_ring_size(const DevTables& t) {
   // NR: padded ring size of the explicit form (0 = explicit form unavailable)
-  if (t.dim != 2 || t.BP != 32) return 0;
-  return t.s <= 8 ? 64 : (t.s <= 16 ? 128 : 0);
+  if (t.dim != 2) return 0;
+  if (t.BP == 32) return t.s <= 8 ? 64 : (t.s <= 16 ? 128 : 0);
+  if ((t.BP == 64 || t.BP == 96) && t.s <= 32) return 256;
+  return 0;
+}
+
+size_t explicit_form_work_elems(const DevTables& t) {
+  return explicit_ring_size(t) == 256 ? (size_t)t.n_sub * t.nb_max * t.BP * 256 : 0;
 }
 
 void launch_schur_form(const DevTables& t, const DevFields& fld, int precision, const void* factor,
-                       void* Sexp, cudaStream_t st) {
+                       void* work, void* Sexp, cudaStream_t st) {
   const int NR = explicit_ring_size(t);
   if (precision == 0) {
     if (NR == 64) run_form<double, 32, 64>(t, fld, factor, Sexp, st);
-    else run_form<double, 32, 128>(t, fld, factor, Sexp, st);
+    else if (NR == 128) run_form<double, 32, 128>(t, fld, factor, Sexp, st);
+    else if (t.BP == 64) run_form_wide<double, 64, 256>(t, fld, factor, work, Sexp, st);
+    else run_form_wide<double, 96, 256>(t, fld, factor, work, Sexp, st);
   } else {
     if (NR == 64) run_form<float, 32, 64>(t, fld, factor, Sexp, st);
-    else run_form<float, 32, 128>(t, fld, factor, Sexp, st);
+    else if (NR == 128) run_form<float, 32, 128>(t, fld, factor, Sexp, st);
+    else if (t.BP == 64) run_form_wide<float, 64, 256>(t, fld, factor, work, Sexp, st);
+    else run_form_wide<float, 96, 256>(t, fld, factor, work, Sexp, st);
   }
 }
 
@@ -1222,21 +1403,28 @@ void launch_split_df(const double* in, float2* out, int64_t n, cudaStream_t st) 
 
 void launch_schur_explicit_df(const DevTables& t, const float2* Sexp, const SchurIO& io,
                               cudaStream_t st) {
-  if (explicit_ring_size(t) == 64)
+  const int NR = explicit_ring_size(t);
+  if (NR == 64)
     schur_explicit_df_kernel<64><<<2 * t.n_sub, 256, 0, st>>>(t, Sexp, io);
-  else
+  else if (NR == 128)
     schur_explicit_df_kernel<128><<<2 * t.n_sub, 256, 0, st>>>(t, Sexp, io);
+  else
+    schur_explicit_df_kernel<256><<<2 * t.n_sub, 256, 0, st>>>(t, Sexp, io);
 }
 
 void launch_schur_explicit(const DevTables& t, int precision, const void* Sexp, const SchurIO& io,
                            cudaStream_t st) {
   const int NR = explicit_ring_size(t);
   if (precision == 0) {
-    if (NR == 64) schur_explicit_kernel<double, 64><<<2 * t.n_sub, 256, 0, st>>>(t, (const double*)Sexp, io);
-    else schur_explicit_kernel<double, 128><<<2 * t.n_sub, 256, 0, st>>>(t, (const double*)Sexp, io);
+    const double* S = (const double*)Sexp;
+    if (NR == 64) schur_explicit_kernel<double, 64><<<2 * t.n_sub, 256, 0, st>>>(t, S, io);
+    else if (NR == 128) schur_explicit_kernel<double, 128><<<2 * t.n_sub, 256, 0, st>>>(t, S, io);
+    else schur_explicit_kernel<double, 256><<<2 * t.n_sub, 256, 0, st>>>(t, S, io);
   } else {
-    if (NR == 64) schur_explicit_kernel<float, 64><<<2 * t.n_sub, 256, 0, st>>>(t, (const float*)Sexp, io);
-    else schur_explicit_kernel<float, 128><<<2 * t.n_sub, 256, 0, st>>>(t, (const float*)Sexp, io);
+    const float* S = (const float*)Sexp;
+    if (NR == 64) schur_explicit_kernel<float, 64><<<2 * t.n_sub, 256, 0, st>>>(t, S, io);
+    else if (NR == 128) schur_explicit_kernel<float, 128><<<2 * t.n_sub, 256, 0, st>>>(t, S, io);
+    else schur_explicit_kernel<float, 256><<<2 * t.n_sub, 256, 0, st>>>(t, S, io);
   }
 }
 
@@ -1272,6 +1460,14 @@ cudaError_t configure_kernels() {
   DDEL_CFG((schur_form2d_kernel<double, 32, 128>));
   DDEL_CFG((schur_form2d_kernel<float, 32, 64>));
   DDEL_CFG((schur_form2d_kernel<float, 32, 128>));
+  DDEL_CFG((form_w2d_kernel<double, 64, 256, kFormGC>));
+  DDEL_CFG((form_w2d_kernel<float, 64, 256, kFormGC>));
+  DDEL_CFG((form_syrk2d_kernel<double, 64, 256, kFormTQ>));
+  DDEL_CFG((form_syrk2d_kernel<float, 64, 256, kFormTQ>));
+  DDEL_CFG((form_w2d_kernel<double, 96, 256, kFormGC>));
+  DDEL_CFG((form_w2d_kernel<float, 96, 256, kFormGC>));
+  DDEL_CFG((form_syrk2d_kernel<double, 96, 256, kFormTQ>));
+  DDEL_CFG((form_syrk2d_kernel<float, 96, 256, kFormTQ>));
 #undef DDEL_CFG
   cudaError_t e3 = configure_kernels3d();
   return e != cudaSuccess ? e : e3;

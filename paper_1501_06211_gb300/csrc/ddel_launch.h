@@ -131,11 +131,14 @@ cudaError_t configure_kernels3d();
 void launch_schur(const DevTables& t, const DevFields& fld, int precision, const void* factor,
                   const SchurIO& io, cudaStream_t st);
 size_t schur_smem_bytes(const DevTables& t, int precision);
-// Explicit local Schur complements (2D, ring size NR <= 128): formation after the
+// Explicit local Schur complements (2D, ring size NR <= 256): formation after the
 // factorisation, and the batched dense apply used inside PCG.
 int explicit_ring_size(const DevTables& t);
+// work: scratch of explicit_form_work_elems() elements of the precision (the
+// per-plane W = L^-1 K_IG of the NR = 256 formation; 0 otherwise).
+size_t explicit_form_work_elems(const DevTables& t);
 void launch_schur_form(const DevTables& t, const DevFields& fld, int precision, const void* factor,
-                       void* Sexp, cudaStream_t st);
+                       void* work, void* Sexp, cudaStream_t st);
 // Double-float form: S_i split into FP32 (hi, lo) pairs; the apply runs on the
 // FP32 pipes with about 48 significant bits (ring output FP64).
 void launch_split_df(const double* in, float2* out, int64_t n, cudaStream_t st);

@@ -21,6 +21,8 @@ CASES = {
     "grf128": workloads.small_config(128, 64, 16, seed=11),
     "mbb64_s8": workloads.small_config(64, 32, 8, seed=5, bc="mbb"),
     "s32": workloads.small_config(128, 64, 32, seed=3),
+    # one row of 32 x 32 subdomains: 33 interior rows per plane (blocks of 96)
+    "s32_row": workloads.small_config(64, 32, 32, seed=6),
     "onerow": workloads.small_config(64, 16, 16, seed=4),
 }
 
