@@ -17,7 +17,11 @@ buffers (host->device copies of densities and loads, device->host copy of the
 displacement inside the timed region).  `learned` compares, on the 256x128
 MBB topology-optimisation workload, the time per Picard solve of plain PCG
 with PCG whose coarse space comes from the last Picard solutions and the
-online-trained U-Net (training time included).
+online-trained U-Net (training time included).  `batch` times 64 independent
+2D problems of uneven size (grids log-uniform 64x32 .. 512x256, subdomain
+edges 8, 16, 32, nu in [0.2, 0.45], GRF densities) solved together by
+ddel_batch_solve (all factorisations in flight, one stream per problem)
+against the same problems solved one after another.
 
 Multi-GPU (torchrun): every rank solves its own independent instance (weak
 scaling, no collective on the data path); the step time is the max over ranks
@@ -265,6 +269,7 @@ def main():
                                  "frac": it_bytes / (us * 1e-6) / 1e9 / roof["peak"] if roof["unit"] == "GB/s" else None,
                                  "source": "t_pcg_ms / iterations of the timed solves"}
     learned = learned_vs_plain(ddel, torch, workloads, stream) if world == 1 else None
+    batch = batched_uneven(ddel, torch, workloads) if world == 1 else None
     ms_best = ms32 if best32 else ms64
     out = {
         "metric": METRIC, "value": ms_best / world, "unit": "ms", "n_gpus": world,
@@ -285,6 +290,8 @@ def main():
     }
     if learned is not None:
         out["learned"] = learned
+    if batch is not None:
+        out["batch"] = batch
     if clk is not None:
         out["clocks"] = clk
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -333,6 +340,52 @@ def learned_vs_plain(ddel, torch, workloads, stream, steps=16, skip=4):
     for name in ("history8", "cnn+history4"):
         res[name]["speedup_vs_plain"] = res["plain"]["ms_per_step"] / res[name]["ms_per_step"]
         res[name]["iteration_ratio"] = res[name]["iters_per_solve"] / res["plain"]["iters_per_solve"]
+    return res
+
+
+def batched_uneven(ddel, torch, workloads, count=64, reps=2):
+    """64 uneven 2D problems (seeded recipe of workloads.batch_problems): the
+    makespan of one ddel_batch_solve (factorisations, condensation, PCG,
+    back-substitution, FP64 residual check of every problem) against
+    factor + solve of the same problems one after another.  Host wall time
+    between device synchronisations (the problems run on their own streams)."""
+    probs = workloads.batch_problems(base_seed=0, count=count)
+    solvers, us = [], []
+    for cfg in probs:
+        s = ddel.Solver(cfg, tol=1e-8, max_it=20000)
+        s.assemble(workloads.density(cfg))
+        solvers.append(s)
+        us.append(torch.zeros(s.n_dof, dtype=torch.float64, device="cuda"))
+    handles = [s.h for s in solvers]
+    ddel.ddel_batch_solve(handles, us)  # warm-up
+    times = []
+    for _ in range(reps):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        code, sts = ddel.ddel_batch_solve(handles, us)
+        torch.cuda.synchronize()
+        times.append(1e3 * (time.perf_counter() - t0))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    cls = {}
+    for cfg, s, u in zip(probs, solvers, us):
+        s.factor()
+        _, st = s.solve(None, u, check=False)
+        c = cls.setdefault(str(cfg["sub"]), {"problems": 0, "iters": 0, "pcg_ms": 0.0})
+        c["problems"] += 1
+        c["iters"] += st.iters
+        c["pcg_ms"] += st.t_pcg_ms
+    torch.cuda.synchronize()
+    seq_ms = 1e3 * (time.perf_counter() - t0)
+    for c in cls.values():
+        c["us_per_iteration"] = 1e3 * c["pcg_ms"] / max(c["iters"], 1)
+    res = {"workload": f"{count} uneven 2D Q1 problems, grids 64x32..512x256, subdomains 8/16/32",
+           "problems": count, "dofs": sum(s.n_dof for s in solvers), "status": code,
+           "iters": sum(st.iters for st in sts), "max_relres": max(st.relres for st in sts),
+           "batched_ms": min(times), "sequential_ms": seq_ms, "speedup_batched": seq_ms / min(times),
+           "by_subdomain_edge": cls, "timing": "host wall time between device synchronisations, L2 not flushed"}
+    for s in solvers:
+        s.close()
     return res
 
 
