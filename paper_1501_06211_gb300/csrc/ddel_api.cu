@@ -367,7 +367,9 @@ int factor_launch(ddel_ctx* ctx, int prec) {
       cudaError_t e = cudaMalloc(&ctx->form_work[prec], we * (prec ? 4 : 8));
       if (e != cudaSuccess) return fail(ctx, DDEL_ENOMEM, "explicit Schur scratch allocation");
     }
-    launch_schur_form(ctx->T, ctx->F, prec, ctx->factor[prec], ctx->form_work[prec], ctx->sexp[prec],
+    // AUTO applies S_i in double-float arithmetic, so it is formed that way too
+    const bool df = prec == 0 && ctx->opt.schur_mode == DDEL_SCHUR_AUTO;
+    launch_schur_form(ctx->T, ctx->F, prec, df, ctx->factor[prec], ctx->form_work[prec], ctx->sexp[prec],
                       ctx->stream);
     ctx->launches += 1;
     CK(cudaGetLastError());

@@ -599,9 +599,9 @@ __global__ void __launch_bounds__(256) schur_form2d_kernel(DevTables t, const T*
       Wb[i] = v;
     }
     __syncthreads();
-#pragma unroll 2
     if (owner)
-    for (int m = 0; m < BP; ++m) {  // S -= W_k^T W_k (upper tiles)
+#pragma unroll 2
+      for (int m = 0; m < BP; ++m) {  // S -= W_k^T W_k (upper tiles)
       T wi[TL], wj[TL];
 #pragma unroll
       for (int a = 0; a < TL; ++a) {
@@ -623,6 +623,121 @@ __global__ void __launch_bounds__(256) schur_form2d_kernel(DevTables t, const T*
       for (int b = 0; b < TL; ++b) {
         out[(ty * TL + a) * NR + tx * TL + b] = acc[a][b];
         out[(tx * TL + b) * NR + ty * TL + a] = acc[a][b];  // mirror
+      }
+  }
+}
+
+// ---- double-float formation --------------------------------------------------
+// schur_form2d_kernel<double> with every product and sum in double-float
+// arithmetic (FP32 (hi, lo) pairs, about 48 significant bits) on the FP32
+// pipes (this GPU issues 2 DFMA per clock per SM): the factor blocks and the
+// K_IG, K_GG entries (computed in FP64) are split once, T, W and the S tiles
+// live as pairs, S_i is stored as FP64 (hi + lo).  Serves the double-float
+// PCG apply, whose operator is rounded to pairs anyway; the FP64 kernel
+// serves the EXPLICIT form.
+__device__ __forceinline__ float2 df_neg(float2 a) { return make_float2(-a.x, -a.y); }
+
+template <int BP, int NR>
+__global__ void __launch_bounds__(256) schur_form2d_df_kernel(DevTables t, const double* __restrict__ Ke_g,
+                                                              const double* __restrict__ scale,
+                                                              const double* __restrict__ factor,
+                                                              double* __restrict__ Sexp) {
+  constexpr int PC = BP * BP, PD = BP * (BP + 1) / 2, STAGE = PC + PD, TL = NR / 16;
+  const int sub = blockIdx.x, tid = threadIdx.x;
+  const SubInfo si = t.subs[sub];
+  const int s = t.s;
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  float2* Wb = reinterpret_cast<float2*>(smem_raw);  // BP x NR
+  float2* Tb = Wb + BP * NR;                          // BP x NR
+  float2* Cs = Tb + BP * NR;                          // PC
+  float2* Ds = Cs + PC;                               // PD
+  double* ke = reinterpret_cast<double*>(Ds + PD);    // 64
+  double* sc = ke + 64;                               // s*s
+  int* rloc = reinterpret_cast<int*>(sc + s * s);     // NR
+  for (int i = tid; i < 64; i += 256) ke[i] = Ke_g[i];
+  for (int i = tid; i < s * s; i += 256)
+    sc[i] = scale[(int64_t)(si.lo[0] + i / s) * t.ne[1] + si.lo[1] + i % s];
+  for (int j = tid; j < NR; j += 256) rloc[j] = j < si.n_ring ? t.ring_loc[si.ring_off + j] : -1;
+  for (int i = tid; i < BP * NR; i += 256) Wb[i] = make_float2(0.f, 0.f);
+  __syncthreads();
+  // threads 0..135 own the 136 upper tiles (ty <= tx) of the 16 x 16 grid
+  int ty = 0, tx = 0;
+  const bool owner = tid < 136;
+  if (owner) {
+    int q = tid;
+    while (q >= 16 - ty) {
+      q -= 16 - ty;
+      ++ty;
+    }
+    tx = ty + q;
+  }
+  float ah[TL][TL], al[TL][TL];
+#pragma unroll
+  for (int a = 0; a < TL; ++a)
+#pragma unroll
+    for (int b = 0; b < TL; ++b) {
+      const float2 v = owner ? df_from(kgg_entry2d<double>(s, ke, sc, rloc[ty * TL + a], rloc[tx * TL + b]))
+                             : make_float2(0.f, 0.f);
+      ah[a][b] = v.x;
+      al[a][b] = v.y;
+    }
+  const double* fb = factor + si.factor_off;
+  for (int k = 0; k < si.nb; ++k) {
+    const double* src = fb + (int64_t)k * STAGE;
+    for (int i = tid; i < STAGE; i += 256) {
+      if (i < PC) {
+        if (k > 0) Cs[i] = df_neg(df_from(src[i]));  // -C_k
+      } else {
+        Ds[i - PC] = df_from(src[i]);
+      }
+    }
+    for (int i = tid; i < BP * NR; i += 256) {
+      const int r = i / NR, j = i % NR;
+      Tb[i] = df_from(kig_entry2d<double>(t, si, ke, sc, k, r, rloc[j]));
+    }
+    __syncthreads();
+    if (k > 0) {  // T = B_k - C_k W_{k-1}
+      for (int i = tid; i < BP * NR; i += 256) {
+        const int r = i / NR, j = i % NR;
+        float2 v = Tb[i];
+#pragma unroll 8
+        for (int m = 0; m < BP; ++m) df_mad(v.x, v.y, Cs[m * BP + r], Wb[m * NR + j]);
+        Tb[i] = v;
+      }
+      __syncthreads();
+    }
+    for (int i = tid; i < BP * NR; i += 256) {  // W_k = D_k T
+      const int r = i / NR, j = i % NR;
+      float h = 0.f, l = 0.f;
+      for (int m = 0; m <= r; ++m) df_mad(h, l, Ds[m * BP - m * (m - 1) / 2 + (r - m)], Tb[m * NR + j]);
+      Wb[i] = make_float2(h, l);
+    }
+    __syncthreads();
+    if (owner)
+#pragma unroll 2
+      for (int m = 0; m < BP; ++m) {  // S -= W_k^T W_k (upper tiles)
+        float2 wi[TL], wj[TL];
+#pragma unroll
+        for (int a = 0; a < TL; ++a) {
+          wi[a] = df_neg(Wb[m * NR + ty * TL + a]);
+          wj[a] = Wb[m * NR + tx * TL + a];
+        }
+#pragma unroll
+        for (int a = 0; a < TL; ++a)
+#pragma unroll
+          for (int b = 0; b < TL; ++b) df_mad(ah[a][b], al[a][b], wi[a], wj[b]);
+      }
+    __syncthreads();
+  }
+  double* out = Sexp + (int64_t)sub * NR * NR;
+  if (owner) {
+#pragma unroll
+    for (int a = 0; a < TL; ++a)
+#pragma unroll
+      for (int b = 0; b < TL; ++b) {
+        const double v = (double)ah[a][b] + (double)al[a][b];
+        out[(ty * TL + a) * NR + tx * TL + b] = v;
+        out[(tx * TL + b) * NR + ty * TL + a] = v;  // mirror
       }
   }
 }
@@ -829,9 +944,10 @@ __global__ void split_df_kernel(const double* __restrict__ in, float2* __restric
 // and JN columns, loading both rows' entries of a column as one 16-byte
 // float4 (S_i stored column-major as (hi, lo) pairs); the H column groups of a
 // row are combined in double-float as well, so FP64 work is left to the
-// final row values.
+// final row values.  Up to 128 ring rows, registers are capped so that 7 CTAs
+// fit an SM: the 1024 CTAs of 512 subdomains then run in one wave.
 template <int NR>
-__global__ void __launch_bounds__(256) schur_explicit_df_kernel(DevTables t, const float2* __restrict__ Sexp,
+__global__ void __launch_bounds__(256, NR <= 128 ? 7 : 1) schur_explicit_df_kernel(DevTables t, const float2* __restrict__ Sexp,
                                                                 SchurIO io) {
   // the flag's load overlaps the gather; nothing is written before the test
   const int done = io.done ? *io.done : 0;
@@ -962,8 +1078,9 @@ __global__ void __launch_bounds__(kRedThreads) pcg_cg_kernel(DevTables t, DevFie
     // E^-1 and E staged in shared memory by all threads at once (thread 0's
     // scalar phase below would otherwise wait on a chain of global loads)
     __shared__ double sEinv[KC > 0 ? KC * KC : 1], sE[KC > 0 ? KC * KC : 1];
+    constexpr int KD = KC > 0 ? KC : 1;  // divisor (no coarse rows when KC = 0)
     for (int i = threadIdx.x; i < KC * KC; i += blockDim.x) {
-      const int a = i / KC, b = i % KC;
+      const int a = i / KD, b = i % KD;
       if (a < k && b < k) {
         sEinv[i] = cd.Einv[a * kMaxCoarse + b];
         sE[i] = 0.5 * (cd.E[a * kMaxCoarse + b] + cd.E[b * kMaxCoarse + a]);
@@ -986,7 +1103,7 @@ __global__ void __launch_bounds__(kRedThreads) pcg_cg_kernel(DevTables t, DevFie
 #pragma unroll
     for (int v = 0; v < NP; ++v) {
       a[v] = 0.0;
-      if (v >= 3 && (v - 3) % KC >= k) continue;  // coarse rows beyond k
+      if (v >= 3 && (v - 3) % (KC > 0 ? KC : 1) >= k) continue;  // coarse rows beyond k
       const double* src = v == 0 ? pd : U + (size_t)(v - 1) * nu;
       const int n = v == 0 ? nd : nu;
       for (int b = threadIdx.x; b < n; b += kRedThreads) a[v] += __ldcg(src + b);
@@ -1351,6 +1468,12 @@ void run_form_wide(const DevTables& t, const DevFields& fld, const void* factor,
                                                 reinterpret_cast<T*>(Sexp));
 }
 
+template <int BP, int NR>
+void run_form_df(const DevTables& t, const DevFields& fld, const void* factor, void* Sexp, cudaStream_t st) {
+  schur_form2d_df_kernel<BP, NR><<<t.n_sub, 256, form_smem<double, BP, NR>(t), st>>>(
+      t, t.Ke64, fld.scale64, reinterpret_cast<const double*>(factor), reinterpret_cast<double*>(Sexp));
+}
+
 template <typename T, int BP, int NR>
 void run_form(const DevTables& t, const DevFields& fld, const void* factor, void* Sexp,
               cudaStream_t st) {
@@ -1381,10 +1504,16 @@ size_t explicit_form_work_elems(const DevTables& t) {
   return explicit_ring_size(t) == 256 ? (size_t)t.n_sub * t.nb_max * t.BP * 256 : 0;
 }
 
-void launch_schur_form(const DevTables& t, const DevFields& fld, int precision, const void* factor,
+void launch_schur_form(const DevTables& t, const DevFields& fld, int precision, bool df, const void* factor,
                        void* work, void* Sexp, cudaStream_t st) {
   const int NR = explicit_ring_size(t);
-  if (precision == 0) {
+  // rings of 256 (32 x 32 subdomains: 31 planes, sums of about 2000 terms)
+  // keep the FP64 formation: formed in double-float their PCG needed half as
+  // many iterations again
+  if (precision == 0 && df && NR <= 128) {
+    if (NR == 64) run_form_df<32, 64>(t, fld, factor, Sexp, st);
+    else run_form_df<32, 128>(t, fld, factor, Sexp, st);
+  } else if (precision == 0) {
     if (NR == 64) run_form<double, 32, 64>(t, fld, factor, Sexp, st);
     else if (NR == 128) run_form<double, 32, 128>(t, fld, factor, Sexp, st);
     else if (t.BP == 64) run_form_wide<double, 64, 256>(t, fld, factor, work, Sexp, st);
@@ -1464,6 +1593,8 @@ cudaError_t configure_kernels() {
   DDEL_CFG((form_w2d_kernel<float, 64, 256, kFormGC>));
   DDEL_CFG((form_syrk2d_kernel<double, 64, 256, kFormTQ>));
   DDEL_CFG((form_syrk2d_kernel<float, 64, 256, kFormTQ>));
+  DDEL_CFG((schur_form2d_df_kernel<32, 64>));
+  DDEL_CFG((schur_form2d_df_kernel<32, 128>));
   DDEL_CFG((form_w2d_kernel<double, 96, 256, kFormGC>));
   DDEL_CFG((form_w2d_kernel<float, 96, 256, kFormGC>));
   DDEL_CFG((form_syrk2d_kernel<double, 96, 256, kFormTQ>));

@@ -135,9 +135,12 @@ size_t schur_smem_bytes(const DevTables& t, int precision);
 // factorisation, and the batched dense apply used inside PCG.
 int explicit_ring_size(const DevTables& t);
 // work: scratch of explicit_form_work_elems() elements of the precision (the
-// per-plane W = L^-1 K_IG of the NR = 256 formation; 0 otherwise).
+// per-plane W = L^-1 K_IG of the NR = 256 formation; 0 otherwise).  df (FP64,
+// rings up to 128): every product and sum of the formation in double-float
+// arithmetic on the FP32 pipes (about 48 significant bits), S_i still stored
+// in FP64.
 size_t explicit_form_work_elems(const DevTables& t);
-void launch_schur_form(const DevTables& t, const DevFields& fld, int precision, const void* factor,
+void launch_schur_form(const DevTables& t, const DevFields& fld, int precision, bool df, const void* factor,
                        void* work, void* Sexp, cudaStream_t st);
 // Double-float form: S_i split into FP32 (hi, lo) pairs; the apply runs on the
 // FP32 pipes with about 48 significant bits (ring output FP64).
