@@ -945,9 +945,10 @@ __global__ void split_df_kernel(const double* __restrict__ in, float2* __restric
 // float4 (S_i stored column-major as (hi, lo) pairs); the H column groups of a
 // row are combined in double-float as well, so FP64 work is left to the
 // final row values.  Up to 128 ring rows, registers are capped so that 7 CTAs
-// fit an SM: the 1024 CTAs of 512 subdomains then run in one wave.
+// fit an SM: the 1024 CTAs of 512 subdomains then run in one wave (rings of
+// 256: 6 CTAs, 40 registers; more registers made that form slower).
 template <int NR>
-__global__ void __launch_bounds__(256, NR <= 128 ? 7 : 1) schur_explicit_df_kernel(DevTables t, const float2* __restrict__ Sexp,
+__global__ void __launch_bounds__(256, NR <= 128 ? 7 : 6) schur_explicit_df_kernel(DevTables t, const float2* __restrict__ Sexp,
                                                                 SchurIO io) {
   // the flag's load overlaps the gather; nothing is written before the test
   const int done = io.done ? *io.done : 0;
