@@ -396,8 +396,9 @@ def launches_per_step(s, st):
 
 # DRAM bytes (read + write) of one launch of schur_explicit_df_kernel<128> on
 # this workload, from one `ncu --set full --clock-control none` capture of the
-# kernel (cold L2): 67.897088 MB read + 0.166144 MB written.
-DF_C1_TRAFFIC = 67897088 + 166144
+# kernel (cold L2, the kernel as built now: 7 CTAs per SM): 67.897088 MB read +
+# 0.246272 MB written.
+DF_C1_TRAFFIC = 67897088 + 246272
 
 
 def kernel_roofline(ddel, s, stream, torch):
