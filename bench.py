@@ -436,7 +436,7 @@ def kernel_roofline(ddel, s, stream, torch):
                 "algorithmic_bytes": bytes_,
                 "note": ("launch_ms: 200 applies (Schur kernel + gamma_sum) timed with CUDA events "
                          "after the timed steps; traffic: one ncu capture, cold L2 "
-                         "(in the PCG loop S_i, 63 MB as FP32 pairs, stays L2-resident)")}
+                         "(a warm-cache capture in the PCG loop reads the same 67 MB from DRAM)")}
     if info["precision"] == 0:
         # FP64 products: GB300 issues 2 DFMA per clock per SM (1.26 TFLOP/s at
         # 2070 MHz on 152 SMs; 1.25 TFLOP/s measured), far below its bandwidth
