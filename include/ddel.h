@@ -287,6 +287,11 @@ int ddel_condense(ddel_ctx* ctx, const double* f, double* g);
 /* y = S x = sum_i (K_GG^(i) x_i - K_{G I_i} K_{I_i I_i}^-1 K_{I_i G} x_i) without forming S
  * (Sec. 3: "avoid the direct construction"); x, y: n_gamma. */
 int ddel_schur_apply(ddel_ctx* ctx, const double* x, double* y);
+/* The per-subdomain half of ddel_schur_apply alone: y_i = S_i x_i for every
+ * subdomain into the context's ring buffer, no sum over the subdomains (the
+ * PCG update kernel forms that sum itself).  For timing the Schur kernel as the
+ * PCG runs it; x: n_gamma (device).  ESTATE before ddel_factor. */
+int ddel_schur_apply_ring(ddel_ctx* ctx, const double* x);
 /* z = S~^-1 r: face-local H~_theta^-1 per component (eq. NumberEight/NumberNine,
  * cross points removed as in Sec. 4) and a diagonal at cross points. */
 int ddel_precond_apply(ddel_ctx* ctx, const double* r, double* z);

@@ -1307,6 +1307,18 @@ int ddel_schur_apply(ddel_ctx* ctx, const double* x, double* y) {
   return DDEL_OK;
 }
 
+int ddel_schur_apply_ring(ddel_ctx* ctx, const double* x) {
+  if (!ctx || !x) return DDEL_EINVAL;
+  const int prec = ctx->active_prec;
+  if (!ctx->factored[prec]) return fail(ctx, DDEL_ESTATE, "factor first");
+  SchurIO io = make_io(ctx);
+  io.x = x;
+  schur_dispatch(ctx, prec, false, io, ctx->stream);
+  ctx->launches += 1;
+  CK(cudaGetLastError());
+  return DDEL_OK;
+}
+
 int ddel_set_coarse(ddel_ctx* ctx, const double* Z, int k, int flags, int on_device) {
   if (!ctx) return DDEL_EINVAL;
   if (k < 0 || k > kMaxCoarse || (k > 0 && !Z))

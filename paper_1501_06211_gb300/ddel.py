@@ -115,6 +115,7 @@ def _load():
         "ddel_apply_K": (c_int, [c_void_p, c_void_p, c_void_p]),
         "ddel_condense": (c_int, [c_void_p, c_void_p, c_void_p]),
         "ddel_schur_apply": (c_int, [c_void_p, c_void_p, c_void_p]),
+        "ddel_schur_apply_ring": (c_int, [c_void_p, c_void_p]),
         "ddel_precond_apply": (c_int, [c_void_p, c_void_p, c_void_p]),
         "ddel_back_substitute": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p]),
         "ddel_pcg": (c_int, [c_void_p, c_void_p, c_void_p, c_double, P(ddel_stats)]),
@@ -249,6 +250,10 @@ def ddel_condense(h, f, g):
 
 def ddel_schur_apply(h, x, y):
     return _lib.ddel_schur_apply(h, _ptr(x), _ptr(y))
+
+
+def ddel_schur_apply_ring(h, x):
+    return _lib.ddel_schur_apply_ring(h, _ptr(x))
 
 
 def ddel_precond_apply(h, r, z):

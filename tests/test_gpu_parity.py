@@ -211,3 +211,22 @@ def test_full_size_config1_residual(prec):
     u_ref = direct.solve(K, f, fixed)
     # error relative to the solution norm, judged against the residual bound
     assert rel(u, u_ref) <= 1e-5, rel(u, u_ref)
+
+
+def test_schur_apply_ring_alone():
+    # the Schur kernel alone (timing entry point): status codes, and the full
+    # apply around it is unchanged bit for bit
+    from paper_1501_06211_gb300 import ddel
+    o = oracle_system("c0")
+    s0 = ddel.Solver(o["cfg"])
+    s0.assemble(o["rho"])
+    x = torch.randn(s0.n_gamma, dtype=torch.float64, device="cuda")
+    assert ddel.ddel_schur_apply_ring(s0.h, x) == ddel.DDEL_ESTATE  # before factor
+    s0.factor()
+    y1 = torch.zeros_like(x)
+    y2 = torch.zeros_like(x)
+    assert ddel.ddel_schur_apply(s0.h, x, y1) == 0
+    assert ddel.ddel_schur_apply_ring(s0.h, x) == 0
+    assert ddel.ddel_schur_apply(s0.h, x, y2) == 0
+    torch.cuda.synchronize()
+    assert torch.equal(y1, y2)
