@@ -230,6 +230,16 @@ typedef struct {
   double* rho_phys;   /* device, n_elem, or NULL: filtered densities of this step */
   void* learner;      /* a ddel_learner of this context (ddel_learn.h) or NULL: coarse
                          space predicted before the solve, observation after it */
+  /* Adaptive tolerance of the analysis (Sec. 5, Table 3: "based on successive
+   * compliance values"; the formula is this library's reading): with
+   * tol_eta > 0 a step solves to tol = clamp(tol_eta |c_k - c_(k-1)| / |c_k|,
+   * ctx tol, tol_max) where c_k = compliance, c_(k-1) = compliance_prev (the
+   * last two steps' compliances), and to tol_max in the first two steps;
+   * tol_eta = 0: the context's tol. */
+  double tol_eta;         /* e.g. 0.1; 0 = off */
+  double tol_max;         /* cap of the adaptive tolerance (0: 1e-3) */
+  double tol_used;        /* out: the tolerance of this step's solve */
+  double compliance_prev; /* kept by ddel_topopt_step: the compliance of the step before */
 } ddel_topopt_state;
 /* Densities must lie in [rho_min, 1]; the loads are those of ddel_bc.
  * Synchronises the stream.  st (may be NULL) receives the solve statistics. */
@@ -238,7 +248,9 @@ int ddel_topopt_step(ddel_ctx* ctx, ddel_topopt_state* state, ddel_stats* st);
 /* Checkpoint / resume of a topology-optimisation run (the paper has no
  * counterpart).  save writes the design densities (state->rho, device), the
  * state scalars (volfrac, r_min, move, iteration, compliance, volume, change,
- * lambda) and the identity of the problem (mesh and material) to `path`,
+ * lambda, tol_eta, tol_max, compliance_prev; files of version 1 hold the first
+ * eight and load as compliance_prev = compliance) and the identity of the
+ * problem (mesh and material) to `path`,
  * through a temporary file renamed into place, with a 64-bit FNV-1a checksum.
  * load checks magic, version, problem identity and checksum, then copies the
  * densities into state->rho (device, n_elem doubles, caller-owned) and sets the

@@ -17,6 +17,10 @@ mathematics of the Lagrangian stationarity condition:
   max(rho_min, rho - m), min(1, rho + m)) with move m = 0.2, the multiplier
   lambda found by 64 bisection steps on [0, 1e9] so that
   V(rho~_new) = v_frac * n_elem.
+
+Sec. 5 (Table 3) solves each Picard step's linear system to an adaptive
+tolerance "based on successive compliance values" and gives no formula; the
+reading (Q23) is `adaptive_tolerance` below.
 """
 import numpy as np
 import scipy.sparse as sp
@@ -97,3 +101,17 @@ def topopt_step(grid, Ke, E, p, Hbar, rho, f, solve, v_frac, rho_min=1e-3, move=
     dv = Hbar.T @ np.ones(len(rho))
     new, _ = oc_update(rho, dc, dv, v_frac * len(rho), rho_min, move)
     return new, c, u, rho_f
+
+
+def adaptive_tolerance(history, eta, tol_min, tol_max):
+    """Krylov tolerance of the next Picard step from the compliances of the
+    steps so far (Sec. 5, Table 3; reading Q23): the relative change of the
+    last two compliances, scaled by eta, clamped to [tol_min, tol_max]; tol_max
+    while fewer than two compliances are known.  A step whose design still
+    moves the compliance by a relative d needs its analysis no more accurate
+    than a fraction eta of d."""
+    tol_max = max(tol_max, tol_min)
+    if len(history) < 2:
+        return tol_max
+    c1, c0 = history[-1], history[-2]
+    return min(tol_max, max(tol_min, eta * abs(c1 - c0) / abs(c1)))

@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 
 #include <cmath>
+#include <cstddef>
 #include <cstdio>
 #include <algorithm>
 #include <cstring>
@@ -936,8 +937,23 @@ int ddel_topopt_step(ddel_ctx* ctx, ddel_topopt_state* ts, ddel_stats* stats) {
   ddel_learner* learner = static_cast<ddel_learner*>(ts->learner);
   if (learner && (rc = ddel_learner_predict(learner, ctx->rho_f))) return rc;
   double* u = ts->u ? ts->u : ctx->topo_u;
+  // adaptive tolerance from the last two compliances (Sec. 5, Table 3)
+  const double tol0 = ctx->opt.tol;
+  double tol = tol0;
+  if (ts->tol_eta > 0.0) {
+    const double tmax = std::max(ts->tol_max > 0.0 ? ts->tol_max : 1e-3, tol0);
+    if (ts->iteration < 2 || !(ts->compliance != 0.0)) {
+      tol = tmax;
+    } else {
+      const double d = ts->tol_eta * std::fabs(ts->compliance - ts->compliance_prev) / std::fabs(ts->compliance);
+      tol = std::min(tmax, std::max(tol0, d));
+    }
+  }
+  ctx->opt.tol = tol;
   rc = ddel_solve(ctx, nullptr, u, 1, stats);
+  ctx->opt.tol = tol0;
   if (rc) return rc;
+  ts->tol_used = tol;
   if (learner && (rc = ddel_learner_observe(learner, ctx->rho_f, u))) return rc;
   launch_dot(ctx->d_load, u, nd, ctx->partials, ctx->ticketK, ctx->topo_out + 3, s);
   launch_sensitivity(ctx->T, ctx->mat.E, ctx->mat.simp_p, ctx->rho_f, u, ctx->dcf, s);
@@ -952,6 +968,7 @@ int ddel_topopt_step(ddel_ctx* ctx, ddel_topopt_state* ts, ddel_stats* stats) {
   ts->lambda = ctx->h_topo[0];
   ts->volume = ctx->h_topo[1] / (double)ne;
   ts->change = ctx->h_topo[2];
+  ts->compliance_prev = ts->compliance;
   ts->compliance = ctx->h_topo[3];
   ts->iteration += 1;
   return DDEL_OK;
@@ -968,8 +985,10 @@ struct CkpHeader {
   int64_t n_elem;
   double volfrac, r_min, move, compliance, volume, change, lambda;
   int64_t iteration;
+  double tol_eta, tol_max, compliance_prev;  // version 2
 };
 constexpr char kCkpMagic[8] = {'D', 'D', 'E', 'L', 'C', 'K', 'P', '1'};
+constexpr size_t kCkpHeaderV1 = offsetof(CkpHeader, tol_eta);
 
 uint64_t fnv1a(const unsigned char* p, size_t n, uint64_t h = 1469598103934665603ull) {
   for (size_t i = 0; i < n; ++i) h = (h ^ p[i]) * 1099511628211ull;
@@ -979,7 +998,7 @@ uint64_t fnv1a(const unsigned char* p, size_t n, uint64_t h = 146959810393466560
 CkpHeader ckp_identity(const ddel_ctx* ctx) {
   CkpHeader h{};
   std::memcpy(h.magic, kCkpMagic, 8);
-  h.version = 1;
+  h.version = 2;
   h.dim = (uint32_t)ctx->mesh.dim;
   h.nx = ctx->mesh.nx;
   h.ny = ctx->mesh.ny;
@@ -1007,6 +1026,9 @@ int ddel_checkpoint_save(const ddel_ctx* cctx, const ddel_topopt_state* ts, cons
   h.change = ts->change;
   h.lambda = ts->lambda;
   h.iteration = ts->iteration;
+  h.tol_eta = ts->tol_eta;
+  h.tol_max = ts->tol_max;
+  h.compliance_prev = ts->compliance_prev;
   std::vector<double> rho(ctx->S.n_elem);
   CK(cudaMemcpyAsync(rho.data(), ts->rho, rho.size() * 8, cudaMemcpyDeviceToHost, ctx->stream));
   CK(cudaStreamSynchronize(ctx->stream));
@@ -1033,8 +1055,13 @@ int ddel_checkpoint_load(ddel_ctx* ctx, ddel_topopt_state* ts, const char* path)
   const CkpHeader want = ckp_identity(ctx);
   std::vector<double> rho;
   uint64_t sum = 0;
-  bool ok = std::fread(&h, sizeof(h), 1, f) == 1 && std::memcmp(h.magic, kCkpMagic, 8) == 0 && h.version == 1 &&
+  // version 1 files end their header before the adaptive-tolerance fields
+  bool ok = std::fread(&h, kCkpHeaderV1, 1, f) == 1 && std::memcmp(h.magic, kCkpMagic, 8) == 0 &&
+            (h.version == 1 || h.version == 2) &&
+            (h.version == 1 ||
+             std::fread(reinterpret_cast<char*>(&h) + kCkpHeaderV1, sizeof(h) - kCkpHeaderV1, 1, f) == 1) &&
             h.n_elem == want.n_elem;
+  const size_t hbytes = h.version == 1 ? kCkpHeaderV1 : sizeof(h);
   if (ok) {
     rho.resize(h.n_elem);
     ok = std::fread(rho.data(), 8, rho.size(), f) == rho.size() && std::fread(&sum, sizeof(sum), 1, f) == 1;
@@ -1042,7 +1069,7 @@ int ddel_checkpoint_load(ddel_ctx* ctx, ddel_topopt_state* ts, const char* path)
   ok = ok && std::fgetc(f) == EOF;
   std::fclose(f);
   if (!ok) return fail(ctx, DDEL_EINVAL, std::string("checkpoint: not a checkpoint of this size: ") + path);
-  uint64_t chk = fnv1a(reinterpret_cast<const unsigned char*>(&h), sizeof(h));
+  uint64_t chk = fnv1a(reinterpret_cast<const unsigned char*>(&h), hbytes);
   chk = fnv1a(reinterpret_cast<const unsigned char*>(rho.data()), rho.size() * 8, chk);
   if (chk != sum) return fail(ctx, DDEL_EINVAL, "checkpoint: checksum mismatch");
   if (h.dim != want.dim || h.nx != want.nx || h.ny != want.ny || h.nz != want.nz || h.sub != want.sub ||
@@ -1059,6 +1086,13 @@ int ddel_checkpoint_load(ddel_ctx* ctx, ddel_topopt_state* ts, const char* path)
   ts->change = h.change;
   ts->lambda = h.lambda;
   ts->iteration = (int)h.iteration;
+  if (h.version >= 2) {
+    ts->tol_eta = h.tol_eta;
+    ts->tol_max = h.tol_max;
+    ts->compliance_prev = h.compliance_prev;
+  } else {
+    ts->compliance_prev = h.compliance;
+  }
   ctx->u_valid = false;  // a WARM start must not pick up an unrelated solution
   return DDEL_OK;
 }

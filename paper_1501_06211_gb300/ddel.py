@@ -76,7 +76,8 @@ class ddel_topopt_state(ctypes.Structure):
     _fields_ = [("rho", c_void_p), ("volfrac", c_double), ("r_min", c_double), ("move", c_double),
                 ("iteration", c_int), ("compliance", c_double), ("volume", c_double),
                 ("change", c_double), ("lambda_", c_double), ("u", c_void_p), ("rho_phys", c_void_p),
-                ("learner", c_void_p)]
+                ("learner", c_void_p), ("tol_eta", c_double), ("tol_max", c_double),
+                ("tol_used", c_double), ("compliance_prev", c_double)]
 
 
 class ddel_learner_options(ctypes.Structure):
@@ -633,11 +634,14 @@ class Solver:
         self._coarse_ref = Z
         _check(ddel_set_coarse(self.h, Z, Z.shape[0], flags, on_dev), self.h)
 
-    def topopt_state(self, rho, volfrac, r_min=1.5, move=0.2, u=None, rho_phys=None, learner=None):
-        """State for ddel_topopt_step; rho is a CUDA tensor updated in place."""
+    def topopt_state(self, rho, volfrac, r_min=1.5, move=0.2, u=None, rho_phys=None, learner=None,
+                     tol_eta=0.0, tol_max=0.0):
+        """State for ddel_topopt_step; rho is a CUDA tensor updated in place.
+        tol_eta > 0: adaptive analysis tolerance from the last two compliances."""
         ts = ddel_topopt_state()
         ts.rho = _ptr(rho)
         ts.volfrac, ts.r_min, ts.move = volfrac, r_min, move
+        ts.tol_eta, ts.tol_max = tol_eta, tol_max
         ts.u = _ptr(u)
         ts.rho_phys = _ptr(rho_phys)
         ts.learner = learner.h.value if learner is not None else None

@@ -103,3 +103,55 @@ def test_compliance_decreases_mbb():
     cs = np.array(cs)
     assert np.all(cs[1:] <= cs[:-1] * (1 + 1e-6))
     assert cs[-1] < 0.5 * cs[0]
+
+
+def test_adaptive_tolerance_rule():
+    # reading Q23: clamp(eta |c_k - c_k-1| / |c_k|, tol_min, tol_max), tol_max
+    # before two compliances exist
+    at = topopt.adaptive_tolerance
+    assert at([], 0.1, 1e-8, 1e-3) == 1e-3
+    assert at([5.0], 0.1, 1e-8, 1e-3) == 1e-3
+    assert at([100.0, 50.0], 0.1, 1e-8, 1e-3) == 1e-3          # large change: cap
+    assert at([50.0, 50.0], 0.1, 1e-8, 1e-3) == 1e-8           # no change: floor
+    assert np.isclose(at([100.0, 99.9], 0.1, 1e-8, 1e-3), 0.1 * 0.1 / 99.9)
+    # invariant under scaling of the compliance, symmetric in the sign of the change
+    assert np.isclose(at([3.0, 2.9], 0.05, 1e-9, 1.0), at([300.0, 290.0], 0.05, 1e-9, 1.0), rtol=1e-14)
+    assert np.isclose(at([2.9, 3.0], 0.05, 1e-9, 1.0), 0.05 * 0.1 / 3.0)
+    # the floor wins over a cap below it
+    assert at([1.0, 2.0], 0.1, 1e-6, 1e-8) == 1e-6
+
+
+def test_adaptive_tolerance_picard_loop():
+    # MBB beam 32 x 16, eight 8 x 8 subdomains, Picard steps whose analysis is
+    # the oracle's interface PCG: with the adaptive tolerance the run ends on
+    # the compliance of the fixed-tolerance run (within 1e-3) using fewer
+    # PCG iterations in all
+    from oracle import dd
+    nx, ny, s = 32, 16, 8
+    grid, fixed, f, Ke = _mbb(nx, ny)
+    H = topopt.filter_matrix((nx, ny), 1.5)
+    norm_f = np.linalg.norm(f)
+
+    def run(adaptive, steps=24):
+        rho = np.full(grid.n_elem, 0.5)
+        hist, its = [], 0
+        for _ in range(steps):
+            tol = topopt.adaptive_tolerance(hist, 0.1, 1e-8, 1e-3) if adaptive else 1e-8
+
+            def solve(fac):
+                nonlocal its
+                dec, K, dds = dd.build(grid, s, fixed, Ke, fac)
+                pre = dd.FacePreconditioner(dec, K)
+                g = dds.condense(f)
+                x, k = dd.pcg(dds.schur_apply, pre.apply, g, tol, 5000, ref_norm=norm_f)[:2]
+                its += k
+                return dds.back_substitute(f, x)
+
+            rho, c, _, _ = topopt.topopt_step(grid, Ke, 1.0, 3.0, H, rho, f, solve, 0.5)
+            hist.append(c)
+        return hist, its
+
+    h_fix, it_fix = run(False)
+    h_ad, it_ad = run(True)
+    assert abs(h_ad[-1] - h_fix[-1]) <= 1e-3 * h_fix[-1], (h_ad[-1], h_fix[-1])
+    assert it_ad < 0.85 * it_fix, (it_ad, it_fix)
