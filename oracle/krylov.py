@@ -79,3 +79,52 @@ def block_right_preconditioner(dd, apply_Sinv):
         return out
 
     return apply
+
+
+def fgmres(apply_A, apply_P, b, tol=1e-10, max_it=200):
+    """Flexible GMRES (Saad 1993), right preconditioned: the preconditioned
+    directions z_j = P_j^-1 v_j are kept, so P may change from step to step
+    (Sec. 3: the inverse Lanczos application of S~^-1 depends on its input).
+    Returns (x, iterations, residual history); x = Z_k y.
+    """
+    n = len(b)
+    beta = np.linalg.norm(b)
+    V = np.zeros((max_it + 1, n))
+    Z = np.zeros((max_it, n))
+    H = np.zeros((max_it + 1, max_it))
+    cs = np.zeros(max_it)
+    sn = np.zeros(max_it)
+    e = np.zeros(max_it + 1)
+    e[0] = beta
+    V[0] = b / beta
+    hist = [beta]
+    k = 0
+    for k in range(max_it):
+        Z[k] = apply_P(V[k])
+        w = apply_A(Z[k])
+        for j in range(k + 1):
+            H[j, k] = w @ V[j]
+            w = w - H[j, k] * V[j]
+        H[k + 1, k] = np.linalg.norm(w)
+        if H[k + 1, k] > 0:
+            V[k + 1] = w / H[k + 1, k]
+        for j in range(k):
+            t = cs[j] * H[j, k] + sn[j] * H[j + 1, k]
+            H[j + 1, k] = -sn[j] * H[j, k] + cs[j] * H[j + 1, k]
+            H[j, k] = t
+        den = np.hypot(H[k, k], H[k + 1, k])
+        cs[k] = H[k, k] / den
+        sn[k] = H[k + 1, k] / den
+        H[k, k] = den
+        H[k + 1, k] = 0.0
+        e[k + 1] = -sn[k] * e[k]
+        e[k] = cs[k] * e[k]
+        hist.append(abs(e[k + 1]))
+        if hist[-1] <= tol * beta:
+            k += 1
+            break
+    else:
+        k = max_it
+    y = np.linalg.solve(np.triu(H[:k, :k]), e[:k])
+    x = Z[:k].T @ y
+    return x, k, hist

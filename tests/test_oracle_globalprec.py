@@ -1,0 +1,118 @@
+"""Pins of the oracle's global-interface preconditioner (Sec. 3, eq.
+NumberEight/NumberNine on all of Gamma) and of flexible GMRES.
+
+Independent checks: the exact application is the inverse of M V diag(lam)
+V^T M assembled from scratch and is SPD; the endpoints theta = 1 (Htilde = M)
+and theta = 0 (Htilde = L) reduce to mass and Laplacian solves, which inverse
+Lanczos reproduces exactly after one and two steps; inverse Lanczos converges
+to the exact application as the steps grow (exact at full dimension); FGMRES
+with a fixed preconditioner is GMRES, and with S~ = S it stops in two
+iterations (reading Q1); on the cantilever the global form needs fewer outer
+iterations than the face-local form and stays nearly flat in h (Table 1).
+"""
+import numpy as np
+import scipy.sparse.linalg as spla
+
+from oracle import dd, globalprec, krylov
+from test_oracle_dd import _system
+
+
+def _case(nx=32, ny=16, sub=8, p=1.0):
+    return _system(nx, ny, sub, p=p)
+
+
+def test_exact_application_is_the_inverse_and_spd():
+    grid, fixed, f, Ke, fac, dec, K, dds = _case()
+    gp = globalprec.GlobalPreconditioner(dec, K, theta=0.5)
+    P = gp.dense()
+    assert np.abs(P - P.T).max() <= 1e-13 * np.abs(P).max()
+    assert np.linalg.eigvalsh(P).min() > 0
+    # S~ per component rebuilt from M, L: W M (M^-1 L)^(1/2) W through a dense
+    # symmetric square root (independent of the generalised eigensolver)
+    M, L = dd.interface_mass_laplacian(dec)
+    G = dec.gamma_dofs
+    for c in gp.comps:
+        nodes = np.array([int(G[k]) // 2 for k in c.pos])
+        Mc = M[nodes][:, nodes].toarray()
+        Lc = L[nodes][:, nodes].toarray()
+        w, U = np.linalg.eigh(Mc)
+        Mh = U @ np.diag(np.sqrt(w)) @ U.T               # M^(1/2)
+        Mih = U @ np.diag(1.0 / np.sqrt(w)) @ U.T        # M^(-1/2)
+        A = Mih @ Lc @ Mih                               # M^-1/2 L M^-1/2, SPD
+        a, Z = np.linalg.eigh(A)
+        H = Mh @ Z @ np.diag(a ** 0.5) @ Z.T @ Mh        # M (M^-1 L)^(1/2) = M^1/2 A^1/2 M^1/2
+        S = np.diag(c.w) @ H @ np.diag(c.w)
+        Pc = P[np.ix_(c.pos, c.pos)]
+        assert np.allclose(Pc @ S, np.eye(len(c.pos)), atol=1e-9)
+
+
+def test_theta_endpoints_mass_and_laplacian():
+    grid, fixed, f, Ke, fac, dec, K, dds = _case()
+    M, L = dd.interface_mass_laplacian(dec)
+    G = dec.gamma_dofs
+    r = np.random.default_rng(3).standard_normal(len(G))
+    for theta, op in ((1.0, M), (0.0, L)):
+        for steps in (None, 1 if theta == 1.0 else 2):
+            gp = globalprec.GlobalPreconditioner(dec, K, theta=theta, steps=steps, face_scaling=False)
+            z = gp.apply(r)
+            for c in gp.comps:
+                nodes = np.array([int(G[k]) // 2 for k in c.pos])
+                Oc = op[nodes][:, nodes].tocsc()
+                ref = spla.spsolve(Oc, r[c.pos])
+                assert np.allclose(z[c.pos], ref, rtol=1e-10, atol=1e-12 * np.abs(ref).max()), (theta, steps)
+
+
+def test_inverse_lanczos_converges_to_the_exact_application():
+    grid, fixed, f, Ke, fac, dec, K, dds = _case()
+    r = np.random.default_rng(4).standard_normal(len(dec.gamma_dofs))
+    z = globalprec.GlobalPreconditioner(dec, K, theta=0.5).apply(r)
+    errs = []
+    for k in (2, 4, 8, 16, 32):
+        zk = globalprec.GlobalPreconditioner(dec, K, theta=0.5, steps=k).apply(r)
+        errs.append(np.linalg.norm(zk - z) / np.linalg.norm(z))
+    assert all(b < a for a, b in zip(errs, errs[1:])), errs
+    assert errs[-1] < 1e-6
+    zn = globalprec.GlobalPreconditioner(dec, K, theta=0.5, steps=10 ** 6).apply(r)
+    assert np.linalg.norm(zn - z) <= 1e-10 * np.linalg.norm(z)
+
+
+def _full_system(grid, fixed, f, dec, K, dds):
+    I = np.concatenate([b[0] for b in dds.blocks])
+    order = np.concatenate([I, dec.gamma_dofs])
+    return K[order][:, order], f[order]
+
+
+def test_fgmres_is_gmres_for_a_fixed_preconditioner_and_two_steps_with_exact_S():
+    grid, fixed, f, Ke, fac, dec, K, dds = _case(16, 8, 4)
+    Kp, b = _full_system(grid, fixed, f, dec, K, dds)
+    pre = dd.FacePreconditioner(dec, K)
+    Pinv = krylov.block_right_preconditioner(dds, pre.apply)
+    x1, k1, _ = krylov.fgmres(lambda v: Kp @ v, Pinv, b, 1e-10, 300)
+    y2, k2, _ = krylov.gmres(lambda v: Kp @ Pinv(v), b, 1e-10, 300)
+    assert k1 == k2
+    assert np.allclose(x1, Pinv(y2), rtol=1e-8, atol=1e-12 * np.abs(x1).max())
+    Sinv = np.linalg.inv(dds.schur_dense())
+    Pexact = krylov.block_right_preconditioner(dds, lambda v: Sinv @ v)
+    _, k, _ = krylov.fgmres(lambda v: Kp @ v, Pexact, b, 1e-10, 50)
+    assert k <= 2
+
+
+def test_table1_global_form_beats_face_local_and_is_flat_in_h():
+    # Table 1's H_0.5 columns (tests/golden/table1_gmres_iterations.txt) stay
+    # flat as h halves; here: FGMRES to 1e-6 on the full system, cantilever,
+    # 8 subdomains (4 x 2), h halved twice, global form exact and with 8
+    # inverse Lanczos steps, against the face-local form of the hot path
+    its = {"global": [], "lanczos8": [], "face": []}
+    for s in (4, 8, 16):
+        grid, fixed, f, Ke, fac, dec, K, dds = _system(4 * s, 2 * s, s, p=1.0)
+        Kp, b = _full_system(grid, fixed, f, dec, K, dds)
+        pres = {"global": globalprec.GlobalPreconditioner(dec, K, 0.5),
+                "lanczos8": globalprec.GlobalPreconditioner(dec, K, 0.5, steps=8),
+                "face": dd.FacePreconditioner(dec, K, 0.5)}
+        for name, pre in pres.items():
+            Pinv = krylov.block_right_preconditioner(dds, pre.apply)
+            its[name].append(krylov.fgmres(lambda v: Kp @ v, Pinv, b, 1e-6, 300)[1])
+    g, l8, fl = its["global"], its["lanczos8"], its["face"]
+    assert all(a < c for a, c in zip(g, fl)), its
+    assert g[-1] <= 1.25 * g[0], its
+    assert all(a <= c for a, c in zip(g, l8)) and l8[-1] <= fl[-1], its
