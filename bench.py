@@ -17,7 +17,8 @@ buffers (host->device copies of densities and loads, device->host copy of the
 displacement inside the timed region).  `learned` compares, on the 256x128
 MBB topology-optimisation workload, the time per Picard solve of plain PCG
 with PCG whose coarse space comes from the last Picard solutions and the
-online-trained U-Net (training time included).  `batch` times 64 independent
+online-trained U-Net (training time included), and with an adaptive PCG
+tolerance from successive compliances (Sec. 5).  `batch` times 64 independent
 2D problems of uneven size (grids log-uniform 64x32 .. 512x256, subdomain
 edges 8, 16, 32, nu in [0.2, 0.45], GRF densities) solved together by
 ddel_batch_solve (all factorisations in flight, one stream per problem)
@@ -337,7 +338,26 @@ def learned_vs_plain(ddel, torch, workloads, stream, steps=16, skip=4):
             res[name]["train_ms"] = L.info().t_train_ms
             L.close()
         s.close()
-    for name in ("history8", "cnn+history4"):
+    # plain PCG to an adaptive tolerance from successive compliances (Sec. 5,
+    # Table 3): eta 0.1, cap 1e-3, floor the 1e-8 of the other runs
+    s = ddel.Solver(cfg, stream=stream.cuda_stream, tol=1e-8, max_it=20000)
+    rho = torch.full((ne,), cfg["v_frac"], dtype=torch.float64, device="cuda")
+    ts = s.topopt_state(rho, cfg["v_frac"], r_min=1.5, move=0.2, tol_eta=0.1, tol_max=1e-3)
+    ms, its = [], []
+    for k in range(steps):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        st = s.topopt_step(ts)
+        e1.record(stream)
+        e1.synchronize()
+        if k >= skip:
+            ms.append(e0.elapsed_time(e1))
+            its.append(st.iters)
+    res["adaptive_tol"] = {"ms_per_step": sum(ms) / len(ms), "iters_per_solve": sum(its) / len(its),
+                           "compliance": ts.compliance, "last_tol": ts.tol_used}
+    s.close()
+    for name in ("history8", "cnn+history4", "adaptive_tol"):
         res[name]["speedup_vs_plain"] = res["plain"]["ms_per_step"] / res[name]["ms_per_step"]
         res[name]["iteration_ratio"] = res[name]["iters_per_solve"] / res["plain"]["iters_per_solve"]
     return res

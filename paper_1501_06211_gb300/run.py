@@ -3,6 +3,7 @@ synthetic workloads through the C ABI and prints the statistics.
 
     python -m paper_1501_06211_gb300.run --workload c1 --solves 2
     python -m paper_1501_06211_gb300.run --workload c4 --topopt-steps 20 --learner history
+    python -m paper_1501_06211_gb300.run --workload c4 --topopt-steps 40 --tol-eta 0.1
 
 Run from the repository root (the workload generators live in `workloads/`).
 """
@@ -21,6 +22,8 @@ def main(argv=None):
     ap.add_argument("--tol", type=float, default=1e-8)
     ap.add_argument("--topopt-steps", type=int, default=0, help="Picard steps instead of solves")
     ap.add_argument("--learner", default="none", choices=["none", "history", "cnn", "cnn+history"])
+    ap.add_argument("--tol-eta", type=float, default=0.0,
+                    help="topology steps: adaptive tolerance from successive compliances (0: --tol)")
     args = ap.parse_args(argv)
     sys.path.insert(0, os.getcwd())
     import torch
@@ -42,12 +45,12 @@ def main(argv=None):
             ne *= n
         vf = cfg.get("v_frac", 0.5)
         rho = torch.full((ne,), vf, dtype=torch.float64, device="cuda")
-        ts = s.topopt_state(rho, vf, r_min=cfg.get("r_min", 1.5), learner=learner)
+        ts = s.topopt_state(rho, vf, r_min=cfg.get("r_min", 1.5), learner=learner, tol_eta=args.tol_eta)
         for k in range(args.topopt_steps):
             st = s.topopt_step(ts)
             print(json.dumps({"step": k, "iters": st.iters, "coarse_k": st.coarse_k,
                               "compliance": ts.compliance, "change": ts.change,
-                              "t_total_ms": st.t_total_ms}), flush=True)
+                              "tol": ts.tol_used, "t_total_ms": st.t_total_ms}), flush=True)
         return
     s.assemble(workloads.density(cfg))
     s.factor()
