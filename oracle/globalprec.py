@@ -24,6 +24,11 @@ Two ways to apply S~^-1 r:
     depends nonlinearly on r for k below the dimension, hence flexible GMRES
     outside (`fgmres`).
 Both act on the Gamma vector in the decomposition's Gamma order.
+
+Solves with L inside inverse Lanczos are exact (sparse factorisation) by
+default; inner="pcg" uses the paper's inner iteration (Sec. 4): PCG to a
+relative residual inner_tol (1e-3 there) preconditioned by L restricted to
+each face Gamma_i with the cross points removed (diagonal at cross points).
 """
 import numpy as np
 import scipy.linalg as sla
@@ -34,11 +39,23 @@ from . import dd
 
 
 class _Component:
-    def __init__(self, pos, M, L, theta):
+    def __init__(self, pos, M, L, theta, groups=None, inner="exact", inner_tol=1e-3):
         self.pos = pos                      # positions in the Gamma vector
         self.M = sp.csc_matrix(M)
         self.L = sp.csc_matrix(L)
         self.theta = theta
+        self.inner = inner
+        self.inner_tol = inner_tol
+        self.inner_its = []                 # inner PCG iterations per solve with L
+        # face blocks of L (cross points removed) for the inner PCG
+        Ld = self.L.toarray()
+        self.groups = []
+        self.cross = np.zeros(0, dtype=np.int64)
+        if groups is not None:
+            faces, cross = groups
+            self.groups = [(g, np.linalg.inv(Ld[np.ix_(g, g)])) for g in faces]
+            self.cross = np.asarray(cross, dtype=np.int64)
+            self.cross_d = np.diag(Ld)[self.cross]
         mu, V = sla.eigh(L.toarray(), M.toarray())  # L V = M V diag(mu), V^T M V = I
         self.singular = mu[0] <= 1e-12 * max(mu[-1], 1.0)
         if self.singular:
@@ -53,6 +70,37 @@ class _Component:
 
     def exact(self, r):
         return self.V @ ((self.V.T @ r) / self.lam)
+
+    def _precond_L(self, r):
+        z = np.zeros_like(r)
+        for g, Linv in self.groups:
+            z[g] = Linv @ r[g]
+        z[self.cross] = r[self.cross] / self.cross_d
+        return z
+
+    def solve_L(self, b):
+        """x = L^-1 b: exact, or the paper's inner PCG (Sec. 4)."""
+        if self.inner == "exact":
+            return self.Llu.solve(b)
+        x = np.zeros_like(b)
+        r = b.copy()
+        z = self._precond_L(r)
+        p = z.copy()
+        rz = r @ z
+        nb = np.linalg.norm(b)
+        k = 0
+        while np.linalg.norm(r) > self.inner_tol * nb and k < 1000:
+            q = self.L @ p
+            a = rz / (p @ q)
+            x += a * p
+            r -= a * q
+            z = self._precond_L(r)
+            rz_new = r @ z
+            p = z + (rz_new / rz) * p
+            rz = rz_new
+            k += 1
+        self.inner_its.append(k)
+        return x
 
     def lanczos(self, r, k):
         """k steps of inverse Lanczos (full M-orthogonalisation)."""
@@ -70,7 +118,7 @@ class _Component:
         Q[:, 0] = b / nb
         m = k
         for j in range(k):
-            w = self.Llu.solve(self.M @ Q[:, j])       # B q_j = L^-1 M q_j
+            w = self.solve_L(self.M @ Q[:, j])         # B q_j = L^-1 M q_j
             alpha[j] = Q[:, j] @ (self.M @ w)
             for i in range(j + 1):                      # M-orthogonalise against Q_j
                 w = w - (Q[:, i] @ (self.M @ w)) * Q[:, i]
@@ -95,7 +143,7 @@ class GlobalPreconditioner:
     False keeps the paper-literal Htilde (homogeneous problems only).
     """
 
-    def __init__(self, dec, K, theta=0.5, steps=None, face_scaling="dof"):
+    def __init__(self, dec, K, theta=0.5, steps=None, face_scaling="dof", inner="exact", inner_tol=1e-3):
         self.dec = dec
         self.steps = steps
         grid = dec.grid
@@ -109,7 +157,17 @@ class GlobalPreconditioner:
             if len(pos) == 0:
                 continue
             nodes = np.array([int(G[k]) // d for k in pos])
-            comp = _Component(pos, M[nodes][:, nodes], L[nodes][:, nodes], theta)
+            # faces (nodes of exactly two subdomains, grouped by the pair) and
+            # cross points, as local indices of this component
+            faces, cross = {}, []
+            for i, n in enumerate(nodes):
+                subs = dec.node_subs[n]
+                if len(subs) == 2:
+                    faces.setdefault(subs, []).append(i)
+                else:
+                    cross.append(i)
+            groups = ([np.array(v) for _, v in sorted(faces.items(), key=lambda kv: sorted(kv[0]))], cross)
+            comp = _Component(pos, M[nodes][:, nodes], L[nodes][:, nodes], theta, groups, inner, inner_tol)
             Hdiag = np.einsum("ij,j,ij->i", comp.M.toarray() @ comp.V, comp.lam, comp.M.toarray() @ comp.V)
             comp.w = np.sqrt(Kdiag[G[pos]] / Hdiag) if face_scaling == "dof" else np.ones(len(pos))
             self.comps.append(comp)

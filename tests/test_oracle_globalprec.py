@@ -116,3 +116,20 @@ def test_table1_global_form_beats_face_local_and_is_flat_in_h():
     assert all(a < c for a, c in zip(g, fl)), its
     assert g[-1] <= 1.25 * g[0], its
     assert all(a <= c for a, c in zip(g, l8)) and l8[-1] <= fl[-1], its
+
+
+def test_inner_pcg_iterations_in_the_papers_range():
+    # Sec. 4: the solves with L inside the Lanczos process by PCG to 1e-3,
+    # preconditioned by L on each face with the cross points removed, took
+    # "typically between 2 and 12" iterations; the outer FGMRES count stays
+    # within two of the exact-inner-solve count
+    for s in (4, 8, 16):
+        grid, fixed, f, Ke, fac, dec, K, dds = _system(4 * s, 2 * s, s, p=1.0)
+        Kp, b = _full_system(grid, fixed, f, dec, K, dds)
+        ex = globalprec.GlobalPreconditioner(dec, K, 0.5, steps=8)
+        ip = globalprec.GlobalPreconditioner(dec, K, 0.5, steps=8, inner="pcg", inner_tol=1e-3)
+        k_ex = krylov.fgmres(lambda v: Kp @ v, krylov.block_right_preconditioner(dds, ex.apply), b, 1e-6, 300)[1]
+        k_ip = krylov.fgmres(lambda v: Kp @ v, krylov.block_right_preconditioner(dds, ip.apply), b, 1e-6, 300)[1]
+        inner = np.array([k for c in ip.comps for k in c.inner_its])
+        assert 2 <= inner.mean() <= 12 and inner.max() <= 12, (s, inner.min(), inner.max(), inner.mean())
+        assert abs(k_ip - k_ex) <= 2, (s, k_ip, k_ex)
