@@ -155,3 +155,59 @@ def test_adaptive_tolerance_picard_loop():
     h_ad, it_ad = run(True)
     assert abs(h_ad[-1] - h_fix[-1]) <= 1e-3 * h_fix[-1], (h_ad[-1], h_fix[-1])
     assert it_ad < 0.85 * it_fix, (it_ad, it_fix)
+
+
+def _table3_rows():
+    import os
+    rows = []
+    with open(os.path.join(os.path.dirname(__file__), "golden", "table3_topopt.txt")) as fh:
+        for line in fh:
+            if line.startswith("#") or not line.strip():
+                continue
+            rows.append([int(v) for v in line.split()[1:]])
+    return np.array(rows)
+
+
+def test_table3_trend_of_the_oracle_picard_loop():
+    # Table 3 (tests/golden/table3_topopt.txt): Picard steps grow from h = 1/16
+    # to 1/32 while the average Krylov count per step barely moves.  The
+    # oracle's loop (p = 1 cantilever, OC, adaptive tolerance Q23, interface
+    # PCG with the face-local preconditioner, 8 subdomains, stop at
+    # max |rho_new - rho| < 0.01; reading Q24) shows the same.
+    from oracle import dd
+    paper = _table3_rows()
+    paper_step_growth = paper[1, 0] / paper[0, 0]          # 4 domains, h 1/16 -> 1/32
+    paper_its_growth = paper[1, 1] / paper[0, 1]
+    out = []
+    for nx in (32, 64):
+        ny, sub = nx // 2, nx // 4
+        grid = fem.Grid(2, nx, ny)
+        fixed, f = fem.bc_from_spec(grid, workloads.cantilever_2d(nx, ny))
+        Ke = fem.element_stiffness(2, 1.0, 0.3)
+        H = topopt.filter_matrix((nx, ny), 1.5)
+        nf = np.linalg.norm(f)
+        rho = np.full(grid.n_elem, 0.5)
+        hist, its, steps = [], 0, 0
+        while steps < 100:
+            tol = topopt.adaptive_tolerance(hist, 0.1, 1e-8, 1e-3)
+
+            def solve(fac):
+                nonlocal its
+                dec, K, dds = dd.build(grid, sub, fixed, Ke, fac)
+                pre = dd.FacePreconditioner(dec, K)
+                x, k = dd.pcg(dds.schur_apply, pre.apply, dds.condense(f), tol, 5000, ref_norm=nf)[:2]
+                its += k
+                return dds.back_substitute(f, x)
+
+            new, c, _, _ = topopt.topopt_step(grid, Ke, 1.0, 1.0, H, rho, f, solve, 0.5)
+            change = np.abs(new - rho).max()
+            rho = new
+            hist.append(c)
+            steps += 1
+            if change < 0.01:
+                break
+        out.append((steps, its / steps))
+    step_growth = out[1][0] / out[0][0]
+    its_growth = out[1][1] / out[0][1]
+    assert step_growth > 1.0 and paper_step_growth > 1.0, out
+    assert abs(its_growth - paper_its_growth) < 0.2, (out, paper_its_growth)
