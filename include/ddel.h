@@ -7,6 +7,9 @@
  *  - Every function returns a ddel_status (0 = success, < 0 = error).  No call
  *    aborts the process and no C++ exception crosses this boundary.
  *    ddel_strerror() gives a message; ddel_last_error() the context's last one.
+ *    Besides the errors a call lists: DDEL_EINVAL for a null context or a null
+ *    required pointer, DDEL_ESTATE for a call before its prerequisite (see the
+ *    step-level section), DDEL_ECUDA when a CUDA runtime call fails.
  *  - Plain pointers and sizes only.  "device" pointers are CUDA device memory
  *    of the current device (e.g. from torch); "host" pointers are ordinary (or
  *    pinned) host memory.  Every pointer argument says which it is.
@@ -291,7 +294,10 @@ int ddel_batch_solve(ddel_ctx* const* ctxs, int n, double* const* u, ddel_stats*
 int ddel_autotune(ddel_ctx* ctx, const char* cache_path, int* chosen_mode, int* chosen_check,
                   int* from_cache);
 
-/* --- Step-level entry points (device pointers; asynchronous) --------------- */
+/* --- Step-level entry points (device pointers; asynchronous) ---------------
+ * Prerequisites (DDEL_ESTATE otherwise): ddel_assemble for apply_K,
+ * precond_apply and residual_norm; ddel_factor for condense, schur_apply,
+ * schur_apply_ring, back_substitute and pcg. */
 /* y = K(rho) x over all free DOFs (fixed rows 0), element by element, FP64. */
 int ddel_apply_K(ddel_ctx* ctx, const double* x, double* y);
 /* g = f_G - sum_i K_{G I_i} K_{I_i I_i}^-1 f_{I_i} (eq. 3MatSplit2, second line). */
