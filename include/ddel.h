@@ -406,6 +406,16 @@ int ddel_plan_face_block(const ddel_plan* plan, int b, int32_t* off, int32_t* n,
                          double* hmean);
 /* Unit-E element stiffness (host, (dim 2^dim)^2 doubles, row-major). */
 int ddel_plan_element_matrix(const ddel_plan* plan, double* Ke);
+/* The interface mass M and Laplacian L of eq. NumberEight assembled on all of
+ * Gamma (the global form of the paper's Tables 1-3, not the face-local one of
+ * the preconditioner) for displacement component comp, restricted to that
+ * component's free Gamma DOFs: CSR matrices of *n rows with *nnz entries,
+ * ascending columns, rows and columns in Gamma order (pos[r] = the Gamma
+ * position of row r).  Host arrays: pos (n), rowptr (n + 1), col, M, L (nnz);
+ * with pos == NULL only *n and *nnz are returned.  Errors: EINVAL (null plan,
+ * comp outside [0, dim), null n or nnz). */
+int ddel_plan_interface_operator(const ddel_plan* plan, int comp, int32_t* n, int64_t* nnz, int32_t* pos,
+                                 int64_t* rowptr, int32_t* col, double* M, double* L);
 /* Interior box of subdomain i: ilo[3], icnt[3] (host int32). */
 int ddel_plan_subdomain(const ddel_plan* plan, int i, int32_t* ilo, int32_t* icnt);
 

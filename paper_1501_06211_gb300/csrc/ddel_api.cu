@@ -1556,6 +1556,25 @@ int ddel_plan_element_matrix(const ddel_plan* plan, double* Ke) {
   return DDEL_OK;
 }
 
+int ddel_plan_interface_operator(const ddel_plan* plan, int comp, int32_t* n, int64_t* nnz, int32_t* pos,
+                                 int64_t* rowptr, int32_t* col, double* M, double* L) {
+  if (!plan || !n || !nnz || comp < 0 || comp >= plan->S.dim) return DDEL_EINVAL;
+  std::vector<int32_t> p, c;
+  std::vector<int64_t> rp;
+  std::vector<double> m, l;
+  interface_operator(plan->S, comp, &p, &rp, &c, &m, &l);
+  *n = (int32_t)p.size();
+  *nnz = (int64_t)c.size();
+  if (!pos) return DDEL_OK;
+  if (!rowptr || !col || !M || !L) return DDEL_EINVAL;
+  std::memcpy(pos, p.data(), p.size() * sizeof(int32_t));
+  std::memcpy(rowptr, rp.data(), rp.size() * sizeof(int64_t));
+  std::memcpy(col, c.data(), c.size() * sizeof(int32_t));
+  std::memcpy(M, m.data(), m.size() * sizeof(double));
+  std::memcpy(L, l.data(), l.size() * sizeof(double));
+  return DDEL_OK;
+}
+
 int ddel_plan_subdomain(const ddel_plan* plan, int i, int32_t* ilo, int32_t* icnt) {
   if (!plan || i < 0 || i >= plan->S.n_sub || !ilo || !icnt) return DDEL_EINVAL;
   for (int a = 0; a < 3; ++a) {

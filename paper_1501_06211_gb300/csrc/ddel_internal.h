@@ -78,6 +78,16 @@ std::string build_setup(int dim, const int ne[3], int sub, double E, double nu, 
 // on unit elements), local node order (0,0),(1,0),(1,1),(0,1) [then z=1].
 void element_stiffness(int dim, double nu, int plane_stress, std::vector<double>* Ke);
 
+// Mass and Laplacian of eq. NumberEight assembled on all of Gamma for one
+// displacement component (the form of the paper's Tables 1-3): unit-edge P1
+// (2D) / unit-square Q1 (3D) element matrices over the facets that lie on
+// Gamma -- those whose normal coordinate is an interior multiple of the
+// subdomain edge -- restricted to the component's free Gamma DOFs.  Rows and
+// columns follow the Gamma order (pos: the Gamma positions of the rows);
+// CSR with ascending columns.
+void interface_operator(const Setup& S, int comp, std::vector<int32_t>* pos, std::vector<int64_t>* rowptr,
+                        std::vector<int32_t>* col, std::vector<double>* M, std::vector<double>* L);
+
 // Generalized symmetric eigenproblem L V = M V diag(mu), V^T M V = I, by a
 // Cholesky reduction and cyclic Jacobi rotations.  n <= 128.  Returns false if
 // M is not positive definite.

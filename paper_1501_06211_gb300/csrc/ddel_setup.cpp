@@ -509,4 +509,92 @@ std::string build_setup(int dim, const int ne_in[3], int sub, double E, double n
   return "";
 }
 
+void interface_operator(const Setup& S, int comp, std::vector<int32_t>* pos, std::vector<int64_t>* rowptr,
+                        std::vector<int32_t>* col, std::vector<double>* M, std::vector<double>* L) {
+  const int dim = S.dim, s = S.sub;
+  // Gamma positions of this component, and the local row of each node
+  std::vector<int32_t> local(S.n_nodes, -1);
+  pos->clear();
+  for (size_t k = 0; k < S.gamma_dof.size(); ++k) {
+    const int64_t d = S.gamma_dof[k];
+    if (d % dim != comp) continue;
+    local[d / dim] = (int32_t)pos->size();
+    pos->push_back((int32_t)k);
+  }
+  const size_t n = pos->size();
+  std::vector<std::map<int32_t, std::pair<double, double>>> rows(n);
+  auto node = [&](const int c[3]) -> int64_t {
+    return ((int64_t)c[0] * S.nn[1] + c[1]) * S.nn[2] + c[2];
+  };
+  auto add = [&](const int64_t* nodes, int m, const double* Me, const double* Le) {
+    for (int a = 0; a < m; ++a) {
+      const int32_t ra = local[nodes[a]];
+      if (ra < 0) continue;
+      for (int b = 0; b < m; ++b) {
+        const int32_t rb = local[nodes[b]];
+        if (rb < 0) continue;
+        auto& e = rows[ra][rb];
+        e.first += Me[a * m + b];
+        e.second += Le[a * m + b];
+      }
+    }
+  };
+  const double M1[4] = {2.0 / 6, 1.0 / 6, 1.0 / 6, 2.0 / 6};
+  const double L1[4] = {1.0, -1.0, -1.0, 1.0};
+  if (dim == 2) {
+    for (int a = 0; a < 2; ++a) {  // edges along axis a on the interface lines of the other axis
+      const int b = 1 - a;
+      for (int y = s; y < S.ne[b]; y += s)
+        for (int x = 0; x < S.ne[a]; ++x) {
+          int c0[3] = {0, 0, 0}, c1[3] = {0, 0, 0};
+          c0[a] = x;
+          c1[a] = x + 1;
+          c0[b] = c1[b] = y;
+          const int64_t nodes[2] = {node(c0), node(c1)};
+          add(nodes, 2, M1, L1);
+        }
+    }
+  } else {
+    // unit-square Q1: M = M1 (x) M1, L = L1 (x) M1 + M1 (x) L1, nodes (i, j) -> 2 i + j
+    double M2[16], L2[16];
+    for (int i1 = 0; i1 < 2; ++i1)
+      for (int j1 = 0; j1 < 2; ++j1)
+        for (int i2 = 0; i2 < 2; ++i2)
+          for (int j2 = 0; j2 < 2; ++j2) {
+            const int r = 2 * i1 + j1, c = 2 * i2 + j2;
+            M2[r * 4 + c] = M1[i1 * 2 + i2] * M1[j1 * 2 + j2];
+            L2[r * 4 + c] = L1[i1 * 2 + i2] * M1[j1 * 2 + j2] + M1[i1 * 2 + i2] * L1[j1 * 2 + j2];
+          }
+    for (int a = 0; a < 3; ++a) {  // quads normal to axis a on the interface planes
+      const int b = a == 0 ? 1 : 0, c = a == 2 ? 1 : 2;
+      for (int x = s; x < S.ne[a]; x += s)
+        for (int eb = 0; eb < S.ne[b]; ++eb)
+          for (int ec = 0; ec < S.ne[c]; ++ec) {
+            int64_t nodes[4];
+            for (int i = 0; i < 2; ++i)
+              for (int j = 0; j < 2; ++j) {
+                int q[3];
+                q[a] = x;
+                q[b] = eb + i;
+                q[c] = ec + j;
+                nodes[2 * i + j] = node(q);
+              }
+            add(nodes, 4, M2, L2);
+          }
+    }
+  }
+  rowptr->assign(n + 1, 0);
+  col->clear();
+  M->clear();
+  L->clear();
+  for (size_t r = 0; r < n; ++r) {
+    for (const auto& kv : rows[r]) {
+      col->push_back(kv.first);
+      M->push_back(kv.second.first);
+      L->push_back(kv.second.second);
+    }
+    (*rowptr)[r + 1] = (int64_t)col->size();
+  }
+}
+
 }  // namespace ddel

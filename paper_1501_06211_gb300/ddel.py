@@ -160,6 +160,8 @@ def _load():
         "ddel_plan_info": (c_int, [c_void_p, P(ddel_info_t)]),
         "ddel_plan_gamma_dofs": (c_int, [c_void_p, c_void_p]),
         "ddel_plan_face_block": (c_int, [c_void_p, c_int, c_void_p, c_void_p, c_void_p, c_void_p]),
+        "ddel_plan_interface_operator": (c_int, [c_void_p, c_int, c_void_p, c_void_p, c_void_p, c_void_p,
+                                                 c_void_p, c_void_p, c_void_p]),
         "ddel_plan_element_matrix": (c_int, [c_void_p, c_void_p]),
         "ddel_plan_subdomain": (c_int, [c_void_p, c_int, c_void_p, c_void_p]),
     }
@@ -552,6 +554,22 @@ class Plan:
         K = np.zeros((nd, nd))
         _check(_lib.ddel_plan_element_matrix(self.h, K.ctypes.data))
         return K
+
+    def interface_operator(self, comp):
+        """(pos, rowptr, col, M, L): CSR mass and Laplacian on all of Gamma for
+        component comp, rows in Gamma order (pos: their Gamma positions)."""
+        n, nnz = ctypes.c_int32(), ctypes.c_int64()
+        _check(_lib.ddel_plan_interface_operator(self.h, comp, ctypes.byref(n), ctypes.byref(nnz),
+                                                 None, None, None, None, None))
+        pos = np.zeros(n.value, dtype=np.int32)
+        rowptr = np.zeros(n.value + 1, dtype=np.int64)
+        col = np.zeros(nnz.value, dtype=np.int32)
+        M = np.zeros(nnz.value)
+        L = np.zeros(nnz.value)
+        _check(_lib.ddel_plan_interface_operator(self.h, comp, ctypes.byref(n), ctypes.byref(nnz),
+                                                 pos.ctypes.data, rowptr.ctypes.data, col.ctypes.data,
+                                                 M.ctypes.data, L.ctypes.data))
+        return pos, rowptr, col, M, L
 
     def subdomain(self, i):
         ilo = np.zeros(3, dtype=np.int32)

@@ -141,3 +141,35 @@ def test_load_vectors_match_oracle():
         # plan reports against the oracle construction instead
         grid, fixed, f, dec = _oracle(cfg)
         assert plan.info.n_gamma == len(dec.gamma_dofs)
+
+
+@pytest.mark.parametrize("cfg", CASES, ids=lambda c: c["name"])
+def test_interface_operator_matches_oracle(cfg):
+    # mass and Laplacian on all of Gamma (the global form of Tables 1-3) per
+    # component, against the oracle's own facet assembly restricted to the
+    # same free Gamma DOFs
+    ddel = _lib()
+    plan = ddel.Plan(cfg, theta=0.5)
+    grid, fixed, f, dec = _oracle(cfg)
+    M, L = dd.interface_mass_laplacian(dec)
+    g_lib = plan.gamma_dofs()
+    d = cfg["dim"]
+    total = 0
+    for c in range(d):
+        pos, rowptr, col, Mv, Lv = plan.interface_operator(c)
+        assert np.all(np.diff(pos) > 0) and np.all(g_lib[pos] % d == c)
+        total += len(pos)
+        nodes = g_lib[pos] // d
+        n = len(pos)
+        Ml = np.zeros((n, n))
+        Ll = np.zeros((n, n))
+        for r in range(n):
+            cols = col[rowptr[r]:rowptr[r + 1]]
+            assert np.all(np.diff(cols) > 0)
+            Ml[r, cols] = Mv[rowptr[r]:rowptr[r + 1]]
+            Ll[r, cols] = Lv[rowptr[r]:rowptr[r + 1]]
+        assert np.allclose(Ml, M[nodes][:, nodes].toarray(), rtol=1e-13, atol=1e-15)
+        assert np.allclose(Ll, L[nodes][:, nodes].toarray(), rtol=1e-13, atol=1e-14)
+    assert total == len(g_lib)
+    with pytest.raises(RuntimeError):
+        plan.interface_operator(d)
