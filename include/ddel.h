@@ -52,7 +52,13 @@ typedef enum {
   DDEL_ETIMEOUT = -8     /* a bounded device wait ran out; the kernel returned */
 } ddel_status;
 
-/* FP64: factors, local Schur complements and their applications in FP64.
+/* FP64: factors and local Schur complements formed in FP64.  How S_i is
+ *       applied inside PCG depends on schur_mode: EXPLICIT and IMPLICIT apply
+ *       it in native FP64 arithmetic (the plain FP64 method); AUTO (the
+ *       default) forms S_i in double-float arithmetic and applies it as FP32
+ *       (hi, lo) pairs, about 48 significant bits -- a reduced-precision
+ *       operator inside an FP64 Krylov iteration, FP64 residual and FP64
+ *       refinement (ddel_kernel_info_t.double_float reports it).
  * FP32: factors and applications in FP32 (FP64 Krylov vectors and dot
  *       products, FP64 residual and refinement).
  * MIXED: FP64 factors and local Schur complements, which are stored and
@@ -138,7 +144,8 @@ typedef struct {
   int bad_subdomain;   /* first subdomain with a failed pivot, or -1 */
   int fallback;        /* bit 0: an FP32 solve switched to the FP64 factors; bit 1: the
                           coarse space was dropped after a Krylov breakdown */
-  double t_factor_ms, t_condense_ms, t_pcg_ms, t_backsub_ms, t_verify_ms, t_total_ms;
+  double t_factor_ms;  /* device time of the context's last ddel_factor (with S_i formation) */
+  double t_condense_ms, t_pcg_ms, t_backsub_ms, t_verify_ms, t_total_ms;
   int coarse_k;        /* coarse dimension used by the interface PCG (0: none) */
   int x0_used;         /* cycles whose PCG started from the Galerkin guess */
 } ddel_stats;
@@ -345,6 +352,14 @@ typedef struct {
 } ddel_kernel_info_t;
 int ddel_kernel_info(const ddel_ctx* ctx, ddel_kernel_info_t* out);
 
+/* Self-test of failure detection without a fault: a kernel waits on a device
+ * barrier that nothing completes, through the same bounded wait (poll_limit
+ * polls, 1 <= poll_limit <= 2^22) and error word as the solver's bulk-copy
+ * waits, and gives up; *status = DDEL_ETIMEOUT when the timeout was detected
+ * and reported (DDEL_OK would mean the wait completed, which cannot happen).
+ * The paper has no counterpart.  Synchronises the device. */
+int ddel_selftest_wait_timeout(unsigned int poll_limit, int* status);
+
 /* --- Residual check without allocation ----------------------------------------
  * The paper has no counterpart: this entry point exists for callers that cannot
  * allocate device memory themselves -- code running under an allocator or
@@ -369,22 +384,15 @@ int ddel_kernel_info(const ddel_ctx* ctx, ddel_kernel_info_t* out);
  * Scratch: a fixed 64 KB device array inside the library (one pair of partial
  * sums per thread block plus an arrival counter), present on every GPU that
  * loads the library until the process exits.  It caps the grid at 1,048,576
- * nodes; larger grids return DDEL_EINVAL without launching.  The first call on
- * each device looks up the array's device address (with that device current);
- * make that first call before any stream capture.  Every call on a device
+ * nodes; larger grids return DDEL_EINVAL without launching.  Every call looks
+ * up the array's device address on the current device (the first call on a
+ * device may load the library's device code there: make it before any stream
+ * capture).  Every call on a device
  * shares the one array: calls whose kernels overlap on the GPU (different
  * streams, no ordering between them) race and may return wrong norms;
  * serialise them.  The call clears the counter itself; no other state carries
  * over between calls.  Errors: EINVAL (sizes, null inputs, grid too large),
  * ECUDA (device address lookup or launch failed). */
-/* Self-test of failure detection without a fault: a kernel waits on a device
- * barrier that nothing completes, through the same bounded wait (poll_limit
- * polls, 1 <= poll_limit <= 2^22) and error word as the solver's bulk-copy
- * waits, and gives up; *status = DDEL_ETIMEOUT when the timeout was detected
- * and reported (DDEL_OK would mean the wait completed, which cannot happen).
- * The paper has no counterpart.  Synchronises the device. */
-int ddel_selftest_wait_timeout(unsigned int poll_limit, int* status);
-
 int ddel_residual_norm_noalloc(int dim, int nx, int ny, int nz, const double* Ke,
                                const double* factors, const uint8_t* fixed, const double* f,
                                const double* u, double* r, double* norms, void* cuda_stream);

@@ -74,7 +74,8 @@ struct ddel_ctx {
   int graph_iters = 0;
   int64_t launches = 0;           // kernel launches issued (graph-contained ones included)
   int64_t launches_at_assemble = 0;
-  cudaEvent_t ev[8] = {};
+  cudaEvent_t ev[10] = {};        // [8], [9]: around the last ddel_factor
+  double t_factor_ms = 0.0;       // device time of the last ddel_factor (with S_i formation)
   // topology optimisation buffers (allocated on first use)
   double *rho_f = nullptr, *dcf = nullptr, *dc = nullptr, *dv = nullptr, *topo_u = nullptr;
   double* topo_out = nullptr;    // device: lambda, volume, change, compliance
@@ -738,6 +739,7 @@ int ddel_factor(ddel_ctx* ctx) {
   if (!ctx) return DDEL_EINVAL;
   if (!ctx->assembled) return fail(ctx, DDEL_ESTATE, "assemble before factor");
   const int want = ctx->opt.precision == DDEL_FP32 ? 1 : 0;
+  CK(cudaEventRecord(ctx->ev[8], ctx->stream));
   int rc = factor_prec(ctx, want);
   if (rc == DDEL_ENOTSPD && want == 1) rc = factor_prec(ctx, 0);  // FP32 pivot failed: FP64
   if (rc == DDEL_OK) ctx->active_prec = ctx->factored[want] ? want : 0;
@@ -752,6 +754,11 @@ int ddel_factor(ddel_ctx* ctx) {
     ctx->launches += 1;
     CK(cudaGetLastError());
     ctx->mixed_ready = true;
+  }
+  if (rc == DDEL_OK) {
+    CK(cudaEventRecord(ctx->ev[9], ctx->stream));
+    CK(cudaEventSynchronize(ctx->ev[9]));
+    ctx->t_factor_ms = elapsed(ctx->ev[8], ctx->ev[9]);
   }
   return rc;
 }
@@ -896,6 +903,7 @@ int ddel_solve(ddel_ctx* ctx, const double* f, double* u, int on_device, ddel_st
     CK(cudaMemcpyAsync(u, ctx->d_u, nd * 8, cudaMemcpyDeviceToHost, s));
   CK(cudaEventRecord(ctx->ev[6], s));
   CK(cudaStreamSynchronize(s));
+  st.t_factor_ms = ctx->t_factor_ms;
   st.t_condense_ms = t_cond;
   st.t_pcg_ms = t_pcg;
   st.t_backsub_ms = t_back;

@@ -10,7 +10,6 @@
 #include <cuda_runtime.h>
 
 #include <cmath>
-#include <mutex>
 
 #include "../../include/ddel.h"
 #include "ddel_device.cuh"
@@ -30,10 +29,6 @@ struct NoAllocScratch {
   unsigned ticket;
 };
 static __device__ __align__(256) NoAllocScratch g_noalloc_scratch;
-
-constexpr int kMaxDevices = 64;
-std::mutex g_mutex;
-NoAllocScratch* g_addr[kMaxDevices] = {};
 
 template <int DIM>
 __global__ void __launch_bounds__(kThreads) residual_noalloc_kernel(
@@ -121,20 +116,13 @@ extern "C" int ddel_residual_norm_noalloc(int dim, int nx, int ny, int nz, const
   if (!Ke || !factors || !f || !u || !norms) return DDEL_EINVAL;
   const int64_t n_nodes = (int64_t)(nx + 1) * (ny + 1) * (dim == 3 ? (int64_t)(nz + 1) : 1);
   if (n_nodes > (int64_t)kMaxBlocks * kThreads) return DDEL_EINVAL;  // beyond the scratch capacity
-  int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return DDEL_ECUDA;
-  NoAllocScratch* scr;
-  {
-    // set-up, once per device, with that device current: the device address of
-    // the scratch array (its host-side name is only a stand-in)
-    std::lock_guard<std::mutex> lock(g_mutex);
-    if (!g_addr[dev]) {
-      void* p = nullptr;
-      if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) return DDEL_ECUDA;
-      g_addr[dev] = static_cast<NoAllocScratch*>(p);
-    }
-    scr = g_addr[dev];
-  }
+  // the device address of the scratch array on the current device (its
+  // host-side name is only a stand-in), looked up on every call: the lookup
+  // allocates nothing, and no address outlives a cudaDeviceReset or a reload
+  // of the library
+  void* p = nullptr;
+  if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) return DDEL_ECUDA;
+  NoAllocScratch* scr = static_cast<NoAllocScratch*>(p);
   cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
   // the arrival counter must start at zero
   if (cudaMemsetAsync(&scr->ticket, 0, sizeof(unsigned), s) != cudaSuccess) return DDEL_ECUDA;

@@ -1,7 +1,8 @@
 """GPU parity of the 3D H8 path against the oracle.
 
 Small grids (several subdomains, boundary planes of different sizes, padded
-blocks) are compared element by element at every step and for the full solve;
+blocks; one of them with the 8^3-element subdomains of the 96x48x48 workload)
+are compared element by element at every step and for the full solve;
 the full 96x48x48 workload (432 subdomains of 8^3) is checked through the
 residual computed by the oracle's own matrix-free K(rho).
 """
@@ -19,6 +20,9 @@ pytestmark = pytest.mark.gpu
 CASES = {
     "3d_16x8x8_s4": workloads.small_config(16, 8, 4, seed=1, nz=8),
     "3d_12x12x8_s4": workloads.small_config(12, 12, 4, seed=2, nz=8),
+    # the subdomains of the 96x48x48 workload (8^3 elements): the middle ones
+    # have interior planes of 7 x 7 nodes (147 DOFs), as there
+    "3d_16x24x24_s8": workloads.small_config(16, 24, 8, seed=3, nz=24),
 }
 
 

@@ -189,28 +189,60 @@ def test_error_paths():
     assert st.status == ddel.DDEL_ENOCONV
 
 
-@pytest.mark.parametrize("prec", [0, 1])
-def test_full_size_config1_residual(prec):
-    # 512x256 Q1, 512 subdomains, GRF densities: the oracle's sparse K(rho)
-    # checks the GPU solution's residual; a sampled comparison against the
-    # oracle's direct solution bounds the error.
+@functools.lru_cache(maxsize=None)
+def config1_oracle():
+    # 512x256 Q1, 512 subdomains, GRF densities: the oracle's sparse K(rho) and
+    # its direct solution (SuperLU + 3 refinement steps with an
+    # extended-precision residual)
     cfg = workloads.config("c1")
-    from paper_1501_06211_gb300 import ddel
     grid = fem.Grid(2, *cfg["ne"])
     fixed, f = fem.bc_from_spec(grid, cfg["bc"])
     rho = workloads.density(cfg)
     Ke = fem.element_stiffness(2, 1.0, cfg["nu"])
     K = fem.assemble(grid, Ke, fem.element_factors(rho, 1.0, 3.0))
-    s = ddel.Solver(cfg, precision=prec, tol=1e-8, max_it=20000)
+    u_ref = direct.solve(K, f, fixed, refine=3)
+    return cfg, rho, K, f, fixed, u_ref
+
+
+@pytest.mark.parametrize("prec,mode", [(0, 1), (0, 2), (1, 2)],
+                         ids=["fp64_native", "fp64_double_float", "fp32_refined"])
+def test_full_size_config1_parity(prec, mode):
+    # The full 512x256 workload solved tighter than the benchmark's 1e-8
+    # (reading Q13: forward error can exceed the residual at contrast 1e9),
+    # then held to the stated bars against the oracle's direct solution:
+    # displacement and energy-norm error <= 1e-8 for the FP64 operator (native
+    # or double-float), <= 1e-6 after refinement for the FP32 form.
+    from paper_1501_06211_gb300 import ddel
+    cfg, rho, K, f, fixed, u_ref = config1_oracle()
+    assert direct.rel_residual(K, f, u_ref, fixed) <= 1e-10  # the FP64 evaluation floor: ~1e-11
+    s = ddel.Solver(cfg, precision=prec, schur_mode=mode, tol=1e-10, max_it=20000, max_cycles=60,
+                    inner_tol=0.1)
+    s.assemble(rho)
+    s.factor()
+    u, st = s.solve(check=False)
+    rr = direct.rel_residual(K, f, u, fixed)
+    assert rr <= 1e-9, (rr, st.as_dict())
+    e = u - u_ref
+    err = rel(u, u_ref)
+    err_energy = np.sqrt(max(e @ (K @ e), 0.0) / (u_ref @ (K @ u_ref)))
+    bar = 1e-8 if prec == 0 else 1e-6
+    assert err <= bar and err_energy <= bar, (err, err_energy, st.as_dict())
+
+
+def test_full_size_config1_sampled_at_bench_tolerance():
+    # the benchmark's own launch configuration (tol 1e-8, default form): the
+    # residual under the oracle's K and sampled displacement entries
+    from paper_1501_06211_gb300 import ddel
+    cfg, rho, K, f, fixed, u_ref = config1_oracle()
+    s = ddel.Solver(cfg, schur_mode=1, tol=1e-8, max_it=20000, inner_tol=0.1, max_cycles=60)
     s.assemble(rho)
     s.factor()
     u, st = s.solve()
     assert st.status == 0
-    rr = direct.rel_residual(K, f, u, fixed)
-    assert rr <= 1e-8, (rr, st.as_dict())
-    u_ref = direct.solve(K, f, fixed)
-    # error relative to the solution norm, judged against the residual bound
-    assert rel(u, u_ref) <= 1e-5, rel(u, u_ref)
+    assert direct.rel_residual(K, f, u, fixed) <= 1e-8
+    idx = np.random.default_rng(7).choice(len(u), 2000, replace=False)
+    scale = np.abs(u_ref).max()
+    assert np.abs(u[idx] - u_ref[idx]).max() <= 1e-5 * scale
 
 
 def test_schur_apply_ring_alone():

@@ -65,6 +65,15 @@ def test_schur_symmetric_spd_and_block_inverse():
     assert np.allclose(dds.schur_apply(x), S @ x, rtol=1e-11, atol=1e-12 * np.abs(S @ x).max())
 
 
+def test_schur_apply_on_a_pool_is_bitwise_serial():
+    # the subdomain pool of the CPU baseline changes no arithmetic
+    import concurrent.futures
+    grid, fixed, f, Ke, fac, dec, K, dds = _system(32, 16, 8, seed=5)
+    x = np.random.default_rng(2).standard_normal(len(dec.gamma_dofs))
+    with concurrent.futures.ThreadPoolExecutor(4) as pool:
+        assert np.array_equal(dds.schur_apply(x, pool=pool), dds.schur_apply(x))
+
+
 @pytest.mark.parametrize("seed", [None, 3])
 def test_dd_solution_equals_direct(seed):
     grid, fixed, f, Ke, fac, dec, K, dds = _system(32, 16, 8, seed=seed)

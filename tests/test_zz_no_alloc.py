@@ -1,4 +1,5 @@
-"""The residual check that allocates nothing, against the context's entry point.
+"""The residual check that allocates nothing, against the context's entry point
+and against the oracle's assembled K(rho).
 
 Callers that cannot allocate device memory (an allocator that forbids
 cudaMalloc, or a component that only receives device buffers) use
@@ -10,6 +11,7 @@ import numpy as np
 import pytest
 
 import workloads
+from oracle import fem
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -30,6 +32,9 @@ def test_noalloc_residual_matches_context_entry_point():
     f = torch.as_tensor(s.load_vector(), device="cuda")
     u = torch.zeros_like(f)
     s.solve(f, u)
+    grid = fem.Grid(2, nx, ny)
+    K_or = fem.assemble(grid, fem.element_stiffness(2, 1.0, cfg["nu"]),
+                        fem.element_factors(rho, cfg["E"], cfg["p"])).tocsr()
     # a second, unconverged displacement so that the two calls differ
     u2 = u * 0.5 + 1e-3 * torch.randn_like(u)
     for uu in (u, u2):  # two calls in a row
@@ -53,6 +58,16 @@ def test_noalloc_residual_matches_context_entry_point():
         expect = torch.where(fixed.bool(), torch.zeros_like(f), f - Ku)
         torch.cuda.synchronize()
         assert float((r - expect).abs().max()) <= 1e-12 * float(f.abs().max())
+        # and against the oracle's own residual: its assembled K(rho) (3x3
+        # Gauss element matrix, eq. NumberTen factors) on the same u
+        un = uu.cpu().numpy()
+        fn_h = f.cpu().numpy()
+        fx = fixed.cpu().numpy().astype(bool)
+        r_or = fn_h - K_or @ np.where(fx, 0.0, un)
+        r_or[fx] = 0.0
+        assert np.abs(r.cpu().numpy() - r_or).max() <= 1e-12 * np.abs(fn_h).max()
+        assert abs(rn - np.linalg.norm(r_or)) <= 1e-12 * np.linalg.norm(fn_h[~fx])
+        assert abs(fn - np.linalg.norm(fn_h[~fx])) <= 1e-14 * fn
 
 
 def test_noalloc_rejects_oversized_grid():
