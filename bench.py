@@ -578,11 +578,20 @@ def cpu_info():
     cores = len(os.sched_getaffinity(0))
     model = None
     try:
-        for line in open("/proc/cpuinfo"):
-            k = line.split(":")[0].strip().lower()
-            if k in ("model name", "cpu model", "hardware"):
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.lower().startswith("model name"):
                 model = line.split(":", 1)[1].strip()
                 break
+    except (OSError, subprocess.SubprocessError):
+        pass
+    try:
+        if model is None:
+            for line in open("/proc/cpuinfo"):
+                k = line.split(":")[0].strip().lower()
+                if k in ("model name", "cpu model", "hardware"):
+                    model = line.split(":", 1)[1].strip()
+                    break
     except OSError:
         pass
     if model is None:

@@ -923,6 +923,61 @@ __global__ void __launch_bounds__(256) schur_explicit_kernel(DevTables t, const 
   schur_pcg_epilogue<RH / 32>(io, d[0], red);  // delta: rows of this CTA
 }
 
+// Native FP64 form of the explicit apply, laid out like the double-float one:
+// each thread owns two adjacent rows and JN columns, reading both rows' entries
+// of a column as one 16-byte load (S_i column-major FP64), with two
+// accumulators per row; the H column groups of a row are added in group order.
+// GB300 issues two DFMA per clock per SM, so this product is bound by the FP64
+// pipe (2 n_ring^2 flop per subdomain) rather than by the bytes it streams.
+template <int NR>
+__global__ void __launch_bounds__(256, NR <= 128 ? 7 : 5) schur_explicit_f64_kernel(DevTables t,
+                                                                                   const double* __restrict__ Sexp,
+                                                                                   SchurIO io) {
+  const int done = io.done ? *io.done : 0;
+  constexpr int RH = NR / 2, RP = RH / 2, H = 256 / RP, JN = NR / H;
+  const int sub = blockIdx.x >> 1, half = blockIdx.x & 1, tid = threadIdx.x;
+  const SubInfo si = t.subs[sub];
+  __shared__ double xr[NR];
+  __shared__ double part[2 * 256];
+  __shared__ double red[RH / 32];
+  for (int j = tid; j < NR; j += 256) {
+    double v = 0.0;
+    if (j < si.n_ring) v = io.x[t.ring_gidx[si.ring_off + j]];
+    xr[j] = v;
+  }
+  if (done) return;  // uniform over the grid: converged in an earlier iteration
+  schur_pcg_prologue(io);
+  __syncthreads();
+  const int rp = tid % RP, h = tid / RP;
+  const int r0 = half * RH + 2 * rp;
+  const double2* Sc = reinterpret_cast<const double2*>(Sexp + (int64_t)sub * NR * NR);
+  double a0 = 0.0, b0 = 0.0, a1 = 0.0, b1 = 0.0;
+#pragma unroll 8
+  for (int q = 0; q < JN; q += 2) {
+    const int j = h * JN + q;
+    const double2 s0 = Sc[(j * NR + r0) >> 1];
+    const double2 s1 = Sc[((j + 1) * NR + r0) >> 1];
+    const double x0 = xr[j], x1 = xr[j + 1];
+    a0 = fma(s0.x, x0, a0);
+    a1 = fma(s0.y, x0, a1);
+    b0 = fma(s1.x, x1, b0);
+    b1 = fma(s1.y, x1, b1);
+  }
+  part[2 * tid] = a0 + b0;
+  part[2 * tid + 1] = a1 + b1;
+  __syncthreads();
+  double d[1] = {0.0};
+  const int row = half * RH + tid;
+  if (tid < RH && row < si.n_ring) {
+    double y = 0.0;
+#pragma unroll
+    for (int q = 0; q < H; ++q) y += part[2 * (q * RP + (tid >> 1)) + (tid & 1)];
+    reinterpret_cast<double*>(io.ring_out)[t.ring_dst[si.ring_off + row]] = y;
+    d[0] = xr[row] * y;
+  }
+  schur_pcg_epilogue<RH / 32>(io, d[0], red);
+}
+
 // ---- double-float form of the explicit apply --------------------------------
 // S_i is stored as pairs (hi, lo) of FP32 with hi + lo = S to 2^-48 relative,
 // the ring vector likewise, and each row sum is accumulated as a pair with the
@@ -1263,6 +1318,255 @@ __global__ void __launch_bounds__(kRedThreads) pcg_cg_kernel(DevTables t, DevFie
   if (threadIdx.x < NV) pu_out[(size_t)threadIdx.x * gridDim.x + blockIdx.x] = red[threadIdx.x * kRedThreads];
 }
 
+// Update j of the PCG (the non-INIT form of pcg_cg_kernel, same arithmetic in
+// the same order, so the iterates are bitwise those of that kernel) laid out
+// for latency: before the block reduces the partial sums and forms alpha_j,
+// beta_j, every lane issues the loads that need no scalar -- for its DOFs of
+// the warp's first face block (up to 32 PE of them) and its first cross-point
+// DOF: the owners' ring entries of S u, u, p, s, x, r and the face weight --
+// so that their latency overlaps the reduction's; only the arithmetic and the
+// preconditioner wait for the scalars.  Further blocks of a warp (more face
+// blocks than warps) load as they come.
+template <typename T, int KC>
+__global__ void __launch_bounds__(kRedThreads, 2) pcg_update_kernel(DevTables t, DevFields fld,
+                                                                 const T* __restrict__ ring, double* x,
+                                                                 double* r, double* u, double* p,
+                                                                 double* sv, PcgState* st, CoarseDev cd,
+                                                                 const double* __restrict__ pd, int nd,
+                                                                 const double* __restrict__ pu_in,
+                                                                 double* __restrict__ pu_out, int par) {
+  const int done = st->done;
+  constexpr int NV = 2 + 2 * KC, NP = 3 + 2 * KC, PE = 2;
+  extern __shared__ double rw_all[];  // (blockDim/32) * max_blk_n doubles, then as many float2
+  __shared__ double red[NP * kRedThreads];
+  __shared__ double sums[NP];
+  __shared__ double sab[2 + kMaxCoarse];
+  __shared__ int sflag;
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  double* rw = rw_all + wib * t.max_blk_n;
+  float2* rwf = reinterpret_cast<float2*>(rw_all + (blockDim.x >> 5) * t.max_blk_n) + wib * t.max_blk_n;
+  const int k = KC > 0 ? cd.k : 0;
+  const bool deflate = KC > 0 && cd.correct == 2;
+  const int j = st->kU;
+  const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int nw = (gridDim.x * blockDim.x) >> 5;
+  // --- loads that need no scalar, issued first
+  struct Dof {
+    double w, u, p, s, x, r, fw;
+  };
+  auto load_dof = [&](int64_t g, double fw) -> Dof {
+    Dof d;
+    d.w = ring_sum<T>(t, ring, g);
+    d.u = u[g];
+    d.p = p[g];
+    d.s = sv[g];
+    d.x = x[g];
+    d.r = r[g];
+    d.fw = fw;
+    return d;
+  };
+  const int b0 = gw;
+  int off0 = 0, n0 = 0;
+  if (b0 < t.n_blocks) {
+    off0 = t.blk_off[b0];
+    n0 = t.blk_n[b0];
+  }
+  const bool pre_ok = n0 <= 32 * PE;
+  Dof pre[PE];
+#pragma unroll
+  for (int e = 0; e < PE; ++e) {
+    const int i = lane + 32 * e;
+    if (pre_ok && i < n0) pre[e] = load_dof(off0 + i, fld.face_w[off0 + i]);
+  }
+  const int64_t gc0 = t.n_face_dofs + blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  Dof prc;
+  if (gc0 < t.n_gamma) prc = load_dof(gc0, fld.cross_scale[gc0 - t.n_face_dofs]);
+  // --- partial sums of the Schur apply (delta) and of update j-1 (gamma, rr,
+  //     coarse sums), then alpha_j, beta_j and the coarse coefficients
+  double alpha = 0.0, beta = 0.0;
+  double cc[KC > 0 ? KC : 1];
+  {
+    __shared__ double sEinv[KC > 0 ? KC * KC : 1], sE[KC > 0 ? KC * KC : 1];
+    constexpr int KD = KC > 0 ? KC : 1;
+    for (int i = threadIdx.x; i < KC * KC; i += blockDim.x) {
+      const int a = i / KD, b = i % KD;
+      if (a < k && b < k) {
+        sEinv[i] = cd.Einv[a * kMaxCoarse + b];
+        sE[i] = 0.5 * (cd.E[a * kMaxCoarse + b] + cd.E[b * kMaxCoarse + a]);
+      }
+    }
+    double tol2 = 0.0, ginv = 0.0, ainv = 0.0;
+    int max_it = 0;
+    if (threadIdx.x == 0) {
+      tol2 = st->tol2;
+      max_it = st->max_it;
+      ginv = st->ginv_s[par ^ 1];
+      ainv = st->ainv_s[par ^ 1];
+    }
+    const double* U = pu_in;
+    const int nu = gridDim.x;
+    double a[NP];
+#pragma unroll
+    for (int v = 0; v < NP; ++v) {
+      a[v] = 0.0;
+      if (v >= 3 && (v - 3) % (KC > 0 ? KC : 1) >= k) continue;
+      const double* src = v == 0 ? pd : U + (size_t)(v - 1) * nu;
+      const int n = v == 0 ? nd : nu;
+      for (int b = threadIdx.x; b < n; b += kRedThreads) a[v] += __ldcg(src + b);
+    }
+    if (done) return;  // uniform over the grid
+    block_tree_sum<NP>(a, NP, red);
+    if (threadIdx.x < NP) sums[threadIdx.x] = red[threadIdx.x * kRedThreads];
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double gamma = sums[1], delta = sums[0];
+      const double rr = sums[2];
+      const double* y = sums + 3;
+      const double* vq = sums + 3 + KC;
+      for (int i = 0; i < k; ++i) {
+        double c = 0.0;
+        for (int q = 0; q < k; ++q) c += sEinv[i * KC + q] * (y[q] - (deflate ? vq[q] : 0.0));
+        sab[2 + i] = c;
+      }
+      for (int i = 0; i < k; ++i) {
+        const double ci = sab[2 + i];
+        gamma += y[i] * ci;
+        double ec = 0.0;
+        for (int q = 0; q < k; ++q) ec += sE[i * KC + q] * sab[2 + q];
+        delta += ci * (2.0 * vq[i] + ec);
+      }
+      int status = 1;
+      double a_ = 0.0, b_ = 0.0, den = delta;
+      const double gi = 1.0 / gamma;
+      if (rr <= tol2) {
+        status = 0;
+      } else if (!isfinite(rr) || !isfinite(gamma)) {
+        status = -6;
+      } else if (j >= max_it) {
+        status = -5;
+      } else {
+        if (j > 0) {
+          b_ = gamma * ginv;
+          den = delta - b_ * gamma * ainv;
+        }
+        if (!(den > 0.0) || !isfinite(den)) status = -6;
+        else a_ = gamma / den;
+      }
+      sab[0] = a_;
+      sab[1] = b_;
+      sflag = status;
+      if (blockIdx.x == 0) {
+        st->rr = rr;
+        st->it = j;
+        if (status != 1) {
+          st->done = 1;
+          st->status = status;
+        } else {
+          st->ainv_s[par] = den * gi;
+          st->ginv_s[par] = gi;
+          st->kS = j + 1;
+        }
+      }
+    }
+    __syncthreads();
+    if (sflag != 1) return;
+    alpha = sab[0];
+    beta = sab[1];
+#pragma unroll
+    for (int i = 0; i < KC; ++i) cc[i] = i < k ? sab[2 + i] : 0.0;
+  }
+  auto coarse = [&](const double* V, int64_t g) -> double {
+    double v = 0.0;
+#pragma unroll
+    for (int i = 0; i < KC; ++i)
+      if (i < k) v += V[i * t.n_gamma + g] * cc[i];
+    return v;
+  };
+  double acc[NV];
+#pragma unroll
+  for (int i = 0; i < NV; ++i) acc[i] = 0.0;
+  // the vector updates at one DOF from its loaded values (the order of
+  // operations of pcg_cg_kernel)
+  auto step = [&](int64_t g, const Dof& d) -> double {
+    const double w = d.w + (KC > 0 ? coarse(cd.SQ, g) : 0.0);
+    const double pg = d.u + (KC > 0 ? coarse(cd.Q, g) : 0.0) + beta * d.p;
+    const double sg = w + beta * d.s;
+    p[g] = pg;
+    sv[g] = sg;
+    x[g] = d.x + alpha * pg;
+    const double rg = d.r - alpha * sg;
+    r[g] = rg;
+    acc[1] += rg * rg;
+#pragma unroll
+    for (int i = 0; i < KC; ++i)
+      if (i < k) acc[2 + i] += cd.Q[i * t.n_gamma + g] * rg;
+    return rg;
+  };
+  auto local = [&](int64_t g, double ri, double ui) {
+    u[g] = ui;
+    acc[0] += ri * ui;
+#pragma unroll
+    for (int i = 0; i < KC; ++i)
+      if (i < k) acc[2 + KC + i] += cd.SQ[i * t.n_gamma + g] * ui;
+  };
+  double rkeep[PE];  // r at this lane's DOFs of the current block
+  for (int b = gw; b < t.n_blocks; b += nw) {
+    const bool first = b == b0 && pre_ok;
+    const int off = first ? off0 : t.blk_off[b], n = first ? n0 : t.blk_n[b];
+    if (n <= 32 * PE) {
+#pragma unroll
+      for (int e = 0; e < PE; ++e) {
+        const int i = lane + 32 * e;
+        if (i < n) {
+          Dof d;
+          if (first) d = pre[e];
+          else d = load_dof(off + i, fld.face_w[off + i]);
+          const double ri = step(off + i, d);
+          rkeep[e] = ri;
+          const double v = ri * d.fw;  // W^-1 r (face_w holds 1 / W_ii)
+          rw[i] = v;
+          const float hi = (float)v;
+          rwf[i] = make_float2(hi, (float)(v - (double)hi));
+        }
+      }
+    } else {
+      for (int i = lane; i < n; i += 32) {
+        const double ri = step(off + i, load_dof(off + i, fld.face_w[off + i]));
+        const double v = ri * fld.face_w[off + i];
+        rw[i] = v;
+        const float hi = (float)v;
+        rwf[i] = make_float2(hi, (float)(v - (double)hi));
+      }
+    }
+    __syncwarp();
+    for (int i = lane; i < n; i += 32) {
+      const float2* Pc = t.ptab_df + t.blk_poff[b] + i;
+      float hi = 0.f, lo = 0.f;
+#pragma unroll 4
+      for (int q = 0; q < n; ++q) {
+        const float2 sq = Pc[q * n], xq = rwf[q];
+        const float pr = __fmul_rn(sq.x, xq.x);
+        lo = __fadd_rn(lo, __fadd_rn(__fmaf_rn(sq.x, xq.x, -pr), __fmaf_rn(sq.x, xq.y, __fmul_rn(sq.y, xq.x))));
+        df_add(hi, lo, pr);
+      }
+      const double zi = (double)hi + (double)lo;
+      const int e = (i - lane) >> 5;
+      const double ri = (n <= 32 * PE) ? (e == 0 ? rkeep[0] : rkeep[PE - 1]) : r[off + i];
+      local(off + i, ri, zi * fld.face_w[off + i]);
+    }
+    __syncwarp();
+  }
+  for (int64_t g = gc0; g < t.n_gamma; g += (int64_t)gridDim.x * blockDim.x) {
+    Dof d;
+    if (g == gc0) d = prc;
+    else d = load_dof(g, fld.cross_scale[g - t.n_face_dofs]);
+    const double ri = step(g, d);
+    local(g, ri, ri * d.fw);
+  }
+  block_tree_sum<NV>(acc, NV, red);
+  if (threadIdx.x < NV) pu_out[(size_t)threadIdx.x * gridDim.x + blockIdx.x] = red[threadIdx.x * kRedThreads];
+}
+
 __global__ void precond_kernel(DevTables t, DevFields fld, const double* __restrict__ r,
                                double* __restrict__ z) {
   const int lane = threadIdx.x & 31;
@@ -1547,9 +1851,9 @@ void launch_schur_explicit(const DevTables& t, int precision, const void* Sexp, 
   const int NR = explicit_ring_size(t);
   if (precision == 0) {
     const double* S = (const double*)Sexp;
-    if (NR == 64) schur_explicit_kernel<double, 64><<<2 * t.n_sub, 256, 0, st>>>(t, S, io);
-    else if (NR == 128) schur_explicit_kernel<double, 128><<<2 * t.n_sub, 256, 0, st>>>(t, S, io);
-    else schur_explicit_kernel<double, 256><<<2 * t.n_sub, 256, 0, st>>>(t, S, io);
+    if (NR == 64) schur_explicit_f64_kernel<64><<<2 * t.n_sub, 256, 0, st>>>(t, S, io);
+    else if (NR == 128) schur_explicit_f64_kernel<128><<<2 * t.n_sub, 256, 0, st>>>(t, S, io);
+    else schur_explicit_f64_kernel<256><<<2 * t.n_sub, 256, 0, st>>>(t, S, io);
   } else {
     const float* S = (const float*)Sexp;
     if (NR == 64) schur_explicit_kernel<float, 64><<<2 * t.n_sub, 256, 0, st>>>(t, S, io);
@@ -1705,16 +2009,16 @@ static void launch_update_t(const DevTables& t, const DevFields& fld, const T* r
   const size_t sm = update_smem(t);
   switch (cd.correct ? coarse_width(cd.k) : 0) {
     case 4:
-      pcg_cg_kernel<T, false, 4><<<nblk, kRedThreads, sm, st>>>(t, fld, nullptr, ring, x, r, u, p, sv, s, cd, pd,
-                                                                nd, pu_in, pu_out, par);
+      pcg_update_kernel<T, 4><<<nblk, kRedThreads, sm, st>>>(t, fld, ring, x, r, u, p, sv, s, cd, pd, nd, pu_in,
+                                                             pu_out, par);
       break;
     case 8:
-      pcg_cg_kernel<T, false, 8><<<nblk, kRedThreads, sm, st>>>(t, fld, nullptr, ring, x, r, u, p, sv, s, cd, pd,
-                                                                nd, pu_in, pu_out, par);
+      pcg_update_kernel<T, 8><<<nblk, kRedThreads, sm, st>>>(t, fld, ring, x, r, u, p, sv, s, cd, pd, nd, pu_in,
+                                                             pu_out, par);
       break;
     default:
-      pcg_cg_kernel<T, false, 0><<<nblk, kRedThreads, sm, st>>>(t, fld, nullptr, ring, x, r, u, p, sv, s, cd, pd,
-                                                                nd, pu_in, pu_out, par);
+      pcg_update_kernel<T, 0><<<nblk, kRedThreads, sm, st>>>(t, fld, ring, x, r, u, p, sv, s, cd, pd, nd, pu_in,
+                                                             pu_out, par);
   }
 }
 

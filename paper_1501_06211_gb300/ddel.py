@@ -326,10 +326,13 @@ def ddel_kernel_info(h):
     k = ddel_kernel_info_t()
     _check(_lib.ddel_kernel_info(h, ctypes.byref(k)), h)
     d = {n: getattr(k, n) for n, _ in k._fields_}
-    d["schur_apply_kernel"] = (
-        "schur_explicit_df_kernel (FP32-pair arithmetic)" if k.double_float else
-        ("schur_explicit_kernel" if k.schur_form else "schur2d_kernel") +
-        ("<float>" if k.precision else "<double>"))
+    if k.double_float:
+        name = "schur_explicit_df_kernel (FP32-pair arithmetic)"
+    elif k.schur_form:
+        name = "schur_explicit_kernel<float>" if k.precision else "schur_explicit_f64_kernel"
+    else:
+        name = "schur2d_kernel" + ("<float>" if k.precision else "<double>")
+    d["schur_apply_kernel"] = name
     return d
 
 
