@@ -103,7 +103,9 @@ typedef struct {
  * n_point nodes (host int64 node indices) with dim force components each (host
  * doubles).  traction_face = 2*axis + side applies the uniform surface
  * traction `traction` (force per unit area) on that face as consistent nodal
- * loads, or -1 for none. */
+ * loads, or -1 for none.  body_force: uniform force per unit volume (the f of
+ * the mixed problem of Sec. 1) as consistent nodal loads, each unit element
+ * giving 1/2^dim of its force to each of its nodes (zeros for none). */
 typedef struct {
   uint32_t clamp_faces;
   const uint8_t* fixed_dof;
@@ -112,6 +114,7 @@ typedef struct {
   const double* point_force;
   int traction_face;
   double traction[3];
+  double body_force[3];
 } ddel_bc;
 
 /* Solver options.  ddel_default_options() fills documented defaults. */

@@ -228,7 +228,10 @@ def bc_from_spec(grid, spec):
     "fix": list of (node_ijk, component); "point": list of (node_ijk, force
     vector); "traction": (axis, side, traction vector) applied as consistent
     nodal loads of a uniform surface traction on that face (each boundary
-    facet of unit area gives 1/2^(dim-1) of its force to each of its nodes).
+    facet of unit area gives 1/2^(dim-1) of its force to each of its nodes);
+    "body": force vector per unit volume, the f of the mixed problem of
+    Sec. 1, as consistent nodal loads of the bilinear (trilinear) elements
+    (each unit element gives 1/2^dim of its force to each of its nodes).
     """
     d = grid.dim
     fixed = np.zeros(grid.n_dof, dtype=bool)
@@ -256,5 +259,12 @@ def bc_from_spec(grid, spec):
                     ijk[a] = c0 + o
                 n = grid.node_index(*ijk)
                 f[d * n:d * n + d] += share * t
+    if "body" in spec:
+        b = np.asarray(spec["body"], dtype=float)
+        en = grid.element_nodes()
+        share = 1.0 / 2 ** d
+        for a in range(en.shape[1]):
+            for c in range(d):
+                np.add.at(f, d * en[:, a] + c, share * b[c])
     f[fixed] = 0.0
     return fixed, f

@@ -128,6 +128,7 @@ class _Component:
                     m = j + 1                            # invariant subspace: exact
                     break
                 Q[:, j + 1] = w / beta[j]
+        self.last_T = (alpha[:m].copy(), beta[: m - 1].copy())  # for step-by-step comparisons
         T = np.diag(alpha[:m]) + np.diag(beta[: m - 1], 1) + np.diag(beta[: m - 1], -1)
         t, U = np.linalg.eigh(T)
         f = np.clip(t, 0.0, None) ** (1.0 - self.theta)  # B^(1-theta), B SPD in <.,.>_M
@@ -140,7 +141,10 @@ class GlobalPreconditioner:
     steps: None for the exact application, else the number of inverse Lanczos
     steps.  face_scaling "dof" (reading Q8, default) scales every component by
     W = diag(sqrt(diag(K_GG) / diag(Htilde))) so that diag(S~) = diag(K_GG);
-    False keeps the paper-literal Htilde (homogeneous problems only).
+    "diag" (reading Q25) uses the surrogate diag(M)^theta diag(L)^(1-theta)
+    in place of diag(Htilde), which needs no eigendecomposition of the whole
+    interface (the form the GPU applies on large grids); False keeps the
+    paper-literal Htilde (homogeneous problems only).
     """
 
     def __init__(self, dec, K, theta=0.5, steps=None, face_scaling="dof", inner="exact", inner_tol=1e-3):
@@ -168,8 +172,14 @@ class GlobalPreconditioner:
                     cross.append(i)
             groups = ([np.array(v) for _, v in sorted(faces.items(), key=lambda kv: sorted(kv[0]))], cross)
             comp = _Component(pos, M[nodes][:, nodes], L[nodes][:, nodes], theta, groups, inner, inner_tol)
-            Hdiag = np.einsum("ij,j,ij->i", comp.M.toarray() @ comp.V, comp.lam, comp.M.toarray() @ comp.V)
-            comp.w = np.sqrt(Kdiag[G[pos]] / Hdiag) if face_scaling == "dof" else np.ones(len(pos))
+            if face_scaling == "dof":
+                Hdiag = np.einsum("ij,j,ij->i", comp.M.toarray() @ comp.V, comp.lam, comp.M.toarray() @ comp.V)
+                comp.w = np.sqrt(Kdiag[G[pos]] / Hdiag)
+            elif face_scaling == "diag":
+                surrogate = comp.M.diagonal() ** theta * comp.L.diagonal() ** (1.0 - theta)
+                comp.w = np.sqrt(Kdiag[G[pos]] / surrogate)
+            else:
+                comp.w = np.ones(len(pos))
             self.comps.append(comp)
 
     def apply(self, r):

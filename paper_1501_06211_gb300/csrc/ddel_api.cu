@@ -538,7 +538,7 @@ int ddel_create(const ddel_mesh* mesh, const ddel_material* mat, const ddel_bc* 
   const int ne[3] = {mesh->nx, mesh->ny, mesh->nz};
   std::string msg = build_setup(mesh->dim, ne, mesh->sub, mat->E, mat->nu, mat->plane_stress,
                                 bc->clamp_faces, bc->fixed_dof, bc->n_point, bc->point_node,
-                                bc->point_force, bc->traction_face, bc->traction, ctx->opt.theta,
+                                bc->point_force, bc->traction_face, bc->traction, bc->body_force, ctx->opt.theta,
                                 &ctx->S);
   if (!msg.empty()) {
     g_create_error = msg;
@@ -1509,7 +1509,7 @@ int ddel_plan_create(const ddel_mesh* mesh, const ddel_material* mat, const ddel
   const int ne[3] = {mesh->nx, mesh->ny, mesh->nz};
   std::string msg = build_setup(mesh->dim, ne, mesh->sub, mat->E, mat->nu, mat->plane_stress,
                                 bc->clamp_faces, bc->fixed_dof, bc->n_point, bc->point_node,
-                                bc->point_force, bc->traction_face, bc->traction, theta, &p->S);
+                                bc->point_force, bc->traction_face, bc->traction, bc->body_force, theta, &p->S);
   if (!msg.empty()) {
     delete p;
     return DDEL_EINVAL;

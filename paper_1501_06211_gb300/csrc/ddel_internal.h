@@ -72,7 +72,7 @@ struct Setup {
 std::string build_setup(int dim, const int ne[3], int sub, double E, double nu, int plane_stress,
                         uint32_t clamp_faces, const uint8_t* fixed_dof, int n_point,
                         const int64_t* point_node, const double* point_force, int traction_face,
-                        const double traction[3], double theta, Setup* out);
+                        const double traction[3], const double body_force[3], double theta, Setup* out);
 
 // Element stiffness for unit E by 2-point Gauss quadrature (exact for Q1/H8
 // on unit elements), local node order (0,0),(1,0),(1,1),(0,1) [then z=1].

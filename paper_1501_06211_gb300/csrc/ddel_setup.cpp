@@ -191,7 +191,8 @@ bool gen_eig(int n, const std::vector<double>& L, const std::vector<double>& M,
 std::string build_setup(int dim, const int ne_in[3], int sub, double E, double nu,
                         int plane_stress, uint32_t clamp_faces, const uint8_t* fixed_dof,
                         int n_point, const int64_t* point_node, const double* point_force,
-                        int traction_face, const double traction[3], double theta, Setup* S) {
+                        int traction_face, const double traction[3], const double body_force[3],
+                        double theta, Setup* S) {
   if (dim != 2 && dim != 3) return "dim must be 2 or 3";
   if (!(E > 0) || !(nu > -1.0 && nu < 0.5)) return "need E > 0 and -1 < nu < 1/2";
   if (sub < 1) return "sub must be positive";
@@ -257,6 +258,20 @@ std::string build_setup(int dim, const int ne_in[3], int sub, double E, double n
             const int64_t n = node_of(c[0], c[1], c[2]);
             for (int comp = 0; comp < dim; ++comp) S->f[dim * n + comp] += share * traction[comp];
           }
+  }
+  if (body_force && (body_force[0] != 0.0 || body_force[1] != 0.0 || (dim == 3 && body_force[2] != 0.0))) {
+    // consistent loads of a uniform body force: every unit element gives
+    // 1/2^dim of its force to each of its nodes
+    const double share = dim == 2 ? 0.25 : 0.125;
+    for (int i = 0; i < S->ne[0]; ++i)
+      for (int j = 0; j < S->ne[1]; ++j)
+        for (int k = 0; k < (dim == 3 ? S->ne[2] : 1); ++k)
+          for (int dx = 0; dx < 2; ++dx)
+            for (int dy = 0; dy < 2; ++dy)
+              for (int dz = 0; dz < (dim == 3 ? 2 : 1); ++dz) {
+                const int64_t n = node_of(i + dx, j + dy, k + dz);
+                for (int comp = 0; comp < dim; ++comp) S->f[dim * n + comp] += share * body_force[comp];
+              }
   }
   for (int64_t d = 0; d < S->n_dof; ++d)
     if (S->fixed[d]) S->f[d] = 0.0;

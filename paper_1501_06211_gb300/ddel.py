@@ -37,7 +37,7 @@ class ddel_material(ctypes.Structure):
 class ddel_bc(ctypes.Structure):
     _fields_ = [("clamp_faces", c_uint32), ("fixed_dof", c_void_p), ("n_point", c_int),
                 ("point_node", c_void_p), ("point_force", c_void_p), ("traction_face", c_int),
-                ("traction", c_double * 3)]
+                ("traction", c_double * 3), ("body_force", c_double * 3)]
 
 
 class ddel_options(ctypes.Structure):
@@ -516,6 +516,8 @@ class _BC:
             self.bc.traction_face = 2 * axis + side
             for k, v in enumerate(t):
                 self.bc.traction[k] = v
+        for k, v in enumerate(spec.get("body", ())):
+            self.bc.body_force[k] = v
 
 
 class Plan:

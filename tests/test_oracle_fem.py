@@ -180,3 +180,26 @@ def test_direct_solver_against_dense():
     ud = np.linalg.solve(K.toarray()[np.ix_(free, free)], f[free])
     assert np.allclose(u[free], ud, rtol=1e-9, atol=0)
     assert direct.rel_residual(K, f, u, fixed) < 1e-13
+
+
+@pytest.mark.parametrize("dim,ne", [(2, (6, 4)), (3, (3, 2, 2))])
+def test_body_force_loads_are_work_equivalent(dim, ne):
+    # consistent nodal loads of a uniform body force b: for any linear field
+    # u(x) = a + B x (interpolated exactly by the bilinear/trilinear elements)
+    # f^T u equals the integral of b . u over the unit-element grid, a closed
+    # form: b . (a V + B c V) with V the volume and c the centroid
+    grid = fem.Grid(dim, *ne)
+    b = np.arange(1.0, dim + 1.0) * np.array([1.0, -0.75, 0.5][:dim])
+    _, f = fem.bc_from_spec(grid, {"body": tuple(b)})
+    rng = np.random.default_rng(8)
+    a = rng.standard_normal(dim)
+    B = rng.standard_normal((dim, dim))
+    X = grid.node_coords().astype(float)
+    u = (a[None, :] + X @ B.T).ravel()
+    V = float(np.prod(ne))
+    c = np.array(ne, dtype=float) / 2.0
+    assert abs(f @ u - b @ (a * V + B @ c * V)) <= 1e-12 * V * np.abs(b).sum() * (1 + np.abs(B).sum())
+    # an interior node carries exactly b (2^dim elements, 1/2^dim each)
+    inner = grid.node_index(*[1] * dim)
+    assert np.allclose(f[dim * inner:dim * inner + dim], b, rtol=1e-15, atol=0)
+

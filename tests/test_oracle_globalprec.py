@@ -173,3 +173,26 @@ def test_three_dimensional_interface():
     assert all(c.singular for c in gp1.comps)
     P1 = gp1.dense()
     assert np.linalg.eigvalsh(0.5 * (P1 + P1.T)).min() > 0
+
+
+def test_diagonal_surrogate_scaling_at_the_theta_endpoints():
+    # reading Q25: W^2 = diag(K_GG) / (diag(M)^theta diag(L)^(1-theta)); at
+    # theta = 1 Htilde = M and at theta = 0 Htilde = L, where the surrogate is
+    # the exact diagonal, so diag(W Htilde W) = diag(K_GG) there
+    grid, fixed, f, Ke, fac, dec, K, dds = _case(16, 8, 4)
+    M, L = dd.interface_mass_laplacian(dec)
+    G = dec.gamma_dofs
+    Kd = K.diagonal()[G]
+    for theta, op in ((1.0, M), (0.0, L)):
+        gp = globalprec.GlobalPreconditioner(dec, K, theta=theta, face_scaling="diag")
+        for c in gp.comps:
+            nodes = np.array([int(G[k]) // 2 for k in c.pos])
+            Oc = op[nodes][:, nodes].toarray()
+            assert np.allclose(c.w * np.diag(Oc) * c.w, Kd[c.pos], rtol=1e-13)
+    # in between, the surrogate is within a modest factor of diag(Htilde)
+    gp = globalprec.GlobalPreconditioner(dec, K, theta=0.5, face_scaling="diag")
+    gx = globalprec.GlobalPreconditioner(dec, K, theta=0.5, face_scaling="dof")
+    for c, cx in zip(gp.comps, gx.comps):
+        ratio = (cx.w / c.w) ** 2
+        assert 0.25 < ratio.min() and ratio.max() < 4.0, (ratio.min(), ratio.max())
+
