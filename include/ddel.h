@@ -304,6 +304,76 @@ int ddel_batch_solve(ddel_ctx* const* ctxs, int n, double* const* u, ddel_stats*
 int ddel_autotune(ddel_ctx* ctx, const char* cache_path, int* chosen_mode, int* chosen_check,
                   int* from_cache);
 
+/* --- Full-system flexible GMRES with the block-triangular preconditioner -------
+ * The Krylov method of the paper's Table 1 (Sec. 3-4): GMRES on the whole
+ * system K u = f (interior and interface DOFs), right-preconditioned by
+ * P~ = [[K_II, K_IG], [0, S~]], whose inverse is applied as
+ * P~^-1 v = (K_II^-1 (v_I - K_IG S~^-1 v_G), S~^-1 v_G) with the context's
+ * subdomain factors (eq. 3MatSplit2).  Flexible (Saad's FGMRES: the
+ * preconditioned directions are stored) because the inverse-Lanczos S~^-1 is
+ * not a fixed linear map.  The interface preconditioner S~ is one of
+ *   DDEL_PREC_IDENTITY  S~ = I (Table 1's first columns);
+ *   DDEL_PREC_FACE      the face-local H~_theta of ddel_precond_apply (the
+ *                       preconditioner of the interface PCG);
+ *   DDEL_PREC_GLOBAL    H~_theta = M (M^-1 L)^(1 - theta) of eq. NumberEight
+ *                       and NumberNine on the whole interface, per displacement
+ *                       component, applied by inverse Lanczos (Sec. 3): k steps
+ *                       of Lanczos for L^-1 M in the M inner product from
+ *                       b = M^-1 r give S~^-1 r ~ ||b||_M Q_k T_k^(1-theta) e_1;
+ *                       each step solves with L by the inner PCG of Sec. 4
+ *                       (relative tolerance inner_tol, preconditioned by L on
+ *                       each face with the cross points removed, diagonal at
+ *                       cross points); b = M^-1 r by Jacobi-preconditioned CG
+ *                       to mass_tol.  Needs a nonsingular interface Laplacian
+ *                       per component (every connected part of the interface
+ *                       meets a clamped node; EINVAL otherwise).
+ * theta is the context's (ddel_options.theta at creation): the H_OPT columns of
+ * Table 1 use one context per theta.  Iterations are capped at max_it (no
+ * restart); the stopping test is the GMRES residual estimate
+ * ||f - K u|| <= tol ||f||; stats.relres is then recomputed in FP64. */
+typedef enum { DDEL_PREC_IDENTITY = 0, DDEL_PREC_FACE = 1, DDEL_PREC_GLOBAL = 2 } ddel_interface_prec;
+#define DDEL_MAX_LANCZOS 32
+typedef struct {
+  int precond;          /* ddel_interface_prec (DDEL_PREC_GLOBAL) */
+  int lanczos_steps;    /* GLOBAL: inverse Lanczos steps k, 1..DDEL_MAX_LANCZOS (8) */
+  double inner_tol;     /* GLOBAL: relative residual of the inner PCG on L (1e-3) */
+  double mass_tol;      /* GLOBAL: relative residual of the CG solve with M (1e-13) */
+  int global_scaling;   /* GLOBAL: 0 none (paper-literal, homogeneous material);
+                           1 W_ii = (diag(K_GG)_ii / (M_ii^theta L_ii^(1-theta)))^(1/2),
+                           S~ = W H~ W (this library's reading for heterogeneous
+                           material) (1) */
+  double tol;           /* relative residual target (1e-6, Table 1's) */
+  int max_it;           /* iteration cap, 1..2000 (300) */
+} ddel_gmres_options;
+typedef struct {
+  int status;           /* DDEL_OK, or DDEL_ENOCONV at max_it */
+  int iters;            /* FGMRES iterations (preconditioner applications) */
+  double est_relres;    /* GMRES residual estimate at exit */
+  double relres;        /* ||f - K u|| / ||f|| recomputed in FP64 */
+  int inner_min, inner_max;  /* GLOBAL: inner PCG iterations per solve with L */
+  double inner_mean;
+  int lanczos_m;        /* GLOBAL: Lanczos steps of the last application (< k on breakdown) */
+  double t_ms;          /* device time of the solve */
+} ddel_gmres_stats;
+void ddel_default_gmres_options(ddel_gmres_options* opt);
+/* f: n_dof doubles or NULL for the loads of ddel_bc; u: n_dof doubles (output);
+ * host when on_device == 0, else device.  Needs ddel_factor (ESTATE).
+ * Allocates its Krylov basis (2 max_it + 1 vectors of n_dof doubles) on first
+ * use.  Synchronises the stream (one small read-back per iteration). */
+int ddel_gmres_solve(ddel_ctx* ctx, const ddel_gmres_options* opt, const double* f, double* u,
+                     int on_device, ddel_gmres_stats* st);
+/* Step level: z = S~^-1 r with the global interface preconditioner above
+ * (device n_gamma vectors, ddel_gamma_dofs order).  lanczos_out (host, may be
+ * NULL): per component c < dim, 2 + 3 DDEL_MAX_LANCZOS doubles at
+ * c (2 + 3 DDEL_MAX_LANCZOS): [m, mass-CG iterations, alpha_0..alpha_{m-1} at
+ * 2.., beta_0..beta_{m-2} at 2 + DDEL_MAX_LANCZOS.., inner PCG iterations of
+ * step j at 2 + 2 DDEL_MAX_LANCZOS + j] (the tridiagonal T_m of the last
+ * application and its iteration counts).  Synchronises when lanczos_out is
+ * given.  Errors: EINVAL (steps or tolerances out of range, a singular
+ * interface Laplacian), ESTATE before ddel_assemble. */
+int ddel_global_precond_apply(ddel_ctx* ctx, const ddel_gmres_options* opt, const double* r, double* z,
+                              double* lanczos_out);
+
 /* --- Step-level entry points (device pointers; asynchronous) ---------------
  * Prerequisites (DDEL_ESTATE otherwise): ddel_assemble for apply_K,
  * precond_apply and residual_norm; ddel_factor for condense, schur_apply,

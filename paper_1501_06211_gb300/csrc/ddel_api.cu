@@ -68,6 +68,7 @@ struct ddel_ctx {
   int* bad_sub = nullptr;
   int* h_err = nullptr;
   int nblk = 0;
+  int nupd = 0;  // blocks of the PCG init / update kernels (their partial-sum count)
   cudaGraphExec_t graph[2] = {nullptr, nullptr};
   bool graph_explicit[2] = {false, false};
   bool graph_apply32[2] = {false, false};
@@ -227,7 +228,7 @@ int pcg_per(const ddel_ctx* ctx) {
   return per + (per & 1);
 }
 
-double* pcg_partials(ddel_ctx* ctx, int par) { return ctx->pcg_pu + (size_t)par * kPcgRows * ctx->nblk; }
+double* pcg_partials(ddel_ctx* ctx, int par) { return ctx->pcg_pu + (size_t)par * kPcgRows * ctx->nupd; }
 
 // One PCG iteration: w = S u (ring) with the partials of delta = (S u, u);
 // then alpha, beta, the vector updates and u = S~^-1 r (+ the coarse part)
@@ -243,7 +244,7 @@ void pcg_iteration(ddel_ctx* ctx, int prec, bool apply32, int par) {
   const int nd = schur_dispatch(ctx, prec, apply32, io, s);
   launch_pcg_update(ctx->T, ctx->F, apply_prec(ctx, prec, apply32), io.ring_out, ctx->x, ctx->r,
                     ctx->z, ctx->p, ctx->sv, ctx->st, ctx->pcg_pd, nd, pcg_partials(ctx, par),
-                    pcg_partials(ctx, par ^ 1), par, s, ctx->nblk, cd);
+                    pcg_partials(ctx, par ^ 1), par, s, ctx->nupd, cd);
 }
 
 // PCG initialisation (asynchronous) and, with use_graph, the CUDA graph of
@@ -256,7 +257,7 @@ int pcg_start(ddel_ctx* ctx, int prec, const double* g, bool apply32) {
     ctx->launches += 1;
   }
   launch_pcg_init(ctx->T, ctx->F, g, ctx->x, ctx->r, ctx->z, ctx->p, ctx->sv, ctx->st, pcg_partials(ctx, 0), s,
-                  ctx->nblk, cd);
+                  ctx->nupd, cd);
   ctx->launches += 1;
   const int per = pcg_per(ctx);
   const bool expl = ctx->explicit_ok[prec];
@@ -586,6 +587,14 @@ int ddel_create(const ddel_mesh* mesh, const ddel_material* mat, const ddel_bc* 
     T.n_face_dofs = S.n_face_dofs;
     T.n_blocks = (int)S.blk_off.size();
     T.max_blk_n = S.max_blk_n > 0 ? S.max_blk_n : 1;
+    T.upd_lanes = 1;
+    while (T.upd_lanes < T.max_blk_n && T.upd_lanes < 32) T.upd_lanes *= 2;
+    // face tables staged in shared memory when the update kernel's dynamic
+    // shared memory stays within 40 KB (eight warps, 32 / upd_lanes blocks each)
+    {
+      const size_t ug = 32 / T.upd_lanes, mb = T.max_blk_n;
+      T.upd_stage_p = 8 * ug * mb * (16 + 8 * mb) <= 40 * 1024 ? 1 : 0;
+    }
     T.n_ring = (int64_t)S.ring_gidx.size();
     T.max_owners = S.max_owners;
     std::vector<float> ke32(S.Ke.begin(), S.Ke.end());
@@ -643,6 +652,13 @@ int ddel_create(const ddel_mesh* mesh, const ddel_material* mat, const ddel_bc* 
     const int zero_err[4] = {0, 0x7fffffff, 0, 0};
     if (bad(cudaMemcpy(ctx->err, zero_err, sizeof(zero_err), cudaMemcpyHostToDevice))) goto fail_out;
     ctx->nblk = 2 * 152;
+    {
+      // PCG update: enough blocks of eight warps for the packed face blocks
+      // and one thread per cross-point DOF, at most two per SM
+      const int64_t ug = 32 / T.upd_lanes, n_cross = T.n_gamma - T.n_face_dofs;
+      const int64_t need = std::max((T.n_blocks + 8 * ug - 1) / (8 * ug), (n_cross + 255) / 256);
+      ctx->nupd = (int)std::min<int64_t>(std::max<int64_t>(need, 1), 2 * 152);
+    }
     for (auto& e : ctx->ev)
       if (bad(cudaEventCreate(&e))) goto fail_out;
   }

@@ -1318,39 +1318,50 @@ __global__ void __launch_bounds__(kRedThreads) pcg_cg_kernel(DevTables t, DevFie
   if (threadIdx.x < NV) pu_out[(size_t)threadIdx.x * gridDim.x + blockIdx.x] = red[threadIdx.x * kRedThreads];
 }
 
-// Update j of the PCG (the non-INIT form of pcg_cg_kernel, same arithmetic in
-// the same order, so the iterates are bitwise those of that kernel) laid out
-// for latency: before the block reduces the partial sums and forms alpha_j,
-// beta_j, every lane issues the loads that need no scalar -- for its DOFs of
-// the warp's first face block (up to 32 PE of them) and its first cross-point
-// DOF: the owners' ring entries of S u, u, p, s, x, r and the face weight --
-// so that their latency overlaps the reduction's; only the arithmetic and the
-// preconditioner wait for the scalars.  Further blocks of a warp (more face
-// blocks than warps) load as they come.
+// Update j of the PCG (the non-INIT form of pcg_cg_kernel: the same
+// arithmetic on every interface DOF, so the iterates agree with that kernel's
+// to rounding of the grid-wide sums) laid out for latency:
+//  * face blocks are packed UL lanes apiece (UL = the power of two >= the
+//    largest block, at most 32), so a warp serves 32 / UL blocks at once;
+//  * before the partial sums are reduced, every lane issues the loads that
+//    need no scalar -- for its DOFs of its first face block and its first
+//    cross-point DOF: the owners' ring entries of S u, u, p, s, x, r and the
+//    face weight -- and, where it fits, the face block's dense H~^-1 table is
+//    copied into shared memory (cp.async), so that their latency overlaps the
+//    reduction's;
+//  * without a coarse space the three grid-wide sums (delta, gamma, rr) are
+//    reduced by one warp each (lane-strided loads, then a shuffle tree; every
+//    block forms bitwise the same totals) instead of a block-wide tree.
+// Further blocks of a warp (more face blocks than lanes) load as they come.
 template <typename T, int KC>
 __global__ void __launch_bounds__(kRedThreads, 2) pcg_update_kernel(DevTables t, DevFields fld,
-                                                                 const T* __restrict__ ring, double* x,
-                                                                 double* r, double* u, double* p,
-                                                                 double* sv, PcgState* st, CoarseDev cd,
-                                                                 const double* __restrict__ pd, int nd,
-                                                                 const double* __restrict__ pu_in,
-                                                                 double* __restrict__ pu_out, int par) {
+                                                                    const T* __restrict__ ring, double* x,
+                                                                    double* r, double* u, double* p,
+                                                                    double* sv, PcgState* st, CoarseDev cd,
+                                                                    const double* __restrict__ pd, int nd,
+                                                                    const double* __restrict__ pu_in,
+                                                                    double* __restrict__ pu_out, int par) {
   const int done = st->done;
   constexpr int NV = 2 + 2 * KC, NP = 3 + 2 * KC, PE = 2;
-  extern __shared__ double rw_all[];  // (blockDim/32) * max_blk_n doubles, then as many float2
+  // dynamic shared memory: per warp UG * max_blk_n doubles (W^-1 r), as many
+  // float2 (its double-float split), then, when staged, UG * max_blk_n^2
+  // float2 per warp (the face tables)
+  extern __shared__ double rw_all[];
   __shared__ double red[NP * kRedThreads];
   __shared__ double sums[NP];
   __shared__ double sab[2 + kMaxCoarse];
   __shared__ int sflag;
-  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-  double* rw = rw_all + wib * t.max_blk_n;
-  float2* rwf = reinterpret_cast<float2*>(rw_all + (blockDim.x >> 5) * t.max_blk_n) + wib * t.max_blk_n;
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5, nwb = blockDim.x >> 5;
+  const int UL = t.upd_lanes, UG = 32 / UL, mbn = t.max_blk_n;
+  const int grp = lane / UL, gl = lane % UL;
+  double* rw = rw_all + (wib * UG + grp) * mbn;
+  float2* rwf = reinterpret_cast<float2*>(rw_all + nwb * UG * mbn) + (wib * UG + grp) * mbn;
+  float2* ptile = reinterpret_cast<float2*>(rw_all + 2 * nwb * UG * mbn) + (size_t)(wib * UG + grp) * mbn * mbn;
   const int k = KC > 0 ? cd.k : 0;
   const bool deflate = KC > 0 && cd.correct == 2;
   const int j = st->kU;
   const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int nw = (gridDim.x * blockDim.x) >> 5;
-  // --- loads that need no scalar, issued first
   struct Dof {
     double w, u, p, s, x, r, fw;
   };
@@ -1365,19 +1376,26 @@ __global__ void __launch_bounds__(kRedThreads, 2) pcg_update_kernel(DevTables t,
     d.fw = fw;
     return d;
   };
-  const int b0 = gw;
-  int off0 = 0, n0 = 0;
+  // --- loads that need no scalar, issued first
+  const int b0 = gw * UG + grp;
+  int off0 = 0, n0 = 0, poff0 = 0;
   if (b0 < t.n_blocks) {
     off0 = t.blk_off[b0];
     n0 = t.blk_n[b0];
+    poff0 = t.blk_poff[b0];
   }
-  const bool pre_ok = n0 <= 32 * PE;
+  const bool pre_ok = n0 <= UL * PE;
   Dof pre[PE];
 #pragma unroll
   for (int e = 0; e < PE; ++e) {
-    const int i = lane + 32 * e;
+    const int i = gl + UL * e;
     if (pre_ok && i < n0) pre[e] = load_dof(off0 + i, fld.face_w[off0 + i]);
   }
+  if (t.upd_stage_p && n0 > 0) {
+    const float2* src = t.ptab_df + poff0;
+    for (int i = gl; i < n0 * n0; i += UL) cp_async8(ptile + i, src + i);
+  }
+  cp_async_commit();
   const int64_t gc0 = t.n_face_dofs + blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   Dof prc;
   if (gc0 < t.n_gamma) prc = load_dof(gc0, fld.cross_scale[gc0 - t.n_face_dofs]);
@@ -1403,21 +1421,37 @@ __global__ void __launch_bounds__(kRedThreads, 2) pcg_update_kernel(DevTables t,
       ginv = st->ginv_s[par ^ 1];
       ainv = st->ainv_s[par ^ 1];
     }
-    const double* U = pu_in;
     const int nu = gridDim.x;
-    double a[NP];
+    if constexpr (KC == 0) {
+      // delta, gamma, rr: one warp each
+      if (wib < 3) {
+        const double* src = wib == 0 ? pd : pu_in + (size_t)(wib - 1) * nu;
+        const double v = reduce_partials_warp(src, wib == 0 ? nd : nu);
+        if (lane == 0) sums[wib] = v;
+      }
+      if (done) {  // uniform over the grid; no copy outlives the block
+        cp_async_wait_all();
+        return;
+      }
+      __syncthreads();
+    } else {
+      double a[NP];
 #pragma unroll
-    for (int v = 0; v < NP; ++v) {
-      a[v] = 0.0;
-      if (v >= 3 && (v - 3) % (KC > 0 ? KC : 1) >= k) continue;
-      const double* src = v == 0 ? pd : U + (size_t)(v - 1) * nu;
-      const int n = v == 0 ? nd : nu;
-      for (int b = threadIdx.x; b < n; b += kRedThreads) a[v] += __ldcg(src + b);
+      for (int v = 0; v < NP; ++v) {
+        a[v] = 0.0;
+        if (v >= 3 && (v - 3) % KD >= k) continue;
+        const double* src = v == 0 ? pd : pu_in + (size_t)(v - 1) * nu;
+        const int n = v == 0 ? nd : nu;
+        for (int b = threadIdx.x; b < n; b += kRedThreads) a[v] += __ldcg(src + b);
+      }
+      if (done) {  // uniform over the grid; no copy outlives the block
+        cp_async_wait_all();
+        return;
+      }
+      block_tree_sum<NP>(a, NP, red);
+      if (threadIdx.x < NP) sums[threadIdx.x] = red[threadIdx.x * kRedThreads];
+      __syncthreads();
     }
-    if (done) return;  // uniform over the grid
-    block_tree_sum<NP>(a, NP, red);
-    if (threadIdx.x < NP) sums[threadIdx.x] = red[threadIdx.x * kRedThreads];
-    __syncthreads();
     if (threadIdx.x == 0) {
       double gamma = sums[1], delta = sums[0];
       const double rr = sums[2];
@@ -1469,7 +1503,10 @@ __global__ void __launch_bounds__(kRedThreads, 2) pcg_update_kernel(DevTables t,
       }
     }
     __syncthreads();
-    if (sflag != 1) return;
+    if (sflag != 1) {
+      cp_async_wait_all();  // no copy outlives the block
+      return;
+    }
     alpha = sab[0];
     beta = sab[1];
 #pragma unroll
@@ -1485,8 +1522,6 @@ __global__ void __launch_bounds__(kRedThreads, 2) pcg_update_kernel(DevTables t,
   double acc[NV];
 #pragma unroll
   for (int i = 0; i < NV; ++i) acc[i] = 0.0;
-  // the vector updates at one DOF from its loaded values (the order of
-  // operations of pcg_cg_kernel)
   auto step = [&](int64_t g, const Dof& d) -> double {
     const double w = d.w + (KC > 0 ? coarse(cd.SQ, g) : 0.0);
     const double pg = d.u + (KC > 0 ? coarse(cd.Q, g) : 0.0) + beta * d.p;
@@ -1509,14 +1544,19 @@ __global__ void __launch_bounds__(kRedThreads, 2) pcg_update_kernel(DevTables t,
     for (int i = 0; i < KC; ++i)
       if (i < k) acc[2 + KC + i] += cd.SQ[i * t.n_gamma + g] * ui;
   };
-  double rkeep[PE];  // r at this lane's DOFs of the current block
-  for (int b = gw; b < t.n_blocks; b += nw) {
-    const bool first = b == b0 && pre_ok;
-    const int off = first ? off0 : t.blk_off[b], n = first ? n0 : t.blk_n[b];
-    if (n <= 32 * PE) {
+  cp_async_wait_all();
+  double rkeep[PE];
+  for (int base = gw * UG; base < t.n_blocks; base += nw * UG) {
+    const int b = base + grp;
+    const bool first = base == gw * UG;
+    const bool has = b < t.n_blocks;
+    const int off = first ? off0 : (has ? t.blk_off[b] : 0);
+    const int n = first ? n0 : (has ? t.blk_n[b] : 0);
+    const bool fast = n <= UL * PE;
+    if (fast) {
 #pragma unroll
       for (int e = 0; e < PE; ++e) {
-        const int i = lane + 32 * e;
+        const int i = gl + UL * e;
         if (i < n) {
           Dof d;
           if (first) d = pre[e];
@@ -1530,7 +1570,7 @@ __global__ void __launch_bounds__(kRedThreads, 2) pcg_update_kernel(DevTables t,
         }
       }
     } else {
-      for (int i = lane; i < n; i += 32) {
+      for (int i = gl; i < n; i += UL) {
         const double ri = step(off + i, load_dof(off + i, fld.face_w[off + i]));
         const double v = ri * fld.face_w[off + i];
         rw[i] = v;
@@ -1539,8 +1579,11 @@ __global__ void __launch_bounds__(kRedThreads, 2) pcg_update_kernel(DevTables t,
       }
     }
     __syncwarp();
-    for (int i = lane; i < n; i += 32) {
-      const float2* Pc = t.ptab_df + t.blk_poff[b] + i;
+    const float2* Ptab = (first && t.upd_stage_p) ? ptile : t.ptab_df + (has ? t.blk_poff[b] : 0);
+    for (int i = gl; i < n; i += UL) {
+      // column i of the symmetric P in double-float arithmetic on the FP32
+      // pipes, the same error-free transformations as the explicit Schur apply
+      const float2* Pc = Ptab + i;
       float hi = 0.f, lo = 0.f;
 #pragma unroll 4
       for (int q = 0; q < n; ++q) {
@@ -1550,8 +1593,8 @@ __global__ void __launch_bounds__(kRedThreads, 2) pcg_update_kernel(DevTables t,
         df_add(hi, lo, pr);
       }
       const double zi = (double)hi + (double)lo;
-      const int e = (i - lane) >> 5;
-      const double ri = (n <= 32 * PE) ? (e == 0 ? rkeep[0] : rkeep[PE - 1]) : r[off + i];
+      const int e = (i - gl) / UL;
+      const double ri = fast ? (e == 0 ? rkeep[0] : rkeep[PE - 1]) : r[off + i];
       local(off + i, ri, zi * fld.face_w[off + i]);
     }
     __syncwarp();
@@ -1904,6 +1947,14 @@ cudaError_t configure_kernels() {
   DDEL_CFG((form_w2d_kernel<float, 96, 256, kFormGC>));
   DDEL_CFG((form_syrk2d_kernel<double, 96, 256, kFormTQ>));
   DDEL_CFG((form_syrk2d_kernel<float, 96, 256, kFormTQ>));
+  // the update kernel's staged face tables plus the coarse variants' static
+  // reduction arrays exceed the default 48 KB
+  DDEL_CFG((pcg_update_kernel<double, 0>));
+  DDEL_CFG((pcg_update_kernel<double, 4>));
+  DDEL_CFG((pcg_update_kernel<double, 8>));
+  DDEL_CFG((pcg_update_kernel<float, 0>));
+  DDEL_CFG((pcg_update_kernel<float, 4>));
+  DDEL_CFG((pcg_update_kernel<float, 8>));
 #undef DDEL_CFG
   cudaError_t e3 = configure_kernels3d();
   return e != cudaSuccess ? e : e3;
@@ -1979,6 +2030,15 @@ static size_t update_smem(const DevTables& t) {
   return (size_t)(kRedThreads / 32) * t.max_blk_n * (sizeof(double) + sizeof(float2));
 }
 
+// The update kernel's shared memory: per warp (32 / upd_lanes) face blocks of
+// W^-1 r as doubles and float pairs, plus their H~^-1 tables when staged.
+static size_t update_kernel_smem(const DevTables& t) {
+  const size_t ug = 32 / t.upd_lanes, w = kRedThreads / 32;
+  size_t b = w * ug * t.max_blk_n * (sizeof(double) + sizeof(float2));
+  if (t.upd_stage_p) b += w * ug * (size_t)t.max_blk_n * t.max_blk_n * sizeof(float2);
+  return b;
+}
+
 // Coarse columns padded to 4 or 8 (template width of the coarse sums).
 static int coarse_width(int k) { return k <= 0 ? 0 : k <= 4 ? 4 : 8; }
 
@@ -2006,7 +2066,7 @@ static void launch_update_t(const DevTables& t, const DevFields& fld, const T* r
                             double* u, double* p, double* sv, PcgState* s, const double* pd, int nd,
                             const double* pu_in, double* pu_out, int par, cudaStream_t st, int nblk,
                             const CoarseDev& cd) {
-  const size_t sm = update_smem(t);
+  const size_t sm = update_kernel_smem(t);
   switch (cd.correct ? coarse_width(cd.k) : 0) {
     case 4:
       pcg_update_kernel<T, 4><<<nblk, kRedThreads, sm, st>>>(t, fld, ring, x, r, u, p, sv, s, cd, pd, nd, pu_in,

@@ -13,6 +13,8 @@ struct DevTables {
   int ne[3], nn[3];
   int64_t n_dof, n_elem, n_gamma;
   int n_face_dofs, n_blocks, max_blk_n;
+  int upd_lanes;    // lanes per face block in the PCG update (power of two >= max_blk_n, <= 32)
+  int upd_stage_p;  // 1: the update kernel stages face tables in shared memory
   SubInfo* subs;
   uint8_t* fixed;
   int32_t* ring_gidx;
