@@ -136,6 +136,9 @@ typedef struct {
                           iteration; IMPLICIT applies it by block substitution */
   int use_graph;       /* capture PCG iterations in a CUDA graph (1) */
   int check_every;     /* PCG iterations between host convergence checks (16) */
+  int tensor_form;     /* 1: form the FP64 local Schur complements of rings of 128 and 256
+                          with W^T W on the tensor cores at FP64 accuracy (Ozaki splitting
+                          into BF16 slices, FP32 accumulation); 0: on the FP64 pipe (1) */
 } ddel_options;
 
 typedef struct {

@@ -16,6 +16,7 @@
 #include "../../include/ddel.h"
 #include "../../include/ddel_learn.h"
 #include "ddel_internal.h"
+#include "ddel_globalprec.h"
 #include "ddel_launch.h"
 #include "ddel_topopt.h"
 
@@ -35,6 +36,7 @@ struct ddel_ctx {
   void* work3d[2] = {nullptr, nullptr};  // 3D factorisation scratch
   void* sexp[2] = {nullptr, nullptr};  // explicit local Schur complements (2D)
   void* form_work[2] = {nullptr, nullptr};  // W = L^-1 K_IG scratch of the widest rings
+  void* tc_work = nullptr;             // BF16 slices of W and column exponents (tensor-core formation)
   float* sexp32 = nullptr;             // MIXED: FP64-formed S_i rounded to FP32
   bool mixed_ready = false;
   float2* sexp_df = nullptr;           // FP64 S_i as FP32 (hi, lo) pairs (double-float apply)
@@ -94,6 +96,14 @@ struct ddel_ctx {
   int coarse_prec = -1;          // precision whose S formed E (-1: stale)
   int graph_ck[2] = {0, 0};      // coarse dimension captured in graph[prec]
   bool u_valid = false;          // d_u holds a converged solution (x0_mode WARM)
+  // global interface preconditioner and full-system FGMRES (first use)
+  GPDev gp{};
+  int gp_state = 0;               // 0 not built, 1 ready, -1 singular interface Laplacian
+  double* gp_out = nullptr;       // device: Lanczos record of the last application
+  double* h_gp_out = nullptr;     // pinned copy
+  double *gm_V = nullptr, *gm_Z = nullptr, *gm_w = nullptr, *gm_h = nullptr, *gm_part = nullptr;
+  double *gm_vg = nullptr, *gm_zg = nullptr, *h_gm = nullptr;
+  int gm_cap = 0;                 // iterations the FGMRES buffers hold
   std::vector<ddel_learner*> learners;  // attached learners (detached on destroy)
   std::string last_error;
 };
@@ -370,11 +380,24 @@ int factor_launch(ddel_ctx* ctx, int prec) {
       cudaError_t e = cudaMalloc(&ctx->form_work[prec], we * (prec ? 4 : 8));
       if (e != cudaSuccess) return fail(ctx, DDEL_ENOMEM, "explicit Schur scratch allocation");
     }
-    // AUTO applies S_i in double-float arithmetic, so it is formed that way too
-    const bool df = prec == 0 && ctx->opt.schur_mode == DDEL_SCHUR_AUTO;
-    launch_schur_form(ctx->T, ctx->F, prec, df, ctx->factor[prec], ctx->form_work[prec], ctx->sexp[prec],
-                      ctx->stream);
-    ctx->launches += 1;
+    if (prec == 0 && ctx->opt.tensor_form && tensor_form_available(ctx->T)) {
+      // FP64-accurate S_i with W^T W on the tensor cores (both FP64 forms)
+      if (!ctx->form_work[0]) {
+        cudaError_t e = cudaMalloc(&ctx->form_work[0], explicit_form_work_elems(ctx->T) * 8);
+        if (e != cudaSuccess) return fail(ctx, DDEL_ENOMEM, "explicit Schur scratch allocation");
+      }
+      if (!ctx->tc_work && cudaMalloc(&ctx->tc_work, tensor_form_work_bytes(ctx->T)) != cudaSuccess)
+        return fail(ctx, DDEL_ENOMEM, "tensor-core formation scratch allocation");
+      launch_schur_form_tc(ctx->T, ctx->F, ctx->factor[0], ctx->form_work[0], ctx->tc_work, ctx->sexp[0],
+                           ctx->err, ctx->stream);
+      ctx->launches += 3;
+    } else {
+      // AUTO applies S_i in double-float arithmetic, so it is formed that way too
+      const bool df = prec == 0 && ctx->opt.schur_mode == DDEL_SCHUR_AUTO;
+      launch_schur_form(ctx->T, ctx->F, prec, df, ctx->factor[prec], ctx->form_work[prec], ctx->sexp[prec],
+                        ctx->stream);
+      ctx->launches += 1;
+    }
     CK(cudaGetLastError());
   }
   ctx->pending_explicit = want_explicit;
@@ -388,6 +411,8 @@ int factor_check(ddel_ctx* ctx, int prec) {
   if (ctx->h_err[2] == kErrBadRho) return fail(ctx, DDEL_EINVAL, "density must be > 0");
   if (ctx->h_err[0] == kErrPivot)
     return fail(ctx, DDEL_ENOTSPD, "pivot failure in subdomain " + std::to_string(ctx->h_err[1]));
+  if (ctx->h_err[0] == kErrTimeout)
+    return fail(ctx, DDEL_ETIMEOUT, "a bounded wait of the tensor-core formation ran out");
   ctx->factored[prec] = true;
   ctx->explicit_ok[prec] = ctx->pending_explicit;
   ctx->coarse_prec = -1;  // E must be formed again with the new S (next ddel_solve)
@@ -479,6 +504,81 @@ int coarse_build(ddel_ctx* ctx, int prec, bool apply32) {
   return DDEL_OK;
 }
 
+// Global interface preconditioner: host set-up of every displacement
+// component (interface M, L, face inverses of L) and device copies with a
+// workspace for the most Lanczos steps.  Returns DDEL_EINVAL for a singular
+// interface Laplacian (a part of Gamma that meets no clamped node).
+int gp_build(ddel_ctx* ctx) {
+  if (ctx->gp_state == 1) return DDEL_OK;
+  if (ctx->gp_state == -1) return fail(ctx, DDEL_EINVAL, "global preconditioner: singular interface Laplacian");
+  const int dim = ctx->S.dim;
+  GPDev gd{};
+  for (int c = 0; c < dim; ++c) {
+    GPHost h;
+    const std::string msg = build_global_prec(ctx->S, c, &h);
+    if (!msg.empty()) return fail(ctx, DDEL_EINVAL, "global preconditioner: " + msg);
+    if (h.singular || h.pos.empty()) {
+      ctx->gp_state = -1;
+      return fail(ctx, DDEL_EINVAL,
+                  "global preconditioner: singular interface Laplacian (a part of the interface meets no "
+                  "clamped node)");
+    }
+    GPComp& g = gd.c[c];
+    g.n = (int)h.pos.size();
+    int32_t *pos, *col, *rf, *fl0, *fn;
+    int64_t *rp, *fio;
+    double *M, *L, *Md, *Ld, *Mi, *ci, *fi, *w, *work;
+    CK(upload(ctx, h.pos, &pos));
+    CK(upload(ctx, h.rowptr, &rp));
+    CK(upload(ctx, h.col, &col));
+    CK(upload(ctx, h.M, &M));
+    CK(upload(ctx, h.L, &L));
+    CK(upload(ctx, h.Mdiag, &Md));
+    CK(upload(ctx, h.Ldiag, &Ld));
+    CK(upload(ctx, h.Minv_diag, &Mi));
+    CK(upload(ctx, h.cross_inv, &ci));
+    CK(upload(ctx, h.row_face, &rf));
+    CK(upload(ctx, h.face_l0, &fl0));
+    CK(upload(ctx, h.face_n, &fn));
+    CK(upload(ctx, h.face_inv_off, &fio));
+    CK(upload(ctx, h.face_inv, &fi));
+    CK(dalloc(ctx, &w, (size_t)g.n * 8));
+    CK(dalloc(ctx, &work, global_prec_work_elems(g.n, kLz) * 8));
+    g.pos = pos;
+    g.rowptr = rp;
+    g.col = col;
+    g.M = M;
+    g.L = L;
+    g.Mdiag = Md;
+    g.Ldiag = Ld;
+    g.Minv_diag = Mi;
+    g.cross_inv = ci;
+    g.row_face = rf;
+    g.face_l0 = fl0;
+    g.face_n = fn;
+    g.face_inv_off = fio;
+    g.face_inv = fi;
+    g.w = w;
+    g.work = work;
+  }
+  gd.ncomp = dim;
+  CK(dalloc(ctx, &ctx->gp_out, (size_t)3 * (2 + 3 * kLz) * 8));
+  CK(cudaMallocHost(&ctx->h_gp_out, (size_t)3 * (2 + 3 * kLz) * 8));
+  ctx->gp = gd;
+  ctx->gp_state = 1;
+  return DDEL_OK;
+}
+
+int gp_check_options(ddel_ctx* ctx, const ddel_gmres_options* o) {
+  if (o->precond < DDEL_PREC_IDENTITY || o->precond > DDEL_PREC_GLOBAL)
+    return fail(ctx, DDEL_EINVAL, "precond must be IDENTITY, FACE or GLOBAL");
+  if (o->precond == DDEL_PREC_GLOBAL &&
+      (o->lanczos_steps < 1 || o->lanczos_steps > kLz || !(o->inner_tol > 0.0 && o->inner_tol < 1.0) ||
+       !(o->mass_tol > 0.0 && o->mass_tol < 1.0)))
+    return fail(ctx, DDEL_EINVAL, "lanczos_steps in 1..32, inner_tol and mass_tol in (0, 1)");
+  return DDEL_OK;
+}
+
 float elapsed(cudaEvent_t a, cudaEvent_t b) {
   float ms = 0.f;
   cudaEventElapsedTime(&ms, a, b);
@@ -503,6 +603,7 @@ void ddel_default_options(ddel_options* o) {
   o->schur_mode = DDEL_SCHUR_AUTO;
   o->use_graph = 1;
   o->check_every = 16;
+  o->tensor_form = 1;
 }
 
 const char* ddel_strerror(int s) {
@@ -684,6 +785,7 @@ void ddel_destroy(ddel_ctx* ctx) {
     if (p) cudaFree(p);
   for (void* p : ctx->form_work)
     if (p) cudaFree(p);
+  if (ctx->tc_work) cudaFree(ctx->tc_work);
   for (void* p : ctx->work3d)
     if (p) cudaFree(p);
   if (ctx->sexp32) cudaFree(ctx->sexp32);
@@ -695,6 +797,10 @@ void ddel_destroy(ddel_ctx* ctx) {
   if (ctx->h_err) cudaFreeHost(ctx->h_err);
   if (ctx->h_topo) cudaFreeHost(ctx->h_topo);
   if (ctx->h_cflags) cudaFreeHost(ctx->h_cflags);
+  if (ctx->h_gp_out) cudaFreeHost(ctx->h_gp_out);
+  if (ctx->h_gm) cudaFreeHost(ctx->h_gm);
+  for (double* p : {ctx->gm_V, ctx->gm_Z, ctx->gm_w, ctx->gm_h, ctx->gm_part, ctx->gm_vg, ctx->gm_zg})
+    if (p) cudaFree(p);
   for (auto& e : ctx->ev)
     if (e) cudaEventDestroy(e);
   if (ctx->own_stream && ctx->stream) cudaStreamDestroy(ctx->stream);
@@ -1332,6 +1438,195 @@ int ddel_autotune(ddel_ctx* ctx, const char* cache_path, int* chosen_mode, int* 
     }
   }
   return DDEL_OK;
+}
+
+void ddel_default_gmres_options(ddel_gmres_options* o) {
+  if (!o) return;
+  o->precond = DDEL_PREC_GLOBAL;
+  o->lanczos_steps = 8;
+  o->inner_tol = 1e-3;
+  o->mass_tol = 1e-13;
+  o->global_scaling = 1;
+  o->tol = 1e-6;
+  o->max_it = 300;
+}
+
+int ddel_global_precond_apply(ddel_ctx* ctx, const ddel_gmres_options* opt, const double* r, double* z,
+                              double* lanczos_out) {
+  if (!ctx || !opt || !r || !z) return DDEL_EINVAL;
+  if (!ctx->assembled) return fail(ctx, DDEL_ESTATE, "assemble first");
+  ddel_gmres_options o = *opt;
+  o.precond = DDEL_PREC_GLOBAL;
+  int rc = gp_check_options(ctx, &o);
+  if (rc) return rc;
+  if ((rc = gp_build(ctx))) return rc;
+  CK(launch_global_prec(ctx->gp, r, z, ctx->F.diagG, ctx->opt.theta, o.lanczos_steps, o.inner_tol, o.mass_tol,
+                        o.global_scaling ? 1 : 0, ctx->gp_out, ctx->stream));
+  ctx->launches += 1;
+  if (lanczos_out) {
+    const size_t per = 2 + 3 * kLz;
+    CK(cudaMemcpyAsync(ctx->h_gp_out, ctx->gp_out, ctx->gp.ncomp * per * 8, cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    std::memcpy(lanczos_out, ctx->h_gp_out, ctx->gp.ncomp * per * 8);
+  }
+  return DDEL_OK;
+}
+
+int ddel_gmres_solve(ddel_ctx* ctx, const ddel_gmres_options* opt, const double* f, double* u, int on_device,
+                     ddel_gmres_stats* stats) {
+  if (!ctx || !opt || !u) return DDEL_EINVAL;
+  const int prec = ctx->active_prec;
+  if (!ctx->factored[prec]) return fail(ctx, DDEL_ESTATE, "factor before solve");
+  int rc = gp_check_options(ctx, opt);
+  if (rc) return rc;
+  if (!(opt->tol > 0.0) || opt->max_it < 1 || opt->max_it > 2000)
+    return fail(ctx, DDEL_EINVAL, "tol > 0 and max_it in 1..2000");
+  if (opt->precond == DDEL_PREC_GLOBAL && (rc = gp_build(ctx))) return rc;
+  cudaStream_t s = ctx->stream;
+  const int64_t n = ctx->S.n_dof, ng = ctx->T.n_gamma;
+  const int cap = opt->max_it;
+  if (ctx->gm_cap < cap) {
+    for (double** p : {&ctx->gm_V, &ctx->gm_Z, &ctx->gm_w, &ctx->gm_h, &ctx->gm_part, &ctx->gm_vg, &ctx->gm_zg})
+      if (*p) {
+        cudaFree(*p);
+        *p = nullptr;
+      }
+    if (ctx->h_gm) cudaFreeHost(ctx->h_gm);
+    ctx->h_gm = nullptr;
+    ctx->gm_cap = 0;
+    if (cudaMalloc(&ctx->gm_V, (size_t)(cap + 1) * n * 8) != cudaSuccess ||
+        cudaMalloc(&ctx->gm_Z, (size_t)cap * n * 8) != cudaSuccess ||
+        cudaMalloc(&ctx->gm_w, (size_t)n * 8) != cudaSuccess ||
+        cudaMalloc(&ctx->gm_h, (size_t)(2 * cap + 8) * 8) != cudaSuccess ||
+        cudaMalloc(&ctx->gm_part, multi_dot_partials(cap + 1) * 8) != cudaSuccess ||
+        cudaMalloc(&ctx->gm_vg, (size_t)(ng + 1) * 8) != cudaSuccess ||
+        cudaMalloc(&ctx->gm_zg, (size_t)(ng + 1) * 8) != cudaSuccess ||
+        cudaMallocHost(&ctx->h_gm, (size_t)(2 * cap + 8) * 8) != cudaSuccess)
+      return fail(ctx, DDEL_ENOMEM, "FGMRES basis allocation");
+    ctx->gm_cap = cap;
+  }
+  double *V = ctx->gm_V, *Z = ctx->gm_Z, *w = ctx->gm_w, *h = ctx->gm_h, *h2 = ctx->gm_h + cap + 2;
+  ddel_gmres_stats st{};
+  st.inner_min = 1 << 30;
+  long long inner_sum = 0, inner_cnt = 0;
+  CK(cudaEventRecord(ctx->ev[0], s));
+  if (!f)
+    CK(cudaMemcpyAsync(ctx->d_f, ctx->d_load, n * 8, cudaMemcpyDeviceToDevice, s));
+  else
+    CK(cudaMemcpyAsync(ctx->d_f, f, n * 8, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
+  launch_multi_dot(ctx->d_f, 0, 1, ctx->d_f, n, ctx->gm_part, h, 0, s);
+  CK(cudaMemcpyAsync(ctx->h_gm, h, 8, cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  const double beta0 = std::sqrt(ctx->h_gm[0]);
+  std::vector<double> H((size_t)(cap + 1) * cap, 0.0), cs(cap), sn(cap), e(cap + 1, 0.0);
+  int k_done = 0;
+  st.status = DDEL_ENOCONV;
+  if (beta0 == 0.0) {
+    CK(cudaMemsetAsync(ctx->d_u, 0, n * 8, s));
+    st.status = DDEL_OK;
+  } else {
+    launch_scale_gm(ctx->d_f, V, n, nullptr, -1, beta0, s);
+    e[0] = beta0;
+    const int per = 2 + 3 * kLz;
+    for (int k = 0; k < cap; ++k) {
+      double* vk = V + (size_t)k * n;
+      double* zk = Z + (size_t)k * n;
+      // z_k = P~^-1 v_k: S~^-1 on the interface part, then the interior solves
+      launch_gather_gamma(ctx->T.gamma_dof, ng, vk, ctx->gm_vg, s);
+      if (opt->precond == DDEL_PREC_IDENTITY) {
+        CK(cudaMemcpyAsync(ctx->gm_zg, ctx->gm_vg, ng * 8, cudaMemcpyDeviceToDevice, s));
+      } else if (opt->precond == DDEL_PREC_FACE) {
+        launch_precond(ctx->T, ctx->F, ctx->gm_vg, ctx->gm_zg, s);
+      } else {
+        CK(launch_global_prec(ctx->gp, ctx->gm_vg, ctx->gm_zg, ctx->F.diagG, ctx->opt.theta, opt->lanczos_steps,
+                              opt->inner_tol, opt->mass_tol, opt->global_scaling ? 1 : 0, ctx->gp_out, s));
+      }
+      back_substitute(ctx, prec, vk, ctx->gm_zg, zk);
+      // w = K z_k, then classical Gram-Schmidt twice against v_0 .. v_k
+      launch_apply_K(ctx->T, ctx->F, zk, nullptr, w, 0, ctx->partials, ctx->ticketK, ctx->nrm, s, ctx->nblk);
+      launch_multi_dot(V, n, k + 1, w, n, ctx->gm_part, h, 0, s);
+      launch_multi_axpy(V, n, k + 1, h, w, n, 0, s);
+      launch_multi_dot(V, n, k + 1, w, n, ctx->gm_part, h2, 0, s);
+      launch_multi_axpy(V, n, k + 1, h2, w, n, 0, s);
+      launch_multi_dot(w, 0, 1, w, n, ctx->gm_part, h2 + k + 1, 0, s);
+      ctx->launches += 12;
+      CK(cudaMemcpyAsync(ctx->h_gm, h, (size_t)(2 * cap + 4) * 8, cudaMemcpyDeviceToHost, s));
+      if (opt->precond == DDEL_PREC_GLOBAL)
+        CK(cudaMemcpyAsync(ctx->h_gp_out, ctx->gp_out, (size_t)ctx->gp.ncomp * per * 8, cudaMemcpyDeviceToHost, s));
+      CK(cudaStreamSynchronize(s));
+      CK(cudaGetLastError());
+      if (opt->precond == DDEL_PREC_GLOBAL) {
+        for (int c = 0; c < ctx->gp.ncomp; ++c) {
+          const double* o = ctx->h_gp_out + c * per;
+          const int m = (int)o[0];
+          st.lanczos_m = m;
+          for (int j = 0; j < m; ++j) {
+            const int it = (int)o[2 + 2 * kLz + j];
+            st.inner_min = std::min(st.inner_min, it);
+            st.inner_max = std::max(st.inner_max, it);
+            inner_sum += it;
+            inner_cnt += 1;
+          }
+        }
+      }
+      const double* hh = ctx->h_gm;
+      const double* hh2 = ctx->h_gm + cap + 2;
+      for (int j = 0; j <= k; ++j) H[(size_t)j * cap + k] = hh[j] + hh2[j];
+      const double hn = std::sqrt(std::max(hh2[k + 1], 0.0));
+      H[(size_t)(k + 1) * cap + k] = hn;
+      if (hn > 0.0 && k + 1 <= cap) launch_scale_gm(w, V + (size_t)(k + 1) * n, n, nullptr, -1, hn, s);
+      // Givens rotations of the Hessenberg column (Saad)
+      for (int j = 0; j < k; ++j) {
+        const double a = H[(size_t)j * cap + k], b = H[(size_t)(j + 1) * cap + k];
+        H[(size_t)j * cap + k] = cs[j] * a + sn[j] * b;
+        H[(size_t)(j + 1) * cap + k] = -sn[j] * a + cs[j] * b;
+      }
+      const double a = H[(size_t)k * cap + k], b = H[(size_t)(k + 1) * cap + k];
+      const double den = std::hypot(a, b);
+      cs[k] = a / den;
+      sn[k] = b / den;
+      H[(size_t)k * cap + k] = den;
+      H[(size_t)(k + 1) * cap + k] = 0.0;
+      e[k + 1] = -sn[k] * e[k];
+      e[k] = cs[k] * e[k];
+      k_done = k + 1;
+      st.est_relres = std::fabs(e[k + 1]) / beta0;
+      if (std::fabs(e[k + 1]) <= opt->tol * beta0 || !(hn > 0.0)) {
+        st.status = DDEL_OK;
+        break;
+      }
+    }
+    // y = R^-1 e, u = Z y
+    std::vector<double> y(k_done, 0.0);
+    for (int i = k_done - 1; i >= 0; --i) {
+      double v = e[i];
+      for (int j = i + 1; j < k_done; ++j) v -= H[(size_t)i * cap + j] * y[j];
+      y[i] = v / H[(size_t)i * cap + i];
+    }
+    std::memcpy(ctx->h_gm, y.data(), k_done * 8);
+    CK(cudaMemcpyAsync(h, ctx->h_gm, k_done * 8, cudaMemcpyHostToDevice, s));
+    launch_multi_axpy(Z, n, k_done, h, ctx->d_u, n, 1, s);
+  }
+  st.iters = k_done;
+  // the FP64 residual of the result
+  launch_apply_K(ctx->T, ctx->F, ctx->d_u, ctx->d_f, ctx->d_r, 1, ctx->partials, ctx->ticketK, ctx->nrm, s,
+                 ctx->nblk);
+  ctx->launches += 2;
+  CK(cudaMemcpyAsync(ctx->h_nrm, ctx->nrm, 16, cudaMemcpyDeviceToHost, s));
+  if (on_device)
+    CK(cudaMemcpyAsync(u, ctx->d_u, n * 8, cudaMemcpyDeviceToDevice, s));
+  else
+    CK(cudaMemcpyAsync(u, ctx->d_u, n * 8, cudaMemcpyDeviceToHost, s));
+  CK(cudaEventRecord(ctx->ev[6], s));
+  CK(cudaStreamSynchronize(s));
+  CK(cudaGetLastError());
+  st.relres = ctx->h_nrm[1] > 0 ? ctx->h_nrm[0] / ctx->h_nrm[1] : 0.0;
+  st.t_ms = elapsed(ctx->ev[0], ctx->ev[6]);
+  if (inner_cnt == 0) st.inner_min = 0;
+  st.inner_mean = inner_cnt ? (double)inner_sum / inner_cnt : 0.0;
+  ctx->u_valid = false;
+  if (stats) *stats = st;
+  return st.status;
 }
 
 int ddel_apply_K(ddel_ctx* ctx, const double* x, double* y) {

@@ -12,6 +12,8 @@
 //  * pcg_*_kernel     : interface PCG with the face-local preconditioner of
 //                       Sec. 3-4; deterministic two-level FP64 dot products.
 //  * apply_K_kernel   : global element-by-element K x / f - K x in FP64.
+#include <cuda_bf16.h>
+
 #include <cmath>
 #include <cstdio>
 
@@ -879,6 +881,8 @@ __global__ void __launch_bounds__(256) form_syrk2d_kernel(DevTables t, const T* 
       if (qa != qb) out[(int64_t)j * NR + i] = acc[a][b];
     }
 }
+
+#include "ddel_ozaki.cuh"
 
 // y_ring = S_i x_ring for every subdomain.
 template <typename T, int NR>
@@ -1840,6 +1844,19 @@ void run_form(const DevTables& t, const DevFields& fld, const void* factor, void
 
 }  // namespace
 
+size_t ozaki_smem_bytes(const DevTables& t) {
+  return (size_t)kOzTile * kOzLd * 8 + 2 * kOzTile * kOzKC * 2 + kOzTile * 8 + kOzTile * 4 + 64 * 8 +
+         (size_t)t.s * t.s * 8 + 3 * kOzTile * 4 + 64;
+}
+
+int ozaki_kp(const DevTables& t) { return ((t.nb_max * t.BP + kOzKC - 1) / kOzKC) * kOzKC; }
+
+size_t ozaki_slice_elems(const DevTables& t, int NR) {
+  const int Kp = ozaki_kp(t);
+  const int bits = Kp <= 1489 ? 6 : 5;
+  return (size_t)t.n_sub * oz_slices(bits) * NR * Kp;
+}
+
 int explicit_ring_size(const DevTables& t) {
   // NR: padded ring size of the explicit form (0 = explicit form unavailable)
   if (t.dim != 2) return 0;
@@ -1849,7 +1866,49 @@ int explicit_ring_size(const DevTables& t) {
 }
 
 size_t explicit_form_work_elems(const DevTables& t) {
-  return explicit_ring_size(t) == 256 ? (size_t)t.n_sub * t.nb_max * t.BP * 256 : 0;
+  // W = L^-1 K_IG of every subdomain: the NR = 256 formation, and the
+  // tensor-core formation of NR = 128
+  const int NR = explicit_ring_size(t);
+  return NR >= 128 ? (size_t)t.n_sub * t.nb_max * t.BP * NR : 0;
+}
+
+bool tensor_form_available(const DevTables& t) {
+  const int NR = explicit_ring_size(t);
+  return NR == 128 || NR == 256;
+}
+
+size_t tensor_form_work_bytes(const DevTables& t) {
+  const int NR = explicit_ring_size(t);
+  if (NR != 128 && NR != 256) return 0;
+  return ozaki_slice_elems(t, NR) * sizeof(__nv_bfloat16) + (size_t)t.n_sub * NR * sizeof(int) + 256;
+}
+
+void launch_schur_form_tc(const DevTables& t, const DevFields& fld, const void* factor, void* work,
+                          void* tc_work, void* Sexp, int* err, cudaStream_t st) {
+  const int NR = explicit_ring_size(t);
+  const int Kp = ozaki_kp(t);
+  __nv_bfloat16* Wsl = reinterpret_cast<__nv_bfloat16*>(tc_work);
+  int* expo = reinterpret_cast<int*>(reinterpret_cast<char*>(tc_work) + ozaki_slice_elems(t, NR) * 2 + 128);
+  double* W = reinterpret_cast<double*>(work);
+  const double* fac = reinterpret_cast<const double*>(factor);
+  if (NR == 128) {
+    form_w2d_kernel<double, 32, 128, kFormGC><<<dim3(t.n_sub, 128 / kFormGC), 256, form_w_smem<double, 32, 128>(t),
+                                                st>>>(t, t.Ke64, fld.scale64, fac, W);
+  } else if (t.BP == 64) {
+    form_w2d_kernel<double, 64, 256, kFormGC><<<dim3(t.n_sub, 256 / kFormGC), 256, form_w_smem<double, 64, 256>(t),
+                                                st>>>(t, t.Ke64, fld.scale64, fac, W);
+  } else {
+    form_w2d_kernel<double, 96, 256, kFormGC><<<dim3(t.n_sub, 256 / kFormGC), 256, form_w_smem<double, 96, 256>(t),
+                                                st>>>(t, t.Ke64, fld.scale64, fac, W);
+  }
+  ozaki_slice_kernel<<<dim3(t.n_sub, (NR + 127) / 128), 128, 0, st>>>(t, W, NR, Kp, Wsl, expo);
+  const size_t sm = ozaki_smem_bytes(t);
+  if (NR == 128)
+    ozaki_syrk_kernel<128><<<dim3(t.n_sub, 1), kOzThreads, sm, st>>>(t, t.Ke64, fld.scale64, Wsl, expo, Kp,
+                                                                     reinterpret_cast<double*>(Sexp), err);
+  else
+    ozaki_syrk_kernel<256><<<dim3(t.n_sub, 3), kOzThreads, sm, st>>>(t, t.Ke64, fld.scale64, Wsl, expo, Kp,
+                                                                     reinterpret_cast<double*>(Sexp), err);
 }
 
 void launch_schur_form(const DevTables& t, const DevFields& fld, int precision, bool df, const void* factor,
@@ -1949,6 +2008,9 @@ cudaError_t configure_kernels() {
   DDEL_CFG((form_syrk2d_kernel<float, 96, 256, kFormTQ>));
   // the update kernel's staged face tables plus the coarse variants' static
   // reduction arrays exceed the default 48 KB
+  DDEL_CFG((ozaki_syrk_kernel<128>));
+  DDEL_CFG((ozaki_syrk_kernel<256>));
+  DDEL_CFG((form_w2d_kernel<double, 32, 128, kFormGC>));
   DDEL_CFG((pcg_update_kernel<double, 0>));
   DDEL_CFG((pcg_update_kernel<double, 4>));
   DDEL_CFG((pcg_update_kernel<double, 8>));

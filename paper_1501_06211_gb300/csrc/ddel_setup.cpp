@@ -9,6 +9,7 @@
 #include <tuple>
 
 #include "ddel_internal.h"
+#include "ddel_globalprec.h"
 
 namespace ddel {
 
@@ -610,6 +611,127 @@ void interface_operator(const Setup& S, int comp, std::vector<int32_t>* pos, std
     }
     (*rowptr)[r + 1] = (int64_t)col->size();
   }
+}
+
+
+// ---- global interface preconditioner (Sec. 3-4): host set-up ---------------
+namespace {
+
+// Inverse of the SPD n x n matrix A (row-major) by Cholesky; false if a pivot
+// is not positive.
+bool spd_inverse(int n, const std::vector<double>& A, std::vector<double>* inv) {
+  std::vector<double> Lc(A);
+  for (int j = 0; j < n; ++j) {
+    double d = Lc[j * n + j];
+    for (int k = 0; k < j; ++k) d -= Lc[j * n + k] * Lc[j * n + k];
+    if (!(d > 0.0)) return false;
+    d = std::sqrt(d);
+    Lc[j * n + j] = d;
+    for (int i = j + 1; i < n; ++i) {
+      double v = Lc[i * n + j];
+      for (int k = 0; k < j; ++k) v -= Lc[i * n + k] * Lc[j * n + k];
+      Lc[i * n + j] = v / d;
+    }
+  }
+  inv->assign((size_t)n * n, 0.0);
+  std::vector<double> e(n), y(n);
+  for (int c = 0; c < n; ++c) {
+    // L y = e_c, L^T x = y
+    for (int i = 0; i < n; ++i) {
+      double v = i == c ? 1.0 : 0.0;
+      for (int k = 0; k < i; ++k) v -= Lc[i * n + k] * y[k];
+      y[i] = v / Lc[i * n + i];
+    }
+    for (int i = n - 1; i >= 0; --i) {
+      double v = y[i];
+      for (int k = i + 1; k < n; ++k) v -= Lc[k * n + i] * e[k];
+      e[i] = v / Lc[i * n + i];
+    }
+    for (int i = 0; i < n; ++i) (*inv)[(size_t)i * n + c] = e[i];
+  }
+  return true;
+}
+
+}  // namespace
+
+std::string build_global_prec(const Setup& S, int comp, GPHost* G) {
+  interface_operator(S, comp, &G->pos, &G->rowptr, &G->col, &G->M, &G->L);
+  const int n = (int)G->pos.size();
+  G->Mdiag.assign(n, 0.0);
+  G->Ldiag.assign(n, 0.0);
+  G->Minv_diag.assign(n, 0.0);
+  G->cross_inv.assign(n, 0.0);
+  std::vector<char> anchored(n, 0);
+  for (int i = 0; i < n; ++i) {
+    double rs = 0.0, amax = 0.0;
+    for (int64_t q = G->rowptr[i]; q < G->rowptr[i + 1]; ++q) {
+      if (G->col[q] == i) {
+        G->Mdiag[i] = G->M[q];
+        G->Ldiag[i] = G->L[q];
+      }
+      rs += G->L[q];
+      amax = std::max(amax, std::fabs(G->L[q]));
+    }
+    if (!(G->Mdiag[i] > 0.0) || !(G->Ldiag[i] > 0.0)) return "interface operator with an empty row";
+    G->Minv_diag[i] = 1.0 / G->Mdiag[i];
+    G->cross_inv[i] = 1.0 / G->Ldiag[i];
+    // a row whose Laplacian entries do not sum to zero touches a removed
+    // (clamped) node: it anchors its connected part of the interface
+    anchored[i] = std::fabs(rs) > 1e-12 * amax;
+  }
+  // singular L: a connected part of the interface graph without an anchor
+  std::vector<int> part(n, -1), stack;
+  G->singular = false;
+  for (int s0 = 0; s0 < n && !G->singular; ++s0) {
+    if (part[s0] >= 0) continue;
+    bool anch = false;
+    stack.assign(1, s0);
+    part[s0] = s0;
+    while (!stack.empty()) {
+      const int i = stack.back();
+      stack.pop_back();
+      anch = anch || anchored[i];
+      for (int64_t q = G->rowptr[i]; q < G->rowptr[i + 1]; ++q) {
+        const int j = G->col[q];
+        if (part[j] < 0) {
+          part[j] = s0;
+          stack.push_back(j);
+        }
+      }
+    }
+    if (!anch) G->singular = true;
+  }
+  // faces: the face-local preconditioner's blocks of this component, as
+  // contiguous ranges of local rows (Gamma positions are ascending in pos)
+  std::vector<int32_t> local(S.gamma_dof.size(), -1);
+  for (int i = 0; i < n; ++i) local[G->pos[i]] = i;
+  G->row_face.assign(n, -1);
+  G->face_l0.clear();
+  G->face_n.clear();
+  G->face_inv_off.clear();
+  G->face_inv.clear();
+  for (size_t b = 0; b < S.blk_off.size(); ++b) {
+    const int off = S.blk_off[b], nb = S.blk_n[b];
+    if (nb <= 0 || S.gamma_dof[off] % S.dim != comp) continue;
+    const int l0 = local[off];
+    if (l0 < 0) return "face block outside its component";
+    for (int a = 0; a < nb; ++a)
+      if (local[off + a] != l0 + a) return "face block not contiguous in its component";
+    std::vector<double> A((size_t)nb * nb, 0.0), inv;
+    for (int a = 0; a < nb; ++a)
+      for (int64_t q = G->rowptr[l0 + a]; q < G->rowptr[l0 + a + 1]; ++q) {
+        const int cb = G->col[q] - l0;
+        if (cb >= 0 && cb < nb) A[(size_t)a * nb + cb] = G->L[q];
+      }
+    if (!spd_inverse(nb, A, &inv)) return "face Laplacian not positive definite";
+    const int f = (int)G->face_l0.size();
+    G->face_l0.push_back(l0);
+    G->face_n.push_back(nb);
+    G->face_inv_off.push_back((int64_t)G->face_inv.size());
+    G->face_inv.insert(G->face_inv.end(), inv.begin(), inv.end());
+    for (int a = 0; a < nb; ++a) G->row_face[l0 + a] = f;
+  }
+  return "";
 }
 
 }  // namespace ddel

@@ -44,7 +44,8 @@ class ddel_options(ctypes.Structure):
     _fields_ = [("precision", c_int), ("theta", c_double), ("face_scaling", c_int),
                 ("crosspoint_mode", c_int), ("tol", c_double), ("max_it", c_int),
                 ("max_cycles", c_int), ("inner_tol", c_double), ("x0_mode", c_int),
-                ("schur_mode", c_int), ("use_graph", c_int), ("check_every", c_int)]
+                ("schur_mode", c_int), ("use_graph", c_int), ("check_every", c_int),
+                ("tensor_form", c_int)]
 
 
 class ddel_stats(ctypes.Structure):
@@ -57,6 +58,24 @@ class ddel_stats(ctypes.Structure):
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class ddel_gmres_options(ctypes.Structure):
+    _fields_ = [("precond", c_int), ("lanczos_steps", c_int), ("inner_tol", c_double),
+                ("mass_tol", c_double), ("global_scaling", c_int), ("tol", c_double), ("max_it", c_int)]
+
+
+class ddel_gmres_stats(ctypes.Structure):
+    _fields_ = [("status", c_int), ("iters", c_int), ("est_relres", c_double), ("relres", c_double),
+                ("inner_min", c_int), ("inner_max", c_int), ("inner_mean", c_double),
+                ("lanczos_m", c_int), ("t_ms", c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+DDEL_PREC_IDENTITY, DDEL_PREC_FACE, DDEL_PREC_GLOBAL = 0, 1, 2
+DDEL_MAX_LANCZOS = 32
 
 
 class ddel_info_t(ctypes.Structure):
@@ -130,6 +149,10 @@ def _load():
         "ddel_topopt_step": (c_int, [c_void_p, P(ddel_topopt_state), P(ddel_stats)]),
         "ddel_set_coarse": (c_int, [c_void_p, c_void_p, c_int, c_int, c_int]),
         "ddel_selftest_wait_timeout": (c_int, [ctypes.c_uint, P(c_int)]),
+        "ddel_default_gmres_options": (None, [P(ddel_gmres_options)]),
+        "ddel_gmres_solve": (c_int, [c_void_p, P(ddel_gmres_options), c_void_p, c_void_p, c_int,
+                                     P(ddel_gmres_stats)]),
+        "ddel_global_precond_apply": (c_int, [c_void_p, P(ddel_gmres_options), c_void_p, c_void_p, c_void_p]),
         "ddel_checkpoint_save": (c_int, [c_void_p, P(ddel_topopt_state), ctypes.c_char_p]),
         "ddel_checkpoint_load": (c_int, [c_void_p, P(ddel_topopt_state), ctypes.c_char_p]),
         "ddel_residual_norm_noalloc": (c_int, [c_int, c_int, c_int, c_int, c_void_p, c_void_p,
@@ -334,6 +357,39 @@ def ddel_kernel_info(h):
         name = "schur2d_kernel" + ("<float>" if k.precision else "<double>")
     d["schur_apply_kernel"] = name
     return d
+
+
+def ddel_default_gmres_options(**kw):
+    o = ddel_gmres_options()
+    _lib.ddel_default_gmres_options(ctypes.byref(o))
+    for k, v in kw.items():
+        setattr(o, k, v)
+    return o
+
+
+def ddel_gmres_solve(h, opt, f, u, on_device):
+    st = ddel_gmres_stats()
+    code = _lib.ddel_gmres_solve(h, ctypes.byref(opt), _ptr(f), _ptr(u), on_device, ctypes.byref(st))
+    return code, st
+
+
+def ddel_global_precond_apply(h, opt, r, z, with_record=False):
+    """z = S~^-1 r (global form); with_record returns the per-component
+    Lanczos record (m, mass iterations, alpha, beta, inner iterations)."""
+    rec = np.zeros(3 * (2 + 3 * DDEL_MAX_LANCZOS)) if with_record else None
+    code = _lib.ddel_global_precond_apply(h, ctypes.byref(opt), _ptr(r), _ptr(z),
+                                          rec.ctypes.data if rec is not None else None)
+    if rec is None:
+        return code, None
+    out = []
+    K = DDEL_MAX_LANCZOS
+    for c in range(3):
+        o = rec[c * (2 + 3 * K):(c + 1) * (2 + 3 * K)]
+        m = int(o[0])
+        out.append({"m": m, "mass_its": int(o[1]), "alpha": o[2:2 + m].copy(),
+                    "beta": o[2 + K:2 + K + max(m - 1, 0)].copy(),
+                    "inner_its": o[2 + 2 * K:2 + 2 * K + m].astype(int).tolist()})
+    return code, out
 
 
 def ddel_residual_norm_noalloc(dim, nx, ny, nz, Ke, factors, fixed, f, u, r, norms, stream=None):
@@ -681,6 +737,19 @@ class Solver:
         code, st = ddel_topopt_step(self.h, ts)
         _check(code, self.h)
         return st
+
+    def gmres(self, f=None, u=None, **options):
+        """Full-system FGMRES with the block-triangular preconditioner
+        (ddel_gmres_solve); options override ddel_default_gmres_options()."""
+        on_dev = u is not None and hasattr(u, "is_cuda") and u.is_cuda
+        if u is None:
+            u = np.zeros(self.n_dof)
+        if f is not None and not on_dev:
+            f = np.ascontiguousarray(f, dtype=np.float64)
+        code, st = ddel_gmres_solve(self.h, ddel_default_gmres_options(**options), f, u, on_dev)
+        if code not in (DDEL_OK, DDEL_ENOCONV):
+            raise DDELError(code, _lib.ddel_last_error(self.h).decode())
+        return u, st
 
     def solve(self, f=None, u=None, check=True):
         """Solve K u = f; f/u torch CUDA tensors (device path) or NumPy (host path)."""

@@ -36,6 +36,27 @@ def cantilever_3d(nx, ny, nz):
     return {"clamp": [(0, 0)], "traction": (0, 1, (0.0, 0.0, -1.0 / (ny * nz)))}
 
 
+def table1_2d(h_inv):
+    """Loads of the paper's Table 1 test problem on (0,2)x(0,1) (reading Q14)
+    for a grid of unit elements standing for elements of width h = 1/h_inv:
+    right edge clamped, downward body force 0.75 (0.75 h^2 per unit element)
+    and outward unit traction on the left edge x = 0 (normal (-1, 0); h per
+    unit edge)."""
+    h = 1.0 / h_inv
+    return {"clamp": [(0, 1)], "traction": (0, 0, (-h, 0.0)), "body": (0.0, -0.75 * h * h)}
+
+
+def table1_config(h_inv, n_sub_x):
+    """Table 1's cantilever on (0,2)x(0,1) with mesh width 1/h_inv: a
+    (2 h_inv) x h_inv grid of unit elements (lengths in units of h) in
+    n_sub_x x n_sub_x / 2 square subdomains; homogeneous material (rho = 1,
+    p = 1), E = 1, nu = 0.3."""
+    nx, ny = 2 * h_inv, h_inv
+    sub = nx // n_sub_x
+    return dict(name=f"table1_h{h_inv}_n{n_sub_x * n_sub_x // 2}", dim=2, ne=(nx, ny), sub=sub, E=1.0,
+                nu=0.3, p=1.0, bc=table1_2d(h_inv), density=("uniform", 1.0))
+
+
 def uniform_density(n_elem, value):
     return np.full(n_elem, float(value))
 
