@@ -298,7 +298,6 @@ def main():
     batch = batched_uneven(ddel, torch, workloads) if world == 1 else None
     three_d = solve_3d(ddel, torch, workloads, stream) if world == 1 else None
     table1 = table1_study(ddel, torch, workloads) if world == 1 else None
-    global_c1 = global_on_config1(ddel, torch, workloads, stream) if world == 1 else None
     out = {
         "metric": METRIC, "value": head["ms"] / world, "unit": "ms", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": head["ms"],
@@ -319,8 +318,6 @@ def main():
         out["batch"] = batch
     if table1 is not None:
         out["table1"] = table1
-    if global_c1 is not None:
-        out["global_preconditioner_c1"] = global_c1
     if clk is not None:
         out["clocks"] = clk
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -455,32 +452,6 @@ def table1_study(ddel, torch, workloads):
     except Exception as e:  # noqa: BLE001 - reported, the headline line must still print
         rows.append({"error": repr(e)})
     return {"problem": "Table 1 cantilever (reading Q14), FGMRES tol 1e-6", "rows": rows}
-
-
-def global_on_config1(ddel, torch, workloads, stream):
-    """The paper's global preconditioner on the 512x256 GRF workload (diagonal
-    material scaling, reading Q25): full-system FGMRES to 1e-8 against the
-    same FGMRES with the face-local preconditioner and the hot path's
-    interface PCG (which reaches the same tolerance)."""
-    try:
-        cfg = workloads.config("c1")
-        rho = workloads.density(cfg)
-        s = ddel.Solver(cfg, stream=stream.cuda_stream)
-        s.assemble(rho)
-        s.factor()
-        res = {"workload": "512x256 GRF cantilever, 512 subdomains, tol 1e-8"}
-        for name, pc in (("fgmres_global", 2), ("fgmres_face_local", 1)):
-            _, st = s.gmres(precond=pc, tol=1e-8, global_scaling=1, max_it=1500)
-            res[name] = {"iters": st.iters, "ms": st.t_ms, "relres": st.relres, "status": st.status}
-            if pc == 2:
-                res[name]["inner_pcg_min_max_mean"] = [st.inner_min, st.inner_max, round(st.inner_mean, 2)]
-        u = torch.zeros(s.n_dof, dtype=torch.float64, device="cuda")
-        _, st = s.solve(None, u)
-        res["pcg_face_local"] = {"iters": st.iters, "ms": st.t_total_ms, "relres": st.relres}
-        s.close()
-        return res
-    except Exception as e:  # noqa: BLE001
-        return {"error": repr(e)}
 
 
 def batched_uneven(ddel, torch, workloads, count=64, reps=2):

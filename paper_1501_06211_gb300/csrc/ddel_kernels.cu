@@ -1845,8 +1845,7 @@ void run_form(const DevTables& t, const DevFields& fld, const void* factor, void
 }  // namespace
 
 size_t ozaki_smem_bytes(const DevTables& t) {
-  return (size_t)kOzTile * kOzLd * 8 + 2 * kOzTile * kOzKC * 2 + kOzTile * 8 + kOzTile * 4 + 64 * 8 +
-         (size_t)t.s * t.s * 8 + 3 * kOzTile * 4 + 64;
+  return (size_t)kOzStages * 32768 + 64 * 8 + (size_t)t.s * t.s * 8 + 4 * kOzTile * 4 + 64;
 }
 
 int ozaki_kp(const DevTables& t) { return ((t.nb_max * t.BP + kOzKC - 1) / kOzKC) * kOzKC; }
@@ -1901,7 +1900,7 @@ void launch_schur_form_tc(const DevTables& t, const DevFields& fld, const void* 
     form_w2d_kernel<double, 96, 256, kFormGC><<<dim3(t.n_sub, 256 / kFormGC), 256, form_w_smem<double, 96, 256>(t),
                                                 st>>>(t, t.Ke64, fld.scale64, fac, W);
   }
-  ozaki_slice_kernel<<<dim3(t.n_sub, (NR + 127) / 128), 128, 0, st>>>(t, W, NR, Kp, Wsl, expo);
+  ozaki_slice_kernel<<<dim3(t.n_sub, NR / 32), 256, 0, st>>>(t, W, NR, Kp, Wsl, expo);
   const size_t sm = ozaki_smem_bytes(t);
   if (NR == 128)
     ozaki_syrk_kernel<128><<<dim3(t.n_sub, 1), kOzThreads, sm, st>>>(t, t.Ke64, fld.scale64, Wsl, expo, Kp,

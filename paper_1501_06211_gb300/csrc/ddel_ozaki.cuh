@@ -31,39 +31,73 @@
 //   lanes = rows) and add it, scaled, into the FP64 tile in shared memory.
 
 
-constexpr int kOzThreads = 128;
+constexpr int kOzThreads = 256;
 constexpr int kOzKC = 64;      // rows of W per operand chunk
 constexpr int kOzTile = 128;   // output tile edge (MMA M = N)
-constexpr int kOzLd = kOzTile + 1;  // FP64 tile row stride (rows in distinct banks)
 
 __device__ __forceinline__ int oz_bits(int K) { return K <= 1489 ? 6 : 5; }
 __device__ __host__ __forceinline__ int oz_slices(int bits) { return (54 + bits - 1) / bits; }
 
+// Byte offset of element (c, k) (c < 128 ring columns of a row tile, k < 64
+// rows of a chunk) in a 16 KB operand image: the canonical K-major layout
+// without swizzling -- K slab k / 16 at 4096 B, in it the 8 x 8 core matrix
+// of column group c / 8 and row half (k % 16) / 8 at 256 B and 128 B steps,
+// 16 bytes per core-matrix row.  The slices are stored as these images, so a
+// chunk reaches shared memory by one bulk copy.
+__device__ __forceinline__ int oz_img_off(int c, int k) {
+  return (k >> 4) * 4096 + (c >> 3) * 256 + ((k >> 3) & 1) * 128 + (c & 7) * 16 + (k & 7) * 2;
+}
+
 // Slices of W for every subdomain.  W: per subdomain nb_max * BP rows of NR
-// doubles; Wsl: per subdomain S * NR * Kp BF16 values (Kp = rows rounded up to
-// kOzKC); expo: per subdomain NR ints.  One thread per (subdomain, column).
-__global__ void ozaki_slice_kernel(DevTables t, const double* __restrict__ W, int NR, int Kp,
-                                   __nv_bfloat16* __restrict__ Wsl, int* __restrict__ expo) {
-  const int sub = blockIdx.x, j = threadIdx.x + blockIdx.y * blockDim.x;
-  if (j >= NR) return;
+// doubles; Wsl: per subdomain, slice p, row tile rt (NR / 128) and chunk kc
+// (Kp / 64) one 16 KB image (oz_img_off); expo: per subdomain NR ints.  Block
+// (subdomain, 32 columns) of 256 threads: the column maxima, then per thread
+// one column and 8 consecutive rows, written as one 16-byte unit per slice.
+__global__ void __launch_bounds__(256) ozaki_slice_kernel(DevTables t, const double* __restrict__ W, int NR, int Kp,
+                                                          __nv_bfloat16* __restrict__ Wsl, int* __restrict__ expo) {
+  const int sub = blockIdx.x, j0 = blockIdx.y * 32, tid = threadIdx.x;
+  const int jl = tid & 31, ko = tid >> 5;  // column in the block, row offset
   const SubInfo si = t.subs[sub];
   const int K = si.nb * t.BP;  // rows of this subdomain's W (the rest are zero)
   const int bits = oz_bits(Kp), S = oz_slices(bits);
-  const double* Wc = W + (int64_t)sub * t.nb_max * t.BP * NR + j;
+  const double* Wb = W + (int64_t)sub * t.nb_max * t.BP * NR;
+  __shared__ double mx_s[8][32];
+  __shared__ int e_s[32];
   double mx = 0.0;
-  for (int k = 0; k < K; ++k) mx = fmax(mx, fabs(Wc[(int64_t)k * NR]));
-  int e = 0;
-  if (mx > 0.0) frexp(mx, &e);  // mx = f 2^e, 0.5 <= f < 1: |W_kj| 2^-e < 1
-  expo[(int64_t)sub * NR + j] = e;
-  __nv_bfloat16* out = Wsl + (int64_t)sub * S * NR * Kp;
+  for (int k = ko; k < K; k += 8) mx = fmax(mx, fabs(Wb[(int64_t)k * NR + j0 + jl]));
+  mx_s[ko][jl] = mx;
+  __syncthreads();
+  if (tid < 32) {
+    double m = 0.0;
+    for (int q = 0; q < 8; ++q) m = fmax(m, mx_s[q][tid]);
+    int e = 0;
+    if (m > 0.0) frexp(m, &e);  // m = f 2^e, 0.5 <= f < 1: |W_kj| 2^-e < 1
+    e_s[tid] = e;
+    expo[(int64_t)sub * NR + j0 + tid] = e;
+  }
+  __syncthreads();
+  const int e = e_s[jl];
+  const int j = j0 + jl, rt = j >> 7, c = j & 127;
+  const int NRT = NR / 128, NKC = Kp / 64;
   const double up = ldexp(1.0, bits);
-  for (int k = 0; k < Kp; ++k) {
-    double v = k < K ? ldexp(Wc[(int64_t)k * NR], -e) : 0.0;
+  unsigned char* img0 = reinterpret_cast<unsigned char*>(Wsl) + (int64_t)sub * S * NRT * NKC * 16384;
+  for (int k8 = ko * 8; k8 < Kp; k8 += 64) {
+    double v[8];
+#pragma unroll
+    for (int r = 0; r < 8; ++r) v[r] = k8 + r < K ? ldexp(Wb[(int64_t)(k8 + r) * NR + j], -e) : 0.0;
+    const int kc = k8 >> 6;
+    const int off = oz_img_off(c, k8 & 63);
     for (int p = 0; p < S; ++p) {
-      const double tv = v * up;    // exact: a power-of-two scaling
-      const double dv = rint(tv);  // |dv| <= 2^bits, an integer
-      v = tv - dv;                 // exact: |v| <= 1/2
-      out[((int64_t)p * NR + j) * Kp + k] = __double2bfloat16(dv);
+      __align__(16) __nv_bfloat16 h[8];
+#pragma unroll
+      for (int r = 0; r < 8; ++r) {
+        const double tv = v[r] * up;    // exact: a power-of-two scaling
+        const double dv = rint(tv);     // |dv| <= 2^bits, an integer
+        v[r] = tv - dv;                 // exact: |v| <= 1/2
+        h[r] = __double2bfloat16(dv);
+      }
+      unsigned char* img = img0 + ((int64_t)(p * NRT + rt) * NKC + kc) * 16384;
+      *reinterpret_cast<uint4*>(img + off) = *reinterpret_cast<const uint4*>(h);
     }
   }
 }
@@ -128,33 +162,28 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
   for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
 }
 
-// Copies rows [r0, r0 + 128) x chunk rows [k0, k0 + 64) of one slice (stored
-// [column][row], rows contiguous) into the operand layout: K slab s (16 rows
-// of W) at s * 4096 bytes, in it the core matrix of 8-column group g and
-// 8-row half h at g * 256 + h * 128, each core-matrix row 16 bytes.
-__device__ __forceinline__ void oz_load_tile(const __nv_bfloat16* __restrict__ sl, int Kp, int c0, int k0,
-                                             unsigned char* dst) {
-  for (int v = threadIdx.x; v < kOzTile * (kOzKC / 8); v += blockDim.x) {
-    const int c = v / (kOzKC / 8), kq = v % (kOzKC / 8);  // column, 8-row octet
-    const uint4 val = *reinterpret_cast<const uint4*>(sl + (int64_t)(c0 + c) * Kp + k0 + 8 * kq);
-    const int s = kq >> 1, h = kq & 1;
-    *reinterpret_cast<uint4*>(dst + s * 4096 + (c >> 3) * 256 + h * 128 + (c & 7) * 16) = val;
-  }
-}
+// S tile (ta, tb) of one subdomain: K_GG entries minus 2^(e_i + e_j) sum_d
+// 2^(-B d) C_d, C_d = sum_{p + q = d} D_p^T D_q accumulated in tensor memory,
+// d from S + 1 down to 2 (small terms first).  256 threads: thread (w, l)
+// keeps row 32 (w % 4) + l, columns 64 (w / 4) .. + 63 of the FP64 tile in
+// registers (warp w reads tensor-memory lanes 32 (w % 4) ..).  Thread 0
+// drives a pipeline of kOzStages stages: per step (pair, chunk) one bulk copy
+// of the A and one of the B image (16 KB each) completing on the stage's
+// full barrier, four 128 x 128 x 16 MMAs committed to the stage's empty
+// barrier, after which the stage is refilled with the step kOzStages ahead
+// (the sequence runs on across groups, so the loads of the next group overlap
+// the drain of this one).  Every wait is bounded; on a timeout the kernel
+// records kErrTimeout in err, stops issuing work, still frees its tensor
+// memory and returns.
+constexpr int kOzStages = 6;
 
-// S tile (ta, tb) of one subdomain: K_GG entries plus -2^(e_i + e_j) sum_d
-// 2^(-B d) C_d, C_d = sum_{p + q = d} D_p^T D_q accumulated in tensor memory.
-// Dynamic shared memory: the FP64 tile (128 x 128), two operand tiles (16 KB
-// each), column scales, the element data of K_GG.  err: set to kErrTimeout
-// when a bounded wait runs out (the kernel then skips the remaining work,
-// still frees its tensor memory and returns).
 template <int NR>
 __global__ void __launch_bounds__(kOzThreads, 1) ozaki_syrk_kernel(DevTables t, const double* __restrict__ Ke_g,
                                                                    const double* __restrict__ scale,
                                                                    const __nv_bfloat16* __restrict__ Wsl,
                                                                    const int* __restrict__ expo, int Kp,
                                                                    double* __restrict__ Sexp, int* err) {
-  constexpr int NT = NR / kOzTile;
+  constexpr int NT = NR / kOzTile, NST = kOzStages;
   const int sub = blockIdx.x, tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   int ta = 0, q = blockIdx.y;  // tile index -> (ta, tb), ta <= tb
   while (q >= NT - ta) {
@@ -166,16 +195,12 @@ __global__ void __launch_bounds__(kOzThreads, 1) ozaki_syrk_kernel(DevTables t, 
   const int s = t.s;
   const int bits = oz_bits(Kp), S = oz_slices(bits);
   extern __shared__ __align__(1024) unsigned char oz_smem[];
-  double* St = reinterpret_cast<double*>(oz_smem);                 // 128 x kOzLd FP64
-  unsigned char* At = oz_smem + kOzTile * kOzLd * 8;               // 16 KB
-  unsigned char* Bt = At + kOzTile * kOzKC * 2;                     // 16 KB
-  double* colsc = reinterpret_cast<double*>(Bt + kOzTile * kOzKC * 2);  // 128: 2^e_j of tile tb
-  float* rowsc = reinterpret_cast<float*>(colsc + kOzTile);         // 128: 2^(e_i - B d) of tile ta
-  double* ke = reinterpret_cast<double*>(rowsc + kOzTile);          // 64
-  double* sc = ke + 64;                                             // s * s
-  int* rl = reinterpret_cast<int*>(sc + s * s);                     // 256: ring locs of ta, tb
-  int* erow = rl + 2 * kOzTile;                                     // 128
-  __shared__ __align__(8) uint64_t bar;
+  unsigned char* stage = oz_smem;                                 // NST x (A 16 KB, B 16 KB)
+  double* ke = reinterpret_cast<double*>(oz_smem + NST * 32768);  // 64
+  double* sc = ke + 64;                                           // s * s
+  int* rl = reinterpret_cast<int*>(sc + s * s);                   // 256: ring locs of ta, tb
+  int* ex = rl + 2 * kOzTile;                                     // 256: exponents of ta, tb
+  __shared__ __align__(8) uint64_t full[NST], empty[NST];
   __shared__ uint32_t tmem_base;
   __shared__ int s_fail;
   for (int i = tid; i < 64; i += kOzThreads) ke[i] = Ke_g[i];
@@ -184,73 +209,93 @@ __global__ void __launch_bounds__(kOzThreads, 1) ozaki_syrk_kernel(DevTables t, 
   for (int j = tid; j < 2 * kOzTile; j += kOzThreads) {
     const int jr = (j < kOzTile ? ta : tb) * kOzTile + j % kOzTile;
     rl[j] = jr < si.n_ring ? t.ring_loc[si.ring_off + jr] : -1;
-  }
-  const int* ex = expo + (int64_t)sub * NR;
-  for (int j = tid; j < kOzTile; j += kOzThreads) {
-    colsc[j] = ldexp(1.0, ex[tb * kOzTile + j]);
-    erow[j] = ex[ta * kOzTile + j];
+    ex[j] = expo[(int64_t)sub * NR + jr];
   }
   if (tid == 0) {
-    mbar_init(&bar, 1);
+    for (int i = 0; i < NST; ++i) {
+      mbar_init(&full[i], 1);
+      mbar_init(&empty[i], 1);
+    }
     fence_mbar_init();
     s_fail = 0;
   }
   if (warp == 0) tmem_alloc(&tmem_base, 128);
-  __syncthreads();
-  // K_GG part of the tile (FP64)
-  for (int v = tid; v < kOzTile * kOzTile; v += kOzThreads) {
-    const int i = v / kOzTile, j = v % kOzTile;
-    St[i * kOzLd + j] = kgg_entry2d<double>(s, ke, sc, rl[i], rl[kOzTile + j]);
-  }
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
+  // this thread's part of the tile: row i, columns jc .. jc + 63, K_GG first
+  const int i = 32 * (warp & 3) + lane, jc = 64 * (warp >> 2);
+  double acc[64];
+#pragma unroll
+  for (int c = 0; c < 64; ++c) acc[c] = kgg_entry2d<double>(s, ke, sc, rl[i], rl[kOzTile + jc + c]);
   const uint32_t dt = tmem_base;
   constexpr uint32_t idesc = idesc_bf16_f32(kOzTile, kOzTile);
-  const __nv_bfloat16* base = Wsl + (int64_t)sub * S * NR * Kp;
-  const int Kv = ((si.nb * t.BP + kOzKC - 1) / kOzKC) * kOzKC;  // rows holding data
-  uint32_t phase = 0;
-  for (int d = S + 1; d >= 2; --d) {
-    int first = 1;
-    for (int p = d - 1 < S ? d - 1 : S; p >= 1 && d - p <= S; --p) {
-      const int qq = d - p;
-      const __nv_bfloat16* sa = base + (int64_t)(p - 1) * NR * Kp;
-      const __nv_bfloat16* sb = base + (int64_t)(qq - 1) * NR * Kp;
-      for (int k0 = 0; k0 < Kv; k0 += kOzKC) {
-        oz_load_tile(sa, Kp, ta * kOzTile, k0, At);
-        oz_load_tile(sb, Kp, tb * kOzTile, k0, Bt);
-        fence_proxy_async_smem();
-        __syncthreads();
-        if (tid == 0 && !s_fail) {
-          tc_fence_after();
-#pragma unroll
-          for (int ks = 0; ks < kOzKC / 16; ++ks)
-            mma_bf16(dt, smem_desc(At + ks * 4096, 128, 256), smem_desc(Bt + ks * 4096, 128, 256), idesc,
-                     (first && ks == 0) ? 0 : 1);
-          mma_commit(&bar);
-        }
-        // every thread waits for the products that read the operand tiles
-        if (!s_fail && !mbar_wait(&bar, phase)) s_fail = 1;
-        phase ^= 1;
-        first = 0;
-        __syncthreads();
+  const int NRT = NR / 128, NKC = Kp / 64;
+  const int nkc = (si.nb * t.BP + 63) / 64;  // chunks holding data
+  const unsigned char* img0 = reinterpret_cast<const unsigned char*>(Wsl) + (int64_t)sub * S * NRT * NKC * 16384;
+  auto img = [&](int p, int rt, int kc) { return img0 + ((int64_t)((p - 1) * NRT + rt) * NKC + kc) * 16384; };
+  // step sequence: d from S + 1 down to 2; p from min(d - 1, S) down to
+  // max(1, d - S) (q = d - p); chunks kc < nkc
+  auto p_hi = [&](int d) { return d - 1 < S ? d - 1 : S; };
+  auto p_lo = [&](int d) { return d - S > 1 ? d - S : 1; };
+  int ld_d = S + 1, ld_p = p_hi(S + 1), ld_kc = 0, ld_n = 0;  // thread 0: the next step to load
+  auto produce = [&]() {
+    if (ld_d < 2 || s_fail) return;
+    const int st = ld_n % NST;
+    if (ld_n >= NST && !mbar_wait(&empty[st], ((ld_n / NST) - 1) & 1)) {
+      s_fail = 1;
+      return;
+    }
+    mbar_expect_tx(&full[st], 32768);
+    bulk_load(stage + st * 32768, img(ld_p, ta, ld_kc), 16384, &full[st]);
+    bulk_load(stage + st * 32768 + 16384, img(ld_d - ld_p, tb, ld_kc), 16384, &full[st]);
+    ++ld_n;
+    if (++ld_kc == nkc) {
+      ld_kc = 0;
+      if (--ld_p < p_lo(ld_d)) {
+        --ld_d;
+        ld_p = p_hi(ld_d);
       }
     }
-    if (s_fail) break;
-    // drain C_d: row i = this thread's lane of its warp's 32 tensor-memory lanes
-    tc_fence_after();
-    const int i = warp * 32 + lane;
-    const float rs = ldexpf(1.0f, erow[i] - bits * d);
-#pragma unroll 1
-    for (int c0 = 0; c0 < kOzTile; c0 += 32) {
-      float v[32];
-      tmem_ld32(dt + ((uint32_t)(warp * 32) << 16) + c0, v);
+  };
+  if (tid == 0)
+    for (int k = 0; k < NST; ++k) produce();
+  int n = 0;  // steps issued so far (the same count in every thread)
+  for (int d = S + 1; d >= 2; --d) {
+    const int steps = (p_hi(d) - p_lo(d) + 1) * nkc;
+    if (tid == 0) {
+      for (int k = 0; k < steps; ++k) {
+        const int st = (n + k) % NST;
+        if (s_fail || !mbar_wait(&full[st], ((n + k) / NST) & 1)) {
+          s_fail = 1;
+          break;
+        }
+        tc_fence_after();
+        const unsigned char* A = stage + st * 32768;
 #pragma unroll
-      for (int c = 0; c < 32; ++c) {
-        const int j = c0 + c;
-        // 2^(e_i - B d) C exact in FP32 (a power-of-two scaling), then 2^e_j in FP64
-        St[i * kOzLd + j] = fma(-(double)__fmul_rn(v[c], rs), colsc[j], St[i * kOzLd + j]);
+        for (int ks = 0; ks < 4; ++ks)
+          mma_bf16(dt, smem_desc(A + ks * 4096, 128, 256), smem_desc(A + 16384 + ks * 4096, 128, 256), idesc,
+                   (k == 0 && ks == 0) ? 0 : 1);
+        mma_commit(&empty[st]);
+        produce();
       }
+    }
+    n += steps;
+    __syncthreads();
+    // the group's last products complete (its commit: step n - 1)
+    if (!s_fail && !mbar_wait(&empty[(n - 1) % NST], ((n - 1) / NST) & 1)) s_fail = 1;
+    __syncthreads();
+    if (s_fail) break;
+    tc_fence_after();
+    const float rs = ldexpf(1.0f, ex[i] - bits * d);
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      float v[32];
+      tmem_ld32(dt + ((uint32_t)(32 * (warp & 3)) << 16) + jc + 32 * h, v);
+#pragma unroll
+      for (int c = 0; c < 32; ++c)  // 2^(e_i - B d) C exact in FP32, then 2^e_j in FP64
+        acc[32 * h + c] = fma(-(double)__fmul_rn(v[c], rs), ldexp(1.0, ex[kOzTile + jc + 32 * h + c]),
+                              acc[32 * h + c]);
     }
     tc_fence_before();
     __syncthreads();
@@ -259,13 +304,12 @@ __global__ void __launch_bounds__(kOzThreads, 1) ozaki_syrk_kernel(DevTables t, 
   if (s_fail && tid == 0) atomicExch(err, kErrTimeout);
   __syncthreads();
   if (warp == 0) tmem_dealloc(tmem_base, 128);
-  // the tile and, off the diagonal, its mirror
   double* out = Sexp + (int64_t)sub * NR * NR;
-  for (int v = tid; v < kOzTile * kOzTile; v += kOzThreads) {
-    const int i = v / kOzTile, j = v % kOzTile;
-    const int gi = ta * kOzTile + i, gj = tb * kOzTile + j;
-    out[(int64_t)gi * NR + gj] = St[i * kOzLd + j];
-    if (ta != tb) out[(int64_t)gj * NR + gi] = St[i * kOzLd + j];
+  const int gi = ta * kOzTile + i;
+#pragma unroll
+  for (int c = 0; c < 64; ++c) {
+    const int gj = tb * kOzTile + jc + c;
+    out[(int64_t)gi * NR + gj] = acc[c];
+    if (ta != tb) out[(int64_t)gj * NR + gi] = acc[c];
   }
 }
-
