@@ -476,6 +476,16 @@ def batched_uneven(ddel, torch, workloads, count=64, reps=2):
         code, sts = ddel.ddel_batch_solve(handles, us)
         torch.cuda.synchronize()
         times.append(1e3 * (time.perf_counter() - t0))
+    # the same batch in persistent launches with the device work queue
+    ddel.ddel_batch_solve(handles, us, persistent=True)  # warm-up
+    ptimes = []
+    pcode = 0
+    for _ in range(reps):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        pcode, psts = ddel.ddel_batch_solve(handles, us, persistent=True)
+        torch.cuda.synchronize()
+        ptimes.append(1e3 * (time.perf_counter() - t0))
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     cls = {}
@@ -495,6 +505,9 @@ def batched_uneven(ddel, torch, workloads, count=64, reps=2):
            "problems": count, "dofs": sum(s.n_dof for s in solvers), "status": code,
            "iters": sum(st.iters for st in sts), "max_relres": max(st.relres for st in sts),
            "batched_ms": min(times), "sequential_ms": seq_ms, "speedup_batched": seq_ms / min(times),
+           "persistent_ms": min(ptimes), "persistent_status": pcode,
+           "persistent_iters": sum(st.iters for st in psts),
+           "speedup_persistent": seq_ms / min(ptimes),
            "by_subdomain_edge": cls, "timing": "host wall time between device synchronisations, L2 not flushed"}
     for s in solvers:
         s.close()

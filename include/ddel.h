@@ -136,9 +136,11 @@ typedef struct {
                           iteration; IMPLICIT applies it by block substitution */
   int use_graph;       /* capture PCG iterations in a CUDA graph (1) */
   int check_every;     /* PCG iterations between host convergence checks (16) */
-  int tensor_form;     /* 1: form the FP64 local Schur complements of rings of 128 and 256
-                          with W^T W on the tensor cores at FP64 accuracy (Ozaki splitting
-                          into BF16 slices, FP32 accumulation); 0: on the FP64 pipe (1) */
+  int tensor_form;     /* 1: form the FP64 local Schur complements with W^T W on the tensor
+                          cores at FP64 accuracy (Ozaki splitting into BF16 slices, FP32
+                          accumulation): rings of 128 and 256 in the EXPLICIT form, rings
+                          of 256 in the AUTO form (whose rings of 128 keep the faster
+                          double-float formation); 0: on the FP64 pipe (1) */
 } ddel_options;
 
 typedef struct {
@@ -291,6 +293,20 @@ int ddel_checkpoint_load(ddel_ctx* ctx, ddel_topopt_state* state, const char* pa
  * ddel_solve.  The result of every problem is bitwise the one of ddel_solve
  * in FP64 (same kernels, same order).  Synchronises all streams. */
 int ddel_batch_solve(ddel_ctx* const* ctxs, int n, double* const* u, ddel_stats* stats);
+
+/* The same batch in one persistent launch per check_every iterations: a
+ * device work queue hands out, in order, for every PCG iteration the Schur
+ * blocks of every problem and then their update blocks (per-problem PCG
+ * scalars stay in each context's device state); a block that depends on
+ * another problem phase waits for it, bounded (a lost arrival returns
+ * DDEL_ETIMEOUT instead of hanging); the blocks compute exactly what the
+ * kernels of ddel_solve compute, so every problem's result is bitwise that of
+ * ddel_solve.  For the default FP64 double-float explicit form in 2D without
+ * a coarse space; other configurations take ddel_batch_solve's path.  The
+ * factorisations, condensation and back-substitution run on each context's
+ * stream as in ddel_batch_solve; the persistent launches use the first
+ * context's stream.  Synchronises all streams. */
+int ddel_batch_solve_persistent(ddel_ctx* const* ctxs, int n, double* const* u, ddel_stats* stats);
 
 /* --- Autotuner ------------------------------------------------------------------
  * Chooses the Schur form (IMPLICIT block substitution, EXPLICIT FP64, or AUTO =

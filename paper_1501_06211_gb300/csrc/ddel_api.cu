@@ -380,8 +380,12 @@ int factor_launch(ddel_ctx* ctx, int prec) {
       cudaError_t e = cudaMalloc(&ctx->form_work[prec], we * (prec ? 4 : 8));
       if (e != cudaSuccess) return fail(ctx, DDEL_ENOMEM, "explicit Schur scratch allocation");
     }
-    if (prec == 0 && ctx->opt.tensor_form && tensor_form_available(ctx->T)) {
-      // FP64-accurate S_i with W^T W on the tensor cores (both FP64 forms)
+    // FP64-accurate S_i with W^T W on the tensor cores: the native FP64 form,
+    // and the double-float form's rings of 256 (for rings of 128 the
+    // double-float form keeps its own, faster double-float formation)
+    const bool tc = prec == 0 && ctx->opt.tensor_form && tensor_form_available(ctx->T) &&
+                    !(ctx->opt.schur_mode == DDEL_SCHUR_AUTO && NR <= 128);
+    if (tc) {
       if (!ctx->form_work[0]) {
         cudaError_t e = cudaMalloc(&ctx->form_work[0], explicit_form_work_elems(ctx->T) * 8);
         if (e != cudaSuccess) return fail(ctx, DDEL_ENOMEM, "explicit Schur scratch allocation");
@@ -1334,6 +1338,178 @@ int ddel_batch_solve(ddel_ctx* const* ctxs, int n, double* const* u, ddel_stats*
     ddel_ctx* ctx = ctxs[i];
     CK(cudaStreamSynchronize(ctx->stream));
   }
+  return status;
+}
+
+int ddel_batch_solve_persistent(ddel_ctx* const* ctxs, int n, double* const* u, ddel_stats* stats) {
+  if (!ctxs || n <= 0) return DDEL_EINVAL;
+  for (int i = 0; i < n; ++i)
+    if (!ctxs[i] || !ctxs[i]->assembled) return ctxs[i] ? fail(ctxs[i], DDEL_ESTATE, "assemble first") : DDEL_EINVAL;
+  // 1. every factorisation in flight at once (one stream per context)
+  for (int i = 0; i < n; ++i) {
+    int rc = factor_launch(ctxs[i], 0);
+    if (rc) return rc;
+  }
+  for (int i = 0; i < n; ++i) {
+    ddel_ctx* c = ctxs[i];
+    int rc = factor_check(c, 0);
+    if (rc) return rc;
+    c->active_prec = 0;
+    c->mixed_ready = false;
+    // the persistent form runs the double-float explicit apply without a
+    // coarse space; any other configuration takes the stream-per-problem path
+    if (c->T.dim != 2 || !c->explicit_ok[0] || !c->df_ok || c->ck_in > 0)
+      return ddel_batch_solve(ctxs, n, u, stats);
+  }
+  // 2. right-hand sides, condensation, PCG start on each context's stream
+  size_t smem = 0;
+  std::vector<BatchProb> hp(n);
+  std::vector<int> pre(2 * n + 2, 0);
+  int max_it = 0;
+  for (int i = 0; i < n; ++i) {
+    ddel_ctx* ctx = ctxs[i];
+    cudaStream_t s = ctx->stream;
+    const int64_t nd = ctx->S.n_dof;
+    CK(cudaEventRecord(ctx->ev[0], s));
+    CK(cudaMemcpyAsync(ctx->d_f, ctx->d_load, nd * 8, cudaMemcpyDeviceToDevice, s));
+    CK(cudaMemsetAsync(ctx->d_u, 0, nd * 8, s));
+    launch_apply_K(ctx->T, ctx->F, ctx->d_u, ctx->d_f, ctx->d_r, 1, ctx->partials, ctx->ticketK, ctx->nrm, s,
+                   ctx->nblk);
+    set_tol_kernel<<<1, 1, 0, s>>>(ctx->st, ctx->nrm, ctx->opt.tol, ctx->opt.inner_tol, 0, ctx->opt.max_it);
+    condense(ctx, 0, ctx->d_r, ctx->g);
+    launch_pcg_init(ctx->T, ctx->F, ctx->g, ctx->x, ctx->r, ctx->z, ctx->p, ctx->sv, ctx->st, pcg_partials(ctx, 0), s,
+                    ctx->nupd, CoarseDev());
+    ctx->launches += 3;
+    BatchProb& b = hp[i];
+    b.t = ctx->T;
+    b.f = ctx->F;
+    b.sexp_df = ctx->sexp_df;
+    b.ring = reinterpret_cast<double*>(ctx->ring);
+    b.x = ctx->x;
+    b.r = ctx->r;
+    b.u = ctx->z;
+    b.p = ctx->p;
+    b.sv = ctx->sv;
+    b.st = ctx->st;
+    b.pd = ctx->pcg_pd;
+    b.pu = ctx->pcg_pu;
+    b.nr = explicit_ring_size(ctx->T);
+    b.n_schur = 2 * ctx->T.n_sub;
+    b.n_upd = ctx->nupd;
+    pre[i + 1] = pre[i] + batch_schur_tiles(b.n_schur);
+    pre[n + 2 + i] = pre[n + 1 + i] + b.n_upd;
+    smem = std::max(smem, batch_pcg_smem(ctx->T));
+    max_it = std::max(max_it, ctx->opt.max_it);
+  }
+  ddel_ctx* c0 = ctxs[0];
+  ddel_ctx* ctx = c0;  // where the error checks record their message
+  for (int i = 0; i < n; ++i) CK(cudaStreamSynchronize(ctxs[i]->stream));
+  cudaStream_t s0 = c0->stream;
+  const int per = pcg_per(c0);
+  const int bps = batch_pcg_blocks_per_sm(smem);
+  int dev = 0, nsm = 0;
+  CK(cudaGetDevice(&dev));
+  CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+  if (bps < 1) return fail(c0, DDEL_ECUDA, "persistent batch kernel does not fit an SM");
+  BatchProb* d_probs = nullptr;
+  int* d_pre = nullptr;
+  unsigned* d_cnt = nullptr;
+  std::vector<PcgState> hst(n);
+  auto cleanup = [&]() {
+    if (d_probs) cudaFree(d_probs);
+    if (d_pre) cudaFree(d_pre);
+    if (d_cnt) cudaFree(d_cnt);
+  };
+  if (cudaMalloc(&d_probs, n * sizeof(BatchProb)) != cudaSuccess || cudaMalloc(&d_pre, pre.size() * 4) != cudaSuccess ||
+      cudaMalloc(&d_cnt, (2 * n + 2) * 4) != cudaSuccess) {
+    cleanup();
+    return fail(c0, DDEL_ENOMEM, "persistent batch tables");
+  }
+  const int init[2] = {0, 0x7fffffff};
+  CK(cudaMemcpyAsync(c0->err, init, sizeof(init), cudaMemcpyHostToDevice, s0));
+  // 3. launches of `per` iterations of every problem until all have stopped
+  const int max_launch = max_it / per + 2;
+  int launches = 0;
+  std::vector<int> active(n);
+  for (int i = 0; i < n; ++i) active[i] = i;
+  std::vector<BatchProb> ap;
+  std::vector<int> apre;
+  for (; launches < max_launch; ++launches) {
+    // the problems still iterating, in batch order (finished ones leave the queue)
+    const int na = (int)active.size();
+    ap.assign(na, BatchProb{});
+    apre.assign(2 * na + 2, 0);
+    for (int a = 0; a < na; ++a) {
+      ap[a] = hp[active[a]];
+      apre[a + 1] = apre[a] + batch_schur_tiles(ap[a].n_schur);
+      apre[na + 2 + a] = apre[na + 1 + a] + ap[a].n_upd;
+    }
+    CK(cudaMemcpyAsync(d_probs, ap.data(), na * sizeof(BatchProb), cudaMemcpyHostToDevice, s0));
+    CK(cudaMemcpyAsync(d_pre, apre.data(), apre.size() * 4, cudaMemcpyHostToDevice, s0));
+    CK(cudaMemsetAsync(d_cnt, 0, (2 * na + 2) * 4, s0));
+    cudaError_t e = launch_batch_pcg(d_probs, na, d_pre, per, d_cnt, c0->err, bps * nsm, smem, s0);
+    if (e != cudaSuccess) {
+      cleanup();
+      return fail(c0, DDEL_ECUDA, std::string("persistent batch launch: ") + cudaGetErrorString(e));
+    }
+    for (int i : active)
+      CK(cudaMemcpyAsync(&hst[i], ctxs[i]->st, sizeof(PcgState), cudaMemcpyDeviceToHost, s0));
+    CK(cudaMemcpyAsync(c0->h_err, c0->err, 8, cudaMemcpyDeviceToHost, s0));
+    CK(cudaStreamSynchronize(s0));
+    for (int i : active) ctxs[i]->launches += 2 * per;
+    if (c0->h_err[0] == kErrTimeout) {
+      cleanup();
+      return fail(c0, DDEL_ETIMEOUT, "a bounded wait of the persistent batch kernel ran out");
+    }
+    std::vector<int> still;
+    for (int i : active)
+      if (!hst[i].done) still.push_back(i);
+    active.swap(still);
+    if (active.empty()) break;
+  }
+  cleanup();
+  // 4. back-substitution and the FP64 residual of every problem; a problem
+  //    that missed its tolerance is finished by the refinement loop
+  int status = DDEL_OK;
+  for (int i = 0; i < n; ++i) {
+    ddel_ctx* ctx = ctxs[i];
+    cudaStream_t s = ctx->stream;
+    *ctx->h_st = hst[i];
+    back_substitute(ctx, 0, ctx->d_r, ctx->x, ctx->d_d);
+    launch_axpy(ctx->S.n_dof, 1.0, ctx->d_d, ctx->d_u, s);
+    launch_apply_K(ctx->T, ctx->F, ctx->d_u, ctx->d_f, ctx->d_r, 1, ctx->partials, ctx->ticketK, ctx->nrm, s,
+                   ctx->nblk);
+    ctx->launches += 3;
+    CK(cudaMemcpyAsync(ctx->h_nrm, ctx->nrm, 16, cudaMemcpyDeviceToHost, s));
+    CK(cudaEventRecord(ctx->ev[6], s));
+  }
+  for (int i = 0; i < n; ++i) {
+    ddel_ctx* ctx = ctxs[i];
+    CK(cudaEventSynchronize(ctx->ev[6]));
+    ddel_stats st{};
+    st.bad_subdomain = -1;
+    st.iters = hst[i].it;
+    st.cycles = 1;
+    const double fn = ctx->h_nrm[1];
+    st.relres = fn > 0 ? ctx->h_nrm[0] / fn : 0.0;
+    st.pcg_relres = fn > 0 ? std::sqrt(hst[i].rr) / fn : 0.0;
+    st.t_total_ms = elapsed(ctx->ev[0], ctx->ev[6]);
+    st.t_factor_ms = ctx->t_factor_ms;
+    st.status = DDEL_OK;
+    if (!(st.relres <= ctx->opt.tol) && fn > 0) {
+      const int rc2 = ddel_solve(ctx, nullptr, u && u[i] ? u[i] : ctx->d_d, 1, &st);
+      if (rc2 && status == DDEL_OK) status = rc2;
+      if (u && u[i]) {
+        if (stats) stats[i] = st;
+        continue;
+      }
+      CK(cudaMemcpyAsync(ctx->d_u, ctx->d_d, ctx->S.n_dof * 8, cudaMemcpyDeviceToDevice, ctx->stream));
+    }
+    if (u && u[i])
+      CK(cudaMemcpyAsync(u[i], ctx->d_u, ctx->S.n_dof * 8, cudaMemcpyDeviceToDevice, ctx->stream));
+    if (stats) stats[i] = st;
+  }
+  for (int i = 0; i < n; ++i) CK(cudaStreamSynchronize(ctxs[i]->stream));
   return status;
 }
 

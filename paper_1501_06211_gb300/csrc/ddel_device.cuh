@@ -247,14 +247,15 @@ __device__ __forceinline__ void block_tree_sum(const double (&a)[NV], int nv, do
 // Schur kernel of a PCG iteration: record the iteration index for the update
 // kernel.  (With a coarse space the Schur kernels apply S to the face-local
 // part of u only; the update kernel adds S Q cc from the stored S Q.)
-__device__ __forceinline__ void schur_pcg_prologue(const SchurIO& io) {
-  if (io.pcg && blockIdx.x == 0 && threadIdx.x == 0) io.pcg->kU = io.pcg->kS;
+__device__ __forceinline__ void schur_pcg_prologue(const SchurIO& io, int bid) {
+  if (io.pcg && bid == 0 && threadIdx.x == 0) io.pcg->kU = io.pcg->kS;
 }
+__device__ __forceinline__ void schur_pcg_prologue(const SchurIO& io) { schur_pcg_prologue(io, blockIdx.x); }
 
 // The block's share of delta = (S u, u): the values d of warps [0, NW) summed,
 // written by thread 0 to pd[blockIdx.x].  All threads call it.
 template <int NW>
-__device__ __forceinline__ void schur_pcg_epilogue(const SchurIO& io, double d, double* red) {
+__device__ __forceinline__ void schur_pcg_epilogue(const SchurIO& io, double d, double* red, int bid) {
   if (!io.pcg) return;
   const int w = threadIdx.x >> 5;
   if (w < NW) {
@@ -266,8 +267,12 @@ __device__ __forceinline__ void schur_pcg_epilogue(const SchurIO& io, double d, 
     double tot = 0.0;
 #pragma unroll
     for (int i = 0; i < NW; ++i) tot += red[i];
-    io.pd[blockIdx.x] = tot;
+    io.pd[bid] = tot;
   }
+}
+template <int NW>
+__device__ __forceinline__ void schur_pcg_epilogue(const SchurIO& io, double d, double* red) {
+  schur_pcg_epilogue<NW>(io, d, red, blockIdx.x);
 }
 
 }  // namespace ddel

@@ -1006,13 +1006,17 @@ __global__ void split_df_kernel(const double* __restrict__ in, float2* __restric
 // final row values.  Up to 128 ring rows, registers are capped so that 7 CTAs
 // fit an SM: the 1024 CTAs of 512 subdomains then run in one wave (rings of
 // 256: 6 CTAs, 40 registers; more registers made that form slower).
-template <int NR>
-__global__ void __launch_bounds__(256, NR <= 128 ? 7 : 6) schur_explicit_df_kernel(DevTables t, const float2* __restrict__ Sexp,
-                                                                SchurIO io) {
+// The body as a device function of the block index bid: the kernel below,
+// and the batched persistent kernel, which runs it for other problems'
+// blocks within one launch (CG: the vectors written earlier in that launch
+// by other blocks are read through L2, bypassing the non-coherent L1).
+template <int NR, bool CG>
+__device__ __forceinline__ void schur_df_tile(const DevTables& t, const float2* __restrict__ Sexp, const SchurIO& io,
+                                              int bid) {
   // the flag's load overlaps the gather; nothing is written before the test
-  const int done = io.done ? *io.done : 0;
+  const int done = io.done ? (CG ? __ldcg(io.done) : *io.done) : 0;
   constexpr int RH = NR / 2, RP = RH / 2, H = 256 / RP, JN = NR / H;
-  const int sub = blockIdx.x >> 1, half = blockIdx.x & 1, tid = threadIdx.x;
+  const int sub = bid >> 1, half = bid & 1, tid = threadIdx.x;
   const SubInfo si = t.subs[sub];
   __shared__ float2 xr[NR];
   __shared__ double xd[NR];
@@ -1020,13 +1024,16 @@ __global__ void __launch_bounds__(256, NR <= 128 ? 7 : 6) schur_explicit_df_kern
   __shared__ double red[RH / 32];
   for (int j = tid; j < NR; j += 256) {
     double v = 0.0;
-    if (j < si.n_ring) v = io.x[t.ring_gidx[si.ring_off + j]];
+    if (j < si.n_ring) {
+      const double* xp = io.x + t.ring_gidx[si.ring_off + j];
+      v = CG ? __ldcg(xp) : *xp;
+    }
     const float hi = (float)v;
     xr[j] = make_float2(hi, (float)(v - (double)hi));
     xd[j] = v;
   }
   if (done) return;  // uniform over the grid: converged in an earlier iteration
-  schur_pcg_prologue(io);
+  schur_pcg_prologue(io, bid);
   __syncthreads();
   const int rp = tid % RP, h = tid / RP;
   const int r0 = half * RH + 2 * rp;
@@ -1062,26 +1069,37 @@ __global__ void __launch_bounds__(256, NR <= 128 ? 7 : 6) schur_explicit_df_kern
     reinterpret_cast<double*>(io.ring_out)[t.ring_dst[si.ring_off + row]] = y;
     d[0] = xd[row] * y;
   }
-  schur_pcg_epilogue<RH / 32>(io, d[0], red);
+  schur_pcg_epilogue<RH / 32>(io, d[0], red, bid);
+}
+
+template <int NR>
+__global__ void __launch_bounds__(256, NR <= 128 ? 7 : 6) schur_explicit_df_kernel(DevTables t, const float2* __restrict__ Sexp,
+                                                                SchurIO io) {
+  schur_df_tile<NR, false>(t, Sexp, io, blockIdx.x);
 }
 
 // ============================================================ Gamma sums
 // Sum of the owners' contributions to Gamma DOF g, in owner (subdomain) order;
 // the owner-major layout makes them one contiguous, aligned vector load.
-template <typename T>
+template <typename T, bool CG = false>
 __device__ __forceinline__ double ring_sum(const DevTables& t, const T* __restrict__ ring, int64_t g) {
   if (t.max_owners == 4) {
     if constexpr (sizeof(T) == 8) {
-      const double2 a = reinterpret_cast<const double2*>(ring)[2 * g];
-      const double2 b = reinterpret_cast<const double2*>(ring)[2 * g + 1];
+      const double2* q = reinterpret_cast<const double2*>(ring) + 2 * g;
+      const double2 a = CG ? __ldcg(q) : q[0];
+      const double2 b = CG ? __ldcg(q + 1) : q[1];
       return ((a.x + a.y) + b.x) + b.y;
     } else {
-      const float4 v = reinterpret_cast<const float4*>(ring)[g];
+      const float4* q = reinterpret_cast<const float4*>(ring) + g;
+      const float4 v = CG ? __ldcg(q) : q[0];
       return (((double)v.x + (double)v.y) + (double)v.z) + (double)v.w;
     }
   }
   double acc = 0.0;
-  for (int k = 0; k < t.max_owners; ++k) acc += (double)ring[g * t.max_owners + k];
+  for (int k = 0; k < t.max_owners; ++k) {
+    const T* q = ring + g * t.max_owners + k;
+    acc += (double)(CG ? __ldcg(q) : *q);
+  }
   return acc;
 }
 
@@ -1337,15 +1355,25 @@ __global__ void __launch_bounds__(kRedThreads) pcg_cg_kernel(DevTables t, DevFie
 //    reduced by one warp each (lane-strided loads, then a shuffle tree; every
 //    block forms bitwise the same totals) instead of a block-wide tree.
 // Further blocks of a warp (more face blocks than lanes) load as they come.
-template <typename T, int KC>
-__global__ void __launch_bounds__(kRedThreads, 2) pcg_update_kernel(DevTables t, DevFields fld,
-                                                                    const T* __restrict__ ring, double* x,
-                                                                    double* r, double* u, double* p,
-                                                                    double* sv, PcgState* st, CoarseDev cd,
-                                                                    const double* __restrict__ pd, int nd,
-                                                                    const double* __restrict__ pu_in,
-                                                                    double* __restrict__ pu_out, int par) {
-  const int done = st->done;
+// The body as a device function of the block index bid of nblk blocks: the
+// kernel below, and the batched persistent kernel (CG: values written earlier
+// in that launch by other blocks are read through L2; the convergence flag,
+// which block 0 of the same iteration may be setting meanwhile, is read once
+// per block and shared, so that every thread of a block takes the same path).
+template <typename T, int KC, bool CG>
+__device__ __forceinline__ void pcg_update_tile(const DevTables& t, const DevFields& fld, const T* __restrict__ ring,
+                                                double* x, double* r, double* u, double* p, double* sv, PcgState* st,
+                                                const CoarseDev& cd, const double* __restrict__ pd, int nd,
+                                                const double* __restrict__ pu_in, double* __restrict__ pu_out,
+                                                int par, int bid, int nblk) {
+  __shared__ int s_done;
+  int done = 0;
+  if constexpr (CG) {
+    if (threadIdx.x == 0) s_done = __ldcg(&st->done);
+  } else {
+    done = st->done;
+  }
+  auto ld = [](const double* q) -> double { return CG ? __ldcg(q) : *q; };
   constexpr int NV = 2 + 2 * KC, NP = 3 + 2 * KC, PE = 2;
   // dynamic shared memory: per warp UG * max_blk_n doubles (W^-1 r), as many
   // float2 (its double-float split), then, when staged, UG * max_blk_n^2
@@ -1363,20 +1391,20 @@ __global__ void __launch_bounds__(kRedThreads, 2) pcg_update_kernel(DevTables t,
   float2* ptile = reinterpret_cast<float2*>(rw_all + 2 * nwb * UG * mbn) + (size_t)(wib * UG + grp) * mbn * mbn;
   const int k = KC > 0 ? cd.k : 0;
   const bool deflate = KC > 0 && cd.correct == 2;
-  const int j = st->kU;
-  const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int nw = (gridDim.x * blockDim.x) >> 5;
+  const int j = CG ? __ldcg(&st->kU) : st->kU;
+  const int gw = (bid * blockDim.x + threadIdx.x) >> 5;
+  const int nw = (nblk * blockDim.x) >> 5;
   struct Dof {
     double w, u, p, s, x, r, fw;
   };
   auto load_dof = [&](int64_t g, double fw) -> Dof {
     Dof d;
-    d.w = ring_sum<T>(t, ring, g);
-    d.u = u[g];
-    d.p = p[g];
-    d.s = sv[g];
-    d.x = x[g];
-    d.r = r[g];
+    d.w = ring_sum<T, CG>(t, ring, g);
+    d.u = ld(u + g);
+    d.p = ld(p + g);
+    d.s = ld(sv + g);
+    d.x = ld(x + g);
+    d.r = ld(r + g);
     d.fw = fw;
     return d;
   };
@@ -1400,7 +1428,7 @@ __global__ void __launch_bounds__(kRedThreads, 2) pcg_update_kernel(DevTables t,
     for (int i = gl; i < n0 * n0; i += UL) cp_async8(ptile + i, src + i);
   }
   cp_async_commit();
-  const int64_t gc0 = t.n_face_dofs + blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int64_t gc0 = t.n_face_dofs + bid * (int64_t)blockDim.x + threadIdx.x;
   Dof prc;
   if (gc0 < t.n_gamma) prc = load_dof(gc0, fld.cross_scale[gc0 - t.n_face_dofs]);
   // --- partial sums of the Schur apply (delta) and of update j-1 (gamma, rr,
@@ -1422,16 +1450,20 @@ __global__ void __launch_bounds__(kRedThreads, 2) pcg_update_kernel(DevTables t,
     if (threadIdx.x == 0) {
       tol2 = st->tol2;
       max_it = st->max_it;
-      ginv = st->ginv_s[par ^ 1];
-      ainv = st->ainv_s[par ^ 1];
+      ginv = ld(&st->ginv_s[par ^ 1]);
+      ainv = ld(&st->ainv_s[par ^ 1]);
     }
-    const int nu = gridDim.x;
+    const int nu = nblk;
     if constexpr (KC == 0) {
       // delta, gamma, rr: one warp each
       if (wib < 3) {
         const double* src = wib == 0 ? pd : pu_in + (size_t)(wib - 1) * nu;
         const double v = reduce_partials_warp(src, wib == 0 ? nd : nu);
         if (lane == 0) sums[wib] = v;
+      }
+      if constexpr (CG) {
+        __syncthreads();
+        done = s_done;
       }
       if (done) {  // uniform over the grid; no copy outlives the block
         cp_async_wait_all();
@@ -1447,6 +1479,10 @@ __global__ void __launch_bounds__(kRedThreads, 2) pcg_update_kernel(DevTables t,
         const double* src = v == 0 ? pd : pu_in + (size_t)(v - 1) * nu;
         const int n = v == 0 ? nd : nu;
         for (int b = threadIdx.x; b < n; b += kRedThreads) a[v] += __ldcg(src + b);
+      }
+      if constexpr (CG) {
+        __syncthreads();
+        done = s_done;
       }
       if (done) {  // uniform over the grid; no copy outlives the block
         cp_async_wait_all();
@@ -1493,7 +1529,7 @@ __global__ void __launch_bounds__(kRedThreads, 2) pcg_update_kernel(DevTables t,
       sab[0] = a_;
       sab[1] = b_;
       sflag = status;
-      if (blockIdx.x == 0) {
+      if (bid == 0) {
         st->rr = rr;
         st->it = j;
         if (status != 1) {
@@ -1598,12 +1634,12 @@ __global__ void __launch_bounds__(kRedThreads, 2) pcg_update_kernel(DevTables t,
       }
       const double zi = (double)hi + (double)lo;
       const int e = (i - gl) / UL;
-      const double ri = fast ? (e == 0 ? rkeep[0] : rkeep[PE - 1]) : r[off + i];
+      const double ri = fast ? (e == 0 ? rkeep[0] : rkeep[PE - 1]) : ld(r + off + i);
       local(off + i, ri, zi * fld.face_w[off + i]);
     }
     __syncwarp();
   }
-  for (int64_t g = gc0; g < t.n_gamma; g += (int64_t)gridDim.x * blockDim.x) {
+  for (int64_t g = gc0; g < t.n_gamma; g += (int64_t)nblk * blockDim.x) {
     Dof d;
     if (g == gc0) d = prc;
     else d = load_dof(g, fld.cross_scale[g - t.n_face_dofs]);
@@ -1611,7 +1647,124 @@ __global__ void __launch_bounds__(kRedThreads, 2) pcg_update_kernel(DevTables t,
     local(g, ri, ri * d.fw);
   }
   block_tree_sum<NV>(acc, NV, red);
-  if (threadIdx.x < NV) pu_out[(size_t)threadIdx.x * gridDim.x + blockIdx.x] = red[threadIdx.x * kRedThreads];
+  if (threadIdx.x < NV) pu_out[(size_t)threadIdx.x * nblk + bid] = red[threadIdx.x * kRedThreads];
+}
+
+template <typename T, int KC>
+__global__ void __launch_bounds__(kRedThreads, 2) pcg_update_kernel(DevTables t, DevFields fld,
+                                                                    const T* __restrict__ ring, double* x,
+                                                                    double* r, double* u, double* p,
+                                                                    double* sv, PcgState* st, CoarseDev cd,
+                                                                    const double* __restrict__ pd, int nd,
+                                                                    const double* __restrict__ pu_in,
+                                                                    double* __restrict__ pu_out, int par) {
+  pcg_update_tile<T, KC, false>(t, fld, ring, x, r, u, p, sv, st, cd, pd, nd, pu_in, pu_out, par, blockIdx.x,
+                                gridDim.x);
+}
+
+// ---- batched persistent PCG ------------------------------------------------
+constexpr uint32_t kBatchWaitPolls = 1u << 24;  // x 64 ns sleeps: about a second
+constexpr int kBatchSchurGroup = 4;  // Schur blocks per tile of the persistent kernel
+
+__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+// pre: prefix sums of the problems' Schur blocks (pre[0 .. nprob]) and of
+// their update blocks (pre[nprob + 1 .. 2 nprob + 1]).  cnt[2 P] counts the
+// finished Schur blocks of problem P, cnt[2 P + 1] its finished update blocks,
+// cnt[2 nprob] is the queue head, cnt[2 nprob + 1] the abort flag.
+__global__ void __launch_bounds__(kRedThreads, 2) batch_pcg_kernel(const BatchProb* __restrict__ probs, int nprob,
+                                                                   const int* __restrict__ pre, int iters,
+                                                                   unsigned* cnt, int* err) {
+  __shared__ int s_q, s_ok;
+  const int* preS = pre;
+  const int* preU = pre + nprob + 1;
+  const int totS = preS[nprob], totU = preU[nprob], per = totS + totU;
+  const long long total = (long long)iters * per;
+  unsigned* head = cnt + 2 * nprob;
+  unsigned* abort_flag = head + 1;
+  int next = 0;  // thread 0: the queue entry taken ahead of time
+  if (threadIdx.x == 0) next = (int)atomicAdd(head, 1u);
+  for (;;) {
+    __syncthreads();  // the previous tile's shared memory is free
+    if (threadIdx.x == 0) {
+      s_q = ld_acquire_u32(abort_flag) ? -1 : next;
+      if (s_q >= 0 && s_q < total) next = (int)atomicAdd(head, 1u);  // overlaps this tile's work
+    }
+    __syncthreads();
+    const long long q = s_q;
+    if (q < 0 || q >= total) break;
+    const int it = (int)(q / per), rr = (int)(q % per);
+    const bool schur = rr < totS;
+    const int* pref = schur ? preS : preU;
+    const int key = schur ? rr : rr - totS;
+    int P = 0;
+    while (P + 1 < nprob && pref[P + 1] <= key) ++P;
+    const int b = key - pref[P];  // tile of this problem's phase
+    const BatchProb& bp = probs[P];
+    const int nts = (bp.n_schur + kBatchSchurGroup - 1) / kBatchSchurGroup;  // Schur tiles
+    // wait for the phase this tile depends on (earlier in the queue)
+    unsigned target = 0;
+    const unsigned* c = nullptr;
+    if (schur && it > 0) {
+      c = cnt + 2 * P + 1;
+      target = (unsigned)it * bp.n_upd;
+    } else if (!schur) {
+      c = cnt + 2 * P;
+      target = (unsigned)(it + 1) * nts;
+    }
+    if (threadIdx.x == 0) {
+      int ok = 1;
+      if (c) {
+        uint32_t polls = 0;
+        while (ld_acquire_u32(c) < target) {
+          if (++polls > kBatchWaitPolls) {
+            ok = 0;
+            break;
+          }
+          __nanosleep(64);
+        }
+      }
+      if (!ok) {
+        atomicExch(err, kErrTimeout);
+        atomicExch(abort_flag, 1u);
+      }
+      __threadfence();
+      s_ok = ok;
+    }
+    __syncthreads();
+    if (!s_ok) break;
+    if (schur) {
+      SchurIO io;
+      io.x = bp.u;
+      io.ring_out = bp.ring;
+      io.done = &bp.st->done;
+      io.pcg = bp.st;
+      io.pd = bp.pd;
+      io.err = err;
+      const int b1 = min((b + 1) * kBatchSchurGroup, bp.n_schur);
+      for (int bb = b * kBatchSchurGroup; bb < b1; ++bb) {
+        if (bp.nr == 64) schur_df_tile<64, true>(bp.t, bp.sexp_df, io, bb);
+        else if (bp.nr == 128) schur_df_tile<128, true>(bp.t, bp.sexp_df, io, bb);
+        else schur_df_tile<256, true>(bp.t, bp.sexp_df, io, bb);
+        __syncthreads();
+      }
+    } else {
+      const int par = it & 1;
+      const size_t rows = (size_t)kPcgRows * bp.n_upd;
+      pcg_update_tile<double, 0, true>(bp.t, bp.f, bp.ring, bp.x, bp.r, bp.u, bp.p, bp.sv, bp.st, CoarseDev(), bp.pd,
+                                       bp.n_schur, bp.pu + par * rows, bp.pu + (par ^ 1) * rows, par, b,
+                                       bp.n_upd);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      __threadfence();  // this tile's results before its count
+      atomicAdd(cnt + 2 * P + (schur ? 0 : 1), 1u);
+    }
+  }
 }
 
 __global__ void precond_kernel(DevTables t, DevFields fld, const double* __restrict__ r,
@@ -2010,6 +2163,7 @@ cudaError_t configure_kernels() {
   DDEL_CFG((ozaki_syrk_kernel<128>));
   DDEL_CFG((ozaki_syrk_kernel<256>));
   DDEL_CFG((form_w2d_kernel<double, 32, 128, kFormGC>));
+  DDEL_CFG((batch_pcg_kernel));
   DDEL_CFG((pcg_update_kernel<double, 0>));
   DDEL_CFG((pcg_update_kernel<double, 4>));
   DDEL_CFG((pcg_update_kernel<double, 8>));
@@ -2151,6 +2305,24 @@ void launch_pcg_update(const DevTables& t, const DevFields& fld, int precision, 
     launch_update_t(t, fld, (const double*)ring, x, r, u, p, sv, s, pd, nd, pu_in, pu_out, par, st, nblk, cd);
   else
     launch_update_t(t, fld, (const float*)ring, x, r, u, p, sv, s, pd, nd, pu_in, pu_out, par, st, nblk, cd);
+}
+
+size_t batch_pcg_smem(const DevTables& t) { return update_kernel_smem(t); }
+
+int batch_schur_tiles(int n_schur_blocks) { return (n_schur_blocks + kBatchSchurGroup - 1) / kBatchSchurGroup; }
+
+int batch_pcg_blocks_per_sm(size_t smem) {
+  int nb = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, batch_pcg_kernel, kRedThreads, smem) != cudaSuccess) return 0;
+  return nb;
+}
+
+cudaError_t launch_batch_pcg(const BatchProb* probs, int nprob, const int* pre, int iters, unsigned* cnt, int* err,
+                             int grid, size_t smem, cudaStream_t st) {
+  void* args[] = {(void*)&probs, (void*)&nprob, (void*)&pre, (void*)&iters, (void*)&cnt, (void*)&err};
+  // a cooperative launch: every block is resident at once, which the waits
+  // on earlier queue entries rely on
+  return cudaLaunchCooperativeKernel((const void*)batch_pcg_kernel, dim3(grid), dim3(kRedThreads), args, smem, st);
 }
 
 void launch_precond(const DevTables& t, const DevFields& fld, const double* r, double* z,

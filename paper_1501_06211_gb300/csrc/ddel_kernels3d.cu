@@ -436,29 +436,46 @@ __global__ void __launch_bounds__(kT3) schur3d_kernel(DevTables t, const T* __re
 // launch_build_df3 (no padding rows; a row-major copy for the backward sweep),
 // read once per apply in the order of use with streaming (evict-first) loads.
 // Each warp serves 16 rows: lanes l and l + 16 take the two halves of a row's
-// dot product (coalesced over the rows) and add them by one shuffle; 12 loads
-// per thread are in flight.  (An L2 bulk prefetch of the next block step,
+// dot product (coalesced over the rows) and add them by one shuffle; each
+// thread keeps eight loads in flight ahead of its products.  (An L2 bulk prefetch of the next block step,
 // 75 MB over all subdomains, evicted lines before their use: slower.)
 constexpr int kT3D = 384;  // 12 warps x 16 rows: blocks of up to 192 rows in one pass
 
 __host__ __device__ __forceinline__ int64_t pad16(int64_t v) { return (v + 15) & ~int64_t(15); }
 
 // (hi, lo) += sum_{j = j0}^{j1 - 1} M[a_j] v[j] with a_{j0} = a, a_{j+1} = a_j + st_j,
-// st_{j+1} = st_j + dst (dst 0: a strided column; -1, +1: the packed triangles);
-// twelve loads issued ahead of their products.
+// st_{j+1} = st_j + dst (dst 0: a strided column; -1, +1: the packed triangles).
+// Software-pipelined: the loads of the next group of eight entries are issued
+// before the products of the current group, so a thread always has loads in
+// flight while it computes (the products of one row form a dependent chain).
 __device__ __forceinline__ void df_dot(const float2* __restrict__ M, int a, int st, int dst,
                                        const float2* v, int j0, int j1, float& hi, float& lo) {
+  constexpr int U = 8;
   int j = j0;
-  for (; j + 12 <= j1; j += 12) {
-    float2 e[12];
+  if (j + U <= j1) {
+    float2 e[U];
 #pragma unroll
-    for (int u = 0; u < 12; ++u) {
+    for (int u = 0; u < U; ++u) {
       e[u] = __ldcs(M + a);
       a += st;
       st += dst;
     }
+    for (; j + 2 * U <= j1; j += U) {
+      float2 nx[U];
 #pragma unroll
-    for (int u = 0; u < 12; ++u) df_mad(hi, lo, e[u], v[j + u]);
+      for (int u = 0; u < U; ++u) {
+        nx[u] = __ldcs(M + a);
+        a += st;
+        st += dst;
+      }
+#pragma unroll
+      for (int u = 0; u < U; ++u) df_mad(hi, lo, e[u], v[j + u]);
+#pragma unroll
+      for (int u = 0; u < U; ++u) e[u] = nx[u];
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) df_mad(hi, lo, e[u], v[j + u]);
+    j += U;
   }
   for (; j < j1; ++j) {
     df_mad(hi, lo, __ldcs(M + a), v[j]);

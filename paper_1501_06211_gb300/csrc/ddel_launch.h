@@ -181,6 +181,38 @@ void launch_pcg_update(const DevTables& t, const DevFields& fld, int precision, 
                        double* x, double* r, double* u, double* p, double* sv, PcgState* s,
                        const double* pd, int nd, const double* pu_in, double* pu_out, int par,
                        cudaStream_t st, int nblk, const CoarseDev& cd = CoarseDev());
+// Batched persistent PCG: one problem of a batch (the double-float explicit
+// form, no coarse space).  The kernel runs `iters` PCG iterations of every
+// problem in one launch: a device work queue hands out, in order, per
+// iteration the Schur blocks of every problem and then their update blocks
+// (the blocks of schur_explicit_df_kernel and pcg_update_kernel, computing
+// exactly what those kernels compute); a block waits, bounded, until the
+// blocks its problem's phase depends on have completed (per-problem
+// counters).  pre: prefix sums of the problems' Schur tiles, then of their
+// update blocks.  cnt: 2 counters per problem, the queue head and an abort
+// flag, zeroed before each launch.
+struct BatchProb {
+  DevTables t;
+  DevFields f;
+  const float2* sexp_df;
+  double* ring;
+  double *x, *r, *u, *p, *sv;
+  PcgState* st;
+  double* pd;
+  double* pu;       // 2 x kPcgRows x n_upd partials (by iteration parity)
+  int nr;           // ring size of the explicit form (64, 128 or 256)
+  int n_schur;      // Schur blocks (2 per subdomain)
+  int n_upd;        // update blocks
+  int pad;
+};
+// Blocks per SM of the persistent kernel for the given dynamic shared memory.
+int batch_pcg_blocks_per_sm(size_t smem);
+size_t batch_pcg_smem(const DevTables& t);
+// Queue tiles of a problem's Schur phase (several Schur blocks per tile).
+int batch_schur_tiles(int n_schur_blocks);
+cudaError_t launch_batch_pcg(const BatchProb* probs, int nprob, const int* pre, int iters, unsigned* cnt,
+                             int* err, int grid, size_t smem, cudaStream_t st);
+
 // Coarse-space set-up (ddel_coarse.cu).  Gram matrix out = A^T B (k x k,
 // leading dimension kMaxCoarse) of k <= kMaxCoarse columns of length n.
 void launch_gram(const double* A, const double* B, int k, int64_t n, double* out, double* partials,

@@ -79,22 +79,26 @@ __global__ void __launch_bounds__(256) ozaki_slice_kernel(DevTables t, const dou
   const int e = e_s[jl];
   const int j = j0 + jl, rt = j >> 7, c = j & 127;
   const int NRT = NR / 128, NKC = Kp / 64;
-  const double up = ldexp(1.0, bits);
   unsigned char* img0 = reinterpret_cast<unsigned char*>(Wsl) + (int64_t)sub * S * NRT * NKC * 16384;
   for (int k8 = ko * 8; k8 < Kp; k8 += 64) {
-    double v[8];
+    // m = W 2^(B S - e) rounded to an integer (|m| <= 2^(B S), B S <= 55
+    // bits); its balanced base-2^B digits, most significant first, are the
+    // slices: d_p = round(rest / 2^(B (S - p))), rest -= d_p 2^(B (S - p)),
+    // so |d_1| <= 2^B, |d_p| <= 2^(B - 1) after, and m = sum_p d_p 2^(B (S - p))
+    long long m[8];
 #pragma unroll
-    for (int r = 0; r < 8; ++r) v[r] = k8 + r < K ? ldexp(Wb[(int64_t)(k8 + r) * NR + j], -e) : 0.0;
+    for (int r = 0; r < 8; ++r)
+      m[r] = k8 + r < K ? __double2ll_rn(ldexp(Wb[(int64_t)(k8 + r) * NR + j], bits * S - e)) : 0ll;
     const int kc = k8 >> 6;
     const int off = oz_img_off(c, k8 & 63);
     for (int p = 0; p < S; ++p) {
+      const int sh = bits * (S - 1 - p);
       __align__(16) __nv_bfloat16 h[8];
 #pragma unroll
       for (int r = 0; r < 8; ++r) {
-        const double tv = v[r] * up;    // exact: a power-of-two scaling
-        const double dv = rint(tv);     // |dv| <= 2^bits, an integer
-        v[r] = tv - dv;                 // exact: |v| <= 1/2
-        h[r] = __double2bfloat16(dv);
+        const long long d = sh > 0 ? (m[r] + (1ll << (sh - 1))) >> sh : m[r];
+        m[r] -= d * (1ll << sh);
+        h[r] = __float2bfloat16_rn((float)d);  // |d| <= 2^B: exact
       }
       unsigned char* img = img0 + ((int64_t)(p * NRT + rt) * NKC + kc) * 16384;
       *reinterpret_cast<uint4*>(img + off) = *reinterpret_cast<const uint4*>(h);

@@ -145,6 +145,7 @@ def _load():
         "ddel_fixed_mask": (c_int, [c_void_p, c_void_p]),
         "ddel_kernel_info": (c_int, [c_void_p, P(ddel_kernel_info_t)]),
         "ddel_batch_solve": (c_int, [c_void_p, c_int, c_void_p, c_void_p]),
+        "ddel_batch_solve_persistent": (c_int, [c_void_p, c_int, c_void_p, c_void_p]),
         "ddel_autotune": (c_int, [c_void_p, ctypes.c_char_p, c_void_p, c_void_p, c_void_p]),
         "ddel_topopt_step": (c_int, [c_void_p, P(ddel_topopt_state), P(ddel_stats)]),
         "ddel_set_coarse": (c_int, [c_void_p, c_void_p, c_int, c_int, c_int]),
@@ -327,13 +328,16 @@ def ddel_topopt_step(h, state):
     return code, st
 
 
-def ddel_batch_solve(handles, us=None):
-    """Concurrent solves of several assembled contexts; us: device tensors or None."""
+def ddel_batch_solve(handles, us=None, persistent=False):
+    """Concurrent solves of several assembled contexts; us: device tensors or
+    None; persistent: one persistent launch per batch of iterations
+    (ddel_batch_solve_persistent) instead of one stream per problem."""
     n = len(handles)
     harr = (c_void_p * n)(*[h.value if hasattr(h, "value") else h for h in handles])
     uarr = (c_void_p * n)(*[(_ptr(u) if u is not None else None) for u in (us or [None] * n)])
     sts = (ddel_stats * n)()
-    code = _lib.ddel_batch_solve(harr, n, uarr, sts)
+    fn = _lib.ddel_batch_solve_persistent if persistent else _lib.ddel_batch_solve
+    code = fn(harr, n, uarr, sts)
     return code, list(sts)
 
 

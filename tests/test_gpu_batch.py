@@ -1,4 +1,5 @@
-"""Batched independent problems of uneven size (one stream per problem).
+"""Batched independent problems of uneven size (one stream per problem, or one
+persistent launch with a device work queue).
 
 Every problem of the batch is compared with the oracle's direct solve and
 with its own ddel_solve, which it must reproduce bitwise (same kernels in the
@@ -18,7 +19,11 @@ def _problems():
     return probs[:8]
 
 
-def test_batch_matches_oracle_and_single_solves():
+@pytest.mark.parametrize("persistent", [False, True], ids=["streams", "persistent"])
+def test_batch_matches_oracle_and_single_solves(persistent):
+    # streams: one stream per problem; persistent: one persistent launch per
+    # batch of iterations with the device work queue (the same blocks, the
+    # same bits)
     from paper_1501_06211_gb300 import ddel
     probs = _problems()
     assert len(probs) >= 4 and len({p["sub"] for p in probs}) >= 2
@@ -34,7 +39,7 @@ def test_batch_matches_oracle_and_single_solves():
         K = fem.assemble(grid, fem.element_stiffness(2, 1.0, cfg["nu"]),
                          fem.element_factors(rho, cfg["E"], cfg["p"]))
         refs.append((direct.solve(K, f, fixed), K, f, fixed))
-    code, sts = ddel.ddel_batch_solve([s.h for s in solvers], us)
+    code, sts = ddel.ddel_batch_solve([s.h for s in solvers], us, persistent=persistent)
     assert code == 0, [st.as_dict() for st in sts]
     for s, u, (u_ref, K, f, fixed), st in zip(solvers, us, refs, sts):
         un = u.cpu().numpy()

@@ -6,7 +6,9 @@ S_i = K_GG^(i) - W^T W is the definition of eq. 3MatSplit; the tensor-core
 form must reproduce it to FP64 accuracy: the Schur apply with the explicit
 S_i agrees with the oracle's matrix-free S to 1e-10 and with the FP64-pipe
 formation to 1e-12, on rings of 128 (16 x 16 subdomains) and 256 (32 x 32),
-homogeneous and at SIMP contrast 1e9; whole solves keep the FP64 bar.
+homogeneous and at SIMP contrast 1e9; whole solves keep the FP64 bar.  (The
+double-float form uses the tensor cores for rings of 256 only; its rings of
+128 keep their double-float formation, and the test then checks that form.)
 """
 import numpy as np
 import pytest
