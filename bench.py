@@ -358,7 +358,8 @@ def pcg_iteration(ddel, run, roof):
 
 def learned_vs_plain(ddel, torch, workloads, stream, steps=100, skip=4):
     """Per-solve time of topology steps on the 256x128 MBB beam (V = 0.4,
-    r_min = 1.5, 100 Picard steps): plain PCG against coarse spaces from the
+    r_min = 1.5, 100 Picard steps): plain PCG against a warm start from the
+    previous Picard solution, against coarse spaces from the
     last Picard solutions (HISTORY, k = 8) and from those plus the online U-Net
     (CNN_HISTORY, 4 + 4 vectors, 4 Adam steps on the 8 newest observations per
     solve), and plain PCG to an adaptive tolerance.  Steps after the first
@@ -372,7 +373,7 @@ def learned_vs_plain(ddel, torch, workloads, stream, steps=100, skip=4):
            "picard_steps": steps, "timed_steps": steps - skip}
 
     def run(s, ts):
-        ms, its = [], []
+        ms, its, pcg, fac = [], [], [], []
         for k in range(steps):
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
@@ -383,13 +384,23 @@ def learned_vs_plain(ddel, torch, workloads, stream, steps=100, skip=4):
             if k >= skip:
                 ms.append(e0.elapsed_time(e1))
                 its.append(st.iters)
-        return {"ms_per_step": sum(ms) / len(ms), "iters_per_solve": sum(its) / len(its),
+                pcg.append(st.t_pcg_ms)
+                fac.append(st.t_factor_ms)
+        n = len(ms)
+        # where a step's time goes: the PCG iterations (with any coarse terms),
+        # the factorisation, and the rest (filter, assembly, condensation,
+        # back-substitution, coarse set-up, prediction, training, OC)
+        return {"ms_per_step": sum(ms) / n, "iters_per_solve": sum(its) / n,
+                "pcg_ms_per_step": sum(pcg) / n, "us_per_pcg_iteration": 1e3 * sum(pcg) / max(sum(its), 1),
+                "factor_ms_per_step": sum(fac) / n,
+                "other_ms_per_step": (sum(ms) - sum(pcg) - sum(fac)) / n,
                 "total_ms": sum(ms), "compliance": ts.compliance}
 
-    for name, lopt in (("plain", None),
-                       ("history8", dict(mode=ddel.DDEL_LEARN_HISTORY, k_history=8)),
-                       ("cnn+history4", dict(mode=ddel.DDEL_LEARN_CNN_HISTORY, k_history=4, train_steps=4, batch=8))):
-        s = ddel.Solver(cfg, stream=stream.cuda_stream, tol=1e-8, max_it=20000)
+    for name, lopt, x0 in (("plain", None, 0), ("warm", None, 1),
+                           ("history8", dict(mode=ddel.DDEL_LEARN_HISTORY, k_history=8), 0),
+                           ("cnn+history4", dict(mode=ddel.DDEL_LEARN_CNN_HISTORY, k_history=4, train_steps=4,
+                                                 batch=8), 0)):
+        s = ddel.Solver(cfg, stream=stream.cuda_stream, tol=1e-8, max_it=20000, x0_mode=x0)
         L = ddel.Learner(s, **lopt) if lopt else None
         rho = torch.full((ne,), cfg["v_frac"], dtype=torch.float64, device="cuda")
         ts = s.topopt_state(rho, cfg["v_frac"], r_min=1.5, move=0.2, learner=L)
@@ -406,7 +417,7 @@ def learned_vs_plain(ddel, torch, workloads, stream, steps=100, skip=4):
     res["adaptive_tol"] = run(s, ts)
     res["adaptive_tol"]["last_tol"] = ts.tol_used
     s.close()
-    for name in ("history8", "cnn+history4", "adaptive_tol"):
+    for name in ("warm", "history8", "cnn+history4", "adaptive_tol"):
         res[name]["speedup_vs_plain"] = res["plain"]["ms_per_step"] / res[name]["ms_per_step"]
         res[name]["iteration_ratio"] = res[name]["iters_per_solve"] / res["plain"]["iters_per_solve"]
         res[name]["net_gain_ms_per_step"] = res["plain"]["ms_per_step"] - res[name]["ms_per_step"]
@@ -562,11 +573,13 @@ def launches_per_step(s):
     return ddel.ddel_kernel_info(s.h)["launches_since_assemble"]
 
 
-# DRAM bytes (read + write) of one launch of schur_explicit_df_kernel<128> on
-# this workload, from one `ncu --set full --clock-control none` capture of the
-# kernel (cold L2, the kernel as built now: 7 CTAs per SM): 67.897088 MB read +
-# 0.246272 MB written.
-TRAFFIC = {"schur_explicit_df_kernel": 67897088 + 246272}
+# DRAM bytes (read + write) of one launch of the explicit Schur kernels on
+# this workload, each from one `ncu --set full --clock-control none` capture
+# (cold L2, the kernels as built now): schur_explicit_df_kernel<128> 67.897088
+# MB read + 0.246272 MB written; schur_explicit_f64_kernel<128> 67.895296 MB
+# read + 0.229120 MB written.
+TRAFFIC = {"schur_explicit_df_kernel": 67897088 + 246272,
+           "schur_explicit_f64_kernel": 67895296 + 229120}
 
 
 def kernel_roofline(ddel, s, stream, torch):

@@ -136,11 +136,13 @@ typedef struct {
                           iteration; IMPLICIT applies it by block substitution */
   int use_graph;       /* capture PCG iterations in a CUDA graph (1) */
   int check_every;     /* PCG iterations between host convergence checks (16) */
-  int tensor_form;     /* 1: form the FP64 local Schur complements with W^T W on the tensor
+  int tensor_form;     /* 1: form the local Schur complements with W^T W on the tensor
                           cores at FP64 accuracy (Ozaki splitting into BF16 slices, FP32
                           accumulation): rings of 128 and 256 in the EXPLICIT form, rings
-                          of 256 in the AUTO form (whose rings of 128 keep the faster
-                          double-float formation); 0: on the FP64 pipe (1) */
+                          of 256 in the AUTO form of FP64 (whose rings of 128 keep the
+                          faster double-float formation), and every ring of 128 or 256 in
+                          FP32 (W from the FP32 factors, S_i rounded once to FP32);
+                          0: on the FP64 / FP32 pipes (1) */
 } ddel_options;
 
 typedef struct {
@@ -310,14 +312,17 @@ int ddel_batch_solve_persistent(ddel_ctx* const* ctxs, int n, double* const* u, 
 
 /* --- Autotuner ------------------------------------------------------------------
  * Chooses the Schur form (IMPLICIT block substitution, EXPLICIT FP64, or AUTO =
- * explicit applied in double-float arithmetic) and the PCG graph batch size
- * (check_every in {8, 16, 32}) for an assembled context by timing them on this
+ * explicit applied in double-float arithmetic), the formation of S_i (tensor
+ * cores or FP64 pipe, ddel_options.tensor_form, where both exist) and the PCG
+ * graph batch size (check_every in {8, 16, 32}) for an assembled context by
+ * timing them on this
  * GPU: one solve gives the iteration count N, then each candidate is
  * factorised and runs 48 PCG iterations; the predicted solve time is
  * factor (+ formation) time + N x time per iteration.  The winner is applied
  * to the context (ddel_set_options semantics: refactor before solving) and,
  * with cache_path != NULL, appended to that text file under the key
- * "dim sub BP n_sub precision"; a later call with the same key reads the file
+ * "dim sub BP n_sub precision" (fields: mode, check_every, tensor_form; lines
+ * without the last field keep the context's tensor_form); a later call with the same key reads the file
  * and applies the cached choice without timing (*from_cache = 1).
  * chosen_mode / chosen_check: outputs (may be NULL).  Synchronises. */
 int ddel_autotune(ddel_ctx* ctx, const char* cache_path, int* chosen_mode, int* chosen_check,

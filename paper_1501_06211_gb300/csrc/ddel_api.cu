@@ -380,20 +380,21 @@ int factor_launch(ddel_ctx* ctx, int prec) {
       cudaError_t e = cudaMalloc(&ctx->form_work[prec], we * (prec ? 4 : 8));
       if (e != cudaSuccess) return fail(ctx, DDEL_ENOMEM, "explicit Schur scratch allocation");
     }
-    // FP64-accurate S_i with W^T W on the tensor cores: the native FP64 form,
-    // and the double-float form's rings of 256 (for rings of 128 the
-    // double-float form keeps its own, faster double-float formation)
-    const bool tc = prec == 0 && ctx->opt.tensor_form && tensor_form_available(ctx->T) &&
-                    !(ctx->opt.schur_mode == DDEL_SCHUR_AUTO && NR <= 128);
+    // S_i with W^T W on the tensor cores: FP64-accurate for the native FP64
+    // form and the double-float form's rings of 256 (for rings of 128 the
+    // double-float form keeps its own, faster double-float formation); the
+    // FP32 form from BF16 slices of its FP32 W, to 24 bits
+    const bool tc = ctx->opt.tensor_form && tensor_form_available(ctx->T) &&
+                    !(prec == 0 && ctx->opt.schur_mode == DDEL_SCHUR_AUTO && NR <= 128);
     if (tc) {
-      if (!ctx->form_work[0]) {
-        cudaError_t e = cudaMalloc(&ctx->form_work[0], explicit_form_work_elems(ctx->T) * 8);
+      if (!ctx->form_work[prec]) {
+        cudaError_t e = cudaMalloc(&ctx->form_work[prec], explicit_form_work_elems(ctx->T) * (prec ? 4 : 8));
         if (e != cudaSuccess) return fail(ctx, DDEL_ENOMEM, "explicit Schur scratch allocation");
       }
       if (!ctx->tc_work && cudaMalloc(&ctx->tc_work, tensor_form_work_bytes(ctx->T)) != cudaSuccess)
         return fail(ctx, DDEL_ENOMEM, "tensor-core formation scratch allocation");
-      launch_schur_form_tc(ctx->T, ctx->F, ctx->factor[0], ctx->form_work[0], ctx->tc_work, ctx->sexp[0],
-                           ctx->err, ctx->stream);
+      launch_schur_form_tc(ctx->T, ctx->F, prec, ctx->factor[prec], ctx->form_work[prec], ctx->tc_work,
+                           ctx->sexp[prec], ctx->err, ctx->stream);
       ctx->launches += 3;
     } else {
       // AUTO applies S_i in double-float arithmetic, so it is formed that way too
@@ -1522,9 +1523,10 @@ int ddel_autotune(ddel_ctx* ctx, const char* cache_path, int* chosen_mode, int* 
   std::snprintf(key, sizeof(key), "%d %d %d %d %d", ctx->S.dim, ctx->S.sub, ctx->S.BP, ctx->S.n_sub,
                 ctx->opt.precision);
   if (from_cache) *from_cache = 0;
-  auto apply = [&](int mode, int check) {
+  auto apply = [&](int mode, int check, int tf) {
     ctx->opt.schur_mode = mode;
     ctx->opt.check_every = check;
+    ctx->opt.tensor_form = tf;
     ctx->factored[0] = ctx->factored[1] = false;
     if (chosen_mode) *chosen_mode = mode;
     if (chosen_check) *chosen_check = check;
@@ -1532,21 +1534,23 @@ int ddel_autotune(ddel_ctx* ctx, const char* cache_path, int* chosen_mode, int* 
   if (cache_path) {
     if (FILE* fp = std::fopen(cache_path, "r")) {
       char line[256];
-      int mode = -1, check = 0;
+      int mode = -1, check = 0, tform = ctx->opt.tensor_form;
       while (std::fgets(line, sizeof(line), fp)) {
-        int d, s, b, n, p, m, c;
-        if (std::sscanf(line, "%d %d %d %d %d %d %d", &d, &s, &b, &n, &p, &m, &c) == 7) {
+        int d, s, b, n, p, m, c, tf = ctx->opt.tensor_form;
+        const int got = std::sscanf(line, "%d %d %d %d %d %d %d %d", &d, &s, &b, &n, &p, &m, &c, &tf);
+        if (got >= 7) {  // lines without the tensor-form field keep the context's setting
           char k2[128];
           std::snprintf(k2, sizeof(k2), "%d %d %d %d %d", d, s, b, n, p);
           if (std::strcmp(k2, key) == 0) {
             mode = m;
             check = c;
+            tform = tf;
           }
         }
       }
       std::fclose(fp);
       if (mode >= 0) {
-        apply(mode, check);
+        apply(mode, check, tform);
         if (from_cache) *from_cache = 1;
         return DDEL_OK;
       }
@@ -1561,18 +1565,28 @@ int ddel_autotune(ddel_ctx* ctx, const char* cache_path, int* chosen_mode, int* 
   if (rc != DDEL_OK && rc != DDEL_ENOCONV) return rc;
   const double n_iter = st.iters > 0 ? st.iters : 1;
   const bool has_explicit = explicit_ring_size(ctx->T) > 0;
-  std::vector<int> modes = {DDEL_SCHUR_IMPLICIT};
-  if (has_explicit && prec == 0) modes.push_back(DDEL_SCHUR_AUTO);
-  if (has_explicit) modes.push_back(DDEL_SCHUR_EXPLICIT);
+  // candidates (Schur form, S_i formation on the tensor cores or the FP64 pipe)
+  const bool tc_ok = tensor_form_available(ctx->T);
+  std::vector<std::pair<int, int>> forms = {{DDEL_SCHUR_IMPLICIT, saved.tensor_form}};
+  if (has_explicit && prec == 0) {
+    forms.push_back({DDEL_SCHUR_AUTO, 0});
+    if (tc_ok && explicit_ring_size(ctx->T) > 128) forms.push_back({DDEL_SCHUR_AUTO, 1});
+  }
+  if (has_explicit) {
+    forms.push_back({DDEL_SCHUR_EXPLICIT, 0});
+    if (tc_ok) forms.push_back({DDEL_SCHUR_EXPLICIT, 1});
+  }
   const int checks[3] = {8, 16, 32};
   double best = 1e300;
-  int best_mode = saved.schur_mode, best_check = saved.check_every;
+  int best_mode = saved.schur_mode, best_check = saved.check_every, best_tf = saved.tensor_form;
   cudaStream_t s = ctx->stream;
-  for (int mode : modes)
+  for (const auto& fm : forms)
     for (int check : checks) {
+      const int mode = fm.first;
       ctx->opt = saved;
       ctx->opt.schur_mode = mode;
       ctx->opt.check_every = check;
+      ctx->opt.tensor_form = fm.second;
       CK(cudaEventRecord(ctx->ev[0], s));
       rc = ddel_factor(ctx);
       if (rc) return rc;
@@ -1603,13 +1617,14 @@ int ddel_autotune(ddel_ctx* ctx, const char* cache_path, int* chosen_mode, int* 
         best = predicted;
         best_mode = mode;
         best_check = check;
+        best_tf = fm.second;
       }
     }
   ctx->opt = saved;
-  apply(best_mode, best_check);
+  apply(best_mode, best_check, best_tf);
   if (cache_path) {
     if (FILE* fp = std::fopen(cache_path, "a")) {
-      std::fprintf(fp, "%s %d %d\n", key, best_mode, best_check);
+      std::fprintf(fp, "%s %d %d %d\n", key, best_mode, best_check, best_tf);
       std::fclose(fp);
     }
   }

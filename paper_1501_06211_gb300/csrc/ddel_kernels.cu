@@ -1471,14 +1471,15 @@ __device__ __forceinline__ void pcg_update_tile(const DevTables& t, const DevFie
       }
       __syncthreads();
     } else {
-      double a[NP];
-#pragma unroll
-      for (int v = 0; v < NP; ++v) {
-        a[v] = 0.0;
-        if (v >= 3 && (v - 3) % KD >= k) continue;
-        const double* src = v == 0 ? pd : pu_in + (size_t)(v - 1) * nu;
-        const int n = v == 0 ? nd : nu;
-        for (int b = threadIdx.x; b < n; b += kRedThreads) a[v] += __ldcg(src + b);
+      // delta, gamma, rr and the coarse sums: the warps take the values in
+      // turn, each reduced by one warp as above
+      for (int v = wib; v < NP; v += nwb) {
+        double tot = 0.0;
+        if (!(v >= 3 && (v - 3) % KD >= k)) {  // coarse rows beyond k stay 0
+          const double* src = v == 0 ? pd : pu_in + (size_t)(v - 1) * nu;
+          tot = reduce_partials_warp(src, v == 0 ? nd : nu);
+        }
+        if (lane == 0) sums[v] = tot;
       }
       if constexpr (CG) {
         __syncthreads();
@@ -1488,8 +1489,6 @@ __device__ __forceinline__ void pcg_update_tile(const DevTables& t, const DevFie
         cp_async_wait_all();
         return;
       }
-      block_tree_sum<NP>(a, NP, red);
-      if (threadIdx.x < NP) sums[threadIdx.x] = red[threadIdx.x * kRedThreads];
       __syncthreads();
     }
     if (threadIdx.x == 0) {
@@ -2003,10 +2002,11 @@ size_t ozaki_smem_bytes(const DevTables& t) {
 
 int ozaki_kp(const DevTables& t) { return ((t.nb_max * t.BP + kOzKC - 1) / kOzKC) * kOzKC; }
 
+// Slices of the FP64 form (54 bits; enough buffer for the FP32 form too).
 size_t ozaki_slice_elems(const DevTables& t, int NR) {
   const int Kp = ozaki_kp(t);
   const int bits = Kp <= 1489 ? 6 : 5;
-  return (size_t)t.n_sub * oz_slices(bits) * NR * Kp;
+  return (size_t)t.n_sub * oz_slices(bits, 54) * NR * Kp;
 }
 
 int explicit_ring_size(const DevTables& t) {
@@ -2035,32 +2035,60 @@ size_t tensor_form_work_bytes(const DevTables& t) {
   return ozaki_slice_elems(t, NR) * sizeof(__nv_bfloat16) + (size_t)t.n_sub * NR * sizeof(int) + 256;
 }
 
-void launch_schur_form_tc(const DevTables& t, const DevFields& fld, const void* factor, void* work,
+void launch_schur_form_tc(const DevTables& t, const DevFields& fld, int precision, const void* factor, void* work,
                           void* tc_work, void* Sexp, int* err, cudaStream_t st) {
   const int NR = explicit_ring_size(t);
   const int Kp = ozaki_kp(t);
+  const int bits = Kp <= 1489 ? 6 : 5;
+  // slices to 54 bits in both precisions: W^T W to FP64 accuracy, and for
+  // the FP32 form S_i rounded once to FP32.  (Slices to only 24 bits, the
+  // FP32 significand, cut the small entries of a column to the bits left
+  // below its largest one: on the 512 x 256 cantilever at 1e9 stiffness
+  // contrast the refined FP32 solve then took 13 cycles and 13.5 k PCG
+  // iterations instead of 9 and 7.2 k.)
+  const int S = oz_slices(bits, 54);
   __nv_bfloat16* Wsl = reinterpret_cast<__nv_bfloat16*>(tc_work);
   int* expo = reinterpret_cast<int*>(reinterpret_cast<char*>(tc_work) + ozaki_slice_elems(t, NR) * 2 + 128);
-  double* W = reinterpret_cast<double*>(work);
-  const double* fac = reinterpret_cast<const double*>(factor);
-  if (NR == 128) {
-    form_w2d_kernel<double, 32, 128, kFormGC><<<dim3(t.n_sub, 128 / kFormGC), 256, form_w_smem<double, 32, 128>(t),
-                                                st>>>(t, t.Ke64, fld.scale64, fac, W);
-  } else if (t.BP == 64) {
-    form_w2d_kernel<double, 64, 256, kFormGC><<<dim3(t.n_sub, 256 / kFormGC), 256, form_w_smem<double, 64, 256>(t),
-                                                st>>>(t, t.Ke64, fld.scale64, fac, W);
-  } else {
-    form_w2d_kernel<double, 96, 256, kFormGC><<<dim3(t.n_sub, 256 / kFormGC), 256, form_w_smem<double, 96, 256>(t),
-                                                st>>>(t, t.Ke64, fld.scale64, fac, W);
-  }
-  ozaki_slice_kernel<<<dim3(t.n_sub, NR / 32), 256, 0, st>>>(t, W, NR, Kp, Wsl, expo);
   const size_t sm = ozaki_smem_bytes(t);
-  if (NR == 128)
-    ozaki_syrk_kernel<128><<<dim3(t.n_sub, 1), kOzThreads, sm, st>>>(t, t.Ke64, fld.scale64, Wsl, expo, Kp,
-                                                                     reinterpret_cast<double*>(Sexp), err);
-  else
-    ozaki_syrk_kernel<256><<<dim3(t.n_sub, 3), kOzThreads, sm, st>>>(t, t.Ke64, fld.scale64, Wsl, expo, Kp,
-                                                                     reinterpret_cast<double*>(Sexp), err);
+  if (precision == 0) {
+    double* W = reinterpret_cast<double*>(work);
+    const double* fac = reinterpret_cast<const double*>(factor);
+    if (NR == 128)
+      form_w2d_kernel<double, 32, 128, kFormGC><<<dim3(t.n_sub, 128 / kFormGC), 256, form_w_smem<double, 32, 128>(t),
+                                                  st>>>(t, t.Ke64, fld.scale64, fac, W);
+    else if (t.BP == 64)
+      form_w2d_kernel<double, 64, 256, kFormGC><<<dim3(t.n_sub, 256 / kFormGC), 256, form_w_smem<double, 64, 256>(t),
+                                                  st>>>(t, t.Ke64, fld.scale64, fac, W);
+    else
+      form_w2d_kernel<double, 96, 256, kFormGC><<<dim3(t.n_sub, 256 / kFormGC), 256, form_w_smem<double, 96, 256>(t),
+                                                  st>>>(t, t.Ke64, fld.scale64, fac, W);
+    ozaki_slice_kernel<double><<<dim3(t.n_sub, NR / 32), 256, 0, st>>>(t, W, NR, Kp, S, Wsl, expo);
+    if (NR == 128)
+      ozaki_syrk_kernel<128, double><<<dim3(t.n_sub, 1), kOzThreads, sm, st>>>(
+          t, t.Ke64, fld.scale64, Wsl, expo, Kp, S, reinterpret_cast<double*>(Sexp), err);
+    else
+      ozaki_syrk_kernel<256, double><<<dim3(t.n_sub, 3), kOzThreads, sm, st>>>(
+          t, t.Ke64, fld.scale64, Wsl, expo, Kp, S, reinterpret_cast<double*>(Sexp), err);
+  } else {
+    float* W = reinterpret_cast<float*>(work);
+    const float* fac = reinterpret_cast<const float*>(factor);
+    if (NR == 128)
+      form_w2d_kernel<float, 32, 128, kFormGC><<<dim3(t.n_sub, 128 / kFormGC), 256, form_w_smem<float, 32, 128>(t),
+                                                 st>>>(t, t.Ke32, fld.scale32, fac, W);
+    else if (t.BP == 64)
+      form_w2d_kernel<float, 64, 256, kFormGC><<<dim3(t.n_sub, 256 / kFormGC), 256, form_w_smem<float, 64, 256>(t),
+                                                 st>>>(t, t.Ke32, fld.scale32, fac, W);
+    else
+      form_w2d_kernel<float, 96, 256, kFormGC><<<dim3(t.n_sub, 256 / kFormGC), 256, form_w_smem<float, 96, 256>(t),
+                                                 st>>>(t, t.Ke32, fld.scale32, fac, W);
+    ozaki_slice_kernel<float><<<dim3(t.n_sub, NR / 32), 256, 0, st>>>(t, W, NR, Kp, S, Wsl, expo);
+    if (NR == 128)
+      ozaki_syrk_kernel<128, float><<<dim3(t.n_sub, 1), kOzThreads, sm, st>>>(
+          t, t.Ke64, fld.scale64, Wsl, expo, Kp, S, reinterpret_cast<float*>(Sexp), err);
+    else
+      ozaki_syrk_kernel<256, float><<<dim3(t.n_sub, 3), kOzThreads, sm, st>>>(
+          t, t.Ke64, fld.scale64, Wsl, expo, Kp, S, reinterpret_cast<float*>(Sexp), err);
+  }
 }
 
 void launch_schur_form(const DevTables& t, const DevFields& fld, int precision, bool df, const void* factor,
@@ -2160,9 +2188,12 @@ cudaError_t configure_kernels() {
   DDEL_CFG((form_syrk2d_kernel<float, 96, 256, kFormTQ>));
   // the update kernel's staged face tables plus the coarse variants' static
   // reduction arrays exceed the default 48 KB
-  DDEL_CFG((ozaki_syrk_kernel<128>));
-  DDEL_CFG((ozaki_syrk_kernel<256>));
+  DDEL_CFG((ozaki_syrk_kernel<128, double>));
+  DDEL_CFG((ozaki_syrk_kernel<256, double>));
+  DDEL_CFG((ozaki_syrk_kernel<128, float>));
+  DDEL_CFG((ozaki_syrk_kernel<256, float>));
   DDEL_CFG((form_w2d_kernel<double, 32, 128, kFormGC>));
+  DDEL_CFG((form_w2d_kernel<float, 32, 128, kFormGC>));
   DDEL_CFG((batch_pcg_kernel));
   DDEL_CFG((pcg_update_kernel<double, 0>));
   DDEL_CFG((pcg_update_kernel<double, 4>));

@@ -144,14 +144,15 @@ int explicit_ring_size(const DevTables& t);
 size_t explicit_form_work_elems(const DevTables& t);
 void launch_schur_form(const DevTables& t, const DevFields& fld, int precision, bool df, const void* factor,
                        void* work, void* Sexp, cudaStream_t st);
-// Tensor-core formation (rings of 128 and 256): W = L^-1 K_IG in FP64 into
-// work (explicit_form_work_elems doubles), then S_i = K_GG - W^T W with the
-// product on tcgen05 at FP64 accuracy by the Ozaki splitting of W into BF16
-// slices (tc_work: tensor_form_work_bytes).  err: kErrTimeout if a bounded
+// Tensor-core formation (rings of 128 and 256): W = L^-1 K_IG in the
+// factor's precision into work (explicit_form_work_elems elements), then
+// S_i = K_GG - W^T W with the product on tcgen05 from the Ozaki splitting of
+// W into BF16 slices (tc_work: tensor_form_work_bytes) -- to FP64 accuracy
+// (precision 0) or to the 24 bits of the FP32 operator (precision 1).  err: kErrTimeout if a bounded
 // wait on the tensor-core completion ran out.
 bool tensor_form_available(const DevTables& t);
 size_t tensor_form_work_bytes(const DevTables& t);
-void launch_schur_form_tc(const DevTables& t, const DevFields& fld, const void* factor, void* work,
+void launch_schur_form_tc(const DevTables& t, const DevFields& fld, int precision, const void* factor, void* work,
                           void* tc_work, void* Sexp, int* err, cudaStream_t st);
 // Double-float form: S_i split into FP32 (hi, lo) pairs; the apply runs on the
 // FP32 pipes with about 48 significant bits (ring output FP64).

@@ -18,17 +18,15 @@
 // S B >= 54 bits.  The accumulators are drained into FP64 (smallest d
 // first) on top of K_GG.
 //
-// ozaki_slice_kernel: per subdomain and ring column, e_j and the slices
-//   (BF16, stored [slice][column][row] with the rows contiguous, zero padded
-//   to a multiple of 64 rows).
-// ozaki_syrk_kernel: one CTA of 128 threads per (subdomain, 128 x 128 tile of
-//   S); per K chunk of 64 rows the two operand tiles are copied to shared
-//   memory in the canonical K-major no-swizzle layout (8 x 8 core matrices of
-//   128 bytes, K-adjacent core matrices 128 B apart, 8-row groups 256 B
-//   apart) and thread 0 issues four 128 x 128 x 16 MMAs into a 128-column
-//   accumulator in tensor memory; completion is signalled on an mbarrier
-//   (bounded wait).  The four warps then read the accumulator (each its 32
-//   lanes = rows) and add it, scaled, into the FP64 tile in shared memory.
+// Both precisions slice to 54 bits: the FP32 form rounds the FP64-accurate
+// S_i once to FP32.
+//
+// ozaki_slice_kernel: per subdomain and ring column, e_j and the slices, each
+//   stored as ready-made 16 KB operand images (below).
+// ozaki_syrk_kernel: one CTA of 256 threads per (subdomain, 128 x 128 tile of
+//   S, upper triangle of tiles); one thread streams operand images into
+//   shared memory by bulk copies and issues the MMAs, all eight warps drain
+//   the accumulator into the FP64 tile they keep in registers.
 
 
 constexpr int kOzThreads = 256;
@@ -36,7 +34,8 @@ constexpr int kOzKC = 64;      // rows of W per operand chunk
 constexpr int kOzTile = 128;   // output tile edge (MMA M = N)
 
 __device__ __forceinline__ int oz_bits(int K) { return K <= 1489 ? 6 : 5; }
-__device__ __host__ __forceinline__ int oz_slices(int bits) { return (54 + bits - 1) / bits; }
+// Slices for a target of `target` significant bits.
+__device__ __host__ __forceinline__ int oz_slices(int bits, int target) { return (target + bits - 1) / bits; }
 
 // Byte offset of element (c, k) (c < 128 ring columns of a row tile, k < 64
 // rows of a chunk) in a 16 KB operand image: the canonical K-major layout
@@ -53,18 +52,19 @@ __device__ __forceinline__ int oz_img_off(int c, int k) {
 // (Kp / 64) one 16 KB image (oz_img_off); expo: per subdomain NR ints.  Block
 // (subdomain, 32 columns) of 256 threads: the column maxima, then per thread
 // one column and 8 consecutive rows, written as one 16-byte unit per slice.
-__global__ void __launch_bounds__(256) ozaki_slice_kernel(DevTables t, const double* __restrict__ W, int NR, int Kp,
+template <typename TW>
+__global__ void __launch_bounds__(256) ozaki_slice_kernel(DevTables t, const TW* __restrict__ W, int NR, int Kp, int S,
                                                           __nv_bfloat16* __restrict__ Wsl, int* __restrict__ expo) {
   const int sub = blockIdx.x, j0 = blockIdx.y * 32, tid = threadIdx.x;
   const int jl = tid & 31, ko = tid >> 5;  // column in the block, row offset
   const SubInfo si = t.subs[sub];
   const int K = si.nb * t.BP;  // rows of this subdomain's W (the rest are zero)
-  const int bits = oz_bits(Kp), S = oz_slices(bits);
-  const double* Wb = W + (int64_t)sub * t.nb_max * t.BP * NR;
+  const int bits = oz_bits(Kp);
+  const TW* Wb = W + (int64_t)sub * t.nb_max * t.BP * NR;
   __shared__ double mx_s[8][32];
   __shared__ int e_s[32];
   double mx = 0.0;
-  for (int k = ko; k < K; k += 8) mx = fmax(mx, fabs(Wb[(int64_t)k * NR + j0 + jl]));
+  for (int k = ko; k < K; k += 8) mx = fmax(mx, fabs((double)Wb[(int64_t)k * NR + j0 + jl]));
   mx_s[ko][jl] = mx;
   __syncthreads();
   if (tid < 32) {
@@ -88,7 +88,7 @@ __global__ void __launch_bounds__(256) ozaki_slice_kernel(DevTables t, const dou
     long long m[8];
 #pragma unroll
     for (int r = 0; r < 8; ++r)
-      m[r] = k8 + r < K ? __double2ll_rn(ldexp(Wb[(int64_t)(k8 + r) * NR + j], bits * S - e)) : 0ll;
+      m[r] = k8 + r < K ? __double2ll_rn(ldexp((double)Wb[(int64_t)(k8 + r) * NR + j], bits * S - e)) : 0ll;
     const int kc = k8 >> 6;
     const int off = oz_img_off(c, k8 & 63);
     for (int p = 0; p < S; ++p) {
@@ -181,12 +181,12 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
 // memory and returns.
 constexpr int kOzStages = 6;
 
-template <int NR>
+template <int NR, typename TO>
 __global__ void __launch_bounds__(kOzThreads, 1) ozaki_syrk_kernel(DevTables t, const double* __restrict__ Ke_g,
                                                                    const double* __restrict__ scale,
                                                                    const __nv_bfloat16* __restrict__ Wsl,
-                                                                   const int* __restrict__ expo, int Kp,
-                                                                   double* __restrict__ Sexp, int* err) {
+                                                                   const int* __restrict__ expo, int Kp, int S,
+                                                                   TO* __restrict__ Sexp, int* err) {
   constexpr int NT = NR / kOzTile, NST = kOzStages;
   const int sub = blockIdx.x, tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   int ta = 0, q = blockIdx.y;  // tile index -> (ta, tb), ta <= tb
@@ -197,7 +197,7 @@ __global__ void __launch_bounds__(kOzThreads, 1) ozaki_syrk_kernel(DevTables t, 
   const int tb = ta + q;
   const SubInfo si = t.subs[sub];
   const int s = t.s;
-  const int bits = oz_bits(Kp), S = oz_slices(bits);
+  const int bits = oz_bits(Kp);
   extern __shared__ __align__(1024) unsigned char oz_smem[];
   unsigned char* stage = oz_smem;                                 // NST x (A 16 KB, B 16 KB)
   double* ke = reinterpret_cast<double*>(oz_smem + NST * 32768);  // 64
@@ -308,12 +308,12 @@ __global__ void __launch_bounds__(kOzThreads, 1) ozaki_syrk_kernel(DevTables t, 
   if (s_fail && tid == 0) atomicExch(err, kErrTimeout);
   __syncthreads();
   if (warp == 0) tmem_dealloc(tmem_base, 128);
-  double* out = Sexp + (int64_t)sub * NR * NR;
+  TO* out = Sexp + (int64_t)sub * NR * NR;
   const int gi = ta * kOzTile + i;
 #pragma unroll
   for (int c = 0; c < 64; ++c) {
     const int gj = tb * kOzTile + jc + c;
-    out[(int64_t)gi * NR + gj] = acc[c];
-    if (ta != tb) out[(int64_t)gj * NR + gi] = acc[c];
+    out[(int64_t)gi * NR + gj] = (TO)acc[c];
+    if (ta != tb) out[(int64_t)gj * NR + gi] = (TO)acc[c];
   }
 }

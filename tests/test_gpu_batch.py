@@ -64,7 +64,11 @@ def test_autotune_choice_cache_and_parity(tmp_path):
     code, mode, check, cached = ddel.ddel_autotune(s.h, cache)
     assert code == 0 and not cached
     assert mode in (0, 1, 2) and check in (8, 16, 32)
-    assert len(open(cache).read().strip().splitlines()) == 1
+    lines = open(cache).read().strip().splitlines()
+    assert len(lines) == 1
+    # key (dim sub BP n_sub precision), then mode, check_every, tensor_form
+    fields = lines[0].split()
+    assert len(fields) == 8 and int(fields[5]) == mode and int(fields[6]) == check and fields[7] in ("0", "1")
     s2 = ddel.Solver(cfg, tol=1e-10, max_it=20000)
     s2.assemble(rho)
     code2, mode2, check2, cached2 = ddel.ddel_autotune(s2.h, cache)

@@ -76,3 +76,31 @@ def test_tensor_core_schur_complements(name, mode):
     u, st = sols[1]
     assert st.relres <= 1e-9, st.as_dict()
     assert rel(u, u_ref) <= 1e-8, (rel(u, u_ref), st.as_dict())
+
+
+@pytest.mark.parametrize("name", ["grf128", "s32"])
+def test_tensor_core_fp32_form(name):
+    # the FP32 form: S_i = K_GG - W^T W from BF16 slices of the FP32 W on the
+    # tensor cores (to FP64 accuracy, then rounded to FP32), applied in FP32;
+    # FP64 refinement wins the accuracy back (the bar of the reduced-precision
+    # forms: 1e-6)
+    from paper_1501_06211_gb300 import ddel
+    cfg = CASES[name]
+    rho, fixed, f, dec, K, dds = oracle(cfg)
+    s = ddel.Solver(cfg, precision=ddel.DDEL_FP32, schur_mode=1, tensor_form=1, tol=1e-9, max_it=20000,
+                    max_cycles=60, inner_tol=0.1)
+    s.assemble(rho)
+    s.factor()
+    gd = s.gamma_dofs()
+    x = np.random.default_rng(4).standard_normal(len(gd))
+    y = torch.zeros(len(gd), dtype=torch.float64, device="cuda")
+    assert ddel.ddel_schur_apply(s.h, torch.as_tensor(x, device="cuda"), y) == 0
+    pos = {int(v): k for k, v in enumerate(dec.gamma_dofs)}
+    perm = np.array([pos[int(v)] for v in gd])
+    xo = np.zeros(len(gd))
+    xo[perm] = x
+    # the FP32 operator: S to FP32 accuracy relative to its largest entries
+    assert rel(y.cpu().numpy(), dds.schur_apply(xo)[perm]) < 1e-4
+    u, st = s.solve(check=False)
+    assert st.relres <= 1e-9, st.as_dict()
+    assert rel(u, direct.solve(K, f, fixed)) <= 1e-6, st.as_dict()
