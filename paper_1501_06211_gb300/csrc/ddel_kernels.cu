@@ -137,103 +137,295 @@ __device__ __forceinline__ T entry2d(const DevTables& t, const SubInfo& si, cons
   return sum;
 }
 
-// Block step k: A_kk -= C_k C_k^T; L_kk = chol(A_kk); D_k = L_kk^-1;
-// C_{k+1} = A_{k+1,k} D_k^T.  Stored per subdomain as [C_k | D_k] for every k
-// (C_k dense column-major BP x BP, D_k packed lower column-major), so that one
-// forward step reads one contiguous [C_k D_k] and one backward step one
-// contiguous [D_k C_{k+1}].
+// Block step k of the block-tridiagonal Cholesky factorisation of K_{I_i I_i}
+// over the planes of interior nodes (eq. NumberFive): A_kk -= C_k C_k^T;
+// L_kk = chol(A_kk); D_k = L_kk^-1; C_{k+1} = A_{k+1,k} D_k^T.  Stored per
+// subdomain as [C_k | D_k] for every k (C_k dense column-major BP x BP, D_k
+// packed lower column-major), so that one forward step reads one contiguous
+// [C_k D_k] and one backward step one contiguous [D_k C_{k+1}].
+//
+// One CTA of kFacThreads threads per subdomain, every block in shared memory:
+//  (a) the lower triangle of A_kk (nonzero only where the nodes' y differ by
+//      at most one) minus C_k C_k^T, in TS x TS register tiles;
+//  (b) blocked right-looking Cholesky with PW-wide panels: the diagonal block
+//      by one warp (one lane per entry of each column step's update), each
+//      panel row by one thread, the trailing update in TS x TS tiles -- three
+//      CTA barriers per panel;
+//  (c) D_k = L_kk^-1 by 8 x 8 blocks: the diagonal blocks inverted by one
+//      thread per column, then block row p from the rows above,
+//      D_pq = -D_pp sum_{q <= m < p} L_pm D_mq, every entry one thread;
+//  (e) C_{k+1} = A_{k+1,k} D_k^T using the sparsity of A_{k+1,k}: a row
+//      couples only to the nodes y - 1, y, y + 1 of the plane before, six
+//      consecutive columns, assembled once per row.
+// The FP64 pipe of this GPU retires one warp instruction per 16 clocks per SM
+// whatever the number of active lanes, so the sequential parts are laid out
+// to keep the lanes of each FP64 instruction busy, and the pivots take one
+// reciprocal square root (Newton) instead of a square root and divisions.
+// A pivot that is not positive is replaced by 1 and reported (kErrPivot, the
+// lowest such subdomain in bad_sub).
+constexpr int kFacThreads = 256;
+
+// 1 / sqrt(d), d > 0: Newton's iteration for f(r) = 1 / r^2 - d,
+// r <- r (3 - d r^2) / 2, from the single-precision estimate; each step
+// doubles the correct bits, two take the estimate's 23 past double precision
+// (a few units in the last place).  Outside the single-precision range the
+// library square root and division serve.
+template <typename T>
+__device__ __forceinline__ T pivot_rsqrt(T d) {
+  if constexpr (sizeof(T) == 8) {
+    if (d > 1e-36 && d < 1e36) {
+      double r = (double)rsqrtf((float)d);
+      r = r * fma(-0.5 * d, r * r, 1.5);
+      r = r * fma(-0.5 * d, r * r, 1.5);
+      return r;
+    }
+    return 1.0 / sqrt(d);
+  } else {
+    return T(1) / sqrt(d);
+  }
+}
+
+template <typename T>
+__device__ __forceinline__ void lds4(const T* p, T (&v)[4]) {
+  if constexpr (sizeof(T) == 8) {
+    const double2 a = reinterpret_cast<const double2*>(p)[0], b = reinterpret_cast<const double2*>(p)[1];
+    v[0] = a.x, v[1] = a.y, v[2] = b.x, v[3] = b.y;
+  } else {
+    const float4 a = *reinterpret_cast<const float4*>(p);
+    v[0] = a.x, v[1] = a.y, v[2] = a.z, v[3] = a.w;
+  }
+}
+
+// tile q of the lower block triangle of an nt x nt tiling -> (ti, tj), tj <= ti
+__device__ __forceinline__ void lower_tile(int q, int nt, int& ti, int& tj) {
+  tj = 0;
+  while (q >= nt - tj) {
+    q -= nt - tj;
+    ++tj;
+  }
+  ti = tj + q;
+}
+
 template <typename T, int BP>
-__global__ void __launch_bounds__(128) factor2d_kernel(DevTables t, const T* __restrict__ Ke_g,
-                                                       const T* __restrict__ scale,
-                                                       T* __restrict__ factor, int* err,
-                                                       int* bad_sub) {
+size_t factor2d_smem() {
+  return (size_t)(2 * BP * (BP + 1) + BP * BP + 64 + BP + 6 * BP) * sizeof(T);
+}
+
+template <typename T, int BP>
+__global__ void __launch_bounds__(kFacThreads, BP == 32 ? 4 : 1)
+    factor2d_kernel(DevTables t, const T* __restrict__ Ke_g, const T* __restrict__ scale, T* __restrict__ factor,
+                    int* err, int* bad_sub) {
   constexpr int LD = BP + 1, PC = BP * BP, PD = BP * (BP + 1) / 2, STAGE = PC + PD;
-  const int sub = blockIdx.x, tid = threadIdx.x;
+  constexpr int TS = BP == 32 ? 2 : 4;                   // register tile edge
+  constexpr int NT = BP / TS;                            // tiles per edge
+  constexpr int PW = BP == 32 ? 8 : 16;                  // Cholesky panel width
+  constexpr int NJ = kFacThreads / BP;                   // column groups of the C product
+  const int sub = blockIdx.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const SubInfo si = t.subs[sub];
   extern __shared__ __align__(128) unsigned char smem_raw[];
-  T* A = reinterpret_cast<T*>(smem_raw);
-  T* Dm = A + BP * LD;
-  T* Cm = Dm + BP * LD;
-  T* ke = Cm + BP * LD;
-  for (int i = tid; i < 64; i += 128) ke[i] = Ke_g[i];
+  T* A = reinterpret_cast<T*>(smem_raw);  // BP x LD, lower part: A_kk, then L_kk
+  T* Dm = A + BP * LD;                    // BP x LD, lower part: D_k
+  T* CT = Dm + BP * LD;                   // BP x BP: CT[m * BP + i] = C_k(i, m)
+  T* ke = CT + BP * BP;                   // 64
+  T* rdiag = ke + 64;                     // BP: 1 / L_kk(j, j)
+  T* anz = rdiag + BP;                    // BP x 6: the nonzeros of a row of A_{k+1,k}
+  __shared__ int s_bad;
+  for (int i = tid; i < 64; i += kFacThreads) ke[i] = Ke_g[i];
+  if (tid == 0) s_bad = 0;
   __syncthreads();
   const int nb = si.nb;
-  bool bad = false;
   T* fb = factor + si.factor_off;
   for (int k = 0; k < nb; ++k) {
-    // (a) assemble the lower triangle of A_kk - C_k C_k^T
-    for (int idx = tid; idx < BP * BP; idx += 128) {
-      const int i = idx / BP, j = idx % BP;
-      if (j > i) continue;
-      T v = entry2d<T>(t, si, ke, scale, k, i, k, j);
+    // (a) lower triangle of A_kk - C_k C_k^T
+    for (int q = tid; q < NT * (NT + 1) / 2; q += kFacThreads) {
+      int ti, tj;
+      lower_tile(q, NT, ti, tj);
+      T acc[TS][TS];
+#pragma unroll
+      for (int u = 0; u < TS; ++u)
+#pragma unroll
+        for (int v = 0; v < TS; ++v) acc[u][v] = T(0);
       if (k > 0) {
-        T s = T(0);
-#pragma unroll 8
-        for (int m = 0; m < BP; ++m) s += Cm[i * LD + m] * Cm[j * LD + m];
-        v -= s;
+#pragma unroll 4
+        for (int m = 0; m < BP; ++m) {
+          T a[TS], b[TS];
+          if constexpr (TS == 4) {
+            lds4(CT + m * BP + 4 * ti, a);
+            lds4(CT + m * BP + 4 * tj, b);
+          } else {
+#pragma unroll
+            for (int u = 0; u < TS; ++u) a[u] = CT[m * BP + TS * ti + u], b[u] = CT[m * BP + TS * tj + u];
+          }
+#pragma unroll
+          for (int u = 0; u < TS; ++u)
+#pragma unroll
+            for (int v = 0; v < TS; ++v) acc[u][v] += a[u] * b[v];
+        }
       }
-      A[i * LD + j] = v;
+#pragma unroll
+      for (int u = 0; u < TS; ++u)
+#pragma unroll
+        for (int v = 0; v < TS; ++v) {
+          const int i = TS * ti + u, j = TS * tj + v;
+          if (j <= i) {
+            const T e = abs((i >> 1) - (j >> 1)) <= 1 ? entry2d<T>(t, si, ke, scale, k, i, k, j) : T(0);
+            A[i * LD + j] = e - acc[u][v];
+          }
+        }
     }
     __syncthreads();
-    // (b) right-looking dense Cholesky, lower, in place
-    for (int j = 0; j < BP; ++j) {
-      if (tid == 0) {
-        T d = A[j * LD + j];
-        if (!(d > T(0)) || !isfinite((double)d)) {
-          bad = true;
-          d = T(1);
+    // (b) blocked right-looking Cholesky, lower, in place
+    for (int j0 = 0; j0 < BP; j0 += PW) {
+      if (warp == 0) {
+        for (int j = j0; j < j0 + PW; ++j) {
+          T d = A[j * LD + j];
+          if (!(d > T(0)) || !isfinite((double)d)) {
+            if (lane == 0) s_bad = 1;
+            d = T(1);
+          }
+          const T rj = pivot_rsqrt(d);
+          __syncwarp();
+          if (lane == 0) {
+            A[j * LD + j] = d * rj;
+            rdiag[j] = rj;
+          }
+          const int i = j + 1 + lane;
+          if (i < j0 + PW) A[i * LD + j] *= rj;
+          __syncwarp();
+          // update of the block's trailing lower triangle (m rows), one lane per entry
+          const int m = j0 + PW - 1 - j;
+          for (int e = lane; e < m * (m + 1) / 2; e += 32) {
+            int r = 0, c = e;
+            while (c > r) {
+              c -= r + 1;
+              ++r;
+            }
+            const int ii = j + 1 + r, cc = j + 1 + c;
+            A[ii * LD + cc] -= A[ii * LD + j] * A[cc * LD + j];
+          }
+          __syncwarp();
         }
-        A[j * LD + j] = sqrt(d);
       }
       __syncthreads();
-      const T ljj = A[j * LD + j];
-      for (int i = j + 1 + tid; i < BP; i += 128) A[i * LD + j] /= ljj;
-      __syncthreads();
-      const int m = BP - j - 1;
-      for (int idx = tid; idx < m * m; idx += 128) {
-        const int ii = j + 1 + idx / m, cc = j + 1 + idx % m;
-        if (cc <= ii) A[ii * LD + cc] -= A[ii * LD + j] * A[cc * LD + j];
+      const int r0 = j0 + PW;
+      if (r0 < BP) {
+        // panel rows below the diagonal block: X L_pp^T = A_ip
+        for (int i = r0 + tid; i < BP; i += kFacThreads) {
+          T x[PW];
+#pragma unroll
+          for (int c = 0; c < PW; ++c) x[c] = A[i * LD + j0 + c];
+#pragma unroll
+          for (int c = 0; c < PW; ++c) {
+            T v = x[c];
+#pragma unroll
+            for (int m = 0; m < c; ++m) v -= x[m] * A[(j0 + c) * LD + j0 + m];
+            x[c] = v * rdiag[j0 + c];
+          }
+#pragma unroll
+          for (int c = 0; c < PW; ++c) A[i * LD + j0 + c] = x[c];
+        }
+        __syncthreads();
+        // trailing update of the lower triangle of rows / columns [r0, BP)
+        const int ntr = (BP - r0) / TS;
+        for (int q = tid; q < ntr * (ntr + 1) / 2; q += kFacThreads) {
+          int ti, tj;
+          lower_tile(q, ntr, ti, tj);
+          const int i0 = r0 + TS * ti, c0 = r0 + TS * tj;
+          T acc[TS][TS];
+#pragma unroll
+          for (int u = 0; u < TS; ++u)
+#pragma unroll
+            for (int v = 0; v < TS; ++v) acc[u][v] = T(0);
+#pragma unroll
+          for (int m = 0; m < PW; ++m) {
+            T a[TS], b[TS];
+#pragma unroll
+            for (int u = 0; u < TS; ++u) a[u] = A[(i0 + u) * LD + j0 + m], b[u] = A[(c0 + u) * LD + j0 + m];
+#pragma unroll
+            for (int u = 0; u < TS; ++u)
+#pragma unroll
+              for (int v = 0; v < TS; ++v) acc[u][v] += a[u] * b[v];
+          }
+#pragma unroll
+          for (int u = 0; u < TS; ++u)
+#pragma unroll
+            for (int v = 0; v < TS; ++v)
+              if (c0 + v <= i0 + u) A[(i0 + u) * LD + c0 + v] -= acc[u][v];
+        }
       }
       __syncthreads();
     }
-    // (c) D = L^-1 row by row (lower)
-    for (int i = 0; i < BP; ++i) {
-      for (int j = tid; j <= i; j += 128) {
-        T s = (i == j) ? T(1) : T(0);
-        for (int m = j; m < i; ++m) s -= A[i * LD + m] * Dm[m * LD + j];
-        Dm[i * LD + j] = s / A[i * LD + i];
+    // (c) D = L^-1 by 8 x 8 blocks.  Diagonal blocks: thread (p, c) inverts
+    // column c of L_pp by forward substitution (zeros above the diagonal).
+    if (tid < BP) {
+      const int p0 = tid & ~7, c = tid & 7;
+      T x[8];
+#pragma unroll
+      for (int r = 0; r < 8; ++r) {
+        T v = r == c ? T(1) : T(0);
+#pragma unroll
+        for (int m = 0; m < r; ++m) v -= A[(p0 + r) * LD + p0 + m] * x[m];
+        x[r] = r >= c ? v * rdiag[p0 + r] : T(0);
+      }
+#pragma unroll
+      for (int r = 0; r < 8; ++r) Dm[(p0 + r) * LD + p0 + c] = x[r];
+    }
+    __syncthreads();
+    // block row p: T_pq = sum_{q <= m < p} L_pm D_mq (into CT, free until (e)),
+    // then D_pq = -D_pp T_pq
+    for (int p = 1; p < BP / 8; ++p) {
+      for (int e = tid; e < p * 64; e += kFacThreads) {
+        const int q = e >> 6, r = (e >> 3) & 7, c = e & 7;
+        const T* Lrow = A + (8 * p + r) * LD;
+        T v = T(0);
+        for (int m = 8 * q; m < 8 * p; ++m) v += Lrow[m] * Dm[m * LD + 8 * q + c];
+        CT[e] = v;
+      }
+      __syncthreads();
+      for (int e = tid; e < p * 64; e += kFacThreads) {
+        const int q = e >> 6, r = (e >> 3) & 7, c = e & 7;
+        T v = T(0);
+#pragma unroll
+        for (int s2 = 0; s2 < 8; ++s2) v += Dm[(8 * p + r) * LD + 8 * p + s2] * CT[(q << 6) + (s2 << 3) + c];
+        Dm[(8 * p + r) * LD + 8 * q + c] = -v;
       }
       __syncthreads();
     }
     // (d) store D_k packed lower column-major
     T* Dg = fb + (int64_t)k * STAGE + PC;
-    for (int idx = tid; idx < BP * BP; idx += 128) {
+    for (int idx = tid; idx < BP * BP; idx += kFacThreads) {
       const int j = idx / BP, r = idx % BP;
       if (r >= j) Dg[j * BP - j * (j - 1) / 2 + (r - j)] = Dm[r * LD + j];
     }
     // (e) C_{k+1} = A_{k+1,k} D_k^T
     if (k + 1 < nb) {
-      for (int idx = tid; idx < BP * BP; idx += 128) {
-        const int i = idx / BP, j = idx % BP;
-        A[i * LD + j] = entry2d<T>(t, si, ke, scale, k + 1, i, k, j);
+      for (int e = tid; e < 6 * BP; e += kFacThreads) {
+        const int i = e / 6, m = 2 * (i >> 1) - 2 + e % 6;
+        anz[e] = (m >= 0 && m < BP) ? entry2d<T>(t, si, ke, scale, k + 1, i, k, m) : T(0);
       }
       __syncthreads();
-      for (int idx = tid; idx < BP * BP; idx += 128) {
-        const int i = idx / BP, j = idx % BP;
-        T s = T(0);
-        for (int m = 0; m <= j; ++m) s += A[i * LD + m] * Dm[j * LD + m];
-        Cm[i * LD + j] = s;
-      }
-      __syncthreads();
-      T* Cg = fb + (int64_t)(k + 1) * STAGE;
-      for (int idx = tid; idx < BP * BP; idx += 128) {
-        const int j = idx / BP, i = idx % BP;
-        Cg[j * BP + i] = Cm[i * LD + j];
+      const int i = tid % BP, jg = tid / BP;
+      if (jg < NJ) {
+        const int m0 = 2 * (i >> 1) - 2;
+        T a[6];
+#pragma unroll
+        for (int w = 0; w < 6; ++w) a[w] = anz[6 * i + w];
+        T* Cg = fb + (int64_t)(k + 1) * STAGE;
+        for (int j = jg; j < BP; j += NJ) {
+          T c = T(0);
+#pragma unroll
+          for (int w = 0; w < 6; ++w) {
+            const int m = m0 + w;
+            if (m >= 0 && m <= j) c += a[w] * Dm[j * LD + m];
+          }
+          CT[j * BP + i] = c;
+          Cg[j * BP + i] = c;
+        }
       }
     }
     __syncthreads();
   }
-  if (tid == 0 && bad) {
+  if (tid == 0 && s_bad) {
     atomicExch(err, kErrPivot);
     atomicMin(bad_sub, sub);
   }
@@ -1919,7 +2111,7 @@ void run_schur(const DevTables& t, const DevFields& fld, const void* factor, con
 template <typename T, int BP>
 void run_factor(const DevTables& t, const DevFields& fld, void* factor, int* err, int* bad_sub,
                 cudaStream_t st) {
-  const size_t smem = (size_t)3 * BP * (BP + 1) * sizeof(T) + 64 * sizeof(T);
+  const size_t smem = factor2d_smem<T, BP>();
   auto kern = factor2d_kernel<T, BP>;
   const T* ke;
   const T* sc;
@@ -1930,7 +2122,7 @@ void run_factor(const DevTables& t, const DevFields& fld, void* factor, int* err
     ke = reinterpret_cast<const T*>(t.Ke32);
     sc = reinterpret_cast<const T*>(fld.scale32);
   }
-  kern<<<t.n_sub, 128, smem, st>>>(t, ke, sc, reinterpret_cast<T*>(factor), err, bad_sub);
+  kern<<<t.n_sub, kFacThreads, smem, st>>>(t, ke, sc, reinterpret_cast<T*>(factor), err, bad_sub);
 }
 
 template <typename T, int BP, int NR>
