@@ -5,7 +5,8 @@
 //    A_kk - C_k C_k^T is assembled in a global scratch matrix, factorised by a
 //    blocked right-looking Cholesky (32-wide panels through shared memory),
 //    inverted by blocked forward substitution (D_k = L_kk^-1), and
-//    C_{k+1} = A_{k+1,k} D_k^T is formed by a tiled product.  The factor layout
+//    C_{k+1} = A_{k+1,k} D_k^T is formed from the 27 nonzeros per row of the
+//    plane coupling A_{k+1,k}.  The factor layout
 //    is the one of the 2D path: [C_k (column-major) | D_k (packed lower,
 //    column-major)] per plane.
 //  * schur3d_kernel: one CTA per subdomain: w = f_I - K_IG x element by element,
@@ -45,10 +46,11 @@ __device__ T entry3d(const DevTables& t, const SubInfo& si, const T* ke, const T
   int xr, yr, zr, cr, xc, yc, zc, cc;
   row_node3(si, kr, r, xr, yr, zr, cr);
   row_node3(si, kc, c, xc, yc, zc, cc);
+  // nodes more than one element apart do not couple (checked before any load)
+  if (abs(xr - xc) > 1 || abs(yr - yc) > 1 || abs(zr - zc) > 1) return T(0);
   const bool fr = t.fixed[3 * node3(t, xr, yr, zr) + cr];
   const bool fc = t.fixed[3 * node3(t, xc, yc, zc) + cc];
   if (fr || fc) return (kr == kc && r == c) ? T(1) : T(0);
-  if (abs(xr - xc) > 1 || abs(yr - yc) > 1 || abs(zr - zc) > 1) return T(0);
   T sum = T(0);
   const int s = t.s;
   for (int ex = max(xr, xc) - 1; ex <= min(xr, xc); ++ex) {
@@ -65,6 +67,18 @@ __device__ T entry3d(const DevTables& t, const SubInfo& si, const T* ke, const T
     }
   }
   return sum;
+}
+
+// Column of the w-th possible nonzero of row i of the plane coupling
+// A_{k+1,k} (w = 9 (dy + 1) + 3 (dz + 1) + component, node (y + dy, z + dz) of
+// the plane before), or -1 when that node lies outside the interior plane or
+// row i is a padding row.
+__device__ __forceinline__ int nz_col3(const SubInfo& si, int i, int w, int BP) {
+  if (i >= si.bsz) return -1;
+  const int q = i / 3, y = q / si.icnt[2] + w / 9 - 1, z = q % si.icnt[2] + (w / 3) % 3 - 1;
+  if (y < 0 || y >= si.icnt[1] || z < 0 || z >= si.icnt[2]) return -1;
+  const int m = 3 * (y * si.icnt[2] + z) + w % 3;
+  return m < BP ? m : -1;
 }
 
 // C(i, j) += alpha * sum_m A(i, m) B(j, m) for i < M, j < N (j <= i when lower),
@@ -236,16 +250,37 @@ __global__ void __launch_bounds__(kT3) factor3d_kernel(DevTables t, const T* __r
       if (r >= j) Dg[j * BP - j * (j - 1) / 2 + (r - j)] = D[(int64_t)r * BP + j];
     }
     if (k + 1 < si.nb) {
-      for (int q = tid; q < PC; q += kT3) {
-        const int i = q / BP, j = q % BP;
-        A[q] = entry3d<T>(t, si, ke, scale, k + 1, i, k, j);
+      // C_{k+1} = A_{k+1,k} D_k^T.  Row i of A_{k+1,k} (node (y, z) of plane
+      // k + 1) couples only to the nodes (y + dy, z + dz), |dy|, |dz| <= 1, of
+      // plane k: 27 columns w = 9 (dy + 1) + 3 (dz + 1) + component.  Their
+      // entries go to anz[w * BP + i] (the scratch A, free after the inverse).
+      T* anz = A;
+      for (int q = tid; q < 27 * BP; q += kT3) {
+        const int w = q / BP, i = q % BP;
+        const int m = nz_col3(si, i, w, BP);
+        anz[q] = m >= 0 ? entry3d<T>(t, si, ke, scale, k + 1, i, k, m) : T(0);
       }
       __syncthreads();
-      // C_{k+1}^T = D N^T, stored row-major = C_{k+1} column-major
+      // C stored column-major: Cg[j * BP + i] = sum_w anz(i, w) D(j, m_w), m_w <= j
       T* Cg = fb + (int64_t)(k + 1) * STAGE;
-      for (int q = tid; q < PC; q += kT3) Cg[q] = T(0);
-      __syncthreads();
-      cta_gemm<T>(BP, BP, BP, D, BP, 1, A, BP, 1, Cg, BP, 1, T(1), false, sA, sB);
+      const int cy = 3 * si.icnt[2];
+      for (int q = tid; q < PC; q += kT3) {
+        const int j = q / BP, i = q % BP;
+        T c = T(0);
+        if (i < si.bsz) {
+          const int n = i / 3, y = n / si.icnt[2], z = n - y * si.icnt[2], base = 3 * n;
+          const bool y0 = y > 0, y2 = y + 1 < si.icnt[1], z0 = z > 0, z2 = z + 1 < si.icnt[2];
+          const T* Dj = D + (int64_t)j * BP;
+#pragma unroll
+          for (int w = 0; w < 27; ++w) {
+            const int dy = w / 9 - 1, dz = (w / 3) % 3 - 1;
+            const bool ok = (dy < 0 ? y0 : (dy > 0 ? y2 : true)) && (dz < 0 ? z0 : (dz > 0 ? z2 : true));
+            const int m = base + dy * cy + 3 * dz + w % 3;
+            if (ok && m <= j) c += anz[w * BP + i] * Dj[m];
+          }
+        }
+        Cg[q] = c;
+      }
     }
     __syncthreads();
   }
