@@ -136,13 +136,14 @@ typedef struct {
                           iteration; IMPLICIT applies it by block substitution */
   int use_graph;       /* capture PCG iterations in a CUDA graph (1) */
   int check_every;     /* PCG iterations between host convergence checks (16) */
-  int tensor_form;     /* 1: form the local Schur complements with W^T W on the tensor
-                          cores at FP64 accuracy (Ozaki splitting into BF16 slices, FP32
-                          accumulation): rings of 128 and 256 in the EXPLICIT form, rings
-                          of 256 in the AUTO form of FP64 (whose rings of 128 keep the
-                          faster double-float formation), and every ring of 128 or 256 in
-                          FP32 (W from the FP32 factors, S_i rounded once to FP32);
-                          0: on the FP64 / FP32 pipes (1) */
+  int tensor_form;     /* 1: form the FP64 local Schur complements with W^T W on the
+                          tensor cores at FP64 accuracy (Ozaki splitting into BF16 slices,
+                          FP32 accumulation): rings of 128 and 256 in the EXPLICIT form,
+                          rings of 256 in the AUTO form (whose rings of 128 keep the
+                          faster double-float formation); FP32 contexts form theirs on
+                          the FP32 pipes; 2: as 1, and FP32 contexts on the tensor cores
+                          too (W from the FP32 factors, S_i rounded once to FP32);
+                          0: every formation on the FP64 / FP32 pipes (1) */
 } ddel_options;
 
 typedef struct {

@@ -380,11 +380,13 @@ int factor_launch(ddel_ctx* ctx, int prec) {
       cudaError_t e = cudaMalloc(&ctx->form_work[prec], we * (prec ? 4 : 8));
       if (e != cudaSuccess) return fail(ctx, DDEL_ENOMEM, "explicit Schur scratch allocation");
     }
-    // S_i with W^T W on the tensor cores: FP64-accurate for the native FP64
+    // S_i with W^T W on the tensor cores, FP64-accurate: for the native FP64
     // form and the double-float form's rings of 256 (for rings of 128 the
     // double-float form keeps its own, faster double-float formation); the
-    // FP32 form from BF16 slices of its FP32 W, to 24 bits
-    const bool tc = ctx->opt.tensor_form && tensor_form_available(ctx->T) &&
+    // FP32 form only with tensor_form = 2 (its FP32-pipe formation is the
+    // faster one, the FP32 pipes being wide)
+    const int tf = ctx->opt.tensor_form;
+    const bool tc = (tf == 2 || (tf == 1 && prec == 0)) && tensor_form_available(ctx->T) &&
                     !(prec == 0 && ctx->opt.schur_mode == DDEL_SCHUR_AUTO && NR <= 128);
     if (tc) {
       if (!ctx->form_work[prec]) {
@@ -1574,7 +1576,7 @@ int ddel_autotune(ddel_ctx* ctx, const char* cache_path, int* chosen_mode, int* 
   }
   if (has_explicit) {
     forms.push_back({DDEL_SCHUR_EXPLICIT, 0});
-    if (tc_ok) forms.push_back({DDEL_SCHUR_EXPLICIT, 1});
+    if (tc_ok) forms.push_back({DDEL_SCHUR_EXPLICIT, prec ? 2 : 1});
   }
   const int checks[3] = {8, 16, 32};
   double best = 1e300;

@@ -159,7 +159,7 @@ __device__ __forceinline__ T entry2d(const DevTables& t, const SubInfo& si, cons
 //      consecutive columns, assembled once per row.
 // The FP64 pipe of this GPU retires one warp instruction per 16 clocks per SM
 // whatever the number of active lanes, so the sequential parts are laid out
-// to keep the lanes of each FP64 instruction busy, and the pivots take one
+// to keep the lanes of each FP64 instruction busy, and the FP64 pivots take one
 // reciprocal square root (Newton) instead of a square root and divisions.
 // A pivot that is not positive is replaced by 1 and reported (kErrPivot, the
 // lowest such subdomain in bad_sub).
@@ -169,20 +169,15 @@ constexpr int kFacThreads = 256;
 // r <- r (3 - d r^2) / 2, from the single-precision estimate; each step
 // doubles the correct bits, two take the estimate's 23 past double precision
 // (a few units in the last place).  Outside the single-precision range the
-// library square root and division serve.
-template <typename T>
-__device__ __forceinline__ T pivot_rsqrt(T d) {
-  if constexpr (sizeof(T) == 8) {
-    if (d > 1e-36 && d < 1e36) {
-      double r = (double)rsqrtf((float)d);
-      r = r * fma(-0.5 * d, r * r, 1.5);
-      r = r * fma(-0.5 * d, r * r, 1.5);
-      return r;
-    }
-    return 1.0 / sqrt(d);
-  } else {
-    return T(1) / sqrt(d);
+// library square root and division serve.  (FP64 only.)
+__device__ __forceinline__ double pivot_rsqrt(double d) {
+  if (d > 1e-36 && d < 1e36) {
+    double r = (double)rsqrtf((float)d);
+    r = r * fma(-0.5 * d, r * r, 1.5);
+    r = r * fma(-0.5 * d, r * r, 1.5);
+    return r;
   }
+  return 1.0 / sqrt(d);
 }
 
 template <typename T>
@@ -283,14 +278,28 @@ __global__ void __launch_bounds__(kFacThreads, BP == 32 ? 4 : 1)
             if (lane == 0) s_bad = 1;
             d = T(1);
           }
-          const T rj = pivot_rsqrt(d);
+          // FP64: one reciprocal square root, products; FP32 (cheap divisions
+          // on this GPU): the correctly rounded square root and quotients
+          T ljj, rj;
+          if constexpr (sizeof(T) == 8) {
+            rj = pivot_rsqrt(d);
+            ljj = d * rj;
+          } else {
+            ljj = sqrt(d);
+            rj = T(1) / ljj;
+          }
           __syncwarp();
           if (lane == 0) {
-            A[j * LD + j] = d * rj;
+            A[j * LD + j] = ljj;
             rdiag[j] = rj;
           }
           const int i = j + 1 + lane;
-          if (i < j0 + PW) A[i * LD + j] *= rj;
+          if (i < j0 + PW) {
+            if constexpr (sizeof(T) == 8)
+              A[i * LD + j] *= rj;
+            else
+              A[i * LD + j] /= ljj;
+          }
           __syncwarp();
           // update of the block's trailing lower triangle (m rows), one lane per entry
           const int m = j0 + PW - 1 - j;
@@ -319,7 +328,10 @@ __global__ void __launch_bounds__(kFacThreads, BP == 32 ? 4 : 1)
             T v = x[c];
 #pragma unroll
             for (int m = 0; m < c; ++m) v -= x[m] * A[(j0 + c) * LD + j0 + m];
-            x[c] = v * rdiag[j0 + c];
+            if constexpr (sizeof(T) == 8)
+              x[c] = v * rdiag[j0 + c];
+            else
+              x[c] = v / A[(j0 + c) * LD + j0 + c];
           }
 #pragma unroll
           for (int c = 0; c < PW; ++c) A[i * LD + j0 + c] = x[c];
@@ -365,7 +377,10 @@ __global__ void __launch_bounds__(kFacThreads, BP == 32 ? 4 : 1)
         T v = r == c ? T(1) : T(0);
 #pragma unroll
         for (int m = 0; m < r; ++m) v -= A[(p0 + r) * LD + p0 + m] * x[m];
-        x[r] = r >= c ? v * rdiag[p0 + r] : T(0);
+        if constexpr (sizeof(T) == 8)
+          x[r] = r >= c ? v * rdiag[p0 + r] : T(0);
+        else
+          x[r] = r >= c ? v / A[(p0 + r) * LD + p0 + r] : T(0);
       }
 #pragma unroll
       for (int r = 0; r < 8; ++r) Dm[(p0 + r) * LD + p0 + c] = x[r];
@@ -1121,8 +1136,8 @@ __global__ void __launch_bounds__(256) schur_explicit_kernel(DevTables t, const 
 
 // Native FP64 form of the explicit apply, laid out like the double-float one:
 // each thread owns two adjacent rows and JN columns, reading both rows' entries
-// of a column as one 16-byte load (S_i column-major FP64), with two
-// accumulators per row; the H column groups of a row are added in group order.
+// of a column as one 16-byte load (S_i column-major FP64), with one
+// accumulator per row; the H column groups of a row are added in group order.
 // GB300 issues two DFMA per clock per SM, so this product is bound by the FP64
 // pipe (2 n_ring^2 flop per subdomain) rather than by the bytes it streams.
 template <int NR>
@@ -1147,20 +1162,23 @@ __global__ void __launch_bounds__(256, NR <= 128 ? 7 : 5) schur_explicit_f64_ker
   const int rp = tid % RP, h = tid / RP;
   const int r0 = half * RH + 2 * rp;
   const double2* Sc = reinterpret_cast<const double2*>(Sexp + (int64_t)sub * NR * NR);
-  double a0 = 0.0, b0 = 0.0, a1 = 0.0, b1 = 0.0;
-#pragma unroll 8
-  for (int q = 0; q < JN; q += 2) {
-    const int j = h * JN + q;
-    const double2 s0 = Sc[(j * NR + r0) >> 1];
-    const double2 s1 = Sc[((j + 1) * NR + r0) >> 1];
-    const double x0 = xr[j], x1 = xr[j + 1];
-    a0 = fma(s0.x, x0, a0);
-    a1 = fma(s0.y, x0, a1);
-    b0 = fma(s1.x, x1, b0);
-    b1 = fma(s1.y, x1, b1);
+  // one accumulator per row: with dozens of warps sharing an SM's FP64 pipe a
+  // warp's FMAs are issued far enough apart to need no second chain, and the
+  // extra additions would cost pipe cycles.  Column groups wholly beyond the
+  // ring (zero padding of subdomains at the domain boundary) are skipped.
+  double a0 = 0.0, a1 = 0.0;
+  if (h * JN < si.n_ring) {
+#pragma unroll 16
+    for (int q = 0; q < JN; ++q) {
+      const int j = h * JN + q;
+      const double2 s0 = Sc[(j * NR + r0) >> 1];
+      const double x0 = xr[j];
+      a0 = fma(s0.x, x0, a0);
+      a1 = fma(s0.y, x0, a1);
+    }
   }
-  part[2 * tid] = a0 + b0;
-  part[2 * tid + 1] = a1 + b1;
+  part[2 * tid] = a0;
+  part[2 * tid + 1] = a1;
   __syncthreads();
   double d[1] = {0.0};
   const int row = half * RH + tid;

@@ -87,7 +87,7 @@ def test_tensor_core_fp32_form(name):
     from paper_1501_06211_gb300 import ddel
     cfg = CASES[name]
     rho, fixed, f, dec, K, dds = oracle(cfg)
-    s = ddel.Solver(cfg, precision=ddel.DDEL_FP32, schur_mode=1, tensor_form=1, tol=1e-9, max_it=20000,
+    s = ddel.Solver(cfg, precision=ddel.DDEL_FP32, schur_mode=1, tensor_form=2, tol=1e-9, max_it=20000,
                     max_cycles=60, inner_tol=0.1)
     s.assemble(rho)
     s.factor()
