@@ -475,6 +475,7 @@ __global__ void __launch_bounds__(kT3) schur3d_kernel(DevTables t, const T* __re
 // thread keeps eight loads in flight ahead of its products.  (An L2 bulk prefetch of the next block step,
 // 75 MB over all subdomains, evicted lines before their use: slower.)
 constexpr int kT3D = 384;  // 12 warps x 16 rows: blocks of up to 192 rows in one pass
+constexpr int kTriSlots = 4;  // chunks of a triangular pass
 
 __host__ __device__ __forceinline__ int64_t pad16(int64_t v) { return (v + 15) & ~int64_t(15); }
 
@@ -536,6 +537,15 @@ __global__ void __launch_bounds__(kT3D, 3) schur3d_df_kernel(DevTables t, const 
   const SubInfo si = t.subs[sub];
   const int s = t.s, s1 = s + 1, nloc = s1 * s1 * s1, NM = t.BP;
   const int n = si.bsz, nb = si.nb, nh = (n + 1) / 2;
+  // triangular passes: kTriSlots column (forward) / row (backward) chunks of
+  // width wc, chunk c serving the rows r >= c wc (forward) or the outputs
+  // j < (c + 1) wc (backward)
+  const int wc = (n + kTriSlots - 1) / kTriSlots;
+  int tri_f = 0, tri_b = 0;  // work items of the forward and backward passes
+  for (int c = 0; c * wc < n; ++c) {
+    tri_f += n - c * wc;
+    tri_b += min(n, (c + 1) * wc);
+  }
   const int szC = (int)pad16((int64_t)n * n), szD = (int)pad16((int64_t)n * (n + 1) / 2);
   const float2* fw = factor + off[sub];
   const float2* bw = fw + (int64_t)nb * szD + (int64_t)(nb - 1) * szC;
@@ -545,6 +555,7 @@ __global__ void __launch_bounds__(kT3D, 3) schur3d_df_kernel(DevTables t, const 
   float2* xloc = vbuf + NM;                             // 3 * nloc
   float2* ke = xloc + 3 * nloc;                         // 576
   float2* sc = ke + 576;                                // s^3
+  float2* part = sc + s * s * s;                        // kTriSlots * NM: triangular-pass partials
   for (int i = tid; i < 576; i += kT3D) ke[i] = df_from(Ke_g[i]);
   for (int i = tid; i < s * s * s; i += kT3D) {
     const int a = i / (s * s), b = (i / s) % s, c = i % s;
@@ -596,15 +607,26 @@ __global__ void __launch_bounds__(kT3D, 3) schur3d_df_kernel(DevTables t, const 
       }
     }
     __syncthreads();
-    for (int r0 = 0; r0 < n; r0 += kT3D / 2) {
-      const int r = r0 + warp * 16 + hl;
-      float ah = 0.f, al = 0.f;
-      if (r < n) {
-        const int j0 = hh ? nh : 0, j1 = min(hh ? n : nh, r + 1);
-        if (j0 < j1) df_dot(D, j0 * n - j0 * (j0 - 1) / 2 + (r - j0), n - j0 - 1, -1, vbuf, j0, j1, ah, al);
+    // triangular pass y_r = sum_{j <= r} D_k(r, j) v_j: column chunk c of
+    // width wc for every row r >= c wc, consecutive threads on consecutive
+    // rows of one chunk (coalesced); partials summed in chunk order
+    for (int q = tid; q < tri_f; q += kT3D) {
+      int c = 0, r = q;
+      while (r >= n - c * wc) {
+        r -= n - c * wc;
+        ++c;
       }
-      df_half_sum(ah, al);
-      if (r < n && hh == 0) ybuf[k * NM + r] = make_float2(ah, al);
+      r += c * wc;
+      const int j0 = c * wc, j1 = min(j0 + wc, r + 1);
+      float ah = 0.f, al = 0.f;
+      df_dot(D, j0 * n - j0 * (j0 - 1) / 2 + (r - j0), n - j0 - 1, -1, vbuf, j0, j1, ah, al);
+      part[c * NM + r] = make_float2(ah, al);
+    }
+    __syncthreads();
+    for (int r = tid; r < n; r += kT3D) {
+      float2 y = part[r];
+      for (int c = 1; c * wc <= r; ++c) df_add2(y.x, y.y, part[c * NM + r].x, part[c * NM + r].y);
+      ybuf[k * NM + r] = y;
     }
     __syncthreads();
   }
@@ -626,15 +648,26 @@ __global__ void __launch_bounds__(kT3D, 3) schur3d_df_kernel(DevTables t, const 
       }
     }
     __syncthreads();
-    for (int j0 = 0; j0 < n; j0 += kT3D / 2) {
-      const int j = j0 + warp * 16 + hl;
-      float ah = 0.f, al = 0.f;
-      if (j < n) {
-        const int i0 = max(j, hh ? nh : 0), i1 = hh ? n : nh;
-        if (i0 < i1) df_dot(Db, i0 * (i0 + 1) / 2 + j, i0 + 1, 1, vbuf, i0, i1, ah, al);
+    // triangular pass t_j = sum_{i >= j} D_k(i, j) v_i over the row-major
+    // copy: row chunk c (rows [c wc, c wc + wc)) for every output j below its
+    // end, consecutive threads on consecutive outputs (coalesced)
+    for (int q = tid; q < tri_b; q += kT3D) {
+      int c = 0, j = q;
+      while (j >= min(n, (c + 1) * wc)) {
+        j -= min(n, (c + 1) * wc);
+        ++c;
       }
-      df_half_sum(ah, al);
-      if (j < n && hh == 0) ybuf[k * NM + j] = make_float2(ah, al);
+      const int i0 = max(j, c * wc), i1 = min(n, (c + 1) * wc);
+      float ah = 0.f, al = 0.f;
+      df_dot(Db, i0 * (i0 + 1) / 2 + j, i0 + 1, 1, vbuf, i0, i1, ah, al);
+      part[c * NM + j] = make_float2(ah, al);
+    }
+    __syncthreads();
+    for (int j = tid; j < n; j += kT3D) {
+      const int c0 = j / wc;
+      float2 y = part[c0 * NM + j];
+      for (int c = c0 + 1; c * wc < n; ++c) df_add2(y.x, y.y, part[c * NM + j].x, part[c * NM + j].y);
+      ybuf[k * NM + j] = y;
     }
     __syncthreads();
   }
@@ -736,10 +769,14 @@ void launch_build_df3(const DevTables& t, const double* factor, const int64_t* o
   build_df3_kernel<<<t.n_sub, 256, 0, st>>>(t, factor, off, out);
 }
 
+size_t schur3d_df_smem(const DevTables& t);
+
 void launch_schur3d_df(const DevTables& t, const DevFields& fld, const float2* factor, const int64_t* off,
                        const SchurIO& io, cudaStream_t st) {
-  schur3d_df_kernel<<<t.n_sub, kT3D, schur3d_smem(t, 0), st>>>(t, t.Ke64, fld.scale64, factor, off, io);
+  schur3d_df_kernel<<<t.n_sub, kT3D, schur3d_df_smem(t), st>>>(t, t.Ke64, fld.scale64, factor, off, io);
 }
+
+size_t schur3d_df_smem(const DevTables& t) { return schur3d_smem(t, 0) + (size_t)kTriSlots * t.BP * 8; }
 
 size_t schur3d_smem(const DevTables& t, int precision) {
   const int s = t.s, nloc = (s + 1) * (s + 1) * (s + 1);

@@ -24,6 +24,8 @@ def main(argv=None):
     ap.add_argument("--learner", default="none", choices=["none", "history", "cnn", "cnn+history"])
     ap.add_argument("--tol-eta", type=float, default=0.0,
                     help="topology steps: adaptive tolerance from successive compliances (0: --tol)")
+    ap.add_argument("--sub", type=int, default=0,
+                    help="subdomain edge in elements instead of the workload's own (0: keep)")
     args = ap.parse_args(argv)
     sys.path.insert(0, os.getcwd())
     import torch
@@ -31,6 +33,8 @@ def main(argv=None):
     from paper_1501_06211_gb300 import ddel
 
     cfg = workloads.config(args.workload)
+    if args.sub > 0:
+        cfg["sub"] = args.sub
     prec = {"fp64": ddel.DDEL_FP64, "fp32": ddel.DDEL_FP32, "mixed": ddel.DDEL_MIXED}[args.precision]
     mode = {"implicit": 0, "explicit": 1, "auto": 2}[args.schur]
     s = ddel.Solver(cfg, precision=prec, schur_mode=mode, tol=args.tol, max_it=20000)
