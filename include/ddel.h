@@ -141,8 +141,10 @@ typedef struct {
                           FP32 accumulation): rings of 128 and 256 in the EXPLICIT form,
                           rings of 256 in the AUTO form (whose rings of 128 keep the
                           faster double-float formation); FP32 contexts form theirs on
-                          the FP32 pipes; 2: as 1, and FP32 contexts on the tensor cores
-                          too (W from the FP32 factors, S_i rounded once to FP32);
+                          the FP32 pipes; 2: as 1, and also FP32 contexts on the tensor
+                          cores (W from the FP32 factors, S_i rounded once to FP32) and
+                          the C_k C_k^T of each plane of the FP64 3D factorisation (FP64
+                          accuracy; slower than the FP64 pipe at these sizes);
                           0: every formation on the FP64 / FP32 pipes (1) */
 } ddel_options;
 

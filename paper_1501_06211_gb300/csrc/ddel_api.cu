@@ -34,6 +34,7 @@ struct ddel_ctx {
   std::vector<void*> allocs;
   void* factor[2] = {nullptr, nullptr};
   void* work3d[2] = {nullptr, nullptr};  // 3D factorisation scratch
+  size_t work3d_bytes[2] = {0, 0};
   void* sexp[2] = {nullptr, nullptr};  // explicit local Schur complements (2D)
   void* form_work[2] = {nullptr, nullptr};  // W = L^-1 K_IG scratch of the widest rings
   void* tc_work = nullptr;             // BF16 slices of W and column exponents (tensor-core formation)
@@ -358,13 +359,22 @@ int factor_launch(ddel_ctx* ctx, int prec) {
   }
   const int init[2] = {0, 0x7fffffff};
   CK(cudaMemcpyAsync(ctx->err, init, sizeof(init), cudaMemcpyHostToDevice, ctx->stream));
-  if (ctx->T.dim == 3 && !ctx->work3d[prec]) {
-    cudaError_t e = cudaMalloc(&ctx->work3d[prec], factor3d_work_elems(ctx->T) * (prec ? 4 : 8));
-    if (e != cudaSuccess) return fail(ctx, DDEL_ENOMEM, "3D factor scratch");
+  if (ctx->T.dim == 3) {
+    // the scratch grows when the tensor-core planes are switched on later
+    const size_t need = factor3d_work_elems(ctx->T, prec, ctx->opt.tensor_form) * (prec ? 4 : 8);
+    if (ctx->work3d[prec] && ctx->work3d_bytes[prec] < need) {
+      CK(cudaStreamSynchronize(ctx->stream));
+      cudaFree(ctx->work3d[prec]);
+      ctx->work3d[prec] = nullptr;
+    }
+    if (!ctx->work3d[prec]) {
+      cudaError_t e = cudaMalloc(&ctx->work3d[prec], need);
+      if (e != cudaSuccess) return fail(ctx, DDEL_ENOMEM, "3D factor scratch");
+      ctx->work3d_bytes[prec] = need;
+    }
   }
-  launch_factor(ctx->T, ctx->F, prec, ctx->factor[prec], ctx->work3d[prec], ctx->err, ctx->bad_sub,
-                ctx->stream);
-  ctx->launches += 1;
+  ctx->launches += launch_factor(ctx->T, ctx->F, prec, ctx->factor[prec], ctx->work3d[prec], ctx->err,
+                                 ctx->bad_sub, ctx->opt.tensor_form, ctx->stream);
   CK(cudaGetLastError());
   ctx->factored[prec] = false;
   ctx->explicit_ok[prec] = false;

@@ -1091,6 +1091,40 @@ __global__ void __launch_bounds__(256) form_syrk2d_kernel(DevTables t, const T* 
 
 #include "ddel_ozaki.cuh"
 
+// Tile policy of the 2D formation: S_i = K_GG - W^T W, K_GG by element
+// entries of the ring, the result into the dense NR x NR S_i (FP64 or FP32).
+template <int NR, typename TO>
+struct FormTile {
+  const double* Ke;
+  const double* scale;
+  TO* Sexp;
+  static size_t smem(const DevTables& t) { return (64 + (size_t)t.s * t.s) * 8 + 2 * kOzTile * 4; }
+  __device__ int rows(const DevTables& t, const SubInfo& si) const { return si.nb * t.BP; }
+  __device__ void setup(const DevTables& t, const SubInfo& si, int ta, int tb, unsigned char* sm) const {
+    double* ke = reinterpret_cast<double*>(sm);
+    double* sc = ke + 64;
+    int* rl = reinterpret_cast<int*>(sc + t.s * t.s);
+    const int s = t.s;
+    for (int i = threadIdx.x; i < 64; i += blockDim.x) ke[i] = Ke[i];
+    for (int i = threadIdx.x; i < s * s; i += blockDim.x)
+      sc[i] = scale[(int64_t)(si.lo[0] + i / s) * t.ne[1] + si.lo[1] + i % s];
+    for (int j = threadIdx.x; j < 2 * kOzTile; j += blockDim.x) {
+      const int jr = (j < kOzTile ? ta : tb) * kOzTile + j % kOzTile;
+      rl[j] = jr < si.n_ring ? t.ring_loc[si.ring_off + jr] : -1;
+    }
+  }
+  __device__ double value(const DevTables& t, const SubInfo&, const unsigned char* sm, int, int, int li,
+                          int lj) const {
+    const double* ke = reinterpret_cast<const double*>(sm);
+    const double* sc = ke + 64;
+    const int* rl = reinterpret_cast<const int*>(sc + t.s * t.s);
+    return kgg_entry2d<double>(t.s, ke, sc, rl[li], rl[kOzTile + lj]);
+  }
+  __device__ void store(const DevTables&, const SubInfo&, int sub, int gi, int gj, double v) const {
+    Sexp[(int64_t)sub * NR * NR + (int64_t)gi * NR + gj] = (TO)v;
+  }
+};
+
 // y_ring = S_i x_ring for every subdomain.
 template <typename T, int NR>
 __global__ void __launch_bounds__(256) schur_explicit_kernel(DevTables t, const T* __restrict__ Sexp,
@@ -2207,7 +2241,7 @@ void run_form(const DevTables& t, const DevFields& fld, const void* factor, void
 }  // namespace
 
 size_t ozaki_smem_bytes(const DevTables& t) {
-  return (size_t)kOzStages * 32768 + 64 * 8 + (size_t)t.s * t.s * 8 + 4 * kOzTile * 4 + 64;
+  return (size_t)kOzStages * 32768 + 2 * kOzTile * 4 + FormTile<128, double>::smem(t) + 64;
 }
 
 int ozaki_kp(const DevTables& t) { return ((t.nb_max * t.BP + kOzKC - 1) / kOzKC) * kOzKC; }
@@ -2272,13 +2306,14 @@ void launch_schur_form_tc(const DevTables& t, const DevFields& fld, int precisio
     else
       form_w2d_kernel<double, 96, 256, kFormGC><<<dim3(t.n_sub, 256 / kFormGC), 256, form_w_smem<double, 96, 256>(t),
                                                   st>>>(t, t.Ke64, fld.scale64, fac, W);
-    ozaki_slice_kernel<double><<<dim3(t.n_sub, NR / 32), 256, 0, st>>>(t, W, NR, Kp, S, Wsl, expo);
+    const OzSlab src{(int64_t)t.nb_max * t.BP * NR, 0, NR, -1, NR};
+    ozaki_slice_kernel<double><<<dim3(t.n_sub, NR / 32), 256, 0, st>>>(t, W, src, NR, Kp, S, Wsl, expo);
     if (NR == 128)
-      ozaki_syrk_kernel<128, double><<<dim3(t.n_sub, 1), kOzThreads, sm, st>>>(
-          t, t.Ke64, fld.scale64, Wsl, expo, Kp, S, reinterpret_cast<double*>(Sexp), err);
+      ozaki_syrk_kernel<128, FormTile<128, double>><<<dim3(t.n_sub, 1), kOzThreads, sm, st>>>(
+          t, FormTile<128, double>{t.Ke64, fld.scale64, reinterpret_cast<double*>(Sexp)}, Wsl, expo, Kp, S, err);
     else
-      ozaki_syrk_kernel<256, double><<<dim3(t.n_sub, 3), kOzThreads, sm, st>>>(
-          t, t.Ke64, fld.scale64, Wsl, expo, Kp, S, reinterpret_cast<double*>(Sexp), err);
+      ozaki_syrk_kernel<256, FormTile<256, double>><<<dim3(t.n_sub, 3), kOzThreads, sm, st>>>(
+          t, FormTile<256, double>{t.Ke64, fld.scale64, reinterpret_cast<double*>(Sexp)}, Wsl, expo, Kp, S, err);
   } else {
     float* W = reinterpret_cast<float*>(work);
     const float* fac = reinterpret_cast<const float*>(factor);
@@ -2291,13 +2326,14 @@ void launch_schur_form_tc(const DevTables& t, const DevFields& fld, int precisio
     else
       form_w2d_kernel<float, 96, 256, kFormGC><<<dim3(t.n_sub, 256 / kFormGC), 256, form_w_smem<float, 96, 256>(t),
                                                  st>>>(t, t.Ke32, fld.scale32, fac, W);
-    ozaki_slice_kernel<float><<<dim3(t.n_sub, NR / 32), 256, 0, st>>>(t, W, NR, Kp, S, Wsl, expo);
+    const OzSlab src{(int64_t)t.nb_max * t.BP * NR, 0, NR, -1, NR};
+    ozaki_slice_kernel<float><<<dim3(t.n_sub, NR / 32), 256, 0, st>>>(t, W, src, NR, Kp, S, Wsl, expo);
     if (NR == 128)
-      ozaki_syrk_kernel<128, float><<<dim3(t.n_sub, 1), kOzThreads, sm, st>>>(
-          t, t.Ke64, fld.scale64, Wsl, expo, Kp, S, reinterpret_cast<float*>(Sexp), err);
+      ozaki_syrk_kernel<128, FormTile<128, float>><<<dim3(t.n_sub, 1), kOzThreads, sm, st>>>(
+          t, FormTile<128, float>{t.Ke64, fld.scale64, reinterpret_cast<float*>(Sexp)}, Wsl, expo, Kp, S, err);
     else
-      ozaki_syrk_kernel<256, float><<<dim3(t.n_sub, 3), kOzThreads, sm, st>>>(
-          t, t.Ke64, fld.scale64, Wsl, expo, Kp, S, reinterpret_cast<float*>(Sexp), err);
+      ozaki_syrk_kernel<256, FormTile<256, float>><<<dim3(t.n_sub, 3), kOzThreads, sm, st>>>(
+          t, FormTile<256, float>{t.Ke64, fld.scale64, reinterpret_cast<float*>(Sexp)}, Wsl, expo, Kp, S, err);
   }
 }
 
@@ -2398,10 +2434,10 @@ cudaError_t configure_kernels() {
   DDEL_CFG((form_syrk2d_kernel<float, 96, 256, kFormTQ>));
   // the update kernel's staged face tables plus the coarse variants' static
   // reduction arrays exceed the default 48 KB
-  DDEL_CFG((ozaki_syrk_kernel<128, double>));
-  DDEL_CFG((ozaki_syrk_kernel<256, double>));
-  DDEL_CFG((ozaki_syrk_kernel<128, float>));
-  DDEL_CFG((ozaki_syrk_kernel<256, float>));
+  DDEL_CFG((ozaki_syrk_kernel<128, FormTile<128, double>>));
+  DDEL_CFG((ozaki_syrk_kernel<256, FormTile<256, double>>));
+  DDEL_CFG((ozaki_syrk_kernel<128, FormTile<128, float>>));
+  DDEL_CFG((ozaki_syrk_kernel<256, FormTile<256, float>>));
   DDEL_CFG((form_w2d_kernel<double, 32, 128, kFormGC>));
   DDEL_CFG((form_w2d_kernel<float, 32, 128, kFormGC>));
   DDEL_CFG((batch_pcg_kernel));
@@ -2428,12 +2464,9 @@ void launch_assemble(const DevTables& t, const DevFields& fld, const double* rho
       t, fld, face_scaling, crosspoint_mode);
 }
 
-void launch_factor(const DevTables& t, const DevFields& fld, int precision, void* factor, void* work,
-                   int* err, int* bad_sub, cudaStream_t st) {
-  if (t.dim == 3) {
-    launch_factor3d(t, fld, precision, factor, work, err, bad_sub, st);
-    return;
-  }
+int launch_factor(const DevTables& t, const DevFields& fld, int precision, void* factor, void* work,
+                  int* err, int* bad_sub, int tensor, cudaStream_t st) {
+  if (t.dim == 3) return launch_factor3d(t, fld, precision, factor, work, err, bad_sub, tensor, st);
   if (precision == 0) {
     if (t.BP == 32) run_factor<double, 32>(t, fld, factor, err, bad_sub, st);
     else if (t.BP == 64) run_factor<double, 64>(t, fld, factor, err, bad_sub, st);
@@ -2443,6 +2476,7 @@ void launch_factor(const DevTables& t, const DevFields& fld, int precision, void
     else if (t.BP == 64) run_factor<float, 64>(t, fld, factor, err, bad_sub, st);
     else run_factor<float, 96>(t, fld, factor, err, bad_sub, st);
   }
+  return 1;
 }
 
 size_t schur_smem_bytes(const DevTables& t, int precision) {

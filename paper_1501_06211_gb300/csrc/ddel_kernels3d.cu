@@ -12,6 +12,8 @@
 //  * schur3d_kernel: one CTA per subdomain: w = f_I - K_IG x element by element,
 //    block forward/backward substitution with coalesced column reads of the
 //    factor, t into the local closure, y = (K^(i) [t; x])_G on the ring.
+#include <cuda_bf16.h>
+
 #include <cmath>
 
 #include "ddel_device.cuh"
@@ -218,7 +220,7 @@ template <typename T>
 __global__ void __launch_bounds__(kT3) factor3d_kernel(DevTables t, const T* __restrict__ Ke_g,
                                                        const T* __restrict__ scale,
                                                        T* __restrict__ factor, T* __restrict__ work,
-                                                       int* err, int* bad_sub) {
+                                                       int* err, int* bad_sub, int k0, int k1, int prepared) {
   const int BP = t.BP, PC = BP * BP, PD = BP * (BP + 1) / 2, STAGE = PC + PD;
   const int sub = blockIdx.x, tid = threadIdx.x;
   const SubInfo si = t.subs[sub];
@@ -231,15 +233,19 @@ __global__ void __launch_bounds__(kT3) factor3d_kernel(DevTables t, const T* __r
   T* A = work + (int64_t)sub * 2 * PC;  // A_kk, then L_kk, then A_{k+1,k}
   T* D = A + PC;                         // dense D_k
   T* fb = factor + si.factor_off;
-  for (int k = 0; k < si.nb; ++k) {
-    for (int q = tid; q < PC; q += kT3) {
-      const int i = q / BP, j = q % BP;
-      A[q] = j <= i ? entry3d<T>(t, si, ke, scale, k, i, k, j) : T(0);
-    }
-    __syncthreads();
-    if (k > 0) {  // A -= C_k C_k^T, C_k column-major in the factor
-      const T* Ck = fb + (int64_t)k * STAGE;
-      cta_gemm<T>(BP, BP, BP, Ck, 1, BP, Ck, 1, BP, A, BP, 1, T(-1), true, sA, sB);
+  for (int k = k0; k < min(k1, si.nb); ++k) {
+    // A_kk - C_k C_k^T, unless an earlier launch (the tensor-core product)
+    // left it in A already
+    if (!(prepared && k > 0)) {
+      for (int q = tid; q < PC; q += kT3) {
+        const int i = q / BP, j = q % BP;
+        A[q] = j <= i ? entry3d<T>(t, si, ke, scale, k, i, k, j) : T(0);
+      }
+      __syncthreads();
+      if (k > 0) {  // A -= C_k C_k^T, C_k column-major in the factor
+        const T* Ck = fb + (int64_t)k * STAGE;
+        cta_gemm<T>(BP, BP, BP, Ck, 1, BP, Ck, 1, BP, A, BP, 1, T(-1), true, sA, sB);
+      }
     }
     cta_cholesky<T>(A, BP, sA, sB, &bad);
     cta_tri_inverse<T>(A, D, BP, sA, sB);
@@ -738,18 +744,101 @@ __global__ void __launch_bounds__(256) build_df3_kernel(DevTables t, const doubl
   }
 }
 
+#include "ddel_ozaki.cuh"
+
+// Tile policy of the FP64 3D factorisation's C_k C_k^T on the tensor cores:
+// the product of plane k is taken from the assembled A_kk (element entries)
+// and the result A_kk - C_k C_k^T written, both triangles, into the
+// subdomain's scratch block A (row-major BP x BP), where factor3d_kernel
+// picks it up.  W is the block C_k itself (its column-major storage is W^T
+// row-major), sliced per row of C_k.
+struct Factor3Tile {
+  const double* Ke;
+  const double* scale;
+  double* work;
+  int plane;
+  static size_t smem(const DevTables&) { return 576 * 8; }
+  __device__ int rows(const DevTables& t, const SubInfo& si) const {
+    return plane >= 1 && plane < si.nb ? t.BP : 0;
+  }
+  __device__ void setup(const DevTables&, const SubInfo&, int, int, unsigned char* sm) const {
+    double* ke = reinterpret_cast<double*>(sm);
+    for (int i = threadIdx.x; i < 576; i += blockDim.x) ke[i] = Ke[i];
+  }
+  __device__ double value(const DevTables& t, const SubInfo& si, const unsigned char* sm, int gi, int gj, int,
+                          int) const {
+    return gi < t.BP && gj < t.BP
+               ? entry3d<double>(t, si, reinterpret_cast<const double*>(sm), scale, plane, gi, plane, gj)
+               : 0.0;
+  }
+  __device__ void store(const DevTables& t, const SubInfo&, int sub, int gi, int gj, double v) const {
+    if (gi < t.BP && gj < t.BP) work[(int64_t)sub * 2 * t.BP * t.BP + (int64_t)gi * t.BP + gj] = v;
+  }
+};
+
 }  // namespace
 
-size_t factor3d_work_elems(const DevTables& t) { return (size_t)t.n_sub * 2 * t.BP * t.BP; }
+// The tensor-core product serves FP64 contexts with planes of up to 256 rows
+// when asked for with tensor = 2.  It does not pay at these sizes: on
+// 96 x 48 x 48 (160-row planes, 432 subdomains) it takes 3.9 ms per plane plus
+// 0.55 ms of slicing against about 3 ms for the FP64-pipe product inside the
+// fused kernel -- 135 bulk-copy steps of 32 KB for 1 M multiply-adds each
+// (the 45 slice pairs of 3 chunks) leave the tensor cores waiting on L2.
+static bool factor3d_tc(const DevTables& t, int precision, int tensor) {
+  return tensor == 2 && precision == 0 && t.BP <= 256;
+}
+static int f3_nr(const DevTables& t) { return t.BP <= 128 ? 128 : 256; }
+static int f3_kp(const DevTables& t) { return ((t.BP + 63) / 64) * 64; }
+static size_t f3_slice_bytes(const DevTables& t) {
+  const int Kp = f3_kp(t);
+  return (size_t)t.n_sub * oz_slices(oz_bits(Kp), 54) * (f3_nr(t) / 128) * (Kp / 64) * 16384;
+}
 
-void launch_factor3d(const DevTables& t, const DevFields& fld, int precision, void* factor,
-                     void* work, int* err, int* bad_sub, cudaStream_t st) {
-  if (precision == 0)
-    factor3d_kernel<double><<<t.n_sub, kT3, 0, st>>>(t, t.Ke64, fld.scale64, (double*)factor,
-                                                     (double*)work, err, bad_sub);
-  else
-    factor3d_kernel<float><<<t.n_sub, kT3, 0, st>>>(t, t.Ke32, fld.scale32, (float*)factor,
-                                                    (float*)work, err, bad_sub);
+size_t factor3d_work_elems(const DevTables& t, int precision, int tensor) {
+  size_t e = (size_t)t.n_sub * 2 * t.BP * t.BP;
+  if (factor3d_tc(t, precision, tensor))  // slices and exponents of C_k (FP64 elements)
+    e += (f3_slice_bytes(t) + (size_t)t.n_sub * f3_nr(t) * 4 + 256 + 7) / 8;
+  return e;
+}
+
+int launch_factor3d(const DevTables& t, const DevFields& fld, int precision, void* factor, void* work, int* err,
+                    int* bad_sub, int tensor, cudaStream_t st) {
+  if (precision != 0) {
+    factor3d_kernel<float><<<t.n_sub, kT3, 0, st>>>(t, t.Ke32, fld.scale32, (float*)factor, (float*)work, err,
+                                                    bad_sub, 0, t.nb_max, 0);
+    return 1;
+  }
+  if (!factor3d_tc(t, precision, tensor)) {
+    factor3d_kernel<double><<<t.n_sub, kT3, 0, st>>>(t, t.Ke64, fld.scale64, (double*)factor, (double*)work, err,
+                                                     bad_sub, 0, t.nb_max, 0);
+    return 1;
+  }
+  // plane by plane: slices of C_k, A_kk - C_k C_k^T on the tensor cores
+  // (FP64 accuracy), then the plane's Cholesky, inverse and C_{k+1}
+  const int NR = f3_nr(t), Kp = f3_kp(t), S = oz_slices(oz_bits(Kp), 54);
+  const int64_t PC = (int64_t)t.BP * t.BP, STAGE = PC + (int64_t)t.BP * (t.BP + 1) / 2;
+  double* wd = reinterpret_cast<double*>(work);
+  __nv_bfloat16* Wsl = reinterpret_cast<__nv_bfloat16*>(wd + (size_t)t.n_sub * 2 * PC);
+  int* expo = reinterpret_cast<int*>(reinterpret_cast<char*>(Wsl) + f3_slice_bytes(t) + 128);
+  const size_t sm = (size_t)kOzStages * 32768 + 2 * kOzTile * 4 + Factor3Tile::smem(t) + 64;
+  int launches = 0;
+  for (int k = 0; k < t.nb_max; ++k) {
+    if (k > 0) {
+      const OzSlab src{0, k * STAGE, t.BP, k, t.BP};
+      ozaki_slice_kernel<double><<<dim3(t.n_sub, NR / 32), 256, 0, st>>>(t, (const double*)factor, src, NR, Kp, S,
+                                                                          Wsl, expo);
+      const Factor3Tile tile{t.Ke64, fld.scale64, wd, k};
+      if (NR == 128)
+        ozaki_syrk_kernel<128, Factor3Tile><<<dim3(t.n_sub, 1), kOzThreads, sm, st>>>(t, tile, Wsl, expo, Kp, S, err);
+      else
+        ozaki_syrk_kernel<256, Factor3Tile><<<dim3(t.n_sub, 3), kOzThreads, sm, st>>>(t, tile, Wsl, expo, Kp, S, err);
+      launches += 2;
+    }
+    factor3d_kernel<double><<<t.n_sub, kT3, 0, st>>>(t, t.Ke64, fld.scale64, (double*)factor, wd, err, bad_sub, k,
+                                                     k + 1, 1);
+    ++launches;
+  }
+  return launches;
 }
 
 size_t schur3d_smem(const DevTables& t, int precision);
@@ -806,6 +895,12 @@ cudaError_t configure_kernels3d() {
                                           big - (int)fa.sharedSizeBytes);
     if (e2 != cudaSuccess) e = e2;
   }
+  for (auto k : {ozaki_syrk_kernel<128, Factor3Tile>, ozaki_syrk_kernel<256, Factor3Tile>})
+    if (cudaFuncGetAttributes(&fa, k) == cudaSuccess) {
+      cudaError_t e2 = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                            big - (int)fa.sharedSizeBytes);
+      if (e2 != cudaSuccess) e = e2;
+    }
   if (cudaFuncGetAttributes(&fa, schur3d_kernel<double>) == cudaSuccess)
     e = cudaFuncSetAttribute(schur3d_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              big - (int)fa.sharedSizeBytes);

@@ -107,12 +107,14 @@ void launch_assemble(const DevTables& t, const DevFields& fld, const double* rho
                      int face_scaling, int crosspoint_mode, int* err, cudaStream_t st);
 // Fused interior assembly + block-tridiagonal Cholesky; factor in T.  work:
 // 3D scratch of factor3d_work_elems() elements of the precision (unused in 2D).
-void launch_factor(const DevTables& t, const DevFields& fld, int precision, void* factor, void* work,
-                   int* err, int* bad_sub, cudaStream_t st);
+// tensor: FP64 3D planes take C_k C_k^T on the tensor cores.  Returns the
+// number of kernel launches.
+int launch_factor(const DevTables& t, const DevFields& fld, int precision, void* factor, void* work,
+                  int* err, int* bad_sub, int tensor, cudaStream_t st);
 // 3D path (ddel_kernels3d.cu)
-size_t factor3d_work_elems(const DevTables& t);
-void launch_factor3d(const DevTables& t, const DevFields& fld, int precision, void* factor,
-                     void* work, int* err, int* bad_sub, cudaStream_t st);
+size_t factor3d_work_elems(const DevTables& t, int precision, int tensor);
+int launch_factor3d(const DevTables& t, const DevFields& fld, int precision, void* factor, void* work, int* err,
+                    int* bad_sub, int tensor, cudaStream_t st);
 void launch_schur3d(const DevTables& t, const DevFields& fld, int precision, const void* factor,
                     const SchurIO& io, cudaStream_t st);
 // FP64 operator in double-float arithmetic on a stream-ordered copy of the

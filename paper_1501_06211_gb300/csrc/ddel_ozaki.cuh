@@ -33,7 +33,7 @@ constexpr int kOzThreads = 256;
 constexpr int kOzKC = 64;      // rows of W per operand chunk
 constexpr int kOzTile = 128;   // output tile edge (MMA M = N)
 
-__device__ __forceinline__ int oz_bits(int K) { return K <= 1489 ? 6 : 5; }
+__device__ __host__ __forceinline__ int oz_bits(int K) { return K <= 1489 ? 6 : 5; }
 // Slices for a target of `target` significant bits.
 __device__ __host__ __forceinline__ int oz_slices(int bits, int target) { return (target + bits - 1) / bits; }
 
@@ -47,24 +47,42 @@ __device__ __forceinline__ int oz_img_off(int c, int k) {
   return (k >> 4) * 4096 + (c >> 3) * 256 + ((k >> 3) & 1) * 128 + (c & 7) * 16 + (k & 7) * 2;
 }
 
-// Slices of W for every subdomain.  W: per subdomain nb_max * BP rows of NR
-// doubles; Wsl: per subdomain, slice p, row tile rt (NR / 128) and chunk kc
-// (Kp / 64) one 16 KB image (oz_img_off); expo: per subdomain NR ints.  Block
-// (subdomain, 32 columns) of 256 threads: the column maxima, then per thread
-// one column and 8 consecutive rows, written as one 16-byte unit per slice.
+// Where a subdomain's matrix W (K rows of ncols columns, row stride ld) lies.
+//  plane < 0: W = L^-1 K_IG of the 2D formation, sub_stride elements per
+//    subdomain, K = nb BP rows of NR columns (ld = ncols = NR);
+//  plane >= 0: the block C_plane of a subdomain's factor (at factor_off +
+//    off, column-major BP x BP, i.e. W(m, i) = C(i, m): K = BP rows of BP
+//    columns), for the product C C^T; K = 0 (nothing) unless 1 <= plane < nb.
+struct OzSlab {
+  int64_t sub_stride;
+  int64_t off;
+  int ld;
+  int plane;
+  int ncols;
+};
+
+// Slices of W for every subdomain.  Wsl: per subdomain, slice p, row tile rt
+// (NR / 128) and chunk kc (Kp / 64) one 16 KB image (oz_img_off); expo: per
+// subdomain NR ints.  Block (subdomain, 32 columns) of 256 threads: the
+// column maxima, then per thread one column and 8 consecutive rows, written as
+// one 16-byte unit per slice.  Columns from ncols to NR and rows from K to Kp
+// are zero.
 template <typename TW>
-__global__ void __launch_bounds__(256) ozaki_slice_kernel(DevTables t, const TW* __restrict__ W, int NR, int Kp, int S,
-                                                          __nv_bfloat16* __restrict__ Wsl, int* __restrict__ expo) {
+__global__ void __launch_bounds__(256) ozaki_slice_kernel(DevTables t, const TW* __restrict__ W, OzSlab src, int NR,
+                                                          int Kp, int S, __nv_bfloat16* __restrict__ Wsl,
+                                                          int* __restrict__ expo) {
   const int sub = blockIdx.x, j0 = blockIdx.y * 32, tid = threadIdx.x;
   const int jl = tid & 31, ko = tid >> 5;  // column in the block, row offset
   const SubInfo si = t.subs[sub];
-  const int K = si.nb * t.BP;  // rows of this subdomain's W (the rest are zero)
+  const int K = src.plane < 0 ? si.nb * t.BP : (src.plane >= 1 && src.plane < si.nb ? t.BP : 0);
+  const int ld = src.ld, jv = j0 + jl < src.ncols;  // this column holds data
   const int bits = oz_bits(Kp);
-  const TW* Wb = W + (int64_t)sub * t.nb_max * t.BP * NR;
+  const TW* Wb = W + (src.plane < 0 ? (int64_t)sub * src.sub_stride : si.factor_off) + src.off;
   __shared__ double mx_s[8][32];
   __shared__ int e_s[32];
   double mx = 0.0;
-  for (int k = ko; k < K; k += 8) mx = fmax(mx, fabs((double)Wb[(int64_t)k * NR + j0 + jl]));
+  if (jv)
+    for (int k = ko; k < K; k += 8) mx = fmax(mx, fabs((double)Wb[(int64_t)k * ld + j0 + jl]));
   mx_s[ko][jl] = mx;
   __syncthreads();
   if (tid < 32) {
@@ -88,7 +106,7 @@ __global__ void __launch_bounds__(256) ozaki_slice_kernel(DevTables t, const TW*
     long long m[8];
 #pragma unroll
     for (int r = 0; r < 8; ++r)
-      m[r] = k8 + r < K ? __double2ll_rn(ldexp((double)Wb[(int64_t)(k8 + r) * NR + j], bits * S - e)) : 0ll;
+      m[r] = jv && k8 + r < K ? __double2ll_rn(ldexp((double)Wb[(int64_t)(k8 + r) * ld + j], bits * S - e)) : 0ll;
     const int kc = k8 >> 6;
     const int off = oz_img_off(c, k8 & 63);
     for (int p = 0; p < S; ++p) {
@@ -166,7 +184,7 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
   for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
 }
 
-// S tile (ta, tb) of one subdomain: K_GG entries minus 2^(e_i + e_j) sum_d
+// Tile (ta, tb) of one subdomain: the tile's own entries (K_GG for S_i) minus 2^(e_i + e_j) sum_d
 // 2^(-B d) C_d, C_d = sum_{p + q = d} D_p^T D_q accumulated in tensor memory,
 // d from S + 1 down to 2 (small terms first).  256 threads: thread (w, l)
 // keeps row 32 (w % 4) + l, columns 64 (w / 4) .. + 63 of the FP64 tile in
@@ -181,12 +199,18 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
 // memory and returns.
 constexpr int kOzStages = 6;
 
-template <int NR, typename TO>
-__global__ void __launch_bounds__(kOzThreads, 1) ozaki_syrk_kernel(DevTables t, const double* __restrict__ Ke_g,
-                                                                   const double* __restrict__ scale,
+// Tile: what the product is subtracted from and where the result goes --
+//   int rows(t, si): rows of W holding data (0: the CTA has nothing to do);
+//   void setup(t, si, ta, tb, sm): stage what value() reads (all threads);
+//   double value(t, si, sm, gi, gj, li, lj): the entry the product is taken
+//     from (global indices gi, gj; li, lj within the tiles ta, tb);
+//   void store(t, si, sub, gi, gj, v): write the result entry;
+//   static size_t smem(t) on the host: bytes of sm.
+template <int NR, class Tile>
+__global__ void __launch_bounds__(kOzThreads, 1) ozaki_syrk_kernel(DevTables t, Tile tile,
                                                                    const __nv_bfloat16* __restrict__ Wsl,
                                                                    const int* __restrict__ expo, int Kp, int S,
-                                                                   TO* __restrict__ Sexp, int* err) {
+                                                                   int* err) {
   constexpr int NT = NR / kOzTile, NST = kOzStages;
   const int sub = blockIdx.x, tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   int ta = 0, q = blockIdx.y;  // tile index -> (ta, tb), ta <= tb
@@ -196,23 +220,19 @@ __global__ void __launch_bounds__(kOzThreads, 1) ozaki_syrk_kernel(DevTables t, 
   }
   const int tb = ta + q;
   const SubInfo si = t.subs[sub];
-  const int s = t.s;
+  const int K = tile.rows(t, si);
+  if (K <= 0) return;  // uniform over the CTA, before any barrier or tensor memory
   const int bits = oz_bits(Kp);
   extern __shared__ __align__(1024) unsigned char oz_smem[];
-  unsigned char* stage = oz_smem;                                 // NST x (A 16 KB, B 16 KB)
-  double* ke = reinterpret_cast<double*>(oz_smem + NST * 32768);  // 64
-  double* sc = ke + 64;                                           // s * s
-  int* rl = reinterpret_cast<int*>(sc + s * s);                   // 256: ring locs of ta, tb
-  int* ex = rl + 2 * kOzTile;                                     // 256: exponents of ta, tb
+  unsigned char* stage = oz_smem;                                // NST x (A 16 KB, B 16 KB)
+  int* ex = reinterpret_cast<int*>(oz_smem + NST * 32768);      // 256: exponents of ta, tb
+  unsigned char* tsm = oz_smem + NST * 32768 + 2 * kOzTile * 4;  // the tile's own data
   __shared__ __align__(8) uint64_t full[NST], empty[NST];
   __shared__ uint32_t tmem_base;
   __shared__ int s_fail;
-  for (int i = tid; i < 64; i += kOzThreads) ke[i] = Ke_g[i];
-  for (int i = tid; i < s * s; i += kOzThreads)
-    sc[i] = scale[(int64_t)(si.lo[0] + i / s) * t.ne[1] + si.lo[1] + i % s];
+  tile.setup(t, si, ta, tb, tsm);
   for (int j = tid; j < 2 * kOzTile; j += kOzThreads) {
     const int jr = (j < kOzTile ? ta : tb) * kOzTile + j % kOzTile;
-    rl[j] = jr < si.n_ring ? t.ring_loc[si.ring_off + jr] : -1;
     ex[j] = expo[(int64_t)sub * NR + jr];
   }
   if (tid == 0) {
@@ -227,15 +247,17 @@ __global__ void __launch_bounds__(kOzThreads, 1) ozaki_syrk_kernel(DevTables t, 
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
-  // this thread's part of the tile: row i, columns jc .. jc + 63, K_GG first
+  // this thread's part of the tile: row i, columns jc .. jc + 63, the tile's
+  // own entries first
   const int i = 32 * (warp & 3) + lane, jc = 64 * (warp >> 2);
   double acc[64];
 #pragma unroll
-  for (int c = 0; c < 64; ++c) acc[c] = kgg_entry2d<double>(s, ke, sc, rl[i], rl[kOzTile + jc + c]);
+  for (int c = 0; c < 64; ++c)
+    acc[c] = tile.value(t, si, tsm, ta * kOzTile + i, tb * kOzTile + jc + c, i, jc + c);
   const uint32_t dt = tmem_base;
   constexpr uint32_t idesc = idesc_bf16_f32(kOzTile, kOzTile);
   const int NRT = NR / 128, NKC = Kp / 64;
-  const int nkc = (si.nb * t.BP + 63) / 64;  // chunks holding data
+  const int nkc = (K + 63) / 64;  // chunks holding data
   const unsigned char* img0 = reinterpret_cast<const unsigned char*>(Wsl) + (int64_t)sub * S * NRT * NKC * 16384;
   auto img = [&](int p, int rt, int kc) { return img0 + ((int64_t)((p - 1) * NRT + rt) * NKC + kc) * 16384; };
   // step sequence: d from S + 1 down to 2; p from min(d - 1, S) down to
@@ -308,12 +330,11 @@ __global__ void __launch_bounds__(kOzThreads, 1) ozaki_syrk_kernel(DevTables t, 
   if (s_fail && tid == 0) atomicExch(err, kErrTimeout);
   __syncthreads();
   if (warp == 0) tmem_dealloc(tmem_base, 128);
-  TO* out = Sexp + (int64_t)sub * NR * NR;
   const int gi = ta * kOzTile + i;
 #pragma unroll
   for (int c = 0; c < 64; ++c) {
     const int gj = tb * kOzTile + jc + c;
-    out[(int64_t)gi * NR + gj] = (TO)acc[c];
-    if (ta != tb) out[(int64_t)gj * NR + gi] = (TO)acc[c];
+    tile.store(t, si, sub, gi, gj, acc[c]);
+    if (ta != tb) tile.store(t, si, sub, gj, gi, acc[c]);
   }
 }

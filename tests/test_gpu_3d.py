@@ -101,6 +101,27 @@ def test_3d_solve(name, prec):
     assert rel(u, o["u_ref"]) <= (1e-8 if prec == 0 else 1e-6), st.as_dict()
 
 
+@pytest.mark.parametrize("name", list(CASES))
+def test_3d_tensor_core_factor_planes(name):
+    # C_k C_k^T of every plane on the tensor cores (tensor_form = 2: Ozaki
+    # slices of C_k, FP64 accuracy): the Schur complement and the solve keep
+    # the bars of the FP64-pipe factorisation
+    from paper_1501_06211_gb300 import ddel
+    s, o = solver(name, tensor_form=2, tol=1e-10, max_it=20000)
+    gd = s.gamma_dofs()
+    pos = {int(v): k for k, v in enumerate(o["dec"].gamma_dofs)}
+    perm = np.array([pos[int(v)] for v in gd])
+    xg = np.random.default_rng(1).standard_normal(len(gd))
+    xo = np.zeros(len(gd))
+    xo[perm] = xg
+    yg = torch.zeros(len(gd), dtype=torch.float64, device="cuda")
+    assert ddel.ddel_schur_apply(s.h, dev(xg), yg) == 0
+    assert rel(yg.cpu().numpy(), o["dds"].schur_apply(xo)[perm]) < 1e-10
+    u, st = s.solve(check=False)
+    assert st.relres <= 1e-9, st.as_dict()
+    assert rel(u, o["u_ref"]) <= 1e-8, st.as_dict()
+
+
 def test_3d_full_size_config2_residual():
     # 96 x 48 x 48 H8, 432 subdomains of 8^3, uniform-random densities: the
     # oracle's matrix-free K checks the residual of the GPU solution
