@@ -165,20 +165,6 @@ __device__ __forceinline__ T entry2d(const DevTables& t, const SubInfo& si, cons
 // lowest such subdomain in bad_sub).
 constexpr int kFacThreads = 256;
 
-// 1 / sqrt(d), d > 0: Newton's iteration for f(r) = 1 / r^2 - d,
-// r <- r (3 - d r^2) / 2, from the single-precision estimate; each step
-// doubles the correct bits, two take the estimate's 23 past double precision
-// (a few units in the last place).  Outside the single-precision range the
-// library square root and division serve.  (FP64 only.)
-__device__ __forceinline__ double pivot_rsqrt(double d) {
-  if (d > 1e-36 && d < 1e36) {
-    double r = (double)rsqrtf((float)d);
-    r = r * fma(-0.5 * d, r * r, 1.5);
-    r = r * fma(-0.5 * d, r * r, 1.5);
-    return r;
-  }
-  return 1.0 / sqrt(d);
-}
 
 template <typename T>
 __device__ __forceinline__ void lds4(const T* p, T (&v)[4]) {

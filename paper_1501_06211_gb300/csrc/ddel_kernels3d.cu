@@ -140,17 +140,33 @@ __device__ void cta_cholesky(T* A, int n, T* sA, T* sB, bool* bad) {
     }
     __syncthreads();
     for (int j = 0; j < w; ++j) {
+      // the pivot, and its reciprocal in sB[j] for the panel below; FP64 by
+      // one Newton reciprocal square root (the FP64 pipe retires a warp
+      // instruction per 16 clocks however few lanes are active), FP32 by the
+      // correctly rounded square root and quotients
       if (tid == 0) {
         T d = sA[j * (TB + 1) + j];
         if (!(d > T(0)) || !isfinite((double)d)) {
           *bad = true;
           d = T(1);
         }
-        sA[j * (TB + 1) + j] = sqrt(d);
+        if constexpr (sizeof(T) == 8) {
+          const T r = pivot_rsqrt(d);
+          sA[j * (TB + 1) + j] = d * r;
+          sB[j] = r;
+        } else {
+          const T l = sqrt(d);
+          sA[j * (TB + 1) + j] = l;
+          sB[j] = T(1) / l;
+        }
       }
       __syncthreads();
-      const T ljj = sA[j * (TB + 1) + j];
-      if (tid > j && tid < w) sA[tid * (TB + 1) + j] /= ljj;
+      if (tid > j && tid < w) {
+        if constexpr (sizeof(T) == 8)
+          sA[tid * (TB + 1) + j] *= sB[j];
+        else
+          sA[tid * (TB + 1) + j] /= sA[j * (TB + 1) + j];
+      }
       __syncthreads();
       for (int q = tid; q < TB * TB; q += kT3) {
         const int a = q / TB, b = q % TB;
@@ -169,7 +185,10 @@ __device__ void cta_cholesky(T* A, int n, T* sA, T* sB, bool* bad) {
       for (int c = 0; c < w; ++c) {
         T v = row[c];
         for (int m = 0; m < c; ++m) v -= row[m] * sA[c * (TB + 1) + m];
-        row[c] = v / sA[c * (TB + 1) + c];
+        if constexpr (sizeof(T) == 8)
+          row[c] = v * sB[c];
+        else
+          row[c] = v / sA[c * (TB + 1) + c];
       }
     }
     __syncthreads();
@@ -204,12 +223,16 @@ __device__ void cta_tri_inverse(const T* L, T* D, int n, T* sA, T* sB) {
       const int a = q / TB, b = q % TB;
       sA[a * (TB + 1) + b] = (a < w && b < w) ? L[(int64_t)(ib + a) * n + ib + b] : T(0);
     }
+    if (sizeof(T) == 8 && tid < w) sB[tid] = T(1) / L[(int64_t)(ib + tid) * n + ib + tid];
     __syncthreads();
     for (int a = 0; a < w; ++a) {
       for (int j = tid; j < ib + w; j += kT3) {
         T v = D[(int64_t)(ib + a) * n + j];
         for (int m = 0; m < a; ++m) v -= sA[a * (TB + 1) + m] * D[(int64_t)(ib + m) * n + j];
-        D[(int64_t)(ib + a) * n + j] = v / sA[a * (TB + 1) + a];
+        if constexpr (sizeof(T) == 8)
+          D[(int64_t)(ib + a) * n + j] = v * sB[a];
+        else
+          D[(int64_t)(ib + a) * n + j] = v / sA[a * (TB + 1) + a];
       }
       __syncthreads();
     }
@@ -273,7 +296,8 @@ __global__ void __launch_bounds__(kT3) factor3d_kernel(DevTables t, const T* __r
       for (int q = tid; q < PC; q += kT3) {
         const int j = q / BP, i = q % BP;
         T c = T(0);
-        if (i < si.bsz) {
+        // the lowest column row i couples to is 3 n - cy - 3: below it C vanishes
+        if (i < si.bsz && j >= 3 * (i / 3) - cy - 3) {
           const int n = i / 3, y = n / si.icnt[2], z = n - y * si.icnt[2], base = 3 * n;
           const bool y0 = y > 0, y2 = y + 1 < si.icnt[1], z0 = z > 0, z2 = z + 1 < si.icnt[2];
           const T* Dj = D + (int64_t)j * BP;
