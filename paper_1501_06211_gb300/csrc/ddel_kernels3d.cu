@@ -83,19 +83,21 @@ __device__ __forceinline__ int nz_col3(const SubInfo& si, int i, int w, int BP) 
   return m < BP ? m : -1;
 }
 
-// C(i, j) += alpha * sum_m A(i, m) B(j, m) for i < M, j < N (j <= i when lower),
+// C(i, j) += alpha * sum_m A(i, m) B(j, m) for i < M, j < N (j <= i when lower;
+// with b_tri the caller guarantees B(j, m) = 0 for m < j),
 // with general strides A(i, m) = A[i * ai + m * am], B(j, m) = B[j * bj + m * bm],
 // C(i, j) = C[i * ci + j * cj].  32 x 32 x 32 tiles through shared memory.
 template <typename T>
 __device__ void cta_gemm(int M, int N, int K, const T* A, int ai, int am, const T* B, int bj, int bm,
-                         T* C, int ci, int cj, T alpha, bool lower, T* sA, T* sB) {
+                         T* C, int ci, int cj, T alpha, bool lower, T* sA, T* sB, bool b_tri = false) {
   const int tid = threadIdx.x;
   const int ty = tid / 16, tx = tid % 16;  // each thread: rows ty, ty+16; cols tx, tx+16
   for (int i0 = 0; i0 < M; i0 += TB)
     for (int j0 = 0; j0 < N; j0 += TB) {
       if (lower && j0 > i0 + TB - 1) continue;
       T acc[2][2] = {{T(0), T(0)}, {T(0), T(0)}};
-      for (int m0 = 0; m0 < K; m0 += TB) {
+      // b_tri: B(j, m) = 0 for m < j, so the tile's products start at m = j0
+      for (int m0 = b_tri ? j0 : 0; m0 < K; m0 += TB) {
         for (int q = tid; q < TB * TB; q += kT3) {
           const int a = q / TB, b = q % TB;  // a: row in tile, b: m in tile
           const int i = i0 + a, j = j0 + a, m = m0 + b;
@@ -217,7 +219,7 @@ __device__ void cta_tri_inverse(const T* L, T* D, int n, T* sA, T* sB) {
     __syncthreads();
     if (ib > 0)
       cta_gemm<T>(w, ib, ib, L + (int64_t)ib * n, n, 1, D, 1, n, D + (int64_t)ib * n, n, 1, T(-1),
-                  false, sA, sB);
+                  false, sA, sB, true);
     // solve L_ii X = R in place (forward substitution down the w rows)
     for (int q = tid; q < TB * TB; q += kT3) {
       const int a = q / TB, b = q % TB;
