@@ -196,6 +196,41 @@ def test_adaptive_tolerance_matches_rule_and_saves_iterations():
     assert it_ad < 0.9 * it_fix, (it_ad, it_fix)
 
 
+def test_history_guess_with_adaptive_tolerance():
+    # the Galerkin guess of the last Picard solutions (HISTORY coarse space,
+    # X0 only: no correction inside the iteration) with the adaptive
+    # tolerance: the same rule on its own compliances, the fixed-tolerance
+    # design's compliance, and fewer PCG iterations than the adaptive
+    # tolerance started from zero
+    from paper_1501_06211_gb300 import ddel
+    cfg = _mbb(128, 64, 16)
+    ne = int(np.prod(cfg["ne"]))
+
+    def run(eta, learner_opts=None, steps=60):
+        s = ddel.Solver(cfg, tol=1e-8, max_it=20000)
+        L = ddel.Learner(s, **learner_opts) if learner_opts else None
+        rho = torch.full((ne,), 0.4, dtype=torch.float64, device="cuda")
+        ts = s.topopt_state(rho, volfrac=0.4, learner=L, tol_eta=eta, tol_max=1e-3)
+        hist, tols, its = [], [], 0
+        for _ in range(steps):
+            st = s.topopt_step(ts)
+            hist.append(ts.compliance)
+            tols.append(ts.tol_used)
+            its += st.iters
+        if L is not None:
+            L.close()
+        s.close()
+        return hist, tols, its
+
+    h_fix, _, _ = run(0.0)
+    _, _, it_ad = run(0.1)
+    h_hx, t_hx, it_hx = run(0.1, dict(mode=ddel.DDEL_LEARN_HISTORY, k_history=4, coarse_flags=ddel.DDEL_COARSE_X0))
+    for k in range(len(h_hx)):
+        assert t_hx[k] == topopt.adaptive_tolerance(h_hx[:k], 0.1, 1e-8, 1e-3), k
+    assert abs(h_hx[-1] - h_fix[-1]) <= 5e-3 * h_fix[-1], (h_hx[-1], h_fix[-1])
+    assert it_hx < 0.8 * it_ad, (it_hx, it_ad)
+
+
 def test_table3_sweep_trends():
     # Table 3's study on the built kernels (cantilever, OC, adaptive
     # tolerance, the variable-thickness sheet p = 1 of Sec. 5): Picard steps
