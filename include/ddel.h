@@ -146,6 +146,9 @@ typedef struct {
                           the C_k C_k^T of each plane of the FP64 3D factorisation (FP64
                           accuracy; slower than the FP64 pipe at these sizes);
                           0: every formation on the FP64 / FP32 pipes (1) */
+  int schur_split;     /* CTAs per subdomain of the native FP64 explicit apply: 1, 2 or 4
+                          (rows per CTA = ring / split, at least 32); 0: by ring size, one
+                          for rings of 64, two for 128 and 256 (0) */
 } ddel_options;
 
 typedef struct {
@@ -316,16 +319,18 @@ int ddel_batch_solve_persistent(ddel_ctx* const* ctxs, int n, double* const* u, 
 /* --- Autotuner ------------------------------------------------------------------
  * Chooses the Schur form (IMPLICIT block substitution, EXPLICIT FP64, or AUTO =
  * explicit applied in double-float arithmetic), the formation of S_i (tensor
- * cores or FP64 pipe, ddel_options.tensor_form, where both exist) and the PCG
- * graph batch size (check_every in {8, 16, 32}) for an assembled context by
- * timing them on this
+ * cores or FP64 pipe, ddel_options.tensor_form, where both exist), the tile
+ * shape of the native FP64 explicit apply (ddel_options.schur_split: 1, 2 or 4
+ * CTAs per subdomain) and the PCG graph batch size (check_every in
+ * {8, 16, 32}) for an assembled context by timing them on this
  * GPU: one solve gives the iteration count N, then each candidate is
  * factorised and runs 48 PCG iterations; the predicted solve time is
  * factor (+ formation) time + N x time per iteration.  The winner is applied
  * to the context (ddel_set_options semantics: refactor before solving) and,
  * with cache_path != NULL, appended to that text file under the key
- * "dim sub BP n_sub precision" (fields: mode, check_every, tensor_form; lines
- * without the last field keep the context's tensor_form); a later call with the same key reads the file
+ * "dim sub BP n_sub precision" (fields: mode, check_every, tensor_form,
+ * schur_split; lines without the last fields keep the context's settings); a
+ * later call with the same key reads the file
  * and applies the cached choice without timing (*from_cache = 1).
  * chosen_mode / chosen_check: outputs (may be NULL).  Synchronises. */
 int ddel_autotune(ddel_ctx* ctx, const char* cache_path, int* chosen_mode, int* chosen_check,

@@ -96,6 +96,7 @@ struct ddel_ctx {
   int coarse_flags = 0;          // DDEL_COARSE_* bits
   int coarse_prec = -1;          // precision whose S formed E (-1: stale)
   int graph_ck[2] = {0, 0};      // coarse dimension captured in graph[prec]
+  int graph_split[2] = {0, 0};   // CTAs per subdomain of the FP64 explicit apply captured
   bool u_valid = false;          // d_u holds a converged solution (x0_mode WARM)
   // global interface preconditioner and full-system FGMRES (first use)
   GPDev gp{};
@@ -206,10 +207,7 @@ int schur_dispatch(ddel_ctx* ctx, int prec, bool apply32, SchurIO& io, cudaStrea
     launch_schur_explicit_df(ctx->T, ctx->sexp_df, io, s);
     return 2 * ctx->T.n_sub;
   }
-  if (expl) {
-    launch_schur_explicit(ctx->T, apply32 ? 1 : prec, smat, io, s);
-    return 2 * ctx->T.n_sub;
-  }
+  if (expl) return launch_schur_explicit(ctx->T, apply32 ? 1 : prec, smat, io, ctx->opt.schur_split, s);
   if (ctx->T.dim == 3 && prec == 0 && !apply32 && ctx->df3_ok)
     launch_schur3d_df(ctx->T, ctx->F, ctx->factor_df, ctx->df3_off, io, s);
   else
@@ -274,9 +272,10 @@ int pcg_start(ddel_ctx* ctx, int prec, const double* g, bool apply32) {
   const bool expl = ctx->explicit_ok[prec];
   const bool df = prec == 0 && ctx->df_ok;
   const int gck = cd.k > 0 && cd.correct ? cd.k : 0;
+  const int gsplit = explicit_split(ctx->T, ctx->opt.schur_split);
   if (ctx->graph[prec] && (ctx->graph_explicit[prec] != expl || ctx->graph_apply32[prec] != apply32 ||
                            ctx->graph_iters != per || (prec == 0 && ctx->graph_df != df) ||
-                           ctx->graph_ck[prec] != gck)) {
+                           ctx->graph_ck[prec] != gck || ctx->graph_split[prec] != gsplit)) {
     cudaGraphExecDestroy(ctx->graph[prec]);
     ctx->graph[prec] = nullptr;
   }
@@ -291,6 +290,7 @@ int pcg_start(ddel_ctx* ctx, int prec, const double* g, bool apply32) {
     ctx->graph_explicit[prec] = expl;
     ctx->graph_apply32[prec] = apply32;
     ctx->graph_ck[prec] = gck;
+    ctx->graph_split[prec] = gsplit;
     if (prec == 0) ctx->graph_df = df;
   }
   return DDEL_OK;
@@ -621,6 +621,7 @@ void ddel_default_options(ddel_options* o) {
   o->use_graph = 1;
   o->check_every = 16;
   o->tensor_form = 1;
+  o->schur_split = 0;
 }
 
 const char* ddel_strerror(int s) {
@@ -748,7 +749,7 @@ int ddel_create(const ddel_mesh* mesh, const ddel_material* mat, const ddel_bc* 
         bad(dalloc(ctx, &ctx->sv, ng * 8)) ||
         bad(dalloc(ctx, &ctx->rho, S.n_elem * 8)) || bad(dalloc(ctx, &ctx->st, sizeof(PcgState))) ||
         bad(dalloc(ctx, &ctx->partials, (size_t)(4 * 152 * (2 + 2 * kMaxCoarse) + 2 * T.n_sub + 64) * 8)) ||
-        bad(dalloc(ctx, &ctx->pcg_pd, (size_t)(2 * T.n_sub + 64) * 8)) ||
+        bad(dalloc(ctx, &ctx->pcg_pd, (size_t)(4 * T.n_sub + 64) * 8)) ||
         bad(dalloc(ctx, &ctx->pcg_pu, (size_t)2 * kPcgRows * 2 * 152 * 8)) ||
         bad(dalloc(ctx, &ctx->ticketK, 16)) || bad(dalloc(ctx, &ctx->nrm, 16)) ||
         bad(dalloc(ctx, &ctx->err, 4 * sizeof(int))))
@@ -1535,10 +1536,11 @@ int ddel_autotune(ddel_ctx* ctx, const char* cache_path, int* chosen_mode, int* 
   std::snprintf(key, sizeof(key), "%d %d %d %d %d", ctx->S.dim, ctx->S.sub, ctx->S.BP, ctx->S.n_sub,
                 ctx->opt.precision);
   if (from_cache) *from_cache = 0;
-  auto apply = [&](int mode, int check, int tf) {
+  auto apply = [&](int mode, int check, int tf, int split) {
     ctx->opt.schur_mode = mode;
     ctx->opt.check_every = check;
     ctx->opt.tensor_form = tf;
+    ctx->opt.schur_split = split;
     ctx->factored[0] = ctx->factored[1] = false;
     if (chosen_mode) *chosen_mode = mode;
     if (chosen_check) *chosen_check = check;
@@ -1546,23 +1548,24 @@ int ddel_autotune(ddel_ctx* ctx, const char* cache_path, int* chosen_mode, int* 
   if (cache_path) {
     if (FILE* fp = std::fopen(cache_path, "r")) {
       char line[256];
-      int mode = -1, check = 0, tform = ctx->opt.tensor_form;
+      int mode = -1, check = 0, tform = ctx->opt.tensor_form, split = ctx->opt.schur_split;
       while (std::fgets(line, sizeof(line), fp)) {
-        int d, s, b, n, p, m, c, tf = ctx->opt.tensor_form;
-        const int got = std::sscanf(line, "%d %d %d %d %d %d %d %d", &d, &s, &b, &n, &p, &m, &c, &tf);
-        if (got >= 7) {  // lines without the tensor-form field keep the context's setting
+        int d, s, b, n, p, m, c, tf = ctx->opt.tensor_form, sp = ctx->opt.schur_split;
+        const int got = std::sscanf(line, "%d %d %d %d %d %d %d %d %d", &d, &s, &b, &n, &p, &m, &c, &tf, &sp);
+        if (got >= 7) {  // lines without the last fields keep the context's settings
           char k2[128];
           std::snprintf(k2, sizeof(k2), "%d %d %d %d %d", d, s, b, n, p);
           if (std::strcmp(k2, key) == 0) {
             mode = m;
             check = c;
             tform = tf;
+            split = sp;
           }
         }
       }
       std::fclose(fp);
       if (mode >= 0) {
-        apply(mode, check, tform);
+        apply(mode, check, tform, split);
         if (from_cache) *from_cache = 1;
         return DDEL_OK;
       }
@@ -1577,28 +1580,38 @@ int ddel_autotune(ddel_ctx* ctx, const char* cache_path, int* chosen_mode, int* 
   if (rc != DDEL_OK && rc != DDEL_ENOCONV) return rc;
   const double n_iter = st.iters > 0 ? st.iters : 1;
   const bool has_explicit = explicit_ring_size(ctx->T) > 0;
-  // candidates (Schur form, S_i formation on the tensor cores or the FP64 pipe)
+  // candidates: Schur form, S_i formation on the tensor cores or the FP64
+  // pipe, and for the native FP64 explicit apply its tile shape (CTAs per
+  // subdomain)
+  struct Cand {
+    int mode, tf, split;
+  };
   const bool tc_ok = tensor_form_available(ctx->T);
-  std::vector<std::pair<int, int>> forms = {{DDEL_SCHUR_IMPLICIT, saved.tensor_form}};
+  std::vector<Cand> forms = {{DDEL_SCHUR_IMPLICIT, saved.tensor_form, saved.schur_split}};
   if (has_explicit && prec == 0) {
-    forms.push_back({DDEL_SCHUR_AUTO, 0});
-    if (tc_ok && explicit_ring_size(ctx->T) > 128) forms.push_back({DDEL_SCHUR_AUTO, 1});
+    forms.push_back({DDEL_SCHUR_AUTO, 0, saved.schur_split});
+    if (tc_ok && explicit_ring_size(ctx->T) > 128) forms.push_back({DDEL_SCHUR_AUTO, 1, saved.schur_split});
   }
   if (has_explicit) {
-    forms.push_back({DDEL_SCHUR_EXPLICIT, 0});
-    if (tc_ok) forms.push_back({DDEL_SCHUR_EXPLICIT, prec ? 2 : 1});
+    for (int split : {1, 2, 4}) {
+      if (prec == 0 ? explicit_split(ctx->T, split) != split : split != 2) continue;
+      forms.push_back({DDEL_SCHUR_EXPLICIT, 0, split});
+      if (tc_ok) forms.push_back({DDEL_SCHUR_EXPLICIT, prec ? 2 : 1, split});
+    }
   }
   const int checks[3] = {8, 16, 32};
   double best = 1e300;
-  int best_mode = saved.schur_mode, best_check = saved.check_every, best_tf = saved.tensor_form;
+  int best_mode = saved.schur_mode, best_check = saved.check_every, best_tf = saved.tensor_form,
+      best_split = saved.schur_split;
   cudaStream_t s = ctx->stream;
   for (const auto& fm : forms)
     for (int check : checks) {
-      const int mode = fm.first;
+      const int mode = fm.mode;
       ctx->opt = saved;
       ctx->opt.schur_mode = mode;
       ctx->opt.check_every = check;
-      ctx->opt.tensor_form = fm.second;
+      ctx->opt.tensor_form = fm.tf;
+      ctx->opt.schur_split = fm.split;
       CK(cudaEventRecord(ctx->ev[0], s));
       rc = ddel_factor(ctx);
       if (rc) return rc;
@@ -1629,14 +1642,15 @@ int ddel_autotune(ddel_ctx* ctx, const char* cache_path, int* chosen_mode, int* 
         best = predicted;
         best_mode = mode;
         best_check = check;
-        best_tf = fm.second;
+        best_tf = fm.tf;
+        best_split = fm.split;
       }
     }
   ctx->opt = saved;
-  apply(best_mode, best_check, best_tf);
+  apply(best_mode, best_check, best_tf, best_split);
   if (cache_path) {
     if (FILE* fp = std::fopen(cache_path, "a")) {
-      std::fprintf(fp, "%s %d %d %d\n", key, best_mode, best_check, best_tf);
+      std::fprintf(fp, "%s %d %d %d %d\n", key, best_mode, best_check, best_tf, best_split);
       std::fclose(fp);
     }
   }

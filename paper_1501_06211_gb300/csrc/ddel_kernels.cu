@@ -1160,13 +1160,17 @@ __global__ void __launch_bounds__(256) schur_explicit_kernel(DevTables t, const 
 // accumulator per row; the H column groups of a row are added in group order.
 // GB300 issues two DFMA per clock per SM, so this product is bound by the FP64
 // pipe (2 n_ring^2 flop per subdomain) rather than by the bytes it streams.
-template <int NR>
+// SPLIT CTAs share a subdomain, NR / SPLIT rows each (the tile shape the
+// autotuner chooses: fewer, longer column groups with SPLIT = 1, more CTAs
+// with SPLIT = 4).
+template <int NR, int SPLIT>
 __global__ void __launch_bounds__(256, NR <= 128 ? 7 : 5) schur_explicit_f64_kernel(DevTables t,
                                                                                    const double* __restrict__ Sexp,
                                                                                    SchurIO io) {
   const int done = io.done ? *io.done : 0;
-  constexpr int RH = NR / 2, RP = RH / 2, H = 256 / RP, JN = NR / H;
-  const int sub = blockIdx.x >> 1, half = blockIdx.x & 1, tid = threadIdx.x;
+  constexpr int RH = NR / SPLIT, RP = RH / 2, H = 256 / RP, JN = NR / H;
+  static_assert(RH >= 32 && RP <= 256 && H * RP == 256 && H * JN == NR, "tile shape");
+  const int sub = blockIdx.x / SPLIT, half = blockIdx.x % SPLIT, tid = threadIdx.x;
   const SubInfo si = t.subs[sub];
   __shared__ double xr[NR];
   __shared__ double part[2 * 256];
@@ -2360,20 +2364,45 @@ void launch_schur_explicit_df(const DevTables& t, const float2* Sexp, const Schu
     schur_explicit_df_kernel<256><<<2 * t.n_sub, 256, 0, st>>>(t, Sexp, io);
 }
 
-void launch_schur_explicit(const DevTables& t, int precision, const void* Sexp, const SchurIO& io,
-                           cudaStream_t st) {
+int explicit_split(const DevTables& t, int split) {
+  // CTAs per subdomain of the native FP64 apply: 1, 2 or 4, at least 32 rows
+  // each; 0 (and anything else) by ring size: one CTA for rings of 64 (8 x 8
+  // subdomains: 33.1 against 40.8 us per PCG iteration on a 512 x 256 grid),
+  // two for the larger ones (128: 28.9 against 30.7 with one and 31.6 with
+  // four; 256: equal)
+  const int NR = explicit_ring_size(t);
+  if (split != 1 && split != 2 && split != 4) split = NR <= 64 ? 1 : 2;
+  if (NR / split < 32) split = NR <= 64 ? 1 : 2;
+  return split;
+}
+
+template <int NR>
+void run_explicit_f64(const DevTables& t, const double* S, const SchurIO& io, int split, cudaStream_t st) {
+  if (split == 1)
+    schur_explicit_f64_kernel<NR, 1><<<t.n_sub, 256, 0, st>>>(t, S, io);
+  else if (split == 4 && NR >= 128)
+    schur_explicit_f64_kernel<NR, (NR >= 128 ? 4 : 2)><<<4 * t.n_sub, 256, 0, st>>>(t, S, io);
+  else
+    schur_explicit_f64_kernel<NR, 2><<<2 * t.n_sub, 256, 0, st>>>(t, S, io);
+}
+
+int launch_schur_explicit(const DevTables& t, int precision, const void* Sexp, const SchurIO& io, int split,
+                          cudaStream_t st) {
   const int NR = explicit_ring_size(t);
   if (precision == 0) {
     const double* S = (const double*)Sexp;
-    if (NR == 64) schur_explicit_f64_kernel<64><<<2 * t.n_sub, 256, 0, st>>>(t, S, io);
-    else if (NR == 128) schur_explicit_f64_kernel<128><<<2 * t.n_sub, 256, 0, st>>>(t, S, io);
-    else schur_explicit_f64_kernel<256><<<2 * t.n_sub, 256, 0, st>>>(t, S, io);
+    split = explicit_split(t, split);
+    if (NR == 64) run_explicit_f64<64>(t, S, io, split, st);
+    else if (NR == 128) run_explicit_f64<128>(t, S, io, split, st);
+    else run_explicit_f64<256>(t, S, io, split, st);
+    return split * t.n_sub;
   } else {
     const float* S = (const float*)Sexp;
     if (NR == 64) schur_explicit_kernel<float, 64><<<2 * t.n_sub, 256, 0, st>>>(t, S, io);
     else if (NR == 128) schur_explicit_kernel<float, 128><<<2 * t.n_sub, 256, 0, st>>>(t, S, io);
     else schur_explicit_kernel<float, 256><<<2 * t.n_sub, 256, 0, st>>>(t, S, io);
   }
+  return 2 * t.n_sub;
 }
 
 // ============================================================ launchers

@@ -161,8 +161,11 @@ void launch_schur_form_tc(const DevTables& t, const DevFields& fld, int precisio
 void launch_split_df(const double* in, float2* out, int64_t n, cudaStream_t st);
 void launch_schur_explicit_df(const DevTables& t, const float2* Sexp, const SchurIO& io,
                               cudaStream_t st);
-void launch_schur_explicit(const DevTables& t, int precision, const void* Sexp, const SchurIO& io,
-                           cudaStream_t st);
+// Returns the number of blocks (one delta partial each); split: CTAs per
+// subdomain of the native FP64 form (1, 2 or 4; others mean 2).
+int launch_schur_explicit(const DevTables& t, int precision, const void* Sexp, const SchurIO& io, int split,
+                          cudaStream_t st);
+int explicit_split(const DevTables& t, int split);
 // Sum ring contributions: out[g] = sign * sum(ring) + (base ? base[gamma_dof[g]] : 0)
 void launch_gamma_sum(const DevTables& t, int precision, const void* ring, const double* base,
                       double sign, double* out, cudaStream_t st);

@@ -45,7 +45,8 @@ class ddel_options(ctypes.Structure):
                 ("crosspoint_mode", c_int), ("tol", c_double), ("max_it", c_int),
                 ("max_cycles", c_int), ("inner_tol", c_double), ("x0_mode", c_int),
                 ("schur_mode", c_int), ("use_graph", c_int), ("check_every", c_int),
-                ("tensor_form", c_int)]
+                ("tensor_form", c_int),
+                ("schur_split", c_int)]
 
 
 class ddel_stats(ctypes.Structure):

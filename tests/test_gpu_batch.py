@@ -66,9 +66,11 @@ def test_autotune_choice_cache_and_parity(tmp_path):
     assert mode in (0, 1, 2) and check in (8, 16, 32)
     lines = open(cache).read().strip().splitlines()
     assert len(lines) == 1
-    # key (dim sub BP n_sub precision), then mode, check_every, tensor_form
+    # key (dim sub BP n_sub precision), then mode, check_every, tensor_form,
+    # schur_split (CTAs per subdomain of the FP64 explicit apply)
     fields = lines[0].split()
-    assert len(fields) == 8 and int(fields[5]) == mode and int(fields[6]) == check and fields[7] in ("0", "1")
+    assert len(fields) == 9 and int(fields[5]) == mode and int(fields[6]) == check
+    assert fields[7] in ("0", "1") and fields[8] in ("0", "1", "2", "4")
     s2 = ddel.Solver(cfg, tol=1e-10, max_it=20000)
     s2.assemble(rho)
     code2, mode2, check2, cached2 = ddel.ddel_autotune(s2.h, cache)
