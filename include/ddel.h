@@ -146,9 +146,10 @@ typedef struct {
                           the C_k C_k^T of each plane of the FP64 3D factorisation (FP64
                           accuracy; slower than the FP64 pipe at these sizes);
                           0: every formation on the FP64 / FP32 pipes (1) */
-  int schur_split;     /* CTAs per subdomain of the native FP64 explicit apply: 1, 2 or 4
-                          (rows per CTA = ring / split, at least 32); 0: by ring size, one
-                          for rings of 64, two for 128 and 256 (0) */
+  int schur_split;     /* CTAs per subdomain of the explicit apply (native FP64 and
+                          double-float): 1, 2 or 4 (rows per CTA = ring / split, at least
+                          32); 0: by ring size, one for rings of 64, two for 128 and 256
+                          (0); the persistent batch runs the default shape only */
 } ddel_options;
 
 typedef struct {

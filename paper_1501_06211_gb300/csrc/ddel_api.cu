@@ -203,10 +203,8 @@ int schur_dispatch(ddel_ctx* ctx, int prec, bool apply32, SchurIO& io, cudaStrea
   const bool expl = ctx->explicit_ok[prec];
   io.ring_out = ring_of(ctx, apply_prec(ctx, prec, apply32));
   const void* smat = apply32 ? (const void*)ctx->sexp32 : ctx->sexp[prec];
-  if (expl && prec == 0 && !apply32 && ctx->df_ok) {
-    launch_schur_explicit_df(ctx->T, ctx->sexp_df, io, s);
-    return 2 * ctx->T.n_sub;
-  }
+  if (expl && prec == 0 && !apply32 && ctx->df_ok)
+    return launch_schur_explicit_df(ctx->T, ctx->sexp_df, io, ctx->opt.schur_split, s);
   if (expl) return launch_schur_explicit(ctx->T, apply32 ? 1 : prec, smat, io, ctx->opt.schur_split, s);
   if (ctx->T.dim == 3 && prec == 0 && !apply32 && ctx->df3_ok)
     launch_schur3d_df(ctx->T, ctx->F, ctx->factor_df, ctx->df3_off, io, s);
@@ -1372,7 +1370,11 @@ int ddel_batch_solve_persistent(ddel_ctx* const* ctxs, int n, double* const* u, 
     c->mixed_ready = false;
     // the persistent form runs the double-float explicit apply without a
     // coarse space; any other configuration takes the stream-per-problem path
-    if (c->T.dim != 2 || !c->explicit_ok[0] || !c->df_ok || c->ck_in > 0)
+    // ... and with the tile shape of its own launches (by ring size), so that
+    // its results equal those of single solves bit for bit
+    const int nr = explicit_ring_size(c->T);
+    if (c->T.dim != 2 || !c->explicit_ok[0] || !c->df_ok || c->ck_in > 0 ||
+        explicit_split(c->T, c->opt.schur_split) != (nr <= 64 ? 1 : 2))
       return ddel_batch_solve(ctxs, n, u, stats);
   }
   // 2. right-hand sides, condensation, PCG start on each context's stream
@@ -1408,7 +1410,7 @@ int ddel_batch_solve_persistent(ddel_ctx* const* ctxs, int n, double* const* u, 
     b.pd = ctx->pcg_pd;
     b.pu = ctx->pcg_pu;
     b.nr = explicit_ring_size(ctx->T);
-    b.n_schur = 2 * ctx->T.n_sub;
+    b.n_schur = (b.nr <= 64 ? 1 : 2) * ctx->T.n_sub;  // one CTA per ring of 64
     b.n_upd = ctx->nupd;
     pre[i + 1] = pre[i] + batch_schur_tiles(b.n_schur);
     pre[n + 2 + i] = pre[n + 1 + i] + b.n_upd;

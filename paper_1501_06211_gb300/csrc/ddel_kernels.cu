@@ -1244,13 +1244,14 @@ __global__ void split_df_kernel(const double* __restrict__ in, float2* __restric
 // and the batched persistent kernel, which runs it for other problems'
 // blocks within one launch (CG: the vectors written earlier in that launch
 // by other blocks are read through L2, bypassing the non-coherent L1).
-template <int NR, bool CG>
+template <int NR, bool CG, int SPLIT = 2>
 __device__ __forceinline__ void schur_df_tile(const DevTables& t, const float2* __restrict__ Sexp, const SchurIO& io,
                                               int bid) {
   // the flag's load overlaps the gather; nothing is written before the test
   const int done = io.done ? (CG ? __ldcg(io.done) : *io.done) : 0;
-  constexpr int RH = NR / 2, RP = RH / 2, H = 256 / RP, JN = NR / H;
-  const int sub = bid >> 1, half = bid & 1, tid = threadIdx.x;
+  constexpr int RH = NR / SPLIT, RP = RH / 2, H = 256 / RP, JN = NR / H;
+  static_assert(RH >= 32 && RP <= 256 && H * RP == 256 && H * JN == NR, "tile shape");
+  const int sub = bid / SPLIT, half = bid % SPLIT, tid = threadIdx.x;
   const SubInfo si = t.subs[sub];
   __shared__ float2 xr[NR];
   __shared__ double xd[NR];
@@ -1306,10 +1307,11 @@ __device__ __forceinline__ void schur_df_tile(const DevTables& t, const float2* 
   schur_pcg_epilogue<RH / 32>(io, d[0], red, bid);
 }
 
-template <int NR>
+// SPLIT CTAs per subdomain (NR / SPLIT rows each; the persistent batch uses 2).
+template <int NR, int SPLIT>
 __global__ void __launch_bounds__(256, NR <= 128 ? 7 : 6) schur_explicit_df_kernel(DevTables t, const float2* __restrict__ Sexp,
                                                                 SchurIO io) {
-  schur_df_tile<NR, false>(t, Sexp, io, blockIdx.x);
+  schur_df_tile<NR, false, SPLIT>(t, Sexp, io, blockIdx.x);
 }
 
 // ============================================================ Gamma sums
@@ -1980,7 +1982,7 @@ __global__ void __launch_bounds__(kRedThreads, 2) batch_pcg_kernel(const BatchPr
       io.err = err;
       const int b1 = min((b + 1) * kBatchSchurGroup, bp.n_schur);
       for (int bb = b * kBatchSchurGroup; bb < b1; ++bb) {
-        if (bp.nr == 64) schur_df_tile<64, true>(bp.t, bp.sexp_df, io, bb);
+        if (bp.nr == 64) schur_df_tile<64, true, 1>(bp.t, bp.sexp_df, io, bb);
         else if (bp.nr == 128) schur_df_tile<128, true>(bp.t, bp.sexp_df, io, bb);
         else schur_df_tile<256, true>(bp.t, bp.sexp_df, io, bb);
         __syncthreads();
@@ -2353,23 +2355,33 @@ void launch_split_df(const double* in, float2* out, int64_t n, cudaStream_t st) 
   split_df_kernel<<<grid_for(n, 256), 256, 0, st>>>(in, out, n);
 }
 
-void launch_schur_explicit_df(const DevTables& t, const float2* Sexp, const SchurIO& io,
-                              cudaStream_t st) {
-  const int NR = explicit_ring_size(t);
-  if (NR == 64)
-    schur_explicit_df_kernel<64><<<2 * t.n_sub, 256, 0, st>>>(t, Sexp, io);
-  else if (NR == 128)
-    schur_explicit_df_kernel<128><<<2 * t.n_sub, 256, 0, st>>>(t, Sexp, io);
+template <int NR>
+void run_explicit_df(const DevTables& t, const float2* S, const SchurIO& io, int split, cudaStream_t st) {
+  if (split == 1)
+    schur_explicit_df_kernel<NR, 1><<<t.n_sub, 256, 0, st>>>(t, S, io);
+  else if (split == 4 && NR >= 128)
+    schur_explicit_df_kernel<NR, (NR >= 128 ? 4 : 2)><<<4 * t.n_sub, 256, 0, st>>>(t, S, io);
   else
-    schur_explicit_df_kernel<256><<<2 * t.n_sub, 256, 0, st>>>(t, Sexp, io);
+    schur_explicit_df_kernel<NR, 2><<<2 * t.n_sub, 256, 0, st>>>(t, S, io);
+}
+
+int launch_schur_explicit_df(const DevTables& t, const float2* Sexp, const SchurIO& io, int split,
+                             cudaStream_t st) {
+  const int NR = explicit_ring_size(t);
+  split = explicit_split(t, split);
+  if (NR == 64) run_explicit_df<64>(t, Sexp, io, split, st);
+  else if (NR == 128) run_explicit_df<128>(t, Sexp, io, split, st);
+  else run_explicit_df<256>(t, Sexp, io, split, st);
+  return split * t.n_sub;
 }
 
 int explicit_split(const DevTables& t, int split) {
-  // CTAs per subdomain of the native FP64 apply: 1, 2 or 4, at least 32 rows
+  // CTAs per subdomain of the explicit apply: 1, 2 or 4, at least 32 rows
   // each; 0 (and anything else) by ring size: one CTA for rings of 64 (8 x 8
-  // subdomains: 33.1 against 40.8 us per PCG iteration on a 512 x 256 grid),
-  // two for the larger ones (128: 28.9 against 30.7 with one and 31.6 with
-  // four; 256: equal)
+  // subdomains on a 512 x 256 grid, per PCG iteration: native FP64 33.1
+  // against 40.8 us, double-float 21.6 against 27.2 us), two for the larger
+  // ones (128: FP64 28.9 against 30.7 with one and 31.6 with four, double-float
+  // equal with one; 256: FP64 equal, double-float 19.7 against 21.6 and 20.8)
   const int NR = explicit_ring_size(t);
   if (split != 1 && split != 2 && split != 4) split = NR <= 64 ? 1 : 2;
   if (NR / split < 32) split = NR <= 64 ? 1 : 2;

@@ -159,8 +159,9 @@ void launch_schur_form_tc(const DevTables& t, const DevFields& fld, int precisio
 // Double-float form: S_i split into FP32 (hi, lo) pairs; the apply runs on the
 // FP32 pipes with about 48 significant bits (ring output FP64).
 void launch_split_df(const double* in, float2* out, int64_t n, cudaStream_t st);
-void launch_schur_explicit_df(const DevTables& t, const float2* Sexp, const SchurIO& io,
-                              cudaStream_t st);
+// Returns the number of blocks; split as for launch_schur_explicit.
+int launch_schur_explicit_df(const DevTables& t, const float2* Sexp, const SchurIO& io, int split,
+                             cudaStream_t st);
 // Returns the number of blocks (one delta partial each); split: CTAs per
 // subdomain of the native FP64 form (1, 2 or 4; others mean 2).
 int launch_schur_explicit(const DevTables& t, int precision, const void* Sexp, const SchurIO& io, int split,
