@@ -4,6 +4,8 @@ synthetic workloads through the C ABI and prints the statistics.
     python -m paper_1501_06211_gb300.run --workload c1 --solves 2
     python -m paper_1501_06211_gb300.run --workload c4 --topopt-steps 20 --learner history
     python -m paper_1501_06211_gb300.run --workload c4 --topopt-steps 40 --tol-eta 0.1
+    python -m paper_1501_06211_gb300.run --workload c4 --topopt-steps 40 --tol-eta 0.1 \
+        --learner history --coarse x0
 
 Run from the repository root (the workload generators live in `workloads/`).
 """
@@ -24,6 +26,8 @@ def main(argv=None):
     ap.add_argument("--learner", default="none", choices=["none", "history", "cnn", "cnn+history"])
     ap.add_argument("--tol-eta", type=float, default=0.0,
                     help="topology steps: adaptive tolerance from successive compliances (0: --tol)")
+    ap.add_argument("--coarse", default="x0+correct", choices=["x0", "x0+correct"],
+                    help="learner coarse space: Galerkin initial guess only, or with the correction")
     ap.add_argument("--sub", type=int, default=0,
                     help="subdomain edge in elements instead of the workload's own (0: keep)")
     args = ap.parse_args(argv)
@@ -43,7 +47,8 @@ def main(argv=None):
         if args.learner != "none":
             m = {"history": ddel.DDEL_LEARN_HISTORY, "cnn": ddel.DDEL_LEARN_CNN,
                  "cnn+history": ddel.DDEL_LEARN_CNN_HISTORY}[args.learner]
-            learner = ddel.Learner(s, mode=m)
+            flags = ddel.DDEL_COARSE_X0 | (ddel.DDEL_COARSE_CORRECT if args.coarse == "x0+correct" else 0)
+            learner = ddel.Learner(s, mode=m, k_history=4, coarse_flags=flags)
         ne = 1
         for n in cfg["ne"]:
             ne *= n
