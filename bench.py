@@ -383,7 +383,7 @@ def learned_vs_plain(ddel, torch, workloads, stream, steps=100, skip=4):
     coarse correction in the iteration.  Steps after the first
     `skip` are timed; time per step is the device time of the whole Picard
     step (filter, assembly, factorisation, coarse set-up, solve, training,
-    OC).  The plain form stays the judge of the error: every form stops on the
+    OC).  The plain form stays the reference for the error: every form stops on the
     same FP64 residual test."""
     cfg = workloads.config("c4")
     ne = int(cfg["ne"][0] * cfg["ne"][1])
