@@ -92,10 +92,11 @@ def test_3d_steps(name):
     assert rel(u.cpu().numpy(), o["dds"].back_substitute(o["f"], xo)) < 1e-10
 
 
+@pytest.mark.parametrize("theta", [0.5, 0.3], ids=["theta_half", "theta_hopt"])
 @pytest.mark.parametrize("prec", [0, 1])
 @pytest.mark.parametrize("name", list(CASES))
-def test_3d_solve(name, prec):
-    s, o = solver(name, precision=prec, tol=1e-10, max_it=20000)
+def test_3d_solve(name, prec, theta):
+    s, o = solver(name, precision=prec, tol=1e-10, max_it=20000, theta=theta)
     u, st = s.solve(check=False)
     assert st.relres <= 1e-9, st.as_dict()
     assert rel(u, o["u_ref"]) <= (1e-8 if prec == 0 else 1e-6), st.as_dict()
