@@ -84,20 +84,26 @@ __device__ __forceinline__ int nz_col3(const SubInfo& si, int i, int w, int BP) 
 }
 
 // C(i, j) += alpha * sum_m A(i, m) B(j, m) for i < M, j < N (j <= i when lower;
-// with b_tri the caller guarantees B(j, m) = 0 for m < j),
+// with b_tri the caller guarantees B(j, m) = 0 for m < j, with a_band >= 0
+// that A(i, m) = 0 for m < i - a_band, which a lower product also needs of B),
 // with general strides A(i, m) = A[i * ai + m * am], B(j, m) = B[j * bj + m * bm],
 // C(i, j) = C[i * ci + j * cj].  32 x 32 x 32 tiles through shared memory.
 template <typename T>
 __device__ void cta_gemm(int M, int N, int K, const T* A, int ai, int am, const T* B, int bj, int bm,
-                         T* C, int ci, int cj, T alpha, bool lower, T* sA, T* sB, bool b_tri = false) {
+                         T* C, int ci, int cj, T alpha, bool lower, T* sA, T* sB, bool b_tri = false,
+                         int a_band = -1) {
   const int tid = threadIdx.x;
   const int ty = tid / 16, tx = tid % 16;  // each thread: rows ty, ty+16; cols tx, tx+16
   for (int i0 = 0; i0 < M; i0 += TB)
     for (int j0 = 0; j0 < N; j0 += TB) {
       if (lower && j0 > i0 + TB - 1) continue;
       T acc[2][2] = {{T(0), T(0)}, {T(0), T(0)}};
-      // b_tri: B(j, m) = 0 for m < j, so the tile's products start at m = j0
-      for (int m0 = b_tri ? j0 : 0; m0 < K; m0 += TB) {
+      // b_tri: B(j, m) = 0 for m < j, so the tile's products start at m = j0;
+      // a_band >= 0: A(i, m) = 0 for m < i - a_band, and with j <= i (lower)
+      // the tile's products start at the chunk holding i0 - a_band
+      int m_start = b_tri ? j0 : 0;
+      if (a_band >= 0 && lower) m_start = max(m_start, ((i0 - a_band) / TB) * TB);
+      for (int m0 = m_start; m0 < K; m0 += TB) {
         for (int q = tid; q < TB * TB; q += kT3) {
           const int a = q / TB, b = q % TB;  // a: row in tile, b: m in tile
           const int i = i0 + a, j = j0 + a, m = m0 + b;
@@ -269,7 +275,11 @@ __global__ void __launch_bounds__(kT3) factor3d_kernel(DevTables t, const T* __r
       __syncthreads();
       if (k > 0) {  // A -= C_k C_k^T, C_k column-major in the factor
         const T* Ck = fb + (int64_t)k * STAGE;
-        cta_gemm<T>(BP, BP, BP, Ck, 1, BP, Ck, 1, BP, A, BP, 1, T(-1), true, sA, sB);
+        // C_k(i, m) = 0 below the lowest column row i couples to in plane
+        // k - 1, 3 (i / 3) - 3 icnt_2 - 3 >= i - 3 icnt_2 - 5: the product
+        // skips those chunks
+        cta_gemm<T>(BP, BP, BP, Ck, 1, BP, Ck, 1, BP, A, BP, 1, T(-1), true, sA, sB, false,
+                    3 * si.icnt[2] + 5);
       }
     }
     cta_cholesky<T>(A, BP, sA, sB, &bad);
