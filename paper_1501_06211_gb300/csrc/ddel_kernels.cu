@@ -146,7 +146,8 @@ __device__ __forceinline__ T entry2d(const DevTables& t, const SubInfo& si, cons
 //
 // One CTA of kFacThreads threads per subdomain, every block in shared memory:
 //  (a) the lower triangle of A_kk (nonzero only where the nodes' y differ by
-//      at most one) minus C_k C_k^T, in TS x TS register tiles;
+//      at most one) minus C_k C_k^T, in TS x TS register tiles, over the
+//      columns where C_k does not vanish;
 //  (b) blocked right-looking Cholesky with PW-wide panels: the diagonal block
 //      by one warp (one lane per entry of each column step's update), each
 //      panel row by one thread, the trailing update in TS x TS tiles -- three
@@ -217,10 +218,16 @@ __global__ void __launch_bounds__(kFacThreads, BP == 32 ? 4 : 1)
   const int nb = si.nb;
   T* fb = factor + si.factor_off;
   for (int k = 0; k < nb; ++k) {
-    // (a) lower triangle of A_kk - C_k C_k^T
+    // (a) lower triangle of A_kk - C_k C_k^T.  C_k(i, m) vanishes below the
+    // lowest column row i couples to, 2 (i / 2) - 2 (the coupling computed in
+    // (e) adds no term there), so a tile row's products start at TS ti - 2;
+    // the tiles go row by row so that the lanes of a warp share that start.
     for (int q = tid; q < NT * (NT + 1) / 2; q += kFacThreads) {
-      int ti, tj;
-      lower_tile(q, NT, ti, tj);
+      int ti = 0, tj = q;
+      while (tj > ti) {
+        tj -= ti + 1;
+        ++ti;
+      }
       T acc[TS][TS];
 #pragma unroll
       for (int u = 0; u < TS; ++u)
@@ -228,7 +235,7 @@ __global__ void __launch_bounds__(kFacThreads, BP == 32 ? 4 : 1)
         for (int v = 0; v < TS; ++v) acc[u][v] = T(0);
       if (k > 0) {
 #pragma unroll 4
-        for (int m = 0; m < BP; ++m) {
+        for (int m = max(0, TS * ti - 2); m < BP; ++m) {
           T a[TS], b[TS];
           if constexpr (TS == 4) {
             lds4(CT + m * BP + 4 * ti, a);
@@ -782,7 +789,7 @@ __global__ void __launch_bounds__(256) schur_form2d_kernel(DevTables t, const T*
         const int r = i / NR, j = i % NR;
         T v = Tb[i];
 #pragma unroll 8
-        for (int m = 0; m < BP; ++m) v -= Cs[m * BP + r] * Wb[m * NR + j];
+        for (int m = max(0, 2 * (r >> 1) - 2); m < BP; ++m) v -= Cs[m * BP + r] * Wb[m * NR + j];  // C_k's band
         Tb[i] = v;
       }
       __syncthreads();
@@ -896,7 +903,8 @@ __global__ void __launch_bounds__(256) schur_form2d_df_kernel(DevTables t, const
         const int r = i / NR, j = i % NR;
         float2 v = Tb[i];
 #pragma unroll 8
-        for (int m = 0; m < BP; ++m) df_mad(v.x, v.y, Cs[m * BP + r], Wb[m * NR + j]);
+        for (int m = max(0, 2 * (r >> 1) - 2); m < BP; ++m)  // C_k vanishes below its band
+          df_mad(v.x, v.y, Cs[m * BP + r], Wb[m * NR + j]);
         Tb[i] = v;
       }
       __syncthreads();
@@ -985,11 +993,13 @@ __global__ void __launch_bounds__(256) form_w2d_kernel(DevTables t, const T* __r
     for (int i = tid; i < BP * GC; i += 256) Tb[i] = kig_entry2d<T>(t, si, ke, sc, k, i / GC, rloc[i % GC]);
     __syncthreads();
     if (k > 0) {  // T = B_k - C_k W_{k-1}
+      // C_k(r, m) vanishes below the lowest column row r couples to in plane
+      // k - 1, 2 (r / 2) - 2: the products start there (a warp shares r)
       for (int i = tid; i < BP * GC; i += 256) {
         const int r = i / GC, j = i % GC;
         T v = Tb[i];
 #pragma unroll 8
-        for (int m = 0; m < BP; ++m) v -= Cs[m * BP + r] * Wp[m * GC + j];
+        for (int m = max(0, 2 * (r >> 1) - 2); m < BP; ++m) v -= Cs[m * BP + r] * Wp[m * GC + j];
         Tb[i] = v;
       }
       __syncthreads();
