@@ -445,7 +445,9 @@ int ddel_fixed_mask(const ddel_ctx* ctx, uint8_t* out);
 /* Counters and work estimates for profiling (host output).  schur_apply_bytes:
  * algorithmic bytes of one Schur application in the active form and precision
  * (explicit: sum of n_ring_i^2 matrix entries; implicit: the nonzero entries of
- * the block factors read twice, forward and backward) plus the ring vectors. */
+ * the block factors -- the D_k triangles and the C_k without their zero band
+ * below each row's lowest coupled column -- read twice, forward and backward)
+ * plus the ring vectors. */
 typedef struct {
   int64_t launches_total;          /* kernel launches issued by the context */
   int64_t launches_since_assemble; /* launches since the last ddel_assemble */

@@ -2016,8 +2016,15 @@ int ddel_kernel_info(const ddel_ctx* ctx, ddel_kernel_info_t* out) {
     if (ctx->explicit_ok[prec]) {
       mat += (int64_t)si.n_ring * si.n_ring;
     } else {
+      // the D_k triangles and the nonzeros of the C_k: C_k(i, m) = 0 below the
+      // lowest column row i couples to in the plane before
       const int64_t b = si.bsz;
-      mat += 2 * (si.nb * b * (b + 1) / 2 + (si.nb > 0 ? si.nb - 1 : 0) * b * b);
+      int64_t cnz = 0;
+      for (int64_t i = 0; i < b; ++i) {
+        const int64_t lo = ctx->S.dim == 3 ? 3 * (i / 3) - 3 * si.icnt[2] - 3 : 2 * (i / 2) - 2;
+        cnz += b - std::max<int64_t>(0, lo);
+      }
+      mat += 2 * (si.nb * b * (b + 1) / 2 + (si.nb > 0 ? si.nb - 1 : 0) * cnz);
     }
   }
   // matrix entries read once, plus the ring gather (z and p, FP64) and the ring output

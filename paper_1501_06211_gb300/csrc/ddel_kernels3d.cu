@@ -439,9 +439,9 @@ __global__ void __launch_bounds__(kT3) schur3d_kernel(DevTables t, const T* __re
           if (have_x) v -= ebe_local3d<T>(ke, sc, xloc, s, x - si.lo[0], y - si.lo[1], z - si.lo[2], c);
         }
       }
-      if (k > 0) {
+      if (k > 0) {  // C_k(r, j) = 0 below column 3 (r / 3) - 3 icnt_2 - 3
         const T* yp = ybuf + (k - 1) * BP;
-        for (int j = 0; j < BP; ++j) v -= Ck[(int64_t)j * BP + r] * yp[j];
+        for (int j = max(0, 3 * (r / 3) - 3 * si.icnt[2] - 3); j < BP; ++j) v -= Ck[(int64_t)j * BP + r] * yp[j];
       }
       vbuf[r] = v;
     }
@@ -461,7 +461,8 @@ __global__ void __launch_bounds__(kT3) schur3d_kernel(DevTables t, const T* __re
       T acc = T(0);
       if (k + 1 < nb) {
         const T* tn = ybuf + (k + 1) * BP;
-        for (int r = lane; r < BP; r += 32) acc += Cn[(int64_t)j * BP + r] * tn[r];
+        // C_{k+1}(r, j) = 0 for r > j + 3 icnt_2 + 5
+        for (int r = lane; r < min(BP, j + 3 * si.icnt[2] + 6); r += 32) acc += Cn[(int64_t)j * BP + r] * tn[r];
       }
       acc = warp_sum(acc);
       if (lane == 0) vbuf[j] = ybuf[k * BP + j] - acc;
@@ -578,7 +579,7 @@ __global__ void __launch_bounds__(kT3D, 3) schur3d_df_kernel(DevTables t, const 
   const int hh = lane >> 4, hl = lane & 15;
   const SubInfo si = t.subs[sub];
   const int s = t.s, s1 = s + 1, nloc = s1 * s1 * s1, NM = t.BP;
-  const int n = si.bsz, nb = si.nb, nh = (n + 1) / 2;
+  const int n = si.bsz, nb = si.nb, cy = 3 * si.icnt[2];
   // triangular passes: kTriSlots column (forward) / row (backward) chunks of
   // width wc, chunk c serving the rows r >= c wc (forward) or the outputs
   // j < (c + 1) wc (backward)
@@ -635,10 +636,14 @@ __global__ void __launch_bounds__(kT3D, 3) schur3d_df_kernel(DevTables t, const 
   for (int k = 0; k < nb; ++k) {
     const float2* D = fw + (int64_t)k * (szC + szD);
     for (int r0 = 0; r0 < n; r0 += kT3D / 2) {
-      const int r = r0 + warp * 16 + hl;
+      const int rg = r0 + warp * 16, r = rg + hl;
       float ah = 0.f, al = 0.f;
       if (k > 0 && r < n) {
-        const int j0 = hh ? nh : 0, j1 = hh ? n : nh;
+        // C_k(r, m) = 0 for m < 3 (r / 3) - cy - 3 (below the lowest node of
+        // plane k - 1 that row r couples to): the 16 rows of this group read
+        // the columns from their first row's bound on, two halves per row
+        const int jl = max(0, 3 * (rg / 3) - cy - 3), jm = jl + (n - jl + 1) / 2;
+        const int j0 = hh ? jm : jl, j1 = hh ? n : jm;
         df_dot(D - szC, j0 * n + r, n, 0, ybuf + (k - 1) * NM, j0, j1, ah, al);
       }
       df_half_sum(ah, al);
@@ -676,10 +681,13 @@ __global__ void __launch_bounds__(kT3D, 3) schur3d_df_kernel(DevTables t, const 
   for (int k = nb - 1; k >= 0; --k) {
     const float2* Db = bw + (int64_t)(nb - 1 - k) * (szC + szD);
     for (int j0 = 0; j0 < n; j0 += kT3D / 2) {
-      const int j = j0 + warp * 16 + hl;
+      const int jg = j0 + warp * 16, j = jg + hl;
       float ah = 0.f, al = 0.f;
       if (k + 1 < nb && j < n) {
-        const int i0 = hh ? nh : 0, i1 = hh ? n : nh;
+        // C_{k+1}(i, j) = 0 for i > j + cy + 5: the group's 16 outputs read
+        // the rows up to its last output's bound, two halves per output
+        const int ie = min(n, jg + cy + 21), im = (ie + 1) / 2;
+        const int i0 = hh ? im : 0, i1 = hh ? ie : im;
         df_dot(Db - szC, i0 * n + j, n, 0, ybuf + (k + 1) * NM, i0, i1, ah, al);
       }
       df_half_sum(ah, al);
