@@ -255,3 +255,56 @@ def test_dof_scaled_face_blocks_match_stiffness_diagonal():
             for fb in pre.blocks:
                 Sf = np.linalg.inv(P[np.ix_(fb.dofs, fb.dofs)])
                 assert np.allclose(np.diag(Sf), Kd[fb.dofs], rtol=1e-10)
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_plane_coupling_of_the_block_cholesky_vanishes_below_its_band(dim):
+    # K_II ordered plane by plane (axis 0) is block tridiagonal (eq.
+    # NumberFive); its block Cholesky couples plane k to plane k - 1 through
+    # C_k = A_{k,k-1} L_{k-1}^-T.  Row i of C_k is L_{k-1}^-1 applied to row i
+    # of A_{k,k-1}, and a lower-triangular solve keeps the leading zeros of its
+    # right-hand side: C_k(i, m) = 0 exactly below the lowest node of plane
+    # k - 1 that row i couples to -- 2 (i // 2) - 2 in 2D, 3 (i // 3) - 3 n_z - 3
+    # in 3D (n_z interior nodes along z).  The factorisation and formation
+    # kernels skip those products.
+    import scipy.linalg as sla
+    if dim == 2:
+        cfg = workloads.small_config(32, 24, 8, seed=2)
+        grid = fem.Grid(2, 32, 24)
+        q = (2, 1)
+    else:
+        cfg = workloads.small_config(16, 12, 4, seed=1, nz=12)
+        grid = fem.Grid(3, 16, 12, 12)
+        q = (2, 1, 1)
+    fixed, _ = fem.bc_from_spec(grid, cfg["bc"])
+    Ke = fem.element_stiffness(dim, cfg["E"], cfg["nu"])
+    rho = workloads.density(cfg)
+    K = fem.assemble(grid, Ke, fem.element_factors(rho, cfg["E"], cfg["p"])).tocsr()
+    dec = dd.Decomposition(grid, cfg["sub"], fixed)
+    I = dec.interior_dofs[dec.sub_index(*q)]  # a subdomain away from every boundary
+    assert not fixed[I].any()
+    n_in = cfg["sub"] - 1  # interior nodes per axis
+    b = dim * n_in ** (dim - 1)  # rows per plane
+    assert len(I) == b * n_in
+    A = K[I][:, I].toarray()
+    Lprev = np.linalg.cholesky(A[:b, :b])
+    S = A[:b, :b]
+    checked = 0
+    for k in range(1, n_in):
+        Akk = A[k * b:(k + 1) * b, k * b:(k + 1) * b]
+        Akm = A[k * b:(k + 1) * b, (k - 1) * b:k * b]
+        C = sla.solve_triangular(Lprev, Akm.T, lower=True).T  # A_{k,k-1} L^-T
+        for i in range(b):
+            lo = 2 * (i // 2) - 2 if dim == 2 else 3 * (i // 3) - 3 * n_in - 3
+            if lo > 0:
+                assert np.all(C[i, :lo] == 0.0), (k, i, lo)
+                checked += lo
+            # and the bound is tight where that node exists (3D: z > 0 too):
+            # its column is nonzero
+            if lo >= 0 and (dim == 2 or (i // 3) % n_in > 0):
+                assert C[i, lo] != 0.0, (k, i, lo)
+        S = Akk - C @ C.T
+        Lprev = np.linalg.cholesky(S)
+    assert checked > 0
+    # and the plane blocks factor the whole interior block exactly
+    assert np.allclose(np.linalg.cholesky(A)[-b:, -b:], Lprev, rtol=1e-10, atol=1e-12 * np.abs(A).max())
