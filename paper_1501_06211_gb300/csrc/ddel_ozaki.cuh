@@ -186,7 +186,7 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
 
 // Tile (ta, tb) of one subdomain: the tile's own entries (K_GG for S_i) minus 2^(e_i + e_j) sum_d
 // 2^(-B d) C_d, C_d = sum_{p + q = d} D_p^T D_q accumulated in tensor memory,
-// d from S + 1 down to 2 (small terms first).  256 threads: thread (w, l)
+// d from S + 1 down to 2 (small terms first), the sum over d in FP64.  256 threads: thread (w, l)
 // keeps row 32 (w % 4) + l, columns 64 (w / 4) .. + 63 of the FP64 tile in
 // registers (warp w reads tensor-memory lanes 32 (w % 4) ..).  Thread 0
 // drives a pipeline of kOzStages stages: per step (pair, chunk) one bulk copy
@@ -247,13 +247,14 @@ __global__ void __launch_bounds__(kOzThreads, 1) ozaki_syrk_kernel(DevTables t, 
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
-  // this thread's part of the tile: row i, columns jc .. jc + 63, the tile's
-  // own entries first
+  // this thread's part of the tile: row i, columns jc .. jc + 63.  acc sums
+  // T = sum_d 2^(-B d) C_d in FP64 (each term exact: an integer-valued FP32
+  // sum times a power of two); the tile's own entries and the column scales
+  // 2^(e_i + e_j) join once, at the end
   const int i = 32 * (warp & 3) + lane, jc = 64 * (warp >> 2);
   double acc[64];
 #pragma unroll
-  for (int c = 0; c < 64; ++c)
-    acc[c] = tile.value(t, si, tsm, ta * kOzTile + i, tb * kOzTile + jc + c, i, jc + c);
+  for (int c = 0; c < 64; ++c) acc[c] = 0.0;
   const uint32_t dt = tmem_base;
   constexpr uint32_t idesc = idesc_bf16_f32(kOzTile, kOzTile);
   const int NRT = NR / 128, NKC = Kp / 64;
@@ -313,15 +314,13 @@ __global__ void __launch_bounds__(kOzThreads, 1) ozaki_syrk_kernel(DevTables t, 
     __syncthreads();
     if (s_fail) break;
     tc_fence_after();
-    const float rs = ldexpf(1.0f, ex[i] - bits * d);
+    const double rsd = ldexp(1.0, -bits * d);
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
       float v[32];
       tmem_ld32(dt + ((uint32_t)(32 * (warp & 3)) << 16) + jc + 32 * h, v);
 #pragma unroll
-      for (int c = 0; c < 32; ++c)  // 2^(e_i - B d) C exact in FP32, then 2^e_j in FP64
-        acc[32 * h + c] = fma(-(double)__fmul_rn(v[c], rs), ldexp(1.0, ex[kOzTile + jc + 32 * h + c]),
-                              acc[32 * h + c]);
+      for (int c = 0; c < 32; ++c) acc[32 * h + c] = fma((double)v[c], rsd, acc[32 * h + c]);
     }
     tc_fence_before();
     __syncthreads();
@@ -334,7 +333,9 @@ __global__ void __launch_bounds__(kOzThreads, 1) ozaki_syrk_kernel(DevTables t, 
 #pragma unroll
   for (int c = 0; c < 64; ++c) {
     const int gj = tb * kOzTile + jc + c;
-    tile.store(t, si, sub, gi, gj, acc[c]);
-    if (ta != tb) tile.store(t, si, sub, gj, gi, acc[c]);
+    // the tile's entry minus 2^(e_i + e_j) T (an exact power-of-two scaling)
+    const double v = tile.value(t, si, tsm, gi, gj, i, jc + c) - ldexp(acc[c], ex[i] + ex[kOzTile + jc + c]);
+    tile.store(t, si, sub, gi, gj, v);
+    if (ta != tb) tile.store(t, si, sub, gj, gi, v);
   }
 }
