@@ -78,7 +78,7 @@ struct ddel_ctx {
   int graph_iters = 0;
   int64_t launches = 0;           // kernel launches issued (graph-contained ones included)
   int64_t launches_at_assemble = 0;
-  cudaEvent_t ev[10] = {};        // [8], [9]: around the last ddel_factor
+  cudaEvent_t ev[11] = {};        // [8], [9]: around the last ddel_factor; [7], [10]: PCG state copies
   double t_factor_ms = 0.0;       // device time of the last ddel_factor (with S_i formation)
   // topology optimisation buffers (allocated on first use)
   double *rho_f = nullptr, *dcf = nullptr, *dc = nullptr, *dv = nullptr, *topo_u = nullptr;
@@ -295,8 +295,9 @@ int pcg_start(ddel_ctx* ctx, int prec, const double* g, bool apply32) {
 }
 
 // Issues check_every iterations and the copy of the PCG state to the host
-// (asynchronous; ctx->ev[7] is recorded after the copy).
-int pcg_issue(ddel_ctx* ctx, int prec, bool apply32) {
+// into h_st[slot] (asynchronous; ctx->ev[7] for slot 0, ctx->ev[10] for slot
+// 1, is recorded after the copy).
+int pcg_issue(ddel_ctx* ctx, int prec, bool apply32, int slot = 0) {
   cudaStream_t s = ctx->stream;
   const int per = pcg_per(ctx);
   if (ctx->opt.use_graph) {
@@ -305,23 +306,39 @@ int pcg_issue(ddel_ctx* ctx, int prec, bool apply32) {
     for (int i = 0; i < per; ++i) pcg_iteration(ctx, prec, apply32, i & 1);
   }
   ctx->launches += 2 * per;
-  CK(cudaMemcpyAsync(ctx->h_st, ctx->st, sizeof(PcgState), cudaMemcpyDeviceToHost, s));
-  CK(cudaEventRecord(ctx->ev[7], s));
+  CK(cudaMemcpyAsync(ctx->h_st + slot, ctx->st, sizeof(PcgState), cudaMemcpyDeviceToHost, s));
+  CK(cudaEventRecord(ctx->ev[slot ? 10 : 7], s));
   return DDEL_OK;
 }
 
+// Batches of `per` iterations until the state read back says done.  The next
+// batch is issued before the state of the current one is read (two in
+// flight, their states in h_st[0] / h_st[1]), so the GPU does not idle while
+// the host waits and decides; a batch issued after convergence exits at once
+// in every kernel (the done flag) and leaves the state as it was.  The final
+// state ends in h_st[0].
 int pcg_run(ddel_ctx* ctx, int prec, const double* g, int* iters, int* status,
             bool apply32 = false) {
   int rc = pcg_start(ctx, prec, g, apply32);
   if (rc) return rc;
   const int per = pcg_per(ctx);
   const int max_checks = ctx->opt.max_it / per + 2;
+  rc = pcg_issue(ctx, prec, apply32, 0);
+  if (rc) return rc;
+  int issued = 1, last = 0;
   for (int chk = 0; chk < max_checks; ++chk) {
-    rc = pcg_issue(ctx, prec, apply32);
-    if (rc) return rc;
-    CK(cudaEventSynchronize(ctx->ev[7]));
-    if (ctx->h_st->done) break;
+    if (issued < max_checks) {
+      rc = pcg_issue(ctx, prec, apply32, issued & 1);
+      if (rc) return rc;
+      ++issued;
+    }
+    last = chk & 1;
+    CK(cudaEventSynchronize(ctx->ev[last ? 10 : 7]));
+    if (ctx->h_st[last].done) break;
   }
+  // no state copy stays in flight past this point
+  CK(cudaEventSynchronize(ctx->ev[((issued - 1) & 1) ? 10 : 7]));
+  if (last) ctx->h_st[0] = ctx->h_st[1];
   *iters = ctx->h_st->it;
   *status = ctx->h_st->done ? ctx->h_st->status : DDEL_ENOCONV;
   return DDEL_OK;
@@ -753,7 +770,7 @@ int ddel_create(const ddel_mesh* mesh, const ddel_material* mat, const ddel_bc* 
         bad(dalloc(ctx, &ctx->err, 4 * sizeof(int))))
       goto fail_out;
     ctx->bad_sub = ctx->err + 1;
-    if (bad(cudaMallocHost(&ctx->h_st, sizeof(PcgState))) ||
+    if (bad(cudaMallocHost(&ctx->h_st, 2 * sizeof(PcgState))) ||
         bad(cudaMallocHost(&ctx->h_nrm, 2 * sizeof(double))) ||
         bad(cudaMallocHost(&ctx->h_err, 4 * sizeof(int))))
       goto fail_out;
