@@ -2,11 +2,12 @@
 // shared memory (interior planes of up to 8 x 8 nodes x 3 components).
 //
 //  * factor3d_kernel: one CTA per subdomain; per interior plane k the block
-//    A_kk - C_k C_k^T is assembled in a global scratch matrix, factorised by a
-//    blocked right-looking Cholesky (32-wide panels through shared memory),
-//    inverted by blocked forward substitution (D_k = L_kk^-1), and
-//    C_{k+1} = A_{k+1,k} D_k^T is formed from the 27 nonzeros per row of the
-//    plane coupling A_{k+1,k}.  The factor layout
+//    A_kk - C_k C_k^T is assembled in a global scratch matrix (the product
+//    over C_k's nonzero band only; optionally on the tensor cores, one launch
+//    per plane), factorised by a blocked right-looking Cholesky (32-wide
+//    panels through shared memory), inverted by blocked forward substitution
+//    (D_k = L_kk^-1), and C_{k+1} = A_{k+1,k} D_k^T is formed from the 27
+//    nonzeros per row of the plane coupling A_{k+1,k}.  The factor layout
 //    is the one of the 2D path: [C_k (column-major) | D_k (packed lower,
 //    column-major)] per plane.
 //  * schur3d_kernel: one CTA per subdomain: w = f_I - K_IG x element by element,

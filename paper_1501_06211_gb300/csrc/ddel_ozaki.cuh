@@ -1,6 +1,8 @@
-// Tensor-core (tcgen05) formation of the local Schur complements at FP64
-// accuracy; included by ddel_kernels.cu inside its anonymous namespace, after
-// the element helpers (kgg_entry2d) it uses.
+// Tensor-core (tcgen05) products W^T W at FP64 accuracy: the formation of
+// the local Schur complements, and (opt-in) the C_k C_k^T of the 3D factor
+// planes.  Included inside the anonymous namespace of ddel_kernels.cu and of
+// ddel_kernels3d.cu, each of which defines the tile policy (what the product
+// is subtracted from, where it goes) it instantiates the SYRK kernel with.
 #pragma once
 
 // Local Schur complements S_i = K_GG^(i) - W^T W (W = L^-1 K_IG^(i), FP64)
@@ -15,8 +17,8 @@
 // magnitude stays below 2^24, which B is chosen for (B = 6 up to 1489 rows of
 // W, else 5); the pairs of one d = p + q share a scale and one accumulator.
 // Dropped pairs (p + q > S + 1) leave a relative truncation below 2^-(B (S+1)),
-// S B >= 54 bits.  The accumulators are drained into FP64 (smallest d
-// first) on top of K_GG.
+// S B >= 54 bits.  The accumulators are drained into an FP64 sum over d
+// (smallest d first), scaled by 2^(e_i + e_j) and subtracted from K_GG once.
 //
 // Both precisions slice to 54 bits: the FP32 form rounds the FP64-accurate
 // S_i once to FP32.
@@ -24,9 +26,9 @@
 // ozaki_slice_kernel: per subdomain and ring column, e_j and the slices, each
 //   stored as ready-made 16 KB operand images (below).
 // ozaki_syrk_kernel: one CTA of 256 threads per (subdomain, 128 x 128 tile of
-//   S, upper triangle of tiles); one thread streams operand images into
-//   shared memory by bulk copies and issues the MMAs, all eight warps drain
-//   the accumulator into the FP64 tile they keep in registers.
+//   the product, upper triangle of tiles); one thread streams operand images
+//   into shared memory by bulk copies and issues the MMAs, all eight warps
+//   drain the accumulator into the FP64 tile they keep in registers.
 
 
 constexpr int kOzThreads = 256;
