@@ -2309,7 +2309,7 @@ void launch_schur_form_tc(const DevTables& t, const DevFields& fld, int precisio
       form_w2d_kernel<double, 96, 256, kFormGC><<<dim3(t.n_sub, 256 / kFormGC), 256, form_w_smem<double, 96, 256>(t),
                                                   st>>>(t, t.Ke64, fld.scale64, fac, W);
     const OzSlab src{(int64_t)t.nb_max * t.BP * NR, 0, NR, -1, NR};
-    ozaki_slice_kernel<double><<<dim3(t.n_sub, NR / 32), 256, 0, st>>>(t, W, src, NR, Kp, S, Wsl, expo);
+    launch_ozaki_slice<double>(dim3(t.n_sub, NR / 32), st, t, W, src, NR, Kp, Wsl, expo);
     if (NR == 128)
       ozaki_syrk_kernel<128, FormTile<128, double>><<<dim3(t.n_sub, 1), kOzThreads, sm, st>>>(
           t, FormTile<128, double>{t.Ke64, fld.scale64, reinterpret_cast<double*>(Sexp)}, Wsl, expo, Kp, S, err);
@@ -2329,7 +2329,7 @@ void launch_schur_form_tc(const DevTables& t, const DevFields& fld, int precisio
       form_w2d_kernel<float, 96, 256, kFormGC><<<dim3(t.n_sub, 256 / kFormGC), 256, form_w_smem<float, 96, 256>(t),
                                                  st>>>(t, t.Ke32, fld.scale32, fac, W);
     const OzSlab src{(int64_t)t.nb_max * t.BP * NR, 0, NR, -1, NR};
-    ozaki_slice_kernel<float><<<dim3(t.n_sub, NR / 32), 256, 0, st>>>(t, W, src, NR, Kp, S, Wsl, expo);
+    launch_ozaki_slice<float>(dim3(t.n_sub, NR / 32), st, t, W, src, NR, Kp, Wsl, expo);
     if (NR == 128)
       ozaki_syrk_kernel<128, FormTile<128, float>><<<dim3(t.n_sub, 1), kOzThreads, sm, st>>>(
           t, FormTile<128, float>{t.Ke64, fld.scale64, reinterpret_cast<float*>(Sexp)}, Wsl, expo, Kp, S, err);

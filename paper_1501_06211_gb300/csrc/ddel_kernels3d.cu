@@ -870,8 +870,7 @@ int launch_factor3d(const DevTables& t, const DevFields& fld, int precision, voi
   for (int k = 0; k < t.nb_max; ++k) {
     if (k > 0) {
       const OzSlab src{0, k * STAGE, t.BP, k, t.BP};
-      ozaki_slice_kernel<double><<<dim3(t.n_sub, NR / 32), 256, 0, st>>>(t, (const double*)factor, src, NR, Kp, S,
-                                                                          Wsl, expo);
+      launch_ozaki_slice<double>(dim3(t.n_sub, NR / 32), st, t, (const double*)factor, src, NR, Kp, Wsl, expo);
       const Factor3Tile tile{t.Ke64, fld.scale64, wd, k};
       if (NR == 128)
         ozaki_syrk_kernel<128, Factor3Tile><<<dim3(t.n_sub, 1), kOzThreads, sm, st>>>(t, tile, Wsl, expo, Kp, S, err);

@@ -69,16 +69,17 @@ struct OzSlab {
 // column maxima, then per thread one column and 8 consecutive rows, written as
 // one 16-byte unit per slice.  Columns from ncols to NR and rows from K to Kp
 // are zero.
-template <typename TW>
+template <typename TW, int B, int S>
 __global__ void __launch_bounds__(256) ozaki_slice_kernel(DevTables t, const TW* __restrict__ W, OzSlab src, int NR,
-                                                          int Kp, int S, __nv_bfloat16* __restrict__ Wsl,
+                                                          int Kp, __nv_bfloat16* __restrict__ Wsl,
                                                           int* __restrict__ expo) {
+  static_assert(B * S >= 54 && B * S <= 55 && 30 % B == 0, "slice shape");
+  constexpr int NLO = 30 / B, HALF = 1 << (B - 1), MASK = (1 << B) - 1;
   const int sub = blockIdx.x, j0 = blockIdx.y * 32, tid = threadIdx.x;
   const int jl = tid & 31, ko = tid >> 5;  // column in the block, row offset
   const SubInfo si = t.subs[sub];
   const int K = src.plane < 0 ? si.nb * t.BP : (src.plane >= 1 && src.plane < si.nb ? t.BP : 0);
   const int ld = src.ld, jv = j0 + jl < src.ncols;  // this column holds data
-  const int bits = oz_bits(Kp);
   const TW* Wb = W + (src.plane < 0 ? (int64_t)sub * src.sub_stride : si.factor_off) + src.off;
   __shared__ double mx_s[8][32];
   __shared__ int e_s[32];
@@ -101,29 +102,52 @@ __global__ void __launch_bounds__(256) ozaki_slice_kernel(DevTables t, const TW*
   const int NRT = NR / 128, NKC = Kp / 64;
   unsigned char* img0 = reinterpret_cast<unsigned char*>(Wsl) + (int64_t)sub * S * NRT * NKC * 16384;
   for (int k8 = ko * 8; k8 < Kp; k8 += 64) {
-    // m = W 2^(B S - e) rounded to an integer (|m| <= 2^(B S), B S <= 55
-    // bits); its balanced base-2^B digits, most significant first, are the
-    // slices: d_p = round(rest / 2^(B (S - p))), rest -= d_p 2^(B (S - p)),
-    // so |d_1| <= 2^B, |d_p| <= 2^(B - 1) after, and m = sum_p d_p 2^(B (S - p))
-    long long m[8];
+    // m = W 2^(B S - e) rounded to an integer (|m| < 2^(B S), B S <= 55 bits);
+    // its balanced base-2^B digits are the slices, m = sum_p d_p 2^(B (S-1-p)):
+    // every digit but the top one in [-2^(B-1), 2^(B-1)), the top one
+    // |d_0| <= 2^B, all exact in BF16.  They are taken least significant
+    // first in 32-bit integers: the low 30 bits (NLO digits), then the high
+    // part plus the carry.
+    __align__(16) __nv_bfloat16 h[S][8];
 #pragma unroll
-    for (int r = 0; r < 8; ++r)
-      m[r] = jv && k8 + r < K ? __double2ll_rn(ldexp((double)Wb[(int64_t)(k8 + r) * ld + j], bits * S - e)) : 0ll;
+    for (int r = 0; r < 8; ++r) {
+      const long long m =
+          jv && k8 + r < K ? __double2ll_rn(ldexp((double)Wb[(int64_t)(k8 + r) * ld + j], B * S - e)) : 0ll;
+      int lo = (int)(m & ((1ll << 30) - 1)), y = (int)(m >> 30);  // m = y 2^30 + lo, 0 <= lo < 2^30
+#pragma unroll
+      for (int q = 0; q < NLO; ++q) {
+        const int d = ((lo + HALF) & MASK) - HALF;
+        lo = (lo - d) >> B;  // exact: lo - d is a non-negative multiple of 2^B
+        h[S - 1 - q][r] = __float2bfloat16_rn((float)d);
+      }
+      y += lo;  // the carry out of the low part, 0 or 1
+#pragma unroll
+      for (int p = S - 1 - NLO; p > 0; --p) {
+        const int d = ((y + HALF) & MASK) - HALF;
+        y = (y - d) >> B;  // exact: a multiple of 2^B
+        h[p][r] = __float2bfloat16_rn((float)d);
+      }
+      h[0][r] = __float2bfloat16_rn((float)y);
+    }
     const int kc = k8 >> 6;
     const int off = oz_img_off(c, k8 & 63);
-    for (int p = 0; p < S; ++p) {
-      const int sh = bits * (S - 1 - p);
-      __align__(16) __nv_bfloat16 h[8];
 #pragma unroll
-      for (int r = 0; r < 8; ++r) {
-        const long long d = sh > 0 ? (m[r] + (1ll << (sh - 1))) >> sh : m[r];
-        m[r] -= d * (1ll << sh);
-        h[r] = __float2bfloat16_rn((float)d);  // |d| <= 2^B: exact
-      }
+    for (int p = 0; p < S; ++p) {
       unsigned char* img = img0 + ((int64_t)(p * NRT + rt) * NKC + kc) * 16384;
-      *reinterpret_cast<uint4*>(img + off) = *reinterpret_cast<const uint4*>(h);
+      *reinterpret_cast<uint4*>(img + off) = *reinterpret_cast<const uint4*>(h[p]);
     }
   }
+}
+
+// Slices of a matrix for the tensor-core products (the digit width B and count
+// S follow from the rows Kp: B = 6, S = 9 up to 1489 rows, else B = 5, S = 11).
+template <typename TW>
+void launch_ozaki_slice(dim3 grid, cudaStream_t st, const DevTables& t, const TW* W, const OzSlab& src, int NR, int Kp,
+                        __nv_bfloat16* Wsl, int* expo) {
+  if (oz_bits(Kp) == 6)
+    ozaki_slice_kernel<TW, 6, 9><<<grid, 256, 0, st>>>(t, W, src, NR, Kp, Wsl, expo);
+  else
+    ozaki_slice_kernel<TW, 5, 11><<<grid, 256, 0, st>>>(t, W, src, NR, Kp, Wsl, expo);
 }
 
 // ---- tcgen05 helpers (single-CTA forms) ------------------------------------
