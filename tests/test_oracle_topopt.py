@@ -211,3 +211,44 @@ def test_table3_trend_of_the_oracle_picard_loop():
     its_growth = out[1][1] / out[0][1]
     assert step_growth > 1.0 and paper_step_growth > 1.0, out
     assert abs(its_growth - paper_its_growth) < 0.2, (out, paper_its_growth)
+
+
+def test_history_guess_under_the_adaptive_tolerance():
+    # The same Picard loop with the adaptive tolerance, each interface PCG
+    # started from the Galerkin guess (energy-norm best approximation) of the
+    # last four interface solutions instead of zero, no correction inside the
+    # iteration: the guess often already meets the step's loose tolerance, so
+    # the run needs far fewer PCG iterations and ends on the same compliance.
+    from oracle import coarse, dd
+    nx, ny, s = 32, 16, 8
+    grid, fixed, f, Ke = _mbb(nx, ny)
+    H = topopt.filter_matrix((nx, ny), 1.5)
+    norm_f = np.linalg.norm(f)
+
+    def run(history, steps=24):
+        rho = np.full(grid.n_elem, 0.5)
+        hist, its, sols = [], 0, []
+        for _ in range(steps):
+            tol = topopt.adaptive_tolerance(hist, 0.1, 1e-8, 1e-3)
+
+            def solve(fac):
+                nonlocal its
+                dec, K, dds = dd.build(grid, s, fixed, Ke, fac)
+                pre = dd.FacePreconditioner(dec, K)
+                g = dds.condense(f)
+                x0 = None
+                if history and sols:
+                    x0 = coarse.CoarseSpace(dds.schur_apply, np.stack(sols[-4:], axis=1)).x0(g)
+                x, k = dd.pcg(dds.schur_apply, pre.apply, g, tol, 5000, x0=x0, ref_norm=norm_f)[:2]
+                its += k
+                sols.append(x)
+                return dds.back_substitute(f, x)
+
+            rho, c, _, _ = topopt.topopt_step(grid, Ke, 1.0, 3.0, H, rho, f, solve, 0.5)
+            hist.append(c)
+        return hist, its
+
+    h_ad, it_ad = run(False)
+    h_hx, it_hx = run(True)
+    assert abs(h_hx[-1] - h_ad[-1]) <= 1e-3 * h_ad[-1], (h_hx[-1], h_ad[-1])
+    assert it_hx < 0.7 * it_ad, (it_hx, it_ad)
