@@ -75,6 +75,17 @@ def dist_env():
     return rank, world, local
 
 
+def max_over_ranks(values, dist=None, device="cpu"):
+    """Element-wise maximum of per-rank times over the process group: the job
+    takes as long as its slowest rank.  Without a process group (one rank) the
+    values come back unchanged."""
+    import torch
+    t = torch.tensor([float(v) for v in values], dtype=torch.float64, device=device)
+    if dist is not None:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return t.tolist()
+
+
 # --------------------------------------------------------------- clocks
 class Clocks:
     """Samples nvidia-smi during the timed region."""
@@ -269,10 +280,8 @@ def main():
         runs[name] = dict(s=s, f=f_d, u=u_d, ms=ms, stats=sts, steps=steps,
                           launches=launches_per_step(s))
     clk = clocks.stop()
-    times = torch.tensor([runs[n]["ms"] for n, *_ in FORMS], device="cuda")
-    if dist is not None:
-        dist.all_reduce(times, op=dist.ReduceOp.MAX)
-    for (n, *_), t in zip(FORMS, times.tolist()):
+    times = max_over_ranks([runs[n]["ms"] for n, *_ in FORMS], dist, "cuda")
+    for (n, *_), t in zip(FORMS, times):
         runs[n]["ms"] = t
 
     head = runs["fp64"]
@@ -291,7 +300,7 @@ def main():
         sb.factor()
         sb.solve(f_h, u_h)
     torch.cuda.synchronize()
-    e2e_ms = 1e3 * (time.perf_counter() - t0) / e2e_steps
+    e2e_ms = max_over_ranks([1e3 * (time.perf_counter() - t0) / e2e_steps], dist, "cuda")[0]
     h2d = rho_h.nbytes + f_h.nbytes
     d2h = u_h.nbytes
 
