@@ -165,13 +165,15 @@ def run_reference(args, rank, world):
         ms, rr = oracle_solve_ms(cfg, rho)
         times.append(ms)
     ms = sum(times) / len(times)
+    cores, model = cpu_info()
     sample = "one full solve per step: assembly + SuperLU direct solve + 2 FP64 refinement steps"
     out = {"impl": "reference", "metric": METRIC, "value": ms, "unit": "ms", "n_gpus": args.gpus,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": False,
            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
            "config": {"workload": WORKLOAD, "solver": "CPU oracle (SciPy SuperLU, serial)"},
            "relres": rr,
-           "cpu_baseline": {"value": ms, "unit": "ms", "cores": 1, "kind": "oracle", "sample": sample},
+           "cpu_baseline": {"value": ms, "unit": "ms", "cores": 1, "kind": "oracle", "sample": sample,
+                            "host": {"cores_available": cores, "cpu_model": model}},
            "e2e": {"value": ms, "unit": "ms", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out))
 

@@ -23,3 +23,4 @@ def test_reference_arm_prints_the_contract_line():
     assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["value"] == d["value"]
     assert d["e2e"] == {"value": d["value"], "unit": "ms", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
     assert d["relres"] <= 1e-8  # the oracle's direct solve meets the benchmark's tolerance
+    assert d["cpu_baseline"]["host"]["cores_available"] >= 1 and d["cpu_baseline"]["host"]["cpu_model"]
