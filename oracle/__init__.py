@@ -19,7 +19,8 @@ dd       Non-overlapping decomposition: Gamma / interior classification (Sec. 1)
          block partition (eq. NumberFour/NumberFive), Schur complement and the
          three-step solve (eq. 3MatSplit2), the face-local fractional interface
          preconditioner (eq. NumberEight, NumberNine, Sec. 3-4) and interface
-         PCG.
+         PCG, also in a relaxed mixed-precision form (a low-precision operator
+         once the residual is small, with FP64 reliable updates).
 direct   Global sparse direct solve with FP64 iterative refinement.
 krylov   GMRES on the full block system with the block upper-triangular right
          preconditioner of Sec. 3.

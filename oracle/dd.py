@@ -16,7 +16,8 @@ Follows the paper's Sec. 1-3 in its own notation:
   removed; the hot path uses exactly that face-local form as S~ (reading Q6),
   with a diagonal at the cross points (Q7) and a per-face scale (Q8).
 * The interface Krylov method is PCG on S u_G = g (reading Q4, stopping test
-  Q12).
+  Q12); `pcg_relaxed` is its mixed-precision form (the paper is silent on
+  precision below its double).
 """
 import itertools
 
@@ -356,6 +357,76 @@ def pcg(apply_S, apply_P, g, tol, max_it, x0=None, ref_norm=None):
         p = z + (rz_new / rz) * p
         rz = rz_new
     return x, it, hist
+
+
+def pcg_relaxed(apply_S, apply_S_lo, apply_P, g, tol, max_it, switch, delta=0.1, check_every=1,
+                ref_norm=None):
+    """PCG on S x = g that switches to a cheaper, less accurate operator S_lo
+    once the residual is small, and stops only on the true residual.
+
+    The paper fixes no precision below its MATLAB double; this is the mixed
+    form of the interface solve (FP64 Schur complements early, a low-precision
+    copy late), built from two published results:
+      * relaxation in inexact Krylov methods (Bouras & Fraysse 2005; van den
+        Eshof & Sleijpen 2004): the error allowed in the operator grows as the
+        residual falls, so S is applied until ||r|| <= switch * ref_norm and
+        S_lo from then on;
+      * reliable updates (Sleijpen & van der Vorst 1996): after the switch,
+        whenever the recursive residual has fallen below delta times its
+        largest value since the last replacement, or below the tolerance, it
+        is replaced by the true residual g - S x computed with S; the search
+        direction is kept, so the Krylov space is not restarted.
+    The decisions (switch, replacement, stop) are taken every check_every
+    iterations and whenever the recursive residual meets the tolerance.  In
+    the S phase the stopping test is the textbook one; in the S_lo phase the
+    iteration stops only after a replacement shows ||g - S x|| <= tol *
+    ref_norm.  With switch = 0 and check_every = 1 this is `pcg` operation for
+    operation.
+
+    Returns (x, iterations, iterations with S_lo, replacements, history of
+    ||r||_2 after each iteration)."""
+    x = np.zeros_like(g)
+    r = g.copy()
+    ref = np.linalg.norm(g) if ref_norm is None else ref_norm
+    hist = [np.linalg.norm(r)]
+    if hist[-1] <= tol * ref:
+        return x, 0, 0, 0, hist
+    z = apply_P(r)
+    p = z.copy()
+    rz = r @ z
+    lo = False
+    r_max = hist[-1]
+    it = n_lo = n_true = 0
+    while it < max_it:
+        q = (apply_S_lo if lo else apply_S)(p)
+        alpha = rz / (p @ q)
+        x += alpha * p
+        r -= alpha * q
+        it += 1
+        n_lo += lo
+        rn = np.linalg.norm(r)
+        if it % check_every == 0 or rn <= tol * ref:
+            if not lo and rn <= tol * ref:
+                hist.append(rn)
+                break
+            if not lo and rn <= switch * ref:
+                lo = True
+                r_max = rn
+            elif lo and (rn < delta * r_max or rn <= tol * ref):
+                r = g - apply_S(x)
+                n_true += 1
+                rn = np.linalg.norm(r)
+                r_max = rn
+                if rn <= tol * ref:
+                    hist.append(rn)
+                    break
+            r_max = max(r_max, rn)
+        hist.append(rn)
+        z = apply_P(r)
+        rz_new = r @ z
+        p = z + (rz_new / rz) * p
+        rz = rz_new
+    return x, it, n_lo, n_true, hist
 
 
 def dd_solve(dd, precond, f, tol=1e-12, max_it=5000, ref="f"):
