@@ -64,7 +64,9 @@ typedef enum {
  * MIXED: FP64 factors and local Schur complements, which are stored and
  *       applied in FP32 inside PCG (FP64 vectors and dot products); condensation,
  *       back-substitution and the refinement residual stay FP64.  Where the
- *       explicit form is unavailable it behaves as FP64. */
+ *       explicit form is unavailable it behaves as FP64.  With
+ *       ddel_options.relax_switch > 0 the FP32 copies enter only the late
+ *       iterations of one PCG that stops on an FP64 residual (relaxed form). */
 typedef enum { DDEL_FP64 = 0, DDEL_FP32 = 1, DDEL_MIXED = 2 } ddel_precision;
 typedef enum { DDEL_SCHUR_IMPLICIT = 0, DDEL_SCHUR_EXPLICIT = 1, DDEL_SCHUR_AUTO = 2 } ddel_schur_mode;
 /* Initial iterate of ddel_solve: ZERO (u = 0), WARM (the previous converged
@@ -150,6 +152,16 @@ typedef struct {
                           double-float): 1, 2 or 4 (rows per CTA = ring / split, at least
                           32); 0: by ring size, one for rings of 64, two for 128 and 256
                           (0); the persistent batch runs the default shape only */
+  double relax_switch; /* MIXED precision, explicit 2D form, no coarse space: > 0 runs
+                          one relaxed PCG instead of refinement cycles -- the FP64 Schur
+                          complements until the recursive residual is below
+                          relax_switch * ||f||, then their FP32 copies, with reliable
+                          updates (r = g - S x with the FP64 operator) whenever the
+                          residual has fallen by relax_delta since the last one and when
+                          it converges; it stops only on such a true residual, and goes
+                          back to the FP64 operator if three updates in a row bring no
+                          new low.  0: refinement cycles as described under MIXED (0) */
+  double relax_delta;  /* residual reduction between reliable updates (0.1) */
 } ddel_options;
 
 typedef struct {
@@ -165,6 +177,8 @@ typedef struct {
   double t_condense_ms, t_pcg_ms, t_backsub_ms, t_verify_ms, t_total_ms;
   int coarse_k;        /* coarse dimension used by the interface PCG (0: none) */
   int x0_used;         /* cycles whose PCG started from the Galerkin guess */
+  int low_iters;       /* relaxed PCG: iterations with the FP32 Schur complements */
+  int replacements;    /* relaxed PCG: reliable updates (FP64 residual replacements) */
 } ddel_stats;
 
 typedef struct {

@@ -76,6 +76,10 @@ struct ddel_ctx {
   bool graph_explicit[2] = {false, false};
   bool graph_apply32[2] = {false, false};
   int graph_iters = 0;
+  // relaxed MIXED PCG: iterations with the FP32-stored S_i (FP64 factors, no
+  // coarse space), captured beside graph[0]
+  cudaGraphExec_t graph_lo = nullptr;
+  int graph_lo_iters = 0, graph_lo_split = 0;
   int64_t launches = 0;           // kernel launches issued (graph-contained ones included)
   int64_t launches_at_assemble = 0;
   cudaEvent_t ev[11] = {};        // [8], [9]: around the last ddel_factor; [7], [10]: PCG state copies
@@ -167,6 +171,7 @@ __global__ void set_tol_kernel(PcgState* st, const double* nrm, double tol, doub
   st->done = 0;
   st->status = 0;
   st->it = 0;
+  st->replaced_ok = 0;
 }
 
 __global__ void set_tol_abs_kernel(PcgState* st, double tol_abs, int max_it) {
@@ -296,12 +301,12 @@ int pcg_start(ddel_ctx* ctx, int prec, const double* g, bool apply32) {
 
 // Issues check_every iterations and the copy of the PCG state to the host
 // into h_st[slot] (asynchronous; ctx->ev[7] for slot 0, ctx->ev[10] for slot
-// 1, is recorded after the copy).
-int pcg_issue(ddel_ctx* ctx, int prec, bool apply32, int slot = 0) {
+// 1, is recorded after the copy).  lo_graph: the relaxed PCG's FP32 graph.
+int pcg_issue(ddel_ctx* ctx, int prec, bool apply32, int slot = 0, bool lo_graph = false) {
   cudaStream_t s = ctx->stream;
   const int per = pcg_per(ctx);
   if (ctx->opt.use_graph) {
-    CK(cudaGraphLaunch(ctx->graph[prec], s));
+    CK(cudaGraphLaunch(lo_graph ? ctx->graph_lo : ctx->graph[prec], s));
   } else {
     for (int i = 0; i < per; ++i) pcg_iteration(ctx, prec, apply32, i & 1);
   }
@@ -341,6 +346,139 @@ int pcg_run(ddel_ctx* ctx, int prec, const double* g, int* iters, int* status,
   if (last) ctx->h_st[0] = ctx->h_st[1];
   *iters = ctx->h_st->it;
   *status = ctx->h_st->done ? ctx->h_st->status : DDEL_ENOCONV;
+  return DDEL_OK;
+}
+
+// The relaxed PCG's graph: check_every iterations with the FP32-stored S_i
+// of a FP64 context (no coarse space), kept beside graph[0].
+int ensure_graph_lo(ddel_ctx* ctx) {
+  const int per = pcg_per(ctx);
+  const int split = explicit_split(ctx->T, ctx->opt.schur_split);
+  if (ctx->graph_lo && (ctx->graph_lo_iters != per || ctx->graph_lo_split != split)) {
+    cudaGraphExecDestroy(ctx->graph_lo);
+    ctx->graph_lo = nullptr;
+  }
+  if (ctx->graph_lo) return DDEL_OK;
+  cudaGraph_t graph;
+  CK(cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal));
+  for (int i = 0; i < per; ++i) pcg_iteration(ctx, 0, true, i & 1);
+  CK(cudaStreamEndCapture(ctx->stream, &graph));
+  CK(cudaGraphInstantiate(&ctx->graph_lo, graph, 0));
+  cudaGraphDestroy(graph);
+  ctx->graph_lo_iters = per;
+  ctx->graph_lo_split = split;
+  return DDEL_OK;
+}
+
+__global__ void set_tol2_kernel(PcgState* st, double tol2) { st->tol2 = tol2; }
+
+// Reliable update after a whole batch: y = S x with the FP64 operator (into
+// the FP64 ring), then r = g - y, u = S~^-1 r and the corrected step length
+// (launch_pcg_replace); waits for the state.
+int pcg_replace(ddel_ctx* ctx, const double* g, double tol2) {
+  cudaStream_t s = ctx->stream;
+  SchurIO io = make_io(ctx);
+  io.x = ctx->x;
+  schur_dispatch(ctx, 0, false, io, s);
+  launch_pcg_replace(ctx->T, ctx->F, g, (const double*)ring_of(ctx, 0), ctx->x, ctx->r, ctx->z, ctx->p, ctx->sv,
+                     ctx->st, pcg_partials(ctx, 0), s, ctx->nupd, tol2);
+  ctx->launches += 3;
+  CK(cudaMemcpyAsync(ctx->h_st, ctx->st, sizeof(PcgState), cudaMemcpyDeviceToHost, s));
+  CK(cudaEventRecord(ctx->ev[7], s));
+  CK(cudaEventSynchronize(ctx->ev[7]));
+  return DDEL_OK;
+}
+
+// Relaxed mixed-precision PCG on S x = g: the Schur apply may lose accuracy
+// as the residual falls (relaxation of inexact Krylov methods, van den Eshof
+// and Sleijpen 2004), so the FP64 S_i serve until the recursive residual is
+// below relax_switch ||f|| and their FP32 copies after; the recursive residual
+// is replaced by the true one, computed with the FP64 operator, whenever it
+// has fallen by relax_delta since the last replacement or meets the
+// tolerance (reliable updates, Sleijpen and van der Vorst 1996), and the
+// iteration stops only on a replaced residual.  The FP32 phase runs with a
+// zero device tolerance, so that its batches never stop early and each
+// replacement follows a whole batch; decisions are taken between batches of
+// check_every iterations, each read back before the next is issued.  Three
+// replacements in a row without a new low of the true residual return the
+// iteration to the FP64 operator (and the device tolerance) for good.
+int pcg_run_relaxed(ddel_ctx* ctx, const double* g, int* iters, int* status, int* low_iters, int* replacements) {
+  int rc = pcg_start(ctx, 0, g, false);
+  if (rc) return rc;
+  const bool use_graph = ctx->opt.use_graph != 0;
+  if (use_graph) {
+    rc = ensure_graph_lo(ctx);
+    if (rc) return rc;
+  }
+  cudaStream_t s = ctx->stream;
+  const int per = pcg_per(ctx);
+  const int max_checks = ctx->opt.max_it / per + 2;
+  const double delta = ctx->opt.relax_delta > 0.0 && ctx->opt.relax_delta < 1.0 ? ctx->opt.relax_delta : 0.1;
+  bool lo = false, allow_lo = true;
+  double tol2 = -1.0, tau = 0.0, r_max = 0.0, best = INFINITY;
+  int stall = 0, it_prev = 0;
+  *low_iters = 0;
+  *replacements = 0;
+  *status = DDEL_ENOCONV;
+  for (int chk = 0; chk < max_checks; ++chk) {
+    rc = pcg_issue(ctx, 0, lo, 0, lo && use_graph);
+    if (rc) return rc;
+    CK(cudaEventSynchronize(ctx->ev[7]));
+    const PcgState h = ctx->h_st[0];
+    if (lo) *low_iters += h.it - it_prev;
+    it_prev = h.it;
+    if (tol2 < 0.0) {
+      // the device tolerance of this cycle, tol2 = (tol ||f|| / 2)^2
+      tol2 = h.tol2;
+      tau = ctx->opt.tol > 0.0 ? ctx->opt.relax_switch * 2.0 * std::sqrt(tol2) / ctx->opt.tol : 0.0;
+    }
+    if (h.done) {
+      // FP64 phase: converged (the textbook stop) or an error status; FP32
+      // phase (zero tolerance): an error status, or an exactly zero recursive
+      // residual, which says nothing of the true one
+      *status = (lo && h.status == 0) ? DDEL_ENOCONV : h.status;
+      break;
+    }
+    const double rn = std::sqrt(h.rr);
+    if (!lo) {
+      if (allow_lo && rn <= tau) {
+        lo = true;
+        r_max = rn;
+        set_tol2_kernel<<<1, 1, 0, s>>>(ctx->st, 0.0);
+        ctx->launches += 1;
+      }
+      continue;
+    }
+    if (rn * rn <= tol2 || rn < delta * r_max) {
+      rc = pcg_replace(ctx, g, tol2);
+      if (rc) return rc;
+      ++*replacements;
+      const PcgState h2 = ctx->h_st[0];
+      if (h2.done) {  // breakdown in the corrected step
+        *status = h2.status;
+        break;
+      }
+      if (h2.replaced_ok) {
+        *status = DDEL_OK;
+        break;
+      }
+      const double rt = std::sqrt(h2.rr);
+      r_max = rt;
+      if (rt < best) {
+        best = rt;
+        stall = 0;
+      } else if (++stall >= 3) {
+        lo = false;
+        allow_lo = false;
+        set_tol2_kernel<<<1, 1, 0, s>>>(ctx->st, tol2);
+        ctx->launches += 1;
+      }
+      continue;
+    }
+    r_max = std::max(r_max, rn);
+  }
+  CK(cudaGetLastError());
+  *iters = ctx->h_st->it;
   return DDEL_OK;
 }
 
@@ -637,6 +775,8 @@ void ddel_default_options(ddel_options* o) {
   o->check_every = 16;
   o->tensor_form = 1;
   o->schur_split = 0;
+  o->relax_switch = 0.0;
+  o->relax_delta = 0.1;
 }
 
 const char* ddel_strerror(int s) {
@@ -666,10 +806,16 @@ int ddel_create(const ddel_mesh* mesh, const ddel_material* mat, const ddel_bc* 
   if (!ctx) return DDEL_ENOMEM;
   ctx->mesh = *mesh;
   ctx->mat = *mat;
-  if (opt)
+  if (opt) {
+    if (!(opt->relax_switch >= 0.0) || !std::isfinite(opt->relax_switch)) {
+      g_create_error = "relax_switch must be a finite value >= 0";
+      delete ctx;
+      return DDEL_EINVAL;
+    }
     ctx->opt = *opt;
-  else
+  } else {
     ddel_default_options(&ctx->opt);
+  }
   const int ne[3] = {mesh->nx, mesh->ny, mesh->nz};
   std::string msg = build_setup(mesh->dim, ne, mesh->sub, mat->E, mat->nu, mat->plane_stress,
                                 bc->clamp_faces, bc->fixed_dof, bc->n_point, bc->point_node,
@@ -811,6 +957,7 @@ void ddel_destroy(ddel_ctx* ctx) {
   ctx->learners.clear();
   for (auto& g : ctx->graph)
     if (g) cudaGraphExecDestroy(g);
+  if (ctx->graph_lo) cudaGraphExecDestroy(ctx->graph_lo);
   for (void* p : ctx->allocs) cudaFree(p);
   for (void* p : ctx->factor)
     if (p) cudaFree(p);
@@ -863,6 +1010,8 @@ int ddel_get_info(const ddel_ctx* ctx, ddel_info_t* info) {
 int ddel_set_options(ddel_ctx* ctx, const ddel_options* opt) {
   if (!ctx || !opt) return DDEL_EINVAL;
   if (opt->theta != ctx->opt.theta) return fail(ctx, DDEL_EINVAL, "theta is fixed at creation");
+  if (!(opt->relax_switch >= 0.0) || !std::isfinite(opt->relax_switch))
+    return fail(ctx, DDEL_EINVAL, "relax_switch must be a finite value >= 0");
   if (opt->schur_mode != ctx->opt.schur_mode || opt->precision != ctx->opt.precision)
     ctx->factored[0] = ctx->factored[1] = false;  // refactor to switch forms
   ctx->opt = *opt;
@@ -944,8 +1093,10 @@ int ddel_solve(ddel_ctx* ctx, const double* f, double* u, int on_device, ddel_st
   int prec = ctx->active_prec;
   bool apply32 = ctx->mixed_ready && prec == 0;
   for (int cyc = 0; cyc < ctx->opt.max_cycles; ++cyc) {
+    // relaxed MIXED: one PCG to the final tolerance (no inner tolerance)
+    const bool relaxed = apply32 && ctx->opt.relax_switch > 0.0 && ctx->ck_in == 0;
     set_tol_kernel<<<1, 1, 0, s>>>(ctx->st, ctx->nrm, ctx->opt.tol, ctx->opt.inner_tol,
-                                   (prec == 1 || apply32) ? 1 : 0, ctx->opt.max_it);
+                                   (prec == 1 || (apply32 && !relaxed)) ? 1 : 0, ctx->opt.max_it);
     ctx->launches += 1;
     CK(cudaEventRecord(ctx->ev[1], s));
     if (ctx->ck_in > 0 && ctx->coarse_prec != prec * 2 + (apply32 ? 1 : 0)) {
@@ -954,10 +1105,13 @@ int ddel_solve(ddel_ctx* ctx, const double* f, double* u, int on_device, ddel_st
     }
     condense(ctx, prec, ctx->d_r, ctx->g);
     CK(cudaEventRecord(ctx->ev[2], s));
-    int it = 0, pst = 0;
-    int rc = pcg_run(ctx, prec, ctx->g, &it, &pst, apply32);
+    int it = 0, pst = 0, low_it = 0, n_repl = 0;
+    int rc = relaxed ? pcg_run_relaxed(ctx, ctx->g, &it, &pst, &low_it, &n_repl)
+                     : pcg_run(ctx, prec, ctx->g, &it, &pst, apply32);
     if (rc) return rc;
     st.iters += it;
+    st.low_iters += low_it;
+    st.replacements += n_repl;
     st.coarse_k = ctx->ck;
     if (ctx->ck > 0 && (ctx->coarse_flags & DDEL_COARSE_X0)) st.x0_used += ctx->h_st->x0_used;
     if (pst == DDEL_EBREAKDOWN && ctx->ck > 0) {

@@ -1374,7 +1374,12 @@ __global__ void gamma_sum_kernel(DevTables t, const T* __restrict__ ring,
 // kernels see only u^; the update adds Q cc to u and S Q cc to w = S u^, and
 // forms gamma = gamma^ + (Q^T r)^T cc and delta = (S u, u) = delta^ +
 // 2 cc^T (S Q)^T u^ + cc^T E cc from the partial sums of Q^T r and (S Q)^T u^.
-template <typename T, bool INIT, int KC>
+// REPL (with INIT, no coarse space): the reliable update of the relaxed
+// mixed-precision PCG -- r = g - (S x from the ring of an accurate apply of
+// the current x), x, p and s kept, u = S~^-1 r with the partials of gamma and
+// rr, and two more rows: (u, s) and (p, s) for the corrected step length
+// (pcg_replace_fix_kernel).
+template <typename T, bool INIT, int KC, bool REPL = false>
 __global__ void __launch_bounds__(kRedThreads) pcg_cg_kernel(DevTables t, DevFields fld,
                                                              const double* __restrict__ gin,
                                                              const T* __restrict__ ring, double* x,
@@ -1383,8 +1388,9 @@ __global__ void __launch_bounds__(kRedThreads) pcg_cg_kernel(DevTables t, DevFie
                                                              const double* __restrict__ pd, int nd,
                                                              const double* __restrict__ pu_in,
                                                              double* __restrict__ pu_out, int par) {
+  static_assert(!REPL || (INIT && KC == 0), "the replacement runs without a coarse space");
   const int done = st->done;  // tested once the prologue's loads are in flight
-  constexpr int NV = 2 + 2 * KC, NP = 3 + 2 * KC;
+  constexpr int NV = 2 + 2 * KC + (REPL ? 2 : 0), NP = 3 + 2 * KC + (REPL ? 1 : 0);
   extern __shared__ double rw_all[];  // (blockDim/32) * max_blk_n doubles, then as many float2
   __shared__ double red[NP * kRedThreads];  // tree sums (prologue NP values, epilogue NV)
   __shared__ double sums[NP];               // delta^, gamma^, rr, Q^T r, (S Q)^T u^
@@ -1496,7 +1502,7 @@ __global__ void __launch_bounds__(kRedThreads) pcg_cg_kernel(DevTables t, DevFie
     if (done) return;
 #pragma unroll
     for (int i = 0; i < KC; ++i) cc[i] = (i < k && cd.x0) ? st->c0[i] : 0.0;
-    if (blockIdx.x == 0 && threadIdx.x == 0) st->kS = 0;
+    if (!REPL && blockIdx.x == 0 && threadIdx.x == 0) st->kS = 0;
   }
   auto coarse = [&](const double* V, int64_t g) -> double {
     double v = 0.0;
@@ -1510,7 +1516,9 @@ __global__ void __launch_bounds__(kRedThreads) pcg_cg_kernel(DevTables t, DevFie
   for (int i = 0; i < NV; ++i) acc[i] = 0.0;
   auto step = [&](int64_t g) -> double {
     double rg;
-    if (INIT) {
+    if constexpr (REPL) {
+      rg = gin[g] - ring_sum<T>(t, ring, g);
+    } else if (INIT) {
       p[g] = 0.0;
       sv[g] = 0.0;
       if (KC > 0) {
@@ -1544,6 +1552,11 @@ __global__ void __launch_bounds__(kRedThreads) pcg_cg_kernel(DevTables t, DevFie
 #pragma unroll
     for (int i = 0; i < KC; ++i)
       if (i < k) acc[2 + KC + i] += cd.SQ[i * t.n_gamma + g] * ui;
+    if constexpr (REPL) {
+      const double sg = sv[g];
+      acc[NV - 2] += ui * sg;
+      acc[NV - 1] += p[g] * sg;
+    }
   };
   const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int nw = (gridDim.x * blockDim.x) >> 5;
@@ -2586,6 +2599,49 @@ void launch_pcg_init(const DevTables& t, const DevFields& fld, const double* g, 
       pcg_cg_kernel<double, true, 0><<<nblk, kRedThreads, sm, st>>>(t, fld, g, nullptr, x, r, u, p, sv, s, cd,
                                                                      nullptr, 0, nullptr, pu_out, 1);
   }
+}
+
+// Step length after a reliable update.  The Chronopoulos-Gear denominator
+// delta - beta gamma / alpha_prev equals (p, S p) only while the new residual
+// is orthogonal to the previous search direction, which a replaced residual
+// is not; the exact value is delta + 2 beta (u, s_prev) + beta^2 (p_prev,
+// s_prev).  Stores the 1 / alpha that makes the next update's formula give
+// it.  The replacement follows a whole batch of an even number of iterations
+// (the relaxed PCG runs its low-precision phase with a zero device
+// tolerance, so no batch stops early): the last update wrote slot 1, which
+// the next batch's first update reads.  Also the true rr and whether it meets
+// tol2 (replaced_ok); an error status (done) is kept.  One block.
+__global__ void __launch_bounds__(kRedThreads) pcg_replace_fix_kernel(PcgState* st, const double* __restrict__ pu,
+                                                                      int nblk, double tol2) {
+  __shared__ double red[4 * kRedThreads];
+  double a[4];
+#pragma unroll
+  for (int v = 0; v < 4; ++v) {
+    a[v] = 0.0;
+    for (int b = threadIdx.x; b < nblk; b += kRedThreads) a[v] += pu[(size_t)v * nblk + b];
+  }
+  block_tree_sum<4>(a, 4, red);
+  if (threadIdx.x != 0) return;
+  const double gamma = red[0], rr = red[kRedThreads], us = red[2 * kRedThreads], ps = red[3 * kRedThreads];
+  st->rr = rr;
+  st->replaced_ok = rr <= tol2 ? 1 : 0;
+  if (st->done) return;  // breakdown or iteration cap: the host stops
+  const double beta = gamma * st->ginv_s[1];
+  const double ainv = -(2.0 * us + beta * ps) / gamma;
+  if (st->kS <= 0 || !isfinite(rr) || !(gamma > 0.0) || !isfinite(ainv)) {
+    st->done = 1;
+    st->status = -6;  // breakdown
+    return;
+  }
+  st->ainv_s[1] = ainv;
+}
+
+void launch_pcg_replace(const DevTables& t, const DevFields& fld, const double* g, const double* ring, double* x,
+                        double* r, double* u, double* p, double* sv, PcgState* s, double* pu_out, cudaStream_t st,
+                        int nblk, double tol2) {
+  pcg_cg_kernel<double, true, 0, true><<<nblk, kRedThreads, update_smem(t), st>>>(
+      t, fld, g, ring, x, r, u, p, sv, s, CoarseDev(), nullptr, 0, nullptr, pu_out, 1);
+  pcg_replace_fix_kernel<<<1, kRedThreads, 0, st>>>(s, pu_out, nblk, tol2);
 }
 
 template <typename T>

@@ -62,6 +62,7 @@ struct PcgState {
   double* partials;  // scratch of grid_sum-based one-off kernels
   double c0[kMaxCoarse];  // coefficients of the initial guess x0 = Q c0
   int x0_used;
+  int replaced_ok;  // relaxed PCG: the last reliable update met the tolerance
 };
 
 // Coarse space of the interface PCG: orthonormal Q (k columns of n_gamma,
@@ -180,6 +181,15 @@ void launch_gamma_sum(const DevTables& t, int precision, const void* ring, const
 void launch_pcg_init(const DevTables& t, const DevFields& fld, const double* g, double* x, double* r,
                      double* u, double* p, double* sv, PcgState* s, double* pu_out, cudaStream_t st,
                      int nblk, const CoarseDev& cd = CoarseDev());
+// Reliable update of the relaxed mixed-precision PCG (no coarse space), after
+// a whole batch of iterations and an accurate Schur apply of x into the FP64
+// ring: r = g - S x, u = S~^-1 r and its partials (x, p, s kept), then the
+// step-length correction, the true rr and replaced_ok = (rr <= tol2) in the
+// state.  Nothing changes once the state is done (an error status).  Two
+// launches.
+void launch_pcg_replace(const DevTables& t, const DevFields& fld, const double* g, const double* ring, double* x,
+                        double* r, double* u, double* p, double* sv, PcgState* s, double* pu_out, cudaStream_t st,
+                        int nblk, double tol2);
 // Update j: pd holds the nd delta partials of the Schur kernel, pu_in the
 // update partials of iteration j (written by update j-1 or init), pu_out
 // receives those of j + 1; par = j & 1 (recurrence scalar slots).  Passing

@@ -46,7 +46,7 @@ class ddel_options(ctypes.Structure):
                 ("max_cycles", c_int), ("inner_tol", c_double), ("x0_mode", c_int),
                 ("schur_mode", c_int), ("use_graph", c_int), ("check_every", c_int),
                 ("tensor_form", c_int),
-                ("schur_split", c_int)]
+                ("schur_split", c_int), ("relax_switch", c_double), ("relax_delta", c_double)]
 
 
 class ddel_stats(ctypes.Structure):
@@ -55,7 +55,7 @@ class ddel_stats(ctypes.Structure):
                 ("t_factor_ms", c_double),
                 ("t_condense_ms", c_double), ("t_pcg_ms", c_double), ("t_backsub_ms", c_double),
                 ("t_verify_ms", c_double), ("t_total_ms", c_double), ("coarse_k", c_int),
-                ("x0_used", c_int)]
+                ("x0_used", c_int), ("low_iters", c_int), ("replacements", c_int)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

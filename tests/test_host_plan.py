@@ -47,6 +47,17 @@ def test_strerror_and_defaults():
     assert "positive definite" in ddel.ddel_strerror(-4)
     o = ddel.ddel_default_options()
     assert o.tol == 1e-8 and o.theta == 0.5 and o.precision == ddel.DDEL_FP64
+    assert o.relax_switch == 0.0 and o.relax_delta == 0.1  # relaxed MIXED PCG off
+
+
+def test_relaxed_switch_rejected_before_device_work():
+    # option validation of ddel_create runs on the host, before any device call
+    ddel = _lib()
+    cfg = workloads.small_config(64, 32, 16)
+    for bad in (-1.0, float("nan"), float("inf")):
+        with pytest.raises(ddel.DDELError) as e:
+            ddel.Solver(cfg, precision=ddel.DDEL_MIXED, relax_switch=bad)
+        assert e.value.code == ddel.DDEL_EINVAL and "relax_switch" in str(e.value)
 
 
 def test_plan_rejects_bad_input():
