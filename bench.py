@@ -192,7 +192,12 @@ THETA_OPT_3D = 0.3  # the same for the 96x48x48 H8 workload (see solve_3d)
 
 # The forms of the 512x256 solve: (name, precision, schur_mode, dtype, form, theta,
 # further solver options)
-RELAX_SWITCH = 1e-2  # relaxed MIXED PCG: FP32 S_i once ||r|| <= 1e-2 ||f||
+# relaxed MIXED PCG: FP32 S_i once ||r|| <= 1e-2 ||f||, the residual replaced
+# after every fivefold drop.  Measured on this workload (ms per solve):
+# switch 3e-3 / 5e-3 / 1e-2 / 1.5e-2 / 2e-2 at drop 0.1 or 0.2 -> 53.7 / 53.5
+# / 50.3-51.2 / 52.5 / 59.8; drop 0.1 / 0.2 / 0.3 / 0.5 at switch 1e-2 ->
+# 52.8 / 50.3-51.2 / 52.0 / 51.8
+RELAX_SWITCH, RELAX_DELTA = 1e-2, 0.2
 FORMS = (
     ("fp64", 0, 1, "f64", "plain FP64: S_i formed and applied in native FP64, theta = H_OPT 0.6", THETA_OPT, {}),
     ("df", 0, 2, "df32x2 operator + f64 Krylov",
@@ -200,8 +205,8 @@ FORMS = (
      "FP64 refinement, theta = H_OPT 0.6", THETA_OPT, {}),
     ("mixed_relaxed", 2, 1, "f64 operator, f32 copy late + f64 reliable updates",
      "FP64 factors and S_i applied in native FP64 until the interface residual is below 1e-2 ||f||, then "
-     "their FP32 copies, with the residual replaced by the FP64 one after every tenfold drop; stops on "
-     "an FP64 residual, theta = H_OPT 0.6", THETA_OPT, {"relax_switch": RELAX_SWITCH}),
+     "their FP32 copies, with the residual replaced by the FP64 one after every fivefold drop; stops on "
+     "an FP64 residual, theta = H_OPT 0.6", THETA_OPT, {"relax_switch": RELAX_SWITCH, "relax_delta": RELAX_DELTA}),
     ("fp32_refined", 1, 2, "f32 operator + f64 Krylov + f64 refinement",
      "FP32 factors, S_i and applies; FP64 PCG vectors, residual and iterative refinement, theta = H_OPT 0.6",
      THETA_OPT, {}),
