@@ -645,13 +645,13 @@ def launches_per_step(s):
 
 
 # DRAM bytes (read + write) of one launch of the explicit Schur kernels on
-# this workload, each from one `ncu --set full --clock-control none` capture
-# (cold L2, the kernels as built now): schur_explicit_df_kernel<128> 67.897088
-# MB read + 0.246272 MB written; schur_explicit_f64_kernel<128> (one
-# accumulator per row, padded column groups skipped) 65.995008 MB read +
-# 0.152832 MB written.
-TRAFFIC = {"schur_explicit_df_kernel": 67897088 + 246272,
-           "schur_explicit_f64_kernel": 65995008 + 152832}
+# this workload, from one `ncu --set full --clock-control none` capture of the
+# kernel as built, or null once the kernel has changed since the counters
+# were taken.  The last captures (schur_explicit_df_kernel<128>: 67.897088 MB
+# read + 0.246272 MB written; schur_explicit_f64_kernel<128>: 65.995008 MB +
+# 0.152832 MB) predate both kernels' templating on the tile shape (1, 2 or 4
+# CTAs per subdomain), so both report null until recaptured.
+TRAFFIC = {}
 
 
 def kernel_roofline(ddel, s, stream, torch):
