@@ -6,6 +6,8 @@ synthetic workloads through the C ABI and prints the statistics.
     python -m paper_1501_06211_gb300.run --workload c4 --topopt-steps 40 --tol-eta 0.1
     python -m paper_1501_06211_gb300.run --workload c4 --topopt-steps 40 --tol-eta 0.1 \
         --learner history --coarse x0
+    python -m paper_1501_06211_gb300.run --workload c1 --precision mixed --schur explicit \
+        --theta 0.6 --relax-switch 1e-2 --relax-delta 0.2
 
 Run from the repository root (the workload generators live in `workloads/`).
 """
@@ -30,6 +32,12 @@ def main(argv=None):
                     help="learner coarse space: Galerkin initial guess only, or with the correction")
     ap.add_argument("--sub", type=int, default=0,
                     help="subdomain edge in elements instead of the workload's own (0: keep)")
+    ap.add_argument("--theta", type=float, default=0.5, help="theta of the face-local preconditioner")
+    ap.add_argument("--relax-switch", type=float, default=0.0,
+                    help="mixed precision: FP32 Schur complements once ||r|| <= this * ||f|| "
+                         "(relaxed PCG with FP64 reliable updates; 0: refinement cycles)")
+    ap.add_argument("--relax-delta", type=float, default=0.1,
+                    help="relaxed PCG: residual drop between FP64 replacements")
     args = ap.parse_args(argv)
     sys.path.insert(0, os.getcwd())
     import torch
@@ -41,7 +49,8 @@ def main(argv=None):
         cfg["sub"] = args.sub
     prec = {"fp64": ddel.DDEL_FP64, "fp32": ddel.DDEL_FP32, "mixed": ddel.DDEL_MIXED}[args.precision]
     mode = {"implicit": 0, "explicit": 1, "auto": 2}[args.schur]
-    s = ddel.Solver(cfg, precision=prec, schur_mode=mode, tol=args.tol, max_it=20000)
+    s = ddel.Solver(cfg, precision=prec, schur_mode=mode, tol=args.tol, max_it=20000, theta=args.theta,
+                    relax_switch=args.relax_switch, relax_delta=args.relax_delta)
     if args.topopt_steps > 0:
         learner = None
         if args.learner != "none":
