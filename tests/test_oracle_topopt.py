@@ -2,10 +2,12 @@
 
 Independent checks: filter partition of unity, adjoint sensitivities against
 central finite differences of the compliance, exact volume after the OC
-bisection, bounds/move limits, compliance = energy, and the (empirical,
+bisection, bounds/move limits, the OC square-root update against its closed
+form (the multiplier cancels between elements; uniform start), compliance = energy, and the (empirical,
 reading Q22) monotone decrease of compliance over the first Picard steps.
 """
 import numpy as np
+import pytest
 
 from oracle import direct, fem, topopt
 import workloads
@@ -82,6 +84,30 @@ def test_oc_volume_bounds_move():
     free = (new > np.maximum(1e-3, rho - 0.2) + 1e-12) & (new < np.minimum(1, rho + 0.2) - 1e-12)
     assert free.any()
     assert np.allclose(new[free], rho[free] * np.sqrt(-dc[free] / (lam * dv[free])), rtol=1e-12)
+
+
+def test_oc_update_is_the_square_root_fixed_point():
+    # Sec. 5's optimality-criteria step rho_e <- rho_e (-dc_e / (lam dv_e))^(1/2)
+    # with lam set by the volume: away from the move limits the multiplier
+    # cancels between elements, so new_e / new_f = sqrt(dc_e / dc_f) exactly,
+    # and for a uniform start rho = v with dv = 1 the volume fixes
+    # lam = mean(sqrt(-dc))^2 in closed form
+    rng = np.random.default_rng(7)
+    n = 40
+    c = rng.uniform(0.8, 1.25, n)  # -dc: every factor sqrt(c / lam) inside [0.6, 1.4]
+    rho = np.full(n, 0.5)
+    new, lam = topopt.oc_update(rho, -c, np.ones(n), 0.5 * n, rho_min=1e-3, move=0.2, steps=200)
+    assert np.all((new > 0.3) & (new < 0.7))  # no move limit active
+    assert np.allclose(new / new[0], np.sqrt(c / c[0]), rtol=1e-12)
+    assert lam == pytest.approx(np.mean(np.sqrt(c)) ** 2, rel=1e-10)
+    assert new.sum() == pytest.approx(0.5 * n, rel=1e-10)
+    # large sensitivities push elements onto the move limit, zero ones onto
+    # the lower move bound
+    c2 = c.copy()
+    c2[:3] = 100.0
+    c2[3:6] = 0.0
+    new2, _ = topopt.oc_update(rho, -c2, np.ones(n), 0.5 * n, rho_min=1e-3, move=0.2, steps=200)
+    assert np.allclose(new2[:3], 0.7) and np.allclose(new2[3:6], 0.3)
 
 
 def test_compliance_decreases_mbb():
