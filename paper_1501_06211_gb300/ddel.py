@@ -49,6 +49,17 @@ class ddel_options(ctypes.Structure):
                 ("schur_split", c_int), ("relax_switch", c_double), ("relax_delta", c_double)]
 
 
+def _set_fields(opt, options):
+    """Copies keyword options into a ddel_options structure; a name that is
+    not one of its fields raises (ctypes would keep it as a plain attribute
+    that the library never sees)."""
+    unknown = sorted(set(options) - {k for k, _ in ddel_options._fields_})
+    if unknown:
+        raise TypeError("unknown ddel_options field(s): " + ", ".join(unknown))
+    for k, v in options.items():
+        setattr(opt, k, v)
+
+
 class ddel_stats(ctypes.Structure):
     _fields_ = [("status", c_int), ("iters", c_int), ("cycles", c_int), ("relres", c_double),
                 ("pcg_relres", c_double), ("bad_subdomain", c_int), ("fallback", c_int),
@@ -658,8 +669,7 @@ class Solver:
         self.mat = ddel_material(cfg["E"], cfg["nu"], 1 if plane_stress else 0, cfg["p"],
                                  cfg.get("rho_min", 1e-3))
         self.opt = ddel_default_options()
-        for k, v in options.items():
-            setattr(self.opt, k, v)
+        _set_fields(self.opt, options)
         bc = _BC(ne, cfg["bc"])
         code, self.h = ddel_create(self.mesh, self.mat, bc.bc, self.opt, stream)
         _check(code)
@@ -677,8 +687,7 @@ class Solver:
             pass
 
     def set_options(self, **options):
-        for k, v in options.items():
-            setattr(self.opt, k, v)
+        _set_fields(self.opt, options)
         _check(ddel_set_options(self.h, self.opt), self.h)
 
     @property

@@ -50,6 +50,15 @@ def test_strerror_and_defaults():
     assert o.relax_switch == 0.0 and o.relax_delta == 0.1  # relaxed MIXED PCG off
 
 
+def test_unknown_option_names_are_rejected():
+    # a misspelt option would otherwise stay a Python attribute of the ctypes
+    # structure and never reach the library
+    ddel = _lib()
+    cfg = workloads.small_config(64, 32, 16)
+    with pytest.raises(TypeError, match="relax_swich"):
+        ddel.Solver(cfg, precision=ddel.DDEL_MIXED, relax_swich=1e-2)
+
+
 def test_relaxed_switch_rejected_before_device_work():
     # option validation of ddel_create runs on the host, before any device call
     ddel = _lib()
