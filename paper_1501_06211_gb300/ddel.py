@@ -50,12 +50,12 @@ class ddel_options(ctypes.Structure):
 
 
 def _set_fields(opt, options):
-    """Copies keyword options into a ddel_options structure; a name that is
-    not one of its fields raises (ctypes would keep it as a plain attribute
-    that the library never sees)."""
-    unknown = sorted(set(options) - {k for k, _ in ddel_options._fields_})
+    """Copies keyword options into an options structure; a name that is not
+    one of its fields raises (ctypes would keep it as a plain attribute that
+    the library never sees)."""
+    unknown = sorted(set(options) - {k for k, _ in type(opt)._fields_})
     if unknown:
-        raise TypeError("unknown ddel_options field(s): " + ", ".join(unknown))
+        raise TypeError(f"unknown {type(opt).__name__} field(s): " + ", ".join(unknown))
     for k, v in options.items():
         setattr(opt, k, v)
 
@@ -378,8 +378,7 @@ def ddel_kernel_info(h):
 def ddel_default_gmres_options(**kw):
     o = ddel_gmres_options()
     _lib.ddel_default_gmres_options(ctypes.byref(o))
-    for k, v in kw.items():
-        setattr(o, k, v)
+    _set_fields(o, kw)
     return o
 
 
@@ -521,11 +520,10 @@ class Learner:
 
     def __init__(self, solver, **options):
         self.opt = ddel_learner_default_options()
-        for k, v in options.items():
-            if k == "widths":
-                self.opt.widths = (c_int * 4)(*v)
-            else:
-                setattr(self.opt, k, v)
+        options = dict(options)
+        if "widths" in options:
+            self.opt.widths = (c_int * 4)(*options.pop("widths"))
+        _set_fields(self.opt, options)
         code, self.h = ddel_learner_create(solver.h, self.opt)
         _check(code, solver.h)
         self._solver = solver  # the context must outlive the learner

@@ -57,6 +57,9 @@ def test_unknown_option_names_are_rejected():
     cfg = workloads.small_config(64, 32, 16)
     with pytest.raises(TypeError, match="relax_swich"):
         ddel.Solver(cfg, precision=ddel.DDEL_MIXED, relax_swich=1e-2)
+    with pytest.raises(TypeError, match="lanczos_step$"):
+        ddel.ddel_default_gmres_options(lanczos_step=8)
+    assert ddel.ddel_default_gmres_options(lanczos_steps=8).lanczos_steps == 8
 
 
 def test_relaxed_switch_rejected_before_device_work():
